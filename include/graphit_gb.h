@@ -1,0 +1,288 @@
+/*
+ * graphit_gb.h -- C ABI of the GB300 edgeset-apply library.
+ *
+ * The operations follow the operator API of GraphIt (Zhang et al., OOPSLA 2018):
+ * the vertexset/edgeset operators of Table 2 (size, from, to, srcFilter,
+ * dstFilter, apply, applyModified with optional deduplication) and the
+ * scheduling choices of Table 3 (configApplyDirection, configApplyParallelization,
+ * configApplyDenseVertexSet, configApplyNumSSG), executed by hand-written CUDA
+ * kernels for sm_103a.
+ *
+ * Conventions for every call:
+ *   - The return value is a status: GI_OK (0) or a negative GI_ERR_* code.  No
+ *     exception or abort crosses the ABI.  gi_last_error() returns a message for
+ *     the calling thread's most recent failure.
+ *   - "dev" pointers are CUDA device pointers owned by the caller; the library
+ *     never frees them and reads/writes them only inside the call's stream order.
+ *   - Handles (gi_graph, gi_vset) are owned by the library and released with the
+ *     matching *_free call.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Work is enqueued on it; calls documented as "syncs" wait for it.
+ *   - Vertex ids and arc offsets are int32 (graphs with fewer than 2^31 arcs).
+ */
+#ifndef GRAPHIT_GB_H
+#define GRAPHIT_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status -- */
+#define GI_OK 0
+#define GI_ERR_INVALID_ARG (-1) /* NULL handle, bad size, unknown enum value        */
+#define GI_ERR_BAD_GRAPH (-2)   /* CSR/CSC failed validation (GI_VALIDATE)           */
+#define GI_ERR_OOM (-3)         /* device or pinned-host allocation failed           */
+#define GI_ERR_CUDA (-4)        /* a CUDA runtime call or kernel launch failed       */
+#define GI_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                */
+#define GI_ERR_UNSUPPORTED (-6) /* combination not implemented (e.g. m >= 2^31)      */
+
+/* Message of the calling thread's last failure ("" if none).  Never NULL. */
+const char *gi_last_error(void);
+/* Library version as major*10000 + minor*100 + patch. */
+int gi_version(void);
+
+/* ----------------------------------------------------------------- graph -- */
+typedef struct gi_graph gi_graph;
+
+#define GI_HOST_PTRS 0x1u /* input arrays are host memory (copied host-to-device)            */
+#define GI_DEV_PTRS 0x2u  /* input arrays are device memory (copied device-to-device)        */
+#define GI_SYMMETRIC 0x4u /* every arc (u,v) has its reverse: the in-edge view aliases CSR   */
+#define GI_VALIDATE 0x8u  /* check offsets/indices on the device; GI_ERR_BAD_GRAPH if bad    */
+
+/*
+ * Load a graph's out-edges in CSR form (the edgeset of Sec. 3; getOutNghs of the
+ * generated code in Sec. 6).  offsets[n+1] (offsets[0] = 0, non-decreasing,
+ * offsets[n] = m), indices[m] in [0,n), each row sorted ascending; weights[m] may
+ * be NULL.  The arrays are copied: the caller may free them after the call
+ * returns (the stream is synchronised before return).  Also builds out-degrees,
+ * 1/out-degree and the pull tiles.  For GI_SYMMETRIC graphs the in-edge (CSC)
+ * view is the CSR itself; otherwise call gi_load_csc before any pull traversal.
+ * Errors: GI_ERR_INVALID_ARG (n < 0, m < 0, NULL pointers with m > 0, both or
+ * neither of HOST/DEV flags), GI_ERR_UNSUPPORTED (n or m >= 2^31),
+ * GI_ERR_BAD_GRAPH (GI_VALIDATE and a check failed), GI_ERR_OOM, GI_ERR_CUDA.
+ */
+int gi_load_csr(const int32_t *offsets, const int32_t *indices, const int32_t *weights, int64_t n, int64_t m,
+                uint32_t flags, void *stream, gi_graph **out);
+
+/*
+ * Attach the in-edges (CSC: getInNghs of Sec. 6) of a non-symmetric graph:
+ * in_offsets[n+1], in_indices[m] (sources, sorted ascending per row),
+ * in_weights[m] or NULL.  Same copy, flag and error rules as gi_load_csr.
+ */
+int gi_load_csc(gi_graph *g, const int32_t *in_offsets, const int32_t *in_indices, const int32_t *in_weights,
+                uint32_t flags, void *stream);
+
+int gi_graph_free(gi_graph *g);
+
+/* n, m and the maximum out-degree.  Any output pointer may be NULL. */
+int gi_graph_info(const gi_graph *g, int64_t *n, int64_t *m, int32_t *max_deg);
+
+/* Device pointers of the library's copy: out-offsets, out-indices, out-weights (NULL if none). */
+int gi_graph_device_csr(const gi_graph *g, const int32_t **offsets, const int32_t **indices,
+                        const int32_t **weights);
+
+/*
+ * Build the segmented subgraphs (SSGs) used by segmented pull (cache
+ * partitioning, Sec. 2 and the SSG code generation of Sec. 6): the in-edges are
+ * split into num_segments groups by source range; segment s keeps the arcs whose
+ * source lies in [s*ceil(n/S), (s+1)*ceil(n/S)), sorted by destination.
+ * num_segments = 1 frees them.  Kept until the next call or gi_graph_free.
+ */
+int gi_graph_build_segments(gi_graph *g, int32_t num_segments, void *stream);
+
+/* ------------------------------------------------------------- vertexset -- */
+typedef struct gi_vset gi_vset;
+
+#define GI_VSET_EMPTY 0  /* no vertex                          */
+#define GI_VSET_ALL 1    /* every vertex (edges.getVertices())  */
+#define GI_VSET_SINGLE 2 /* the single vertex `v`               */
+
+/* Representations (Sec. 2 "Direction Optimization and Frontier Data Structure"). */
+#define GI_REP_SPARSE 0x1u /* array of vertex ids + count (SparsePush frontier)      */
+#define GI_REP_BOOL 0x2u   /* one byte per vertex (boolean map)                      */
+#define GI_REP_BITMAP 0x4u /* one bit per vertex, uint32 words (bitvector)           */
+
+/* Create a vertexset over g's vertices; it stays valid until gi_vset_free. */
+int gi_vset_create(gi_graph *g, int32_t init, int32_t v, void *stream, gi_vset **out);
+int gi_vset_free(gi_vset *s);
+
+/* size() of Table 2.  Syncs the stream. */
+int gi_vset_size(gi_vset *s, int64_t *out, void *stream);
+
+/* Which representations currently hold the set (a mask of GI_REP_*). */
+int gi_vset_reps(const gi_vset *s, uint32_t *reps);
+
+/* Make the sparse representation valid (bitmap/bool -> ids, ascending order). */
+int gi_vset_to_sparse(gi_vset *s, void *stream);
+
+/* Make a dense representation valid: rep = GI_REP_BOOL or GI_REP_BITMAP. */
+int gi_vset_to_dense(gi_vset *s, uint32_t rep, void *stream);
+
+/*
+ * Write the members in ascending order to dev_out (device, cap entries) and the
+ * member count to *count (host).  Syncs the stream.  GI_ERR_INVALID_ARG if the set
+ * has more than cap members (nothing is written then).
+ */
+int gi_vset_export(gi_vset *s, int32_t *dev_out, int64_t cap, int64_t *count, void *stream);
+
+/* Replace the members by k device-resident ids (each in [0,n); duplicates removed). */
+int gi_vset_import(gi_vset *s, const int32_t *dev_ids, int64_t k, void *stream);
+
+/* --------------------------------------------------------------- schedule -- */
+/* configApplyDirection (Table 3) */
+#define GI_DIR_SPARSE_PUSH 0  /* SparsePush                                   */
+#define GI_DIR_DENSE_PUSH 1   /* DensePush                                    */
+#define GI_DIR_DENSE_PULL 2   /* DensePull                                    */
+#define GI_DIR_HYBRID_PULL 3  /* DensePull-SparsePush, chosen per iteration    */
+#define GI_DIR_HYBRID_DPUSH 4 /* DensePush-SparsePush, chosen per iteration    */
+#define GI_DIR_LEARNED 5      /* MLP picks SparsePush/DensePush/DensePull      */
+
+/* configApplyParallelization (Table 3) */
+#define GI_BAL_VERTEX 0     /* vertex-parallel: one thread per vertex                     */
+#define GI_BAL_EDGE_AWARE 1 /* edge-aware: thread / warp / CTA by degree (t_warp, t_cta)   */
+
+/* threshold rule used by the hybrid directions */
+#define GI_RULE_BEAMER 0 /* push->pull when m_f > m_u/alpha; pull->push when |F| < n/beta */
+#define GI_RULE_LIGRA 1  /* pull iff |F| + m_f > m/20                                     */
+
+typedef struct gi_schedule {
+  int32_t direction;    /* GI_DIR_*                                                  */
+  uint32_t dense_rep;   /* frontier rep for dense traversals: GI_REP_BITMAP or BOOL  */
+  int32_t balance;      /* GI_BAL_*                                                  */
+  int32_t num_segments; /* SSG count for segmented pull (configApplyNumSSG); 1 = off  */
+  int32_t block;        /* threads per block of traversal kernels (64..1024, /32)    */
+  int32_t t_warp;       /* edge-aware: degree >= t_warp goes to a warp                */
+  int32_t t_cta;        /* edge-aware: degree >= t_cta goes to a whole block          */
+  int32_t rule;         /* GI_RULE_*                                                 */
+  float alpha, beta;    /* Beamer constants                                          */
+  int32_t tile_edges;   /* pull tiles: arcs per tile (power of two, 256..16384)       */
+} gi_schedule;
+
+/* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment, 256 threads, t_warp 32,
+ * t_cta 1024, Beamer alpha 14 beta 24, 2048-arc tiles. */
+void gi_schedule_default(gi_schedule *s);
+
+/* ------------------------------------------------------------ edgeset apply -- */
+/*
+ * Built-in edge functions (the `f` of apply/applyModified).  Each names the
+ * vertex vectors it reads/writes through a kernel_args struct of device
+ * pointers.  Push directions apply f with atomics, pull directions without
+ * (dependence rules of Sec. 6).  All reductions are commutative and
+ * associative or asyncMin, so any traversal order gives the same result
+ * (integers bit-exact; float sums up to rounding order).
+ */
+#define GI_K_BFS 1   /* dstFilter depth[v]==-1; f: depth[v]=level, parent[v]=min(parent[v],u) */
+#define GI_K_SSSP 2  /* f: dist[v] = min(dist[v], snap[u] + w(u,v))                         */
+#define GI_K_CC 3    /* f: label[v] = min(label[v], snap[u])                                 */
+#define GI_K_SUM 4   /* f: acc[v] += contrib[u]  (PageRank / PageRankDelta updateEdge)        */
+#define GI_K_PROBE 5 /* f: count[v] += 1; srcsum[v] += u+1  (records the selected edges)      */
+
+typedef struct { int32_t *depth; int32_t *parent; int32_t level; } gi_bfs_args;
+/* parent may be NULL; otherwise unvisited entries must hold INT32_MAX on entry. */
+typedef struct { int32_t *dist; const int32_t *snap; } gi_sssp_args;
+/* snap[u] = dist of u at the start of the round, read for frontier sources only. */
+typedef struct { int32_t *label; const int32_t *snap; } gi_cc_args;
+typedef struct { const float *contrib; float *acc; } gi_sum_args;
+typedef struct { int32_t *count; unsigned long long *srcsum; } gi_probe_args;
+
+/* applyModified without deduplication (Table 2, disable_deduplication).  Honoured
+ * for GI_K_BFS, whose function modifies each destination at most once; the other
+ * kernels always deduplicate so the output never holds more than n entries. */
+#define GI_NO_DEDUP 0x1u
+
+/*
+ * edges.from(from).to(to).srcFilter/dstFilter(kernel_id's filter).apply(f)
+ * (out_modified == NULL) or .applyModified(f) (out_modified != NULL: receives
+ * the destinations whose vector entry f changed, deduplicated unless
+ * GI_NO_DEDUP).  from/to == NULL mean all vertices.  The traversal follows
+ * sched->direction; hybrid and learned directions pick per call (this syncs
+ * the stream to read the frontier statistics).  out_modified must not alias
+ * from or to.  Errors: GI_ERR_INVALID_ARG, GI_ERR_UNSUPPORTED (pull direction
+ * on a non-symmetric graph without gi_load_csc), GI_ERR_CUDA.
+ */
+int gi_edgeset_apply(gi_graph *g, gi_vset *from, gi_vset *to, const gi_schedule *sched, int32_t kernel_id,
+                     const void *kernel_args, gi_vset *out_modified, uint32_t flags, void *stream);
+
+/* ---------------------------------------------------------------- drivers -- */
+/*
+ * Per-iteration trace of a driver run (optional, host memory): for iteration i,
+ * direction[i] (GI_DIR_SPARSE_PUSH/DENSE_PUSH/DENSE_PULL actually used),
+ * frontier[i] = |F|, edges[i] = m_f (sum of out-degrees over F) and, if
+ * features != NULL, the 16 selector features of the iteration at
+ * features[16*i .. 16*i+15].  Any array pointer may be NULL.  Iterations past
+ * `cap` run but are not recorded; `iterations` counts all of them.
+ */
+typedef struct gi_trace {
+  int32_t cap;        /* entries available in the arrays below                */
+  int32_t iterations; /* filled in: number of iterations run                  */
+  int32_t *direction;
+  int64_t *frontier;
+  int64_t *edges;
+  float *features;
+} gi_trace;
+
+/*
+ * Level-synchronous BFS from src (Sec. 7's BFS: SparsePush, DensePull with a
+ * bitvector frontier and early exit, DensePush, or a hybrid).  depth_dev[n]:
+ * hops from src, -1 if unreached.  parent_dev[n] (may be NULL): the smallest-id
+ * in-neighbour one level closer to src (parent[src] = src, -1 if unreached);
+ * the rule makes parents identical under every schedule.
+ */
+int gi_bfs(gi_graph *g, int32_t src, int32_t *depth_dev, int32_t *parent_dev, const gi_schedule *sched,
+           gi_trace *trace, void *stream);
+
+/*
+ * Frontier Bellman-Ford from src on the graph's int32 weights (Sec. 7's SSSP):
+ * synchronous rounds; round r relaxes the out-arcs of vertices whose distance
+ * dropped in round r-1 using their start-of-round distance.  dist_dev[n]:
+ * INT32_MAX if unreachable.  GI_ERR_INVALID_ARG if the graph has no weights.
+ */
+int gi_sssp(gi_graph *g, int32_t src, int32_t *dist_dev, const gi_schedule *sched, gi_trace *trace,
+            void *stream);
+
+/*
+ * Connected components by synchronous min-label propagation (Sec. 7's CC):
+ * label_dev[n] = smallest vertex id of v's component (symmetric graphs).
+ */
+int gi_cc(gi_graph *g, int32_t *label_dev, const gi_schedule *sched, gi_trace *trace, void *stream);
+
+/*
+ * PageRank (Sec. 7's PR): iters power iterations of
+ * PR[v] = (1-d)/n + d * sum_{u in in(v)} PR[u]/outdeg(u) from PR = 1/n in FP32
+ * (FP32 accumulation), then division by the FP64 sum of all ranks.
+ * sched->direction: DENSE_PULL (default; segmented when num_segments > 1) or
+ * DENSE_PUSH.  rank_dev[n] receives the normalised ranks.
+ */
+int gi_pagerank(gi_graph *g, float damping, int32_t iters, float *rank_dev, const gi_schedule *sched,
+                void *stream);
+
+/*
+ * PageRankDelta (Fig. 1, with the round-1 update order of the GraphIt program
+ * of Fig. 3): Rank = 0, Delta = 1/n, all vertices active; each round the active
+ * vertices propagate Delta/outdeg, every vertex updates Delta and Rank, and
+ * those with |Delta| > eps*Rank stay active.  iters rounds, FP32.  rank_dev[n]
+ * receives Rank (not normalised).  The edge traversal per round follows sched
+ * (hybrid by default: DensePull when the active set is large, SparsePush else).
+ */
+int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t iters, float *rank_dev,
+                      const gi_schedule *sched, gi_trace *trace, void *stream);
+
+/* ------------------------------------------------------------ selector -- */
+/*
+ * Load the learned direction selector: a 16-64-64-3 ReLU perceptron, params as
+ * float32 W1[64][16], b1[64], W2[64][64], b2[64], W3[3][64], b3[3] (host memory,
+ * `count` = 5443 floats), plus feature normalisation mean[16] and inv_std[16].
+ * Used by GI_DIR_LEARNED; until loaded, LEARNED falls back to the Beamer rule.
+ */
+int gi_selector_load(const float *params, int32_t count, const float *mean, const float *inv_std);
+
+/* Number of parameters of the selector network (5443). */
+int gi_selector_num_params(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRAPHIT_GB_H */

@@ -1,0 +1,250 @@
+"""GB300 edgeset-apply library (GraphIt's operators and schedules on sm_103a).
+
+Thin Python binding of the C ABI in include/graphit_gb.h: every function here
+marshals arguments (torch tensors for device memory, torch streams) and calls
+the CUDA library; all graph work runs in its kernels.  Importing the package
+loads (and if needed builds) libgraphit_gb.so and raises if that fails: there
+is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import (GI_BAL_EDGE_AWARE, GI_BAL_VERTEX, GI_DIR_DENSE_PULL, GI_DIR_DENSE_PUSH,  # noqa: F401
+                   GI_DIR_HYBRID_DPUSH, GI_DIR_HYBRID_PULL, GI_DIR_LEARNED, GI_DIR_SPARSE_PUSH, GI_K_BFS,
+                   GI_K_CC, GI_K_PROBE, GI_K_SSSP, GI_K_SUM, GI_NO_DEDUP, GI_REP_BITMAP, GI_REP_BOOL,
+                   GI_REP_SPARSE, GI_RULE_BEAMER, GI_RULE_LIGRA, GI_VSET_ALL, GI_VSET_EMPTY, GI_VSET_SINGLE,
+                   GIError, gi_bfs_args, gi_cc_args, gi_probe_args, gi_schedule, gi_sssp_args, gi_sum_args,
+                   gi_trace)
+
+_C = L.load()
+check = L.check
+
+
+def lib():
+    """The loaded ctypes library (functions named as in graphit_gb.h)."""
+    return _C
+
+
+def _vp(x) -> ctypes.c_void_p:
+    if x is None:
+        return ctypes.c_void_p(None)
+    if isinstance(x, torch.Tensor):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def schedule(direction="hybrid_pull", **kw) -> gi_schedule:
+    """A gi_schedule with the library defaults, overridden by keyword fields."""
+    s = gi_schedule()
+    _C.gi_schedule_default(ctypes.byref(s))
+    if isinstance(direction, str):
+        direction = L.DIRECTIONS[direction]
+    s.direction = direction
+    for k, v in kw.items():
+        if k == "balance" and isinstance(v, str):
+            v = {"vertex": GI_BAL_VERTEX, "edge_aware": GI_BAL_EDGE_AWARE}[v]
+        if k == "rule" and isinstance(v, str):
+            v = {"beamer": GI_RULE_BEAMER, "ligra": GI_RULE_LIGRA}[v]
+        setattr(s, k, v)
+    return s
+
+
+class Graph:
+    """A graph loaded into the library (gi_load_csr / gi_load_csc).
+
+    row_ptr/col/wt are host numpy arrays (copied host-to-device) or CUDA
+    tensors (copied device-to-device), int32.
+    """
+
+    def __init__(self, row_ptr, col, wt=None, symmetric=True, validate=False, in_edges=None, stream=None):
+        on_dev = isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda
+        if not on_dev:
+            row_ptr = np.ascontiguousarray(row_ptr, np.int32)
+            col = np.ascontiguousarray(col, np.int32)
+            wt = None if wt is None else np.ascontiguousarray(wt, np.int32)
+        self._keep = (row_ptr, col, wt)
+        n = int(row_ptr.shape[0]) - 1
+        m = int(col.shape[0])
+        flags = (L.GI_DEV_PTRS if on_dev else L.GI_HOST_PTRS) | (L.GI_SYMMETRIC if symmetric else 0) | \
+            (L.GI_VALIDATE if validate else 0)
+        h = ctypes.c_void_p()
+        check(_C.gi_load_csr(_vp(row_ptr), _vp(col), _vp(wt), n, m, flags, _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self._keep = None
+        if in_edges is not None and not symmetric:
+            ip, ic, iw = (list(in_edges) + [None])[:3]
+            if not on_dev:
+                ip, ic = np.ascontiguousarray(ip, np.int32), np.ascontiguousarray(ic, np.int32)
+                iw = None if iw is None else np.ascontiguousarray(iw, np.int32)
+            check(_C.gi_load_csc(h, _vp(ip), _vp(ic), _vp(iw),
+                                 (L.GI_DEV_PTRS if on_dev else L.GI_HOST_PTRS) | (L.GI_VALIDATE if validate else 0),
+                                 _stream(stream)))
+        n_, m_, md = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        check(_C.gi_graph_info(h, ctypes.byref(n_), ctypes.byref(m_), ctypes.byref(md)))
+        self.n, self.m, self.max_deg = n_.value, m_.value, md.value
+        self.weighted = wt is not None
+
+    @classmethod
+    def from_host(cls, hg, validate=False, stream=None, in_edges=None):
+        """From a graphgen.HostGraph-like object (n, row_ptr, col, wt, symmetric)."""
+        return cls(hg.row_ptr, hg.col, getattr(hg, "wt", None), symmetric=getattr(hg, "symmetric", True),
+                   validate=validate, in_edges=in_edges, stream=stream)
+
+    def build_segments(self, num_segments: int, stream=None):
+        check(_C.gi_graph_build_segments(self.handle, int(num_segments), _stream(stream)))
+
+    def free(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            check(_C.gi_graph_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class VertexSet:
+    """A gi_vset (sparse queue / bool map / bitmap frontier)."""
+
+    def __init__(self, g: Graph, init=GI_VSET_EMPTY, v: int = 0, stream=None):
+        h = ctypes.c_void_p()
+        check(_C.gi_vset_create(g.handle, int(init), int(v), _stream(stream), ctypes.byref(h)))
+        self.handle, self.g = h, g
+
+    def size(self, stream=None) -> int:
+        out = ctypes.c_int64()
+        check(_C.gi_vset_size(self.handle, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def reps(self) -> int:
+        out = ctypes.c_uint32()
+        check(_C.gi_vset_reps(self.handle, ctypes.byref(out)))
+        return out.value
+
+    def to_sparse(self, stream=None):
+        check(_C.gi_vset_to_sparse(self.handle, _stream(stream)))
+
+    def to_dense(self, rep=GI_REP_BITMAP, stream=None):
+        check(_C.gi_vset_to_dense(self.handle, int(rep), _stream(stream)))
+
+    def export(self, stream=None) -> torch.Tensor:
+        out = torch.empty(max(self.g.n, 1), dtype=torch.int32, device="cuda")
+        cnt = ctypes.c_int64()
+        check(_C.gi_vset_export(self.handle, _vp(out), out.numel(), ctypes.byref(cnt), _stream(stream)))
+        return out[:cnt.value]
+
+    def import_ids(self, ids: torch.Tensor, stream=None):
+        ids = ids.to(device="cuda", dtype=torch.int32).contiguous()
+        check(_C.gi_vset_import(self.handle, _vp(ids), ids.numel(), _stream(stream)))
+
+    def free(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            check(_C.gi_vset_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Trace:
+    """Host arrays for a gi_trace of up to `cap` iterations."""
+
+    def __init__(self, cap: int = 4096):
+        self.direction = np.zeros(cap, np.int32)
+        self.frontier = np.zeros(cap, np.int64)
+        self.edges = np.zeros(cap, np.int64)
+        self.features = np.zeros((cap, 16), np.float32)
+        self.c = gi_trace(cap, 0, self.direction.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                          self.frontier.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                          self.edges.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                          self.features.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+
+    @property
+    def iterations(self) -> int:
+        return int(self.c.iterations)
+
+    def as_dict(self):
+        k = min(self.iterations, self.direction.shape[0])
+        return dict(direction=self.direction[:k].copy(), frontier=self.frontier[:k].copy(),
+                    edges=self.edges[:k].copy(), features=self.features[:k].copy(), iterations=self.iterations)
+
+
+def _sched(s):
+    return s if s is not None else schedule()
+
+
+def _tr(trace):
+    return ctypes.byref(trace.c) if trace is not None else None
+
+
+def bfs(g: Graph, src: int, want_parent=True, sched=None, trace: Trace | None = None, stream=None, out=None):
+    """gi_bfs: (depth, parent or None) as int32 CUDA tensors."""
+    depth = out[0] if out else torch.empty(g.n, dtype=torch.int32, device="cuda")
+    parent = (out[1] if out else torch.empty(g.n, dtype=torch.int32, device="cuda")) if want_parent else None
+    check(_C.gi_bfs(g.handle, int(src), _vp(depth), _vp(parent), ctypes.byref(_sched(sched)), _tr(trace),
+                    _stream(stream)))
+    return depth, parent
+
+
+def sssp(g: Graph, src: int, sched=None, trace: Trace | None = None, stream=None, out=None):
+    dist = out if out is not None else torch.empty(g.n, dtype=torch.int32, device="cuda")
+    check(_C.gi_sssp(g.handle, int(src), _vp(dist), ctypes.byref(_sched(sched)), _tr(trace), _stream(stream)))
+    return dist
+
+
+def cc(g: Graph, sched=None, trace: Trace | None = None, stream=None, out=None):
+    label = out if out is not None else torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
+    check(_C.gi_cc(g.handle, _vp(label), ctypes.byref(_sched(sched)), _tr(trace), _stream(stream)))
+    return label[:g.n]
+
+
+def pagerank(g: Graph, damping=0.85, iters=20, sched=None, stream=None, out=None):
+    rank = out if out is not None else torch.empty(max(g.n, 1), dtype=torch.float32, device="cuda")
+    check(_C.gi_pagerank(g.handle, float(damping), int(iters), _vp(rank),
+                         ctypes.byref(_sched(sched if sched is not None else schedule("dense_pull"))),
+                         _stream(stream)))
+    return rank[:g.n]
+
+
+def pagerank_delta(g: Graph, damping=0.85, eps=1e-7, iters=10, sched=None, trace: Trace | None = None,
+                   stream=None, out=None):
+    rank = out if out is not None else torch.empty(max(g.n, 1), dtype=torch.float32, device="cuda")
+    check(_C.gi_pagerank_delta(g.handle, float(damping), float(eps), int(iters), _vp(rank),
+                               ctypes.byref(_sched(sched)), _tr(trace), _stream(stream)))
+    return rank[:g.n]
+
+
+def edgeset_apply(g: Graph, frm: VertexSet | None, to: VertexSet | None, sched, kernel_id: int, args,
+                  out: VertexSet | None = None, flags: int = 0, stream=None):
+    """gi_edgeset_apply: args is one of the gi_*_args ctypes structs."""
+    check(_C.gi_edgeset_apply(g.handle, frm.handle if frm else None, to.handle if to else None,
+                              ctypes.byref(_sched(sched)), int(kernel_id), ctypes.byref(args),
+                              out.handle if out else None, int(flags), _stream(stream)))
+
+
+def selector_load(params: np.ndarray, mean: np.ndarray, inv_std: np.ndarray):
+    p = np.ascontiguousarray(params, np.float32)
+    mu = np.ascontiguousarray(mean, np.float32)
+    isd = np.ascontiguousarray(inv_std, np.float32)
+    check(_C.gi_selector_load(_vp(p), int(p.size), _vp(mu), _vp(isd)))
+
+
+def selector_num_params() -> int:
+    return int(_C.gi_selector_num_params())

@@ -1,0 +1,498 @@
+// Algorithm drivers built on the edgeset apply kernels: BFS, Bellman-Ford
+// SSSP, label-propagation CC, PageRank and PageRankDelta (Sec. 7's
+// benchmarks).  Each iteration: fused frontier statistics + direction choice,
+// one traversal, and (where the algorithm needs one) a vertex epilogue.
+#include <cmath>
+#include <vector>
+
+#include "gi_traverse.cuh"
+
+namespace gi {
+
+// ------------------------------------------------------------ helper kernels --
+__global__ void k_fill_i32(int32_t *x, int64_t n, int32_t val) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = val;
+}
+
+__global__ void k_iota2(int32_t *a, int32_t *b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = b[i] = (int32_t)i;
+}
+
+__global__ void k_bfs_init(int32_t *depth, int32_t *parent, int64_t n, int32_t src) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    depth[i] = i == src ? 0 : -1;
+    if (parent) parent[i] = i == src ? src : INT32_MAX;
+  }
+}
+
+__global__ void k_parent_fix(int32_t *parent, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (parent[i] == INT32_MAX) parent[i] = -1;
+}
+
+__global__ void k_set_one(int32_t *x, int32_t i, int32_t val) { x[i] = val; }
+
+// snapshot maintenance for synchronous rounds: frontier members carry their
+// start-of-round value in snap[], everyone else INT32_MAX
+__global__ void k_snap_reset(const int32_t *__restrict__ q, const int32_t *__restrict__ qc, int32_t *snap) {
+  int32_t c = *qc;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) snap[q[i]] = INT32_MAX;
+}
+
+__global__ void k_snap_set(const int32_t *__restrict__ q, const int32_t *__restrict__ qc, int32_t *snap,
+                           const int32_t *__restrict__ x) {
+  int32_t c = *qc;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+    int32_t v = q[i];
+    snap[v] = x[v];
+  }
+}
+
+__global__ void k_pr_init(float *contrib, const float *__restrict__ inv_deg, int64_t n, float init) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    contrib[i] = init * inv_deg[i];
+}
+
+__global__ void k_fill_f32(float *x, int64_t n, float val) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = val;
+}
+
+// PageRank vertex update after a push iteration: rank = base + d*acc
+__global__ void k_pr_vertex(float *acc, float *contrib_out, float *rank_out, const float *__restrict__ inv_deg,
+                            int64_t n, float base, float damping) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float r = fmaf(damping, acc[i], base);
+    acc[i] = 0.0f;
+    if (rank_out) rank_out[i] = r;
+    else contrib_out[i] = r * inv_deg[i];
+  }
+}
+
+// FP64 sum of ranks: per-block partial sums, then each block of the scale
+// kernel adds the partials in the same fixed order and divides its range.
+__global__ void k_sum_f64(const float *__restrict__ x, int64_t n, double *partial) {
+  __shared__ double sw[32];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)x[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += sw[w];
+    partial[blockIdx.x] = b;
+  }
+}
+
+__global__ void k_scale_f64(float *x, int64_t n, const double *__restrict__ partial, int32_t np) {
+  __shared__ double total;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < np; ++i) t += partial[i];
+    total = t;
+  }
+  __syncthreads();
+  const double inv = total != 0.0 ? 1.0 / total : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (float)((double)x[i] * inv);
+}
+
+// PageRankDelta vertex filter after a push round (Fig. 1): Delta, Rank,
+// DeltaSum reset, next frontier (bitmap word per warp + queue), next contrib.
+__global__ void k_prd_vertex(float *dsum, float *rank, float *contrib_out, const float *__restrict__ inv_deg,
+                             int64_t n, float damping, float first_base, float inv_n, float eps, int32_t first_round,
+                             uint32_t *out_bm, int32_t *out_q, int32_t *out_qc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (n + 31) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t v = w * 32 + lane;
+    bool active = false;
+    if (v < n) {
+      float s = dsum[v], r = rank[v], delta;
+      if (first_round) {
+        delta = fmaf(damping, s, first_base);
+        r += delta;
+        delta -= inv_n;
+      } else {
+        delta = damping * s;
+        r += delta;
+      }
+      rank[v] = r;
+      dsum[v] = 0.0f;
+      active = fabsf(delta) > eps * r;
+      contrib_out[v] = active ? delta * inv_deg[v] : 0.0f;
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, active);
+    if (lane == 0) out_bm[w] = word;
+    if (word) {
+      int32_t base = 0;
+      if (lane == 0) base = atomicAdd(out_qc, __popc(word));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (active) out_q[base + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- helpers --
+struct VsetPair {
+  gi_vset a, b;
+  gi_vset *F = &a, *N = &b;
+  void swap() {
+    gi_vset *t = F;
+    F = N;
+    N = t;
+  }
+};
+
+static int pair_alloc(gi_graph *g, VsetPair &p, cudaStream_t s) {
+  GI_TRY(vset_alloc(g, &p.a, s));
+  GI_TRY(vset_alloc(g, &p.b, s));
+  return GI_OK;
+}
+
+static void pair_free(VsetPair &p, cudaStream_t s) {
+  for (gi_vset *v : {&p.a, &p.b}) {
+    dev_free(v->queue, s);
+    dev_free(v->count, s);
+    dev_free(v->bitmap, s);
+    dev_free(v->boolmap, s);
+    v->queue = v->count = nullptr;
+    v->bitmap = nullptr;
+    v->boolmap = nullptr;
+  }
+}
+
+// F = {v} (v >= 0), all vertices (v == -1)
+__global__ void k_front_init(int32_t *q, int32_t *qc, uint32_t *bm, int64_t words, int64_t n, int32_t v) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t word = 0;
+    if (v < 0) {
+      int64_t rem = n - w * 32;
+      word = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    } else if ((v >> 5) == w) {
+      word = 1u << (v & 31);
+    }
+    bm[w] = word;
+  }
+  if (v < 0) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      q[i] = (int32_t)i;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (v >= 0) q[0] = v;
+    *qc = v >= 0 ? 1 : (int32_t)n;
+  }
+}
+
+static int front_init(gi_graph *g, gi_vset *F, int32_t v, cudaStream_t s) {
+  int64_t work = g->n > F->words ? g->n : F->words;
+  k_front_init<<<grid_for(g, work, 256), 256, 0, s>>>(F->queue, F->count, F->bitmap, F->words, g->n, v);
+  GI_LAUNCH_CHECK();
+  F->reps = GI_REP_SPARSE | GI_REP_BITMAP;
+  return GI_OK;
+}
+
+static void trace_put(gi_trace *tr, int32_t it, const int64_t *ctrl_host) {
+  if (!tr) return;
+  tr->iterations = it + 1;
+  if (it >= tr->cap) return;
+  if (tr->direction) tr->direction[it] = (int32_t)ctrl_host[kDecision];
+  if (tr->frontier) tr->frontier[it] = ctrl_host[kNf];
+  if (tr->edges) tr->edges[it] = ctrl_host[kMf];
+  if (tr->features) {
+    const float *f = reinterpret_cast<const float *>(ctrl_host + kFeat);
+    for (int k = 0; k < 16; ++k) tr->features[16 * it + k] = f[k];
+  }
+}
+
+static int pull_available(gi_graph *g, int32_t dir) {
+  if (dir == GI_DIR_DENSE_PULL && !g->has_csc) {
+    set_error("DensePull needs the in-edges: load a symmetric graph or call gi_load_csc");
+    return GI_ERR_UNSUPPORTED;
+  }
+  return GI_OK;
+}
+
+// Frontier loop shared by BFS / SSSP / CC: decide, stop when empty, traverse.
+template <class Step>
+static int frontier_loop(gi_graph *g, VsetPair &P, const gi_schedule &sc, bool track_unvisited, gi_trace *tr,
+                         cudaStream_t s, Step step) {
+  for (int32_t it = 0;; ++it) {
+    DecideParams p = decide_params(sc, it, track_unvisited);
+    GI_TRY(frontier_decide(g, P.F, p, s));
+    GI_TRY(ctrl_fetch(g, s));
+    if (g->ctrl_host[kNf] == 0) {
+      if (tr) tr->iterations = it;
+      break;
+    }
+    int32_t dir = (int32_t)g->ctrl_host[kDecision];
+    if (dir == GI_DIR_DENSE_PULL && !g->has_csc) dir = GI_DIR_DENSE_PUSH;
+    trace_put(tr, it, g->ctrl_host);
+    GI_TRY(step(it, dir));
+    P.swap();
+  }
+  return GI_OK;
+}
+
+}  // namespace gi
+
+using namespace gi;
+
+// ===================================================================== BFS ==
+extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent, const gi_schedule *sched,
+                      gi_trace *trace, void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_TRY(check_schedule(sched));
+  GI_ARG(src >= 0 && src < g->n, "source out of range");
+  GI_ARG(depth != nullptr, "depth is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const gi_schedule sc = *sched;
+  if (sc.direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sc.direction));
+  GI_TRY(ensure_tiles(g, sc, s));
+  VsetPair P;
+  int st = pair_alloc(g, P, s);
+  if (st == GI_OK) {
+    k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(depth, parent, g->n, src);
+    st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+  }
+  if (st == GI_OK) st = front_init(g, P.F, src, s);
+  if (st == GI_OK) st = ctrl_init(g, g->n, g->m, s);
+  if (st == GI_OK)
+    st = frontier_loop(g, P, sc, true, trace, s, [&](int32_t it, int32_t dir) {
+      gi_bfs_args a{depth, parent, it + 1};
+      return apply_dispatch(g, P.F, nullptr, dir, sc, GI_K_BFS, &a, P.N, GI_NO_DEDUP, s);
+    });
+  if (st == GI_OK && parent) {
+    k_parent_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n);
+    st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+  }
+  pair_free(P, s);
+  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "bfs", __FILE__, __LINE__);
+  return st;
+}
+
+// =========================================================== SSSP and CC ==
+// Synchronous rounds on x[] (dist or label): snap[] holds the start-of-round
+// value of frontier members (INT32_MAX elsewhere) and is what every source
+// reads, so push and pull rounds compute the same thing.
+static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src, const gi_schedule &sc,
+                        gi_trace *trace, cudaStream_t s) {
+  GI_TRY(ensure_tiles(g, sc, s));
+  VsetPair P;
+  int32_t *snap = nullptr;
+  int st = pair_alloc(g, P, s);
+  if (st == GI_OK) st = dev_alloc_n(&snap, g->n, s);
+  if (st == GI_OK) {
+    if (kernel_id == GI_K_CC) {
+      k_iota2<<<grid_for(g, g->n, 256), 256, 0, s>>>(x, snap, g->n);
+    } else {
+      k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(x, g->n, INT32_MAX);
+      k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(snap, g->n, INT32_MAX);
+      k_set_one<<<1, 1, 0, s>>>(x, src, 0);
+      k_set_one<<<1, 1, 0, s>>>(snap, src, 0);
+    }
+    st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+  }
+  if (st == GI_OK) st = front_init(g, P.F, kernel_id == GI_K_CC ? -1 : src, s);
+  if (st == GI_OK) st = ctrl_init(g, 0, 0, s);
+  if (st == GI_OK)
+    st = frontier_loop(g, P, sc, false, trace, s, [&](int32_t, int32_t dir) -> int {
+      int r;
+      if (kernel_id == GI_K_CC) {
+        gi_cc_args a{x, snap};
+        r = apply_dispatch(g, P.F, nullptr, dir, sc, GI_K_CC, &a, P.N, 0, s);
+      } else {
+        gi_sssp_args a{x, snap};
+        r = apply_dispatch(g, P.F, nullptr, dir, sc, GI_K_SSSP, &a, P.N, 0, s);
+      }
+      if (r != GI_OK) return r;
+      int grid = g->num_sms * 4;
+      k_snap_reset<<<grid, 256, 0, s>>>(P.F->queue, P.F->count, snap);
+      k_snap_set<<<grid, 256, 0, s>>>(P.N->queue, P.N->count, snap, x);
+      GI_LAUNCH_CHECK();
+      return GI_OK;
+    });
+  dev_free(snap, s);
+  pair_free(P, s);
+  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "minlabel", __FILE__, __LINE__);
+  return st;
+}
+
+extern "C" int gi_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedule *sched, gi_trace *trace,
+                       void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_TRY(check_schedule(sched));
+  GI_ARG(src >= 0 && src < g->n, "source out of range");
+  GI_ARG(dist != nullptr, "dist is NULL");
+  GI_ARG(g->out.wt != nullptr, "SSSP needs edge weights");
+  if (sched->direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sched->direction));
+  if (sched->direction == GI_DIR_DENSE_PULL || sched->direction == GI_DIR_HYBRID_PULL) {
+    GI_ARG(g->symmetric || g->in.wt != nullptr, "pull SSSP needs in-edge weights (gi_load_csc with weights)");
+  }
+  return minlabel_run(g, dist, GI_K_SSSP, src, *sched, trace, (cudaStream_t)stream);
+}
+
+extern "C" int gi_cc(gi_graph *g, int32_t *label, const gi_schedule *sched, gi_trace *trace, void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_TRY(check_schedule(sched));
+  GI_ARG(label != nullptr, "label is NULL");
+  if (sched->direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sched->direction));
+  if (g->n == 0) return GI_OK;
+  return minlabel_run(g, label, GI_K_CC, 0, *sched, trace, (cudaStream_t)stream);
+}
+
+// ================================================================ PageRank ==
+static int pr_normalize(gi_graph *g, float *rank, cudaStream_t s) {
+  const int np = g->num_sms * 2;
+  double *partial = nullptr;
+  GI_TRY(dev_alloc_n(&partial, np, s));
+  k_sum_f64<<<np, 256, 0, s>>>(rank, g->n, partial);
+  k_scale_f64<<<grid_for(g, g->n, 256), 256, 0, s>>>(rank, g->n, partial, np);
+  cudaError_t e = cudaGetLastError();
+  dev_free(partial, s);
+  if (e != cudaSuccess) return cuda_fail(e, "normalize", __FILE__, __LINE__);
+  return GI_OK;
+}
+
+extern "C" int gi_pagerank(gi_graph *g, float damping, int32_t iters, float *rank, const gi_schedule *sched,
+                           void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_TRY(check_schedule(sched));
+  GI_ARG(rank != nullptr || g->n == 0, "rank is NULL");
+  GI_ARG(iters >= 0, "iters must be >= 0");
+  GI_ARG(damping >= 0.0f && damping <= 1.0f, "damping must be in [0,1]");
+  if (g->n == 0) return GI_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const gi_schedule sc = *sched;
+  const bool push = sc.direction == GI_DIR_DENSE_PUSH || sc.direction == GI_DIR_SPARSE_PUSH;
+  if (!push) GI_TRY(pull_available(g, GI_DIR_DENSE_PULL));
+  GI_TRY(ensure_tiles(g, sc, s));
+  const bool segmented = !push && sc.num_segments > 1;
+  if (segmented && g->segs.num != sc.num_segments) GI_TRY(gi_graph_build_segments(g, sc.num_segments, s));
+  const float base = (1.0f - damping) / (float)g->n, init = 1.0f / (float)g->n;
+  float *buf[2] = {nullptr, nullptr}, *acc = nullptr;
+  int st = dev_alloc_n(&buf[0], g->n, s);
+  if (st == GI_OK) st = dev_alloc_n(&buf[1], g->n, s);
+  if (st == GI_OK && (push || segmented)) st = dev_alloc_n(&acc, g->n, s);
+  if (st == GI_OK) {
+    if (iters == 0) k_fill_f32<<<grid_for(g, g->n, 256), 256, 0, s>>>(rank, g->n, init);
+    k_pr_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(buf[0], g->inv_out_deg, g->n, init);
+    if (acc) k_fill_f32<<<grid_for(g, g->n, 256), 256, 0, s>>>(acc, g->n, 0.0f);
+    st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+  }
+  for (int32_t k = 0; k < iters && st == GI_OK; ++k) {
+    const bool last = (k == iters - 1);
+    float *cin = buf[k & 1], *cout = buf[(k + 1) & 1];
+    if (push) {
+      OpSum op{cin, acc};
+      st = launch_push(g, op, kSrcAll, nullptr, nullptr, OutSet(), sc, s);
+      if (st == GI_OK) {
+        k_pr_vertex<<<grid_for(g, g->n, 256), 256, 0, s>>>(acc, last ? nullptr : cout, last ? rank : nullptr,
+                                                           g->inv_out_deg, g->n, base, damping);
+        st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+      }
+    } else if (segmented) {
+      // one SSG at a time (Sec. 6): acc accumulates over segments without
+      // atomics; the last segment applies the vertex update.
+      for (int sid = 0; sid < g->segs.num && st == GI_OK; ++sid) {
+        if (sid + 1 < g->segs.num) {
+          OpSum op{cin, acc};
+          st = launch_pull_tiled(g, op, g->segs.seg[sid], g->segs.tiles[sid], nullptr, nullptr, OutSet(), s);
+        } else {
+          OpSum op{cin, acc};
+          st = launch_pull_tiled(g, op, g->segs.seg[sid], g->segs.tiles[sid], nullptr, nullptr, OutSet(), s);
+          if (st == GI_OK) {
+            k_pr_vertex<<<grid_for(g, g->n, 256), 256, 0, s>>>(acc, last ? nullptr : cout, last ? rank : nullptr,
+                                                               g->inv_out_deg, g->n, base, damping);
+            st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+          }
+        }
+      }
+    } else {
+      OpPR op{cin, last ? nullptr : cout, last ? rank : nullptr, g->inv_out_deg, base, damping};
+      st = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, OutSet(), s);
+    }
+  }
+  if (st == GI_OK) st = pr_normalize(g, rank, s);
+  dev_free(buf[0], s);
+  dev_free(buf[1], s);
+  dev_free(acc, s);
+  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "pagerank", __FILE__, __LINE__);
+  return st;
+}
+
+// =========================================================== PageRankDelta ==
+extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t iters, float *rank,
+                                 const gi_schedule *sched, gi_trace *trace, void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_TRY(check_schedule(sched));
+  GI_ARG(rank != nullptr || g->n == 0, "rank is NULL");
+  GI_ARG(iters >= 0, "iters must be >= 0");
+  GI_ARG(eps >= 0.0f, "eps must be >= 0");
+  if (g->n == 0) return GI_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const gi_schedule sc = *sched;
+  if (sc.direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sc.direction));
+  GI_TRY(ensure_tiles(g, sc, s));
+  const float inv_n = 1.0f / (float)g->n, first_base = (1.0f - damping) / (float)g->n;
+  VsetPair P;
+  float *cb[2] = {nullptr, nullptr}, *dsum = nullptr;
+  int st = pair_alloc(g, P, s);
+  if (st == GI_OK) st = dev_alloc_n(&cb[0], g->n, s);
+  if (st == GI_OK) st = dev_alloc_n(&cb[1], g->n, s);
+  if (st == GI_OK) st = dev_alloc_n(&dsum, g->n, s);
+  if (st == GI_OK) {
+    k_fill_f32<<<grid_for(g, g->n, 256), 256, 0, s>>>(rank, g->n, 0.0f);
+    k_fill_f32<<<grid_for(g, g->n, 256), 256, 0, s>>>(dsum, g->n, 0.0f);
+    k_pr_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(cb[0], g->inv_out_deg, g->n, inv_n);
+    st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+  }
+  if (st == GI_OK) st = front_init(g, P.F, -1, s);
+  if (st == GI_OK) st = ctrl_init(g, 0, 0, s);
+  int cur = 0;
+  for (int32_t round = 1; round <= iters && st == GI_OK; ++round) {
+    DecideParams p = decide_params(sc, round - 1, false);
+    if ((st = frontier_decide(g, P.F, p, s)) != GI_OK) break;
+    if ((st = ctrl_fetch(g, s)) != GI_OK) break;
+    if (g->ctrl_host[kNf] == 0 && round > 1) {
+      if (trace) trace->iterations = round - 1;
+      break;  // nothing active: Delta = 0 from now on, ranks stay
+    }
+    int32_t dir = (int32_t)g->ctrl_host[kDecision];
+    if (dir == GI_DIR_DENSE_PULL && !g->has_csc) dir = GI_DIR_DENSE_PUSH;
+    trace_put(trace, round - 1, g->ctrl_host);
+    if ((st = vset_clear(P.N, s)) != GI_OK) break;
+    float *cin = cb[cur], *cout = cb[cur ^ 1];
+    if (dir == GI_DIR_DENSE_PULL) {
+      OpPRD op{cin, cout, rank, g->inv_out_deg, damping, first_base, inv_n, eps, round == 1 ? 1 : 0};
+      st = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, out_of(P.N), s);
+    } else {
+      OpSum op{cin, dsum};
+      st = launch_push(g, op, dir == GI_DIR_SPARSE_PUSH ? kSrcQueue : kSrcBitmap, P.F, nullptr, OutSet(), sc, s);
+      if (st == GI_OK) {
+        k_prd_vertex<<<grid_for(g, g->n, 256), 256, 0, s>>>(dsum, rank, cout, g->inv_out_deg, g->n, damping,
+                                                            first_base, inv_n, eps, round == 1 ? 1 : 0, P.N->bitmap,
+                                                            P.N->queue, P.N->count);
+        st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+      }
+    }
+    P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
+    P.swap();
+    cur ^= 1;
+  }
+  dev_free(cb[0], s);
+  dev_free(cb[1], s);
+  dev_free(dsum, s);
+  pair_free(P, s);
+  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "prdelta", __FILE__, __LINE__);
+  return st;
+}

@@ -1,0 +1,1043 @@
+// Graph storage, vertexsets, scans, pull tiles, frontier statistics and the
+// direction decision (Beamer / Ligra threshold or the learned selector).
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "gi_internal.cuh"
+
+namespace gi {
+
+// ================================================================ errors ==
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+  set_error("CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
+  return e == cudaErrorMemoryAllocation ? GI_ERR_OOM : GI_ERR_CUDA;
+}
+
+// ============================================================ allocation ==
+// Stream-ordered allocations from the device's default pool; the pool keeps
+// freed memory (release threshold = max) so repeated graph loads reuse it.
+static std::once_flag g_pool_once[64];
+
+int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  GI_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64) {
+    std::call_once(g_pool_once[dev], [dev]() {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+    });
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return GI_ERR_OOM;
+  }
+  return GI_OK;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+int grid_for(const gi_graph *g, int64_t work, int block, int per_sm) {
+  int64_t want = (work + block - 1) / block;
+  int64_t cap = (int64_t)g->num_sms * per_sm;
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+
+// ============================================================= workspace ==
+struct Workspace {
+  int32_t *scan_blocks = nullptr;  // block sums for scans
+  int64_t scan_cap = 0;
+  int32_t *tmp_i32 = nullptr;      // n+1 scratch
+  int32_t *tmp2_i32 = nullptr;     // n+1 scratch
+};
+
+static int ws_get(gi_graph *g, cudaStream_t s) {
+  if (g->ws) return GI_OK;
+  g->ws = new Workspace();
+  int64_t nb = (g->n + 2047) / 2048 + 2;
+  nb = nb < ((g->m + 255) / 256 + 2) ? ((g->m + 255) / 256 + 2) : nb;  // tile counts can exceed n/2048
+  GI_TRY(dev_alloc_n(&g->ws->scan_blocks, nb + 2048, s));
+  g->ws->scan_cap = nb + 2048;
+  GI_TRY(dev_alloc_n(&g->ws->tmp_i32, g->n + 2, s));
+  GI_TRY(dev_alloc_n(&g->ws->tmp2_i32, g->n + 2, s));
+  return GI_OK;
+}
+
+static void ws_free(gi_graph *g, cudaStream_t s) {
+  if (!g->ws) return;
+  dev_free(g->ws->scan_blocks, s);
+  dev_free(g->ws->tmp_i32, s);
+  dev_free(g->ws->tmp2_i32, s);
+  delete g->ws;
+  g->ws = nullptr;
+}
+
+// ================================================================== scan ==
+// Three-phase exclusive scan of int32 counts: per-block scan of 2048 items,
+// scan of the block totals by one block, then add the block offsets.
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *total, int32_t *smem_warp) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = lane < nw ? smem_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) smem_warp[lane] = w;
+  }
+  __syncthreads();
+  int32_t warp_off = warp > 0 ? smem_warp[warp - 1] : 0;
+  *total = smem_warp[nw - 1];
+  __syncthreads();
+  return warp_off + x - v;
+}
+
+__global__ void k_scan_blocks(const int32_t *__restrict__ in, int32_t *__restrict__ out, int64_t n,
+                              int32_t *__restrict__ block_sums) {
+  __shared__ int32_t s[kScanTile];
+  __shared__ int32_t sw[32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + threadIdx.x + k * kScanThreads;
+    s[threadIdx.x + k * kScanThreads] = i < n ? in[i] : 0;
+  }
+  __syncthreads();
+  int32_t loc[kScanItems], sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    loc[k] = sum;
+    sum += s[threadIdx.x * kScanItems + k];
+  }
+  int32_t total;
+  int32_t off = block_exclusive_scan(sum, &total, sw);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) s[threadIdx.x * kScanItems + k] = loc[k] + off;
+  __syncthreads();
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + threadIdx.x + k * kScanThreads;
+    if (i < n) out[i] = s[threadIdx.x + k * kScanThreads];
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// single block: exclusive scan of nb block sums in place; writes grand total to *total_out
+__global__ void k_scan_top(int32_t *sums, int64_t nb, int32_t *total_out) {
+  __shared__ int32_t sw[32];
+  int32_t carry = 0;
+  for (int64_t base = 0; base < nb; base += kScanThreads) {
+    int64_t i = base + threadIdx.x;
+    int32_t v = i < nb ? sums[i] : 0;
+    int32_t total;
+    int32_t ex = block_exclusive_scan(v, &total, sw);
+    if (i < nb) sums[i] = ex + carry;
+    carry += total;
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *__restrict__ block_off) {
+  int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+  int32_t off = block_off[blockIdx.x];
+  for (int k = 0; k < kScanItems; ++k, i += kScanThreads)
+    if (i < n) out[i] += off;
+}
+
+int scan_exclusive(gi_graph *g, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s) {
+  GI_TRY(ws_get(g, s));
+  int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb + 1 > g->ws->scan_cap) {
+    set_error("scan of %lld items exceeds workspace", (long long)n);
+    return GI_ERR_UNSUPPORTED;
+  }
+  if (nb > 0) {
+    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, g->ws->scan_blocks);
+    GI_LAUNCH_CHECK();
+  }
+  k_scan_top<<<1, kScanThreads, 0, s>>>(g->ws->scan_blocks, nb, out + n);
+  GI_LAUNCH_CHECK();
+  if (nb > 0) {
+    k_scan_add<<<(unsigned)nb, kScanThreads, 0, s>>>(out, n, g->ws->scan_blocks);
+    GI_LAUNCH_CHECK();
+  }
+  return GI_OK;
+}
+
+// ============================================================ graph load ==
+__global__ void k_validate(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t n, int64_t m,
+                           int64_t *err) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t a = ptr[v], b = ptr[v + 1];
+    if (a > b || a < 0 || b > m) {
+      atomicCAS(reinterpret_cast<unsigned long long *>(err), 0ull, (unsigned long long)(1 + v));
+      continue;
+    }
+    for (int32_t e = a; e < b; ++e) {
+      int32_t u = idx[e];
+      if (u < 0 || u >= n || (e > a && idx[e - 1] >= u))
+        atomicCAS(reinterpret_cast<unsigned long long *>(err), 0ull, (unsigned long long)(1 + v));
+    }
+  }
+}
+
+__global__ void k_degrees(const int32_t *__restrict__ ptr, int64_t n, int32_t *__restrict__ deg,
+                          float *__restrict__ inv, int32_t *__restrict__ max_deg) {
+  int32_t local_max = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t d = ptr[v + 1] - ptr[v];
+    deg[v] = d;
+    inv[v] = d > 0 ? 1.0f / (float)d : 0.0f;
+    local_max = d > local_max ? d : local_max;
+  }
+  for (int o = 16; o > 0; o >>= 1) local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(max_deg, local_max);
+}
+
+static int copy_in(int32_t **dst, const int32_t *src, int64_t count, uint32_t flags, cudaStream_t s) {
+  GI_TRY(dev_alloc_n(dst, count, s));
+  if (count > 0)
+    GI_CUDA(cudaMemcpyAsync(*dst, src, sizeof(int32_t) * (size_t)count,
+                            (flags & GI_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  return GI_OK;
+}
+
+static int validate_csr_dev(gi_graph *g, const Csr &c, cudaStream_t s) {
+  GI_CUDA(cudaMemsetAsync(g->ctrl + kErr, 0, sizeof(int64_t), s));
+  k_validate<<<grid_for(g, g->n, 256), 256, 0, s>>>(c.ptr, c.idx, g->n, g->m, g->ctrl + kErr);
+  GI_LAUNCH_CHECK();
+  int32_t first_last[2];
+  GI_CUDA(cudaMemcpyAsync(&first_last[0], c.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaMemcpyAsync(&first_last[1], c.ptr + g->n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  int64_t err = 0;
+  GI_CUDA(cudaMemcpyAsync(&err, g->ctrl + kErr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  if (first_last[0] != 0 || first_last[1] != g->m) {
+    set_error("bad graph: offsets[0]=%d offsets[n]=%d, expected 0 and %lld", first_last[0], first_last[1],
+              (long long)g->m);
+    return GI_ERR_BAD_GRAPH;
+  }
+  if (err) {
+    set_error("bad graph: row %lld has non-monotone offsets, an index out of range or an unsorted/duplicate entry",
+              (long long)(err - 1));
+    return GI_ERR_BAD_GRAPH;
+  }
+  return GI_OK;
+}
+
+}  // namespace gi
+
+using namespace gi;
+
+extern "C" const char *gi_last_error(void) { return g_err; }
+extern "C" int gi_version(void) { return 100; }
+
+static void graph_release(gi_graph *g, cudaStream_t s) {
+  if (!g) return;
+  free_tiles(&g->in_tiles, s);
+  if (g->segs.seg) {
+    for (int i = 0; i < g->segs.num; ++i) {
+      dev_free(g->segs.seg[i].ptr, s);
+      dev_free(g->segs.seg[i].idx, s);
+      dev_free(g->segs.seg[i].wt, s);
+      free_tiles(&g->segs.tiles[i], s);
+    }
+    delete[] g->segs.seg;
+    delete[] g->segs.tiles;
+  }
+  if (!g->symmetric) {
+    dev_free(g->in.ptr, s);
+    dev_free(g->in.idx, s);
+    dev_free(g->in.wt, s);
+  }
+  dev_free(g->out.ptr, s);
+  dev_free(g->out.idx, s);
+  dev_free(g->out.wt, s);
+  dev_free(g->out_deg, s);
+  dev_free(g->inv_out_deg, s);
+  dev_free(g->ctrl, s);
+  ws_free(g, s);
+  if (g->ctrl_host) cudaFreeHost(g->ctrl_host);
+  delete g;
+}
+
+extern "C" int gi_load_csr(const int32_t *offsets, const int32_t *indices, const int32_t *weights, int64_t n,
+                           int64_t m, uint32_t flags, void *stream, gi_graph **out) {
+  GI_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  GI_ARG(n >= 0 && m >= 0, "n and m must be >= 0");
+  GI_ARG(((flags & GI_HOST_PTRS) != 0) != ((flags & GI_DEV_PTRS) != 0), "exactly one of GI_HOST_PTRS/GI_DEV_PTRS");
+  GI_ARG(offsets != nullptr, "offsets is NULL");
+  GI_ARG(m == 0 || indices != nullptr, "indices is NULL");
+  if (n >= INT32_MAX || m >= INT32_MAX) {
+    set_error("graphs need n, m < 2^31 (int32 ids and offsets); got n=%lld m=%lld", (long long)n, (long long)m);
+    return GI_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  gi_graph *g = new gi_graph();
+  g->n = n;
+  g->m = m;
+  g->symmetric = (flags & GI_SYMMETRIC) != 0;
+  int st = GI_OK;
+  do {
+    if (cudaGetDevice(&g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "device query", __FILE__, __LINE__);
+      break;
+    }
+    if ((st = dev_alloc_n(&g->ctrl, kCtrlWords, s)) != GI_OK) break;
+    if (cudaMemsetAsync(g->ctrl, 0, sizeof(int64_t) * kCtrlWords, s) != cudaSuccess) { st = GI_ERR_CUDA; break; }
+    if (cudaHostAlloc((void **)&g->ctrl_host, sizeof(int64_t) * kCtrlWords, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("pinned host allocation failed");
+      st = GI_ERR_OOM;
+      break;
+    }
+    if ((st = copy_in(&g->out.ptr, offsets, n + 1, flags, s)) != GI_OK) break;
+    if ((st = copy_in(&g->out.idx, indices, m, flags, s)) != GI_OK) break;
+    if (weights && (st = copy_in(&g->out.wt, weights, m, flags, s)) != GI_OK) break;
+    if ((flags & GI_VALIDATE) && (st = validate_csr_dev(g, g->out, s)) != GI_OK) break;
+    if ((st = dev_alloc_n(&g->out_deg, n, s)) != GI_OK) break;
+    if ((st = dev_alloc_n(&g->inv_out_deg, n, s)) != GI_OK) break;
+    if (cudaMemsetAsync(g->ctrl + kErr, 0, sizeof(int64_t), s) != cudaSuccess) { st = GI_ERR_CUDA; break; }
+    k_degrees<<<grid_for(g, n, 256), 256, 0, s>>>(g->out.ptr, n, g->out_deg, g->inv_out_deg,
+                                                  reinterpret_cast<int32_t *>(g->ctrl + kErr));
+    if ((st = (cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA)) != GI_OK) break;
+    int64_t md = 0;
+    if (cudaMemcpyAsync(&md, g->ctrl + kErr, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "max degree", __FILE__, __LINE__);
+      break;
+    }
+    g->max_deg = (int32_t)(md & 0xffffffff);
+    if (g->symmetric) {
+      g->in = g->out;
+      g->has_csc = true;
+      if ((st = build_tiles(g, g->in, 2048, &g->in_tiles, s)) != GI_OK) break;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "load sync", __FILE__, __LINE__);
+      break;
+    }
+  } while (0);
+  if (st != GI_OK) {
+    cudaStreamSynchronize(s);
+    graph_release(g, s);
+    return st;
+  }
+  *out = g;
+  return GI_OK;
+}
+
+extern "C" int gi_load_csc(gi_graph *g, const int32_t *in_offsets, const int32_t *in_indices,
+                           const int32_t *in_weights, uint32_t flags, void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_ARG(in_offsets != nullptr && (g->m == 0 || in_indices != nullptr), "in-edge arrays are NULL");
+  GI_ARG(((flags & GI_HOST_PTRS) != 0) != ((flags & GI_DEV_PTRS) != 0), "exactly one of GI_HOST_PTRS/GI_DEV_PTRS");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->symmetric) return GI_OK;  // the CSR already is the in-edge view
+  if (g->has_csc) {
+    free_tiles(&g->in_tiles, s);
+    dev_free(g->in.ptr, s);
+    dev_free(g->in.idx, s);
+    dev_free(g->in.wt, s);
+    g->in = Csr();
+    g->has_csc = false;
+  }
+  GI_TRY(copy_in(&g->in.ptr, in_offsets, g->n + 1, flags, s));
+  GI_TRY(copy_in(&g->in.idx, in_indices, g->m, flags, s));
+  if (in_weights) GI_TRY(copy_in(&g->in.wt, in_weights, g->m, flags, s));
+  if (flags & GI_VALIDATE) GI_TRY(validate_csr_dev(g, g->in, s));
+  GI_TRY(build_tiles(g, g->in, 2048, &g->in_tiles, s));
+  g->has_csc = true;
+  GI_CUDA(cudaStreamSynchronize(s));
+  return GI_OK;
+}
+
+extern "C" int gi_graph_free(gi_graph *g) {
+  if (!g) return GI_OK;
+  cudaStream_t s = 0;
+  cudaDeviceSynchronize();
+  graph_release(g, s);
+  GI_CUDA(cudaStreamSynchronize(s));
+  return GI_OK;
+}
+
+extern "C" int gi_graph_info(const gi_graph *g, int64_t *n, int64_t *m, int32_t *max_deg) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (max_deg) *max_deg = g->max_deg;
+  return GI_OK;
+}
+
+extern "C" int gi_graph_device_csr(const gi_graph *g, const int32_t **offsets, const int32_t **indices,
+                                   const int32_t **weights) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  if (offsets) *offsets = g->out.ptr;
+  if (indices) *indices = g->out.idx;
+  if (weights) *weights = g->out.wt;
+  return GI_OK;
+}
+
+namespace gi {
+
+// ================================================================= tiles ==
+// Row r starts a short tile when it is short and (r is the first row, the
+// previous row is long, r is a multiple of kTileRows, or ptr[r] lies in a
+// different tile_edges bucket than ptr[r-1]).  Rows with degree above
+// tile_edges/kLongRowDiv get ceil(deg/tile_edges) tiles of their own.  So a
+// short tile holds at most kTileRows rows and fewer than
+// tile_edges*(1+1/kLongRowDiv) arcs.
+__global__ void k_tile_count(const int32_t *__restrict__ ptr, int64_t n, int32_t te, int32_t *cnt,
+                             int32_t *split_cnt) {
+  const int32_t t_long = te / kLongRowDiv;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    int32_t a = ptr[r], d = ptr[r + 1] - a;
+    int32_t c, sc = 0;
+    if (d > t_long) {
+      c = (d + te - 1) / te;
+      sc = c > 1 ? 1 : 0;
+    } else if (r == 0 || (r % kTileRows) == 0) {
+      c = 1;
+    } else {
+      int32_t pa = ptr[r - 1];
+      bool prev_long = (a - pa) > t_long;
+      c = (prev_long || (a / te) != (pa / te)) ? 1 : 0;
+    }
+    cnt[r] = c;
+    split_cnt[r] = sc;
+  }
+}
+
+__global__ void k_tile_write(const int32_t *__restrict__ ptr, int64_t n, int32_t te, const int32_t *__restrict__ off,
+                             const int32_t *__restrict__ soff, int4 *tiles, int4 *splits, int32_t *tile_row) {
+  const int32_t t_long = te / kLongRowDiv;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    int32_t c = off[r + 1] - off[r];
+    if (c == 0) continue;
+    int32_t t = off[r];
+    int32_t a = ptr[r], d = ptr[r + 1] - a;
+    if (d > t_long) {
+      for (int32_t k = 0; k < c; ++k) {
+        int32_t e0 = a + k * te, e1 = min(a + (k + 1) * te, a + d);
+        tiles[t + k] = make_int4((int32_t)r, c > 1 ? -1 : (int32_t)r, e0, e1);
+        tile_row[t + k] = (int32_t)r;
+      }
+      if (c > 1) splits[soff[r]] = make_int4((int32_t)r, t, c, 0);
+    } else {
+      tiles[t] = make_int4((int32_t)r, 0, 0, 0);  // r1 filled by k_tile_close
+      tile_row[t] = (int32_t)r;
+    }
+  }
+}
+
+// short tile t ends where tile t+1 begins (or at n)
+__global__ void k_tile_close(int4 *tiles, const int32_t *__restrict__ tile_row, int32_t nt, int64_t n) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    int4 x = tiles[t];
+    if (x.y == 0 && x.z == 0 && x.w == 0) {
+      x.y = (t + 1 < nt) ? tile_row[t + 1] : (int32_t)n;
+      tiles[t] = x;
+    }
+  }
+}
+
+int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cudaStream_t s) {
+  free_tiles(ts, s);
+  GI_TRY(ws_get(g, s));
+  ts->tile_edges = tile_edges;
+  int64_t n = g->n;
+  if (n == 0) return GI_OK;
+  int32_t *cnt = g->ws->tmp_i32, *scnt = g->ws->tmp2_i32;
+  int32_t *off = nullptr, *soff = nullptr;
+  GI_TRY(dev_alloc_n(&off, n + 1, s));
+  GI_TRY(dev_alloc_n(&soff, n + 1, s));
+  k_tile_count<<<grid_for(g, n, 256), 256, 0, s>>>(c.ptr, n, tile_edges, cnt, scnt);
+  GI_LAUNCH_CHECK();
+  GI_TRY(scan_exclusive(g, cnt, off, n, s));
+  GI_TRY(scan_exclusive(g, scnt, soff, n, s));
+  int32_t totals[2];
+  GI_CUDA(cudaMemcpyAsync(&totals[0], off + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaMemcpyAsync(&totals[1], soff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  ts->num_tiles = totals[0];
+  ts->num_splits = totals[1];
+  int32_t *tile_row = nullptr;
+  GI_TRY(dev_alloc_n(&ts->tiles, ts->num_tiles, s));
+  GI_TRY(dev_alloc_n(&ts->splits, ts->num_splits, s));
+  GI_TRY(dev_alloc(&ts->partial, 16 * (size_t)(ts->num_tiles > 0 ? ts->num_tiles : 1), s));
+  GI_TRY(dev_alloc_n(&tile_row, ts->num_tiles, s));
+  k_tile_write<<<grid_for(g, n, 256), 256, 0, s>>>(c.ptr, n, tile_edges, off, soff, ts->tiles, ts->splits, tile_row);
+  GI_LAUNCH_CHECK();
+  if (ts->num_tiles > 0) {
+    k_tile_close<<<grid_for(g, ts->num_tiles, 256), 256, 0, s>>>(ts->tiles, tile_row, ts->num_tiles, n);
+    GI_LAUNCH_CHECK();
+  }
+  dev_free(off, s);
+  dev_free(soff, s);
+  dev_free(tile_row, s);
+  return GI_OK;
+}
+
+void free_tiles(TileSet *ts, cudaStream_t s) {
+  dev_free(ts->tiles, s);
+  dev_free(ts->splits, s);
+  dev_free(ts->partial, s);
+  *ts = TileSet();
+}
+
+// ============================================================== segments ==
+// Segment s keeps in-arcs whose source lies in [s*seg, (s+1)*seg), rows kept
+// in destination order and sources ascending (a stable filter of the CSC).
+__global__ void k_seg_count(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t n,
+                            int32_t seg_size, int32_t sid, int32_t *cnt) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    int32_t lo = sid * seg_size, hi = lo + seg_size, c = 0;
+    for (int32_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+      int32_t u = idx[e];
+      c += (u >= lo && u < hi);
+    }
+    cnt[r] = c;
+  }
+}
+
+__global__ void k_seg_fill(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                           const int32_t *__restrict__ wt, int64_t n, int32_t seg_size, int32_t sid,
+                           const int32_t *__restrict__ sptr, int32_t *sidx, int32_t *swt) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    int32_t lo = sid * seg_size, hi = lo + seg_size, o = sptr[r];
+    for (int32_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+      int32_t u = idx[e];
+      if (u >= lo && u < hi) {
+        sidx[o] = u;
+        if (swt) swt[o] = wt[e];
+        ++o;
+      }
+    }
+  }
+}
+
+}  // namespace gi
+
+extern "C" int gi_graph_build_segments(gi_graph *g, int32_t num_segments, void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_ARG(num_segments >= 1 && num_segments <= 1024, "num_segments must be in [1, 1024]");
+  if (!g->has_csc) {
+    set_error("segmented pull needs the in-edges: load a symmetric graph or call gi_load_csc");
+    return GI_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->segs.seg) {
+    for (int i = 0; i < g->segs.num; ++i) {
+      dev_free(g->segs.seg[i].ptr, s);
+      dev_free(g->segs.seg[i].idx, s);
+      dev_free(g->segs.seg[i].wt, s);
+      free_tiles(&g->segs.tiles[i], s);
+    }
+    delete[] g->segs.seg;
+    delete[] g->segs.tiles;
+    g->segs = Segments();
+  }
+  if (num_segments == 1) return GI_OK;
+  GI_TRY(ws_get(g, s));
+  int64_t n = g->n;
+  int32_t seg_size = (int32_t)((n + num_segments - 1) / num_segments);
+  g->segs.num = num_segments;
+  g->segs.seg_size = seg_size;
+  g->segs.seg = new Csr[num_segments];
+  g->segs.tiles = new TileSet[num_segments];
+  for (int sid = 0; sid < num_segments; ++sid) {
+    Csr &c = g->segs.seg[sid];
+    GI_TRY(dev_alloc_n(&c.ptr, n + 1, s));
+    k_seg_count<<<grid_for(g, n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, n, seg_size, sid, g->ws->tmp_i32);
+    GI_LAUNCH_CHECK();
+    GI_TRY(scan_exclusive(g, g->ws->tmp_i32, c.ptr, n, s));
+    int32_t cnt = 0;
+    GI_CUDA(cudaMemcpyAsync(&cnt, c.ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GI_CUDA(cudaStreamSynchronize(s));
+    GI_TRY(dev_alloc_n(&c.idx, cnt, s));
+    if (g->in.wt) GI_TRY(dev_alloc_n(&c.wt, cnt, s));
+    k_seg_fill<<<grid_for(g, n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->in.wt, n, seg_size, sid, c.ptr, c.idx,
+                                                   c.wt);
+    GI_LAUNCH_CHECK();
+    GI_TRY(build_tiles(g, c, g->in_tiles.tile_edges > 0 ? g->in_tiles.tile_edges : 2048, &g->segs.tiles[sid], s));
+  }
+  GI_CUDA(cudaStreamSynchronize(s));
+  return GI_OK;
+}
+
+namespace gi {
+
+// ============================================================ vertexsets ==
+__global__ void k_bitmap_from_queue(const int32_t *__restrict__ q, const int32_t *__restrict__ count, uint32_t *bm) {
+  int32_t c = *count;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+    int32_t v = q[i];
+    atomicOr(bm + (v >> 5), 1u << (v & 31));
+  }
+}
+
+__global__ void k_bitmap_from_bool(const uint8_t *__restrict__ b, int64_t n, uint32_t *bm) {
+  // one warp writes one word: lane i tests vertex 32*w + i
+  int64_t nw = (n + 31) / 32;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    int64_t v = w * 32 + lane_id();
+    unsigned word = __ballot_sync(0xffffffffu, v < n && b[v]);
+    if (lane_id() == 0) bm[w] = word;
+  }
+}
+
+__global__ void k_bool_from_bitmap(const uint32_t *__restrict__ bm, int64_t n, uint8_t *b) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    b[v] = (bm[v >> 5] >> (v & 31)) & 1u;
+}
+
+__global__ void k_word_popc(const uint32_t *__restrict__ bm, int64_t nw, int32_t *cnt) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x)
+    cnt[w] = __popc(bm[w]);
+}
+
+// ordered compaction: word w writes its set bits at off[w]...
+__global__ void k_compact_bitmap(const uint32_t *__restrict__ bm, int64_t nw, const int32_t *__restrict__ off,
+                                 int32_t *q, int32_t *count) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t x = bm[w];
+    int32_t o = off[w];
+    while (x) {
+      int b = __ffs(x) - 1;
+      q[o++] = (int32_t)(w * 32 + b);
+      x &= x - 1;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count = off[nw];
+}
+
+__global__ void k_vset_init(int32_t *q, int32_t *count, uint32_t *bm, int64_t words, int64_t n, int32_t init,
+                            int32_t v) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t word = 0;
+    if (init == GI_VSET_ALL) {
+      int64_t lo = w * 32, rem = n - lo;
+      word = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    } else if (init == GI_VSET_SINGLE && (v >> 5) == w) {
+      word = 1u << (v & 31);
+    }
+    bm[w] = word;
+  }
+  if (init == GI_VSET_ALL) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      q[i] = (int32_t)i;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (init == GI_VSET_SINGLE) q[0] = v;
+    *count = init == GI_VSET_ALL ? (int32_t)n : (init == GI_VSET_SINGLE ? 1 : 0);
+  }
+}
+
+int vset_alloc(gi_graph *g, gi_vset *v, cudaStream_t s) {
+  v->g = g;
+  v->n = g->n;
+  v->words = (g->n + 31) / 32;
+  GI_TRY(dev_alloc_n(&v->queue, g->n, s));
+  GI_TRY(dev_alloc_n(&v->count, 1, s));
+  GI_TRY(dev_alloc_n(&v->bitmap, v->words, s));
+  return GI_OK;
+}
+
+int vset_clear(gi_vset *v, cudaStream_t s) {
+  GI_CUDA(cudaMemsetAsync(v->bitmap, 0, sizeof(uint32_t) * (size_t)(v->words > 0 ? v->words : 1), s));
+  GI_CUDA(cudaMemsetAsync(v->count, 0, sizeof(int32_t), s));
+  if (v->boolmap) GI_CUDA(cudaMemsetAsync(v->boolmap, 0, (size_t)(v->n > 0 ? v->n : 1), s));
+  v->reps = GI_REP_SPARSE | GI_REP_BITMAP | (v->boolmap ? GI_REP_BOOL : 0);
+  return GI_OK;
+}
+
+int vset_ensure_bitmap(gi_vset *v, cudaStream_t s) {
+  if (v->reps & GI_REP_BITMAP) return GI_OK;
+  gi_graph *g = v->g;
+  if (v->reps & GI_REP_BOOL) {
+    k_bitmap_from_bool<<<grid_for(g, v->words * 32, 256), 256, 0, s>>>(v->boolmap, v->n, v->bitmap);
+  } else {
+    GI_CUDA(cudaMemsetAsync(v->bitmap, 0, sizeof(uint32_t) * (size_t)(v->words > 0 ? v->words : 1), s));
+    k_bitmap_from_queue<<<grid_for(g, v->n, 256), 256, 0, s>>>(v->queue, v->count, v->bitmap);
+  }
+  GI_LAUNCH_CHECK();
+  v->reps |= GI_REP_BITMAP;
+  return GI_OK;
+}
+
+int vset_ensure_bool(gi_vset *v, cudaStream_t s) {
+  if (v->reps & GI_REP_BOOL) return GI_OK;
+  if (!v->boolmap) GI_TRY(dev_alloc_n(&v->boolmap, v->n, s));
+  GI_TRY(vset_ensure_bitmap(v, s));
+  k_bool_from_bitmap<<<grid_for(v->g, v->n, 256), 256, 0, s>>>(v->bitmap, v->n, v->boolmap);
+  GI_LAUNCH_CHECK();
+  v->reps |= GI_REP_BOOL;
+  return GI_OK;
+}
+
+// sparse from bitmap: ascending ids (ordered compaction by word popcount scan)
+int vset_ensure_queue(gi_vset *v, cudaStream_t s) {
+  if (v->reps & GI_REP_SPARSE) return GI_OK;
+  GI_TRY(vset_ensure_bitmap(v, s));
+  gi_graph *g = v->g;
+  GI_TRY(ws_get(g, s));
+  k_word_popc<<<grid_for(g, v->words, 256), 256, 0, s>>>(v->bitmap, v->words, g->ws->tmp_i32);
+  GI_LAUNCH_CHECK();
+  GI_TRY(scan_exclusive(g, g->ws->tmp_i32, g->ws->tmp2_i32, v->words, s));
+  k_compact_bitmap<<<grid_for(g, v->words, 256), 256, 0, s>>>(v->bitmap, v->words, g->ws->tmp2_i32, v->queue,
+                                                              v->count);
+  GI_LAUNCH_CHECK();
+  v->reps |= GI_REP_SPARSE;
+  return GI_OK;
+}
+
+}  // namespace gi
+
+extern "C" int gi_vset_create(gi_graph *g, int32_t init, int32_t v, void *stream, gi_vset **out) {
+  GI_ARG(g != nullptr && out != nullptr, "NULL graph or output");
+  GI_ARG(init == GI_VSET_EMPTY || init == GI_VSET_ALL || init == GI_VSET_SINGLE, "unknown init");
+  GI_ARG(init != GI_VSET_SINGLE || (v >= 0 && v < g->n), "vertex out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  gi_vset *x = new gi_vset();
+  int st = vset_alloc(g, x, s);
+  if (st == GI_OK) {
+    k_vset_init<<<grid_for(g, g->n > x->words ? g->n : x->words, 256), 256, 0, s>>>(x->queue, x->count, x->bitmap,
+                                                                                   x->words, g->n, init, v);
+    if (cudaGetLastError() != cudaSuccess) st = GI_ERR_CUDA;
+  }
+  if (st != GI_OK) {
+    gi_vset_free(x);
+    return st;
+  }
+  x->reps = GI_REP_SPARSE | GI_REP_BITMAP;
+  *out = x;
+  return GI_OK;
+}
+
+extern "C" int gi_vset_free(gi_vset *x) {
+  if (!x) return GI_OK;
+  cudaStream_t s = 0;
+  cudaDeviceSynchronize();
+  dev_free(x->queue, s);
+  dev_free(x->count, s);
+  dev_free(x->bitmap, s);
+  dev_free(x->boolmap, s);
+  delete x;
+  GI_CUDA(cudaStreamSynchronize(s));
+  return GI_OK;
+}
+
+extern "C" int gi_vset_reps(const gi_vset *x, uint32_t *reps) {
+  GI_ARG(x != nullptr && reps != nullptr, "NULL argument");
+  *reps = x->reps;
+  return GI_OK;
+}
+
+extern "C" int gi_vset_size(gi_vset *x, int64_t *out, void *stream) {
+  GI_ARG(x != nullptr && out != nullptr, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  GI_TRY(vset_ensure_queue(x, s));
+  int32_t c = 0;
+  GI_CUDA(cudaMemcpyAsync(&c, x->count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  *out = c;
+  return GI_OK;
+}
+
+extern "C" int gi_vset_to_sparse(gi_vset *x, void *stream) {
+  GI_ARG(x != nullptr, "NULL vertexset");
+  return vset_ensure_queue(x, (cudaStream_t)stream);
+}
+
+extern "C" int gi_vset_to_dense(gi_vset *x, uint32_t rep, void *stream) {
+  GI_ARG(x != nullptr, "NULL vertexset");
+  GI_ARG(rep == GI_REP_BOOL || rep == GI_REP_BITMAP, "rep must be GI_REP_BOOL or GI_REP_BITMAP");
+  cudaStream_t s = (cudaStream_t)stream;
+  return rep == GI_REP_BOOL ? vset_ensure_bool(x, s) : vset_ensure_bitmap(x, s);
+}
+
+extern "C" int gi_vset_export(gi_vset *x, int32_t *dev_out, int64_t cap, int64_t *count, void *stream) {
+  GI_ARG(x != nullptr && count != nullptr, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  // ascending order: go through the bitmap
+  GI_TRY(vset_ensure_bitmap(x, s));
+  x->reps = GI_REP_BITMAP | (x->reps & GI_REP_BOOL);
+  GI_TRY(vset_ensure_queue(x, s));
+  int32_t c = 0;
+  GI_CUDA(cudaMemcpyAsync(&c, x->count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  *count = c;
+  if (c > cap) {
+    set_error("vertexset has %d members, output holds %lld", c, (long long)cap);
+    return GI_ERR_INVALID_ARG;
+  }
+  GI_ARG(c == 0 || dev_out != nullptr, "dev_out is NULL");
+  if (c > 0) GI_CUDA(cudaMemcpyAsync(dev_out, x->queue, sizeof(int32_t) * (size_t)c, cudaMemcpyDeviceToDevice, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  return GI_OK;
+}
+
+namespace gi {
+__global__ void k_import(const int32_t *__restrict__ ids, int64_t k, int64_t n, uint32_t *bm, int64_t *err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = ids[i];
+    if (v < 0 || v >= n) {
+      atomicCAS(reinterpret_cast<unsigned long long *>(err), 0ull, (unsigned long long)(i + 1));
+      continue;
+    }
+    atomicOr(bm + (v >> 5), 1u << (v & 31));
+  }
+}
+}  // namespace gi
+
+extern "C" int gi_vset_import(gi_vset *x, const int32_t *dev_ids, int64_t k, void *stream) {
+  GI_ARG(x != nullptr, "NULL vertexset");
+  GI_ARG(k >= 0 && (k == 0 || dev_ids != nullptr), "bad id array");
+  cudaStream_t s = (cudaStream_t)stream;
+  gi_graph *g = x->g;
+  GI_CUDA(cudaMemsetAsync(x->bitmap, 0, sizeof(uint32_t) * (size_t)(x->words > 0 ? x->words : 1), s));
+  GI_CUDA(cudaMemsetAsync(g->ctrl + kErr, 0, sizeof(int64_t), s));
+  if (k > 0) {
+    k_import<<<grid_for(g, k, 256), 256, 0, s>>>(dev_ids, k, x->n, x->bitmap, g->ctrl + kErr);
+    GI_LAUNCH_CHECK();
+  }
+  int64_t err = 0;
+  GI_CUDA(cudaMemcpyAsync(&err, g->ctrl + kErr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  if (err) {
+    set_error("vertex id at position %lld is out of range", (long long)(err - 1));
+    return GI_ERR_INVALID_ARG;
+  }
+  x->reps = GI_REP_BITMAP;
+  return vset_ensure_queue(x, s);
+}
+
+// ========================================================= selector MLP ==
+namespace gi {
+
+constexpr int kDIn = 16, kH = 64, kDOut = 3;
+constexpr int kNParam = kH * kDIn + kH + kH * kH + kH + kDOut * kH + kDOut;
+
+__device__ float d_sel_params[kNParam];
+__device__ float d_sel_mean[kDIn];
+__device__ float d_sel_istd[kDIn];
+static bool g_sel_loaded = false;
+
+bool selector_loaded() { return g_sel_loaded; }
+
+// features of one level (same definition as the selector's training data)
+__device__ void level_features(float *x, int64_t n, int64_t m, int32_t maxdeg, int64_t nf, int64_t mf, int64_t nu,
+                               int64_t mu, int32_t level, int32_t was_pull, int64_t nf_prev) {
+  float V = (float)(n > 0 ? n : 1), E = (float)(m > 0 ? m : 1);
+  x[0] = log2f(1.0f + (float)nf);
+  x[1] = log2f(1.0f + (float)mf);
+  x[2] = log2f(1.0f + (float)nu);
+  x[3] = log2f(1.0f + (float)mu);
+  x[4] = log2f(1.0f + (float)n);
+  x[5] = log2f(1.0f + (float)m);
+  x[6] = (float)nf / V;
+  x[7] = (float)mf / E;
+  x[8] = (float)nu / V;
+  x[9] = (float)mu / E;
+  x[10] = log2f(1.0f + (float)((double)mf / (double)(nf > 0 ? nf : 1)));
+  x[11] = log2f(1.0f + (float)maxdeg);
+  x[12] = log2f(1.0f + (float)((double)m / (double)V));
+  x[13] = log2f(1.0f + (float)level);
+  x[14] = was_pull ? 1.0f : 0.0f;
+  x[15] = log2f(1.0f + (float)nf_prev);
+}
+
+// MLP forward by one block (>= 64 threads); returns argmin of predicted log-time
+__device__ int32_t selector_forward(const float *x_raw, float *sh /* >= 16+64+64+3 floats */) {
+  float *x = sh, *h1 = sh + kDIn, *h2 = h1 + kH, *y = h2 + kH;
+  const float *W1 = d_sel_params, *b1 = W1 + kH * kDIn, *W2 = b1 + kH, *b2 = W2 + kH * kH, *W3 = b2 + kH,
+              *b3 = W3 + kDOut * kH;
+  int t = threadIdx.x;
+  if (t < kDIn) x[t] = (x_raw[t] - d_sel_mean[t]) * d_sel_istd[t];
+  __syncthreads();
+  if (t < kH) {
+    float s = b1[t];
+    for (int i = 0; i < kDIn; ++i) s = fmaf(W1[t * kDIn + i], x[i], s);
+    h1[t] = fmaxf(s, 0.0f);
+  }
+  __syncthreads();
+  if (t < kH) {
+    float s = b2[t];
+    for (int i = 0; i < kH; ++i) s = fmaf(W2[t * kH + i], h1[i], s);
+    h2[t] = fmaxf(s, 0.0f);
+  }
+  __syncthreads();
+  if (t < kDOut) {
+    float s = b3[t];
+    for (int i = 0; i < kH; ++i) s = fmaf(W3[t * kH + i], h2[i], s);
+    y[t] = s;
+  }
+  __syncthreads();
+  int32_t best = 0;
+  for (int j = 1; j < kDOut; ++j)
+    if (y[j] < y[best]) best = j;
+  return best;  // 0 SparsePush, 1 DensePush, 2 DensePull
+}
+
+// ================================================ frontier statistics ==
+// One pass over F's queue sums out-degrees; the last block to finish
+// (ticket) computes the features and the direction for this iteration.
+__global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *__restrict__ count,
+                                  const int32_t *__restrict__ deg, int64_t *ctrl, DecideParams p, int64_t n,
+                                  int64_t m, int32_t maxdeg, int use_selector) {
+  __shared__ unsigned long long s_sum[32];
+  __shared__ float sh[kDIn + kH + kH + 4];
+  __shared__ float feat[kDIn];
+  __shared__ bool last;
+  int32_t c = *count;
+  unsigned long long local = 0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) local += deg[q[i]];
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if (lane_id() == 0) s_sum[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_sum[w];
+    atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kMf), b);
+    __threadfence();
+    unsigned long long t = atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kTicket), 1ull);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  int64_t nf = c;
+  int64_t mf = *(volatile int64_t *)(ctrl + kMf);
+  int64_t nu = ctrl[kNu], mu = ctrl[kMu];
+  if (p.track_unvisited) {
+    nu -= nf;
+    mu -= mf;
+  }
+  int32_t was_pull = (int32_t)ctrl[kWasPull];
+  int64_t nf_prev = ctrl[kNfPrev];
+  if (threadIdx.x == 0) level_features(feat, n, m, maxdeg, nf, mf, nu, mu, p.level, was_pull, nf_prev);
+  __syncthreads();
+  int32_t dir;
+  if (p.mode == 0) {
+    dir = p.forced;
+  } else if (p.mode == 2 && use_selector) {
+    int32_t k = selector_forward(feat, sh);
+    dir = k == 0 ? GI_DIR_SPARSE_PUSH : (k == 1 ? GI_DIR_DENSE_PUSH : GI_DIR_DENSE_PULL);
+  } else {
+    bool dense;
+    if (p.rule == GI_RULE_LIGRA || !p.track_unvisited) {
+      dense = (nf + mf) > m / 20;
+    } else if (!was_pull) {
+      dense = (double)mf > (double)mu / (double)p.alpha;
+    } else {
+      dense = !((double)nf < (double)n / (double)p.beta);
+    }
+    int32_t dense_dir = (p.hybrid_kind == GI_DIR_HYBRID_DPUSH) ? GI_DIR_DENSE_PUSH : GI_DIR_DENSE_PULL;
+    dir = dense ? dense_dir : GI_DIR_SPARSE_PUSH;
+  }
+  if (threadIdx.x < kDIn) reinterpret_cast<float *>(ctrl + kFeat)[threadIdx.x] = feat[threadIdx.x];
+  if (threadIdx.x == 0) {
+    ctrl[kNf] = nf;
+    ctrl[kMf] = mf;
+    ctrl[kNu] = nu;
+    ctrl[kMu] = mu;
+    ctrl[kDecision] = dir;
+    ctrl[kWasPull] = (dir == GI_DIR_DENSE_PULL) ? 1 : 0;
+    ctrl[kLevel] = p.level;
+    ctrl[kNfPrev] = nf;
+    ctrl[kTicket] = 0;
+  }
+}
+
+__global__ void k_ctrl_init(int64_t *ctrl, int64_t nu, int64_t mu) {
+  for (int i = threadIdx.x; i < kCtrlWords; i += blockDim.x) ctrl[i] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctrl[kNu] = nu;
+    ctrl[kMu] = mu;
+  }
+}
+
+int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s) {
+  k_ctrl_init<<<1, 64, 0, s>>>(g->ctrl, nu, mu);
+  GI_LAUNCH_CHECK();
+  return GI_OK;
+}
+
+int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s) {
+  GI_TRY(vset_ensure_queue(F, s));
+  GI_CUDA(cudaMemsetAsync(g->ctrl + kMf, 0, sizeof(int64_t), s));
+  int blocks = g->num_sms * 2;
+  k_frontier_decide<<<blocks, 256, 0, s>>>(F->queue, F->count, g->out_deg, g->ctrl, p, g->n, g->m, g->max_deg,
+                                           g_sel_loaded ? 1 : 0);
+  GI_LAUNCH_CHECK();
+  return GI_OK;
+}
+
+int ctrl_fetch(gi_graph *g, cudaStream_t s) {
+  GI_CUDA(cudaMemcpyAsync(g->ctrl_host, g->ctrl, sizeof(int64_t) * kCtrlWords, cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  return GI_OK;
+}
+
+}  // namespace gi
+
+extern "C" int gi_selector_num_params(void) { return gi::kNParam; }
+
+extern "C" int gi_selector_load(const float *params, int32_t count, const float *mean, const float *inv_std) {
+  GI_ARG(params != nullptr && mean != nullptr && inv_std != nullptr, "NULL argument");
+  GI_ARG(count == gi::kNParam, "selector expects 5443 parameters");
+  GI_CUDA(cudaMemcpyToSymbol(gi::d_sel_params, params, sizeof(float) * gi::kNParam));
+  GI_CUDA(cudaMemcpyToSymbol(gi::d_sel_mean, mean, sizeof(float) * gi::kDIn));
+  GI_CUDA(cudaMemcpyToSymbol(gi::d_sel_istd, inv_std, sizeof(float) * gi::kDIn));
+  gi::g_sel_loaded = true;
+  return GI_OK;
+}
+
+extern "C" void gi_schedule_default(gi_schedule *s) {
+  if (!s) return;
+  s->direction = GI_DIR_HYBRID_PULL;
+  s->dense_rep = GI_REP_BITMAP;
+  s->balance = GI_BAL_EDGE_AWARE;
+  s->num_segments = 1;
+  s->block = 256;
+  s->t_warp = 32;
+  s->t_cta = 1024;
+  s->rule = GI_RULE_BEAMER;
+  s->alpha = 14.0f;
+  s->beta = 24.0f;
+  s->tile_edges = 2048;
+}

@@ -1,0 +1,211 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the public ABI (see include/graphit_gb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+
+#include "../../include/graphit_gb.h"
+
+// ------------------------------------------------------------------ errors --
+namespace gi {
+
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+}  // namespace gi
+
+#define GI_CUDA(call)                                                           \
+  do {                                                                          \
+    cudaError_t _e = (call);                                                    \
+    if (_e != cudaSuccess) return gi::cuda_fail(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define GI_LAUNCH_CHECK() GI_CUDA(cudaGetLastError())
+
+#define GI_ARG(cond, msg)                                   \
+  do {                                                      \
+    if (!(cond)) {                                          \
+      gi::set_error("invalid argument: %s", msg);           \
+      return GI_ERR_INVALID_ARG;                            \
+    }                                                       \
+  } while (0)
+
+#define GI_TRY(expr)            \
+  do {                          \
+    int _s = (expr);            \
+    if (_s != GI_OK) return _s; \
+  } while (0)
+
+namespace gi {
+
+// ------------------------------------------------------------ constants --
+constexpr int kMaxBlock = 1024;
+constexpr int kLongRowDiv = 2;         // rows with degree > tile_edges/kLongRowDiv get their own tiles
+constexpr int kTileRows = 512;         // at most this many rows per short tile
+constexpr int kCtrlWords = 64;         // int64 words in the per-graph control block
+
+// Control-block slots (int64) written by the frontier-statistics kernel.
+enum CtrlSlot {
+  kNf = 0,        // |F|
+  kMf = 1,        // sum of out-degrees over F
+  kNu = 2,        // unvisited vertices (BFS)
+  kMu = 3,        // sum of out-degrees over unvisited vertices
+  kDecision = 4,  // chosen direction (GI_DIR_SPARSE_PUSH / DENSE_PUSH / DENSE_PULL)
+  kWasPull = 5,
+  kLevel = 6,
+  kNfPrev = 7,
+  kTicket = 8,    // last-block ticket of the statistics kernel
+  kErr = 9,       // device-side error flag (bounded waits, bounds checks)
+  kFeat = 16,     // 16 float features stored as float bits in 8 int64 words (slots 16..23)
+};
+
+// --------------------------------------------------------------- graph --
+struct Csr {
+  int32_t *ptr = nullptr;  // n+1
+  int32_t *idx = nullptr;  // m
+  int32_t *wt = nullptr;   // m or null
+};
+
+// Pull tile: {r0, r1, e0, e1}.
+//   r1 >  r0 : short tile, rows [r0, r1), arcs [ptr[r0], ptr[r1])
+//   r1 == r0 : one long row r0, arcs [e0, e1) = the whole row
+//   r1 == -1 : piece [e0, e1) of long row r0 split over several tiles; the
+//              partial result goes to slot = tile index, combined by a fix-up.
+struct TileSet {
+  int4 *tiles = nullptr;
+  int4 *splits = nullptr;  // {row, first tile, piece count, 0}
+  int32_t num_tiles = 0;
+  int32_t num_splits = 0;
+  int32_t tile_edges = 0;
+  void *partial = nullptr;  // 16 bytes per tile (largest reduction value)
+};
+
+struct Segments {
+  int32_t num = 1;
+  int32_t seg_size = 0;       // vertices per source segment
+  Csr *seg = nullptr;         // host array of per-segment CSCs (device pointers)
+  TileSet *tiles = nullptr;   // host array: tiles of each segment
+};
+
+struct Workspace;  // per-graph scratch (frontiers, buffers); defined in gi_core.cu
+
+}  // namespace gi
+
+struct gi_graph {
+  int64_t n = 0, m = 0;
+  int32_t max_deg = 0;
+  bool symmetric = false;
+  bool has_csc = false;
+  gi::Csr out;            // CSR (out-edges)
+  gi::Csr in;             // CSC (in-edges); aliases `out` when symmetric
+  int32_t *out_deg = nullptr;
+  float *inv_out_deg = nullptr;  // 1/outdeg (0 for degree 0)
+  gi::TileSet in_tiles;          // tiles over the in-edges for pull
+  gi::Segments segs;
+  int64_t *ctrl = nullptr;       // device control block (kCtrlWords)
+  int64_t *ctrl_host = nullptr;  // pinned mirror
+  gi::Workspace *ws = nullptr;
+  int device = 0;
+  int num_sms = 0;
+};
+
+struct gi_vset {
+  gi_graph *g = nullptr;
+  int64_t n = 0;
+  uint32_t reps = 0;          // valid representations (GI_REP_*)
+  int32_t *queue = nullptr;   // n entries
+  int32_t *count = nullptr;   // device counter (int32) for the queue
+  uint8_t *boolmap = nullptr; // n bytes (allocated on first use)
+  uint32_t *bitmap = nullptr; // (n+31)/32 words
+  int64_t words = 0;
+};
+
+namespace gi {
+
+// ---------------------------------------------------------- allocation --
+int dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+template <class T>
+inline int dev_alloc_n(T **p, int64_t n, cudaStream_t s) {
+  return dev_alloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)(n > 0 ? n : 1), s);
+}
+
+// --------------------------------------------------------------- utils --
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+int grid_for(const gi_graph *g, int64_t work, int block, int per_sm = 8);
+
+// exclusive scan of n int32 counts into out[n+1] (out[n] = total); scratch owned by g's workspace
+int scan_exclusive(gi_graph *g, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+
+// tiles
+int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cudaStream_t s);
+void free_tiles(TileSet *ts, cudaStream_t s);
+
+// vertexset internals
+int vset_alloc(gi_graph *g, gi_vset *v, cudaStream_t s);
+int vset_clear(gi_vset *v, cudaStream_t s);       // empty set, all reps valid (bitmap + queue)
+int vset_ensure_bitmap(gi_vset *v, cudaStream_t s);
+int vset_ensure_queue(gi_vset *v, cudaStream_t s);
+int vset_ensure_bool(gi_vset *v, cudaStream_t s);
+
+// frontier statistics + direction decision (fused); reads F's queue.
+// mode: 0 = forced direction `forced`, 1 = rule (hybrid), 2 = learned.
+struct DecideParams {
+  int32_t mode;
+  int32_t forced;      // GI_DIR_* when mode == 0
+  int32_t hybrid_kind; // GI_DIR_HYBRID_PULL or GI_DIR_HYBRID_DPUSH
+  int32_t rule;
+  float alpha, beta;
+  int32_t track_unvisited;  // subtract |F|, m_f from n_u, m_u after deciding (BFS)
+  int32_t level;
+};
+int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s);
+int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s);
+int ctrl_fetch(gi_graph *g, cudaStream_t s);  // copies ctrl to pinned host + syncs
+
+// selector weights (device constant memory) and state
+bool selector_loaded();
+
+// traversal entry (gi_traverse.cu)
+int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const gi_schedule &sc, int32_t kernel_id,
+                   const void *args, gi_vset *out, uint32_t flags, cudaStream_t s);
+
+// schedule helpers (gi_traverse.cu)
+int check_schedule(const gi_schedule *sc);
+DecideParams decide_params(const gi_schedule &sc, int32_t level, bool track_unvisited);
+int ensure_tiles(gi_graph *g, const gi_schedule &sc, cudaStream_t s);
+
+}  // namespace gi
+
+// ----------------------------------------------------------- device helpers --
+namespace gi {
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ bool bit_test(const uint32_t *bm, int32_t v) {
+  return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// set bit; returns true if this call changed it from 0 to 1
+__device__ __forceinline__ bool bit_test_and_set(uint32_t *bm, int32_t v) {
+  uint32_t mask = 1u << (v & 31);
+  uint32_t old = atomicOr(bm + (v >> 5), mask);
+  return (old & mask) == 0;
+}
+
+// warp-aggregated append of `v` (for lanes with `want`) to queue/count
+__device__ __forceinline__ void warp_append(int32_t *queue, int32_t *count, bool want, int32_t v) {
+  unsigned active = __activemask();
+  unsigned ball = __ballot_sync(active, want);
+  if (!ball) return;
+  int leader = __ffs(ball) - 1;
+  int base = 0;
+  if (lane_id() == leader) base = atomicAdd(count, __popc(ball));
+  base = __shfl_sync(active, base, leader);
+  if (want) queue[base + __popc(ball & ((1u << lane_id()) - 1))] = v;
+}
+
+}  // namespace gi

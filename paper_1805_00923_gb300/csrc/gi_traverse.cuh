@@ -1,0 +1,562 @@
+// Edge functions and traversal kernels (templates), shared by the edgeset
+// apply entry point and the algorithm drivers.
+//
+// Directions follow Sec. 2 of the paper: SparsePush iterates the frontier's
+// out-edges and updates destinations with atomics; DensePush scans every
+// vertex, tests frontier membership and pushes like SparsePush; DensePull
+// iterates destinations and reads in-edges, updating its own destination
+// without atomics (the dependence rules of Sec. 6).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gi_internal.cuh"
+
+namespace gi {
+
+// Where a traversal reports modified destinations (applyModified): the bit is
+// set in `bm` and the vertex appended to `q` (count in *qc).  With dedup the
+// append happens only for the call that set the bit.
+struct OutSet {
+  uint32_t *bm = nullptr;
+  int32_t *q = nullptr;
+  int32_t *qc = nullptr;
+  bool dedup = true;
+  __device__ __forceinline__ bool enabled() const { return bm != nullptr; }
+};
+
+__device__ __forceinline__ void out_mark(const OutSet &o, int32_t v) {
+  bool fresh;
+  if (o.dedup) {
+    fresh = bit_test_and_set(o.bm, v);
+  } else {
+    atomicOr(o.bm + (v >> 5), 1u << (v & 31));
+    fresh = true;
+  }
+  if (fresh) {
+    int32_t pos = atomicAdd(o.qc, 1);
+    o.q[pos] = v;
+  }
+}
+
+__device__ __forceinline__ bool in_set(const uint32_t *bm, int32_t v) { return bm == nullptr || bit_test(bm, v); }
+
+// Whole-warp marking when lane l owns destination v0 + l (each destination is
+// owned by one thread, so no test-and-set is needed): the ballot is split over
+// the (at most two) bitmap words the 32 ids touch, and the queue append is
+// one atomicAdd per warp.
+__device__ __forceinline__ void mark_consecutive(const OutSet &o, int32_t v0, bool mod) {
+  const unsigned ball = __ballot_sync(0xffffffffu, mod);
+  if (!ball) return;
+  const int lane = threadIdx.x & 31;
+  const int32_t w_lo = v0 >> 5, sh = v0 & 31;
+  if (lane == 0) {
+    const unsigned lo = ball << sh;
+    const unsigned hi = sh ? (ball >> (32 - sh)) : 0u;
+    if (lo) atomicOr(o.bm + w_lo, lo);
+    if (hi) atomicOr(o.bm + w_lo + 1, hi);
+  }
+  int32_t base = 0;
+  if (lane == 0) base = atomicAdd(o.qc, __popc(ball));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (mod) o.q[base + __popc(ball & ((1u << lane) - 1u))] = v0 + lane;
+}
+
+// ------------------------------------------------------------ edge functions --
+// Each op provides:
+//   V, identity(), combine(a,b)         reduction used by pull
+//   edge_val(u, e)                      value one selected in-edge contributes
+//   finish(v, acc) -> bool              pull epilogue for destination v; true if modified
+//   push(u, v, e) -> bool               atomic update for push; true if v modified
+//   dst_ok(v)                           dstFilter (true = keep)
+
+struct OpMinInt {  // CC (no weights) and SSSP (weights): x[v] = min(x[v], snap[u] + w)
+  using V = int32_t;
+  int32_t *x;
+  const int32_t *snap;
+  const int32_t *wt;  // pull: in-edge weights; push: out-edge weights (same array for symmetric graphs)
+  __device__ static V identity() { return INT32_MAX; }
+  __device__ static V combine(V a, V b) { return a < b ? a : b; }
+  __device__ V edge_val(int32_t u, int32_t e) const {
+    int32_t s = __ldg(snap + u);
+    if (s == INT32_MAX) return INT32_MAX;
+    long long t = (long long)s + (wt ? __ldg(wt + e) : 0);
+    return t < INT32_MAX ? (int32_t)t : INT32_MAX;
+  }
+  __device__ bool dst_ok(int32_t) const { return true; }
+  __device__ bool finish(int32_t v, V acc) const {
+    if (acc < x[v]) {
+      x[v] = acc;
+      return true;
+    }
+    return false;
+  }
+  __device__ bool push(int32_t u, int32_t v, int32_t e) const {
+    V c = edge_val(u, e);
+    if (c >= *(volatile int32_t *)(x + v)) return false;
+    return c < atomicMin(x + v, c);
+  }
+};
+
+struct SumCount {
+  float s;
+  int32_t c;
+};
+
+struct OpSum {  // acc[v] += contrib[u]; modified = destinations with a selected in-edge
+  using V = SumCount;
+  const float *contrib;
+  float *acc;
+  __device__ static V identity() { return {0.0f, 0}; }
+  __device__ static V combine(V a, V b) { return {a.s + b.s, a.c + b.c}; }
+  __device__ V edge_val(int32_t u, int32_t) const { return {__ldg(contrib + u), 1}; }
+  __device__ bool dst_ok(int32_t) const { return true; }
+  __device__ bool finish(int32_t v, V a) const {
+    if (a.c > 0) acc[v] += a.s;
+    return a.c > 0;
+  }
+  __device__ bool push(int32_t u, int32_t v, int32_t) const {
+    atomicAdd(acc + v, __ldg(contrib + u));
+    return true;
+  }
+};
+
+struct ProbeVal {
+  int32_t c;
+  unsigned long long s;
+};
+
+struct OpProbe {  // count[v] += 1, srcsum[v] += u+1 per selected edge (u,v)
+  using V = ProbeVal;
+  int32_t *count;
+  unsigned long long *srcsum;
+  __device__ static V identity() { return {0, 0ull}; }
+  __device__ static V combine(V a, V b) { return {a.c + b.c, a.s + b.s}; }
+  __device__ V edge_val(int32_t u, int32_t) const { return {1, (unsigned long long)u + 1ull}; }
+  __device__ bool dst_ok(int32_t) const { return true; }
+  __device__ bool finish(int32_t v, V a) const {
+    if (a.c > 0) {
+      count[v] += a.c;
+      srcsum[v] += a.s;
+    }
+    return a.c > 0;
+  }
+  __device__ bool push(int32_t u, int32_t v, int32_t) const {
+    atomicAdd(count + v, 1);
+    atomicAdd(srcsum + v, (unsigned long long)u + 1ull);
+    return true;
+  }
+};
+
+// PageRank pull with the vertex update fused into the epilogue:
+// r = base + d * sum; contrib_out[v] = r / outdeg (or rank_out[v] = r on the last iteration)
+struct OpPR {
+  using V = float;
+  const float *contrib;
+  float *contrib_out;
+  float *rank_out;
+  const float *inv_deg;
+  float base, damping;
+  __device__ static V identity() { return 0.0f; }
+  __device__ static V combine(V a, V b) { return a + b; }
+  __device__ V edge_val(int32_t u, int32_t) const { return __ldg(contrib + u); }
+  __device__ bool dst_ok(int32_t) const { return true; }
+  __device__ bool finish(int32_t v, V s) const {
+    float r = fmaf(damping, s, base);
+    if (rank_out) rank_out[v] = r;
+    else contrib_out[v] = r * __ldg(inv_deg + v);
+    return false;
+  }
+  __device__ bool push(int32_t, int32_t, int32_t) const { return false; }
+};
+
+// PageRankDelta pull round with the vertex filter of Fig. 1 fused into the
+// epilogue.  contrib[u] = Delta[u]/outdeg(u) for active u and 0 otherwise, so
+// the sum over all in-edges equals the sum over frontier sources.
+struct OpPRD {
+  using V = float;
+  const float *contrib;
+  float *contrib_out;
+  float *rank;
+  const float *inv_deg;
+  float damping, first_base, inv_n, eps;
+  int32_t first_round;
+  __device__ static V identity() { return 0.0f; }
+  __device__ static V combine(V a, V b) { return a + b; }
+  __device__ V edge_val(int32_t u, int32_t) const { return __ldg(contrib + u); }
+  __device__ bool dst_ok(int32_t) const { return true; }
+  __device__ bool finish(int32_t v, V s) const {
+    float delta, r = rank[v];
+    if (first_round) {
+      delta = fmaf(damping, s, first_base);
+      r += delta;
+      delta -= inv_n;
+    } else {
+      delta = damping * s;
+      r += delta;
+    }
+    rank[v] = r;
+    bool active = fabsf(delta) > eps * r;
+    contrib_out[v] = active ? delta * __ldg(inv_deg + v) : 0.0f;
+    return active;
+  }
+  __device__ bool push(int32_t, int32_t, int32_t) const { return false; }
+};
+
+struct OpBFS {  // dstFilter depth[v] == -1; depth[v] = level, parent[v] = min frontier in-neighbour
+  int32_t *depth;
+  int32_t *parent;
+  int32_t level;
+  __device__ bool push(int32_t u, int32_t v, int32_t) const {
+    int32_t d = *(volatile int32_t *)(depth + v);
+    if (d != -1 && d != level) return false;
+    bool won = false;
+    if (d == -1) {
+      int32_t old = atomicCAS(depth + v, -1, level);
+      won = (old == -1);
+      if (!won && old != level) return false;
+    }
+    if (parent && u < *(volatile int32_t *)(parent + v)) atomicMin(parent + v, u);
+    return won;
+  }
+};
+
+// ------------------------------------------------------------------ reductions --
+template <class V, class Op>
+__device__ __forceinline__ V warp_reduce(V x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    V y;
+    if constexpr (sizeof(V) == 4) {
+      int32_t bits = __shfl_xor_sync(0xffffffffu, *reinterpret_cast<int32_t *>(&x), o);
+      y = *reinterpret_cast<V *>(&bits);
+    } else if constexpr (sizeof(V) == 8) {
+      long long bits = __shfl_xor_sync(0xffffffffu, *reinterpret_cast<long long *>(&x), o);
+      y = *reinterpret_cast<V *>(&bits);
+    } else {
+      static_assert(sizeof(V) == 16, "unsupported reduction type");
+      int4 bits = *reinterpret_cast<int4 *>(&x);
+      bits.x = __shfl_xor_sync(0xffffffffu, bits.x, o);
+      bits.y = __shfl_xor_sync(0xffffffffu, bits.y, o);
+      bits.z = __shfl_xor_sync(0xffffffffu, bits.z, o);
+      bits.w = __shfl_xor_sync(0xffffffffu, bits.w, o);
+      y = *reinterpret_cast<V *>(&bits);
+    }
+    x = Op::combine(x, y);
+  }
+  return x;
+}
+
+// ------------------------------------------------------------------ tiled pull --
+// One block per tile (see TileSet).  Short tiles stage the selected in-edge
+// values of all their rows in shared memory with coalesced loads, then reduce
+// row by row (a thread per row below 32 arcs, the owning warp above); long
+// rows are reduced by the whole block.  Pieces of split rows leave a partial
+// value that k_pull_fixup combines in tile order (deterministic).
+template <class Op, int kBlock>
+__global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__restrict__ ptr,
+                                                       const int32_t *__restrict__ idx, const int4 *__restrict__ tiles,
+                                                       int32_t num_tiles, int32_t tile_edges,
+                                                       const uint32_t *__restrict__ F, const uint32_t *__restrict__ to,
+                                                       OutSet out, typename Op::V *partial) {
+  using V = typename Op::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *vals = reinterpret_cast<V *>(smem_raw);
+  int32_t *rp = reinterpret_cast<int32_t *>(smem_raw + sizeof(V) * (size_t)(tile_edges + tile_edges / kLongRowDiv));
+  __shared__ V s_red[kBlock / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+    const int4 T = tiles[t];
+    if (T.y > T.x) {
+      const int32_t r0 = T.x, R = T.y - T.x;
+      for (int i = tid; i <= R; i += kBlock) rp[i] = __ldg(ptr + r0 + i);
+      __syncthreads();
+      const int32_t e0 = rp[0], ne = rp[R] - e0;
+      for (int32_t k = tid; k < ne; k += kBlock) {
+        int32_t u = __ldg(idx + e0 + k);
+        vals[k] = in_set(F, u) ? op.edge_val(u, e0 + k) : Op::identity();
+      }
+      __syncthreads();
+      for (int i0 = 0; i0 < R; i0 += kBlock) {
+        const int i = i0 + tid;
+        const bool valid = i < R;
+        int32_t a = 0, b = 0;
+        if (valid) {
+          a = rp[i] - e0;
+          b = rp[i + 1] - e0;
+        }
+        const bool big = valid && (b - a) >= 32;
+        V acc = Op::identity();
+        if (valid && !big)
+          for (int32_t k = a; k < b; ++k) acc = Op::combine(acc, vals[k]);
+        unsigned bal = __ballot_sync(0xffffffffu, big);
+        while (bal) {
+          const int l = __ffs(bal) - 1;
+          bal &= bal - 1;
+          const int32_t la = __shfl_sync(0xffffffffu, a, l), lb = __shfl_sync(0xffffffffu, b, l);
+          V x = Op::identity();
+          for (int32_t k = la + lane; k < lb; k += 32) x = Op::combine(x, vals[k]);
+          x = warp_reduce<V, Op>(x);
+          if (lane == l) acc = x;
+        }
+        const int32_t v = r0 + i;
+        bool mod = false;
+        if (valid && in_set(to, v) && op.dst_ok(v)) mod = op.finish(v, acc);
+        if (out.enabled()) mark_consecutive(out, r0 + i0, mod);
+      }
+      __syncthreads();
+    } else {
+      const int32_t r = T.x, e0 = T.z, e1 = T.w;
+      V x = Op::identity();
+#pragma unroll 4
+      for (int32_t e = e0 + tid; e < e1; e += kBlock) {
+        int32_t u = __ldg(idx + e);
+        if (in_set(F, u)) x = Op::combine(x, op.edge_val(u, e));
+      }
+      x = warp_reduce<V, Op>(x);
+      if (lane == 0) s_red[warp] = x;
+      __syncthreads();
+      if (tid == 0) {
+        V y = Op::identity();
+        for (int w = 0; w < kBlock / 32; ++w) y = Op::combine(y, s_red[w]);
+        if (T.y == r) {
+          if (in_set(to, r) && op.dst_ok(r) && op.finish(r, y) && out.enabled()) out_mark(out, r);
+        } else {
+          partial[t] = y;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <class Op>
+__global__ void k_pull_fixup(Op op, const int4 *__restrict__ splits, int32_t num_splits,
+                             const typename Op::V *__restrict__ partial, const uint32_t *__restrict__ to, OutSet out) {
+  using V = typename Op::V;
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < num_splits; s += gridDim.x * blockDim.x) {
+    const int4 S = splits[s];
+    V y = Op::identity();
+    for (int32_t k = 0; k < S.z; ++k) y = Op::combine(y, partial[S.y + k]);
+    if (in_set(to, S.x) && op.dst_ok(S.x) && op.finish(S.x, y) && out.enabled()) out_mark(out, S.x);
+  }
+}
+
+// ------------------------------------------------------------- BFS pull ------
+// DensePull for BFS with early exit (Sec. 2): a warp owns 32 consecutive
+// destinations (one output bitmap word).  Unvisited destinations scan their
+// in-neighbours in ascending order and stop at the first frontier member,
+// which is the smallest-id parent.  Rows with at least t_warp arcs are
+// scanned by the whole warp 32 arcs at a time (ballot picks the first hit).
+static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                                  int64_t n, const uint32_t *__restrict__ F,
+                                                  const uint32_t *__restrict__ to, int32_t *depth, int32_t *parent,
+                                                  int32_t level, int32_t t_warp, uint32_t *out_bm, int32_t *out_q,
+                                                  int32_t *out_qc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (n + 31) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t v = w * 32 + lane;
+    bool active = v < n && depth[v] == -1 && in_set(to, (int32_t)v);
+    int32_t a = 0, b = 0;
+    if (active) {
+      a = __ldg(ptr + v);
+      b = __ldg(ptr + v + 1);
+    }
+    int32_t found = -1;
+    const bool big = active && (b - a) >= t_warp;
+    if (active && !big) {
+      for (int32_t e = a; e < b; ++e) {
+        int32_t u = __ldg(idx + e);
+        if (in_set(F, u)) {
+          found = u;
+          break;
+        }
+      }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, big);
+    while (bal) {
+      const int l = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int32_t la = __shfl_sync(0xffffffffu, a, l), lb = __shfl_sync(0xffffffffu, b, l);
+      int32_t hit = -1;
+      for (int32_t base = la; base < lb; base += 32) {
+        const int32_t e = base + lane;
+        int32_t u = e < lb ? __ldg(idx + e) : 0;
+        unsigned h = __ballot_sync(0xffffffffu, e < lb && in_set(F, u));
+        if (h) {
+          hit = __shfl_sync(0xffffffffu, u, __ffs(h) - 1);
+          break;
+        }
+      }
+      if (lane == l) found = hit;
+    }
+    const bool got = found >= 0;
+    if (got) {
+      depth[v] = level;
+      if (parent) parent[v] = found;
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, got);
+    if (out_bm == nullptr) continue;
+    if (lane == 0 && word) out_bm[w] |= word;
+    if (word) {
+      int32_t base = 0;
+      if (lane == 0) base = atomicAdd(out_qc, __popc(word));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (got) out_q[base + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------- push ------
+// Push from a frontier given as a queue (SparsePush), a bitmap scanned over
+// all vertices (DensePush) or all vertices (from = all).  Load balance
+// (edge-aware mode): sources with >= t_cta arcs are expanded by the whole
+// block, >= t_warp by their warp, the rest by their own thread.  Vertex-parallel
+// mode passes t_warp = t_cta = INT32_MAX.
+enum SrcMode { kSrcQueue = 0, kSrcBitmap = 1, kSrcAll = 2 };
+
+template <class Op>
+__device__ __forceinline__ void push_edge(const Op &op, int32_t u, int32_t e, const int32_t *__restrict__ idx,
+                                          const uint32_t *__restrict__ to, const OutSet &out) {
+  const int32_t v = __ldg(idx + e);
+  const bool mod = in_set(to, v) && op.push(u, v, e);
+  if (out.enabled()) {
+    bool fresh = false;
+    if (mod) {
+      if (out.dedup) {
+        fresh = bit_test_and_set(out.bm, v);
+      } else {
+        atomicOr(out.bm + (v >> 5), 1u << (v & 31));
+        fresh = true;
+      }
+    }
+    warp_append(out.q, out.qc, fresh, v);
+  }
+}
+
+template <class Op, int kMode>
+__global__ void __launch_bounds__(256) k_push(Op op, const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                              const int32_t *__restrict__ q, const int32_t *__restrict__ qcount,
+                                              const uint32_t *__restrict__ Fbm, int64_t n,
+                                              const uint32_t *__restrict__ to, OutSet out, int32_t t_warp,
+                                              int32_t t_cta) {
+  __shared__ int32_t s_owner, s_u, s_a, s_deg;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t total = (kMode == kSrcQueue) ? (int64_t)(*qcount) : n;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + tid;
+    int32_t u = -1, a = 0, deg = 0;
+    if (i < total) {
+      if (kMode == kSrcQueue) u = q[i];
+      else if (kMode == kSrcBitmap) u = bit_test(Fbm, (int32_t)i) ? (int32_t)i : -1;
+      else u = (int32_t)i;
+      if (u >= 0) {
+        a = __ldg(ptr + u);
+        deg = __ldg(ptr + u + 1) - a;
+      }
+    }
+    // block-cooperative expansion of very high-degree sources
+    while (true) {
+      if (tid == 0) s_owner = -1;
+      __syncthreads();
+      if (deg >= t_cta) s_owner = tid;
+      __syncthreads();
+      const int owner = s_owner;
+      if (owner < 0) break;
+      if (tid == owner) {
+        s_u = u;
+        s_a = a;
+        s_deg = deg;
+        deg = 0;
+      }
+      __syncthreads();
+      const int32_t cu = s_u, ca = s_a, cd = s_deg;
+      for (int32_t k = tid; k < cd; k += blockDim.x) push_edge(op, cu, ca + k, idx, to, out);
+      __syncthreads();
+    }
+    // warp-cooperative expansion
+    while (true) {
+      unsigned bal = __ballot_sync(0xffffffffu, deg >= t_warp);
+      if (!bal) break;
+      const int l = __ffs(bal) - 1;
+      const int32_t wu = __shfl_sync(0xffffffffu, u, l), wa = __shfl_sync(0xffffffffu, a, l),
+                    wd = __shfl_sync(0xffffffffu, deg, l);
+      if (lane == l) deg = 0;
+      for (int32_t k = lane; k < wd; k += 32) push_edge(op, wu, wa + k, idx, to, out);
+    }
+    for (int32_t k = 0; k < deg; ++k) push_edge(op, u, a + k, idx, to, out);
+  }
+}
+
+}  // namespace gi
+
+// =================================================================== host side ==
+namespace gi {
+
+template <class Op>
+size_t pull_smem_bytes(int32_t tile_edges) {
+  return sizeof(typename Op::V) * (size_t)(tile_edges + tile_edges / kLongRowDiv) + sizeof(int32_t) * (kTileRows + 1);
+}
+
+// Tiled pull over the in-edges `c` with tiles `ts` (the whole graph or one segment).
+template <class Op>
+int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts, const uint32_t *F,
+                      const uint32_t *to, const OutSet &out, cudaStream_t s) {
+  if (ts.num_tiles == 0) return GI_OK;
+  constexpr int kB = 256;
+  const size_t smem = pull_smem_bytes<Op>(ts.tile_edges);
+  if (smem > 48 * 1024) {
+    GI_CUDA(cudaFuncSetAttribute(k_pull_tiled<Op, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  k_pull_tiled<Op, kB><<<ts.num_tiles, kB, smem, s>>>(op, c.ptr, c.idx, ts.tiles, ts.num_tiles, ts.tile_edges, F, to,
+                                                      out, reinterpret_cast<typename Op::V *>(ts.partial));
+  GI_LAUNCH_CHECK();
+  if (ts.num_splits > 0) {
+    k_pull_fixup<Op><<<div_up(ts.num_splits, 128), 128, 0, s>>>(
+        op, ts.splits, ts.num_splits, reinterpret_cast<const typename Op::V *>(ts.partial), to, out);
+    GI_LAUNCH_CHECK();
+  }
+  return GI_OK;
+}
+
+// Push along the out-edges.  mode: kSrcQueue (from's queue), kSrcBitmap (scan
+// from's bitmap over all vertices), kSrcAll.
+template <class Op>
+int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const uint32_t *to, const OutSet &out,
+                const gi_schedule &sc, cudaStream_t s) {
+  int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
+  int32_t tc = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_cta > 0 ? sc.t_cta : 1024);
+  int block = sc.block >= 64 && sc.block <= 256 && sc.block % 32 == 0 ? sc.block : 256;
+  int grid;
+  if (mode == kSrcQueue) {
+    grid = g->num_sms * (2048 / block);
+    k_push<Op, kSrcQueue><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, from->queue, from->count, nullptr, g->n,
+                                                 to, out, tw, tc);
+  } else if (mode == kSrcBitmap) {
+    grid = grid_for(g, g->n, block, 2048 / block);
+    k_push<Op, kSrcBitmap><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, from->bitmap, g->n,
+                                                  to, out, tw, tc);
+  } else {
+    grid = grid_for(g, g->n, block, 2048 / block);
+    k_push<Op, kSrcAll><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, nullptr, g->n, to, out,
+                                               tw, tc);
+  }
+  GI_LAUNCH_CHECK();
+  return GI_OK;
+}
+
+inline OutSet out_of(gi_vset *v, bool dedup = true) {
+  OutSet o;
+  if (v) {
+    o.bm = v->bitmap;
+    o.q = v->queue;
+    o.qc = v->count;
+    o.dedup = dedup;
+  }
+  return o;
+}
+
+}  // namespace gi

@@ -1,0 +1,84 @@
+"""The C ABI library loads and exports every function include/*.h declares.
+
+Only argument checks run here (they return before any CUDA call), so this
+needs no GPU.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(?:int|void|const char\s*\*)\s*\*?\s*(gi_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1805_00923_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_functions():
+    names = _declared()
+    assert "gi_load_csr" in names and "gi_edgeset_apply" in names and "gi_bfs" in names
+    assert len(names) >= 25
+
+
+def test_every_declared_symbol_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header(lib):
+    from paper_1805_00923_gb300 import _lib
+    assert set(_declared()) <= set(_lib.SIGNATURES), set(_declared()) - set(_lib.SIGNATURES)
+
+
+def test_argument_errors_without_gpu(lib):
+    from paper_1805_00923_gb300 import _lib as L
+    out = ctypes.c_void_p()
+    a = (ctypes.c_int32 * 2)(0, 0)
+    # NULL output handle
+    assert lib.gi_load_csr(a, a, None, 1, 0, L.GI_HOST_PTRS, None, None) == L.GI_ERR_INVALID_ARG
+    # negative sizes
+    assert lib.gi_load_csr(a, a, None, -1, 0, L.GI_HOST_PTRS, None, ctypes.byref(out)) == L.GI_ERR_INVALID_ARG
+    # both / neither pointer kinds
+    assert lib.gi_load_csr(a, a, None, 1, 0, L.GI_HOST_PTRS | L.GI_DEV_PTRS, None,
+                           ctypes.byref(out)) == L.GI_ERR_INVALID_ARG
+    assert lib.gi_load_csr(a, a, None, 1, 0, 0, None, ctypes.byref(out)) == L.GI_ERR_INVALID_ARG
+    # too large for int32 offsets
+    assert lib.gi_load_csr(a, a, None, 1, 2**31, L.GI_HOST_PTRS, None, ctypes.byref(out)) == L.GI_ERR_UNSUPPORTED
+    assert b"int32" in lib.gi_last_error()
+    # NULL graph handles
+    s = L.gi_schedule()
+    lib.gi_schedule_default(ctypes.byref(s))
+    assert lib.gi_bfs(None, 0, None, None, ctypes.byref(s), None, None) == L.GI_ERR_INVALID_ARG
+    assert lib.gi_pagerank(None, 0.85, 20, None, ctypes.byref(s), None) == L.GI_ERR_INVALID_ARG
+    assert lib.gi_graph_free(None) == L.GI_OK
+    assert lib.gi_selector_load(None, 0, None, None) == L.GI_ERR_INVALID_ARG
+
+
+def test_schedule_defaults(lib):
+    from paper_1805_00923_gb300 import _lib as L
+    s = L.gi_schedule()
+    lib.gi_schedule_default(ctypes.byref(s))
+    assert s.direction == L.GI_DIR_HYBRID_PULL and s.dense_rep == L.GI_REP_BITMAP
+    assert s.balance == L.GI_BAL_EDGE_AWARE and s.num_segments == 1 and s.block == 256
+    assert (s.t_warp, s.t_cta, s.rule, s.alpha, s.beta, s.tile_edges) == (32, 1024, L.GI_RULE_BEAMER, 14.0, 24.0,
+                                                                          2048)
+
+
+def test_selector_param_count_matches_oracle(lib):
+    import oracle
+    assert lib.gi_selector_num_params() == oracle.mlp_num_params()

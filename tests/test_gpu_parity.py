@@ -1,0 +1,301 @@
+"""CUDA path vs the oracle, element by element, through the C ABI.
+
+Integer outputs (BFS depth and parent, SSSP distance, CC label, per-round
+frontier sizes, selected-edge probes) must be bit-exact; PageRank within 1e-4
+max relative error of the FP64 oracle.  Each schedule is forced in turn, then
+the hybrid rules.
+"""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+from _graphs import ADVERSARIAL, adversarial, grid, rmat
+
+pytestmark = pytest.mark.gpu
+
+INT_MAX = np.iinfo(np.int32).max
+DIRS = ["sparse_push", "dense_push", "dense_pull", "hybrid_pull", "hybrid_dpush"]
+PR_TOL = 1e-4
+
+
+def _load(gi, hg):
+    return gi.Graph.from_host(hg, validate=True)
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+def _max_rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-30))) if a.size else 0.0
+
+
+# ----------------------------------------------------------------------- BFS
+
+@pytest.mark.parametrize("direction", DIRS)
+@pytest.mark.parametrize("balance", ["edge_aware", "vertex"])
+def test_bfs_rmat16_all_schedules(gi, direction, balance):
+    hg = rmat(16)
+    g = _load(gi, hg)
+    for src in [0, *gg.pick_sources(hg, 3, seed=2)]:
+        want_d, want_p, levels = oracle.bfs(hg, int(src))
+        tr = gi.Trace(64)
+        d, p = gi.bfs(g, int(src), sched=gi.schedule(direction, balance=balance), trace=tr)
+        assert np.array_equal(_np(d), want_d)
+        assert np.array_equal(_np(p), want_p)
+        t = tr.as_dict()
+        assert t["iterations"] == len(levels)
+        assert np.array_equal(t["frontier"], levels)
+
+
+@pytest.mark.parametrize("name", ADVERSARIAL)
+@pytest.mark.parametrize("direction", DIRS)
+def test_bfs_adversarial(gi, name, direction):
+    hg = adversarial(name)
+    g = _load(gi, hg)
+    for src in sorted({0, hg.n // 2, hg.n - 1}):
+        want_d, want_p, _ = oracle.bfs(hg, src)
+        d, p = gi.bfs(g, src, sched=gi.schedule(direction, t_cta=256))
+        assert np.array_equal(_np(d), want_d), (name, src)
+        assert np.array_equal(_np(p), want_p), (name, src)
+
+
+def test_bfs_grid_high_diameter(gi):
+    hg = grid(96)
+    g = _load(gi, hg)
+    want_d, want_p, levels = oracle.bfs(hg, 5)
+    for direction in ["sparse_push", "hybrid_pull"]:
+        d, p = gi.bfs(g, 5, sched=gi.schedule(direction))
+        assert np.array_equal(_np(d), want_d) and np.array_equal(_np(p), want_p)
+
+
+def test_bfs_beamer_decisions_replayed_on_cpu(gi):
+    """The hybrid's per-level choice equals Beamer's rule evaluated by the oracle."""
+    hg = rmat(16)
+    g = _load(gi, hg)
+    src = 0
+    depth, _, levels = oracle.bfs(hg, src)
+    deg = hg.degrees().astype(np.int64)
+    tr = gi.Trace(64)
+    gi.bfs(g, src, sched=gi.schedule("hybrid_pull"), trace=tr)
+    t = tr.as_dict()
+    visited_deg = 0
+    nu, mu = hg.n, int(deg.sum())
+    was_pull = 0
+    for lvl in range(len(levels)):
+        front = depth == lvl
+        nf, mf = int(front.sum()), int(deg[front].sum())
+        nu, mu = nu - nf, mu - mf
+        assert t["frontier"][lvl] == nf and t["edges"][lvl] == mf
+        want = oracle.beamer(hg.n, nf, mf, mu, was_pull)
+        got = 1 if t["direction"][lvl] == gi.GI_DIR_DENSE_PULL else 0
+        assert got == want, lvl
+        x = oracle.features(hg.n, hg.m, int(deg.max()), nf, mf, nu, mu, lvl, was_pull,
+                            0 if lvl == 0 else int(levels[lvl - 1]))
+        assert np.allclose(t["features"][lvl], x, rtol=2e-6, atol=1e-6), lvl
+        was_pull = want
+        visited_deg += mf
+
+
+# ---------------------------------------------------------------------- SSSP
+
+@pytest.mark.parametrize("direction", DIRS)
+def test_sssp_rmat_all_schedules(gi, direction):
+    hg = rmat(14, weights=True)
+    g = _load(gi, hg)
+    for src in [0, *gg.pick_sources(hg, 2, seed=4)]:
+        want, fs = oracle.sssp(hg, int(src))
+        tr = gi.Trace(256)
+        d = gi.sssp(g, int(src), sched=gi.schedule(direction), trace=tr)
+        assert np.array_equal(_np(d), want)
+        t = tr.as_dict()
+        assert np.array_equal(t["frontier"], fs)   # synchronous rounds: same frontiers
+
+
+@pytest.mark.parametrize("name", ["path", "components", "hub_tail", "single"])
+@pytest.mark.parametrize("direction", ["sparse_push", "dense_pull", "dense_push"])
+def test_sssp_adversarial(gi, name, direction):
+    hg = adversarial(name, weights=True)
+    g = _load(gi, hg)
+    want, _ = oracle.sssp(hg, 0)
+    assert np.array_equal(_np(gi.sssp(g, 0, sched=gi.schedule(direction))), want)
+
+
+def test_sssp_grid(gi):
+    hg = grid(64, weights=True)
+    g = _load(gi, hg)
+    want, fs = oracle.sssp(hg, 100)
+    tr = gi.Trace(4096)
+    d = gi.sssp(g, 100, sched=gi.schedule("hybrid_pull"), trace=tr)
+    assert np.array_equal(_np(d), want)
+    assert np.array_equal(tr.as_dict()["frontier"], fs)
+
+
+# ------------------------------------------------------------------------ CC
+
+@pytest.mark.parametrize("direction", DIRS)
+def test_cc_all_schedules(gi, direction):
+    for hg in [rmat(14), adversarial("components"), adversarial("path"), grid(40, shortcut_frac=0.0)]:
+        g = _load(gi, hg)
+        want, fs = oracle.cc(hg)
+        tr = gi.Trace(4096)
+        lab = gi.cc(g, sched=gi.schedule(direction), trace=tr)
+        assert np.array_equal(_np(lab), want)
+        assert np.array_equal(tr.as_dict()["frontier"], fs)
+
+
+# ------------------------------------------------------------------ PageRank
+
+@pytest.mark.parametrize("variant", ["pull", "pull_vertex", "push", "seg4", "tile512", "tile8192"])
+def test_pagerank_rmat16(gi, variant):
+    hg = rmat(16)
+    g = _load(gi, hg)
+    sched = {"pull": gi.schedule("dense_pull"),
+             "pull_vertex": gi.schedule("dense_pull", balance="vertex"),
+             "push": gi.schedule("dense_push"),
+             "seg4": gi.schedule("dense_pull", num_segments=4),
+             "tile512": gi.schedule("dense_pull", tile_edges=512),
+             "tile8192": gi.schedule("dense_pull", tile_edges=8192)}[variant]
+    want = oracle.pagerank(hg, 0.85, 20)
+    got = _np(gi.pagerank(g, 0.85, 20, sched=sched))
+    assert _max_rel(got, want) < PR_TOL
+    assert abs(float(np.sum(got.astype(np.float64))) - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["single", "isolated", "star", "path", "hub_tail"])
+def test_pagerank_adversarial(gi, name):
+    hg = adversarial(name)
+    g = _load(gi, hg)
+    want = oracle.pagerank(hg, 0.85, 20)
+    for d in ["dense_pull", "dense_push"]:
+        assert _max_rel(_np(gi.pagerank(g, 0.85, 20, sched=gi.schedule(d))), want) < PR_TOL
+
+
+def test_pagerank_zero_iterations_and_grid(gi):
+    hg = grid(50)
+    g = _load(gi, hg)
+    assert _max_rel(_np(gi.pagerank(g, 0.85, 0)), oracle.pagerank(hg, 0.85, 0)) < 1e-6
+    assert _max_rel(_np(gi.pagerank(g, 0.85, 20)), oracle.pagerank(hg, 0.85, 20)) < PR_TOL
+
+
+# ------------------------------------------------------------- PageRankDelta
+
+@pytest.mark.parametrize("direction", ["dense_pull", "sparse_push", "dense_push", "hybrid_pull"])
+def test_prdelta_rmat16(gi, direction):
+    hg = rmat(16)
+    g = _load(gi, hg)
+    want, fs = oracle.prdelta(hg, 0.85, 1e-7, 10)
+    tr = gi.Trace(16)
+    got = _np(gi.pagerank_delta(g, 0.85, 1e-7, 10, sched=gi.schedule(direction), trace=tr))
+    assert _max_rel(got, want) < PR_TOL
+    t = tr.as_dict()
+    assert t["frontier"][0] == hg.n
+    assert np.all(np.abs(t["frontier"] - fs[:len(t["frontier"])]) <= max(10, hg.n // 1000))
+
+
+@pytest.mark.parametrize("direction", ["dense_pull", "sparse_push", "hybrid_pull"])
+def test_prdelta_sparse_rounds(gi, direction):
+    """eps = 1e-2 makes the active set shrink, exercising sparse rounds."""
+    hg = rmat(14)
+    g = _load(gi, hg)
+    want, fs = oracle.prdelta(hg, 0.85, 1e-2, 10)
+    tr = gi.Trace(16)
+    got = _np(gi.pagerank_delta(g, 0.85, 1e-2, 10, sched=gi.schedule(direction), trace=tr))
+    rel = np.abs(got - want) / np.maximum(want, 1e-30)
+    # a threshold decision that lands within FP32 rounding of eps*Rank may flip
+    # and perturb a few neighbours by O(eps); everything else stays within 1e-4
+    assert np.mean(rel < PR_TOL) > 0.999 and rel.max() < 0.05
+    assert fs[-1] < fs[0]
+
+
+def test_prdelta_eps0_is_pagerank(gi):
+    hg = rmat(12)
+    g = _load(gi, hg)
+    want = oracle.pagerank(hg, 0.85, 5, normalize=False)
+    assert _max_rel(_np(gi.pagerank_delta(g, 0.85, 0.0, 5, sched=gi.schedule("dense_pull"))), want) < PR_TOL
+
+
+# -------------------------------------------------------------- edgeset apply
+
+def _mask_set(gi, g, mask):
+    vs = gi.VertexSet(g)
+    vs.import_ids(torch.from_numpy(np.flatnonzero(mask).astype(np.int32)).cuda())
+    return vs
+
+
+@pytest.mark.parametrize("direction", ["sparse_push", "dense_push", "dense_pull", "hybrid_pull"])
+@pytest.mark.parametrize("dedup", [True, False])
+def test_edgeset_apply_selection_probe(gi, direction, dedup):
+    """from/to selection and applyModified output equal the oracle's edge set."""
+    hg = rmat(12)
+    g = _load(gi, hg)
+    rng = np.random.default_rng(11)
+    for p_from, p_to in [(0.05, 1.0), (0.5, 0.3), (1.0, 1.0)]:
+        fm = (rng.random(hg.n) < p_from).astype(np.uint8)
+        tm = (rng.random(hg.n) < p_to).astype(np.uint8)
+        u, v = oracle.edgeset_select(hg, fm, tm)
+        cnt = np.bincount(v, minlength=hg.n)
+        ssum = np.bincount(v, weights=u.astype(np.float64) + 1, minlength=hg.n).astype(np.uint64)
+        F, T, OUT = _mask_set(gi, g, fm), _mask_set(gi, g, tm), gi.VertexSet(g)
+        count = torch.zeros(hg.n, dtype=torch.int32, device="cuda")
+        srcsum = torch.zeros(hg.n, dtype=torch.int64, device="cuda")
+        args = gi.gi_probe_args(count.data_ptr(), srcsum.data_ptr())
+        gi.edgeset_apply(g, F, T if p_to < 1 else None, gi.schedule(direction), gi.GI_K_PROBE, args, OUT,
+                         flags=0 if dedup else gi.GI_NO_DEDUP)
+        assert np.array_equal(_np(count), cnt)
+        assert np.array_equal(_np(srcsum).astype(np.uint64), ssum)
+        mod = _np(OUT.export())
+        assert np.array_equal(mod, np.flatnonzero(cnt > 0))
+
+
+def test_edgeset_apply_worked_example(gi):
+    import json
+    import os
+    ex = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "gis_worked_example.json")))
+    n = ex["n"]
+    hg = gg.from_edge_list(n, map(tuple, ex["edges_directed"]), symmetrize=False)
+    in_ptr, in_col, _ = gg.transpose(hg)
+    g = gi.Graph(hg.row_ptr, hg.col, symmetric=False, in_edges=(in_ptr, in_col), validate=True)
+    fm = np.zeros(n, np.uint8)
+    fm[ex["frontier"]] = 1
+    for direction in ["sparse_push", "dense_push", "dense_pull"]:
+        count = torch.zeros(n, dtype=torch.int32, device="cuda")
+        srcsum = torch.zeros(n, dtype=torch.int64, device="cuda")
+        gi.edgeset_apply(g, _mask_set(gi, g, fm), None, gi.schedule(direction), gi.GI_K_PROBE,
+                         gi.gi_probe_args(count.data_ptr(), srcsum.data_ptr()))
+        got = sorted((int(s) - 1, v) for v in range(n) for s in ([_np(srcsum)[v]] if _np(count)[v] else []))
+        assert got == sorted(map(tuple, ex["push_space"])), direction
+
+
+# ----------------------------------------------------------------- vertexsets
+
+def test_vertexset_roundtrip(gi):
+    hg = rmat(12)
+    g = _load(gi, hg)
+    rng = np.random.default_rng(2)
+    ids = np.unique(rng.integers(0, hg.n, 700)).astype(np.int32)
+    vs = gi.VertexSet(g)
+    vs.import_ids(torch.from_numpy(rng.permutation(np.r_[ids, ids[:50]]).astype(np.int32)).cuda())
+    assert vs.size() == ids.size
+    assert np.array_equal(_np(vs.export()), ids)
+    vs.to_dense(gi.GI_REP_BOOL)
+    vs.to_sparse()
+    assert vs.reps() & gi.GI_REP_SPARSE
+    assert np.array_equal(_np(vs.export()), ids)
+    assert gi.VertexSet(g, gi.GI_VSET_ALL).size() == hg.n
+    assert gi.VertexSet(g, gi.GI_VSET_EMPTY).size() == 0
+    one = gi.VertexSet(g, gi.GI_VSET_SINGLE, 77)
+    assert _np(one.export()).tolist() == [77]
+
+
+def test_bad_graph_rejected(gi):
+    hg = rmat(8)
+    col = hg.col.copy()
+    col[5] = hg.n + 3
+    with pytest.raises(gi.GIError) as e:
+        gi.Graph(hg.row_ptr, col, validate=True)
+    assert e.value.code == -2
