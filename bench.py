@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the edgeset-apply hot path on one GB300 (or N replicas).
+
+Workload (one "step"): on a symmetrized R-MAT graph of scale 22 (edge factor
+16, a=.57 b=.19 c=.19, seed 1; ~4.19M vertices, ~128M arcs), run
+  PageRank        20 iterations, damping 0.85, DensePull (FP32, FP64 normalisation)
+  PageRankDelta   10 rounds, eps 1e-7, hybrid DensePull-SparsePush
+  CC              label propagation to convergence, hybrid DensePull-SparsePush
+Value = arcs traversed by the step / step time, in GTEPS (10^9 arcs/s): PR
+counts iters*m, PRD and CC count m for pull rounds and m_f (the frontier's
+out-degree sum) for push rounds.  Inputs (CSR ~0.5 GB) exceed the 126 MB L2.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS per algorithm & graph, learned vs heuristic schedule; % of HBM roofline"
+DAMPING, PR_ITERS, PRD_EPS, PRD_ITERS = 0.85, 20, 1e-7, 10
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["gi", "reference"], default="gi")
+    p.add_argument("--scale", type=int, default=22)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(hg, scale):
+    return {"workload": f"rmat{scale}_pr{PR_ITERS}_prd{PRD_ITERS}_cc", "graph": "R-MAT symmetrized",
+            "scale": scale, "edge_factor": 16, "abc": [0.57, 0.19, 0.19], "seed": 1, "n": hg.n, "m": hg.m,
+            "pagerank": {"iters": PR_ITERS, "damping": DAMPING, "schedule": "DensePull"},
+            "pagerank_delta": {"iters": PRD_ITERS, "eps": PRD_EPS, "schedule": "DensePull-SparsePush (Ligra rule)"},
+            "cc": {"schedule": "DensePull-SparsePush (Ligra rule)"},
+            "l2": "inputs larger than L2 (CSR %.0f MB vs 126 MB L2); no flush" % ((4 * (hg.n + 1) + 4 * hg.m) / 1e6)}
+
+
+def oracle_sample(hg, seconds):
+    """Time the oracle's PageRank on the full graph for as many iterations as fit ~`seconds`."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.pagerank(hg, DAMPING, 1)
+    t1 = time.perf_counter() - t0
+    iters = max(1, min(PR_ITERS, int(seconds / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.pagerank(hg, DAMPING, iters)
+    t = time.perf_counter() - t0
+    return iters * hg.m / t / 1e9, iters, t
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import graphgen as gg
+    import oracle
+    oracle.build()
+    hg = gg.rmat_graph(args.scale, seed=1)
+    iters = 2
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.pagerank(hg, DAMPING, iters)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = args.steps * iters * hg.m / total / 1e9
+    sample = f"oracle PageRank, {iters} iterations per step on the full scale-{args.scale} graph (single thread)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(hg, args.scale),
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gi_traverse.cuh", "gi_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1805_00923_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from profiles/traffic.txt if recorded for the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 4 and not ln.startswith("#") and parts[0] == want and parts[1] == kernel \
+                and parts[2] == workload:
+            return float(parts[3])
+    return None
+
+
+def measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def run_gi(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import graphgen as gg
+    import paper_1805_00923_gb300 as gi
+
+    hg = gg.rmat_graph(args.scale, seed=1)
+    n, m = hg.n, hg.m
+    stream = torch.cuda.current_stream()
+    g = gi.Graph.from_host(hg)
+    pr_s = gi.schedule("dense_pull")
+    hyb = gi.schedule("hybrid_pull")
+    rank_buf = torch.empty(n, dtype=torch.float32, device="cuda")
+    prd_buf = torch.empty(n, dtype=torch.float32, device="cuda")
+    lab_buf = torch.empty(n, dtype=torch.int32, device="cuda")
+    tr_p, tr_c = gi.Trace(64), gi.Trace(256)
+
+    def traversed(tr):
+        t = tr.as_dict()
+        return int(sum(m if d == gi.GI_DIR_DENSE_PULL else e for d, e in zip(t["direction"], t["edges"])))
+
+    def step(graph, ev=None):
+        if ev:
+            ev[0].record()
+        gi.pagerank(graph, DAMPING, PR_ITERS, sched=pr_s, out=rank_buf)
+        if ev:
+            ev[1].record()
+        gi.pagerank_delta(graph, DAMPING, PRD_EPS, PRD_ITERS, sched=hyb, trace=tr_p, out=prd_buf)
+        if ev:
+            ev[2].record()
+        gi.cc(graph, sched=hyb, trace=tr_c, out=lab_buf)
+        if ev:
+            ev[3].record()
+        return PR_ITERS * m, traversed(tr_p), traversed(tr_c)
+
+    for _ in range(args.warmup):
+        step(g)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    gi.stats_reset()
+    gi.stats_enable(True)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    edges = np.zeros(3, np.float64)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    for k in range(args.steps):
+        edges += step(g, evs[k])
+    stop.record()
+    torch.cuda.synchronize()
+    gi.stats_enable(False)
+    launches, pr_launches, pr_ms = gi.stats_read("pr_pull")
+    clocks = sampler.stop()
+    total_ms = start.elapsed_time(stop)
+    per_alg_ms = np.zeros(3)
+    for ev in evs:
+        per_alg_ms += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * edges.sum() / (total_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI from pinned host buffers
+    rp_h = torch.from_numpy(hg.row_ptr).pin_memory()
+    col_h = torch.from_numpy(hg.col).pin_memory()
+    out_h = [torch.empty(n, dtype=torch.float32).pin_memory(), torch.empty(n, dtype=torch.float32).pin_memory(),
+             torch.empty(n, dtype=torch.int32).pin_memory()]
+    h2d = 4 * (n + 1) + 4 * m
+    d2h = 3 * 4 * n
+    e2e_ms, e2e_edges = [], 0.0
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ge = gi.Graph(rp_h.numpy(), col_h.numpy(), symmetric=True)
+        ed = step(ge)
+        out_h[0].copy_(rank_buf, non_blocking=True)
+        out_h[1].copy_(prd_buf, non_blocking=True)
+        out_h[2].copy_(lab_buf, non_blocking=True)
+        torch.cuda.synchronize()
+        ge.free()
+        dt = (time.perf_counter() - t0) * 1e3
+        if k > 0:  # first one warms the allocator pool
+            e2e_ms.append(dt)
+            e2e_edges += sum(ed)
+    e2e_value = world * e2e_edges / (sum(e2e_ms) * 1e-3) / 1e9
+
+    peak, peak_kind = measured_hbm()
+    bytes_per_launch = 4 * m + 16 * n + 4
+    avg_ms = pr_ms / max(pr_launches, 1)
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic("k_pull_tiled_OpPR", f"rmat{args.scale}")
+
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(hg, args.scale),
+            "per_algorithm": {
+                "pagerank": {"gteps": edges[0] / (per_alg_ms[0] * 1e-3) / 1e9, "ms": per_alg_ms[0] / args.steps},
+                "pagerank_delta": {"gteps": edges[1] / (per_alg_ms[1] * 1e-3) / 1e9,
+                                   "ms": per_alg_ms[1] / args.steps},
+                "cc": {"gteps": edges[2] / (per_alg_ms[2] * 1e-3) / 1e9, "ms": per_alg_ms[2] / args.steps}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_pull_tiled<OpPR> (PageRank DensePull iteration)",
+                         "bytes_model": "4m + 16n + 4 per launch", "launches_timed": pr_launches,
+                         "avg_launch_ms": avg_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
+            "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": sum(e2e_ms) / max(len(e2e_ms), 1)},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, iters, t = oracle_sample(hg, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                                "sample": f"oracle PageRank, {iters} iterations on the full graph ({t:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.free()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gi(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

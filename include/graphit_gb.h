@@ -282,6 +282,31 @@ int gi_selector_load(const float *params, int32_t count, const float *mean, cons
 /* Number of parameters of the selector network (5443). */
 int gi_selector_num_params(void);
 
+/* -------------------------------------------------------------- profiling -- */
+/*
+ * Host-side instrumentation for benchmarks (not part of the paper).  The
+ * library counts every kernel it launches.  With timing on, each launch of the
+ * timed kernel classes below is bracketed by CUDA events recorded on the
+ * launching stream.  Process-wide state; not meant for concurrent callers.
+ */
+#define GI_KCLASS_PR_PULL 0    /* tiled DensePull of PageRank (vertex update fused)        */
+#define GI_KCLASS_PRD_PULL 1   /* tiled DensePull of PageRankDelta (vertex filter fused)   */
+#define GI_KCLASS_MIN_PULL 2   /* tiled DensePull of CC / SSSP (min reduction)             */
+#define GI_KCLASS_PUSH 3       /* SparsePush / DensePush expansion                         */
+#define GI_KCLASS_BFS_PULL 4   /* early-exit BFS DensePull                                 */
+#define GI_KCLASS_OTHER_PULL 5 /* other tiled pulls (sum, probe, segments)                 */
+
+/* Turn per-launch event timing on (1) or off (0); counting is always on. */
+int gi_stats_enable(int timing_on);
+/* Zero the launch counter and drop recorded timings. */
+int gi_stats_reset(void);
+/*
+ * Launches since the last reset (*launches), and for kernel class `kclass`
+ * (-1 = all timed classes) the number of timed launches and their summed
+ * device time in milliseconds.  Waits for the recorded events.
+ */
+int gi_stats_read(int32_t kclass, int64_t *launches, int64_t *timed_launches, double *timed_ms);
+
 #ifdef __cplusplus
 }
 #endif

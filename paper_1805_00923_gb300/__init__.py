@@ -248,3 +248,20 @@ def selector_load(params: np.ndarray, mean: np.ndarray, inv_std: np.ndarray):
 
 def selector_num_params() -> int:
     return int(_C.gi_selector_num_params())
+
+
+def stats_enable(timing: bool = True):
+    check(_C.gi_stats_enable(1 if timing else 0))
+
+
+def stats_reset():
+    check(_C.gi_stats_reset())
+
+
+def stats_read(kclass: int | str = -1):
+    """(launches since reset, timed launches of kclass, their device ms)."""
+    if isinstance(kclass, str):
+        kclass = L.KCLASS[kclass]
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    check(_C.gi_stats_read(int(kclass), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value

@@ -91,7 +91,11 @@ SIGNATURES = {
     "gi_pagerank_delta": (ctypes.c_int, [_vp, _f32, _f32, _i32, _vp, _P(gi_schedule), _P(gi_trace), _vp]),
     "gi_selector_load": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
     "gi_selector_num_params": (ctypes.c_int, []),
+    "gi_stats_enable": (ctypes.c_int, [ctypes.c_int]),
+    "gi_stats_reset": (ctypes.c_int, []),
+    "gi_stats_read": (ctypes.c_int, [_i32, _P(_i64), _P(_i64), _P(ctypes.c_double)]),
 }
+KCLASS = {"pr_pull": 0, "prd_pull": 1, "min_pull": 2, "push": 3, "bfs_pull": 4, "other_pull": 5}
 
 _lib = None
 

@@ -61,11 +61,12 @@ __global__ void k_fill_f32(float *x, int64_t n, float val) {
 }
 
 // PageRank vertex update after a push iteration: rank = base + d*acc
-__global__ void k_pr_vertex(float *acc, float *contrib_out, float *rank_out, const float *__restrict__ inv_deg,
+template <class A>
+__global__ void k_pr_vertex(A *acc, float *contrib_out, float *rank_out, const float *__restrict__ inv_deg,
                             int64_t n, float base, float damping) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float r = fmaf(damping, acc[i], base);
-    acc[i] = 0.0f;
+    float r = fmaf(damping, (float)acc[i], base);
+    acc[i] = 0;
     if (rank_out) rank_out[i] = r;
     else contrib_out[i] = r * inv_deg[i];
   }
@@ -103,7 +104,7 @@ __global__ void k_scale_f64(float *x, int64_t n, const double *__restrict__ part
 
 // PageRankDelta vertex filter after a push round (Fig. 1): Delta, Rank,
 // DeltaSum reset, next frontier (bitmap word per warp + queue), next contrib.
-__global__ void k_prd_vertex(float *dsum, float *rank, float *contrib_out, const float *__restrict__ inv_deg,
+__global__ void k_prd_vertex(double *dsum, float *rank, float *contrib_out, const float *__restrict__ inv_deg,
                              int64_t n, float damping, float first_base, float inv_n, float eps, int32_t first_round,
                              uint32_t *out_bm, int32_t *out_q, int32_t *out_qc) {
   const int lane = threadIdx.x & 31;
@@ -113,7 +114,7 @@ __global__ void k_prd_vertex(float *dsum, float *rank, float *contrib_out, const
     const int64_t v = w * 32 + lane;
     bool active = false;
     if (v < n) {
-      float s = dsum[v], r = rank[v], delta;
+      float s = (float)dsum[v], r = rank[v], delta;
       if (first_round) {
         delta = fmaf(damping, s, first_base);
         r += delta;
@@ -123,7 +124,7 @@ __global__ void k_prd_vertex(float *dsum, float *rank, float *contrib_out, const
         r += delta;
       }
       rank[v] = r;
-      dsum[v] = 0.0f;
+      dsum[v] = 0.0;
       active = fabsf(delta) > eps * r;
       contrib_out[v] = active ? delta * inv_deg[v] : 0.0f;
     }
@@ -258,7 +259,7 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
   int st = pair_alloc(g, P, s);
   if (st == GI_OK) {
     k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(depth, parent, g->n, src);
-    st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+    st = launch_status(1);
   }
   if (st == GI_OK) st = front_init(g, P.F, src, s);
   if (st == GI_OK) st = ctrl_init(g, g->n, g->m, s);
@@ -269,7 +270,7 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     });
   if (st == GI_OK && parent) {
     k_parent_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n);
-    st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+    st = launch_status(1);
   }
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
@@ -297,7 +298,7 @@ static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src,
       k_set_one<<<1, 1, 0, s>>>(x, src, 0);
       k_set_one<<<1, 1, 0, s>>>(snap, src, 0);
     }
-    st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+    st = launch_status(kernel_id == GI_K_CC ? 1 : 4);
   }
   if (st == GI_OK) st = front_init(g, P.F, kernel_id == GI_K_CC ? -1 : src, s);
   if (st == GI_OK) st = ctrl_init(g, 0, 0, s);
@@ -315,8 +316,7 @@ static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src,
       int grid = g->num_sms * 4;
       k_snap_reset<<<grid, 256, 0, s>>>(P.F->queue, P.F->count, snap);
       k_snap_set<<<grid, 256, 0, s>>>(P.N->queue, P.N->count, snap, x);
-      GI_LAUNCH_CHECK();
-      return GI_OK;
+      return launch_status(2);
     });
   dev_free(snap, s);
   pair_free(P, s);
@@ -355,10 +355,9 @@ static int pr_normalize(gi_graph *g, float *rank, cudaStream_t s) {
   GI_TRY(dev_alloc_n(&partial, np, s));
   k_sum_f64<<<np, 256, 0, s>>>(rank, g->n, partial);
   k_scale_f64<<<grid_for(g, g->n, 256), 256, 0, s>>>(rank, g->n, partial, np);
-  cudaError_t e = cudaGetLastError();
+  int st = launch_status(2);
   dev_free(partial, s);
-  if (e != cudaSuccess) return cuda_fail(e, "normalize", __FILE__, __LINE__);
-  return GI_OK;
+  return st;
 }
 
 extern "C" int gi_pagerank(gi_graph *g, float damping, int32_t iters, float *rank, const gi_schedule *sched,
@@ -378,25 +377,29 @@ extern "C" int gi_pagerank(gi_graph *g, float damping, int32_t iters, float *ran
   if (segmented && g->segs.num != sc.num_segments) GI_TRY(gi_graph_build_segments(g, sc.num_segments, s));
   const float base = (1.0f - damping) / (float)g->n, init = 1.0f / (float)g->n;
   float *buf[2] = {nullptr, nullptr}, *acc = nullptr;
+  double *acc64 = nullptr;
   int st = dev_alloc_n(&buf[0], g->n, s);
   if (st == GI_OK) st = dev_alloc_n(&buf[1], g->n, s);
-  if (st == GI_OK && (push || segmented)) st = dev_alloc_n(&acc, g->n, s);
+  if (st == GI_OK && segmented) st = dev_alloc_n(&acc, g->n, s);
+  if (st == GI_OK && push) st = dev_alloc_n(&acc64, g->n, s);
+  if (st == GI_OK && acc) st = cudaMemsetAsync(acc, 0, sizeof(float) * g->n, s) == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+  if (st == GI_OK && acc64)
+    st = cudaMemsetAsync(acc64, 0, sizeof(double) * g->n, s) == cudaSuccess ? GI_OK : GI_ERR_CUDA;
   if (st == GI_OK) {
     if (iters == 0) k_fill_f32<<<grid_for(g, g->n, 256), 256, 0, s>>>(rank, g->n, init);
     k_pr_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(buf[0], g->inv_out_deg, g->n, init);
-    if (acc) k_fill_f32<<<grid_for(g, g->n, 256), 256, 0, s>>>(acc, g->n, 0.0f);
-    st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+    st = launch_status(1 + (iters == 0 ? 1 : 0));
   }
   for (int32_t k = 0; k < iters && st == GI_OK; ++k) {
     const bool last = (k == iters - 1);
     float *cin = buf[k & 1], *cout = buf[(k + 1) & 1];
     if (push) {
-      OpSum op{cin, acc};
+      OpSumPush64 op{cin, acc64};
       st = launch_push(g, op, kSrcAll, nullptr, nullptr, OutSet(), sc, s);
       if (st == GI_OK) {
-        k_pr_vertex<<<grid_for(g, g->n, 256), 256, 0, s>>>(acc, last ? nullptr : cout, last ? rank : nullptr,
+        k_pr_vertex<<<grid_for(g, g->n, 256), 256, 0, s>>>(acc64, last ? nullptr : cout, last ? rank : nullptr,
                                                            g->inv_out_deg, g->n, base, damping);
-        st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+        st = launch_status(1);
       }
     } else if (segmented) {
       // one SSG at a time (Sec. 6): acc accumulates over segments without
@@ -411,19 +414,20 @@ extern "C" int gi_pagerank(gi_graph *g, float damping, int32_t iters, float *ran
           if (st == GI_OK) {
             k_pr_vertex<<<grid_for(g, g->n, 256), 256, 0, s>>>(acc, last ? nullptr : cout, last ? rank : nullptr,
                                                                g->inv_out_deg, g->n, base, damping);
-            st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+            st = launch_status(1);
           }
         }
       }
     } else {
       OpPR op{cin, last ? nullptr : cout, last ? rank : nullptr, g->inv_out_deg, base, damping};
-      st = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, OutSet(), s);
+      st = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, OutSet(), s, kClassPrPull);
     }
   }
   if (st == GI_OK) st = pr_normalize(g, rank, s);
   dev_free(buf[0], s);
   dev_free(buf[1], s);
   dev_free(acc, s);
+  dev_free(acc64, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "pagerank", __FILE__, __LINE__);
   return st;
@@ -444,16 +448,18 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
   GI_TRY(ensure_tiles(g, sc, s));
   const float inv_n = 1.0f / (float)g->n, first_base = (1.0f - damping) / (float)g->n;
   VsetPair P;
-  float *cb[2] = {nullptr, nullptr}, *dsum = nullptr;
+  float *cb[2] = {nullptr, nullptr};
+  double *dsum = nullptr;
   int st = pair_alloc(g, P, s);
   if (st == GI_OK) st = dev_alloc_n(&cb[0], g->n, s);
   if (st == GI_OK) st = dev_alloc_n(&cb[1], g->n, s);
   if (st == GI_OK) st = dev_alloc_n(&dsum, g->n, s);
   if (st == GI_OK) {
     k_fill_f32<<<grid_for(g, g->n, 256), 256, 0, s>>>(rank, g->n, 0.0f);
-    k_fill_f32<<<grid_for(g, g->n, 256), 256, 0, s>>>(dsum, g->n, 0.0f);
     k_pr_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(cb[0], g->inv_out_deg, g->n, inv_n);
-    st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+    st = launch_status(2);
+    if (st == GI_OK && cudaMemsetAsync(dsum, 0, sizeof(double) * g->n, s) != cudaSuccess)
+      st = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__);
   }
   if (st == GI_OK) st = front_init(g, P.F, -1, s);
   if (st == GI_OK) st = ctrl_init(g, 0, 0, s);
@@ -473,15 +479,15 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
     float *cin = cb[cur], *cout = cb[cur ^ 1];
     if (dir == GI_DIR_DENSE_PULL) {
       OpPRD op{cin, cout, rank, g->inv_out_deg, damping, first_base, inv_n, eps, round == 1 ? 1 : 0};
-      st = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, out_of(P.N), s);
+      st = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, out_of(P.N), s, kClassPrdPull);
     } else {
-      OpSum op{cin, dsum};
+      OpSumPush64 op{cin, dsum};
       st = launch_push(g, op, dir == GI_DIR_SPARSE_PUSH ? kSrcQueue : kSrcBitmap, P.F, nullptr, OutSet(), sc, s);
       if (st == GI_OK) {
         k_prd_vertex<<<grid_for(g, g->n, 256), 256, 0, s>>>(dsum, rank, cout, g->inv_out_deg, g->n, damping,
                                                             first_base, inv_n, eps, round == 1 ? 1 : 0, P.N->bitmap,
                                                             P.N->queue, P.N->count);
-        st = cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA;
+        st = launch_status(1);
       }
     }
     P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;

@@ -2,10 +2,12 @@
 // direction decision (Beamer / Ligra threshold or the learned selector).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "gi_internal.cuh"
 
@@ -24,6 +26,56 @@ void set_error(const char *fmt, ...) {
 int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
   set_error("CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
   return e == cudaErrorMemoryAllocation ? GI_ERR_OOM : GI_ERR_CUDA;
+}
+
+// ======================================================= launch accounting ==
+static std::atomic<long long> g_launches{0};
+static std::atomic<bool> g_timing{false};
+struct TimedRec {
+  int kclass;
+  cudaEvent_t a, b;
+};
+static std::mutex g_timing_mu;
+static std::vector<TimedRec> g_recs;
+static std::vector<cudaEvent_t> g_event_pool;
+
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int launch_status(int n) {
+  note_launch(n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch", __FILE__, __LINE__);
+  return GI_OK;
+}
+
+static cudaEvent_t pool_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+int timing_begin(int kclass, cudaStream_t s) {
+  if (!g_timing.load(std::memory_order_relaxed)) return -1;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  TimedRec r{kclass, pool_event(), pool_event()};
+  if (!r.a || !r.b) return -1;
+  cudaEventRecord(r.a, s);
+  g_recs.push_back(r);
+  return (int)g_recs.size() - 1;
+}
+
+void timing_end(int token, cudaStream_t s) {
+  if (token < 0) return;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  if (token < (int)g_recs.size()) cudaEventRecord(g_recs[token].b, s);
 }
 
 // ============================================================ allocation ==
@@ -260,6 +312,41 @@ static int validate_csr_dev(gi_graph *g, const Csr &c, cudaStream_t s) {
 using namespace gi;
 
 extern "C" const char *gi_last_error(void) { return g_err; }
+
+extern "C" int gi_stats_enable(int timing_on) {
+  g_timing.store(timing_on != 0);
+  return GI_OK;
+}
+
+extern "C" int gi_stats_reset(void) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  for (auto &r : g_recs) {
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_recs.clear();
+  g_launches.store(0);
+  return GI_OK;
+}
+
+extern "C" int gi_stats_read(int32_t kclass, int64_t *launches, int64_t *timed_launches, double *timed_ms) {
+  GI_ARG(kclass >= -1 && kclass < kNumClasses, "unknown kernel class");
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  if (launches) *launches = g_launches.load();
+  int64_t cnt = 0;
+  double ms = 0.0;
+  for (auto &r : g_recs) {
+    if (kclass >= 0 && r.kclass != kclass) continue;
+    GI_CUDA(cudaEventSynchronize(r.b));
+    float t = 0.0f;
+    GI_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    ms += t;
+    ++cnt;
+  }
+  if (timed_launches) *timed_launches = cnt;
+  if (timed_ms) *timed_ms = ms;
+  return GI_OK;
+}
 extern "C" int gi_version(void) { return 100; }
 
 static void graph_release(gi_graph *g, cudaStream_t s) {
@@ -332,7 +419,7 @@ extern "C" int gi_load_csr(const int32_t *offsets, const int32_t *indices, const
     if (cudaMemsetAsync(g->ctrl + kErr, 0, sizeof(int64_t), s) != cudaSuccess) { st = GI_ERR_CUDA; break; }
     k_degrees<<<grid_for(g, n, 256), 256, 0, s>>>(g->out.ptr, n, g->out_deg, g->inv_out_deg,
                                                   reinterpret_cast<int32_t *>(g->ctrl + kErr));
-    if ((st = (cudaGetLastError() == cudaSuccess ? GI_OK : GI_ERR_CUDA)) != GI_OK) break;
+    if ((st = launch_status(1)) != GI_OK) break;
     int64_t md = 0;
     if (cudaMemcpyAsync(&md, g->ctrl + kErr, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -736,7 +823,7 @@ extern "C" int gi_vset_create(gi_graph *g, int32_t init, int32_t v, void *stream
   if (st == GI_OK) {
     k_vset_init<<<grid_for(g, g->n > x->words ? g->n : x->words, 256), 256, 0, s>>>(x->queue, x->count, x->bitmap,
                                                                                    x->words, g->n, init, v);
-    if (cudaGetLastError() != cudaSuccess) st = GI_ERR_CUDA;
+    st = launch_status(1);
   }
   if (st != GI_OK) {
     gi_vset_free(x);

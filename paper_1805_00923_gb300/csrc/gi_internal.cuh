@@ -15,6 +15,18 @@ namespace gi {
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 
+// launch accounting: every kernel launch is counted; launch_status counts n
+// launches and reports a launch error as GI_ERR_CUDA.
+void note_launch(int n);
+int launch_status(int n);
+
+// CUDA-event timing of selected kernel classes (gi_stats_*): returns a token
+// for timing_end, or -1 when timing is off.
+enum KernelClass { kClassPrPull = 0, kClassPrdPull = 1, kClassMinPull = 2, kClassPush = 3, kClassBfsPull = 4,
+                   kClassOtherPull = 5, kNumClasses = 6 };
+int timing_begin(int kclass, cudaStream_t s);
+void timing_end(int token, cudaStream_t s);
+
 }  // namespace gi
 
 #define GI_CUDA(call)                                                           \
@@ -23,7 +35,11 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
     if (_e != cudaSuccess) return gi::cuda_fail(_e, #call, __FILE__, __LINE__); \
   } while (0)
 
-#define GI_LAUNCH_CHECK() GI_CUDA(cudaGetLastError())
+#define GI_LAUNCH_CHECK()                  \
+  do {                                     \
+    gi::note_launch(1);                    \
+    GI_CUDA(cudaGetLastError());           \
+  } while (0)
 
 #define GI_ARG(cond, msg)                                   \
   do {                                                      \

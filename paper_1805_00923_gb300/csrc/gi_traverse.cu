@@ -31,21 +31,23 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
       case GI_K_BFS: {
         const gi_bfs_args *a = static_cast<const gi_bfs_args *>(args);
         int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
+        const int tok = timing_begin(kClassBfsPull, s);
         k_pull_bfs<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->n, F, to_bm, a->depth, a->parent,
                                                           a->level, tw, o.bm, o.q, o.qc);
+        timing_end(tok, s);
         GI_LAUNCH_CHECK();
         break;
       }
       case GI_K_SSSP: {
         const gi_sssp_args *a = static_cast<const gi_sssp_args *>(args);
         OpMinInt op{a->dist, a->snap, g->in.wt};
-        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s));
+        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s, kClassMinPull));
         break;
       }
       case GI_K_CC: {
         const gi_cc_args *a = static_cast<const gi_cc_args *>(args);
         OpMinInt op{a->label, a->snap, nullptr};
-        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s));
+        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s, kClassMinPull));
         break;
       }
       case GI_K_SUM: {

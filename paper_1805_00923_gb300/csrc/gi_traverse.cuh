@@ -122,6 +122,18 @@ struct OpSum {  // acc[v] += contrib[u]; modified = destinations with a selected
   }
 };
 
+// Push accumulation for the PageRank drivers: FP64 atomics, because FP32
+// atomic accumulation in arbitrary order onto a high in-degree vertex drifts
+// beyond the 1e-4 bound (the pull direction sums in a fixed tree order).
+struct OpSumPush64 {
+  const float *contrib;
+  double *acc;
+  __device__ bool push(int32_t u, int32_t v, int32_t) const {
+    atomicAdd(acc + v, (double)__ldg(contrib + u));
+    return false;
+  }
+};
+
 struct ProbeVal {
   int32_t c;
   unsigned long long s;
@@ -303,7 +315,7 @@ __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__r
         const int32_t v = r0 + i;
         bool mod = false;
         if (valid && in_set(to, v) && op.dst_ok(v)) mod = op.finish(v, acc);
-        if (out.enabled()) mark_consecutive(out, r0 + i0, mod);
+        if (out.enabled()) mark_consecutive(out, r0 + i0 + (tid & ~31), mod);
       }
       __syncthreads();
     } else {
@@ -504,15 +516,17 @@ size_t pull_smem_bytes(int32_t tile_edges) {
 // Tiled pull over the in-edges `c` with tiles `ts` (the whole graph or one segment).
 template <class Op>
 int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts, const uint32_t *F,
-                      const uint32_t *to, const OutSet &out, cudaStream_t s) {
+                      const uint32_t *to, const OutSet &out, cudaStream_t s, int kclass = kClassOtherPull) {
   if (ts.num_tiles == 0) return GI_OK;
   constexpr int kB = 256;
   const size_t smem = pull_smem_bytes<Op>(ts.tile_edges);
   if (smem > 48 * 1024) {
     GI_CUDA(cudaFuncSetAttribute(k_pull_tiled<Op, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
+  const int tok = timing_begin(kclass, s);
   k_pull_tiled<Op, kB><<<ts.num_tiles, kB, smem, s>>>(op, c.ptr, c.idx, ts.tiles, ts.num_tiles, ts.tile_edges, F, to,
                                                       out, reinterpret_cast<typename Op::V *>(ts.partial));
+  timing_end(tok, s);
   GI_LAUNCH_CHECK();
   if (ts.num_splits > 0) {
     k_pull_fixup<Op><<<div_up(ts.num_splits, 128), 128, 0, s>>>(
@@ -531,6 +545,7 @@ int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const 
   int32_t tc = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_cta > 0 ? sc.t_cta : 1024);
   int block = sc.block >= 64 && sc.block <= 256 && sc.block % 32 == 0 ? sc.block : 256;
   int grid;
+  const int tok = timing_begin(kClassPush, s);
   if (mode == kSrcQueue) {
     grid = g->num_sms * (2048 / block);
     k_push<Op, kSrcQueue><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, from->queue, from->count, nullptr, g->n,
@@ -544,6 +559,7 @@ int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const 
     k_push<Op, kSrcAll><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, nullptr, g->n, to, out,
                                                tw, tc);
   }
+  timing_end(tok, s);
   GI_LAUNCH_CHECK();
   return GI_OK;
 }
