@@ -158,7 +158,7 @@ typedef struct gi_schedule {
   int32_t t_cta;        /* edge-aware: degree >= t_cta goes to a whole block          */
   int32_t rule;         /* GI_RULE_*                                                 */
   float alpha, beta;    /* Beamer constants                                          */
-  int32_t tile_edges;   /* pull tiles: arcs per tile (power of two, 256..16384)       */
+  int32_t tile_edges;   /* pull tiles: arcs per tile (power of two, 512..8192)        */
 } gi_schedule;
 
 /* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment, 256 threads, t_warp 32,

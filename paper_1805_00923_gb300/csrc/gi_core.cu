@@ -1011,7 +1011,16 @@ __global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *
   __shared__ bool last;
   int32_t c = *count;
   unsigned long long local = 0;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) local += deg[q[i]];
+  // 8 independent queue loads, then 8 independent degree gathers, per round trip
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < c; i0 += 8 * stride) {
+    int32_t v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = i0 + j * stride < c ? q[i0 + j * stride] : -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (v[j] >= 0) local += deg[v[j]];
+  }
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
   if (lane_id() == 0) s_sum[threadIdx.x >> 5] = local;
   __syncthreads();

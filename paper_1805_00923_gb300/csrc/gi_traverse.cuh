@@ -266,29 +266,62 @@ __device__ __forceinline__ V warp_reduce(V x) {
 // row by row (a thread per row below 32 arcs, the owning warp above); long
 // rows are reduced by the whole block.  Pieces of split rows leave a partial
 // value that k_pull_fixup combines in tile order (deterministic).
+//
+// Memory-level parallelism: each thread issues kBatch index loads, then the
+// kBatch dependent gathers, before touching any result, so a tile costs about
+// two memory round trips per kBatch arcs per thread instead of two per arc.
+constexpr int kBatch = 8;
+
 template <class Op, int kBlock>
+__device__ __forceinline__ void stage_batch(const Op &op, const int32_t *__restrict__ idx,
+                                            const uint32_t *__restrict__ F, int32_t e0, int32_t k0, int32_t ne,
+                                            typename Op::V *vals) {
+  int32_t u[kBatch];
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) {
+    const int32_t k = k0 + j * kBlock;
+    u[j] = k < ne ? __ldg(idx + e0 + k) : -1;
+  }
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) {
+    const int32_t k = k0 + j * kBlock;
+    if (k < ne) vals[k] = (u[j] >= 0 && in_set(F, u[j])) ? op.edge_val(u[j], e0 + k) : Op::identity();
+  }
+}
+
+template <class Op, int kBlock, int kTE>
 __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__restrict__ ptr,
                                                        const int32_t *__restrict__ idx, const int4 *__restrict__ tiles,
-                                                       int32_t num_tiles, int32_t tile_edges,
-                                                       const uint32_t *__restrict__ F, const uint32_t *__restrict__ to,
-                                                       OutSet out, typename Op::V *partial) {
+                                                       int32_t num_tiles, const uint32_t *__restrict__ F,
+                                                       const uint32_t *__restrict__ to, OutSet out,
+                                                       typename Op::V *partial) {
   using V = typename Op::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *vals = reinterpret_cast<V *>(smem_raw);
-  int32_t *rp = reinterpret_cast<int32_t *>(smem_raw + sizeof(V) * (size_t)(tile_edges + tile_edges / kLongRowDiv));
+  int32_t *rp = reinterpret_cast<int32_t *>(smem_raw + sizeof(V) * (size_t)(kTE + kTE / kLongRowDiv));
   __shared__ V s_red[kBlock / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
     const int4 T = tiles[t];
     if (T.y > T.x) {
       const int32_t r0 = T.x, R = T.y - T.x;
-      for (int i = tid; i <= R; i += kBlock) rp[i] = __ldg(ptr + r0 + i);
+      {
+        constexpr int kRp = (kTileRows + 1 + kBlock - 1) / kBlock;
+        int32_t p[kRp];
+#pragma unroll
+        for (int j = 0; j < kRp; ++j) {
+          const int i = tid + j * kBlock;
+          p[j] = i <= R ? __ldg(ptr + r0 + i) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kRp; ++j) {
+          const int i = tid + j * kBlock;
+          if (i <= R) rp[i] = p[j];
+        }
+      }
       __syncthreads();
       const int32_t e0 = rp[0], ne = rp[R] - e0;
-      for (int32_t k = tid; k < ne; k += kBlock) {
-        int32_t u = __ldg(idx + e0 + k);
-        vals[k] = in_set(F, u) ? op.edge_val(u, e0 + k) : Op::identity();
-      }
+      for (int32_t k0 = tid; k0 < ne; k0 += kBatch * kBlock) stage_batch<Op, kBlock>(op, idx, F, e0, k0, ne, vals);
       __syncthreads();
       for (int i0 = 0; i0 < R; i0 += kBlock) {
         const int i = i0 + tid;
@@ -319,12 +352,18 @@ __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__r
       }
       __syncthreads();
     } else {
-      const int32_t r = T.x, e0 = T.z, e1 = T.w;
+      const int32_t r = T.x, e0 = T.z, ne = T.w - T.z;
       V x = Op::identity();
-#pragma unroll 4
-      for (int32_t e = e0 + tid; e < e1; e += kBlock) {
-        int32_t u = __ldg(idx + e);
-        if (in_set(F, u)) x = Op::combine(x, op.edge_val(u, e));
+      for (int32_t k0 = tid; k0 < ne; k0 += kBatch * kBlock) {
+        int32_t u[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+          const int32_t k = k0 + j * kBlock;
+          u[j] = k < ne ? __ldg(idx + e0 + k) : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j)
+          if (u[j] >= 0 && in_set(F, u[j])) x = Op::combine(x, op.edge_val(u[j], e0 + k0 + j * kBlock));
       }
       x = warp_reduce<V, Op>(x);
       if (lane == 0) s_red[warp] = x;
@@ -380,12 +419,18 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
     int32_t found = -1;
     const bool big = active && (b - a) >= t_warp;
     if (active && !big) {
-      for (int32_t e = a; e < b; ++e) {
-        int32_t u = __ldg(idx + e);
-        if (in_set(F, u)) {
-          found = u;
-          break;
-        }
+      // 4 neighbours per round trip: 4 independent index loads, then 4
+      // independent frontier-bit loads; the first hit in order is the min id
+      for (int32_t e = a; e < b && found < 0; e += 4) {
+        int32_t u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) u[j] = e + j < b ? __ldg(idx + e + j) : -1;
+        bool h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = u[j] >= 0 && in_set(F, u[j]);
+#pragma unroll
+        for (int j = 3; j >= 0; --j)
+          if (h[j]) found = u[j];
       }
     }
     unsigned bal = __ballot_sync(0xffffffffu, big);
@@ -423,18 +468,11 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
 }
 
 // ------------------------------------------------------------------- push ------
-// Push from a frontier given as a queue (SparsePush), a bitmap scanned over
-// all vertices (DensePush) or all vertices (from = all).  Load balance
-// (edge-aware mode): sources with >= t_cta arcs are expanded by the whole
-// block, >= t_warp by their warp, the rest by their own thread.  Vertex-parallel
-// mode passes t_warp = t_cta = INT32_MAX.
-enum SrcMode { kSrcQueue = 0, kSrcBitmap = 1, kSrcAll = 2 };
 
 template <class Op>
-__device__ __forceinline__ void push_edge(const Op &op, int32_t u, int32_t e, const int32_t *__restrict__ idx,
-                                          const uint32_t *__restrict__ to, const OutSet &out) {
-  const int32_t v = __ldg(idx + e);
-  const bool mod = in_set(to, v) && op.push(u, v, e);
+__device__ __forceinline__ void push_apply(const Op &op, int32_t u, int32_t v, int32_t e,
+                                           const uint32_t *__restrict__ to, const OutSet &out) {
+  const bool mod = v >= 0 && in_set(to, v) && op.push(u, v, e);
   if (out.enabled()) {
     bool fresh = false;
     if (mod) {
@@ -449,16 +487,75 @@ __device__ __forceinline__ void push_edge(const Op &op, int32_t u, int32_t e, co
   }
 }
 
+// arcs [a + k0, a + k0 + step, ...) of source u: kPushBatch destination loads
+// in flight before the updates
+constexpr int kPushBatch = 4;
+
+template <class Op>
+__device__ __forceinline__ void push_strided(const Op &op, int32_t u, int32_t a, int32_t deg, int32_t k0,
+                                             int32_t step, const int32_t *__restrict__ idx,
+                                             const uint32_t *__restrict__ to, const OutSet &out) {
+  for (int32_t k = k0; k < deg; k += kPushBatch * step) {
+    int32_t v[kPushBatch];
+#pragma unroll
+    for (int j = 0; j < kPushBatch; ++j) v[j] = (k + j * step < deg) ? __ldg(idx + a + k + j * step) : -1;
+#pragma unroll
+    for (int j = 0; j < kPushBatch; ++j) push_apply(op, u, v[j], a + k + j * step, to, out);
+  }
+}
+
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *total, int32_t *sw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sw[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = lane < nw ? sw[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) sw[lane] = w;
+  }
+  __syncthreads();
+  const int32_t off = (warp > 0 ? sw[warp - 1] : 0) + x - v;
+  *total = sw[nw - 1];
+  __syncthreads();
+  return off;
+}
+
+// Push from a frontier given as a queue (SparsePush), a bitmap scanned over
+// all vertices (DensePush) or all vertices (from = all).  Load balance
+// (edge-aware mode, after Merrill et al.'s scan-based gathering): sources with
+// >= t_cta arcs are expanded by the whole block, >= t_warp by their warp; the
+// arcs of the remaining sources of the block are laid out back to back in
+// shared memory (an owner byte per arc) and expanded one arc per thread.
+// Vertex-parallel mode (t_warp = t_cta = INT32_MAX) expands each source's
+// arcs serially in its own thread.
+enum SrcMode { kSrcQueue = 0, kSrcBitmap = 1, kSrcAll = 2 };
+constexpr int kPushBlock = 256;
+constexpr int kMaxTWarp = 64;  // owner table holds kPushBlock * (kMaxTWarp - 1) arcs
+
 template <class Op, int kMode>
-__global__ void __launch_bounds__(256) k_push(Op op, const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                                              const int32_t *__restrict__ q, const int32_t *__restrict__ qcount,
-                                              const uint32_t *__restrict__ Fbm, int64_t n,
-                                              const uint32_t *__restrict__ to, OutSet out, int32_t t_warp,
-                                              int32_t t_cta) {
+__global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__restrict__ ptr,
+                                                     const int32_t *__restrict__ idx, const int32_t *__restrict__ q,
+                                                     const int32_t *__restrict__ qcount,
+                                                     const uint32_t *__restrict__ Fbm, int64_t n,
+                                                     const uint32_t *__restrict__ to, OutSet out, int32_t t_warp,
+                                                     int32_t t_cta) {
   __shared__ int32_t s_owner, s_u, s_a, s_deg;
+  __shared__ int32_t s_src[kPushBlock], s_beg[kPushBlock], s_off[kPushBlock], s_sw[32];
+  __shared__ uint8_t s_own[kPushBlock * (kMaxTWarp - 1)];
   const int tid = threadIdx.x, lane = tid & 31;
+  const bool fine = t_warp <= kMaxTWarp;  // scan-based gathering of small sources
   const int64_t total = (kMode == kSrcQueue) ? (int64_t)(*qcount) : n;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t base = (int64_t)blockIdx.x * kPushBlock; base < total; base += (int64_t)gridDim.x * kPushBlock) {
     const int64_t i = base + tid;
     int32_t u = -1, a = 0, deg = 0;
     if (i < total) {
@@ -485,8 +582,7 @@ __global__ void __launch_bounds__(256) k_push(Op op, const int32_t *__restrict__
         deg = 0;
       }
       __syncthreads();
-      const int32_t cu = s_u, ca = s_a, cd = s_deg;
-      for (int32_t k = tid; k < cd; k += blockDim.x) push_edge(op, cu, ca + k, idx, to, out);
+      push_strided(op, s_u, s_a, s_deg, tid, kPushBlock, idx, to, out);
       __syncthreads();
     }
     // warp-cooperative expansion
@@ -497,9 +593,39 @@ __global__ void __launch_bounds__(256) k_push(Op op, const int32_t *__restrict__
       const int32_t wu = __shfl_sync(0xffffffffu, u, l), wa = __shfl_sync(0xffffffffu, a, l),
                     wd = __shfl_sync(0xffffffffu, deg, l);
       if (lane == l) deg = 0;
-      for (int32_t k = lane; k < wd; k += 32) push_edge(op, wu, wa + k, idx, to, out);
+      push_strided(op, wu, wa, wd, lane, 32, idx, to, out);
     }
-    for (int32_t k = 0; k < deg; ++k) push_edge(op, u, a + k, idx, to, out);
+    if (fine) {
+      int32_t T;
+      const int32_t off = block_excl_scan(deg, &T, s_sw);
+      s_src[tid] = u;
+      s_beg[tid] = a;
+      s_off[tid] = off;
+      for (int32_t k = 0; k < deg; ++k) s_own[off + k] = (uint8_t)tid;
+      __syncthreads();
+      for (int32_t j0 = tid; j0 < T; j0 += kPushBatch * kPushBlock) {
+        int32_t uu[kPushBatch], ee[kPushBatch], vv[kPushBatch];
+#pragma unroll
+        for (int b = 0; b < kPushBatch; ++b) {
+          const int32_t j = j0 + b * kPushBlock;
+          if (j < T) {
+            const int o = s_own[j];
+            uu[b] = s_src[o];
+            ee[b] = s_beg[o] + (j - s_off[o]);
+            vv[b] = __ldg(idx + ee[b]);
+          } else {
+            uu[b] = -1;
+            ee[b] = 0;
+            vv[b] = -1;
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < kPushBatch; ++b) push_apply(op, uu[b], vv[b], ee[b], to, out);
+      }
+      __syncthreads();
+    } else {
+      push_strided(op, u, a, deg, 0, 1, idx, to, out);
+    }
   }
 }
 
@@ -513,19 +639,35 @@ size_t pull_smem_bytes(int32_t tile_edges) {
   return sizeof(typename Op::V) * (size_t)(tile_edges + tile_edges / kLongRowDiv) + sizeof(int32_t) * (kTileRows + 1);
 }
 
+template <class Op, int kTE>
+int launch_pull_tiled_te(const Op &op, const Csr &c, const TileSet &ts, const uint32_t *F, const uint32_t *to,
+                         const OutSet &out, cudaStream_t s) {
+  constexpr int kB = 256;
+  const size_t smem = pull_smem_bytes<Op>(kTE);
+  if (smem > 48 * 1024) {
+    GI_CUDA(cudaFuncSetAttribute(k_pull_tiled<Op, kB, kTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  k_pull_tiled<Op, kB, kTE><<<ts.num_tiles, kB, smem, s>>>(op, c.ptr, c.idx, ts.tiles, ts.num_tiles, F, to, out,
+                                                           reinterpret_cast<typename Op::V *>(ts.partial));
+  return GI_OK;
+}
+
 // Tiled pull over the in-edges `c` with tiles `ts` (the whole graph or one segment).
 template <class Op>
 int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts, const uint32_t *F,
                       const uint32_t *to, const OutSet &out, cudaStream_t s, int kclass = kClassOtherPull) {
   if (ts.num_tiles == 0) return GI_OK;
-  constexpr int kB = 256;
-  const size_t smem = pull_smem_bytes<Op>(ts.tile_edges);
-  if (smem > 48 * 1024) {
-    GI_CUDA(cudaFuncSetAttribute(k_pull_tiled<Op, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
   const int tok = timing_begin(kclass, s);
-  k_pull_tiled<Op, kB><<<ts.num_tiles, kB, smem, s>>>(op, c.ptr, c.idx, ts.tiles, ts.num_tiles, ts.tile_edges, F, to,
-                                                      out, reinterpret_cast<typename Op::V *>(ts.partial));
+  switch (ts.tile_edges) {
+    case 512: GI_TRY((launch_pull_tiled_te<Op, 512>(op, c, ts, F, to, out, s))); break;
+    case 1024: GI_TRY((launch_pull_tiled_te<Op, 1024>(op, c, ts, F, to, out, s))); break;
+    case 2048: GI_TRY((launch_pull_tiled_te<Op, 2048>(op, c, ts, F, to, out, s))); break;
+    case 4096: GI_TRY((launch_pull_tiled_te<Op, 4096>(op, c, ts, F, to, out, s))); break;
+    case 8192: GI_TRY((launch_pull_tiled_te<Op, 8192>(op, c, ts, F, to, out, s))); break;
+    default:
+      set_error("unsupported tile size %d", ts.tile_edges);
+      return GI_ERR_UNSUPPORTED;
+  }
   timing_end(tok, s);
   GI_LAUNCH_CHECK();
   if (ts.num_splits > 0) {
@@ -543,7 +685,9 @@ int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const 
                 const gi_schedule &sc, cudaStream_t s) {
   int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
   int32_t tc = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_cta > 0 ? sc.t_cta : 1024);
-  int block = sc.block >= 64 && sc.block <= 256 && sc.block % 32 == 0 ? sc.block : 256;
+  if (tw != INT32_MAX && tw > kMaxTWarp) tw = kMaxTWarp;
+  if (tc < tw) tc = tw;
+  const int block = kPushBlock;
   int grid;
   const int tok = timing_begin(kClassPush, s);
   if (mode == kSrcQueue) {
