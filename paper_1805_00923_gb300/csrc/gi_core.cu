@@ -506,7 +506,7 @@ namespace gi {
 // tile_edges/kLongRowDiv get ceil(deg/tile_edges) tiles of their own.  So a
 // short tile holds at most kTileRows rows and fewer than
 // tile_edges*(1+1/kLongRowDiv) arcs.
-__global__ void k_tile_count(const int32_t *__restrict__ ptr, int64_t n, int32_t te, int32_t *cnt,
+__global__ void k_tile_count(const int32_t *__restrict__ ptr, int64_t n, int32_t te, int32_t rows_max, int32_t *cnt,
                              int32_t *split_cnt) {
   const int32_t t_long = te / kLongRowDiv;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
@@ -515,7 +515,7 @@ __global__ void k_tile_count(const int32_t *__restrict__ ptr, int64_t n, int32_t
     if (d > t_long) {
       c = (d + te - 1) / te;
       sc = c > 1 ? 1 : 0;
-    } else if (r == 0 || (r % kTileRows) == 0) {
+    } else if (r == 0 || (r % rows_max) == 0) {
       c = 1;
     } else {
       int32_t pa = ptr[r - 1];
@@ -549,12 +549,16 @@ __global__ void k_tile_write(const int32_t *__restrict__ ptr, int64_t n, int32_t
   }
 }
 
-// short tile t ends where tile t+1 begins (or at n)
-__global__ void k_tile_close(int4 *tiles, const int32_t *__restrict__ tile_row, int32_t nt, int64_t n) {
+// short tile t ends where tile t+1 begins (or at n); its arc range is
+// [ptr[r0], ptr[r1])
+__global__ void k_tile_close(int4 *tiles, const int32_t *__restrict__ tile_row, const int32_t *__restrict__ ptr,
+                             int32_t nt, int64_t n) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
     int4 x = tiles[t];
     if (x.y == 0 && x.z == 0 && x.w == 0) {
       x.y = (t + 1 < nt) ? tile_row[t + 1] : (int32_t)n;
+      x.z = ptr[x.x];
+      x.w = ptr[x.y];
       tiles[t] = x;
     }
   }
@@ -570,7 +574,7 @@ int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cuda
   int32_t *off = nullptr, *soff = nullptr;
   GI_TRY(dev_alloc_n(&off, n + 1, s));
   GI_TRY(dev_alloc_n(&soff, n + 1, s));
-  k_tile_count<<<grid_for(g, n, 256), 256, 0, s>>>(c.ptr, n, tile_edges, cnt, scnt);
+  k_tile_count<<<grid_for(g, n, 256), 256, 0, s>>>(c.ptr, n, tile_edges, tile_rows_for(tile_edges), cnt, scnt);
   GI_LAUNCH_CHECK();
   GI_TRY(scan_exclusive(g, cnt, off, n, s));
   GI_TRY(scan_exclusive(g, scnt, soff, n, s));
@@ -588,7 +592,7 @@ int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cuda
   k_tile_write<<<grid_for(g, n, 256), 256, 0, s>>>(c.ptr, n, tile_edges, off, soff, ts->tiles, ts->splits, tile_row);
   GI_LAUNCH_CHECK();
   if (ts->num_tiles > 0) {
-    k_tile_close<<<grid_for(g, ts->num_tiles, 256), 256, 0, s>>>(ts->tiles, tile_row, ts->num_tiles, n);
+    k_tile_close<<<grid_for(g, ts->num_tiles, 256), 256, 0, s>>>(ts->tiles, tile_row, c.ptr, ts->num_tiles, n);
     GI_LAUNCH_CHECK();
   }
   dev_free(off, s);

@@ -60,7 +60,10 @@ namespace gi {
 // ------------------------------------------------------------ constants --
 constexpr int kMaxBlock = 1024;
 constexpr int kLongRowDiv = 2;         // rows with degree > tile_edges/kLongRowDiv get their own tiles
-constexpr int kTileRows = 512;         // at most this many rows per short tile
+constexpr int kTileRows = 512;         // at most this many rows per short block tile
+constexpr int kWarpTileEdges = 256;    // tile_edges value that selects warp-sized tiles
+constexpr int kWarpTileRows = 64;      // at most this many rows per short warp tile
+inline int tile_rows_for(int tile_edges) { return tile_edges == kWarpTileEdges ? kWarpTileRows : kTileRows; }
 constexpr int kCtrlWords = 64;         // int64 words in the per-graph control block
 
 // Control-block slots (int64) written by the frontier-statistics kernel.

@@ -123,9 +123,9 @@ int check_schedule(const gi_schedule *sc) {
   GI_ARG(sc->balance == GI_BAL_VERTEX || sc->balance == GI_BAL_EDGE_AWARE, "unknown balance mode");
   GI_ARG(sc->num_segments >= 1 && sc->num_segments <= 1024, "num_segments must be in [1, 1024]");
   GI_ARG(sc->rule == GI_RULE_BEAMER || sc->rule == GI_RULE_LIGRA, "unknown rule");
-  GI_ARG(sc->tile_edges == 0 || (sc->tile_edges >= 512 && sc->tile_edges <= 8192 &&
+  GI_ARG(sc->tile_edges == 0 || (sc->tile_edges >= 256 && sc->tile_edges <= 8192 &&
                                  (sc->tile_edges & (sc->tile_edges - 1)) == 0),
-         "tile_edges must be a power of two in [512, 8192]");
+         "tile_edges must be a power of two in [256, 8192]");
   return GI_OK;
 }
 

@@ -382,6 +382,93 @@ __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__r
   }
 }
 
+// Warp tiles (tile_edges = 256): every warp owns whole tiles and no block
+// barrier is ever taken, so the SM overlaps the memory latency of up to 64
+// independent warps.  A short warp tile holds <= 64 complete rows of <= 128
+// arcs and < 384 arcs in all: the lanes stage the arc values (12 index loads,
+// then 12 gathers, per lane) in the warp's shared-memory slice, then each lane
+// sums its rows serially.  Long-row pieces (<= 256 arcs) are reduced across
+// the warp.  Split rows leave partials for k_pull_fixup as with block tiles.
+constexpr int kWarpsPerBlock = 8;
+
+template <class Op>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_pull_warp(Op op, const int32_t *__restrict__ ptr,
+                                                                   const int32_t *__restrict__ idx,
+                                                                   const int4 *__restrict__ tiles, int32_t num_tiles,
+                                                                   const uint32_t *__restrict__ F,
+                                                                   const uint32_t *__restrict__ to, OutSet out,
+                                                                   typename Op::V *partial) {
+  using V = typename Op::V;
+  constexpr int kCap = kWarpTileEdges + kWarpTileEdges / kLongRowDiv;
+  constexpr int kPer = kCap / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  V *wb = reinterpret_cast<V *>(smem_raw) + warp * kCap;
+  const int32_t stride = gridDim.x * kWarpsPerBlock;
+  for (int32_t t = blockIdx.x * kWarpsPerBlock + warp; t < num_tiles; t += stride) {
+    const int4 T = tiles[t];
+    if (T.y > T.x) {
+      const int32_t r0 = T.x, R = T.y - T.x, e0 = T.z, ne = T.w - T.z;
+      // row bounds of this lane's rows (issued before the arc loads)
+      int32_t ra[kWarpTileRows / 32], rb[kWarpTileRows / 32];
+#pragma unroll
+      for (int j = 0; j < kWarpTileRows / 32; ++j) {
+        const int i = lane + 32 * j;
+        ra[j] = i < R ? __ldg(ptr + r0 + i) - e0 : 0;
+        rb[j] = i < R ? __ldg(ptr + r0 + i + 1) - e0 : 0;
+      }
+      int32_t u[kPer];
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int32_t k = lane + 32 * j;
+        u[j] = k < ne ? __ldg(idx + e0 + k) : -1;
+      }
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int32_t k = lane + 32 * j;
+        if (k < ne) wb[k] = (u[j] >= 0 && in_set(F, u[j])) ? op.edge_val(u[j], e0 + k) : Op::identity();
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < kWarpTileRows / 32; ++j) {
+        if (32 * j >= R) break;
+        const int i = lane + 32 * j;
+        const bool valid = i < R;
+        V acc = Op::identity();
+        if (valid)
+          for (int32_t k = ra[j]; k < rb[j]; ++k) acc = Op::combine(acc, wb[k]);
+        const int32_t v = r0 + i;
+        bool mod = false;
+        if (valid && in_set(to, v) && op.dst_ok(v)) mod = op.finish(v, acc);
+        if (out.enabled()) mark_consecutive(out, r0 + 32 * j, mod);
+      }
+      __syncwarp();
+    } else {
+      const int32_t r = T.x, e0 = T.z, ne = T.w - T.z;
+      V x = Op::identity();
+      for (int32_t k0 = lane; k0 < ne; k0 += 32 * kBatch) {
+        int32_t uu[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+          const int32_t k = k0 + 32 * j;
+          uu[j] = k < ne ? __ldg(idx + e0 + k) : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j)
+          if (uu[j] >= 0 && in_set(F, uu[j])) x = Op::combine(x, op.edge_val(uu[j], e0 + k0 + 32 * j));
+      }
+      x = warp_reduce<V, Op>(x);
+      if (lane == 0) {
+        if (T.y == r) {
+          if (in_set(to, r) && op.dst_ok(r) && op.finish(r, x) && out.enabled()) out_mark(out, r);
+        } else {
+          partial[t] = x;
+        }
+      }
+    }
+  }
+}
+
 template <class Op>
 __global__ void k_pull_fixup(Op op, const int4 *__restrict__ splits, int32_t num_splits,
                              const typename Op::V *__restrict__ partial, const uint32_t *__restrict__ to, OutSet out) {
@@ -659,6 +746,16 @@ int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts
   if (ts.num_tiles == 0) return GI_OK;
   const int tok = timing_begin(kclass, s);
   switch (ts.tile_edges) {
+    case kWarpTileEdges: {
+      constexpr int kCap = kWarpTileEdges + kWarpTileEdges / kLongRowDiv;
+      const size_t smem = sizeof(typename Op::V) * kCap * kWarpsPerBlock;
+      if (smem > 48 * 1024)
+        GI_CUDA(cudaFuncSetAttribute(k_pull_warp<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int grid = (ts.num_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      k_pull_warp<Op><<<grid, 32 * kWarpsPerBlock, smem, s>>>(op, c.ptr, c.idx, ts.tiles, ts.num_tiles, F, to, out,
+                                                              reinterpret_cast<typename Op::V *>(ts.partial));
+      break;
+    }
     case 512: GI_TRY((launch_pull_tiled_te<Op, 512>(op, c, ts, F, to, out, s))); break;
     case 1024: GI_TRY((launch_pull_tiled_te<Op, 1024>(op, c, ts, F, to, out, s))); break;
     case 2048: GI_TRY((launch_pull_tiled_te<Op, 2048>(op, c, ts, F, to, out, s))); break;

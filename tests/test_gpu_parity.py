@@ -150,7 +150,7 @@ def test_cc_all_schedules(gi, direction):
 
 # ------------------------------------------------------------------ PageRank
 
-@pytest.mark.parametrize("variant", ["pull", "pull_vertex", "push", "seg4", "tile512", "tile8192"])
+@pytest.mark.parametrize("variant", ["pull", "pull_vertex", "push", "seg4", "tile256", "tile512", "tile8192"])
 def test_pagerank_rmat16(gi, variant):
     hg = rmat(16)
     g = _load(gi, hg)
@@ -158,6 +158,7 @@ def test_pagerank_rmat16(gi, variant):
              "pull_vertex": gi.schedule("dense_pull", balance="vertex"),
              "push": gi.schedule("dense_push"),
              "seg4": gi.schedule("dense_pull", num_segments=4),
+             "tile256": gi.schedule("dense_pull", tile_edges=256),
              "tile512": gi.schedule("dense_pull", tile_edges=512),
              "tile8192": gi.schedule("dense_pull", tile_edges=8192)}[variant]
     want = oracle.pagerank(hg, 0.85, 20)
@@ -299,3 +300,31 @@ def test_bad_graph_rejected(gi):
     with pytest.raises(gi.GIError) as e:
         gi.Graph(hg.row_ptr, col, validate=True)
     assert e.value.code == -2
+
+
+@pytest.mark.parametrize("te", [256, 512, 8192])
+def test_pull_tile_sizes(gi, te):
+    """Every tile shape gives the oracle's results for min, sum and probe pulls."""
+    hg = rmat(14, weights=True)
+    g = _load(gi, hg)
+    sc = gi.schedule("dense_pull", tile_edges=te)
+    want, fs = oracle.cc(hg)
+    tr = gi.Trace(64)
+    assert np.array_equal(_np(gi.cc(g, sched=sc, trace=tr)), want)
+    assert np.array_equal(tr.as_dict()["frontier"], fs)
+    want, _ = oracle.sssp(hg, 3)
+    assert np.array_equal(_np(gi.sssp(g, 3, sched=sc)), want)
+    want, _ = oracle.prdelta(hg, 0.85, 1e-7, 10)
+    assert _max_rel(_np(gi.pagerank_delta(g, 0.85, 1e-7, 10, sched=sc)), want) < PR_TOL
+    hub = adversarial("hub_tail")
+    gh = _load(gi, hub)
+    assert _max_rel(_np(gi.pagerank(gh, 0.85, 20, sched=sc)), oracle.pagerank(hub, 0.85, 20)) < PR_TOL
+    fm = (np.random.default_rng(te).random(hg.n) < 0.3).astype(np.uint8)
+    u, v = oracle.edgeset_select(hg, fm)
+    count = torch.zeros(hg.n, dtype=torch.int32, device="cuda")
+    srcsum = torch.zeros(hg.n, dtype=torch.int64, device="cuda")
+    OUT = gi.VertexSet(g)
+    gi.edgeset_apply(g, _mask_set(gi, g, fm), None, sc, gi.GI_K_PROBE,
+                     gi.gi_probe_args(count.data_ptr(), srcsum.data_ptr()), OUT)
+    assert np.array_equal(_np(count), np.bincount(v, minlength=hg.n))
+    assert np.array_equal(_np(OUT.export()), np.flatnonzero(np.bincount(v, minlength=hg.n) > 0))
