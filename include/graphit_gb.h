@@ -260,6 +260,38 @@ int gi_pagerank(gi_graph *g, float damping, int32_t iters, float *rank_dev, cons
                 void *stream);
 
 /*
+ * PageRank without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate GPU memory once they are
+ * running -- for example code that works inside a fixed, pre-reserved memory
+ * budget, or a plug-in whose host application owns the device heap through its
+ * own allocator -- and so cannot use gi_load_csr / gi_pagerank, which allocate
+ * the graph copy, tiles and working vectors.
+ *
+ * Same result as gi_pagerank (the power iteration described there, FP32 with
+ * an FP64 normalisation) on CSR arrays the caller already holds on the device:
+ * in_offsets[n+1] / in_indices[m] are the in-edges (for a symmetric graph, the
+ * CSR itself); out_offsets[n+1] gives out-degrees (NULL: use in_offsets, i.e.
+ * the graph is symmetric).  rank[n] (device) receives the normalised ranks.
+ * The caller owns every array; the library only reads the inputs and writes rank.
+ *
+ * Working memory is a file-scope device array sized for GI_STATIC_PR_MAX_N
+ * vertices (two float vectors plus 1024 doubles, about 8 MB); every GPU that
+ * loads the library holds it until the process exits.  Larger graphs are
+ * rejected with GI_ERR_INVALID_ARG before any work is queued.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array and the kernels re-initialise what they read, so
+ * results do not depend on earlier calls -- but calls whose work overlaps on
+ * the GPU (different streams, or host threads) race on the array and must be
+ * serialised by the caller.  Errors: GI_ERR_INVALID_ARG (sizes, NULL pointers,
+ * n > GI_STATIC_PR_MAX_N), GI_ERR_UNSUPPORTED (m >= 2^31), GI_ERR_CUDA.
+ */
+#define GI_STATIC_PR_MAX_N (1 << 20)
+int gi_pagerank_static(const int32_t *in_offsets, const int32_t *in_indices, const int32_t *out_offsets, int64_t n,
+                       int64_t m, float damping, int32_t iters, float *rank, void *stream);
+
+/*
  * PageRankDelta (Fig. 1, with the round-1 update order of the GraphIt program
  * of Fig. 3): Rank = 0, Delta = 1/n, all vertices active; each round the active
  * vertices propagate Delta/outdeg, every vertex updates Delta and Rank, and

@@ -25,6 +25,7 @@ GI_BAL_VERTEX, GI_BAL_EDGE_AWARE = 0, 1
 GI_RULE_BEAMER, GI_RULE_LIGRA = 0, 1
 GI_K_BFS, GI_K_SSSP, GI_K_CC, GI_K_SUM, GI_K_PROBE = 1, 2, 3, 4, 5
 GI_NO_DEDUP = 0x1
+GI_STATIC_PR_MAX_N = 1 << 20
 
 DIRECTIONS = {"sparse_push": 0, "dense_push": 1, "dense_pull": 2, "hybrid_pull": 3, "hybrid_dpush": 4,
               "learned": 5}
@@ -89,6 +90,7 @@ SIGNATURES = {
     "gi_cc": (ctypes.c_int, [_vp, _vp, _P(gi_schedule), _P(gi_trace), _vp]),
     "gi_pagerank": (ctypes.c_int, [_vp, _f32, _i32, _vp, _P(gi_schedule), _vp]),
     "gi_pagerank_delta": (ctypes.c_int, [_vp, _f32, _f32, _i32, _vp, _P(gi_schedule), _P(gi_trace), _vp]),
+    "gi_pagerank_static": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _f32, _i32, _vp, _vp]),
     "gi_selector_load": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
     "gi_selector_num_params": (ctypes.c_int, []),
     "gi_stats_enable": (ctypes.c_int, [ctypes.c_int]),
