@@ -158,11 +158,13 @@ typedef struct gi_schedule {
   int32_t t_cta;        /* edge-aware: degree >= t_cta goes to a whole block          */
   int32_t rule;         /* GI_RULE_*                                                 */
   float alpha, beta;    /* Beamer constants                                          */
-  int32_t tile_edges;   /* pull tiles: arcs per tile (power of two, 512..8192)        */
+  int32_t tile_edges;   /* pull tiles: arcs per tile (power of two, 256..8192; 256 =   */
+                        /* one warp per tile, larger = one block per tile)            */
+  int32_t t_heavy;      /* edge-aware push: degree >= t_heavy is split over all blocks */
 } gi_schedule;
 
 /* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment, 256 threads, t_warp 32,
- * t_cta 1024, Beamer alpha 14 beta 24, 2048-arc tiles. */
+ * t_cta 1024, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 16384. */
 void gi_schedule_default(gi_schedule *s);
 
 /* ------------------------------------------------------------ edgeset apply -- */
@@ -313,6 +315,34 @@ int gi_selector_load(const float *params, int32_t count, const float *mean, cons
 
 /* Number of parameters of the selector network (5443). */
 int gi_selector_num_params(void);
+
+/*
+ * Training of the selector on the GPU (not in the paper).  All pointers are
+ * device memory, float32.  params: the 5443 parameters in the layout of
+ * gi_selector_load; X[B][16] features, T[B][3] targets (log-time of
+ * SparsePush, DensePush, DensePull), M[B][3] mask (1 = target measured).
+ * gi_mlp_loss_grad writes grad[5443] (overwritten) and loss[2] = {masked MSE
+ * sum_{b,j} M (Y-T)^2 / sum M, sum M}.  gi_mlp_forward writes Y[B][3].
+ * gi_mlp_adam applies one Adam step (Kingma & Ba) with step number t >= 1,
+ * updating params and the moment vectors m, v in place.
+ */
+int gi_mlp_loss_grad(const float *params, const float *X, const float *T, const float *M, int64_t B, float *grad,
+                     float *loss, void *stream);
+int gi_mlp_forward(const float *params, const float *X, int64_t B, float *Y, void *stream);
+int gi_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t t, float lr, float b1, float b2,
+                float eps, void *stream);
+
+/*
+ * Training data for the selector (not in the paper): run BFS (GI_K_BFS) or
+ * SSSP (GI_K_SSSP) from src; at every level keep the state, run SparsePush,
+ * DensePush and DensePull from it, each timed with CUDA events on `stream`,
+ * and continue from the common result.  For level i < cap, features[16*i..]
+ * (host) receive the level's 16 selector features and times_ms[3*i..] (host)
+ * the three durations in milliseconds; *levels the number of levels recorded.
+ * Syncs the stream.  Needs the in-edges (symmetric graph or gi_load_csc).
+ */
+int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, const gi_schedule *sched, int32_t cap,
+                        float *features, float *times_ms, int32_t *levels, void *stream);
 
 /* -------------------------------------------------------------- profiling -- */
 /*

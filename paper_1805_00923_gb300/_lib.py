@@ -38,7 +38,7 @@ _P = ctypes.POINTER
 class gi_schedule(ctypes.Structure):
     _fields_ = [("direction", _i32), ("dense_rep", _u32), ("balance", _i32), ("num_segments", _i32),
                 ("block", _i32), ("t_warp", _i32), ("t_cta", _i32), ("rule", _i32), ("alpha", _f32),
-                ("beta", _f32), ("tile_edges", _i32)]
+                ("beta", _f32), ("tile_edges", _i32), ("t_heavy", _i32)]
 
 
 class gi_trace(ctypes.Structure):
@@ -93,6 +93,10 @@ SIGNATURES = {
     "gi_pagerank_static": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _f32, _i32, _vp, _vp]),
     "gi_selector_load": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
     "gi_selector_num_params": (ctypes.c_int, []),
+    "gi_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "gi_mlp_forward": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "gi_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _f32, _f32, _f32, _f32, _vp]),
+    "gi_selector_profile": (ctypes.c_int, [_vp, _i32, _i32, _P(gi_schedule), _i32, _vp, _vp, _P(_i32), _vp]),
     "gi_stats_enable": (ctypes.c_int, [ctypes.c_int]),
     "gi_stats_reset": (ctypes.c_int, []),
     "gi_stats_read": (ctypes.c_int, [_i32, _P(_i64), _P(_i64), _P(ctypes.c_double)]),

@@ -265,12 +265,16 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
   if (st == GI_OK) st = ctrl_init(g, g->n, g->m, s);
   if (st == GI_OK)
     st = frontier_loop(g, P, sc, true, trace, s, [&](int32_t it, int32_t dir) {
-      gi_bfs_args a{depth, parent, it + 1};
+      // push levels set depth only (no atomics on parents); the canonical
+      // parents of their vertices come from k_bfs_parents afterwards
+      gi_bfs_args a{depth, dir == GI_DIR_DENSE_PULL ? parent : nullptr, it + 1};
       return apply_dispatch(g, P.F, nullptr, dir, sc, GI_K_BFS, &a, P.N, GI_NO_DEDUP, s);
     });
   if (st == GI_OK && parent) {
+    const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
+    k_bfs_parents<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->n, depth, parent, tw);
     k_parent_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n);
-    st = launch_status(1);
+    st = launch_status(2);
   }
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
@@ -500,5 +504,109 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "prdelta", __FILE__, __LINE__);
+  return st;
+}
+
+// ======================================================= selector profiling ==
+// Training data for the learned selector: at every level of a BFS or SSSP run
+// the state is kept, each of SparsePush / DensePush / DensePull runs from it
+// and is timed with CUDA events, and the run continues from the (identical)
+// result.  The level's features are those the selector sees at inference;
+// "was_pull" follows the Beamer / Ligra rule's choice.
+extern "C" int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, const gi_schedule *sched, int32_t cap,
+                                   float *features, float *times_ms, int32_t *levels, void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_TRY(check_schedule(sched));
+  GI_ARG(kernel_id == GI_K_BFS || kernel_id == GI_K_SSSP, "profiling supports GI_K_BFS and GI_K_SSSP");
+  GI_ARG(src >= 0 && src < g->n, "source out of range");
+  GI_ARG(cap >= 0 && features != nullptr && times_ms != nullptr && levels != nullptr, "NULL output");
+  if (kernel_id == GI_K_SSSP) GI_ARG(g->out.wt != nullptr, "SSSP needs edge weights");
+  if (!g->has_csc) {
+    set_error("profiling runs DensePull and needs the in-edges");
+    return GI_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  gi_schedule sc = *sched;
+  sc.direction = GI_DIR_HYBRID_PULL;
+  GI_TRY(ensure_tiles(g, sc, s));
+  const bool bfs = kernel_id == GI_K_BFS;
+  VsetPair P;
+  int32_t *x = nullptr, *snap = nullptr, *keep = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int st = pair_alloc(g, P, s);
+  if (st == GI_OK) st = dev_alloc_n(&x, g->n, s);
+  if (st == GI_OK) st = dev_alloc_n(&keep, g->n, s);
+  if (st == GI_OK && !bfs) st = dev_alloc_n(&snap, g->n, s);
+  if (st == GI_OK && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess))
+    st = cuda_fail(cudaGetLastError(), "event create", __FILE__, __LINE__);
+  if (st == GI_OK) {
+    if (bfs) {
+      k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(x, nullptr, g->n, src);
+      st = launch_status(1);
+    } else {
+      k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(x, g->n, INT32_MAX);
+      k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(snap, g->n, INT32_MAX);
+      k_set_one<<<1, 1, 0, s>>>(x, src, 0);
+      k_set_one<<<1, 1, 0, s>>>(snap, src, 0);
+      st = launch_status(4);
+    }
+  }
+  if (st == GI_OK) st = front_init(g, P.F, src, s);
+  if (st == GI_OK) st = ctrl_init(g, bfs ? g->n : 0, bfs ? g->m : 0, s);
+  int32_t lv = 0;
+  for (int32_t it = 0; st == GI_OK && lv < cap; ++it) {
+    DecideParams p = decide_params(sc, it, bfs);
+    if ((st = frontier_decide(g, P.F, p, s)) != GI_OK) break;
+    if ((st = ctrl_fetch(g, s)) != GI_OK) break;
+    if (g->ctrl_host[kNf] == 0) break;
+    const float *f = reinterpret_cast<const float *>(g->ctrl_host + kFeat);
+    for (int k = 0; k < 16; ++k) features[16 * lv + k] = f[k];
+    if (cudaMemcpyAsync(keep, x, sizeof(int32_t) * g->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "snapshot", __FILE__, __LINE__);
+      break;
+    }
+    const int32_t dirs[3] = {GI_DIR_SPARSE_PUSH, GI_DIR_DENSE_PUSH, GI_DIR_DENSE_PULL};
+    for (int k = 0; k < 3 && st == GI_OK; ++k) {
+      if (k > 0 && cudaMemcpyAsync(x, keep, sizeof(int32_t) * g->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        st = cuda_fail(cudaGetLastError(), "restore", __FILE__, __LINE__);
+        break;
+      }
+      cudaEventRecord(ev[0], s);
+      if (bfs) {
+        gi_bfs_args a{x, nullptr, it + 1};
+        st = apply_dispatch(g, P.F, nullptr, dirs[k], sc, GI_K_BFS, &a, P.N, GI_NO_DEDUP, s);
+      } else {
+        gi_sssp_args a{x, snap};
+        st = apply_dispatch(g, P.F, nullptr, dirs[k], sc, GI_K_SSSP, &a, P.N, 0, s);
+      }
+      cudaEventRecord(ev[1], s);
+      if (st != GI_OK) break;
+      if (cudaEventSynchronize(ev[1]) != cudaSuccess) {
+        st = cuda_fail(cudaGetLastError(), "profile sync", __FILE__, __LINE__);
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      times_ms[3 * lv + k] = ms;
+    }
+    if (st != GI_OK) break;
+    if (!bfs) {
+      int grid = g->num_sms * 4;
+      k_snap_reset<<<grid, 256, 0, s>>>(P.F->queue, P.F->count, snap);
+      k_snap_set<<<grid, 256, 0, s>>>(P.N->queue, P.N->count, snap, x);
+      if ((st = launch_status(2)) != GI_OK) break;
+    }
+    P.swap();
+    ++lv;
+  }
+  *levels = lv;
+  if (ev[0]) cudaEventDestroy(ev[0]);
+  if (ev[1]) cudaEventDestroy(ev[1]);
+  dev_free(x, s);
+  dev_free(keep, s);
+  dev_free(snap, s);
+  pair_free(P, s);
+  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "profile", __FILE__, __LINE__);
   return st;
 }

@@ -109,6 +109,12 @@ void dev_free(void *p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
 
+int heavy_get(gi_graph *g, cudaStream_t s) {
+  if (g->heavy_q) return GI_OK;
+  // queue of n entries followed by its counter
+  return dev_alloc_n(&g->heavy_q, g->n + 1, s);
+}
+
 int grid_for(const gi_graph *g, int64_t work, int block, int per_sm) {
   int64_t want = (work + block - 1) / block;
   int64_t cap = (int64_t)g->num_sms * per_sm;
@@ -373,6 +379,7 @@ static void graph_release(gi_graph *g, cudaStream_t s) {
   dev_free(g->out_deg, s);
   dev_free(g->inv_out_deg, s);
   dev_free(g->ctrl, s);
+  dev_free(g->heavy_q, s);
   ws_free(g, s);
   if (g->ctrl_host) cudaFreeHost(g->ctrl_host);
   delete g;
@@ -1140,4 +1147,5 @@ extern "C" void gi_schedule_default(gi_schedule *s) {
   s->alpha = 14.0f;
   s->beta = 24.0f;
   s->tile_edges = 2048;
+  s->t_heavy = 16384;
 }

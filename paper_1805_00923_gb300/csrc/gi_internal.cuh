@@ -125,6 +125,7 @@ struct gi_graph {
   gi::TileSet in_tiles;          // tiles over the in-edges for pull
   gi::Segments segs;
   int64_t *ctrl = nullptr;       // device control block (kCtrlWords)
+  int32_t *heavy_q = nullptr;    // sources deferred to the all-block expansion (n entries + count)
   int64_t *ctrl_host = nullptr;  // pinned mirror
   gi::Workspace *ws = nullptr;
   int device = 0;
@@ -155,6 +156,7 @@ inline int dev_alloc_n(T **p, int64_t n, cudaStream_t s) {
 // --------------------------------------------------------------- utils --
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 int grid_for(const gi_graph *g, int64_t work, int block, int per_sm = 8);
+int heavy_get(gi_graph *g, cudaStream_t s);  // allocates g->heavy_q on first use
 
 // exclusive scan of n int32 counts into out[n+1] (out[n] = total); scratch owned by g's workspace
 int scan_exclusive(gi_graph *g, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);

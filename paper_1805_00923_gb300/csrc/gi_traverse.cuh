@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__res
                                                      const int32_t *__restrict__ qcount,
                                                      const uint32_t *__restrict__ Fbm, int64_t n,
                                                      const uint32_t *__restrict__ to, OutSet out, int32_t t_warp,
-                                                     int32_t t_cta) {
+                                                     int32_t t_cta, int32_t t_heavy, int32_t *heavy_q) {
   __shared__ int32_t s_owner, s_u, s_a, s_deg;
   __shared__ int32_t s_src[kPushBlock], s_beg[kPushBlock], s_off[kPushBlock], s_sw[32];
   __shared__ uint8_t s_own[kPushBlock * (kMaxTWarp - 1)];
@@ -653,6 +653,11 @@ __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__res
         a = __ldg(ptr + u);
         deg = __ldg(ptr + u + 1) - a;
       }
+    }
+    // the largest sources are expanded afterwards by every block (k_push_heavy)
+    if (deg >= t_heavy) {
+      heavy_q[atomicAdd(heavy_q + n, 1)] = u;
+      deg = 0;
     }
     // block-cooperative expansion of very high-degree sources
     while (true) {
@@ -713,6 +718,96 @@ __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__res
     } else {
       push_strided(op, u, a, deg, 0, 1, idx, to, out);
     }
+  }
+}
+
+}  // namespace gi
+
+namespace gi {
+
+// Sources with >= t_heavy arcs, collected by k_push: their arcs are cut into
+// chunks of kHeavyChunk and chunk c (numbered across all deferred sources) is
+// expanded by block c mod gridDim, so one hub no longer serialises a block.
+constexpr int32_t kHeavyChunk = 4096;
+
+template <class Op>
+__global__ void __launch_bounds__(kPushBlock) k_push_heavy(Op op, const int32_t *__restrict__ ptr,
+                                                           const int32_t *__restrict__ idx,
+                                                           const int32_t *__restrict__ heavy_q, int64_t n,
+                                                           const uint32_t *__restrict__ to, OutSet out) {
+  const int32_t H = heavy_q[n];
+  int64_t first = 0;  // global index of source i's first chunk
+  for (int32_t i = 0; i < H; ++i) {
+    const int32_t u = heavy_q[i];
+    const int32_t a = __ldg(ptr + u), deg = __ldg(ptr + u + 1) - a;
+    const int64_t nch = (deg + kHeavyChunk - 1) / kHeavyChunk;
+    int64_t c = ((int64_t)blockIdx.x - first) % gridDim.x;
+    if (c < 0) c += gridDim.x;
+    for (; c < nch; c += gridDim.x) {
+      const int32_t k0 = (int32_t)c * kHeavyChunk;
+      const int32_t len = min(kHeavyChunk, deg - k0);
+      push_strided(op, u, a + k0, len, (int32_t)threadIdx.x, kPushBlock, idx, to, out);
+    }
+    first += nch;
+  }
+}
+
+// Canonical BFS parents for vertices discovered by push levels (which set
+// depth only): the smallest-id in-neighbour one level closer, found by
+// scanning the sorted in-neighbours (4 per round trip; a warp 32 at a time
+// for rows of >= t_warp arcs).  Vertices found by pull levels already hold it.
+static __global__ void __launch_bounds__(256) k_bfs_parents(const int32_t *__restrict__ ptr,
+                                                            const int32_t *__restrict__ idx, int64_t n,
+                                                            const int32_t *__restrict__ depth, int32_t *parent,
+                                                            int32_t t_warp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (n + 31) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t v = w * 32 + lane;
+    int32_t target = -1, a = 0, b = 0;
+    if (v < n) {
+      const int32_t d = depth[v];
+      if (d > 0 && parent[v] == INT32_MAX) {
+        target = d - 1;
+        a = __ldg(ptr + v);
+        b = __ldg(ptr + v + 1);
+      }
+    }
+    int32_t found = -1;
+    const bool big = target >= 0 && (b - a) >= t_warp;
+    if (target >= 0 && !big) {
+      for (int32_t e = a; e < b && found < 0; e += 4) {
+        int32_t u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) u[j] = e + j < b ? __ldg(idx + e + j) : -1;
+        bool h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = u[j] >= 0 && depth[u[j]] == target;
+#pragma unroll
+        for (int j = 3; j >= 0; --j)
+          if (h[j]) found = u[j];
+      }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, big);
+    while (bal) {
+      const int l = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int32_t la = __shfl_sync(0xffffffffu, a, l), lb = __shfl_sync(0xffffffffu, b, l),
+                    lt = __shfl_sync(0xffffffffu, target, l);
+      int32_t hit = -1;
+      for (int32_t base = la; base < lb; base += 32) {
+        const int32_t e = base + lane;
+        const int32_t u = e < lb ? __ldg(idx + e) : 0;
+        const unsigned hm = __ballot_sync(0xffffffffu, e < lb && depth[u] == lt);
+        if (hm) {
+          hit = __shfl_sync(0xffffffffu, u, __ffs(hm) - 1);
+          break;
+        }
+      }
+      if (lane == l) found = hit;
+    }
+    if (found >= 0) parent[v] = found;
   }
 }
 
@@ -784,24 +879,33 @@ int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const 
   int32_t tc = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_cta > 0 ? sc.t_cta : 1024);
   if (tw != INT32_MAX && tw > kMaxTWarp) tw = kMaxTWarp;
   if (tc < tw) tc = tw;
+  const int32_t th = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_heavy > 0 ? max(sc.t_heavy, tc) : INT32_MAX);
+  if (th != INT32_MAX) {
+    GI_TRY(heavy_get(g, s));
+    GI_CUDA(cudaMemsetAsync(g->heavy_q + g->n, 0, sizeof(int32_t), s));
+  }
   const int block = kPushBlock;
   int grid;
   const int tok = timing_begin(kClassPush, s);
   if (mode == kSrcQueue) {
     grid = g->num_sms * (2048 / block);
     k_push<Op, kSrcQueue><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, from->queue, from->count, nullptr, g->n,
-                                                 to, out, tw, tc);
+                                                 to, out, tw, tc, th, g->heavy_q);
   } else if (mode == kSrcBitmap) {
     grid = grid_for(g, g->n, block, 2048 / block);
     k_push<Op, kSrcBitmap><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, from->bitmap, g->n,
-                                                  to, out, tw, tc);
+                                                  to, out, tw, tc, th, g->heavy_q);
   } else {
     grid = grid_for(g, g->n, block, 2048 / block);
     k_push<Op, kSrcAll><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, nullptr, g->n, to, out,
-                                               tw, tc);
+                                               tw, tc, th, g->heavy_q);
+  }
+  GI_LAUNCH_CHECK();
+  if (th != INT32_MAX) {
+    k_push_heavy<Op><<<g->num_sms * 4, block, 0, s>>>(op, g->out.ptr, g->out.idx, g->heavy_q, g->n, to, out);
+    GI_LAUNCH_CHECK();
   }
   timing_end(tok, s);
-  GI_LAUNCH_CHECK();
   return GI_OK;
 }
 
