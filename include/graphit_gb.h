@@ -344,6 +344,28 @@ int gi_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t t,
 int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, const gi_schedule *sched, int32_t cap,
                         float *features, float *times_ms, int32_t *levels, void *stream);
 
+/* ------------------------------------------------------------- autotuner -- */
+/* algorithms the autotuner runs (the drivers above with their Sec. 7 settings) */
+#define GI_ALGO_BFS 1            /* gi_bfs from src, depths only          */
+#define GI_ALGO_SSSP 2           /* gi_sssp from src                      */
+#define GI_ALGO_CC 3             /* gi_cc                                 */
+#define GI_ALGO_PAGERANK 4       /* gi_pagerank, damping 0.85, 20 iters   */
+#define GI_ALGO_PAGERANK_DELTA 5 /* gi_pagerank_delta, 0.85, 1e-7, 10     */
+
+/*
+ * Schedule autotuner (the paper tunes schedules with OpenTuner, Sec. 6): keeps
+ * start->direction/balance/rule and searches tile_edges, t_warp, t_cta,
+ * t_heavy, num_segments (PageRank DensePull) and, for rule-based BFS hybrids,
+ * Beamer's alpha/beta: random candidates for the first third of `budget`
+ * trials, then hill climbing around the best.  Each candidate runs once to
+ * warm up and is timed (best of 2) with CUDA events on `stream`; a candidate
+ * whose output differs from start's (integers bit-exact, ranks beyond 1e-4
+ * relative) is rejected.  *best receives the fastest valid schedule, *best_ms
+ * and *start_ms (may be NULL) its time and start's.  Syncs the stream.
+ */
+int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_schedule *start, int32_t budget, uint64_t seed,
+                gi_schedule *best, double *best_ms, double *start_ms, void *stream);
+
 /* -------------------------------------------------------------- profiling -- */
 /*
  * Host-side instrumentation for benchmarks (not part of the paper).  The

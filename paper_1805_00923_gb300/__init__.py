@@ -265,3 +265,22 @@ def stats_read(kclass: int | str = -1):
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
     check(_C.gi_stats_read(int(kclass), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+ALGOS = {"bfs": L.GI_ALGO_BFS, "sssp": L.GI_ALGO_SSSP, "cc": L.GI_ALGO_CC, "pagerank": L.GI_ALGO_PAGERANK,
+         "pagerank_delta": L.GI_ALGO_PAGERANK_DELTA}
+
+
+def autotune(g: Graph, algo, src: int = 0, start=None, budget: int = 30, seed: int = 1, stream=None):
+    """gi_autotune: (best schedule, best ms, start ms)."""
+    algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    best = gi_schedule()
+    bms, sms = ctypes.c_double(), ctypes.c_double()
+    st = start if start is not None else schedule()
+    check(_C.gi_autotune(g.handle, algo, int(src), ctypes.byref(st), int(budget), int(seed), ctypes.byref(best),
+                         ctypes.byref(bms), ctypes.byref(sms), _stream(stream)))
+    return best, bms.value, sms.value
+
+
+def schedule_dict(s: gi_schedule) -> dict:
+    return {f: getattr(s, f) for f, _ in gi_schedule._fields_}

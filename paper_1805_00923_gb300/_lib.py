@@ -26,6 +26,7 @@ GI_RULE_BEAMER, GI_RULE_LIGRA = 0, 1
 GI_K_BFS, GI_K_SSSP, GI_K_CC, GI_K_SUM, GI_K_PROBE = 1, 2, 3, 4, 5
 GI_NO_DEDUP = 0x1
 GI_STATIC_PR_MAX_N = 1 << 20
+GI_ALGO_BFS, GI_ALGO_SSSP, GI_ALGO_CC, GI_ALGO_PAGERANK, GI_ALGO_PAGERANK_DELTA = 1, 2, 3, 4, 5
 
 DIRECTIONS = {"sparse_push": 0, "dense_push": 1, "dense_pull": 2, "hybrid_pull": 3, "hybrid_dpush": 4,
               "learned": 5}
@@ -97,6 +98,8 @@ SIGNATURES = {
     "gi_mlp_forward": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "gi_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _f32, _f32, _f32, _f32, _vp]),
     "gi_selector_profile": (ctypes.c_int, [_vp, _i32, _i32, _P(gi_schedule), _i32, _vp, _vp, _P(_i32), _vp]),
+    "gi_autotune": (ctypes.c_int, [_vp, _i32, _i32, _P(gi_schedule), _i32, ctypes.c_uint64, _P(gi_schedule),
+                                   _P(ctypes.c_double), _P(ctypes.c_double), _vp]),
     "gi_stats_enable": (ctypes.c_int, [ctypes.c_int]),
     "gi_stats_reset": (ctypes.c_int, []),
     "gi_stats_read": (ctypes.c_int, [_i32, _P(_i64), _P(_i64), _P(ctypes.c_double)]),

@@ -111,8 +111,11 @@ void dev_free(void *p, cudaStream_t s) {
 
 int heavy_get(gi_graph *g, cudaStream_t s) {
   if (g->heavy_q) return GI_OK;
-  // queue of n entries followed by its counter
-  return dev_alloc_n(&g->heavy_q, g->n + 1, s);
+  // queue of n entries, then its count and the finishing-block ticket; the
+  // expansion kernel returns both to zero after each use
+  GI_TRY(dev_alloc_n(&g->heavy_q, g->n + 2, s));
+  GI_CUDA(cudaMemsetAsync(g->heavy_q + g->n, 0, 2 * sizeof(int32_t), s));
+  return GI_OK;
 }
 
 int grid_for(const gi_graph *g, int64_t work, int block, int per_sm) {

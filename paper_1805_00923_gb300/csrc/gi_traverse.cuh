@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push_heavy(Op op, const int32_t 
                                                            const int32_t *__restrict__ idx,
                                                            const int32_t *__restrict__ heavy_q, int64_t n,
                                                            const uint32_t *__restrict__ to, OutSet out) {
-  const int32_t H = heavy_q[n];
+  const int32_t H = *(volatile int32_t *)(heavy_q + n);
   int64_t first = 0;  // global index of source i's first chunk
   for (int32_t i = 0; i < H; ++i) {
     const int32_t u = heavy_q[i];
@@ -749,6 +749,17 @@ __global__ void __launch_bounds__(kPushBlock) k_push_heavy(Op op, const int32_t 
       push_strided(op, u, a + k0, len, (int32_t)threadIdx.x, kPushBlock, idx, to, out);
     }
     first += nch;
+  }
+  // the last block to finish empties the list for the next push (every block
+  // has read H before it takes its ticket)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(heavy_q + n + 1, 1) == (int32_t)gridDim.x - 1) {
+      heavy_q[n] = 0;
+      heavy_q[n + 1] = 0;
+      __threadfence();
+    }
   }
 }
 
@@ -880,10 +891,7 @@ int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const 
   if (tw != INT32_MAX && tw > kMaxTWarp) tw = kMaxTWarp;
   if (tc < tw) tc = tw;
   const int32_t th = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_heavy > 0 ? max(sc.t_heavy, tc) : INT32_MAX);
-  if (th != INT32_MAX) {
-    GI_TRY(heavy_get(g, s));
-    GI_CUDA(cudaMemsetAsync(g->heavy_q + g->n, 0, sizeof(int32_t), s));
-  }
+  if (th != INT32_MAX) GI_TRY(heavy_get(g, s));
   const int block = kPushBlock;
   int grid;
   const int tok = timing_begin(kClassPush, s);

@@ -1,0 +1,202 @@
+// Autotuner for schedule parameters (the paper tunes schedules with OpenTuner,
+// Sec. 6 "Autotuning"; this is a small search written for the GPU knobs).
+//
+// Search: the start schedule, then random candidates, then hill climbing (one
+// parameter moved to a neighbouring value of the best so far).  Every
+// candidate is timed with CUDA events (best of `reps` runs after one warm-up)
+// and is rejected when its output differs from the start schedule's output
+// (integers bit-exact, ranks within 1e-4 relative) -- the paper's tuner
+// likewise discards invalid schedules.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "gi_internal.cuh"
+
+namespace gi {
+
+struct Knob {
+  int32_t gi_schedule::*field;
+  std::vector<int32_t> values;
+};
+
+__global__ void k_count_diff_i32(const int32_t *__restrict__ a, const int32_t *__restrict__ b, int64_t n,
+                                 unsigned long long *out) {
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    c += a[i] != b[i];
+  if (c) atomicAdd(out, c);
+}
+
+__global__ void k_count_far_f32(const float *__restrict__ a, const float *__restrict__ b, int64_t n, float rtol,
+                                unsigned long long *out) {
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float d = fabsf(a[i] - b[i]), r = fabsf(b[i]);
+    c += !(d <= rtol * r + 1e-30f);
+  }
+  if (c) atomicAdd(out, c);
+}
+
+struct Runner {
+  gi_graph *g;
+  int32_t algo, src;
+  cudaStream_t s;
+  void *out = nullptr;      // current output
+  void *ref = nullptr;      // start schedule's output
+  unsigned long long *diff = nullptr;
+
+  int run(const gi_schedule &sc) {
+    switch (algo) {
+      case GI_ALGO_BFS: return gi_bfs(g, src, (int32_t *)out, nullptr, &sc, nullptr, s);
+      case GI_ALGO_SSSP: return gi_sssp(g, src, (int32_t *)out, &sc, nullptr, s);
+      case GI_ALGO_CC: return gi_cc(g, (int32_t *)out, &sc, nullptr, s);
+      case GI_ALGO_PAGERANK: return gi_pagerank(g, 0.85f, 20, (float *)out, &sc, s);
+      case GI_ALGO_PAGERANK_DELTA: return gi_pagerank_delta(g, 0.85f, 1e-7f, 10, (float *)out, &sc, nullptr, s);
+    }
+    return GI_ERR_INVALID_ARG;
+  }
+
+  bool is_float() const { return algo == GI_ALGO_PAGERANK || algo == GI_ALGO_PAGERANK_DELTA; }
+
+  // 0 = same as reference, 1 = differs, <0 error
+  int compare() {
+    if (cudaMemsetAsync(diff, 0, sizeof(unsigned long long), s) != cudaSuccess) return GI_ERR_CUDA;
+    if (is_float())
+      k_count_far_f32<<<grid_for(g, g->n, 256), 256, 0, s>>>((const float *)out, (const float *)ref, g->n, 1e-4f,
+                                                             diff);
+    else
+      k_count_diff_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>((const int32_t *)out, (const int32_t *)ref, g->n,
+                                                              diff);
+    GI_TRY(launch_status(1));
+    unsigned long long h = 0;
+    GI_CUDA(cudaMemcpyAsync(&h, diff, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GI_CUDA(cudaStreamSynchronize(s));
+    return h ? 1 : 0;
+  }
+
+  // best-of-reps milliseconds after one warm-up run
+  int time(const gi_schedule &sc, int reps, double *ms) {
+    GI_TRY(run(sc));
+    cudaEvent_t a, b;
+    GI_CUDA(cudaEventCreate(&a));
+    GI_CUDA(cudaEventCreate(&b));
+    double best = 1e300;
+    int st = GI_OK;
+    for (int r = 0; r < reps && st == GI_OK; ++r) {
+      cudaEventRecord(a, s);
+      st = run(sc);
+      cudaEventRecord(b, s);
+      if (st == GI_OK && cudaEventSynchronize(b) == cudaSuccess) {
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, a, b);
+        best = t < best ? t : best;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms = best;
+    return st;
+  }
+};
+
+}  // namespace gi
+
+using namespace gi;
+
+extern "C" int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_schedule *start, int32_t budget,
+                           uint64_t seed, gi_schedule *best, double *best_ms, double *start_ms, void *stream) {
+  GI_ARG(g != nullptr && start != nullptr && best != nullptr, "NULL argument");
+  GI_TRY(check_schedule(start));
+  GI_ARG(algo >= GI_ALGO_BFS && algo <= GI_ALGO_PAGERANK_DELTA, "unknown algorithm");
+  GI_ARG(budget >= 1 && budget <= 100000, "budget must be in [1, 100000]");
+  if (algo == GI_ALGO_BFS || algo == GI_ALGO_SSSP) GI_ARG(src >= 0 && src < g->n, "source out of range");
+  if (algo == GI_ALGO_SSSP) GI_ARG(g->out.wt != nullptr, "SSSP needs edge weights");
+  if (g->n == 0) {
+    *best = *start;
+    if (best_ms) *best_ms = 0.0;
+    if (start_ms) *start_ms = 0.0;
+    return GI_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Runner R{g, algo, src, s};
+  int st = dev_alloc(&R.out, 4 * (size_t)g->n, s);
+  if (st == GI_OK) st = dev_alloc(&R.ref, 4 * (size_t)g->n, s);
+  if (st == GI_OK) st = dev_alloc_n(&R.diff, 1, s);
+  std::vector<Knob> knobs = {
+      {&gi_schedule::tile_edges, {256, 512, 1024, 2048, 4096, 8192}},
+      {&gi_schedule::t_warp, {8, 16, 32, 64}},
+      {&gi_schedule::t_cta, {256, 512, 1024, 2048, 4096}},
+      {&gi_schedule::t_heavy, {4096, 8192, 16384, 32768, 65536, INT32_MAX}},
+  };
+  if (algo == GI_ALGO_PAGERANK && start->direction == GI_DIR_DENSE_PULL)
+    knobs.push_back({&gi_schedule::num_segments, {1, 2, 4, 8}});
+  std::mt19937_64 rng(seed);
+  const int reps = 2;
+  gi_schedule cur = *start, top = *start;
+  double t_start = 0.0, t_top = 0.0;
+  if (st == GI_OK) st = R.time(cur, reps, &t_start);
+  if (st == GI_OK && cudaMemcpyAsync(R.ref, R.out, 4 * (size_t)g->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "autotune reference", __FILE__, __LINE__);
+  t_top = t_start;
+  // Beamer constants are knobs for rule-based hybrids of BFS (float fields)
+  const bool tune_ab = algo == GI_ALGO_BFS && (start->direction == GI_DIR_HYBRID_PULL ||
+                                               start->direction == GI_DIR_HYBRID_DPUSH);
+  const float alphas[] = {4.f, 8.f, 14.f, 24.f, 48.f}, betas[] = {8.f, 16.f, 24.f, 48.f, 96.f};
+  for (int32_t trial = 1; trial < budget && st == GI_OK; ++trial) {
+    gi_schedule cand = top;
+    if (trial < budget / 3) {  // random phase
+      for (auto &k : knobs) cand.*(k.field) = k.values[rng() % k.values.size()];
+      if (tune_ab) {
+        cand.alpha = alphas[rng() % 5];
+        cand.beta = betas[rng() % 5];
+      }
+    } else {  // hill climbing around the best
+      const int nk = (int)knobs.size() + (tune_ab ? 2 : 0);
+      const int which = (int)(rng() % nk);
+      const int dirn = (rng() & 1) ? 1 : -1;
+      if (which < (int)knobs.size()) {
+        auto &k = knobs[which];
+        int pos = 0;
+        while (pos < (int)k.values.size() && k.values[pos] != top.*(k.field)) ++pos;
+        pos = pos >= (int)k.values.size() ? 0 : pos + dirn;
+        if (pos < 0 || pos >= (int)k.values.size()) continue;
+        cand.*(k.field) = k.values[pos];
+      } else {
+        const float *vals = which == (int)knobs.size() ? alphas : betas;
+        float &f = which == (int)knobs.size() ? cand.alpha : cand.beta;
+        int pos = 0;
+        while (pos < 5 && vals[pos] != f) ++pos;
+        pos = pos >= 5 ? 2 : pos + dirn;
+        if (pos < 0 || pos >= 5) continue;
+        f = vals[pos];
+      }
+    }
+    if (cand.t_cta < cand.t_warp) cand.t_cta = cand.t_warp;
+    double t = 0.0;
+    st = R.time(cand, reps, &t);
+    if (st != GI_OK) break;
+    const int d = R.compare();
+    if (d < 0) {
+      st = d;
+      break;
+    }
+    if (d == 0 && t < t_top) {
+      top = cand;
+      t_top = t;
+    }
+  }
+  dev_free(R.out, s);
+  dev_free(R.ref, s);
+  dev_free(R.diff, s);
+  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "autotune", __FILE__, __LINE__);
+  if (st != GI_OK) return st;
+  *best = top;
+  if (best_ms) *best_ms = t_top;
+  if (start_ms) *start_ms = t_start;
+  return GI_OK;
+}

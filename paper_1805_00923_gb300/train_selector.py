@@ -1,0 +1,129 @@
+"""Train the learned direction selector on the GPU and write its weights.
+
+    python -m paper_1805_00923_gb300.train_selector --out selector_weights.npz
+
+Training data are per-level timings of SparsePush, DensePush and DensePull
+(gi_selector_profile) for BFS and SSSP on seeded synthetic graphs: R-MAT graphs
+of scales 12-20 with edge factors 8-32 (social/web-like) and 2-D grids with 1%
+local shortcuts of sides 128-1024 (road-like), several sources each.  The
+network learns log(time in us) of each direction; training is full-batch Adam
+with the library's own kernels.  Held-out graphs (other seeds) report the
+recorded cost of the learned choices against Beamer's rule and the
+per-level optimum.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def workloads(seed_base: int, quick: bool):
+    import graphgen as gg
+    out = []
+    scales = [12, 14, 16, 18] if quick else [12, 14, 16, 18, 20, 22]
+    for sc in scales:
+        for ef in (8, 16, 32):
+            out.append(("bfs", f"rmat{sc}_ef{ef}", lambda sc=sc, ef=ef: gg.rmat_graph(sc, ef, seed=seed_base + sc)))
+    for sc in scales[:-1]:
+        out.append(("sssp", f"rmat{sc}_w", lambda sc=sc: gg.rmat_graph(sc, 16, seed=seed_base + 50 + sc,
+                                                                         weights=(1, 1000))))
+    sides = [128, 256, 512] if quick else [128, 256, 512, 1024, 2048]
+    for side in sides:
+        out.append(("bfs", f"grid{side}", lambda side=side: gg.grid_graph(side, seed=seed_base + side)))
+    for side in sides[:-1]:
+        out.append(("sssp", f"grid{side}_w", lambda side=side: gg.grid_graph(side, seed=seed_base + 7 * side,
+                                                                             weights=(1, 100))))
+    return out
+
+
+def collect(items, n_src: int, max_levels_per_run: int = 400):
+    import graphgen as gg
+    import paper_1805_00923_gb300 as gi
+    from paper_1805_00923_gb300 import selector as sel
+    X, T, tags = [], [], []
+    for algo, name, make in items:
+        hg = make()
+        g = gi.Graph.from_host(hg)
+        kern = gi.GI_K_BFS if algo == "bfs" else gi.GI_K_SSSP
+        for s in gg.pick_sources(hg, n_src, seed=len(name)):
+            f, t = sel.profile(g, kern, int(s))
+            if len(f) > max_levels_per_run:  # keep long road-like runs from swamping the data
+                keep = np.linspace(0, len(f) - 1, max_levels_per_run).astype(int)
+                f, t = f[keep], t[keep]
+            X.append(f)
+            T.append(t)
+            tags += [f"{algo}:{name}"] * len(f)
+        g.free()
+    return np.concatenate(X), np.concatenate(T), np.array(tags)
+
+
+def evaluate(params, mean, inv_std, items, n_src: int):
+    """Recorded cost of learned vs Beamer/Ligra vs per-level best on held-out runs."""
+    import graphgen as gg
+    import paper_1805_00923_gb300 as gi
+    from paper_1805_00923_gb300 import selector as sel
+    rows = []
+    for algo, name, make in items:
+        hg = make()
+        g = gi.Graph.from_host(hg)
+        kern = gi.GI_K_BFS if algo == "bfs" else gi.GI_K_SSSP
+        tot = np.zeros(3)
+        for s in gg.pick_sources(hg, n_src, seed=99):
+            f, t = sel.profile(g, kern, int(s))
+            tr = gi.Trace(1 << 16)
+            if algo == "bfs":
+                gi.bfs(g, int(s), want_parent=False, sched=gi.schedule("hybrid_pull"), trace=tr)
+            else:
+                gi.sssp(g, int(s), sched=gi.schedule("hybrid_pull"), trace=tr)
+            rule = tr.as_dict()["direction"][:len(t)]
+            learned = sel.choose(params, mean, inv_std, f)
+            idx = np.arange(len(t))
+            tot += [t[idx, learned].sum(), t[idx, rule].sum(), t.min(axis=1).sum()]
+        rows.append(dict(graph=f"{algo}:{name}", learned_ms=tot[0], rule_ms=tot[1], best_ms=tot[2]))
+        g.free()
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                  "selector_weights.npz"))
+    ap.add_argument("--sources", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--report", default=None)
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1805_00923_gb300 import selector as sel
+    t0 = time.time()
+    X, Tms, tags = collect(workloads(1000, args.quick), args.sources)
+    t1 = time.time()
+    T = sel.targets(Tms)
+    params, mean, inv_std, losses = sel.train(X, T, steps=args.steps)
+    t2 = time.time()
+    sel.save(args.out, params, mean, inv_std, samples=X.shape[0], steps=args.steps, losses=np.array(losses))
+    held = [it for it in workloads(5000, True)]
+    rows = evaluate(params, mean, inv_std, held, 2)
+    tot = {k: float(sum(r[k] for r in rows)) for k in ("learned_ms", "rule_ms", "best_ms")}
+    report = dict(samples=int(X.shape[0]), collect_s=t1 - t0, train_s=t2 - t1, loss_first=losses[0],
+                  loss_last=losses[-1], heldout=rows, heldout_total=tot,
+                  train_choice_share=np.bincount(np.argmin(Tms, 1), minlength=3).tolist())
+    txt = json.dumps(report, indent=1, default=float)
+    print(txt)
+    if args.report:
+        with open(args.report, "w") as f:
+            f.write(txt)
+
+
+if __name__ == "__main__":
+    main()

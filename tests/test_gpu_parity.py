@@ -328,3 +328,28 @@ def test_pull_tile_sizes(gi, te):
                      gi.gi_probe_args(count.data_ptr(), srcsum.data_ptr()), OUT)
     assert np.array_equal(_np(count), np.bincount(v, minlength=hg.n))
     assert np.array_equal(_np(OUT.export()), np.flatnonzero(np.bincount(v, minlength=hg.n) > 0))
+
+
+# ----------------------------------------------------------------- autotuner
+
+@pytest.mark.parametrize("algo", ["bfs", "sssp", "cc", "pagerank", "pagerank_delta"])
+def test_autotune_returns_valid_faster_schedule(gi, algo):
+    hg = rmat(14, weights=True)
+    g = _load(gi, hg)
+    start = gi.schedule("dense_pull" if algo == "pagerank" else "hybrid_pull")
+    best, best_ms, start_ms = gi.autotune(g, algo, src=0, start=start, budget=8, seed=3)
+    assert best_ms <= start_ms
+    assert best.direction == start.direction and best.balance == start.balance
+    if algo == "bfs":
+        d, p = gi.bfs(g, 0, sched=best)
+        wd, wp, _ = oracle.bfs(hg, 0)
+        assert np.array_equal(_np(d), wd) and np.array_equal(_np(p), wp)
+    elif algo == "sssp":
+        assert np.array_equal(_np(gi.sssp(g, 0, sched=best)), oracle.sssp(hg, 0)[0])
+    elif algo == "cc":
+        assert np.array_equal(_np(gi.cc(g, sched=best)), oracle.cc(hg)[0])
+    elif algo == "pagerank":
+        assert _max_rel(_np(gi.pagerank(g, 0.85, 20, sched=best)), oracle.pagerank(hg, 0.85, 20)) < PR_TOL
+    else:
+        assert _max_rel(_np(gi.pagerank_delta(g, 0.85, 1e-7, 10, sched=best)),
+                        oracle.prdelta(hg, 0.85, 1e-7, 10)[0]) < PR_TOL
