@@ -733,7 +733,7 @@ constexpr int32_t kHeavyChunk = 4096;
 template <class Op>
 __global__ void __launch_bounds__(kPushBlock) k_push_heavy(Op op, const int32_t *__restrict__ ptr,
                                                            const int32_t *__restrict__ idx,
-                                                           const int32_t *__restrict__ heavy_q, int64_t n,
+                                                           int32_t *heavy_q, int64_t n,
                                                            const uint32_t *__restrict__ to, OutSet out) {
   const int32_t H = *(volatile int32_t *)(heavy_q + n);
   int64_t first = 0;  // global index of source i's first chunk

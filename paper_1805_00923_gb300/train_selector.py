@@ -4,8 +4,8 @@
 
 Training data are per-level timings of SparsePush, DensePush and DensePull
 (gi_selector_profile) for BFS and SSSP on seeded synthetic graphs: R-MAT graphs
-of scales 12-20 with edge factors 8-32 (social/web-like) and 2-D grids with 1%
-local shortcuts of sides 128-1024 (road-like), several sources each.  The
+of scales 12-22 with edge factors 8-32 (social/web-like) and 2-D grids with 1%
+local shortcuts of sides 128-2048 (road-like), several sources each.  The
 network learns log(time in us) of each direction; training is full-batch Adam
 with the library's own kernels.  Held-out graphs (other seeds) report the
 recorded cost of the learned choices against Beamer's rule and the
