@@ -344,6 +344,40 @@ int gi_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t t,
 int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, const gi_schedule *sched, int32_t cap,
                         float *features, float *times_ms, int32_t *levels, void *stream);
 
+/* ---------------------------------------------------------------- batched -- */
+/*
+ * Many BFS / SSSP queries over several graphs in one persistent launch (not in
+ * the paper, which runs one query at a time).  The launch is a grid of
+ * thread-block clusters; each cluster claims the next query from a global
+ * counter and runs it to completion with cluster barriers between levels
+ * (BFS: SparsePush or early-exit DensePull per level; SSSP: synchronous
+ * Bellman-Ford push).  No cluster ever waits for another.
+ */
+typedef struct gi_batch_opts {
+  int32_t cluster_size; /* CTAs per query: 1, 2, 4 or 8 (default 4)                       */
+  int32_t clusters;     /* clusters launched; 0 = SM count / cluster_size                  */
+  int32_t selector;     /* BFS direction per level: GI_DIR_SPARSE_PUSH (always push),      */
+                        /* GI_DIR_HYBRID_PULL (Beamer rule) or GI_DIR_LEARNED (the MLP)    */
+  float alpha, beta;    /* Beamer constants                                                */
+  int64_t level_cap;    /* give up after this many levels (0 = n+2): GI_ERR_TIMEOUT       */
+} gi_batch_opts;
+
+void gi_batch_opts_default(gi_batch_opts *o);
+
+/*
+ * graphs[n_graphs]: loaded graphs.  Query i (host arrays): graph q_graph[i],
+ * source q_src[i], algorithm q_algo[i] (GI_ALGO_BFS or GI_ALGO_SSSP); its
+ * result goes to out_dev[i] (a device pointer with n of that graph entries:
+ * BFS depth, -1 if unreached; SSSP distance, INT32_MAX if unreachable --
+ * the same values as gi_bfs / gi_sssp).  q_ns[n_q] (host, may be NULL)
+ * receives each query's device time in nanoseconds (%globaltimer).  opts may
+ * be NULL (defaults).  Syncs the stream.  Errors: GI_ERR_INVALID_ARG,
+ * GI_ERR_TIMEOUT (a query hit level_cap), GI_ERR_OOM, GI_ERR_CUDA.
+ */
+int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int32_t *q_graph, const int32_t *q_src,
+                 const int32_t *q_algo, int32_t n_q, int32_t *const *out_dev, int64_t *q_ns,
+                 const gi_batch_opts *opts, void *stream);
+
 /* ------------------------------------------------------------- autotuner -- */
 /* algorithms the autotuner runs (the drivers above with their Sec. 7 settings) */
 #define GI_ALGO_BFS 1            /* gi_bfs from src, depths only          */
@@ -379,6 +413,7 @@ int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_schedule *start
 #define GI_KCLASS_PUSH 3       /* SparsePush / DensePush expansion                         */
 #define GI_KCLASS_BFS_PULL 4   /* early-exit BFS DensePull                                 */
 #define GI_KCLASS_OTHER_PULL 5 /* other tiled pulls (sum, probe, segments)                 */
+#define GI_KCLASS_BATCH 6      /* the batched persistent engine                            */
 
 /* Turn per-launch event timing on (1) or off (0); counting is always on. */
 int gi_stats_enable(int timing_on);

@@ -18,7 +18,7 @@ from ._lib import (GI_BAL_EDGE_AWARE, GI_BAL_VERTEX, GI_DIR_DENSE_PULL, GI_DIR_D
                    GI_DIR_HYBRID_DPUSH, GI_DIR_HYBRID_PULL, GI_DIR_LEARNED, GI_DIR_SPARSE_PUSH, GI_K_BFS,
                    GI_K_CC, GI_K_PROBE, GI_K_SSSP, GI_K_SUM, GI_NO_DEDUP, GI_REP_BITMAP, GI_REP_BOOL,
                    GI_REP_SPARSE, GI_RULE_BEAMER, GI_RULE_LIGRA, GI_VSET_ALL, GI_VSET_EMPTY, GI_VSET_SINGLE,
-                   GIError, gi_bfs_args, gi_cc_args, gi_probe_args, gi_schedule, gi_sssp_args, gi_sum_args,
+                   GIError, gi_batch_opts, gi_bfs_args, gi_cc_args, gi_probe_args, gi_schedule, gi_sssp_args, gi_sum_args,
                    gi_trace)
 
 _C = L.load()
@@ -284,3 +284,30 @@ def autotune(g: Graph, algo, src: int = 0, start=None, budget: int = 30, seed: i
 
 def schedule_dict(s: gi_schedule) -> dict:
     return {f: getattr(s, f) for f, _ in gi_schedule._fields_}
+
+
+def batch_opts(**kw) -> gi_batch_opts:
+    o = gi_batch_opts()
+    _C.gi_batch_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "selector" and isinstance(v, str):
+            v = L.DIRECTIONS[v]
+        setattr(o, k, v)
+    return o
+
+
+def batch_run(graphs, queries, outs=None, opts=None, stream=None):
+    """gi_batch_run.  queries: list of (graph index, source, "bfs"|"sssp").
+    Returns (list of int32 CUDA result tensors, per-query ns as numpy int64)."""
+    n_q = len(queries)
+    qg = np.array([q[0] for q in queries], np.int32)
+    qs = np.array([q[1] for q in queries], np.int32)
+    qa = np.array([ALGOS[q[2]] if isinstance(q[2], str) else q[2] for q in queries], np.int32)
+    if outs is None:
+        outs = [torch.empty(max(graphs[q[0]].n, 1), dtype=torch.int32, device="cuda") for q in queries]
+    handles = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+    optr = (ctypes.c_void_p * max(n_q, 1))(*[o.data_ptr() for o in outs])
+    ns = np.zeros(max(n_q, 1), np.int64)
+    check(_C.gi_batch_run(handles, len(graphs), _vp(qg), _vp(qs), _vp(qa), n_q, optr, _vp(ns),
+                          ctypes.byref(opts if opts is not None else batch_opts()), _stream(stream)))
+    return [o[:graphs[q[0]].n] for o, q in zip(outs, queries)], ns[:n_q]

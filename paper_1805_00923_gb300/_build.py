@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgraphit_gb.so")
-SOURCES = ["gi_core.cu", "gi_traverse.cu", "gi_algos.cu", "gi_static.cu", "gi_mlp.cu", "gi_tune.cu"]
+SOURCES = ["gi_core.cu", "gi_traverse.cu", "gi_algos.cu", "gi_static.cu", "gi_mlp.cu", "gi_tune.cu", "gi_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -47,6 +47,11 @@ class gi_trace(ctypes.Structure):
                 ("edges", _P(_i64)), ("features", _P(_f32))]
 
 
+class gi_batch_opts(ctypes.Structure):
+    _fields_ = [("cluster_size", _i32), ("clusters", _i32), ("selector", _i32), ("alpha", _f32), ("beta", _f32),
+                ("level_cap", _i64)]
+
+
 class gi_bfs_args(ctypes.Structure):
     _fields_ = [("depth", _vp), ("parent", _vp), ("level", _i32)]
 
@@ -100,11 +105,13 @@ SIGNATURES = {
     "gi_selector_profile": (ctypes.c_int, [_vp, _i32, _i32, _P(gi_schedule), _i32, _vp, _vp, _P(_i32), _vp]),
     "gi_autotune": (ctypes.c_int, [_vp, _i32, _i32, _P(gi_schedule), _i32, ctypes.c_uint64, _P(gi_schedule),
                                    _P(ctypes.c_double), _P(ctypes.c_double), _vp]),
+    "gi_batch_opts_default": (None, [_P(gi_batch_opts)]),
+    "gi_batch_run": (ctypes.c_int, [_P(_vp), _i32, _vp, _vp, _vp, _i32, _P(_vp), _vp, _P(gi_batch_opts), _vp]),
     "gi_stats_enable": (ctypes.c_int, [ctypes.c_int]),
     "gi_stats_reset": (ctypes.c_int, []),
     "gi_stats_read": (ctypes.c_int, [_i32, _P(_i64), _P(_i64), _P(ctypes.c_double)]),
 }
-KCLASS = {"pr_pull": 0, "prd_pull": 1, "min_pull": 2, "push": 3, "bfs_pull": 4, "other_pull": 5}
+KCLASS = {"pr_pull": 0, "prd_pull": 1, "min_pull": 2, "push": 3, "bfs_pull": 4, "other_pull": 5, "batch": 6}
 
 _lib = None
 

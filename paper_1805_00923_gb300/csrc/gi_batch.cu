@@ -1,0 +1,497 @@
+// Batched multi-query traversal in one persistent launch (not part of the
+// paper; the paper runs one query at a time on a multicore CPU).
+//
+// The launch is a grid of thread-block clusters.  Each cluster repeatedly
+// claims the next query from a global counter and runs it to completion:
+// level-synchronous BFS (SparsePush or early-exit DensePull per level, chosen
+// by Beamer's rule or the learned selector) or synchronous Bellman-Ford SSSP
+// (push).  The only waits are cluster barriers (barrier.cluster, hardware
+// co-scheduled CTAs) taken the same number of times by every CTA of a
+// cluster: all loop bounds come from values read after a barrier.  Clusters
+// never wait on each other, so a cluster that starts late simply finds the
+// work counter exhausted.  A level cap bounds every loop; exceeding it sets
+// an error flag that the host reports as GI_ERR_TIMEOUT.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "gi_features.cuh"
+#include "gi_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gi {
+
+// this translation unit's copy of the selector weights (see gi_selector_load)
+__device__ float d_sel_params[64 * 16 + 64 + 64 * 64 + 64 + 3 * 64 + 3];
+__device__ float d_sel_mean[16];
+__device__ float d_sel_istd[16];
+
+int batch_selector_upload(const float *params, const float *mean, const float *inv_std) {
+  GI_CUDA(cudaMemcpyToSymbol(d_sel_params, params, sizeof(d_sel_params)));
+  GI_CUDA(cudaMemcpyToSymbol(d_sel_mean, mean, sizeof(d_sel_mean)));
+  GI_CUDA(cudaMemcpyToSymbol(d_sel_istd, inv_std, sizeof(d_sel_istd)));
+  return GI_OK;
+}
+
+struct BatchGraph {
+  const int32_t *ptr, *idx, *wt, *iptr, *iidx;
+  int64_t n, m;
+  int32_t maxdeg;
+};
+
+struct BatchQuery {
+  int32_t graph, src, algo;
+  int32_t *out;
+};
+
+struct ClusterWs {  // per-cluster working memory (device pointers)
+  int32_t *q[2];    // frontier queues
+  int32_t *qd[2];   // SSSP: start-of-round distance of each queue entry
+  uint32_t *inq;    // SSSP: dedup bitmap of the next frontier
+  int64_t *cnt;     // [0..2] rotating counts, [3..5] rotating out-degree sums, [6] claimed query
+};
+
+constexpr int kBT = 256;  // threads per CTA
+
+__device__ __forceinline__ void csync(cg::cluster_group &cl) {
+  __threadfence();
+  cl.sync();
+}
+
+// learned / rule decision for BFS level, computed identically by every CTA
+__device__ bool batch_decide_pull(const BatchGraph &G, int64_t nf, int64_t mf, int64_t nu, int64_t mu, int32_t level,
+                                  int32_t was_pull, int64_t nf_prev, int mode, float alpha, float beta, float *sh) {
+  if (mode == 2) {
+    float *x = sh, *h1 = sh + 16, *h2 = h1 + 64, *y = h2 + 64;
+    const float *W1 = d_sel_params, *b1 = W1 + 64 * 16, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
+                *b3 = W3 + 3 * 64;
+    const int t = threadIdx.x;
+    if (t == 0) {
+      float raw[16];
+      level_features(raw, G.n, G.m, G.maxdeg, nf, mf, nu, mu, level, was_pull, nf_prev);
+      for (int i = 0; i < 16; ++i) x[i] = (raw[i] - d_sel_mean[i]) * d_sel_istd[i];
+    }
+    __syncthreads();
+    if (t < 64) {
+      float s = b1[t];
+      for (int i = 0; i < 16; ++i) s = fmaf(W1[t * 16 + i], x[i], s);
+      h1[t] = fmaxf(s, 0.0f);
+    }
+    __syncthreads();
+    if (t < 64) {
+      float s = b2[t];
+      for (int i = 0; i < 64; ++i) s = fmaf(W2[t * 64 + i], h1[i], s);
+      h2[t] = fmaxf(s, 0.0f);
+    }
+    __syncthreads();
+    if (t < 3) {
+      float s = b3[t];
+      for (int i = 0; i < 64; ++i) s = fmaf(W3[t * 64 + i], h2[i], s);
+      y[t] = s;
+    }
+    __syncthreads();
+    // the engine has push and pull; DensePush predictions fold into push
+    const float push = fminf(y[0], y[1]);
+    const bool pull = y[2] < push;
+    __syncthreads();
+    return pull;
+  }
+  if (!was_pull) return (double)mf > (double)mu / (double)alpha;
+  return !((double)nf < (double)G.n / (double)beta);
+}
+
+// BFS SparsePush over queue entries [0, nf) of this level: block / warp /
+// thread expansion by degree; newly reached vertices get depth L+1 and are
+// appended to the next queue with their out-degree added to the edge count.
+__device__ void batch_bfs_push(const BatchGraph &G, int32_t *depth, const int32_t *cur, int64_t nf, int32_t *next,
+                               int64_t *ncnt, int64_t *necnt, int32_t L, int rank, int csize) {
+  __shared__ int32_t s_owner, s_u, s_a, s_d;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t T = (int64_t)csize * kBT;
+  auto visit = [&](int32_t v) {
+    bool won = false;
+    if (*(volatile int32_t *)(depth + v) == -1) won = atomicCAS(depth + v, -1, L + 1) == -1;
+    const unsigned active = __activemask();
+    const unsigned ball = __ballot_sync(active, won);
+    if (ball) {
+      const int leader = __ffs(ball) - 1;
+      long long base = 0;
+      if (lane == leader) base = atomicAdd(reinterpret_cast<unsigned long long *>(ncnt), (unsigned long long)__popc(ball));
+      base = __shfl_sync(active, base, leader);
+      if (won) {
+        next[base + __popc(ball & ((1u << lane) - 1u))] = v;
+        atomicAdd(reinterpret_cast<unsigned long long *>(necnt), (unsigned long long)(G.ptr[v + 1] - G.ptr[v]));
+      }
+    }
+  };
+  for (int64_t base = (int64_t)rank * kBT; base < nf; base += T) {
+    const int64_t i = base + tid;
+    int32_t u = -1, a = 0, d = 0;
+    if (i < nf) {
+      u = cur[i];
+      a = G.ptr[u];
+      d = G.ptr[u + 1] - a;
+    }
+    while (true) {
+      if (tid == 0) s_owner = -1;
+      __syncthreads();
+      if (d >= 1024) s_owner = tid;
+      __syncthreads();
+      const int owner = s_owner;
+      if (owner < 0) break;
+      if (tid == owner) {
+        s_u = u;
+        s_a = a;
+        s_d = d;
+        d = 0;
+      }
+      __syncthreads();
+      for (int32_t k = tid; k < s_d; k += kBT) visit(G.idx[s_a + k]);
+      __syncthreads();
+    }
+    while (true) {
+      const unsigned bal = __ballot_sync(0xffffffffu, d >= 32);
+      if (!bal) break;
+      const int l = __ffs(bal) - 1;
+      const int32_t wa = __shfl_sync(0xffffffffu, a, l), wd = __shfl_sync(0xffffffffu, d, l);
+      if (lane == l) d = 0;
+      for (int32_t k = lane; k < wd; k += 32) visit(G.idx[wa + k]);
+    }
+    for (int32_t k = 0; k < d; ++k) visit(G.idx[a + k]);
+  }
+}
+
+// BFS DensePull with early exit: the frontier is {u : depth[u] == L}
+__device__ void batch_bfs_pull(const BatchGraph &G, int32_t *depth, int32_t *next, int64_t *ncnt, int64_t *necnt,
+                               int32_t L, int rank, int csize) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (G.n + 31) >> 5;
+  const int64_t wstride = (int64_t)csize * (kBT / 32);
+  for (int64_t w = (int64_t)rank * (kBT / 32) + (threadIdx.x >> 5); w < nw; w += wstride) {
+    const int64_t v = w * 32 + lane;
+    const bool active = v < G.n && depth[v] == -1;
+    int32_t a = 0, b = 0;
+    if (active) {
+      a = G.iptr[v];
+      b = G.iptr[v + 1];
+    }
+    bool found = false;
+    const bool big = active && (b - a) >= 32;
+    if (active && !big) {
+      for (int32_t e = a; e < b && !found; e += 4) {
+        int32_t u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) u[j] = e + j < b ? G.iidx[e + j] : -1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) found |= u[j] >= 0 && depth[u[j]] == L;
+      }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, big);
+    while (bal) {
+      const int l = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int32_t la = __shfl_sync(0xffffffffu, a, l), lb = __shfl_sync(0xffffffffu, b, l);
+      bool hit = false;
+      for (int32_t base = la; base < lb && !hit; base += 32) {
+        const int32_t e = base + lane;
+        hit = __ballot_sync(0xffffffffu, e < lb && depth[G.iidx[e]] == L) != 0;
+      }
+      if (lane == l) found = hit;
+    }
+    if (found) depth[v] = L + 1;
+    const unsigned word = __ballot_sync(0xffffffffu, found);
+    if (word) {
+      long long base = 0;
+      if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(ncnt), (unsigned long long)__popc(word));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (found) {
+        next[base + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
+        atomicAdd(reinterpret_cast<unsigned long long *>(necnt), (unsigned long long)(G.ptr[v + 1] - G.ptr[v]));
+      }
+    }
+  }
+}
+
+// SSSP push relax of this round's queue (start-of-round distances in curd)
+__device__ void batch_sssp_push(const BatchGraph &G, int32_t *dist, const int32_t *cur, const int32_t *curd,
+                                int64_t nf, int32_t *next, int64_t *ncnt, uint32_t *inq, int rank, int csize) {
+  __shared__ int32_t s_owner, s_a, s_d, s_du;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t T = (int64_t)csize * kBT;
+  auto relax = [&](int32_t du, int32_t e) {
+    const int32_t v = G.idx[e];
+    const long long nd = (long long)du + G.wt[e];
+    bool fresh = false;
+    if (nd < *(volatile int32_t *)(dist + v)) {
+      const int32_t old = atomicMin(dist + v, (int32_t)nd);
+      if (nd < old) {
+        const uint32_t mask = 1u << (v & 31);
+        fresh = (atomicOr(inq + (v >> 5), mask) & mask) == 0;
+      }
+    }
+    const unsigned active = __activemask();
+    const unsigned ball = __ballot_sync(active, fresh);
+    if (ball) {
+      const int leader = __ffs(ball) - 1;
+      long long base = 0;
+      if (lane == leader) base = atomicAdd(reinterpret_cast<unsigned long long *>(ncnt), (unsigned long long)__popc(ball));
+      base = __shfl_sync(active, base, leader);
+      if (fresh) next[base + __popc(ball & ((1u << lane) - 1u))] = v;
+    }
+  };
+  for (int64_t base = (int64_t)rank * kBT; base < nf; base += T) {
+    const int64_t i = base + tid;
+    int32_t a = 0, d = 0, du = 0;
+    if (i < nf) {
+      const int32_t u = cur[i];
+      du = curd[i];
+      a = G.ptr[u];
+      d = G.ptr[u + 1] - a;
+    }
+    while (true) {
+      if (tid == 0) s_owner = -1;
+      __syncthreads();
+      if (d >= 1024) s_owner = tid;
+      __syncthreads();
+      const int owner = s_owner;
+      if (owner < 0) break;
+      if (tid == owner) {
+        s_a = a;
+        s_d = d;
+        s_du = du;
+        d = 0;
+      }
+      __syncthreads();
+      for (int32_t k = tid; k < s_d; k += kBT) relax(s_du, s_a + k);
+      __syncthreads();
+    }
+    while (true) {
+      const unsigned bal = __ballot_sync(0xffffffffu, d >= 32);
+      if (!bal) break;
+      const int l = __ffs(bal) - 1;
+      const int32_t wa = __shfl_sync(0xffffffffu, a, l), wd = __shfl_sync(0xffffffffu, d, l),
+                    wdu = __shfl_sync(0xffffffffu, du, l);
+      if (lane == l) d = 0;
+      for (int32_t k = lane; k < wd; k += 32) relax(wdu, wa + k);
+    }
+    for (int32_t k = 0; k < d; ++k) relax(du, a + k);
+  }
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ graphs,
+                                               const BatchQuery *__restrict__ queries, int32_t n_q,
+                                               int32_t *work, ClusterWs *ws, int64_t *q_ns, int mode, float alpha,
+                                               float beta, int64_t level_cap, int32_t *err) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
+  const int cid = blockIdx.x / csize;
+  const int64_t T = (int64_t)csize * kBT;
+  const int64_t gtid = (int64_t)rank * kBT + threadIdx.x;
+  ClusterWs W = ws[cid];
+  __shared__ float sh[16 + 64 + 64 + 4];
+  while (true) {
+    if (rank == 0 && threadIdx.x == 0) W.cnt[6] = atomicAdd(work, 1);
+    csync(cl);
+    const int32_t qi = (int32_t)*(volatile int64_t *)(W.cnt + 6);
+    csync(cl);  // everyone has read the claim before it can be overwritten
+    if (qi >= n_q) break;
+    const BatchQuery Q = queries[qi];
+    const BatchGraph G = graphs[Q.graph];
+    unsigned long long t0 = 0;
+    if (gtid == 0) t0 = global_ns();
+    const bool bfs = Q.algo == GI_ALGO_BFS;
+    for (int64_t v = gtid; v < G.n; v += T) Q.out[v] = bfs ? -1 : INT32_MAX;
+    if (!bfs)
+      for (int64_t w = gtid; w < (G.n + 31) / 32; w += T) W.inq[w] = 0u;
+    if (gtid == 0) {
+      for (int k = 0; k < 6; ++k) W.cnt[k] = 0;
+      W.cnt[0] = 1;
+      W.cnt[3] = G.ptr[Q.src + 1] - G.ptr[Q.src];
+      W.q[0][0] = Q.src;
+      W.qd[0][0] = 0;
+    }
+    csync(cl);
+    if (gtid == 0) Q.out[Q.src] = 0;
+    csync(cl);
+    int64_t nu = G.n, mu = G.m, nf_prev = 0;
+    int32_t was_pull = 0;
+    for (int32_t L = 0;; ++L) {
+      const int64_t nf = *(volatile int64_t *)(W.cnt + (L % 3));
+      const int64_t mf = *(volatile int64_t *)(W.cnt + 3 + (L % 3));
+      if (nf == 0) break;
+      if (L >= level_cap) {  // uniform: every CTA sees the same L
+        if (gtid == 0) atomicExch(err, 1);
+        break;
+      }
+      if (gtid == 0) {
+        W.cnt[(L + 2) % 3] = 0;
+        W.cnt[3 + (L + 2) % 3] = 0;
+      }
+      int32_t *cur = W.q[L & 1], *next = W.q[(L + 1) & 1];
+      int64_t *ncnt = W.cnt + (L + 1) % 3, *necnt = W.cnt + 3 + (L + 1) % 3;
+      if (bfs) {
+        nu -= nf;
+        mu -= mf;
+        const bool pull = (mode == 0) ? false
+                                      : batch_decide_pull(G, nf, mf, nu, mu, L, was_pull, nf_prev, mode, alpha, beta,
+                                                          sh);
+        if (pull) batch_bfs_pull(G, Q.out, next, ncnt, necnt, L, rank, csize);
+        else batch_bfs_push(G, Q.out, cur, nf, next, ncnt, necnt, L, rank, csize);
+        was_pull = pull ? 1 : 0;
+        nf_prev = nf;
+        csync(cl);
+      } else {
+        batch_sssp_push(G, Q.out, cur, W.qd[L & 1], nf, next, ncnt, W.inq, rank, csize);
+        csync(cl);
+        const int64_t nn = *(volatile int64_t *)ncnt;
+        int32_t *nextd = W.qd[(L + 1) & 1];
+        for (int64_t i = gtid; i < nn; i += T) {
+          const int32_t v = next[i];
+          nextd[i] = Q.out[v];
+          atomicAnd(W.inq + (v >> 5), ~(1u << (v & 31)));
+        }
+        csync(cl);
+      }
+    }
+    if (gtid == 0 && q_ns) q_ns[qi] = (int64_t)(global_ns() - t0);
+    csync(cl);
+  }
+}
+
+}  // namespace gi
+
+using namespace gi;
+
+extern "C" int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int32_t *q_graph, const int32_t *q_src,
+                            const int32_t *q_algo, int32_t n_q, int32_t *const *out_dev, int64_t *q_ns,
+                            const gi_batch_opts *opts, void *stream) {
+  GI_ARG(graphs != nullptr && n_graphs > 0, "no graphs");
+  GI_ARG(n_q >= 0 && (n_q == 0 || (q_graph && q_src && q_algo && out_dev)), "bad query arrays");
+  gi_batch_opts o;
+  gi_batch_opts_default(&o);
+  if (opts) o = *opts;
+  GI_ARG(o.cluster_size == 1 || o.cluster_size == 2 || o.cluster_size == 4 || o.cluster_size == 8,
+         "cluster_size must be 1, 2, 4 or 8");
+  GI_ARG(o.selector == GI_DIR_SPARSE_PUSH || o.selector == GI_DIR_HYBRID_PULL || o.selector == GI_DIR_LEARNED,
+         "selector must be GI_DIR_SPARSE_PUSH, GI_DIR_HYBRID_PULL or GI_DIR_LEARNED");
+  std::vector<BatchGraph> hg(n_graphs);
+  int64_t nmax = 1;
+  for (int i = 0; i < n_graphs; ++i) {
+    const gi_graph *g = graphs[i];
+    GI_ARG(g != nullptr, "NULL graph");
+    hg[i] = BatchGraph{g->out.ptr, g->out.idx, g->out.wt, g->in.ptr, g->in.idx, g->n, g->m, g->max_deg};
+    nmax = g->n > nmax ? g->n : nmax;
+  }
+  std::vector<BatchQuery> hq(n_q);
+  for (int i = 0; i < n_q; ++i) {
+    GI_ARG(q_graph[i] >= 0 && q_graph[i] < n_graphs, "query graph index out of range");
+    const gi_graph *g = graphs[q_graph[i]];
+    GI_ARG(q_src[i] >= 0 && q_src[i] < g->n, "query source out of range");
+    GI_ARG(q_algo[i] == GI_ALGO_BFS || q_algo[i] == GI_ALGO_SSSP, "query algorithm must be BFS or SSSP");
+    if (q_algo[i] == GI_ALGO_SSSP) GI_ARG(g->out.wt != nullptr, "SSSP query on a graph without weights");
+    if (q_algo[i] == GI_ALGO_BFS && o.selector != GI_DIR_SPARSE_PUSH)
+      GI_ARG(g->has_csc, "pull levels need the in-edges (symmetric graph or gi_load_csc)");
+    GI_ARG(out_dev[i] != nullptr, "NULL output");
+    hq[i] = BatchQuery{q_graph[i], q_src[i], q_algo[i], out_dev[i]};
+  }
+  if (n_q == 0) return GI_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  GI_CUDA(cudaGetDevice(&dev));
+  GI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int clusters = o.clusters > 0 ? o.clusters : sms / o.cluster_size;
+  if (clusters > n_q) clusters = n_q;
+  if (clusters < 1) clusters = 1;
+  const int64_t words = (nmax + 31) / 32;
+  // device copies and per-cluster working memory
+  BatchGraph *dg = nullptr;
+  BatchQuery *dq = nullptr;
+  ClusterWs *dws = nullptr;
+  int32_t *work = nullptr, *slab = nullptr;
+  int64_t *cnts = nullptr, *dns = nullptr;
+  std::vector<ClusterWs> hws(clusters);
+  const int64_t per = 4 * nmax + words;  // 2 queues + 2 distance queues + bitmap, in int32 words
+  int st = dev_alloc_n(&dg, n_graphs, s);
+  if (st == GI_OK) st = dev_alloc_n(&dq, n_q, s);
+  if (st == GI_OK) st = dev_alloc_n(&dws, clusters, s);
+  if (st == GI_OK) st = dev_alloc_n(&work, 2, s);
+  if (st == GI_OK) st = dev_alloc_n(&slab, per * clusters, s);
+  if (st == GI_OK) st = dev_alloc_n(&cnts, 8 * clusters, s);
+  if (st == GI_OK && q_ns) st = dev_alloc_n(&dns, n_q, s);
+  if (st == GI_OK) {
+    for (int c = 0; c < clusters; ++c) {
+      int32_t *b = slab + per * c;
+      hws[c].q[0] = b;
+      hws[c].q[1] = b + nmax;
+      hws[c].qd[0] = b + 2 * nmax;
+      hws[c].qd[1] = b + 3 * nmax;
+      hws[c].inq = reinterpret_cast<uint32_t *>(b + 4 * nmax);
+      hws[c].cnt = cnts + 8 * c;
+    }
+    if (cudaMemcpyAsync(dg, hg.data(), sizeof(BatchGraph) * n_graphs, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dq, hq.data(), sizeof(BatchQuery) * n_q, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dws, hws.data(), sizeof(ClusterWs) * clusters, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(work, 0, 2 * sizeof(int32_t), s) != cudaSuccess)
+      st = cuda_fail(cudaGetLastError(), "batch setup", __FILE__, __LINE__);
+  }
+  if (st == GI_OK) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * o.cluster_size));
+    cfg.blockDim = dim3(kBT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)o.cluster_size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int mode = o.selector == GI_DIR_SPARSE_PUSH ? 0 : (o.selector == GI_DIR_LEARNED && selector_loaded() ? 2 : 1);
+    const int64_t cap = o.level_cap > 0 ? o.level_cap : nmax + 2;
+    const int tok = timing_begin(kClassBatch, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch, (const BatchGraph *)dg, (const BatchQuery *)dq, n_q, work, dws,
+                                       dns, mode, o.alpha, o.beta, cap, work + 1);
+    timing_end(tok, s);
+    note_launch(1);
+    if (e != cudaSuccess) st = cuda_fail(e, "batch launch", __FILE__, __LINE__);
+  }
+  int32_t err = 0;
+  if (st == GI_OK && cudaMemcpyAsync(&err, work + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "batch status", __FILE__, __LINE__);
+  if (st == GI_OK && q_ns &&
+      cudaMemcpyAsync(q_ns, dns, sizeof(int64_t) * n_q, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "batch times", __FILE__, __LINE__);
+  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "batch", __FILE__, __LINE__);
+  dev_free(dg, s);
+  dev_free(dq, s);
+  dev_free(dws, s);
+  dev_free(work, s);
+  dev_free(slab, s);
+  dev_free(cnts, s);
+  dev_free(dns, s);
+  if (st == GI_OK && err) {
+    set_error("a query exceeded the level cap of the batched engine");
+    return GI_ERR_TIMEOUT;
+  }
+  return st;
+}
+
+extern "C" void gi_batch_opts_default(gi_batch_opts *o) {
+  if (!o) return;
+  o->cluster_size = 4;
+  o->clusters = 0;
+  o->selector = GI_DIR_HYBRID_PULL;
+  o->alpha = 14.0f;
+  o->beta = 24.0f;
+  o->level_cap = 0;
+}

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <vector>
 
+#include "gi_features.cuh"
 #include "gi_internal.cuh"
 
 namespace gi {
@@ -959,28 +960,6 @@ static bool g_sel_loaded = false;
 
 bool selector_loaded() { return g_sel_loaded; }
 
-// features of one level (same definition as the selector's training data)
-__device__ void level_features(float *x, int64_t n, int64_t m, int32_t maxdeg, int64_t nf, int64_t mf, int64_t nu,
-                               int64_t mu, int32_t level, int32_t was_pull, int64_t nf_prev) {
-  float V = (float)(n > 0 ? n : 1), E = (float)(m > 0 ? m : 1);
-  x[0] = log2f(1.0f + (float)nf);
-  x[1] = log2f(1.0f + (float)mf);
-  x[2] = log2f(1.0f + (float)nu);
-  x[3] = log2f(1.0f + (float)mu);
-  x[4] = log2f(1.0f + (float)n);
-  x[5] = log2f(1.0f + (float)m);
-  x[6] = (float)nf / V;
-  x[7] = (float)mf / E;
-  x[8] = (float)nu / V;
-  x[9] = (float)mu / E;
-  x[10] = log2f(1.0f + (float)((double)mf / (double)(nf > 0 ? nf : 1)));
-  x[11] = log2f(1.0f + (float)maxdeg);
-  x[12] = log2f(1.0f + (float)((double)m / (double)V));
-  x[13] = log2f(1.0f + (float)level);
-  x[14] = was_pull ? 1.0f : 0.0f;
-  x[15] = log2f(1.0f + (float)nf_prev);
-}
-
 // MLP forward by one block (>= 64 threads); returns argmin of predicted log-time
 __device__ int32_t selector_forward(const float *x_raw, float *sh /* >= 16+64+64+3 floats */) {
   float *x = sh, *h1 = sh + kDIn, *h2 = h1 + kH, *y = h2 + kH;
@@ -1133,6 +1112,7 @@ extern "C" int gi_selector_load(const float *params, int32_t count, const float 
   GI_CUDA(cudaMemcpyToSymbol(gi::d_sel_params, params, sizeof(float) * gi::kNParam));
   GI_CUDA(cudaMemcpyToSymbol(gi::d_sel_mean, mean, sizeof(float) * gi::kDIn));
   GI_CUDA(cudaMemcpyToSymbol(gi::d_sel_istd, inv_std, sizeof(float) * gi::kDIn));
+  GI_TRY(gi::batch_selector_upload(params, mean, inv_std));
   gi::g_sel_loaded = true;
   return GI_OK;
 }

@@ -23,7 +23,7 @@ int launch_status(int n);
 // CUDA-event timing of selected kernel classes (gi_stats_*): returns a token
 // for timing_end, or -1 when timing is off.
 enum KernelClass { kClassPrPull = 0, kClassPrdPull = 1, kClassMinPull = 2, kClassPush = 3, kClassBfsPull = 4,
-                   kClassOtherPull = 5, kNumClasses = 6 };
+                   kClassOtherPull = 5, kClassBatch = 6, kNumClasses = 7 };
 int timing_begin(int kclass, cudaStream_t s);
 void timing_end(int token, cudaStream_t s);
 
@@ -187,8 +187,10 @@ int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t
 int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s);
 int ctrl_fetch(gi_graph *g, cudaStream_t s);  // copies ctrl to pinned host + syncs
 
-// selector weights (device constant memory) and state
+// selector weights (device memory) and state; the batched engine keeps its
+// own copy of the weights, uploaded by gi_selector_load
 bool selector_loaded();
+int batch_selector_upload(const float *params, const float *mean, const float *inv_std);
 
 // traversal entry (gi_traverse.cu)
 int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const gi_schedule &sc, int32_t kernel_id,

@@ -1,0 +1,85 @@
+"""Batched persistent engine: every query's result equals the oracle's
+(bit-exact BFS depths and SSSP distances) for all cluster sizes and
+direction selectors; the level cap ends a run cleanly with GI_ERR_TIMEOUT."""
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from _graphs import adversarial, grid, rmat
+
+pytestmark = pytest.mark.gpu
+INT_MAX = np.iinfo(np.int32).max
+
+
+def _graphs():
+    return [rmat(12, weights=True), rmat(14, weights=True), grid(64, weights=True), adversarial("path", True),
+            adversarial("components", True), adversarial("hub_tail", True)]
+
+
+def _queries(hgs, n_q, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_q):
+        gi_ = int(rng.integers(0, len(hgs)))
+        src = int(rng.integers(0, hgs[gi_].n))
+        out.append((gi_, src, "bfs" if i % 2 == 0 else "sssp"))
+    return out
+
+
+def _check(hgs, queries, results):
+    for (gidx, src, algo), got in zip(queries, results):
+        hg = hgs[gidx]
+        got = got.cpu().numpy()
+        if algo == "bfs":
+            want, _, _ = oracle.bfs(hg, src)
+        else:
+            want, _ = oracle.sssp(hg, src)
+        assert np.array_equal(got, want), (gidx, src, algo)
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+@pytest.mark.parametrize("selector", ["sparse_push", "hybrid_pull"])
+def test_batch_matches_oracle(gi, cluster, selector):
+    hgs = _graphs()
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    qs = _queries(hgs, 48, seed=cluster)
+    res, ns = gi.batch_run(gs, qs, opts=gi.batch_opts(cluster_size=cluster, selector=selector))
+    _check(hgs, qs, res)
+    assert (ns > 0).all()
+
+
+def test_batch_fewer_clusters_than_queries(gi):
+    hgs = _graphs()
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    qs = _queries(hgs, 40, seed=11)
+    res, _ = gi.batch_run(gs, qs, opts=gi.batch_opts(cluster_size=2, clusters=3))
+    _check(hgs, qs, res)
+
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1805_00923_gb300",
+                       "selector_weights.npz")
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained selector weights committed")
+def test_batch_learned_selector(gi):
+    from paper_1805_00923_gb300 import selector as sel
+    sel.install(WEIGHTS)
+    hgs = _graphs()
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    qs = _queries(hgs, 32, seed=5)
+    res, _ = gi.batch_run(gs, qs, opts=gi.batch_opts(cluster_size=4, selector="learned"))
+    _check(hgs, qs, res)
+
+
+def test_batch_level_cap_returns_timeout(gi):
+    hg = adversarial("path", True)
+    g = gi.Graph.from_host(hg)
+    with pytest.raises(gi.GIError) as e:
+        gi.batch_run([g], [(0, 0, "bfs")], opts=gi.batch_opts(level_cap=10))
+    assert e.value.code == -5
+    # the context is still usable
+    res, _ = gi.batch_run([g], [(0, 0, "bfs"), (0, 5, "sssp")])
+    _check([hg], [(0, 0, "bfs"), (0, 5, "sssp")], res)
