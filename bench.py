@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--tune-budget", type=int, default=12, help="autotuner trials per algorithm (untimed)")
+    p.add_argument("--only", choices=["pagerank", "pagerank_delta", "cc", "bfs", "sssp"], default=None,
+                   help="profiling case: run just this algorithm --steps times on the workload graph")
     return p.parse_args()
 
 
@@ -56,9 +59,10 @@ def dist_setup():
 def workload_config(hg, scale):
     return {"workload": f"rmat{scale}_pr{PR_ITERS}_prd{PRD_ITERS}_cc", "graph": "R-MAT symmetrized",
             "scale": scale, "edge_factor": 16, "abc": [0.57, 0.19, 0.19], "seed": 1, "n": hg.n, "m": hg.m,
-            "pagerank": {"iters": PR_ITERS, "damping": DAMPING, "schedule": "DensePull"},
-            "pagerank_delta": {"iters": PRD_ITERS, "eps": PRD_EPS, "schedule": "DensePull-SparsePush (Ligra rule)"},
-            "cc": {"schedule": "DensePull-SparsePush (Ligra rule)"},
+            "pagerank": {"iters": PR_ITERS, "damping": DAMPING, "schedule": "DensePull, autotuned"},
+            "pagerank_delta": {"iters": PRD_ITERS, "eps": PRD_EPS,
+                               "schedule": "DensePull-SparsePush (Ligra rule), autotuned"},
+            "cc": {"schedule": "DensePull-SparsePush (Ligra rule), autotuned"},
             "l2": "inputs larger than L2 (CSR %.0f MB vs 126 MB L2); no flush" % ((4 * (hg.n + 1) + 4 * hg.m) / 1e6)}
 
 
@@ -208,8 +212,30 @@ def run_gi(args):
     n, m = hg.n, hg.m
     stream = torch.cuda.current_stream()
     g = gi.Graph.from_host(hg)
-    pr_s = gi.schedule("dense_pull")
-    hyb = gi.schedule("hybrid_pull")
+    # the autotuner picks tile shape / thresholds / segment count (untimed setup)
+    pr_s, pr_tuned_ms, pr_start_ms = gi.autotune(g, "pagerank", start=gi.schedule("dense_pull"),
+                                                 budget=args.tune_budget, seed=1)
+    prd_s, prd_tuned_ms, prd_start_ms = gi.autotune(g, "pagerank_delta", start=gi.schedule("hybrid_pull"),
+                                                    budget=args.tune_budget, seed=2)
+    cc_s, cc_tuned_ms, cc_start_ms = gi.autotune(g, "cc", start=gi.schedule("hybrid_pull"), budget=args.tune_budget,
+                                                 seed=3)
+    tuned = {"pagerank": dict(gi.schedule_dict(pr_s), tuned_ms=pr_tuned_ms, default_ms=pr_start_ms),
+             "pagerank_delta": dict(gi.schedule_dict(prd_s), tuned_ms=prd_tuned_ms, default_ms=prd_start_ms),
+             "cc": dict(gi.schedule_dict(cc_s), tuned_ms=cc_tuned_ms, default_ms=cc_start_ms)}
+    # the three PageRank directions of the workload, one timed run each (untimed setup)
+    compare = {}
+    for name, sc in [("dense_pull", gi.schedule("dense_pull")),
+                     ("segmented_pull_4", gi.schedule("dense_pull", num_segments=4)),
+                     ("dense_push", gi.schedule("dense_push"))]:
+        gi.pagerank(g, DAMPING, PR_ITERS, sched=sc)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gi.pagerank(g, DAMPING, PR_ITERS, sched=sc)
+        e1.record()
+        torch.cuda.synchronize()
+        compare[name] = PR_ITERS * m / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    g.build_segments(1)
+    hyb = prd_s
     rank_buf = torch.empty(n, dtype=torch.float32, device="cuda")
     prd_buf = torch.empty(n, dtype=torch.float32, device="cuda")
     lab_buf = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -228,7 +254,7 @@ def run_gi(args):
         gi.pagerank_delta(graph, DAMPING, PRD_EPS, PRD_ITERS, sched=hyb, trace=tr_p, out=prd_buf)
         if ev:
             ev[2].record()
-        gi.cc(graph, sched=hyb, trace=tr_c, out=lab_buf)
+        gi.cc(graph, sched=cc_s, trace=tr_c, out=lab_buf)
         if ev:
             ev[3].record()
         return PR_ITERS * m, traversed(tr_p), traversed(tr_c)
@@ -312,7 +338,8 @@ def run_gi(args):
                          "avg_launch_ms": avg_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": sum(e2e_ms) / max(len(e2e_ms), 1)},
-            "gpu_launches": launches, "clocks": clocks}
+            "gpu_launches": launches, "clocks": clocks,
+            "autotuned": tuned, "pagerank_direction_gteps": compare}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, iters, t = oracle_sample(hg, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
@@ -326,8 +353,34 @@ def run_gi(args):
     return 0
 
 
+def run_only(args):
+    """A small fixed case for profilers: one algorithm, default schedule, --steps runs."""
+    import torch
+    import graphgen as gg
+    import paper_1805_00923_gb300 as gi
+    torch.cuda.set_device(0)
+    hg = gg.rmat_graph(args.scale, seed=1, weights=(1, 1000) if args.only == "sssp" else None)
+    g = gi.Graph.from_host(hg)
+    for _ in range(args.steps):
+        if args.only == "pagerank":
+            gi.pagerank(g, DAMPING, PR_ITERS, sched=gi.schedule("dense_pull"))
+        elif args.only == "pagerank_delta":
+            gi.pagerank_delta(g, DAMPING, PRD_EPS, PRD_ITERS)
+        elif args.only == "cc":
+            gi.cc(g)
+        elif args.only == "bfs":
+            gi.bfs(g, 0)
+        else:
+            gi.sssp(g, 0)
+    torch.cuda.synchronize()
+    print(json.dumps({"only": args.only, "scale": args.scale, "n": hg.n, "m": hg.m, "runs": args.steps}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.only:
+        return run_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gi(args)

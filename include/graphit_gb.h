@@ -360,6 +360,7 @@ typedef struct gi_batch_opts {
                         /* GI_DIR_HYBRID_PULL (Beamer rule) or GI_DIR_LEARNED (the MLP)    */
   float alpha, beta;    /* Beamer constants                                                */
   int64_t level_cap;    /* give up after this many levels (0 = n+2): GI_ERR_TIMEOUT       */
+  int32_t *levels;      /* host, n_q entries or NULL: levels (BFS) / rounds (SSSP) run     */
 } gi_batch_opts;
 
 void gi_batch_opts_default(gi_batch_opts *o);

@@ -288,8 +288,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ graphs,
                                                const BatchQuery *__restrict__ queries, int32_t n_q,
-                                               int32_t *work, ClusterWs *ws, int64_t *q_ns, int mode, float alpha,
-                                               float beta, int64_t level_cap, int32_t *err) {
+                                               int32_t *work, ClusterWs *ws, int64_t *q_ns, int32_t *q_levels,
+                                               int mode, float alpha, float beta, int64_t level_cap, int32_t *err) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
   const int cid = blockIdx.x / csize;
@@ -322,10 +322,11 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
     if (gtid == 0) Q.out[Q.src] = 0;
     csync(cl);
     int64_t nu = G.n, mu = G.m, nf_prev = 0;
-    int32_t was_pull = 0;
+    int32_t was_pull = 0, levels = 0;
     for (int32_t L = 0;; ++L) {
       const int64_t nf = *(volatile int64_t *)(W.cnt + (L % 3));
       const int64_t mf = *(volatile int64_t *)(W.cnt + 3 + (L % 3));
+      levels = L;
       if (nf == 0) break;
       if (L >= level_cap) {  // uniform: every CTA sees the same L
         if (gtid == 0) atomicExch(err, 1);
@@ -362,6 +363,7 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
       }
     }
     if (gtid == 0 && q_ns) q_ns[qi] = (int64_t)(global_ns() - t0);
+    if (gtid == 0 && q_levels) q_levels[qi] = levels;
     csync(cl);
   }
 }
@@ -415,7 +417,7 @@ extern "C" int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int
   BatchGraph *dg = nullptr;
   BatchQuery *dq = nullptr;
   ClusterWs *dws = nullptr;
-  int32_t *work = nullptr, *slab = nullptr;
+  int32_t *work = nullptr, *slab = nullptr, *dlev = nullptr;
   int64_t *cnts = nullptr, *dns = nullptr;
   std::vector<ClusterWs> hws(clusters);
   const int64_t per = 4 * nmax + words;  // 2 queues + 2 distance queues + bitmap, in int32 words
@@ -426,6 +428,7 @@ extern "C" int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int
   if (st == GI_OK) st = dev_alloc_n(&slab, per * clusters, s);
   if (st == GI_OK) st = dev_alloc_n(&cnts, 8 * clusters, s);
   if (st == GI_OK && q_ns) st = dev_alloc_n(&dns, n_q, s);
+  if (st == GI_OK && o.levels) st = dev_alloc_n(&dlev, n_q, s);
   if (st == GI_OK) {
     for (int c = 0; c < clusters; ++c) {
       int32_t *b = slab + per * c;
@@ -459,7 +462,7 @@ extern "C" int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int
     const int64_t cap = o.level_cap > 0 ? o.level_cap : nmax + 2;
     const int tok = timing_begin(kClassBatch, s);
     cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch, (const BatchGraph *)dg, (const BatchQuery *)dq, n_q, work, dws,
-                                       dns, mode, o.alpha, o.beta, cap, work + 1);
+                                       dns, dlev, mode, o.alpha, o.beta, cap, work + 1);
     timing_end(tok, s);
     note_launch(1);
     if (e != cudaSuccess) st = cuda_fail(e, "batch launch", __FILE__, __LINE__);
@@ -470,8 +473,12 @@ extern "C" int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int
   if (st == GI_OK && q_ns &&
       cudaMemcpyAsync(q_ns, dns, sizeof(int64_t) * n_q, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "batch times", __FILE__, __LINE__);
+  if (st == GI_OK && o.levels &&
+      cudaMemcpyAsync(o.levels, dlev, sizeof(int32_t) * n_q, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "batch levels", __FILE__, __LINE__);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "batch", __FILE__, __LINE__);
+  dev_free(dlev, s);
   dev_free(dg, s);
   dev_free(dq, s);
   dev_free(dws, s);
@@ -494,4 +501,5 @@ extern "C" void gi_batch_opts_default(gi_batch_opts *o) {
   o->alpha = 14.0f;
   o->beta = 24.0f;
   o->level_cap = 0;
+  o->levels = nullptr;
 }

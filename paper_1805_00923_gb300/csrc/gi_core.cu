@@ -361,7 +361,7 @@ extern "C" int gi_version(void) { return 100; }
 
 static void graph_release(gi_graph *g, cudaStream_t s) {
   if (!g) return;
-  free_tiles(&g->in_tiles, s);
+  free_tile_cache(g, s);
   if (g->segs.seg) {
     for (int i = 0; i < g->segs.num; ++i) {
       dev_free(g->segs.seg[i].ptr, s);
@@ -441,7 +441,7 @@ extern "C" int gi_load_csr(const int32_t *offsets, const int32_t *indices, const
     if (g->symmetric) {
       g->in = g->out;
       g->has_csc = true;
-      if ((st = build_tiles(g, g->in, 2048, &g->in_tiles, s)) != GI_OK) break;
+      if ((st = use_tiles(g, 2048, s)) != GI_OK) break;
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) {
       st = cuda_fail(cudaGetLastError(), "load sync", __FILE__, __LINE__);
@@ -465,7 +465,7 @@ extern "C" int gi_load_csc(gi_graph *g, const int32_t *in_offsets, const int32_t
   cudaStream_t s = (cudaStream_t)stream;
   if (g->symmetric) return GI_OK;  // the CSR already is the in-edge view
   if (g->has_csc) {
-    free_tiles(&g->in_tiles, s);
+    free_tile_cache(g, s);
     dev_free(g->in.ptr, s);
     dev_free(g->in.idx, s);
     dev_free(g->in.wt, s);
@@ -476,8 +476,8 @@ extern "C" int gi_load_csc(gi_graph *g, const int32_t *in_offsets, const int32_t
   GI_TRY(copy_in(&g->in.idx, in_indices, g->m, flags, s));
   if (in_weights) GI_TRY(copy_in(&g->in.wt, in_weights, g->m, flags, s));
   if (flags & GI_VALIDATE) GI_TRY(validate_csr_dev(g, g->in, s));
-  GI_TRY(build_tiles(g, g->in, 2048, &g->in_tiles, s));
   g->has_csc = true;
+  GI_TRY(use_tiles(g, 2048, s));
   GI_CUDA(cudaStreamSynchronize(s));
   return GI_OK;
 }
@@ -610,6 +610,23 @@ int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cuda
   dev_free(soff, s);
   dev_free(tile_row, s);
   return GI_OK;
+}
+
+int use_tiles(gi_graph *g, int32_t tile_edges, cudaStream_t s) {
+  int k = 0;
+  while (k < 6 && (256 << k) != tile_edges) ++k;
+  if (k == 6) {
+    set_error("unsupported tile size %d", tile_edges);
+    return GI_ERR_UNSUPPORTED;
+  }
+  if (g->tile_cache[k].tile_edges != tile_edges) GI_TRY(build_tiles(g, g->in, tile_edges, &g->tile_cache[k], s));
+  g->in_tiles = g->tile_cache[k];
+  return GI_OK;
+}
+
+void free_tile_cache(gi_graph *g, cudaStream_t s) {
+  for (auto &t : g->tile_cache) free_tiles(&t, s);
+  g->in_tiles = TileSet();
 }
 
 void free_tiles(TileSet *ts, cudaStream_t s) {

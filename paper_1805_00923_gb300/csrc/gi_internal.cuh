@@ -122,7 +122,8 @@ struct gi_graph {
   gi::Csr in;             // CSC (in-edges); aliases `out` when symmetric
   int32_t *out_deg = nullptr;
   float *inv_out_deg = nullptr;  // 1/outdeg (0 for degree 0)
-  gi::TileSet in_tiles;          // tiles over the in-edges for pull
+  gi::TileSet in_tiles;          // active tile set over the in-edges (a view into tile_cache)
+  gi::TileSet tile_cache[6];     // owned tile sets for tile_edges 256, 512, ..., 8192 (built on first use)
   gi::Segments segs;
   int64_t *ctrl = nullptr;       // device control block (kCtrlWords)
   int32_t *heavy_q = nullptr;    // sources deferred to the all-block expansion (n entries + count)
@@ -163,6 +164,8 @@ int scan_exclusive(gi_graph *g, const int32_t *in, int32_t *out, int64_t n, cuda
 
 // tiles
 int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cudaStream_t s);
+int use_tiles(gi_graph *g, int32_t tile_edges, cudaStream_t s);  // select (building once) the in-edge tiles
+void free_tile_cache(gi_graph *g, cudaStream_t s);
 void free_tiles(TileSet *ts, cudaStream_t s);
 
 // vertexset internals

@@ -27,6 +27,7 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
       GI_TRY(vset_ensure_bitmap(from, s));
       F = from->bitmap;
     }
+    const bool vp = sc.balance == GI_BAL_VERTEX;
     switch (kernel_id) {
       case GI_K_BFS: {
         const gi_bfs_args *a = static_cast<const gi_bfs_args *>(args);
@@ -41,25 +42,25 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
       case GI_K_SSSP: {
         const gi_sssp_args *a = static_cast<const gi_sssp_args *>(args);
         OpMinInt op{a->dist, a->snap, g->in.wt};
-        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s, kClassMinPull));
+        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s, kClassMinPull, vp));
         break;
       }
       case GI_K_CC: {
         const gi_cc_args *a = static_cast<const gi_cc_args *>(args);
         OpMinInt op{a->label, a->snap, nullptr};
-        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s, kClassMinPull));
+        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s, kClassMinPull, vp));
         break;
       }
       case GI_K_SUM: {
         const gi_sum_args *a = static_cast<const gi_sum_args *>(args);
         OpSum op{a->contrib, a->acc};
-        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s));
+        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s, kClassOtherPull, vp));
         break;
       }
       case GI_K_PROBE: {
         const gi_probe_args *a = static_cast<const gi_probe_args *>(args);
         OpProbe op{a->count, a->srcsum};
-        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s));
+        GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s, kClassOtherPull, vp));
         break;
       }
       default:
@@ -151,7 +152,7 @@ DecideParams decide_params(const gi_schedule &sc, int32_t level, bool track_unvi
 // keep the in-edge tiles at the schedule's tile size
 int ensure_tiles(gi_graph *g, const gi_schedule &sc, cudaStream_t s) {
   int32_t te = sc.tile_edges > 0 ? sc.tile_edges : 2048;
-  if (g->has_csc && g->in_tiles.tile_edges != te) GI_TRY(build_tiles(g, g->in, te, &g->in_tiles, s));
+  if (g->has_csc && g->in_tiles.tile_edges != te) GI_TRY(use_tiles(g, te, s));
   return GI_OK;
 }
 

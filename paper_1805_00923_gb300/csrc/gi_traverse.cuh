@@ -469,6 +469,38 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_pull_warp(Op op, const 
   }
 }
 
+// Vertex-parallel DensePull (configApplyParallelization's vertex-parallel
+// mode): one thread per destination, in-edges scanned serially with 4 loads in
+// flight.  Consecutive destinations sit in consecutive lanes, so the modified
+// set is marked one bitmap word per warp.
+template <class Op>
+__global__ void __launch_bounds__(256) k_pull_vertex(Op op, const int32_t *__restrict__ ptr,
+                                                     const int32_t *__restrict__ idx, int64_t n,
+                                                     const uint32_t *__restrict__ F, const uint32_t *__restrict__ to,
+                                                     OutSet out) {
+  using V = typename Op::V;
+  const int64_t nw = (n + 31) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t v = w * 32 + (threadIdx.x & 31);
+    bool mod = false;
+    if (v < n && in_set(to, (int32_t)v) && op.dst_ok((int32_t)v)) {
+      const int32_t a = __ldg(ptr + v), b = __ldg(ptr + v + 1);
+      V acc = Op::identity();
+      for (int32_t e = a; e < b; e += 4) {
+        int32_t u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) u[j] = e + j < b ? __ldg(idx + e + j) : -1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (u[j] >= 0 && in_set(F, u[j])) acc = Op::combine(acc, op.edge_val(u[j], e + j));
+      }
+      mod = op.finish((int32_t)v, acc);
+    }
+    if (out.enabled()) mark_consecutive(out, (int32_t)(w * 32), mod);
+  }
+}
+
 template <class Op>
 __global__ void k_pull_fixup(Op op, const int4 *__restrict__ splits, int32_t num_splits,
                              const typename Op::V *__restrict__ partial, const uint32_t *__restrict__ to, OutSet out) {
@@ -848,7 +880,15 @@ int launch_pull_tiled_te(const Op &op, const Csr &c, const TileSet &ts, const ui
 // Tiled pull over the in-edges `c` with tiles `ts` (the whole graph or one segment).
 template <class Op>
 int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts, const uint32_t *F,
-                      const uint32_t *to, const OutSet &out, cudaStream_t s, int kclass = kClassOtherPull) {
+                      const uint32_t *to, const OutSet &out, cudaStream_t s, int kclass = kClassOtherPull,
+                      bool vertex_parallel = false) {
+  if (vertex_parallel) {
+    const int tok = timing_begin(kclass, s);
+    k_pull_vertex<Op><<<grid_for(g, g->n, 256), 256, 0, s>>>(op, c.ptr, c.idx, g->n, F, to, out);
+    timing_end(tok, s);
+    GI_LAUNCH_CHECK();
+    return GI_OK;
+  }
   if (ts.num_tiles == 0) return GI_OK;
   const int tok = timing_begin(kclass, s);
   switch (ts.tile_edges) {

@@ -302,12 +302,14 @@ def test_bad_graph_rejected(gi):
     assert e.value.code == -2
 
 
-@pytest.mark.parametrize("te", [256, 512, 8192])
+@pytest.mark.parametrize("te", [256, 512, 8192, "vertex"])
 def test_pull_tile_sizes(gi, te):
-    """Every tile shape gives the oracle's results for min, sum and probe pulls."""
+    """Every tile shape (and the vertex-parallel pull) gives the oracle's results
+    for min, sum and probe pulls."""
     hg = rmat(14, weights=True)
     g = _load(gi, hg)
-    sc = gi.schedule("dense_pull", tile_edges=te)
+    sc = gi.schedule("dense_pull", balance="vertex") if te == "vertex" else gi.schedule("dense_pull", tile_edges=te)
+    te = 2048 if te == "vertex" else te
     want, fs = oracle.cc(hg)
     tr = gi.Trace(64)
     assert np.array_equal(_np(gi.cc(g, sched=sc, trace=tr)), want)
