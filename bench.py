@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--tune-budget", type=int, default=12, help="autotuner trials per algorithm (untimed)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the untimed autotuning and direction comparison (profiling runs)")
     p.add_argument("--only", choices=["pagerank", "pagerank_delta", "cc", "bfs", "sssp"], default=None,
                    help="profiling case: run just this algorithm --steps times on the workload graph")
     return p.parse_args()
@@ -213,6 +215,8 @@ def run_gi(args):
     stream = torch.cuda.current_stream()
     g = gi.Graph.from_host(hg)
     # the autotuner picks tile shape / thresholds / segment count (untimed setup)
+    if args.no_extras:
+        args.tune_budget = 1
     pr_s, pr_tuned_ms, pr_start_ms = gi.autotune(g, "pagerank", start=gi.schedule("dense_pull"),
                                                  budget=args.tune_budget, seed=1)
     prd_s, prd_tuned_ms, prd_start_ms = gi.autotune(g, "pagerank_delta", start=gi.schedule("hybrid_pull"),
@@ -224,9 +228,10 @@ def run_gi(args):
              "cc": dict(gi.schedule_dict(cc_s), tuned_ms=cc_tuned_ms, default_ms=cc_start_ms)}
     # the three PageRank directions of the workload, one timed run each (untimed setup)
     compare = {}
-    for name, sc in [("dense_pull", gi.schedule("dense_pull")),
-                     ("segmented_pull_4", gi.schedule("dense_pull", num_segments=4)),
-                     ("dense_push", gi.schedule("dense_push"))]:
+    for name, sc in ([] if args.no_extras else
+                     [("dense_pull", gi.schedule("dense_pull")),
+                      ("segmented_pull_4", gi.schedule("dense_pull", num_segments=4)),
+                      ("dense_push", gi.schedule("dense_push"))]):
         gi.pagerank(g, DAMPING, PR_ITERS, sched=sc)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()

@@ -18,6 +18,7 @@
 
 #include "gi_features.cuh"
 #include "gi_internal.cuh"
+#include "gi_traverse.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -102,37 +103,42 @@ __device__ bool batch_decide_pull(const BatchGraph &G, int64_t nf, int64_t mf, i
   return !((double)nf < (double)G.n / (double)beta);
 }
 
-// BFS SparsePush over queue entries [0, nf) of this level: block / warp /
-// thread expansion by degree; newly reached vertices get depth L+1 and are
-// appended to the next queue with their out-degree added to the edge count.
-__device__ void batch_bfs_push(const BatchGraph &G, int32_t *depth, const int32_t *cur, int64_t nf, int32_t *next,
-                               int64_t *ncnt, int64_t *necnt, int32_t L, int rank, int csize) {
-  __shared__ int32_t s_owner, s_u, s_a, s_d;
+// Frontier expansion shared by BFS and SSSP push: every thread takes one
+// queue entry; arcs of sources with >= 1024 arcs are spread over the block,
+// >= 32 over the warp; the arcs of the remaining sources of the block are laid
+// out back to back (block scan of the degrees, an owner byte per arc) and
+// expanded one arc per thread, kBatchArcs loads in flight.  fn(du, e, v)
+// handles arc e (destination v) of a source whose snapshot value is du.
+constexpr int kBatchArcs = 4;
+
+template <class Fn>
+__device__ __forceinline__ void strided_arcs(int32_t du, int32_t a, int32_t d, int32_t k0, int32_t step,
+                                             const int32_t *__restrict__ idx, Fn &fn) {
+  for (int32_t k = k0; k < d; k += kBatchArcs * step) {
+    int32_t v[kBatchArcs];
+#pragma unroll
+    for (int j = 0; j < kBatchArcs; ++j) v[j] = k + j * step < d ? __ldg(idx + a + k + j * step) : -1;
+#pragma unroll
+    for (int j = 0; j < kBatchArcs; ++j) fn(du, a + k + j * step, v[j]);
+  }
+}
+
+template <class Fn>
+__device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_t *curd, int64_t nf, int rank,
+                           int csize, Fn &fn) {
+  __shared__ int32_t s_owner, s_a, s_d, s_du;
+  __shared__ int32_t s_beg[kBT], s_off[kBT], s_dus[kBT], s_sw[32];
+  __shared__ uint8_t s_own[kBT * 31];
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t T = (int64_t)csize * kBT;
-  auto visit = [&](int32_t v) {
-    bool won = false;
-    if (*(volatile int32_t *)(depth + v) == -1) won = atomicCAS(depth + v, -1, L + 1) == -1;
-    const unsigned active = __activemask();
-    const unsigned ball = __ballot_sync(active, won);
-    if (ball) {
-      const int leader = __ffs(ball) - 1;
-      long long base = 0;
-      if (lane == leader) base = atomicAdd(reinterpret_cast<unsigned long long *>(ncnt), (unsigned long long)__popc(ball));
-      base = __shfl_sync(active, base, leader);
-      if (won) {
-        next[base + __popc(ball & ((1u << lane) - 1u))] = v;
-        atomicAdd(reinterpret_cast<unsigned long long *>(necnt), (unsigned long long)(G.ptr[v + 1] - G.ptr[v]));
-      }
-    }
-  };
   for (int64_t base = (int64_t)rank * kBT; base < nf; base += T) {
     const int64_t i = base + tid;
-    int32_t u = -1, a = 0, d = 0;
+    int32_t a = 0, d = 0, du = 0;
     if (i < nf) {
-      u = cur[i];
-      a = G.ptr[u];
-      d = G.ptr[u + 1] - a;
+      const int32_t u = cur[i];
+      du = curd ? curd[i] : 0;
+      a = __ldg(G.ptr + u);
+      d = __ldg(G.ptr + u + 1) - a;
     }
     while (true) {
       if (tid == 0) s_owner = -1;
@@ -142,25 +148,79 @@ __device__ void batch_bfs_push(const BatchGraph &G, int32_t *depth, const int32_
       const int owner = s_owner;
       if (owner < 0) break;
       if (tid == owner) {
-        s_u = u;
         s_a = a;
         s_d = d;
+        s_du = du;
         d = 0;
       }
       __syncthreads();
-      for (int32_t k = tid; k < s_d; k += kBT) visit(G.idx[s_a + k]);
+      strided_arcs(s_du, s_a, s_d, tid, kBT, G.idx, fn);
       __syncthreads();
     }
     while (true) {
       const unsigned bal = __ballot_sync(0xffffffffu, d >= 32);
       if (!bal) break;
       const int l = __ffs(bal) - 1;
-      const int32_t wa = __shfl_sync(0xffffffffu, a, l), wd = __shfl_sync(0xffffffffu, d, l);
+      const int32_t wa = __shfl_sync(0xffffffffu, a, l), wd = __shfl_sync(0xffffffffu, d, l),
+                    wdu = __shfl_sync(0xffffffffu, du, l);
       if (lane == l) d = 0;
-      for (int32_t k = lane; k < wd; k += 32) visit(G.idx[wa + k]);
+      strided_arcs(wdu, wa, wd, lane, 32, G.idx, fn);
     }
-    for (int32_t k = 0; k < d; ++k) visit(G.idx[a + k]);
+    int32_t total;
+    const int32_t off = block_excl_scan(d, &total, s_sw);
+    s_beg[tid] = a;
+    s_off[tid] = off;
+    s_dus[tid] = du;
+    for (int32_t k = 0; k < d; ++k) s_own[off + k] = (uint8_t)tid;
+    __syncthreads();
+    for (int32_t j0 = tid; j0 < total; j0 += kBatchArcs * kBT) {
+      int32_t e[kBatchArcs], dd[kBatchArcs], v[kBatchArcs];
+#pragma unroll
+      for (int b2 = 0; b2 < kBatchArcs; ++b2) {
+        const int32_t j = j0 + b2 * kBT;
+        if (j < total) {
+          const int o = s_own[j];
+          e[b2] = s_beg[o] + (j - s_off[o]);
+          dd[b2] = s_dus[o];
+          v[b2] = __ldg(G.idx + e[b2]);
+        } else {
+          e[b2] = 0;
+          dd[b2] = 0;
+          v[b2] = -1;
+        }
+      }
+#pragma unroll
+      for (int b2 = 0; b2 < kBatchArcs; ++b2) fn(dd[b2], e[b2], v[b2]);
+    }
+    __syncthreads();
   }
+}
+
+__device__ __forceinline__ void append_warp(bool want, int32_t v, int32_t *next, int64_t *ncnt) {
+  const int lane = threadIdx.x & 31;
+  const unsigned active = __activemask();
+  const unsigned ball = __ballot_sync(active, want);
+  if (!ball) return;
+  const int leader = __ffs(ball) - 1;
+  long long base = 0;
+  if (lane == leader) base = atomicAdd(reinterpret_cast<unsigned long long *>(ncnt), (unsigned long long)__popc(ball));
+  base = __shfl_sync(active, base, leader);
+  if (want) next[base + __popc(ball & ((1u << lane) - 1u))] = v;
+}
+
+// BFS SparsePush of this level's queue: newly reached vertices get depth L+1
+// and join the next queue (their out-degrees summed into the edge count).
+__device__ void batch_bfs_push(const BatchGraph &G, int32_t *depth, const int32_t *cur, int64_t nf, int32_t *next,
+                               int64_t *ncnt, int64_t *necnt, int32_t L, int rank, int csize) {
+  auto fn = [&](int32_t, int32_t, int32_t v) {
+    bool won = false;
+    if (v >= 0 && *(volatile int32_t *)(depth + v) == -1) won = atomicCAS(depth + v, -1, L + 1) == -1;
+    append_warp(won, v, next, ncnt);
+    if (won)
+      atomicAdd(reinterpret_cast<unsigned long long *>(necnt), (unsigned long long)(__ldg(G.ptr + v + 1) -
+                                                                                   __ldg(G.ptr + v)));
+  };
+  cta_expand(G, cur, nullptr, nf, rank, csize, fn);
 }
 
 // BFS DensePull with early exit: the frontier is {u : depth[u] == L}
@@ -214,70 +274,25 @@ __device__ void batch_bfs_pull(const BatchGraph &G, int32_t *depth, int32_t *nex
   }
 }
 
-// SSSP push relax of this round's queue (start-of-round distances in curd)
+// SSSP push relax of this round's queue (start-of-round distances in curd);
+// each improved destination joins the next queue once (dedup bitmap inq).
 __device__ void batch_sssp_push(const BatchGraph &G, int32_t *dist, const int32_t *cur, const int32_t *curd,
                                 int64_t nf, int32_t *next, int64_t *ncnt, uint32_t *inq, int rank, int csize) {
-  __shared__ int32_t s_owner, s_a, s_d, s_du;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int64_t T = (int64_t)csize * kBT;
-  auto relax = [&](int32_t du, int32_t e) {
-    const int32_t v = G.idx[e];
-    const long long nd = (long long)du + G.wt[e];
+  auto fn = [&](int32_t du, int32_t e, int32_t v) {
     bool fresh = false;
-    if (nd < *(volatile int32_t *)(dist + v)) {
-      const int32_t old = atomicMin(dist + v, (int32_t)nd);
-      if (nd < old) {
-        const uint32_t mask = 1u << (v & 31);
-        fresh = (atomicOr(inq + (v >> 5), mask) & mask) == 0;
+    if (v >= 0) {
+      const long long nd = (long long)du + __ldg(G.wt + e);
+      if (nd < *(volatile int32_t *)(dist + v)) {
+        const int32_t old = atomicMin(dist + v, (int32_t)nd);
+        if (nd < old) {
+          const uint32_t mask = 1u << (v & 31);
+          fresh = (atomicOr(inq + (v >> 5), mask) & mask) == 0;
+        }
       }
     }
-    const unsigned active = __activemask();
-    const unsigned ball = __ballot_sync(active, fresh);
-    if (ball) {
-      const int leader = __ffs(ball) - 1;
-      long long base = 0;
-      if (lane == leader) base = atomicAdd(reinterpret_cast<unsigned long long *>(ncnt), (unsigned long long)__popc(ball));
-      base = __shfl_sync(active, base, leader);
-      if (fresh) next[base + __popc(ball & ((1u << lane) - 1u))] = v;
-    }
+    append_warp(fresh, v, next, ncnt);
   };
-  for (int64_t base = (int64_t)rank * kBT; base < nf; base += T) {
-    const int64_t i = base + tid;
-    int32_t a = 0, d = 0, du = 0;
-    if (i < nf) {
-      const int32_t u = cur[i];
-      du = curd[i];
-      a = G.ptr[u];
-      d = G.ptr[u + 1] - a;
-    }
-    while (true) {
-      if (tid == 0) s_owner = -1;
-      __syncthreads();
-      if (d >= 1024) s_owner = tid;
-      __syncthreads();
-      const int owner = s_owner;
-      if (owner < 0) break;
-      if (tid == owner) {
-        s_a = a;
-        s_d = d;
-        s_du = du;
-        d = 0;
-      }
-      __syncthreads();
-      for (int32_t k = tid; k < s_d; k += kBT) relax(s_du, s_a + k);
-      __syncthreads();
-    }
-    while (true) {
-      const unsigned bal = __ballot_sync(0xffffffffu, d >= 32);
-      if (!bal) break;
-      const int l = __ffs(bal) - 1;
-      const int32_t wa = __shfl_sync(0xffffffffu, a, l), wd = __shfl_sync(0xffffffffu, d, l),
-                    wdu = __shfl_sync(0xffffffffu, du, l);
-      if (lane == l) d = 0;
-      for (int32_t k = lane; k < wd; k += 32) relax(wdu, wa + k);
-    }
-    for (int32_t k = 0; k < d; ++k) relax(du, a + k);
-  }
+  cta_expand(G, cur, curd, nf, rank, csize, fn);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
