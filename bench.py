@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--tune-budget", type=int, default=12, help="autotuner trials per algorithm (untimed)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the untimed autotuning and direction comparison (profiling runs)")
+    p.add_argument("--workload", choices=["rmat22", "rmat24_bfs_sssp", "grid4096", "batch512"], default="rmat22",
+                   help="rmat22 (default): the timed PR+PRD+CC step; the others measure the remaining "
+                        "configurations and print their own JSON line")
+    p.add_argument("--sources", type=int, default=16, help="sources per graph for the BFS/SSSP workloads")
     p.add_argument("--only", choices=["pagerank", "pagerank_delta", "cc", "bfs", "sssp"], default=None,
                    help="profiling case: run just this algorithm --steps times on the workload graph")
     return p.parse_args()
@@ -382,10 +386,153 @@ def run_only(args):
     return 0
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _traversed(tr, m, pull_dir):
+    t = tr.as_dict()
+    return int(sum(e for e in t["edges"]))
+
+
+def run_rmat24(args):
+    """R-MAT scale 24, BFS + SSSP from --sources sources: Beamer vs learned vs exhaustive best per level."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import paper_1805_00923_gb300 as gi
+    from paper_1805_00923_gb300 import selector as sel
+    torch.cuda.set_device(0)
+    sel.install()
+    hg = gg.rmat_graph(24, seed=1, weights=(1, 1000))
+    g = gi.Graph.from_host(hg)
+    srcs = gg.pick_sources(hg, args.sources, seed=1)
+    out = {}
+    for algo in ("bfs", "sssp"):
+        res = {}
+        for pol in ("hybrid_pull", "learned"):
+            ms, edges = 0.0, 0
+            for s_ in srcs:
+                tr = gi.Trace(4096)
+                run = (lambda: gi.bfs(g, int(s_), want_parent=False, sched=gi.schedule(pol), trace=tr)) \
+                    if algo == "bfs" else (lambda: gi.sssp(g, int(s_), sched=gi.schedule(pol), trace=tr))
+                run()
+                a, b = _events()
+                a.record()
+                run()
+                b.record()
+                torch.cuda.synchronize()
+                ms += a.elapsed_time(b)
+                edges += int(tr.as_dict()["edges"].sum())
+            res[pol] = {"gteps": edges / (ms * 1e-3) / 1e9, "ms_per_query": ms / len(srcs)}
+        best_ms = 0.0
+        for s_ in srcs[:max(1, len(srcs) // 4)]:
+            f, t = sel.profile(g, gi.GI_K_BFS if algo == "bfs" else gi.GI_K_SSSP, int(s_))
+            best_ms += float(t.min(axis=1).sum())
+        res["exhaustive_best_ms_per_query"] = best_ms / max(1, len(srcs) // 4)
+        out[algo] = res
+    val = (out["bfs"]["learned"]["gteps"] + out["sssp"]["learned"]["gteps"]) / 2
+    print(json.dumps({"metric": METRIC, "workload": "rmat24_bfs_sssp", "value": val, "unit": "GTEPS",
+                      "n": hg.n, "m": hg.m, "sources": len(srcs), "results": out,
+                      "note": "value = mean of BFS and SSSP GTEPS under the learned selector; edges = sum of m_f"}))
+    return 0
+
+
+def run_grid4096(args):
+    """4096x4096 grid, BFS + SSSP from --sources sources: host-driven drivers vs the batched engine."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import paper_1805_00923_gb300 as gi
+    from paper_1805_00923_gb300 import selector as sel
+    torch.cuda.set_device(0)
+    sel.install()
+    hg = gg.grid_graph(4096, seed=1, weights=(1, 100))
+    g = gi.Graph.from_host(hg)
+    srcs = gg.pick_sources(hg, args.sources, seed=1)
+    out = {}
+    for algo in ("bfs", "sssp"):
+        t0 = time.perf_counter()
+        for s_ in srcs[:2]:
+            if algo == "bfs":
+                gi.bfs(g, int(s_), want_parent=False, sched=gi.schedule("learned"))
+            else:
+                gi.sssp(g, int(s_), sched=gi.schedule("learned"))
+        torch.cuda.synchronize()
+        host_ms = (time.perf_counter() - t0) * 1e3 / 2
+        qs = [(0, int(s_), algo) for s_ in srcs]
+        plan = gi.BatchPlan([g], qs, opts=gi.batch_opts(cluster_size=8, selector="learned"))
+        plan.launch()
+        plan.results()
+        a, b = _events()
+        a.record()
+        plan.launch()
+        b.record()
+        torch.cuda.synchronize()
+        res, ns, lev = plan.results()
+        plan.free()
+        bms = a.elapsed_time(b)
+        out[algo] = {"host_driven_ms_per_query": host_ms, "batch_ms_total": bms,
+                     "batch_gteps_nominal": len(qs) * hg.m / (bms * 1e-3) / 1e9,
+                     "p50_ms": float(np.percentile(ns, 50) / 1e6), "p99_ms": float(np.percentile(ns, 99) / 1e6),
+                     "levels_mean": float(lev.mean())}
+    val = sum(out[a]["batch_gteps_nominal"] for a in out) / 2
+    print(json.dumps({"metric": METRIC, "workload": "grid4096_bfs_sssp", "value": val, "unit": "GTEPS",
+                      "n": hg.n, "m": hg.m, "sources": len(srcs), "results": out,
+                      "note": "nominal GTEPS = queries * m / time"}))
+    return 0
+
+
+def run_batch512(args):
+    """32 graphs (16 R-MAT scale 12-20, ef 8-32; 16 grids 256-2048), 512 BFS/SSSP queries in one launch."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import paper_1805_00923_gb300 as gi
+    from paper_1805_00923_gb300 import selector as sel
+    torch.cuda.set_device(0)
+    sel.install()
+    rng = np.random.default_rng(1)
+    hgs = [gg.rmat_graph(int(rng.integers(12, 21)), int(rng.choice([8, 16, 32])), seed=100 + i, weights=(1, 1000))
+           for i in range(16)]
+    hgs += [gg.grid_graph(int(rng.choice([256, 512, 1024, 2048])), seed=200 + i, weights=(1, 1000))
+            for i in range(16)]
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    qs = []
+    for i in range(512):
+        k = int(rng.integers(0, 32))
+        qs.append((k, int(gg.pick_sources(hgs[k], 1, seed=1000 + i)[0]), "bfs" if i % 2 == 0 else "sssp"))
+    edges = sum(hgs[q[0]].m for q in qs)
+    out = {}
+    for cs in (2, 4):
+        plan = gi.BatchPlan(gs, qs, opts=gi.batch_opts(cluster_size=cs, selector="learned"))
+        plan.launch()
+        plan.results()
+        a, b = _events()
+        a.record()
+        plan.launch()
+        b.record()
+        torch.cuda.synchronize()
+        _, ns, lev = plan.results()
+        plan.free()
+        ms = a.elapsed_time(b)
+        out[f"cluster{cs}"] = {"ms": ms, "gteps_nominal": edges / (ms * 1e-3) / 1e9,
+                               "p50_ms": float(np.percentile(ns, 50) / 1e6),
+                               "p99_ms": float(np.percentile(ns, 99) / 1e6)}
+    best = max(out.values(), key=lambda r: r["gteps_nominal"])
+    print(json.dumps({"metric": METRIC, "workload": "batch512", "value": best["gteps_nominal"], "unit": "GTEPS",
+                      "graphs": 32, "queries": 512, "results": out,
+                      "note": "nominal GTEPS = sum over queries of the graph's m / time"}))
+    return 0
+
+
 def main():
     args = parse()
     if args.only:
         return run_only(args)
+    if args.impl == "gi" and args.workload != "rmat22":
+        return {"rmat24_bfs_sssp": run_rmat24, "grid4096": run_grid4096, "batch512": run_batch512}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gi(args)

@@ -350,8 +350,10 @@ int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, const gi_sc
  * the paper, which runs one query at a time).  The launch is a grid of
  * thread-block clusters; each cluster claims the next query from a global
  * counter and runs it to completion with cluster barriers between levels
- * (BFS: SparsePush or early-exit DensePull per level; SSSP: synchronous
- * Bellman-Ford push).  No cluster ever waits for another.
+ * (BFS: SparsePush or early-exit DensePull per level; SSSP: Bellman-Ford push
+ * with asynchronous min updates, i.e. the asyncMin of Sec. 6 -- same final
+ * distances as gi_sssp, different round counts).  No cluster ever waits for
+ * another.
  */
 typedef struct gi_batch_opts {
   int32_t cluster_size; /* CTAs per query: 1, 2, 4 or 8 (default 4)                       */
@@ -378,6 +380,25 @@ void gi_batch_opts_default(gi_batch_opts *o);
 int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int32_t *q_graph, const int32_t *q_src,
                  const int32_t *q_algo, int32_t n_q, int32_t *const *out_dev, int64_t *q_ns,
                  const gi_batch_opts *opts, void *stream);
+
+/*
+ * The same in three steps, so that the launch can be captured in a CUDA graph
+ * and replayed: gi_batch_plan_create validates the queries, allocates the
+ * working memory and uploads the query tables (syncs the stream);
+ * gi_batch_plan_launch enqueues one memset and the single persistent kernel
+ * on `stream` (no allocation, no host synchronisation: capturable);
+ * gi_batch_plan_results copies per-query times and level counts (either may be
+ * NULL) and reports GI_ERR_TIMEOUT if a query hit the level cap (syncs);
+ * gi_batch_plan_free releases everything.  Outputs go to the out_dev pointers
+ * given at creation, which must stay valid while the plan is used.
+ */
+typedef struct gi_batch_plan gi_batch_plan;
+int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, const int32_t *q_graph, const int32_t *q_src,
+                         const int32_t *q_algo, int32_t n_q, int32_t *const *out_dev, const gi_batch_opts *opts,
+                         void *stream, gi_batch_plan **out);
+int gi_batch_plan_launch(gi_batch_plan *p, void *stream);
+int gi_batch_plan_results(gi_batch_plan *p, int64_t *q_ns, int32_t *levels, void *stream);
+int gi_batch_plan_free(gi_batch_plan *p);
 
 /* ------------------------------------------------------------- autotuner -- */
 /* algorithms the autotuner runs (the drivers above with their Sec. 7 settings) */

@@ -311,3 +311,45 @@ def batch_run(graphs, queries, outs=None, opts=None, stream=None):
     check(_C.gi_batch_run(handles, len(graphs), _vp(qg), _vp(qs), _vp(qa), n_q, optr, _vp(ns),
                           ctypes.byref(opts if opts is not None else batch_opts()), _stream(stream)))
     return [o[:graphs[q[0]].n] for o, q in zip(outs, queries)], ns[:n_q]
+
+
+class BatchPlan:
+    """gi_batch_plan: the batched engine split into create / launch (capturable) / results."""
+
+    def __init__(self, graphs, queries, opts=None, outs=None, stream=None):
+        n_q = len(queries)
+        qg = np.array([q[0] for q in queries], np.int32)
+        qs = np.array([q[1] for q in queries], np.int32)
+        qa = np.array([ALGOS[q[2]] if isinstance(q[2], str) else q[2] for q in queries], np.int32)
+        self.outs = outs if outs is not None else [torch.empty(max(graphs[q[0]].n, 1), dtype=torch.int32,
+                                                               device="cuda") for q in queries]
+        self.queries = queries
+        self.graphs = graphs
+        handles = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+        optr = (ctypes.c_void_p * n_q)(*[o.data_ptr() for o in self.outs])
+        h = ctypes.c_void_p()
+        check(_C.gi_batch_plan_create(handles, len(graphs), _vp(qg), _vp(qs), _vp(qa), n_q, optr,
+                                      ctypes.byref(opts if opts is not None else batch_opts()), _stream(stream),
+                                      ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        check(_C.gi_batch_plan_launch(self.handle, _stream(stream)))
+
+    def results(self, stream=None):
+        n_q = len(self.queries)
+        ns = np.zeros(n_q, np.int64)
+        lev = np.zeros(n_q, np.int32)
+        check(_C.gi_batch_plan_results(self.handle, _vp(ns), _vp(lev), _stream(stream)))
+        return [o[:self.graphs[q[0]].n] for o, q in zip(self.outs, self.queries)], ns, lev
+
+    def free(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            check(_C.gi_batch_plan_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -107,6 +107,11 @@ SIGNATURES = {
                                    _P(ctypes.c_double), _P(ctypes.c_double), _vp]),
     "gi_batch_opts_default": (None, [_P(gi_batch_opts)]),
     "gi_batch_run": (ctypes.c_int, [_P(_vp), _i32, _vp, _vp, _vp, _i32, _P(_vp), _vp, _P(gi_batch_opts), _vp]),
+    "gi_batch_plan_create": (ctypes.c_int, [_P(_vp), _i32, _vp, _vp, _vp, _i32, _P(_vp), _P(gi_batch_opts), _vp,
+                                            _P(_vp)]),
+    "gi_batch_plan_launch": (ctypes.c_int, [_vp, _vp]),
+    "gi_batch_plan_results": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "gi_batch_plan_free": (ctypes.c_int, [_vp]),
     "gi_stats_enable": (ctypes.c_int, [ctypes.c_int]),
     "gi_stats_reset": (ctypes.c_int, []),
     "gi_stats_read": (ctypes.c_int, [_i32, _P(_i64), _P(_i64), _P(ctypes.c_double)]),

@@ -4,8 +4,8 @@
 // The launch is a grid of thread-block clusters.  Each cluster repeatedly
 // claims the next query from a global counter and runs it to completion:
 // level-synchronous BFS (SparsePush or early-exit DensePull per level, chosen
-// by Beamer's rule or the learned selector) or synchronous Bellman-Ford SSSP
-// (push).  The only waits are cluster barriers (barrier.cluster, hardware
+// by Beamer's rule or the learned selector) or Bellman-Ford SSSP with
+// asynchronous min relaxation (push).  The only waits are cluster barriers (barrier.cluster, hardware
 // co-scheduled CTAs) taken the same number of times by every CTA of a
 // cluster: all loop bounds come from values read after a barrier.  Clusters
 // never wait on each other, so a cluster that starts late simply finds the
@@ -123,9 +123,10 @@ __device__ __forceinline__ void strided_arcs(int32_t du, int32_t a, int32_t d, i
   }
 }
 
+// du of a source: curd[i] (a snapshot), else the current value in live[u], else 0
 template <class Fn>
-__device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_t *curd, int64_t nf, int rank,
-                           int csize, Fn &fn) {
+__device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_t *curd, const int32_t *live,
+                           int64_t nf, int rank, int csize, Fn &fn) {
   __shared__ int32_t s_owner, s_a, s_d, s_du;
   __shared__ int32_t s_beg[kBT], s_off[kBT], s_dus[kBT], s_sw[32];
   __shared__ uint8_t s_own[kBT * 31];
@@ -136,7 +137,7 @@ __device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_
     int32_t a = 0, d = 0, du = 0;
     if (i < nf) {
       const int32_t u = cur[i];
-      du = curd ? curd[i] : 0;
+      du = curd ? curd[i] : (live ? *(volatile const int32_t *)(live + u) : 0);
       a = __ldg(G.ptr + u);
       d = __ldg(G.ptr + u + 1) - a;
     }
@@ -220,7 +221,7 @@ __device__ void batch_bfs_push(const BatchGraph &G, int32_t *depth, const int32_
       atomicAdd(reinterpret_cast<unsigned long long *>(necnt), (unsigned long long)(__ldg(G.ptr + v + 1) -
                                                                                    __ldg(G.ptr + v)));
   };
-  cta_expand(G, cur, nullptr, nf, rank, csize, fn);
+  cta_expand(G, cur, nullptr, nullptr, nf, rank, csize, fn);
 }
 
 // BFS DensePull with early exit: the frontier is {u : depth[u] == L}
@@ -274,9 +275,13 @@ __device__ void batch_bfs_pull(const BatchGraph &G, int32_t *depth, int32_t *nex
   }
 }
 
-// SSSP push relax of this round's queue (start-of-round distances in curd);
-// each improved destination joins the next queue once (dedup bitmap inq).
-__device__ void batch_sssp_push(const BatchGraph &G, int32_t *dist, const int32_t *cur, const int32_t *curd,
+// SSSP push relax of this round's queue with asynchronous min updates (the
+// asyncMin of Sec. 6): each source offers its current distance, so an
+// improvement made earlier in the round propagates at once.  The final
+// distances are the unique shortest distances, as with synchronous rounds;
+// the rounds and frontiers are not (the engine does not report them per
+// round).  Each improved destination joins the next queue once (dedup bitmap).
+__device__ void batch_sssp_push(const BatchGraph &G, int32_t *dist, const int32_t *cur, const int32_t *,
                                 int64_t nf, int32_t *next, int64_t *ncnt, uint32_t *inq, int rank, int csize) {
   auto fn = [&](int32_t du, int32_t e, int32_t v) {
     bool fresh = false;
@@ -292,7 +297,7 @@ __device__ void batch_sssp_push(const BatchGraph &G, int32_t *dist, const int32_
     }
     append_warp(fresh, v, next, ncnt);
   };
-  cta_expand(G, cur, curd, nf, rank, csize, fn);
+  cta_expand(G, cur, nullptr, dist, nf, rank, csize, fn);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -368,10 +373,8 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
         batch_sssp_push(G, Q.out, cur, W.qd[L & 1], nf, next, ncnt, W.inq, rank, csize);
         csync(cl);
         const int64_t nn = *(volatile int64_t *)ncnt;
-        int32_t *nextd = W.qd[(L + 1) & 1];
         for (int64_t i = gtid; i < nn; i += T) {
           const int32_t v = next[i];
-          nextd[i] = Q.out[v];
           atomicAnd(W.inq + (v >> 5), ~(1u << (v & 31)));
         }
         csync(cl);
@@ -387,11 +390,40 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
 
 using namespace gi;
 
-extern "C" int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int32_t *q_graph, const int32_t *q_src,
-                            const int32_t *q_algo, int32_t n_q, int32_t *const *out_dev, int64_t *q_ns,
-                            const gi_batch_opts *opts, void *stream) {
+struct gi_batch_plan {
+  gi::BatchGraph *dg = nullptr;
+  gi::BatchQuery *dq = nullptr;
+  gi::ClusterWs *dws = nullptr;
+  int32_t *work = nullptr;  // [0] query counter, [1] error flag
+  int32_t *slab = nullptr;
+  int64_t *cnts = nullptr, *dns = nullptr;
+  int32_t *dlev = nullptr;
+  int32_t n_q = 0, clusters = 0, cluster_size = 0, selector = 0;
+  float alpha = 14.0f, beta = 24.0f;
+  int64_t cap = 0;
+  int32_t *levels_host = nullptr;
+};
+
+static void plan_release(gi_batch_plan *p, cudaStream_t s) {
+  dev_free(p->dg, s);
+  dev_free(p->dq, s);
+  dev_free(p->dws, s);
+  dev_free(p->work, s);
+  dev_free(p->slab, s);
+  dev_free(p->cnts, s);
+  dev_free(p->dns, s);
+  dev_free(p->dlev, s);
+  delete p;
+}
+
+extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, const int32_t *q_graph,
+                                    const int32_t *q_src, const int32_t *q_algo, int32_t n_q,
+                                    int32_t *const *out_dev, const gi_batch_opts *opts, void *stream,
+                                    gi_batch_plan **out) {
+  GI_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
   GI_ARG(graphs != nullptr && n_graphs > 0, "no graphs");
-  GI_ARG(n_q >= 0 && (n_q == 0 || (q_graph && q_src && q_algo && out_dev)), "bad query arrays");
+  GI_ARG(n_q > 0 && q_graph && q_src && q_algo && out_dev, "bad query arrays");
   gi_batch_opts o;
   gi_batch_opts_default(&o);
   if (opts) o = *opts;
@@ -419,93 +451,117 @@ extern "C" int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int
     GI_ARG(out_dev[i] != nullptr, "NULL output");
     hq[i] = BatchQuery{q_graph[i], q_src[i], q_algo[i], out_dev[i]};
   }
-  if (n_q == 0) return GI_OK;
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, sms = 0;
   GI_CUDA(cudaGetDevice(&dev));
   GI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  int clusters = o.clusters > 0 ? o.clusters : sms / o.cluster_size;
-  if (clusters > n_q) clusters = n_q;
-  if (clusters < 1) clusters = 1;
+  gi_batch_plan *p = new gi_batch_plan();
+  p->n_q = n_q;
+  p->cluster_size = o.cluster_size;
+  p->clusters = o.clusters > 0 ? o.clusters : sms / o.cluster_size;
+  if (p->clusters > n_q) p->clusters = n_q;
+  if (p->clusters < 1) p->clusters = 1;
+  p->selector = o.selector;
+  p->alpha = o.alpha;
+  p->beta = o.beta;
+  p->cap = o.level_cap > 0 ? o.level_cap : nmax + 2;
   const int64_t words = (nmax + 31) / 32;
-  // device copies and per-cluster working memory
-  BatchGraph *dg = nullptr;
-  BatchQuery *dq = nullptr;
-  ClusterWs *dws = nullptr;
-  int32_t *work = nullptr, *slab = nullptr, *dlev = nullptr;
-  int64_t *cnts = nullptr, *dns = nullptr;
-  std::vector<ClusterWs> hws(clusters);
   const int64_t per = 4 * nmax + words;  // 2 queues + 2 distance queues + bitmap, in int32 words
-  int st = dev_alloc_n(&dg, n_graphs, s);
-  if (st == GI_OK) st = dev_alloc_n(&dq, n_q, s);
-  if (st == GI_OK) st = dev_alloc_n(&dws, clusters, s);
-  if (st == GI_OK) st = dev_alloc_n(&work, 2, s);
-  if (st == GI_OK) st = dev_alloc_n(&slab, per * clusters, s);
-  if (st == GI_OK) st = dev_alloc_n(&cnts, 8 * clusters, s);
-  if (st == GI_OK && q_ns) st = dev_alloc_n(&dns, n_q, s);
-  if (st == GI_OK && o.levels) st = dev_alloc_n(&dlev, n_q, s);
+  std::vector<ClusterWs> hws(p->clusters);
+  int st = dev_alloc_n(&p->dg, n_graphs, s);
+  if (st == GI_OK) st = dev_alloc_n(&p->dq, n_q, s);
+  if (st == GI_OK) st = dev_alloc_n(&p->dws, p->clusters, s);
+  if (st == GI_OK) st = dev_alloc_n(&p->work, 2, s);
+  if (st == GI_OK) st = dev_alloc_n(&p->slab, per * p->clusters, s);
+  if (st == GI_OK) st = dev_alloc_n(&p->cnts, 8 * p->clusters, s);
+  if (st == GI_OK) st = dev_alloc_n(&p->dns, n_q, s);
+  if (st == GI_OK) st = dev_alloc_n(&p->dlev, n_q, s);
   if (st == GI_OK) {
-    for (int c = 0; c < clusters; ++c) {
-      int32_t *b = slab + per * c;
+    for (int c = 0; c < p->clusters; ++c) {
+      int32_t *b = p->slab + per * c;
       hws[c].q[0] = b;
       hws[c].q[1] = b + nmax;
       hws[c].qd[0] = b + 2 * nmax;
       hws[c].qd[1] = b + 3 * nmax;
       hws[c].inq = reinterpret_cast<uint32_t *>(b + 4 * nmax);
-      hws[c].cnt = cnts + 8 * c;
+      hws[c].cnt = p->cnts + 8 * c;
     }
-    if (cudaMemcpyAsync(dg, hg.data(), sizeof(BatchGraph) * n_graphs, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(dq, hq.data(), sizeof(BatchQuery) * n_q, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(dws, hws.data(), sizeof(ClusterWs) * clusters, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(work, 0, 2 * sizeof(int32_t), s) != cudaSuccess)
-      st = cuda_fail(cudaGetLastError(), "batch setup", __FILE__, __LINE__);
+    if (cudaMemcpyAsync(p->dg, hg.data(), sizeof(BatchGraph) * n_graphs, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(p->dq, hq.data(), sizeof(BatchQuery) * n_q, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(p->dws, hws.data(), sizeof(ClusterWs) * p->clusters, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = cuda_fail(cudaGetLastError(), "batch plan", __FILE__, __LINE__);
   }
-  if (st == GI_OK) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(clusters * o.cluster_size));
-    cfg.blockDim = dim3(kBT);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)o.cluster_size;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const int mode = o.selector == GI_DIR_SPARSE_PUSH ? 0 : (o.selector == GI_DIR_LEARNED && selector_loaded() ? 2 : 1);
-    const int64_t cap = o.level_cap > 0 ? o.level_cap : nmax + 2;
-    const int tok = timing_begin(kClassBatch, s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch, (const BatchGraph *)dg, (const BatchQuery *)dq, n_q, work, dws,
-                                       dns, dlev, mode, o.alpha, o.beta, cap, work + 1);
-    timing_end(tok, s);
-    note_launch(1);
-    if (e != cudaSuccess) st = cuda_fail(e, "batch launch", __FILE__, __LINE__);
+  if (st != GI_OK) {
+    cudaStreamSynchronize(s);
+    plan_release(p, s);
+    return st;
   }
+  *out = p;
+  return GI_OK;
+}
+
+extern "C" int gi_batch_plan_launch(gi_batch_plan *p, void *stream) {
+  GI_ARG(p != nullptr, "plan is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  GI_CUDA(cudaMemsetAsync(p->work, 0, 2 * sizeof(int32_t), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(p->clusters * p->cluster_size));
+  cfg.blockDim = dim3(kBT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)p->cluster_size;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int mode = p->selector == GI_DIR_SPARSE_PUSH ? 0 : (p->selector == GI_DIR_LEARNED && selector_loaded() ? 2 : 1);
+  const int tok = timing_begin(kClassBatch, s);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch, (const BatchGraph *)p->dg, (const BatchQuery *)p->dq, p->n_q,
+                                     p->work, p->dws, p->dns, p->dlev, mode, p->alpha, p->beta, p->cap, p->work + 1);
+  timing_end(tok, s);
+  note_launch(1);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch", __FILE__, __LINE__);
+  return GI_OK;
+}
+
+extern "C" int gi_batch_plan_results(gi_batch_plan *p, int64_t *q_ns, int32_t *levels, void *stream) {
+  GI_ARG(p != nullptr, "plan is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
   int32_t err = 0;
-  if (st == GI_OK && cudaMemcpyAsync(&err, work + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    st = cuda_fail(cudaGetLastError(), "batch status", __FILE__, __LINE__);
-  if (st == GI_OK && q_ns &&
-      cudaMemcpyAsync(q_ns, dns, sizeof(int64_t) * n_q, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    st = cuda_fail(cudaGetLastError(), "batch times", __FILE__, __LINE__);
-  if (st == GI_OK && o.levels &&
-      cudaMemcpyAsync(o.levels, dlev, sizeof(int32_t) * n_q, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    st = cuda_fail(cudaGetLastError(), "batch levels", __FILE__, __LINE__);
-  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
-    st = cuda_fail(cudaGetLastError(), "batch", __FILE__, __LINE__);
-  dev_free(dlev, s);
-  dev_free(dg, s);
-  dev_free(dq, s);
-  dev_free(dws, s);
-  dev_free(work, s);
-  dev_free(slab, s);
-  dev_free(cnts, s);
-  dev_free(dns, s);
-  if (st == GI_OK && err) {
+  GI_CUDA(cudaMemcpyAsync(&err, p->work + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (q_ns) GI_CUDA(cudaMemcpyAsync(q_ns, p->dns, sizeof(int64_t) * p->n_q, cudaMemcpyDeviceToHost, s));
+  if (levels) GI_CUDA(cudaMemcpyAsync(levels, p->dlev, sizeof(int32_t) * p->n_q, cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  if (err) {
     set_error("a query exceeded the level cap of the batched engine");
     return GI_ERR_TIMEOUT;
   }
-  return st;
+  return GI_OK;
+}
+
+extern "C" int gi_batch_plan_free(gi_batch_plan *p) {
+  if (!p) return GI_OK;
+  cudaDeviceSynchronize();
+  plan_release(p, 0);
+  GI_CUDA(cudaStreamSynchronize(0));
+  return GI_OK;
+}
+
+extern "C" int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int32_t *q_graph, const int32_t *q_src,
+                            const int32_t *q_algo, int32_t n_q, int32_t *const *out_dev, int64_t *q_ns,
+                            const gi_batch_opts *opts, void *stream) {
+  GI_ARG(n_q >= 0, "n_q must be >= 0");
+  if (n_q == 0) return GI_OK;
+  gi_batch_plan *p = nullptr;
+  GI_TRY(gi_batch_plan_create(graphs, n_graphs, q_graph, q_src, q_algo, n_q, out_dev, opts, stream, &p));
+  int st = gi_batch_plan_launch(p, stream);
+  if (st == GI_OK) st = gi_batch_plan_results(p, q_ns, opts ? opts->levels : nullptr, stream);
+  const int st2 = gi_batch_plan_free(p);
+  return st != GI_OK ? st : st2;
 }
 
 extern "C" void gi_batch_opts_default(gi_batch_opts *o) {

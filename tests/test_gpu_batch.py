@@ -83,3 +83,28 @@ def test_batch_level_cap_returns_timeout(gi):
     # the context is still usable
     res, _ = gi.batch_run([g], [(0, 0, "bfs"), (0, 5, "sssp")])
     _check([hg], [(0, 0, "bfs"), (0, 5, "sssp")], res)
+
+
+def test_batch_plan_graph_capture_replay(gi):
+    """The plan's launch is captured in a CUDA graph and replayed; each replay
+    recomputes every query (outputs are cleared in between)."""
+    import torch
+    hgs = _graphs()
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    qs = _queries(hgs, 24, seed=21)
+    plan = gi.BatchPlan(gs, qs, opts=gi.batch_opts(cluster_size=2))
+    plan.launch()
+    res, ns, lev = plan.results()
+    _check(hgs, qs, res)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.launch()
+    for _ in range(2):
+        for o in plan.outs:
+            o.fill_(12345)
+        graph.replay()
+        torch.cuda.synchronize()
+        res, ns2, lev2 = plan.results()
+        _check(hgs, qs, res)
+        assert np.array_equal(lev, lev2)
+    plan.free()
