@@ -296,9 +296,8 @@ def run_gi(args):
     for ev in evs:
         per_alg_ms += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_1805_00923_gb300 import replicas
+        total_ms = replicas.max_over_ranks(total_ms, device="cuda")
     value = world * edges.sum() / (total_ms * 1e-3) / 1e9
 
     # end to end through the C ABI from pinned host buffers
@@ -389,11 +388,6 @@ def run_only(args):
 def _events():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-
-def _traversed(tr, m, pull_dir):
-    t = tr.as_dict()
-    return int(sum(e for e in t["edges"]))
 
 
 def run_rmat24(args):

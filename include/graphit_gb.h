@@ -448,6 +448,18 @@ int gi_stats_reset(void);
  */
 int gi_stats_read(int32_t kclass, int64_t *launches, int64_t *timed_launches, double *timed_ms);
 
+/* ------------------------------------------------------- fault injection -- */
+/*
+ * Test hooks (host-side, process-wide; not in the paper).  After n more
+ * successful device allocations, every allocation the library attempts fails
+ * and the call returns GI_ERR_OOM (n < 0 turns the hook off).  Every call must
+ * release what it allocated on such a failure; gi_debug_pool_used reports the
+ * bytes currently allocated from the device's default pool, which the library
+ * allocates from, so a test can check that nothing leaked.
+ */
+int gi_debug_fail_allocs_after(int64_t n);
+int gi_debug_pool_used(int64_t *bytes);
+
 #ifdef __cplusplus
 }
 #endif

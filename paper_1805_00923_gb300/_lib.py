@@ -112,6 +112,8 @@ SIGNATURES = {
     "gi_batch_plan_launch": (ctypes.c_int, [_vp, _vp]),
     "gi_batch_plan_results": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "gi_batch_plan_free": (ctypes.c_int, [_vp]),
+    "gi_debug_fail_allocs_after": (ctypes.c_int, [_i64]),
+    "gi_debug_pool_used": (ctypes.c_int, [_P(_i64)]),
     "gi_stats_enable": (ctypes.c_int, [ctypes.c_int]),
     "gi_stats_reset": (ctypes.c_int, []),
     "gi_stats_read": (ctypes.c_int, [_i32, _P(_i64), _P(_i64), _P(ctypes.c_double)]),

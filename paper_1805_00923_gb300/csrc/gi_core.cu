@@ -84,7 +84,16 @@ void timing_end(int token, cudaStream_t s) {
 // freed memory (release threshold = max) so repeated graph loads reuse it.
 static std::once_flag g_pool_once[64];
 
+// test hook: after g_alloc_budget more successes every allocation fails (< 0: off)
+static std::atomic<long long> g_alloc_budget{-1};
+
 int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (g_alloc_budget.load() >= 0 && g_alloc_budget.fetch_sub(1) <= 0) {
+    g_alloc_budget.store(0);
+    set_error("device allocation of %zu bytes refused by the fault-injection hook", bytes);
+    return GI_ERR_OOM;
+  }
   int dev = 0;
   GI_CUDA(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64) {
@@ -134,16 +143,19 @@ struct Workspace {
   int32_t *tmp2_i32 = nullptr;     // n+1 scratch
 };
 
+static void ws_free(gi_graph *g, cudaStream_t s);
+
 static int ws_get(gi_graph *g, cudaStream_t s) {
   if (g->ws) return GI_OK;
   g->ws = new Workspace();
   int64_t nb = (g->n + 2047) / 2048 + 2;
   nb = nb < ((g->m + 255) / 256 + 2) ? ((g->m + 255) / 256 + 2) : nb;  // tile counts can exceed n/2048
-  GI_TRY(dev_alloc_n(&g->ws->scan_blocks, nb + 2048, s));
+  int st = dev_alloc_n(&g->ws->scan_blocks, nb + 2048, s);
   g->ws->scan_cap = nb + 2048;
-  GI_TRY(dev_alloc_n(&g->ws->tmp_i32, g->n + 2, s));
-  GI_TRY(dev_alloc_n(&g->ws->tmp2_i32, g->n + 2, s));
-  return GI_OK;
+  if (st == GI_OK) st = dev_alloc_n(&g->ws->tmp_i32, g->n + 2, s);
+  if (st == GI_OK) st = dev_alloc_n(&g->ws->tmp2_i32, g->n + 2, s);
+  if (st != GI_OK) ws_free(g, s);  // all or nothing
+  return st;
 }
 
 static void ws_free(gi_graph *g, cudaStream_t s) {
@@ -322,6 +334,23 @@ static int validate_csr_dev(gi_graph *g, const Csr &c, cudaStream_t s) {
 using namespace gi;
 
 extern "C" const char *gi_last_error(void) { return g_err; }
+
+extern "C" int gi_debug_fail_allocs_after(int64_t n) {
+  g_alloc_budget.store(n < 0 ? -1 : n);
+  return GI_OK;
+}
+
+extern "C" int gi_debug_pool_used(int64_t *bytes) {
+  GI_ARG(bytes != nullptr, "NULL output");
+  int dev = 0;
+  GI_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  GI_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t used = 0;
+  GI_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  *bytes = (int64_t)used;
+  return GI_OK;
+}
 
 extern "C" int gi_stats_enable(int timing_on) {
   g_timing.store(timing_on != 0);
@@ -582,34 +611,41 @@ int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cuda
   int64_t n = g->n;
   if (n == 0) return GI_OK;
   int32_t *cnt = g->ws->tmp_i32, *scnt = g->ws->tmp2_i32;
-  int32_t *off = nullptr, *soff = nullptr;
-  GI_TRY(dev_alloc_n(&off, n + 1, s));
-  GI_TRY(dev_alloc_n(&soff, n + 1, s));
-  k_tile_count<<<grid_for(g, n, 256), 256, 0, s>>>(c.ptr, n, tile_edges, tile_rows_for(tile_edges), cnt, scnt);
-  GI_LAUNCH_CHECK();
-  GI_TRY(scan_exclusive(g, cnt, off, n, s));
-  GI_TRY(scan_exclusive(g, scnt, soff, n, s));
-  int32_t totals[2];
-  GI_CUDA(cudaMemcpyAsync(&totals[0], off + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  GI_CUDA(cudaMemcpyAsync(&totals[1], soff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  GI_CUDA(cudaStreamSynchronize(s));
+  int32_t *off = nullptr, *soff = nullptr, *tile_row = nullptr;
+  int st = dev_alloc_n(&off, n + 1, s);
+  if (st == GI_OK) st = dev_alloc_n(&soff, n + 1, s);
+  if (st == GI_OK) {
+    k_tile_count<<<grid_for(g, n, 256), 256, 0, s>>>(c.ptr, n, tile_edges, tile_rows_for(tile_edges), cnt, scnt);
+    st = launch_status(1);
+  }
+  if (st == GI_OK) st = scan_exclusive(g, cnt, off, n, s);
+  if (st == GI_OK) st = scan_exclusive(g, scnt, soff, n, s);
+  int32_t totals[2] = {0, 0};
+  if (st == GI_OK &&
+      (cudaMemcpyAsync(&totals[0], off + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+       cudaMemcpyAsync(&totals[1], soff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess))
+    st = cuda_fail(cudaGetLastError(), "tile counts", __FILE__, __LINE__);
   ts->num_tiles = totals[0];
   ts->num_splits = totals[1];
-  int32_t *tile_row = nullptr;
-  GI_TRY(dev_alloc_n(&ts->tiles, ts->num_tiles, s));
-  GI_TRY(dev_alloc_n(&ts->splits, ts->num_splits, s));
-  GI_TRY(dev_alloc(&ts->partial, 16 * (size_t)(ts->num_tiles > 0 ? ts->num_tiles : 1), s));
-  GI_TRY(dev_alloc_n(&tile_row, ts->num_tiles, s));
-  k_tile_write<<<grid_for(g, n, 256), 256, 0, s>>>(c.ptr, n, tile_edges, off, soff, ts->tiles, ts->splits, tile_row);
-  GI_LAUNCH_CHECK();
-  if (ts->num_tiles > 0) {
+  if (st == GI_OK) st = dev_alloc_n(&ts->tiles, ts->num_tiles, s);
+  if (st == GI_OK) st = dev_alloc_n(&ts->splits, ts->num_splits, s);
+  if (st == GI_OK) st = dev_alloc(&ts->partial, 16 * (size_t)(ts->num_tiles > 0 ? ts->num_tiles : 1), s);
+  if (st == GI_OK) st = dev_alloc_n(&tile_row, ts->num_tiles, s);
+  if (st == GI_OK) {
+    k_tile_write<<<grid_for(g, n, 256), 256, 0, s>>>(c.ptr, n, tile_edges, off, soff, ts->tiles, ts->splits,
+                                                     tile_row);
+    st = launch_status(1);
+  }
+  if (st == GI_OK && ts->num_tiles > 0) {
     k_tile_close<<<grid_for(g, ts->num_tiles, 256), 256, 0, s>>>(ts->tiles, tile_row, c.ptr, ts->num_tiles, n);
-    GI_LAUNCH_CHECK();
+    st = launch_status(1);
   }
   dev_free(off, s);
   dev_free(soff, s);
   dev_free(tile_row, s);
-  return GI_OK;
+  if (st != GI_OK) free_tiles(ts, s);  // leaves ts empty (tile_edges 0: rebuilt on next use)
+  return st;
 }
 
 int use_tiles(gi_graph *g, int32_t tile_edges, cudaStream_t s) {
