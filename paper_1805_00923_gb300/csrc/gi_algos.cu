@@ -309,7 +309,15 @@ static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src,
   if (st == GI_OK)
     st = frontier_loop(g, P, sc, false, trace, s, [&](int32_t, int32_t dir) -> int {
       int r;
-      if (kernel_id == GI_K_CC) {
+      if (dir == GI_DIR_DENSE_PULL) {
+        // snap holds INT32_MAX outside the frontier, so the pull needs no
+        // frontier test: a non-member contributes the identity of min
+        GI_TRY(vset_clear(P.N, s));
+        OpMinInt op{x, snap, kernel_id == GI_K_CC ? nullptr : g->in.wt};
+        r = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, out_of(P.N), s, kClassMinPull,
+                              sc.balance == GI_BAL_VERTEX);
+        P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
+      } else if (kernel_id == GI_K_CC) {
         gi_cc_args a{x, snap};
         r = apply_dispatch(g, P.F, nullptr, dir, sc, GI_K_CC, &a, P.N, 0, s);
       } else {

@@ -355,3 +355,38 @@ def test_autotune_returns_valid_faster_schedule(gi, algo):
     else:
         assert _max_rel(_np(gi.pagerank_delta(g, 0.85, 1e-7, 10, sched=best)),
                         oracle.prdelta(hg, 0.85, 1e-7, 10)[0]) < PR_TOL
+
+
+# ------------------------------------------------------------ directed graphs
+
+def _directed(n, ne, seed, weights=False):
+    rng = np.random.default_rng(seed)
+    e = rng.integers(0, n, (ne, 2))
+    return gg.from_edge_list(n, map(tuple, e), symmetrize=False, weights=(seed, 1, 500) if weights else None)
+
+
+@pytest.mark.parametrize("direction", ["sparse_push", "dense_push", "dense_pull", "hybrid_pull"])
+def test_directed_graph_with_separate_in_edges(gi, direction):
+    """Pull directions read the in-edges loaded by gi_load_csc; results still match."""
+    hg = _directed(3000, 12000, 4, weights=True)
+    in_ptr, in_col, in_wt = gg.transpose(hg)
+    g = gi.Graph(hg.row_ptr, hg.col, hg.wt, symmetric=False, in_edges=(in_ptr, in_col, in_wt), validate=True)
+    sc = gi.schedule(direction)
+    for src in (0, 1234):
+        wd, wp, _ = oracle.bfs(hg, src, in_edges=(in_ptr, in_col))
+        d, p = gi.bfs(g, src, sched=sc)
+        assert np.array_equal(_np(d), wd) and np.array_equal(_np(p), wp)
+        assert np.array_equal(_np(gi.sssp(g, src, sched=sc)), oracle.sssp(hg, src)[0])
+    want = oracle.pagerank(hg, 0.85, 20, in_edges=(in_ptr, in_col))
+    pr_dir = "dense_push" if direction in ("sparse_push", "dense_push") else "dense_pull"
+    assert _max_rel(_np(gi.pagerank(g, 0.85, 20, sched=gi.schedule(pr_dir))), want) < PR_TOL
+
+
+def test_directed_graph_without_in_edges_rejects_pull(gi):
+    hg = _directed(100, 300, 5)
+    g = gi.Graph(hg.row_ptr, hg.col, symmetric=False)
+    with pytest.raises(gi.GIError) as e:
+        gi.bfs(g, 0, sched=gi.schedule("dense_pull"))
+    assert e.value.code == -6
+    d, _ = gi.bfs(g, 0, sched=gi.schedule("hybrid_pull"))   # hybrid falls back to push
+    assert np.array_equal(_np(d), oracle.bfs(hg, 0, in_edges=gg.transpose(hg)[:2])[0])
