@@ -361,8 +361,10 @@ typedef struct gi_batch_opts {
   int32_t selector;     /* BFS direction per level: GI_DIR_SPARSE_PUSH (always push),      */
                         /* GI_DIR_HYBRID_PULL (Beamer rule) or GI_DIR_LEARNED (the MLP)    */
   float alpha, beta;    /* Beamer constants                                                */
-  int64_t level_cap;    /* give up after this many levels (0 = n+2): GI_ERR_TIMEOUT       */
+  int64_t level_cap;    /* give up after this many levels (0 = 4n+16): GI_ERR_TIMEOUT     */
   int32_t *levels;      /* host, n_q entries or NULL: levels (BFS) / rounds (SSSP) run     */
+  float sssp_delta;     /* SSSP threshold step = sssp_delta x mean arc weight (0: 2.0;     */
+                        /* < 0: no threshold, every frontier source relaxed each round)    */
 } gi_batch_opts;
 
 void gi_batch_opts_default(gi_batch_opts *o);

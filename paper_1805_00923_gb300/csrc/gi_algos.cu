@@ -222,7 +222,7 @@ static int pull_available(gi_graph *g, int32_t dir) {
 // Frontier loop shared by BFS / SSSP / CC: decide, stop when empty, traverse.
 template <class Step>
 static int frontier_loop(gi_graph *g, VsetPair &P, const gi_schedule &sc, bool track_unvisited, gi_trace *tr,
-                         cudaStream_t s, Step step) {
+                         cudaStream_t s, Step step, bool pull_ok = true) {
   for (int32_t it = 0;; ++it) {
     DecideParams p = decide_params(sc, it, track_unvisited);
     GI_TRY(frontier_decide(g, P.F, p, s));
@@ -232,7 +232,8 @@ static int frontier_loop(gi_graph *g, VsetPair &P, const gi_schedule &sc, bool t
       break;
     }
     int32_t dir = (int32_t)g->ctrl_host[kDecision];
-    if (dir == GI_DIR_DENSE_PULL && !g->has_csc) dir = GI_DIR_DENSE_PUSH;
+    if (dir == GI_DIR_DENSE_PULL && (!g->has_csc || !pull_ok)) dir = GI_DIR_DENSE_PUSH;
+    g->ctrl_host[kDecision] = dir;
     trace_put(tr, it, g->ctrl_host);
     GI_TRY(step(it, dir));
     P.swap();
@@ -265,16 +266,21 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
   if (st == GI_OK) st = ctrl_init(g, g->n, g->m, s);
   if (st == GI_OK)
     st = frontier_loop(g, P, sc, true, trace, s, [&](int32_t it, int32_t dir) {
-      // push levels set depth only (no atomics on parents); the canonical
-      // parents of their vertices come from k_bfs_parents afterwards
-      gi_bfs_args a{depth, dir == GI_DIR_DENSE_PULL ? parent : nullptr, it + 1};
+      // with in-edges, push levels set depth only (no atomics on parents) and
+      // the canonical parents of their vertices come from k_bfs_parents
+      // afterwards; without in-edges push levels take the min with atomics
+      gi_bfs_args a{depth, (dir == GI_DIR_DENSE_PULL || !g->has_csc) ? parent : nullptr, it + 1};
       return apply_dispatch(g, P.F, nullptr, dir, sc, GI_K_BFS, &a, P.N, GI_NO_DEDUP, s);
     });
   if (st == GI_OK && parent) {
-    const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
-    k_bfs_parents<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->n, depth, parent, tw);
+    int launched = 0;
+    if (g->has_csc) {
+      const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
+      k_bfs_parents<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->n, depth, parent, tw);
+      ++launched;
+    }
     k_parent_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n);
-    st = launch_status(2);
+    st = launch_status(launched + 1);
   }
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
@@ -329,7 +335,7 @@ static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src,
       k_snap_reset<<<grid, 256, 0, s>>>(P.F->queue, P.F->count, snap);
       k_snap_set<<<grid, 256, 0, s>>>(P.N->queue, P.N->count, snap, x);
       return launch_status(2);
-    });
+    }, /*pull_ok=*/kernel_id == GI_K_CC || g->symmetric || g->in.wt != nullptr);
   dev_free(snap, s);
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)

@@ -14,6 +14,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <vector>
 
 #include "gi_features.cuh"
@@ -40,6 +41,7 @@ struct BatchGraph {
   const int32_t *ptr, *idx, *wt, *iptr, *iidx;
   int64_t n, m;
   int32_t maxdeg;
+  int32_t delta;  // SSSP distance-threshold step (0: relax every frontier source each round)
 };
 
 struct BatchQuery {
@@ -51,7 +53,8 @@ struct ClusterWs {  // per-cluster working memory (device pointers)
   int32_t *q[2];    // frontier queues
   int32_t *qd[2];   // SSSP: start-of-round distance of each queue entry
   uint32_t *inq;    // SSSP: dedup bitmap of the next frontier
-  int64_t *cnt;     // [0..2] rotating counts, [3..5] rotating out-degree sums, [6] claimed query
+  int64_t *cnt;     // [0..2] rotating counts, [3..5] rotating out-degree sums, [6] claimed query,
+                    // [8..11] rotating relaxed-source counts, [12..15] rotating minimum deferred distance
 };
 
 constexpr int kBT = 256;  // threads per CTA
@@ -124,9 +127,13 @@ __device__ __forceinline__ void strided_arcs(int32_t du, int32_t a, int32_t d, i
 }
 
 // du of a source: curd[i] (a snapshot), else the current value in live[u], else 0
-template <class Fn>
+struct KeepAll {
+  __device__ bool operator()(int32_t, int32_t) const { return true; }
+};
+
+template <class Fn, class Keep = KeepAll>
 __device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_t *curd, const int32_t *live,
-                           int64_t nf, int rank, int csize, Fn &fn) {
+                           int64_t nf, int rank, int csize, Fn &fn, Keep keep = Keep()) {
   __shared__ int32_t s_owner, s_a, s_d, s_du;
   __shared__ int32_t s_beg[kBT], s_off[kBT], s_dus[kBT], s_sw[32];
   __shared__ uint8_t s_own[kBT * 31];
@@ -138,8 +145,10 @@ __device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_
     if (i < nf) {
       const int32_t u = cur[i];
       du = curd ? curd[i] : (live ? *(volatile const int32_t *)(live + u) : 0);
-      a = __ldg(G.ptr + u);
-      d = __ldg(G.ptr + u + 1) - a;
+      if (keep(u, du)) {
+        a = __ldg(G.ptr + u);
+        d = __ldg(G.ptr + u + 1) - a;
+      }
     }
     while (true) {
       if (tid == 0) s_owner = -1;
@@ -281,8 +290,31 @@ __device__ void batch_bfs_pull(const BatchGraph &G, int32_t *depth, int32_t *nex
 // distances are the unique shortest distances, as with synchronous rounds;
 // the rounds and frontiers are not (the engine does not report them per
 // round).  Each improved destination joins the next queue once (dedup bitmap).
-__device__ void batch_sssp_push(const BatchGraph &G, int32_t *dist, const int32_t *cur, const int32_t *,
-                                int64_t nf, int32_t *next, int64_t *ncnt, uint32_t *inq, int rank, int csize) {
+//
+// With a threshold theta (G.delta > 0), a frontier source whose distance is
+// >= theta is not relaxed this round: it stays in the frontier, and the
+// smallest such distance is recorded so that theta can move past it when a
+// round relaxes nothing (a near/far ordering of the same label-correcting
+// relaxation; any order reaches the same distances).
+__device__ void batch_sssp_push(const BatchGraph &G, int32_t *dist, const int32_t *cur, int64_t nf, int32_t *next,
+                                int64_t *ncnt, uint32_t *inq, int64_t theta, int64_t *relaxed, int64_t *mindef,
+                                int rank, int csize) {
+  const int lane = threadIdx.x & 31;
+  auto keep = [&](int32_t u, int32_t du) -> bool {
+    const bool near = (int64_t)du < theta;
+    bool fresh = false;
+    if (!near) {
+      const uint32_t mask = 1u << (u & 31);
+      fresh = (atomicOr(inq + (u >> 5), mask) & mask) == 0;
+      atomicMin(reinterpret_cast<long long *>(mindef), (long long)du);
+    }
+    append_warp(fresh, u, next, ncnt);
+    const unsigned active = __activemask();
+    const unsigned ball = __ballot_sync(active, near);
+    if (ball && lane == __ffs(ball) - 1)
+      atomicAdd(reinterpret_cast<unsigned long long *>(relaxed), (unsigned long long)__popc(ball));
+    return near;
+  };
   auto fn = [&](int32_t du, int32_t e, int32_t v) {
     bool fresh = false;
     if (v >= 0) {
@@ -297,7 +329,7 @@ __device__ void batch_sssp_push(const BatchGraph &G, int32_t *dist, const int32_
     }
     append_warp(fresh, v, next, ncnt);
   };
-  cta_expand(G, cur, nullptr, dist, nf, rank, csize, fn);
+  cta_expand(G, cur, nullptr, dist, nf, rank, csize, fn, keep);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -333,6 +365,8 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
       for (int64_t w = gtid; w < (G.n + 31) / 32; w += T) W.inq[w] = 0u;
     if (gtid == 0) {
       for (int k = 0; k < 6; ++k) W.cnt[k] = 0;
+      for (int k = 8; k < 12; ++k) W.cnt[k] = 0;
+      for (int k = 12; k < 16; ++k) W.cnt[k] = INT64_MAX;
       W.cnt[0] = 1;
       W.cnt[3] = G.ptr[Q.src + 1] - G.ptr[Q.src];
       W.q[0][0] = Q.src;
@@ -343,6 +377,7 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
     csync(cl);
     int64_t nu = G.n, mu = G.m, nf_prev = 0;
     int32_t was_pull = 0, levels = 0;
+    int64_t theta = G.delta > 0 ? (int64_t)G.delta : INT64_MAX;
     for (int32_t L = 0;; ++L) {
       const int64_t nf = *(volatile int64_t *)(W.cnt + (L % 3));
       const int64_t mf = *(volatile int64_t *)(W.cnt + 3 + (L % 3));
@@ -355,6 +390,9 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
       if (gtid == 0) {
         W.cnt[(L + 2) % 3] = 0;
         W.cnt[3 + (L + 2) % 3] = 0;
+        // slots read at the end of round L-2 (barriers since), written in round L+2
+        W.cnt[8 + (L + 2) % 4] = 0;
+        W.cnt[12 + (L + 2) % 4] = INT64_MAX;
       }
       int32_t *cur = W.q[L & 1], *next = W.q[(L + 1) & 1];
       int64_t *ncnt = W.cnt + (L + 1) % 3, *necnt = W.cnt + 3 + (L + 1) % 3;
@@ -370,7 +408,8 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
         nf_prev = nf;
         csync(cl);
       } else {
-        batch_sssp_push(G, Q.out, cur, W.qd[L & 1], nf, next, ncnt, W.inq, rank, csize);
+        batch_sssp_push(G, Q.out, cur, nf, next, ncnt, W.inq, theta, W.cnt + 8 + L % 4, W.cnt + 12 + L % 4,
+                        rank, csize);
         csync(cl);
         const int64_t nn = *(volatile int64_t *)ncnt;
         for (int64_t i = gtid; i < nn; i += T) {
@@ -378,6 +417,8 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
           atomicAnd(W.inq + (v >> 5), ~(1u << (v & 31)));
         }
         csync(cl);
+        if (G.delta > 0 && *(volatile int64_t *)(W.cnt + 8 + L % 4) == 0)
+          theta = *(volatile int64_t *)(W.cnt + 12 + L % 4) + G.delta;  // nothing was near: move past the nearest
       }
     }
     if (gtid == 0 && q_ns) q_ns[qi] = (int64_t)(global_ns() - t0);
@@ -436,7 +477,13 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
   for (int i = 0; i < n_graphs; ++i) {
     const gi_graph *g = graphs[i];
     GI_ARG(g != nullptr, "NULL graph");
-    hg[i] = BatchGraph{g->out.ptr, g->out.idx, g->out.wt, g->in.ptr, g->in.idx, g->n, g->m, g->max_deg};
+    int32_t delta = 0;
+    if (g->out.wt && o.sssp_delta >= 0.0f) {
+      const double scale = o.sssp_delta > 0.0f ? o.sssp_delta : 2.0;
+      delta = (int32_t)fmin(scale * g->wt_mean + 0.5, 1e9);
+      if (delta < 1) delta = 1;
+    }
+    hg[i] = BatchGraph{g->out.ptr, g->out.idx, g->out.wt, g->in.ptr, g->in.idx, g->n, g->m, g->max_deg, delta};
     nmax = g->n > nmax ? g->n : nmax;
   }
   std::vector<BatchQuery> hq(n_q);
@@ -464,7 +511,7 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
   p->selector = o.selector;
   p->alpha = o.alpha;
   p->beta = o.beta;
-  p->cap = o.level_cap > 0 ? o.level_cap : nmax + 2;
+  p->cap = o.level_cap > 0 ? o.level_cap : 4 * nmax + 16;  // threshold rounds can exceed n
   const int64_t words = (nmax + 31) / 32;
   const int64_t per = 4 * nmax + words;  // 2 queues + 2 distance queues + bitmap, in int32 words
   std::vector<ClusterWs> hws(p->clusters);
@@ -473,7 +520,7 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
   if (st == GI_OK) st = dev_alloc_n(&p->dws, p->clusters, s);
   if (st == GI_OK) st = dev_alloc_n(&p->work, 2, s);
   if (st == GI_OK) st = dev_alloc_n(&p->slab, per * p->clusters, s);
-  if (st == GI_OK) st = dev_alloc_n(&p->cnts, 8 * p->clusters, s);
+  if (st == GI_OK) st = dev_alloc_n(&p->cnts, 16 * p->clusters, s);
   if (st == GI_OK) st = dev_alloc_n(&p->dns, n_q, s);
   if (st == GI_OK) st = dev_alloc_n(&p->dlev, n_q, s);
   if (st == GI_OK) {
@@ -484,7 +531,7 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
       hws[c].qd[0] = b + 2 * nmax;
       hws[c].qd[1] = b + 3 * nmax;
       hws[c].inq = reinterpret_cast<uint32_t *>(b + 4 * nmax);
-      hws[c].cnt = p->cnts + 8 * c;
+      hws[c].cnt = p->cnts + 16 * c;
     }
     if (cudaMemcpyAsync(p->dg, hg.data(), sizeof(BatchGraph) * n_graphs, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(p->dq, hq.data(), sizeof(BatchQuery) * n_q, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -573,4 +620,5 @@ extern "C" void gi_batch_opts_default(gi_batch_opts *o) {
   o->beta = 24.0f;
   o->level_cap = 0;
   o->levels = nullptr;
+  o->sssp_delta = 0.0f;
 }

@@ -298,6 +298,14 @@ __global__ void k_degrees(const int32_t *__restrict__ ptr, int64_t n, int32_t *_
   if ((threadIdx.x & 31) == 0) atomicMax(max_deg, local_max);
 }
 
+__global__ void k_sum_weights(const int32_t *__restrict__ wt, int64_t m, unsigned long long *out) {
+  unsigned long long s = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    s += (unsigned long long)(long long)wt[e];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
 static int copy_in(int32_t **dst, const int32_t *src, int64_t count, uint32_t flags, cudaStream_t s) {
   GI_TRY(dev_alloc_n(dst, count, s));
   if (count > 0)
@@ -467,6 +475,19 @@ extern "C" int gi_load_csr(const int32_t *offsets, const int32_t *indices, const
       break;
     }
     g->max_deg = (int32_t)(md & 0xffffffff);
+    if (weights && m > 0) {
+      unsigned long long wsum = 0;
+      if (cudaMemsetAsync(g->ctrl + kErr, 0, sizeof(int64_t), s) != cudaSuccess) { st = GI_ERR_CUDA; break; }
+      k_sum_weights<<<grid_for(g, m, 256), 256, 0, s>>>(g->out.wt, m,
+                                                        reinterpret_cast<unsigned long long *>(g->ctrl + kErr));
+      if ((st = launch_status(1)) != GI_OK) break;
+      if (cudaMemcpyAsync(&wsum, g->ctrl + kErr, sizeof(wsum), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        st = cuda_fail(cudaGetLastError(), "weight sum", __FILE__, __LINE__);
+        break;
+      }
+      g->wt_mean = (double)(long long)wsum / (double)m;
+    }
     if (g->symmetric) {
       g->in = g->out;
       g->has_csc = true;

@@ -116,6 +116,7 @@ struct Workspace;  // per-graph scratch (frontiers, buffers); defined in gi_core
 struct gi_graph {
   int64_t n = 0, m = 0;
   int32_t max_deg = 0;
+  double wt_mean = 0.0;          // mean arc weight (0 without weights)
   bool symmetric = false;
   bool has_csc = false;
   gi::Csr out;            // CSR (out-edges)

@@ -41,6 +41,10 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
       }
       case GI_K_SSSP: {
         const gi_sssp_args *a = static_cast<const gi_sssp_args *>(args);
+        if (!g->symmetric && g->in.wt == nullptr) {
+          gi::set_error("pull SSSP needs in-edge weights (gi_load_csc with weights)");
+          return GI_ERR_UNSUPPORTED;
+        }
         OpMinInt op{a->dist, a->snap, g->in.wt};
         GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, F, to_bm, o, s, kClassMinPull, vp));
         break;

@@ -108,3 +108,13 @@ def test_batch_plan_graph_capture_replay(gi):
         _check(hgs, qs, res)
         assert np.array_equal(lev, lev2)
     plan.free()
+
+
+@pytest.mark.parametrize("delta", [-1.0, 0.5, 2.0, 20.0])
+def test_batch_sssp_threshold_orders(gi, delta):
+    """Any distance-threshold step (or none) gives the oracle's distances."""
+    hgs = [grid(48, weights=True), rmat(12, weights=True), adversarial("hub_tail", True)]
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    qs = [(k, s, "sssp") for k in range(3) for s in (0, 7, hgs[k].n - 1)]
+    res, _ = gi.batch_run(gs, qs, opts=gi.batch_opts(cluster_size=2, sssp_delta=delta))
+    _check(hgs, qs, res)
