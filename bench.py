@@ -324,6 +324,27 @@ def run_gi(args):
             e2e_edges += sum(ed)
     e2e_value = world * e2e_edges / (sum(e2e_ms) * 1e-3) / 1e9
 
+    # learned vs heuristic direction selection on the same graph (BFS from 8 sources; untimed extra)
+    selector = None
+    if not args.no_extras:
+        from paper_1805_00923_gb300 import selector as sel
+        sel.install()
+        srcs = gg.pick_sources(hg, 8, seed=7)
+        selector = {}
+        for pol in ("hybrid_pull", "learned"):
+            ms, ed = 0.0, 0
+            for s_ in srcs:
+                tr = gi.Trace(64)
+                gi.bfs(g, int(s_), want_parent=False, sched=gi.schedule(pol), trace=tr)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                gi.bfs(g, int(s_), want_parent=False, sched=gi.schedule(pol), trace=tr)
+                e1.record()
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                ed += int(tr.as_dict()["edges"].sum())
+            selector["bfs_" + ("beamer" if pol == "hybrid_pull" else "learned") + "_gteps"] = ed / (ms * 1e-3) / 1e9
+
     peak, peak_kind = measured_hbm()
     bytes_per_launch = 4 * m + 16 * n + 4
     avg_ms = pr_ms / max(pr_launches, 1)
@@ -347,7 +368,7 @@ def run_gi(args):
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": sum(e2e_ms) / max(len(e2e_ms), 1)},
             "gpu_launches": launches, "clocks": clocks,
-            "autotuned": tuned, "pagerank_direction_gteps": compare}
+            "autotuned": tuned, "pagerank_direction_gteps": compare, "selector": selector}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, iters, t = oracle_sample(hg, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",

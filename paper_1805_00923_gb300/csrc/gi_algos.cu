@@ -104,7 +104,8 @@ __global__ void k_scale_f64(float *x, int64_t n, const double *__restrict__ part
 
 // PageRankDelta vertex filter after a push round (Fig. 1): Delta, Rank,
 // DeltaSum reset, next frontier (bitmap word per warp + queue), next contrib.
-__global__ void k_prd_vertex(double *dsum, float *rank, float *contrib_out, const float *__restrict__ inv_deg,
+template <class A>
+__global__ void k_prd_vertex(A *dsum, float *rank, float *contrib_out, const float *__restrict__ inv_deg,
                              int64_t n, float damping, float first_base, float inv_n, float eps, int32_t first_round,
                              uint32_t *out_bm, int32_t *out_q, int32_t *out_qc) {
   const int lane = threadIdx.x & 31;
@@ -124,7 +125,7 @@ __global__ void k_prd_vertex(double *dsum, float *rank, float *contrib_out, cons
         r += delta;
       }
       rank[v] = r;
-      dsum[v] = 0.0;
+      dsum[v] = 0;
       active = fabsf(delta) > eps * r;
       contrib_out[v] = active ? delta * inv_deg[v] : 0.0f;
     }
@@ -135,6 +136,35 @@ __global__ void k_prd_vertex(double *dsum, float *rank, float *contrib_out, cons
       if (lane == 0) base = atomicAdd(out_qc, __popc(word));
       base = __shfl_sync(0xffffffffu, base, 0);
       if (active) out_q[base + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
+    }
+  }
+}
+
+// Segmented min pull, vertex pass: x[v] = min(x[v], acc[v]) (acc holds the
+// minimum over all segments), marks lowered vertices (bitmap word per warp +
+// queue) and resets acc for the next round.
+__global__ void k_min_apply(int32_t *x, int32_t *acc, int64_t n, uint32_t *out_bm, int32_t *out_q, int32_t *out_qc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (n + 31) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t v = w * 32 + lane;
+    bool low = false;
+    if (v < n) {
+      const int32_t c = acc[v];
+      acc[v] = INT32_MAX;
+      if (c < x[v]) {
+        x[v] = c;
+        low = true;
+      }
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, low);
+    if (lane == 0) out_bm[w] = word;
+    if (word) {
+      int32_t base = 0;
+      if (lane == 0) base = atomicAdd(out_qc, __popc(word));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (low) out_q[base + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
     }
   }
 }
@@ -296,9 +326,17 @@ static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src,
                         gi_trace *trace, cudaStream_t s) {
   GI_TRY(ensure_tiles(g, sc, s));
   VsetPair P;
-  int32_t *snap = nullptr;
+  int32_t *snap = nullptr, *seg_acc = nullptr;
   int st = pair_alloc(g, P, s);
   if (st == GI_OK) st = dev_alloc_n(&snap, g->n, s);
+  if (st == GI_OK && sc.num_segments > 1 && g->has_csc) {
+    if (g->segs.num != sc.num_segments) st = gi_graph_build_segments(g, sc.num_segments, s);
+    if (st == GI_OK) st = dev_alloc_n(&seg_acc, g->n, s);
+    if (st == GI_OK) {
+      k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(seg_acc, g->n, INT32_MAX);
+      st = launch_status(1);
+    }
+  }
   if (st == GI_OK) {
     if (kernel_id == GI_K_CC) {
       k_iota2<<<grid_for(g, g->n, 256), 256, 0, s>>>(x, snap, g->n);
@@ -315,7 +353,20 @@ static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src,
   if (st == GI_OK)
     st = frontier_loop(g, P, sc, false, trace, s, [&](int32_t, int32_t dir) -> int {
       int r;
-      if (dir == GI_DIR_DENSE_PULL) {
+      if (dir == GI_DIR_DENSE_PULL && seg_acc) {
+        // cache-partitioned pull: one source segment at a time folds its
+        // minimum into seg_acc (no atomics: each destination row belongs to
+        // one tile), then one vertex pass applies and marks
+        GI_TRY(vset_clear(P.N, s));
+        for (int sid = 0; sid < g->segs.num; ++sid) {
+          OpMinInt op{seg_acc, snap, kernel_id == GI_K_CC ? nullptr : g->segs.seg[sid].wt};
+          GI_TRY(launch_pull_tiled(g, op, g->segs.seg[sid], g->segs.tiles[sid], nullptr, nullptr, OutSet(), s,
+                                   kClassMinPull));
+        }
+        k_min_apply<<<grid_for(g, g->n, 256), 256, 0, s>>>(x, seg_acc, g->n, P.N->bitmap, P.N->queue, P.N->count);
+        r = launch_status(1);
+        P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
+      } else if (dir == GI_DIR_DENSE_PULL) {
         // snap holds INT32_MAX outside the frontier, so the pull needs no
         // frontier test: a non-member contributes the identity of min
         GI_TRY(vset_clear(P.N, s));
@@ -337,6 +388,7 @@ static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src,
       return launch_status(2);
     }, /*pull_ok=*/kernel_id == GI_K_CC || g->symmetric || g->in.wt != nullptr);
   dev_free(snap, s);
+  dev_free(seg_acc, s);
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "minlabel", __FILE__, __LINE__);
@@ -467,12 +519,19 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
   GI_TRY(ensure_tiles(g, sc, s));
   const float inv_n = 1.0f / (float)g->n, first_base = (1.0f - damping) / (float)g->n;
   VsetPair P;
-  float *cb[2] = {nullptr, nullptr};
+  float *cb[2] = {nullptr, nullptr}, *seg_sum = nullptr;
   double *dsum = nullptr;
   int st = pair_alloc(g, P, s);
   if (st == GI_OK) st = dev_alloc_n(&cb[0], g->n, s);
   if (st == GI_OK) st = dev_alloc_n(&cb[1], g->n, s);
   if (st == GI_OK) st = dev_alloc_n(&dsum, g->n, s);
+  const bool segmented = sc.num_segments > 1 && g->has_csc;
+  if (st == GI_OK && segmented) {
+    if (g->segs.num != sc.num_segments) st = gi_graph_build_segments(g, sc.num_segments, s);
+    if (st == GI_OK) st = dev_alloc_n(&seg_sum, g->n, s);
+    if (st == GI_OK && cudaMemsetAsync(seg_sum, 0, sizeof(float) * g->n, s) != cudaSuccess)
+      st = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__);
+  }
   if (st == GI_OK) {
     k_fill_f32<<<grid_for(g, g->n, 256), 256, 0, s>>>(rank, g->n, 0.0f);
     k_pr_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(cb[0], g->inv_out_deg, g->n, inv_n);
@@ -496,7 +555,20 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
     trace_put(trace, round - 1, g->ctrl_host);
     if ((st = vset_clear(P.N, s)) != GI_OK) break;
     float *cin = cb[cur], *cout = cb[cur ^ 1];
-    if (dir == GI_DIR_DENSE_PULL) {
+    if (dir == GI_DIR_DENSE_PULL && segmented) {
+      // cache-partitioned pull: segments add into seg_sum, then the vertex filter
+      for (int sid = 0; sid < g->segs.num && st == GI_OK; ++sid) {
+        OpSum op{cin, seg_sum};
+        st = launch_pull_tiled(g, op, g->segs.seg[sid], g->segs.tiles[sid], nullptr, nullptr, OutSet(), s,
+                               kClassPrdPull);
+      }
+      if (st == GI_OK) {
+        k_prd_vertex<<<grid_for(g, g->n, 256), 256, 0, s>>>(seg_sum, rank, cout, g->inv_out_deg, g->n, damping,
+                                                            first_base, inv_n, eps, round == 1 ? 1 : 0, P.N->bitmap,
+                                                            P.N->queue, P.N->count);
+        st = launch_status(1);
+      }
+    } else if (dir == GI_DIR_DENSE_PULL) {
       OpPRD op{cin, cout, rank, g->inv_out_deg, damping, first_base, inv_n, eps, round == 1 ? 1 : 0};
       st = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, out_of(P.N), s, kClassPrdPull,
                              sc.balance == GI_BAL_VERTEX);
@@ -517,6 +589,7 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
   dev_free(cb[0], s);
   dev_free(cb[1], s);
   dev_free(dsum, s);
+  dev_free(seg_sum, s);
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "prdelta", __FILE__, __LINE__);

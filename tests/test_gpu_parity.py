@@ -390,3 +390,22 @@ def test_directed_graph_without_in_edges_rejects_pull(gi):
     assert e.value.code == -6
     d, _ = gi.bfs(g, 0, sched=gi.schedule("hybrid_pull"))   # hybrid falls back to push
     assert np.array_equal(_np(d), oracle.bfs(hg, 0, in_edges=gg.transpose(hg)[:2])[0])
+
+
+@pytest.mark.parametrize("segs", [2, 5])
+def test_segmented_pull_all_algorithms(gi, segs):
+    """Cache-partitioned (segmented) pull for PR, PRD, CC and SSSP matches the oracle."""
+    hg = rmat(14, weights=True)
+    g = _load(gi, hg)
+    sc = gi.schedule("dense_pull", num_segments=segs)
+    assert _max_rel(_np(gi.pagerank(g, 0.85, 20, sched=sc)), oracle.pagerank(hg, 0.85, 20)) < PR_TOL
+    want, _ = oracle.prdelta(hg, 0.85, 1e-7, 10)
+    assert _max_rel(_np(gi.pagerank_delta(g, 0.85, 1e-7, 10, sched=sc)), want) < PR_TOL
+    want, fs = oracle.cc(hg)
+    tr = gi.Trace(64)
+    assert np.array_equal(_np(gi.cc(g, sched=sc, trace=tr)), want)
+    assert np.array_equal(tr.as_dict()["frontier"], fs)
+    want, fs = oracle.sssp(hg, 9)
+    tr = gi.Trace(256)
+    assert np.array_equal(_np(gi.sssp(g, 9, sched=sc, trace=tr)), want)
+    assert np.array_equal(tr.as_dict()["frontier"], fs)
