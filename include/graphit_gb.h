@@ -161,10 +161,15 @@ typedef struct gi_schedule {
   int32_t tile_edges;   /* pull tiles: arcs per tile (power of two, 256..8192; 256 =   */
                         /* one warp per tile, larger = one block per tile)            */
   int32_t t_heavy;      /* edge-aware push: degree >= t_heavy is split over all blocks */
+  int32_t persistent;   /* gi_bfs / gi_sssp: 1 = run every level inside one cooperative */
+                        /* persistent kernel (the batched engine's whole-GPU mode), the */
+                        /* direction chosen on the device (LEARNED: the MLP; SPARSE_PUSH */
+                        /* or DENSE_PUSH: push only; otherwise Beamer's rule); the trace */
+                        /* then records only the level count.  0 = one launch per level. */
 } gi_schedule;
 
 /* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment, 256 threads, t_warp 32,
- * t_cta 1024, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 16384. */
+ * t_cta 1024, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 16384, not persistent. */
 void gi_schedule_default(gi_schedule *s);
 
 /* ------------------------------------------------------------ edgeset apply -- */
@@ -356,7 +361,10 @@ int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, const gi_sc
  * another.
  */
 typedef struct gi_batch_opts {
-  int32_t cluster_size; /* CTAs per query: 1, 2, 4 or 8 (default 4)                       */
+  int32_t cluster_size; /* CTAs per query: 1, 2, 4 or 8 (default 4); 0 = whole GPU: every  */
+                        /* co-resident block (cooperative launch) works on one query at a */
+                        /* time, levels separated by a software grid barrier whose wait   */
+                        /* gives up after ~2 s with GI_ERR_TIMEOUT                         */
   int32_t clusters;     /* clusters launched; 0 = SM count / cluster_size                  */
   int32_t selector;     /* BFS direction per level: GI_DIR_SPARSE_PUSH (always push),      */
                         /* GI_DIR_HYBRID_PULL (Beamer rule) or GI_DIR_LEARNED (the MLP)    */
@@ -461,6 +469,13 @@ int gi_stats_read(int32_t kclass, int64_t *launches, int64_t *timed_launches, do
  */
 int gi_debug_fail_allocs_after(int64_t n);
 int gi_debug_pool_used(int64_t *bytes);
+/*
+ * The grid barrier of the whole-GPU persistent mode (gi_batch_opts.cluster_size
+ * = 0) waits for k more arrivals than there are blocks, so its bounded wait
+ * (about 2 s) runs out: the kernel then stops and the call returns
+ * GI_ERR_TIMEOUT with the context intact.  k = 0 restores normal operation.
+ */
+int gi_debug_barrier_phantoms(int32_t k);
 
 #ifdef __cplusplus
 }

@@ -275,6 +275,32 @@ static int frontier_loop(gi_graph *g, VsetPair &P, const gi_schedule &sc, bool t
 
 using namespace gi;
 
+// Single query in the batched engine's whole-GPU persistent mode.
+static int run_persistent(gi_graph *g, int32_t algo, int32_t src, int32_t *out, const gi_schedule &sc,
+                          gi_trace *trace, cudaStream_t s) {
+  gi_batch_opts o;
+  gi_batch_opts_default(&o);
+  o.cluster_size = 0;
+  o.selector = sc.direction == GI_DIR_LEARNED
+                   ? GI_DIR_LEARNED
+                   : ((sc.direction == GI_DIR_SPARSE_PUSH || sc.direction == GI_DIR_DENSE_PUSH || !g->has_csc)
+                          ? GI_DIR_SPARSE_PUSH
+                          : GI_DIR_HYBRID_PULL);
+  o.alpha = sc.alpha > 0 ? sc.alpha : 14.0f;
+  o.beta = sc.beta > 0 ? sc.beta : 24.0f;
+  gi_graph *gs[1] = {g};
+  int32_t *outs[1] = {out};
+  const int32_t qg = 0, qs = src, qa = algo;
+  gi_batch_plan *p = nullptr;
+  GI_TRY(gi_batch_plan_create(gs, 1, &qg, &qs, &qa, 1, outs, &o, s, &p));
+  int32_t levels = 0;
+  int st = gi_batch_plan_launch(p, s);
+  if (st == GI_OK) st = gi_batch_plan_results(p, nullptr, &levels, s);
+  const int st2 = gi_batch_plan_free(p);
+  if (trace) trace->iterations = levels;
+  return st != GI_OK ? st : st2;
+}
+
 // ===================================================================== BFS ==
 extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent, const gi_schedule *sched,
                       gi_trace *trace, void *stream) {
@@ -285,6 +311,19 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
   cudaStream_t s = (cudaStream_t)stream;
   const gi_schedule sc = *sched;
   if (sc.direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sc.direction));
+  if (sc.persistent && (!parent || g->has_csc)) {
+    // depths in one persistent launch; canonical parents by the in-edge pass
+    GI_TRY(run_persistent(g, GI_ALGO_BFS, src, depth, sc, trace, s));
+    if (!parent) return GI_OK;
+    k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n, INT32_MAX);
+    k_set_one<<<1, 1, 0, s>>>(parent, src, src);
+    const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
+    k_bfs_parents<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->n, depth, parent, tw);
+    k_parent_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n);
+    GI_TRY(launch_status(4));
+    GI_CUDA(cudaStreamSynchronize(s));
+    return GI_OK;
+  }
   GI_TRY(ensure_tiles(g, sc, s));
   VsetPair P;
   int st = pair_alloc(g, P, s);
@@ -406,6 +445,7 @@ extern "C" int gi_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedul
   if (sched->direction == GI_DIR_DENSE_PULL || sched->direction == GI_DIR_HYBRID_PULL) {
     GI_ARG(g->symmetric || g->in.wt != nullptr, "pull SSSP needs in-edge weights (gi_load_csc with weights)");
   }
+  if (sched->persistent) return run_persistent(g, GI_ALGO_SSSP, src, dist, *sched, trace, (cudaStream_t)stream);
   return minlabel_run(g, dist, GI_K_SSSP, src, *sched, trace, (cudaStream_t)stream);
 }
 

@@ -64,6 +64,67 @@ __device__ __forceinline__ void csync(cg::cluster_group &cl) {
   cl.sync();
 }
 
+// Software barrier over the whole (cooperatively launched, hence co-resident)
+// grid: arrival counter + generation word.  The wait gives up after
+// kBarrierLimitNs of %globaltimer time, sets *err = 2 and reports failure, so
+// a broken barrier ends the kernel instead of hanging it.  The verdict is
+// taken by thread 0 and shared through shared memory, so a block decides
+// uniformly.  `nblocks` is the arrival count that releases the barrier.
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long barrier_clock() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool grid_sync(unsigned *count, unsigned *gen, unsigned nblocks, int32_t *err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    __threadfence();
+    const unsigned g0 = *(volatile unsigned *)gen;
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      *(volatile unsigned *)count = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = barrier_clock();
+      while (*(volatile unsigned *)gen == g0) {
+        if (barrier_clock() - t0 > kBarrierLimitNs) {
+          atomicExch(err, 2);
+          ok = false;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = ok && *(volatile int32_t *)err == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// One barrier interface for both launch shapes: a hardware cluster barrier
+// (cluster mode) or the bounded software grid barrier (whole-GPU mode).
+template <bool kGrid>
+struct Barrier {
+  unsigned *count, *gen;
+  int32_t *err;
+  int32_t phantoms;  // extra arrivals expected (a test hook; 0 in normal use)
+  __device__ bool operator()() const {
+    if constexpr (kGrid) {
+      return grid_sync(count, gen, gridDim.x + (unsigned)phantoms, err);
+    } else {
+      cg::cluster_group cl = cg::this_cluster();
+      csync(cl);
+      return true;
+    }
+  }
+};
+
 // learned / rule decision for BFS level, computed identically by every CTA
 __device__ bool batch_decide_pull(const BatchGraph &G, int64_t nf, int64_t mf, int64_t nu, int64_t mu, int32_t level,
                                   int32_t was_pull, int64_t nf_prev, int mode, float alpha, float beta, float *sh) {
@@ -338,12 +399,23 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+template <bool kGrid>
 __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ graphs,
                                                const BatchQuery *__restrict__ queries, int32_t n_q,
                                                int32_t *work, ClusterWs *ws, int64_t *q_ns, int32_t *q_levels,
-                                               int mode, float alpha, float beta, int64_t level_cap, int32_t *err) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
+                                               int mode, float alpha, float beta, int64_t level_cap, int32_t *err,
+                                               int32_t phantoms) {
+  int rank, csize;
+  if constexpr (kGrid) {
+    rank = blockIdx.x;
+    csize = gridDim.x;
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    rank = (int)cl.block_rank();
+    csize = (int)cl.num_blocks();
+  }
+  const Barrier<kGrid> bar{reinterpret_cast<unsigned *>(work + 2), reinterpret_cast<unsigned *>(work + 3), err,
+                           phantoms};
   const int cid = blockIdx.x / csize;
   const int64_t T = (int64_t)csize * kBT;
   const int64_t gtid = (int64_t)rank * kBT + threadIdx.x;
@@ -351,9 +423,9 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
   __shared__ float sh[16 + 64 + 64 + 4];
   while (true) {
     if (rank == 0 && threadIdx.x == 0) W.cnt[6] = atomicAdd(work, 1);
-    csync(cl);
+    if (!bar()) return;
     const int32_t qi = (int32_t)*(volatile int64_t *)(W.cnt + 6);
-    csync(cl);  // everyone has read the claim before it can be overwritten
+    if (!bar()) return;  // everyone has read the claim before it can be overwritten
     if (qi >= n_q) break;
     const BatchQuery Q = queries[qi];
     const BatchGraph G = graphs[Q.graph];
@@ -372,9 +444,9 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
       W.q[0][0] = Q.src;
       W.qd[0][0] = 0;
     }
-    csync(cl);
+    if (!bar()) return;
     if (gtid == 0) Q.out[Q.src] = 0;
-    csync(cl);
+    if (!bar()) return;
     int64_t nu = G.n, mu = G.m, nf_prev = 0;
     int32_t was_pull = 0, levels = 0;
     int64_t theta = G.delta > 0 ? (int64_t)G.delta : INT64_MAX;
@@ -406,30 +478,39 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
         else batch_bfs_push(G, Q.out, cur, nf, next, ncnt, necnt, L, rank, csize);
         was_pull = pull ? 1 : 0;
         nf_prev = nf;
-        csync(cl);
+        if (!bar()) return;
       } else {
         batch_sssp_push(G, Q.out, cur, nf, next, ncnt, W.inq, theta, W.cnt + 8 + L % 4, W.cnt + 12 + L % 4,
                         rank, csize);
-        csync(cl);
+        if (!bar()) return;
         const int64_t nn = *(volatile int64_t *)ncnt;
         for (int64_t i = gtid; i < nn; i += T) {
           const int32_t v = next[i];
           atomicAnd(W.inq + (v >> 5), ~(1u << (v & 31)));
         }
-        csync(cl);
+        if (!bar()) return;
         if (G.delta > 0 && *(volatile int64_t *)(W.cnt + 8 + L % 4) == 0)
           theta = *(volatile int64_t *)(W.cnt + 12 + L % 4) + G.delta;  // nothing was near: move past the nearest
       }
     }
     if (gtid == 0 && q_ns) q_ns[qi] = (int64_t)(global_ns() - t0);
     if (gtid == 0 && q_levels) q_levels[qi] = levels;
-    csync(cl);
+    if (!bar()) return;
   }
 }
 
 }  // namespace gi
 
 using namespace gi;
+
+// test hook (gi_debug_barrier_phantoms): extra arrivals the grid barrier waits for
+static int32_t g_barrier_phantoms = 0;
+
+extern "C" int gi_debug_barrier_phantoms(int32_t k) {
+  GI_ARG(k >= 0 && k <= 1024, "phantom count must be in [0, 1024]");
+  g_barrier_phantoms = k;
+  return GI_OK;
+}
 
 struct gi_batch_plan {
   gi::BatchGraph *dg = nullptr;
@@ -439,7 +520,7 @@ struct gi_batch_plan {
   int32_t *slab = nullptr;
   int64_t *cnts = nullptr, *dns = nullptr;
   int32_t *dlev = nullptr;
-  int32_t n_q = 0, clusters = 0, cluster_size = 0, selector = 0;
+  int32_t n_q = 0, clusters = 0, cluster_size = 0, selector = 0, grid_blocks = 0;
   float alpha = 14.0f, beta = 24.0f;
   int64_t cap = 0;
   int32_t *levels_host = nullptr;
@@ -468,8 +549,9 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
   gi_batch_opts o;
   gi_batch_opts_default(&o);
   if (opts) o = *opts;
-  GI_ARG(o.cluster_size == 1 || o.cluster_size == 2 || o.cluster_size == 4 || o.cluster_size == 8,
-         "cluster_size must be 1, 2, 4 or 8");
+  GI_ARG(o.cluster_size == 0 || o.cluster_size == 1 || o.cluster_size == 2 || o.cluster_size == 4 ||
+             o.cluster_size == 8,
+         "cluster_size must be 0 (whole GPU), 1, 2, 4 or 8");
   GI_ARG(o.selector == GI_DIR_SPARSE_PUSH || o.selector == GI_DIR_HYBRID_PULL || o.selector == GI_DIR_LEARNED,
          "selector must be GI_DIR_SPARSE_PUSH, GI_DIR_HYBRID_PULL or GI_DIR_LEARNED");
   std::vector<BatchGraph> hg(n_graphs);
@@ -505,9 +587,21 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
   gi_batch_plan *p = new gi_batch_plan();
   p->n_q = n_q;
   p->cluster_size = o.cluster_size;
-  p->clusters = o.clusters > 0 ? o.clusters : sms / o.cluster_size;
-  if (p->clusters > n_q) p->clusters = n_q;
-  if (p->clusters < 1) p->clusters = 1;
+  if (o.cluster_size == 0) {
+    // whole-GPU mode: one group of every co-resident block (cooperative launch)
+    int per_sm = 0;
+    GI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<true>, kBT, 0));
+    if (per_sm < 1) {
+      set_error("the persistent kernel does not fit on an SM");
+      return GI_ERR_UNSUPPORTED;
+    }
+    p->clusters = 1;
+    p->grid_blocks = sms * (per_sm < 2 ? per_sm : 2);
+  } else {
+    p->clusters = o.clusters > 0 ? o.clusters : sms / o.cluster_size;
+    if (p->clusters > n_q) p->clusters = n_q;
+    if (p->clusters < 1) p->clusters = 1;
+  }
   p->selector = o.selector;
   p->alpha = o.alpha;
   p->beta = o.beta;
@@ -518,7 +612,7 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
   int st = dev_alloc_n(&p->dg, n_graphs, s);
   if (st == GI_OK) st = dev_alloc_n(&p->dq, n_q, s);
   if (st == GI_OK) st = dev_alloc_n(&p->dws, p->clusters, s);
-  if (st == GI_OK) st = dev_alloc_n(&p->work, 2, s);
+  if (st == GI_OK) st = dev_alloc_n(&p->work, 4, s);
   if (st == GI_OK) st = dev_alloc_n(&p->slab, per * p->clusters, s);
   if (st == GI_OK) st = dev_alloc_n(&p->cnts, 16 * p->clusters, s);
   if (st == GI_OK) st = dev_alloc_n(&p->dns, n_q, s);
@@ -552,23 +646,35 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
 extern "C" int gi_batch_plan_launch(gi_batch_plan *p, void *stream) {
   GI_ARG(p != nullptr, "plan is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  GI_CUDA(cudaMemsetAsync(p->work, 0, 2 * sizeof(int32_t), s));
+  // work: [0] query counter, [1] error flag, [2] grid-barrier arrivals, [3] grid-barrier generation
+  GI_CUDA(cudaMemsetAsync(p->work, 0, 4 * sizeof(int32_t), s));
+  const bool grid_mode = p->cluster_size == 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(p->clusters * p->cluster_size));
+  cfg.gridDim = dim3((unsigned)(grid_mode ? p->grid_blocks : p->clusters * p->cluster_size));
   cfg.blockDim = dim3(kBT);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)p->cluster_size;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  if (grid_mode) {
+    attr[0].id = cudaLaunchAttributeCooperative;  // guarantees co-residency for the grid barrier
+    attr[0].val.cooperative = 1;
+  } else {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)p->cluster_size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+  }
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const int mode = p->selector == GI_DIR_SPARSE_PUSH ? 0 : (p->selector == GI_DIR_LEARNED && selector_loaded() ? 2 : 1);
   const int tok = timing_begin(kClassBatch, s);
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch, (const BatchGraph *)p->dg, (const BatchQuery *)p->dq, p->n_q,
-                                     p->work, p->dws, p->dns, p->dlev, mode, p->alpha, p->beta, p->cap, p->work + 1);
+  cudaError_t e = grid_mode
+                      ? cudaLaunchKernelEx(&cfg, k_batch<true>, (const BatchGraph *)p->dg, (const BatchQuery *)p->dq,
+                                           p->n_q, p->work, p->dws, p->dns, p->dlev, mode, p->alpha, p->beta, p->cap,
+                                           p->work + 1, g_barrier_phantoms)
+                      : cudaLaunchKernelEx(&cfg, k_batch<false>, (const BatchGraph *)p->dg,
+                                           (const BatchQuery *)p->dq, p->n_q, p->work, p->dws, p->dns, p->dlev, mode,
+                                           p->alpha, p->beta, p->cap, p->work + 1, 0);
   timing_end(tok, s);
   note_launch(1);
   if (e != cudaSuccess) return cuda_fail(e, "batch launch", __FILE__, __LINE__);
@@ -584,7 +690,8 @@ extern "C" int gi_batch_plan_results(gi_batch_plan *p, int64_t *q_ns, int32_t *l
   if (levels) GI_CUDA(cudaMemcpyAsync(levels, p->dlev, sizeof(int32_t) * p->n_q, cudaMemcpyDeviceToHost, s));
   GI_CUDA(cudaStreamSynchronize(s));
   if (err) {
-    set_error("a query exceeded the level cap of the batched engine");
+    set_error(err == 2 ? "a grid barrier of the persistent kernel timed out"
+                       : "a query exceeded the level cap of the batched engine");
     return GI_ERR_TIMEOUT;
   }
   return GI_OK;

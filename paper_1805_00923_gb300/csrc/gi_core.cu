@@ -1205,4 +1205,5 @@ extern "C" void gi_schedule_default(gi_schedule *s) {
   s->beta = 24.0f;
   s->tile_edges = 2048;
   s->t_heavy = 16384;
+  s->persistent = 0;
 }

@@ -118,3 +118,41 @@ def test_batch_sssp_threshold_orders(gi, delta):
     qs = [(k, s, "sssp") for k in range(3) for s in (0, 7, hgs[k].n - 1)]
     res, _ = gi.batch_run(gs, qs, opts=gi.batch_opts(cluster_size=2, sssp_delta=delta))
     _check(hgs, qs, res)
+
+
+@pytest.mark.parametrize("selector", ["sparse_push", "hybrid_pull", "learned"])
+def test_persistent_single_queries(gi, selector):
+    """BFS (depth + canonical parent) and SSSP in the whole-GPU persistent mode."""
+    if selector == "learned":
+        if not os.path.exists(WEIGHTS):
+            pytest.skip("no trained selector weights committed")
+        from paper_1805_00923_gb300 import selector as sel
+        sel.install(WEIGHTS)
+    for hg in [rmat(14, weights=True), grid(64, weights=True), adversarial("path", True),
+               adversarial("components", True), adversarial("single", True)]:
+        g = gi.Graph.from_host(hg)
+        sc = gi.schedule(selector, persistent=1)
+        for src in sorted({0, hg.n // 3, hg.n - 1}):
+            wd, wp, levels = oracle.bfs(hg, src)
+            tr = gi.Trace(16)
+            d, p = gi.bfs(g, src, sched=sc, trace=tr)
+            assert np.array_equal(d.cpu().numpy(), wd) and np.array_equal(p.cpu().numpy(), wp)
+            assert tr.iterations == len(levels)
+            assert np.array_equal(gi.sssp(g, src, sched=sc).cpu().numpy(), oracle.sssp(hg, src)[0])
+
+
+def test_grid_barrier_wait_runs_out(gi):
+    """A barrier waiting for arrivals that never come gives up (~2 s) with
+    GI_ERR_TIMEOUT; the context stays usable."""
+    hg = rmat(10)
+    g = gi.Graph.from_host(hg)
+    lib = gi.lib()
+    assert lib.gi_debug_barrier_phantoms(1) == 0
+    try:
+        with pytest.raises(gi.GIError) as e:
+            gi.batch_run([g], [(0, 0, "bfs")], opts=gi.batch_opts(cluster_size=0))
+        assert e.value.code == -5 and b"grid barrier" in lib.gi_last_error()
+    finally:
+        lib.gi_debug_barrier_phantoms(0)
+    res, _ = gi.batch_run([g], [(0, 0, "bfs"), (0, 3, "bfs")], opts=gi.batch_opts(cluster_size=0))
+    _check([hg], [(0, 0, "bfs"), (0, 3, "bfs")], res)
