@@ -481,6 +481,18 @@ def run_grid4096(args):
                 gi.sssp(g, int(s_), sched=gi.schedule("learned"))
         torch.cuda.synchronize()
         host_ms = (time.perf_counter() - t0) * 1e3 / 2
+        # the same queries as single calls in the whole-GPU persistent mode
+        pers = gi.schedule("learned", persistent=1)
+        a, b = _events()
+        a.record()
+        for s_ in srcs[:4]:
+            if algo == "bfs":
+                gi.bfs(g, int(s_), want_parent=False, sched=pers)
+            else:
+                gi.sssp(g, int(s_), sched=pers)
+        b.record()
+        torch.cuda.synchronize()
+        pers_ms = a.elapsed_time(b) / 4
         qs = [(0, int(s_), algo) for s_ in srcs]
         plan = gi.BatchPlan([g], qs, opts=gi.batch_opts(cluster_size=8, selector="learned"))
         plan.launch()
@@ -493,7 +505,7 @@ def run_grid4096(args):
         res, ns, lev = plan.results()
         plan.free()
         bms = a.elapsed_time(b)
-        out[algo] = {"host_driven_ms_per_query": host_ms, "batch_ms_total": bms,
+        out[algo] = {"host_driven_ms_per_query": host_ms, "persistent_ms_per_query": pers_ms, "batch_ms_total": bms,
                      "batch_gteps_nominal": len(qs) * hg.m / (bms * 1e-3) / 1e9,
                      "p50_ms": float(np.percentile(ns, 50) / 1e6), "p99_ms": float(np.percentile(ns, 99) / 1e6),
                      "levels_mean": float(lev.mean())}
