@@ -22,10 +22,15 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
       gi::set_error("pull traversal needs the in-edges: load a symmetric graph or call gi_load_csc");
       return GI_ERR_UNSUPPORTED;
     }
-    const uint32_t *F = nullptr;
+    FSet F;
     if (from) {
-      GI_TRY(vset_ensure_bitmap(from, s));
-      F = from->bitmap;
+      if (sc.dense_rep == GI_REP_BOOL) {
+        GI_TRY(vset_ensure_bool(from, s));
+        F = FSet(static_cast<const uint8_t *>(from->boolmap));
+      } else {
+        GI_TRY(vset_ensure_bitmap(from, s));
+        F = FSet(static_cast<const uint32_t *>(from->bitmap));
+      }
     }
     const bool vp = sc.balance == GI_BAL_VERTEX;
     switch (kernel_id) {
@@ -77,6 +82,9 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
       if (dir == GI_DIR_SPARSE_PUSH) {
         GI_TRY(vset_ensure_queue(from, s));
         mode = kSrcQueue;
+      } else if (sc.dense_rep == GI_REP_BOOL) {
+        GI_TRY(vset_ensure_bool(from, s));
+        mode = kSrcBitmap;
       } else {
         GI_TRY(vset_ensure_bitmap(from, s));
         mode = kSrcBitmap;
@@ -128,6 +136,7 @@ int check_schedule(const gi_schedule *sc) {
   GI_ARG(sc->balance == GI_BAL_VERTEX || sc->balance == GI_BAL_EDGE_AWARE, "unknown balance mode");
   GI_ARG(sc->num_segments >= 1 && sc->num_segments <= 1024, "num_segments must be in [1, 1024]");
   GI_ARG(sc->rule == GI_RULE_BEAMER || sc->rule == GI_RULE_LIGRA, "unknown rule");
+  GI_ARG(sc->dense_rep == GI_REP_BITMAP || sc->dense_rep == GI_REP_BOOL, "dense_rep must be GI_REP_BITMAP or BOOL");
   GI_ARG(sc->tile_edges == 0 || (sc->tile_edges >= 256 && sc->tile_edges <= 8192 &&
                                  (sc->tile_edges & (sc->tile_edges - 1)) == 0),
          "tile_edges must be a power of two in [256, 8192]");

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstddef>
+
 #include "gi_internal.cuh"
 
 namespace gi {
@@ -41,6 +43,22 @@ __device__ __forceinline__ void out_mark(const OutSet &o, int32_t v) {
 }
 
 __device__ __forceinline__ bool in_set(const uint32_t *bm, int32_t v) { return bm == nullptr || bit_test(bm, v); }
+
+// Frontier as a traversal reads it (configApplyDenseVertexSet): a bitmap
+// (bitvector), a boolean map (one byte per vertex), or neither (all vertices).
+struct FSet {
+  const uint32_t *bm = nullptr;
+  const uint8_t *bytes = nullptr;
+  __host__ __device__ FSet() {}
+  __host__ __device__ FSet(std::nullptr_t) {}
+  __host__ __device__ FSet(const uint32_t *b) : bm(b) {}
+  __host__ __device__ FSet(const uint8_t *y) : bytes(y) {}
+};
+
+__device__ __forceinline__ bool in_set(const FSet &f, int32_t v) {
+  if (f.bytes) return __ldg(f.bytes + v) != 0;
+  return f.bm == nullptr || bit_test(f.bm, v);
+}
 
 // Whole-warp marking when lane l owns destination v0 + l (each destination is
 // owned by one thread, so no test-and-set is needed): the ballot is split over
@@ -274,7 +292,7 @@ constexpr int kBatch = 8;
 
 template <class Op, int kBlock>
 __device__ __forceinline__ void stage_batch(const Op &op, const int32_t *__restrict__ idx,
-                                            const uint32_t *__restrict__ F, int32_t e0, int32_t k0, int32_t ne,
+                                            FSet F, int32_t e0, int32_t k0, int32_t ne,
                                             typename Op::V *vals) {
   int32_t u[kBatch];
 #pragma unroll
@@ -292,7 +310,7 @@ __device__ __forceinline__ void stage_batch(const Op &op, const int32_t *__restr
 template <class Op, int kBlock, int kTE>
 __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__restrict__ ptr,
                                                        const int32_t *__restrict__ idx, const int4 *__restrict__ tiles,
-                                                       int32_t num_tiles, const uint32_t *__restrict__ F,
+                                                       int32_t num_tiles, FSet F,
                                                        const uint32_t *__restrict__ to, OutSet out,
                                                        typename Op::V *partial) {
   using V = typename Op::V;
@@ -395,7 +413,7 @@ template <class Op>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_pull_warp(Op op, const int32_t *__restrict__ ptr,
                                                                    const int32_t *__restrict__ idx,
                                                                    const int4 *__restrict__ tiles, int32_t num_tiles,
-                                                                   const uint32_t *__restrict__ F,
+                                                                   FSet F,
                                                                    const uint32_t *__restrict__ to, OutSet out,
                                                                    typename Op::V *partial) {
   using V = typename Op::V;
@@ -476,7 +494,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_pull_warp(Op op, const 
 template <class Op>
 __global__ void __launch_bounds__(256) k_pull_vertex(Op op, const int32_t *__restrict__ ptr,
                                                      const int32_t *__restrict__ idx, int64_t n,
-                                                     const uint32_t *__restrict__ F, const uint32_t *__restrict__ to,
+                                                     FSet F, const uint32_t *__restrict__ to,
                                                      OutSet out) {
   using V = typename Op::V;
   const int64_t nw = (n + 31) >> 5;
@@ -520,7 +538,7 @@ __global__ void k_pull_fixup(Op op, const int4 *__restrict__ splits, int32_t num
 // which is the smallest-id parent.  Rows with at least t_warp arcs are
 // scanned by the whole warp 32 arcs at a time (ballot picks the first hit).
 static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                                                  int64_t n, const uint32_t *__restrict__ F,
+                                                  int64_t n, FSet F,
                                                   const uint32_t *__restrict__ to, int32_t *depth, int32_t *parent,
                                                   int32_t level, int32_t t_warp, uint32_t *out_bm, int32_t *out_q,
                                                   int32_t *out_qc) {
@@ -664,8 +682,7 @@ constexpr int kMaxTWarp = 64;  // owner table holds kPushBlock * (kMaxTWarp - 1)
 template <class Op, int kMode>
 __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__restrict__ ptr,
                                                      const int32_t *__restrict__ idx, const int32_t *__restrict__ q,
-                                                     const int32_t *__restrict__ qcount,
-                                                     const uint32_t *__restrict__ Fbm, int64_t n,
+                                                     const int32_t *__restrict__ qcount, FSet Fbm, int64_t n,
                                                      const uint32_t *__restrict__ to, OutSet out, int32_t t_warp,
                                                      int32_t t_cta, int32_t t_heavy, int32_t *heavy_q) {
   __shared__ int32_t s_owner, s_u, s_a, s_deg;
@@ -679,7 +696,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__res
     int32_t u = -1, a = 0, deg = 0;
     if (i < total) {
       if (kMode == kSrcQueue) u = q[i];
-      else if (kMode == kSrcBitmap) u = bit_test(Fbm, (int32_t)i) ? (int32_t)i : -1;
+      else if (kMode == kSrcBitmap) u = in_set(Fbm, (int32_t)i) ? (int32_t)i : -1;
       else u = (int32_t)i;
       if (u >= 0) {
         a = __ldg(ptr + u);
@@ -865,7 +882,7 @@ size_t pull_smem_bytes(int32_t tile_edges) {
 }
 
 template <class Op, int kTE>
-int launch_pull_tiled_te(const Op &op, const Csr &c, const TileSet &ts, const uint32_t *F, const uint32_t *to,
+int launch_pull_tiled_te(const Op &op, const Csr &c, const TileSet &ts, FSet F, const uint32_t *to,
                          const OutSet &out, cudaStream_t s) {
   constexpr int kB = 256;
   const size_t smem = pull_smem_bytes<Op>(kTE);
@@ -879,7 +896,7 @@ int launch_pull_tiled_te(const Op &op, const Csr &c, const TileSet &ts, const ui
 
 // Tiled pull over the in-edges `c` with tiles `ts` (the whole graph or one segment).
 template <class Op>
-int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts, const uint32_t *F,
+int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts, FSet F,
                       const uint32_t *to, const OutSet &out, cudaStream_t s, int kclass = kClassOtherPull,
                       bool vertex_parallel = false) {
   if (vertex_parallel) {
@@ -941,8 +958,11 @@ int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const 
                                                  to, out, tw, tc, th, g->heavy_q);
   } else if (mode == kSrcBitmap) {
     grid = grid_for(g, g->n, block, 2048 / block);
-    k_push<Op, kSrcBitmap><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, from->bitmap, g->n,
-                                                  to, out, tw, tc, th, g->heavy_q);
+    const FSet fs = (sc.dense_rep == GI_REP_BOOL && from->boolmap && (from->reps & GI_REP_BOOL))
+                        ? FSet(static_cast<const uint8_t *>(from->boolmap))
+                        : FSet(static_cast<const uint32_t *>(from->bitmap));
+    k_push<Op, kSrcBitmap><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, fs, g->n, to, out, tw,
+                                                  tc, th, g->heavy_q);
   } else {
     grid = grid_for(g, g->n, block, 2048 / block);
     k_push<Op, kSrcAll><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, nullptr, g->n, to, out,

@@ -409,3 +409,23 @@ def test_segmented_pull_all_algorithms(gi, segs):
     tr = gi.Trace(256)
     assert np.array_equal(_np(gi.sssp(g, 9, sched=sc, trace=tr)), want)
     assert np.array_equal(tr.as_dict()["frontier"], fs)
+
+
+@pytest.mark.parametrize("direction", ["dense_push", "dense_pull", "hybrid_pull"])
+def test_boolean_map_frontier(gi, direction):
+    """configApplyDenseVertexSet: dense traversals reading a boolean map instead of a bitvector."""
+    hg = rmat(14, weights=True)
+    g = _load(gi, hg)
+    sc = gi.schedule(direction, dense_rep=gi.GI_REP_BOOL)
+    wd, wp, _ = oracle.bfs(hg, 0)
+    d, p = gi.bfs(g, 0, sched=sc)
+    assert np.array_equal(_np(d), wd) and np.array_equal(_np(p), wp)
+    assert np.array_equal(_np(gi.sssp(g, 4, sched=sc)), oracle.sssp(hg, 4)[0])
+    assert np.array_equal(_np(gi.cc(g, sched=sc)), oracle.cc(hg)[0])
+    fm = (np.random.default_rng(3).random(hg.n) < 0.2).astype(np.uint8)
+    u, v = oracle.edgeset_select(hg, fm)
+    count = torch.zeros(hg.n, dtype=torch.int32, device="cuda")
+    srcsum = torch.zeros(hg.n, dtype=torch.int64, device="cuda")
+    gi.edgeset_apply(g, _mask_set(gi, g, fm), None, sc, gi.GI_K_PROBE,
+                     gi.gi_probe_args(count.data_ptr(), srcsum.data_ptr()))
+    assert np.array_equal(_np(count), np.bincount(v, minlength=hg.n))
