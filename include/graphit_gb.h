@@ -153,7 +153,7 @@ typedef struct gi_schedule {
   uint32_t dense_rep;   /* frontier rep for dense traversals: GI_REP_BITMAP or BOOL  */
   int32_t balance;      /* GI_BAL_*                                                  */
   int32_t num_segments; /* SSG count for segmented pull (configApplyNumSSG); 1 = off  */
-  int32_t block;        /* threads per block of traversal kernels (64..1024, /32)    */
+  int32_t block;        /* reserved (traversal kernels run 256-thread blocks)        */
   int32_t t_warp;       /* edge-aware: degree >= t_warp goes to a warp                */
   int32_t t_cta;        /* edge-aware: degree >= t_cta goes to a whole block          */
   int32_t rule;         /* GI_RULE_*                                                 */

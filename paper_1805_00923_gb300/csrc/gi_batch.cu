@@ -67,7 +67,7 @@ __device__ __forceinline__ void csync(cg::cluster_group &cl) {
 // Software barrier over the whole (cooperatively launched, hence co-resident)
 // grid: arrival counter + generation word.  The wait gives up after
 // kBarrierLimitNs of %globaltimer time, sets *err = 2 and reports failure, so
-// a broken barrier ends the kernel instead of hanging it.  The verdict is
+// a broken barrier ends the kernel instead of hanging it.  The outcome is
 // taken by thread 0 and shared through shared memory, so a block decides
 // uniformly.  `nblocks` is the arrival count that releases the barrier.
 constexpr unsigned long long kBarrierLimitNs = 2000000000ull;

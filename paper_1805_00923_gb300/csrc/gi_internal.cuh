@@ -58,7 +58,6 @@ void timing_end(int token, cudaStream_t s);
 namespace gi {
 
 // ------------------------------------------------------------ constants --
-constexpr int kMaxBlock = 1024;
 constexpr int kLongRowDiv = 2;         // rows with degree > tile_edges/kLongRowDiv get their own tiles
 constexpr int kTileRows = 512;         // at most this many rows per short block tile
 constexpr int kWarpTileEdges = 256;    // tile_edges value that selects warp-sized tiles
