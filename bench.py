@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--sources", type=int, default=16, help="sources per graph for the BFS/SSSP workloads")
     p.add_argument("--only", choices=["pagerank", "pagerank_delta", "cc", "bfs", "sssp"], default=None,
                    help="profiling case: run just this algorithm --steps times on the workload graph")
+    p.add_argument("--hot-cache", type=int, choices=[0, 1, 2], default=0,
+                   help="profiling case: PageRank / PageRankDelta pulls with the hot-source cache")
     return p.parse_args()
 
 
@@ -239,6 +241,7 @@ def run_gi(args):
     compare = {}
     for name, sc in ([] if args.no_extras else
                      [("dense_pull", gi.schedule("dense_pull")),
+                      ("dense_pull_hot_cache", gi.schedule("dense_pull", hot_cache=1)),
                       ("segmented_pull_4", gi.schedule("dense_pull", num_segments=4)),
                       ("dense_push", gi.schedule("dense_push"))]):
         gi.pagerank(g, DAMPING, PR_ITERS, sched=sc)
@@ -354,7 +357,9 @@ def run_gi(args):
     bytes_per_launch = 4 * m + 16 * n + 4
     avg_ms = pr_ms / max(pr_launches, 1)
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
-    traffic = recorded_traffic("k_pull_tiled_OpPR", f"rmat{args.scale}")
+    hot = int(pr_s.hot_cache) if pr_s.direction == gi.GI_DIR_DENSE_PULL and pr_s.num_segments == 1 else 0
+    kname = {0: "k_pull_tiled_OpPR", 1: "k_pull_hot_OpPR", 2: "k_pull_tiled_hotL1_OpPR"}[hot]
+    traffic = recorded_traffic(kname, f"rmat{args.scale}")
 
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -367,7 +372,11 @@ def run_gi(args):
                 "cc": {"gteps": edges[2] / (per_alg_ms[2] * 1e-3) / 1e9, "ms": per_alg_ms[2] / args.steps}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_pull_tiled<OpPR> (PageRank DensePull iteration)",
+                         "kernel": {0: "k_pull_tiled<OpPR> (PageRank DensePull iteration)",
+                                    1: "k_hot_gather + k_pull_hot<OpPR> (PageRank DensePull iteration, hot sources "
+                                       "in shared memory)",
+                                    2: "k_hot_gather + k_pull_tiled<OpPR, hot L1> (PageRank DensePull iteration, hot "
+                                       "sources kept in L1)"}[hot],
                          "bytes_model": "4m + 16n + 4 per launch", "launches_timed": pr_launches,
                          "avg_launch_ms": avg_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -397,9 +406,9 @@ def run_only(args):
     g = gi.Graph.from_host(hg)
     for _ in range(args.steps):
         if args.only == "pagerank":
-            gi.pagerank(g, DAMPING, PR_ITERS, sched=gi.schedule("dense_pull"))
+            gi.pagerank(g, DAMPING, PR_ITERS, sched=gi.schedule("dense_pull", hot_cache=args.hot_cache))
         elif args.only == "pagerank_delta":
-            gi.pagerank_delta(g, DAMPING, PRD_EPS, PRD_ITERS)
+            gi.pagerank_delta(g, DAMPING, PRD_EPS, PRD_ITERS, sched=gi.schedule("hybrid_pull", hot_cache=args.hot_cache))
         elif args.only == "cc":
             gi.cc(g)
         elif args.only == "bfs":

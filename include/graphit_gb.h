@@ -80,6 +80,15 @@ int gi_graph_free(gi_graph *g);
 /* n, m and the maximum out-degree.  Any output pointer may be NULL. */
 int gi_graph_info(const gi_graph *g, int64_t *n, int64_t *m, int32_t *max_deg);
 
+/*
+ * The hot-source set of the shared-memory pull (gi_schedule.hot_cache), built
+ * on first use from the in-edges (this call builds it, syncing `stream`): *k
+ * sources, those of out-degree >= *min_deg, where min_deg is the smallest
+ * threshold with at most 40,960 sources (k = 0, min_deg = 0 for a graph
+ * without arcs).  Errors: GI_ERR_UNSUPPORTED without in-edges, GI_ERR_OOM.
+ */
+int gi_graph_hot_info(gi_graph *g, int32_t *k, int32_t *min_deg, void *stream);
+
 /* Device pointers of the library's copy: out-offsets, out-indices, out-weights (NULL if none). */
 int gi_graph_device_csr(const gi_graph *g, const int32_t **offsets, const int32_t **indices,
                         const int32_t **weights);
@@ -166,10 +175,19 @@ typedef struct gi_schedule {
                         /* direction chosen on the device (LEARNED: the MLP; SPARSE_PUSH */
                         /* or DENSE_PUSH: push only; otherwise Beamer's rule); the trace */
                         /* then records only the level count.  0 = one launch per level. */
+  int32_t hot_cache;    /* PageRank / PageRankDelta DensePull over the whole graph:      */
+                        /* the values of the (up to 40,960) highest-out-degree sources   */
+                        /* are read from on-chip memory instead of one L2 sector per     */
+                        /* arc (the GPU form of the cache partitioning of Sec. 5).       */
+                        /* 1 = in shared memory, one persistent block per SM (tiles of   */
+                        /* 512..2048 arcs); 2 = a dense array kept in L1 (tiles of       */
+                        /* 512..8192 arcs); 0 = off.  Results are bit-identical to 0.    */
+                        /* Ignored elsewhere.  Built once per graph (4m bytes).          */
 } gi_schedule;
 
 /* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment, 256 threads, t_warp 32,
- * t_cta 1024, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 16384, not persistent. */
+ * t_cta 1024, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 16384, not persistent,
+ * hot_cache 0. */
 void gi_schedule_default(gi_schedule *s);
 
 /* ------------------------------------------------------------ edgeset apply -- */

@@ -84,13 +84,7 @@ class Graph:
         self.handle = h
         self._keep = None
         if in_edges is not None and not symmetric:
-            ip, ic, iw = (list(in_edges) + [None])[:3]
-            if not on_dev:
-                ip, ic = np.ascontiguousarray(ip, np.int32), np.ascontiguousarray(ic, np.int32)
-                iw = None if iw is None else np.ascontiguousarray(iw, np.int32)
-            check(_C.gi_load_csc(h, _vp(ip), _vp(ic), _vp(iw),
-                                 (L.GI_DEV_PTRS if on_dev else L.GI_HOST_PTRS) | (L.GI_VALIDATE if validate else 0),
-                                 _stream(stream)))
+            self.load_in_edges(*(list(in_edges) + [None])[:3], validate=validate, stream=stream)
         n_, m_, md = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         check(_C.gi_graph_info(h, ctypes.byref(n_), ctypes.byref(m_), ctypes.byref(md)))
         self.n, self.m, self.max_deg = n_.value, m_.value, md.value
@@ -101,6 +95,22 @@ class Graph:
         """From a graphgen.HostGraph-like object (n, row_ptr, col, wt, symmetric)."""
         return cls(hg.row_ptr, hg.col, getattr(hg, "wt", None), symmetric=getattr(hg, "symmetric", True),
                    validate=validate, in_edges=in_edges, stream=stream)
+
+    def load_in_edges(self, in_ptr, in_col, in_wt=None, validate=False, stream=None):
+        """gi_load_csc: attach (or replace) the in-edges of a non-symmetric graph."""
+        on_dev = isinstance(in_ptr, torch.Tensor) and in_ptr.is_cuda
+        if not on_dev:
+            in_ptr, in_col = np.ascontiguousarray(in_ptr, np.int32), np.ascontiguousarray(in_col, np.int32)
+            in_wt = None if in_wt is None else np.ascontiguousarray(in_wt, np.int32)
+        check(_C.gi_load_csc(self.handle, _vp(in_ptr), _vp(in_col), _vp(in_wt),
+                             (L.GI_DEV_PTRS if on_dev else L.GI_HOST_PTRS) | (L.GI_VALIDATE if validate else 0),
+                             _stream(stream)))
+
+    def hot_info(self, stream=None):
+        """gi_graph_hot_info: (k, min_deg) of the hot-source set of the shared-memory pull."""
+        k, d = ctypes.c_int32(), ctypes.c_int32()
+        check(_C.gi_graph_hot_info(self.handle, ctypes.byref(k), ctypes.byref(d), _stream(stream)))
+        return k.value, d.value
 
     def build_segments(self, num_segments: int, stream=None):
         check(_C.gi_graph_build_segments(self.handle, int(num_segments), _stream(stream)))

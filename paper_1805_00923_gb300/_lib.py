@@ -39,7 +39,8 @@ _P = ctypes.POINTER
 class gi_schedule(ctypes.Structure):
     _fields_ = [("direction", _i32), ("dense_rep", _u32), ("balance", _i32), ("num_segments", _i32),
                 ("block", _i32), ("t_warp", _i32), ("t_cta", _i32), ("rule", _i32), ("alpha", _f32),
-                ("beta", _f32), ("tile_edges", _i32), ("t_heavy", _i32), ("persistent", _i32)]
+                ("beta", _f32), ("tile_edges", _i32), ("t_heavy", _i32), ("persistent", _i32),
+                ("hot_cache", _i32)]
 
 
 class gi_trace(ctypes.Structure):
@@ -114,6 +115,7 @@ SIGNATURES = {
     "gi_batch_plan_free": (ctypes.c_int, [_vp]),
     "gi_debug_fail_allocs_after": (ctypes.c_int, [_i64]),
     "gi_debug_pool_used": (ctypes.c_int, [_P(_i64)]),
+    "gi_graph_hot_info": (ctypes.c_int, [_vp, _P(_i32), _P(_i32), _vp]),
     "gi_debug_barrier_phantoms": (ctypes.c_int, [_i32]),
     "gi_stats_enable": (ctypes.c_int, [ctypes.c_int]),
     "gi_stats_reset": (ctypes.c_int, []),

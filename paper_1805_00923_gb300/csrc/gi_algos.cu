@@ -531,7 +531,7 @@ extern "C" int gi_pagerank(gi_graph *g, float damping, int32_t iters, float *ran
     } else {
       OpPR op{cin, last ? nullptr : cout, last ? rank : nullptr, g->inv_out_deg, base, damping};
       st = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, OutSet(), s, kClassPrPull,
-                             sc.balance == GI_BAL_VERTEX);
+                             sc.balance == GI_BAL_VERTEX, sc.hot_cache);
     }
   }
   if (st == GI_OK) st = pr_normalize(g, rank, s);
@@ -611,7 +611,7 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
     } else if (dir == GI_DIR_DENSE_PULL) {
       OpPRD op{cin, cout, rank, g->inv_out_deg, damping, first_base, inv_n, eps, round == 1 ? 1 : 0};
       st = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, out_of(P.N), s, kClassPrdPull,
-                             sc.balance == GI_BAL_VERTEX);
+                             sc.balance == GI_BAL_VERTEX, sc.hot_cache);
     } else {
       OpSumPush64 op{cin, dsum};
       st = launch_push(g, op, dir == GI_DIR_SPARSE_PUSH ? kSrcQueue : kSrcBitmap, P.F, nullptr, OutSet(), sc, s);

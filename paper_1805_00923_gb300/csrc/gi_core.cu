@@ -684,6 +684,7 @@ int use_tiles(gi_graph *g, int32_t tile_edges, cudaStream_t s) {
 void free_tile_cache(gi_graph *g, cudaStream_t s) {
   for (auto &t : g->tile_cache) free_tiles(&t, s);
   g->in_tiles = TileSet();
+  hot_free(g, s);  // derived from the in-edges as well
 }
 
 void free_tiles(TileSet *ts, cudaStream_t s) {
@@ -691,6 +692,172 @@ void free_tiles(TileSet *ts, cudaStream_t s) {
   dev_free(ts->splits, s);
   dev_free(ts->partial, s);
   *ts = TileSet();
+}
+
+// =========================================================== hot sources ==
+// Selection of the hot sources for the shared-memory cache of the dense pull:
+// a histogram of out-degrees (65,536 bins, the last one open-ended) gives the
+// smallest degree threshold whose count of sources does not exceed kHotMax.
+// Since m < 2^31, fewer than 32,768 vertices have degree >= 65,535, so the
+// threshold always exists.  Slots follow vertex-id order (exclusive scan).
+constexpr int kHotBins = 65536, kHotSmemBins = 4096;
+
+__global__ void k_hot_hist(const int32_t *__restrict__ deg, int64_t n, int32_t *hist) {
+  __shared__ int32_t sh[kHotSmemBins];
+  for (int i = threadIdx.x; i < kHotSmemBins; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = min(deg[v], kHotBins - 1);
+    if (d < kHotSmemBins) atomicAdd(sh + d, 1);
+    else atomicAdd(hist + d, 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHotSmemBins; i += blockDim.x)
+    if (sh[i]) atomicAdd(hist + i, sh[i]);
+}
+
+// One block of 1024 threads; thread t owns bins [64t, 64t+64).  out = {threshold, count}.
+__global__ void __launch_bounds__(1024) k_hot_pick(const int32_t *__restrict__ hist, int32_t cap, int32_t *out) {
+  constexpr int kPer = kHotBins / 1024;
+  __shared__ int64_t s_warp[32];
+  __shared__ int32_t s_best;
+  const int t = threadIdx.x;
+  int64_t own = 0;
+  for (int i = 0; i < kPer; ++i) own += hist[t * kPer + i];
+  // suffix sum over threads t' >= t: an inclusive scan in reversed thread order
+  const int r = 1023 - t, rl = r & 31, rw = r >> 5;
+  int64_t x = own;
+  // lanes of one warp hold consecutive r (reversed), so shuffle down in t
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_down_sync(0xffffffffu, x, o);
+    if (rl >= o) x += y;
+  }
+  if (rl == 31) s_warp[rw] = x;  // warp total (its lowest t, lane 0)
+  if (t == 0) s_best = kHotBins;
+  __syncthreads();
+  int64_t before = 0;  // totals of the warps with larger t
+  for (int w = 0; w < rw; ++w) before += s_warp[w];
+  const int64_t after = before + x - own;  // sources with degree in bins above this thread's range
+  int64_t run = after;
+  int32_t cand = kHotBins;
+  for (int d = t * kPer + kPer - 1; d >= t * kPer && d >= 1; --d) {
+    run += hist[d];
+    if (run <= cap) cand = d;
+    else break;
+  }
+  if (cand < kHotBins) atomicMin(&s_best, cand);
+  __syncthreads();
+  if (cand == s_best && cand < kHotBins) {
+    int64_t cnt = after;
+    for (int d = t * kPer + kPer - 1; d >= cand; --d) cnt += hist[d];
+    out[0] = cand;
+    out[1] = (int32_t)cnt;
+  }
+  if (t == 0 && s_best == kHotBins) {
+    out[0] = kHotBins;
+    out[1] = 0;
+  }
+}
+
+__global__ void k_hot_flags(const int32_t *__restrict__ deg, int64_t n, int32_t min_deg, int32_t *flag) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = deg[v] >= min_deg ? 1 : 0;
+}
+
+__global__ void k_hot_src(const int32_t *__restrict__ deg, int64_t n, int32_t min_deg,
+                          const int32_t *__restrict__ slot, int32_t *src) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    if (deg[v] >= min_deg) src[slot[v]] = (int32_t)v;
+}
+
+__global__ void k_hot_remap(const int32_t *__restrict__ idx, int64_t m, const int32_t *__restrict__ deg,
+                            int32_t min_deg, const int32_t *__restrict__ slot, int32_t *hidx) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = idx[e];
+    hidx[e] = deg[u] >= min_deg ? ~slot[u] : u;
+  }
+}
+
+int hot_get(gi_graph *g, cudaStream_t s) {
+  if (g->hot.built) return GI_OK;
+  GI_TRY(ws_get(g, s));
+  HotSet h;
+  const int64_t n = g->n, m = g->m;
+  int st = GI_OK;
+  if (n > 0 && m > 0 && g->has_csc) {
+    int32_t *hist = nullptr;
+    st = dev_alloc_n(&hist, kHotBins + 2, s);
+    if (st == GI_OK && cudaMemsetAsync(hist, 0, sizeof(int32_t) * (kHotBins + 2), s) != cudaSuccess)
+      st = cuda_fail(cudaGetLastError(), "hot histogram", __FILE__, __LINE__);
+    if (st == GI_OK) {
+      k_hot_hist<<<grid_for(g, n, 256, 2), 256, 0, s>>>(g->out_deg, n, hist);
+      k_hot_pick<<<1, 1024, 0, s>>>(hist, kHotMax, hist + kHotBins);
+      st = launch_status(2);
+    }
+    int32_t pick[2] = {kHotBins, 0};
+    if (st == GI_OK && (cudaMemcpyAsync(pick, hist + kHotBins, sizeof(pick), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+      st = cuda_fail(cudaGetLastError(), "hot threshold", __FILE__, __LINE__);
+    dev_free(hist, s);
+    h.min_deg = pick[0];
+    h.k = pick[1];
+    if (st == GI_OK && h.k > 0) {
+      int32_t *flag = g->ws->tmp_i32, *slot = g->ws->tmp2_i32;
+      const int k4 = (h.k + 3) & ~3;
+      st = dev_alloc_n(&h.src, h.k, s);
+      if (st == GI_OK) st = dev_alloc_n(&h.vals, k4, s);
+      if (st == GI_OK) st = dev_alloc_n(&h.idx, m, s);
+      if (st == GI_OK && cudaMemsetAsync(h.vals, 0, sizeof(float) * k4, s) != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "hot values", __FILE__, __LINE__);
+      if (st == GI_OK) {
+        k_hot_flags<<<grid_for(g, n, 256), 256, 0, s>>>(g->out_deg, n, h.min_deg, flag);
+        st = launch_status(1);
+      }
+      if (st == GI_OK) st = scan_exclusive(g, flag, slot, n, s);
+      if (st == GI_OK) {
+        k_hot_src<<<grid_for(g, n, 256), 256, 0, s>>>(g->out_deg, n, h.min_deg, slot, h.src);
+        k_hot_remap<<<grid_for(g, m, 256), 256, 0, s>>>(g->in.idx, m, g->out_deg, h.min_deg, slot, h.idx);
+        st = launch_status(2);
+      }
+      if (st != GI_OK) {
+        dev_free(h.src, s);
+        dev_free(h.vals, s);
+        dev_free(h.idx, s);
+        return st;
+      }
+    }
+  }
+  if (st != GI_OK) return st;
+  h.built = true;
+  if (h.k == 0) h.min_deg = 0;
+  g->hot = h;
+  return GI_OK;
+}
+
+}  // namespace gi
+
+extern "C" int gi_graph_hot_info(gi_graph *g, int32_t *k, int32_t *min_deg, void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  if (!g->has_csc) {
+    gi::set_error("the hot-source set needs the in-edges: load a symmetric graph or call gi_load_csc");
+    return GI_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  GI_TRY(gi::hot_get(g, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  if (k) *k = g->hot.k;
+  if (min_deg) *min_deg = g->hot.min_deg;
+  return GI_OK;
+}
+
+namespace gi {
+
+void hot_free(gi_graph *g, cudaStream_t s) {
+  dev_free(g->hot.src, s);
+  dev_free(g->hot.idx, s);
+  dev_free(g->hot.vals, s);
+  g->hot = HotSet();
 }
 
 // ============================================================== segments ==
@@ -1206,4 +1373,5 @@ extern "C" void gi_schedule_default(gi_schedule *s) {
   s->tile_edges = 2048;
   s->t_heavy = 16384;
   s->persistent = 0;
+  s->hot_cache = 0;
 }

@@ -108,6 +108,21 @@ struct Segments {
   TileSet *tiles = nullptr;   // host array: tiles of each segment
 };
 
+// Hot-source cache for dense pulls over the whole graph: the sources of
+// highest out-degree (out_deg >= min_deg, at most kHotMax of them) get slots
+// in vertex-id order; `idx` is the in-edge column array with each hot source
+// u replaced by ~slot(u) (negative), so a pull kernel that holds the hot
+// sources' values in shared memory reads them there without a lookup.
+constexpr int kHotMax = 40960;  // 160 KB of fp32 values per block
+struct HotSet {
+  bool built = false;
+  int32_t k = 0;              // hot sources (0: the cache does not apply)
+  int32_t min_deg = 0;
+  int32_t *src = nullptr;     // k: slot -> vertex id
+  int32_t *idx = nullptr;     // m: remapped in-edge sources
+  float *vals = nullptr;      // round_up(k, 4): source values staged for one launch
+};
+
 struct Workspace;  // per-graph scratch (frontiers, buffers); defined in gi_core.cu
 
 }  // namespace gi
@@ -125,6 +140,7 @@ struct gi_graph {
   gi::TileSet in_tiles;          // active tile set over the in-edges (a view into tile_cache)
   gi::TileSet tile_cache[6];     // owned tile sets for tile_edges 256, 512, ..., 8192 (built on first use)
   gi::Segments segs;
+  gi::HotSet hot;                // built on first use of the hot-source pull
   int64_t *ctrl = nullptr;       // device control block (kCtrlWords)
   int32_t *heavy_q = nullptr;    // sources deferred to the all-block expansion (n entries + count)
   int64_t *ctrl_host = nullptr;  // pinned mirror
@@ -167,6 +183,8 @@ int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cuda
 int use_tiles(gi_graph *g, int32_t tile_edges, cudaStream_t s);  // select (building once) the in-edge tiles
 void free_tile_cache(gi_graph *g, cudaStream_t s);
 void free_tiles(TileSet *ts, cudaStream_t s);
+int hot_get(gi_graph *g, cudaStream_t s);  // build (once) g->hot from the in-edges
+void hot_free(gi_graph *g, cudaStream_t s);
 
 // vertexset internals
 int vset_alloc(gi_graph *g, gi_vset *v, cudaStream_t s);

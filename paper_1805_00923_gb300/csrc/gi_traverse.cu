@@ -140,6 +140,7 @@ int check_schedule(const gi_schedule *sc) {
   GI_ARG(sc->tile_edges == 0 || (sc->tile_edges >= 256 && sc->tile_edges <= 8192 &&
                                  (sc->tile_edges & (sc->tile_edges - 1)) == 0),
          "tile_edges must be a power of two in [256, 8192]");
+  GI_ARG(sc->hot_cache >= 0 && sc->hot_cache <= 2, "hot_cache must be 0, 1 or 2");
   return GI_OK;
 }
 

@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include <cstddef>
+#include <type_traits>
 
 #include "gi_internal.cuh"
 
@@ -191,6 +192,7 @@ struct OpPR {
   __device__ static V identity() { return 0.0f; }
   __device__ static V combine(V a, V b) { return a + b; }
   __device__ V edge_val(int32_t u, int32_t) const { return __ldg(contrib + u); }
+  __host__ __device__ const float *hot_source() const { return contrib; }
   __device__ bool dst_ok(int32_t) const { return true; }
   __device__ bool finish(int32_t v, V s) const {
     float r = fmaf(damping, s, base);
@@ -215,6 +217,7 @@ struct OpPRD {
   __device__ static V identity() { return 0.0f; }
   __device__ static V combine(V a, V b) { return a + b; }
   __device__ V edge_val(int32_t u, int32_t) const { return __ldg(contrib + u); }
+  __host__ __device__ const float *hot_source() const { return contrib; }
   __device__ bool dst_ok(int32_t) const { return true; }
   __device__ bool finish(int32_t v, V s) const {
     float delta, r = rank[v];
@@ -290,114 +293,243 @@ __device__ __forceinline__ V warp_reduce(V x) {
 // two memory round trips per kBatch arcs per thread instead of two per arc.
 constexpr int kBatch = 8;
 
-template <class Op, int kBlock>
-__device__ __forceinline__ void stage_batch(const Op &op, const int32_t *__restrict__ idx,
-                                            FSet F, int32_t e0, int32_t k0, int32_t ne,
-                                            typename Op::V *vals) {
+// Bytes of shared memory one tile reduction stages: the arc values (with
+// room for a long row's piece) and the tile's row pointers.
+template <class V>
+__host__ __device__ constexpr size_t pull_stage_bytes(int tile_edges) {
+  return sizeof(V) * (size_t)(tile_edges + tile_edges / kLongRowDiv) + sizeof(int32_t) * (kTileRows + 1);
+}
+
+// Read-only loads with an L1 eviction policy: hot values stay (evict_last),
+// streamed indices and cold gathers do not allocate in L1.
+__device__ __forceinline__ float ld_keep_f32(const float *p) {
+  float v;
+  asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_stream_f32(const float *p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_stream_i32(const int32_t *p) {
+  int32_t v;
+  asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+// Where a tile's arc values come from (kMode):
+//   kGatherPlain: op.edge_val(u, e) for sources u in F;
+//   kGatherHotSmem / kGatherHotL1: F is all vertices and the in-edge sources
+//   were remapped by the graph's HotSet; a negative entry ~s reads slot s of
+//   the hot sources' values -- the block's shared-memory copy (s_hot), or the
+//   dense global array hot (kept in L1 with evict_last; the other loads
+//   bypass L1 so they do not evict it).
+constexpr int kGatherPlain = 0, kGatherHotSmem = 1, kGatherHotL1 = 2;
+
+template <class Op, int kMode>
+struct Gather {
+  const Op &op;
+  FSet F;
+  const float *hot;  // shared memory (kGatherHotSmem) or global (kGatherHotL1)
+  __device__ __forceinline__ int32_t src(const int32_t *p) const {
+    if constexpr (kMode == kGatherHotL1) return ld_stream_i32(p);
+    else return __ldg(p);
+  }
+  __device__ __forceinline__ typename Op::V hot_val(int32_t u, int32_t e) const {
+    if constexpr (kMode == kGatherHotSmem) return u < 0 ? hot[~u] : op.edge_val(u, e);
+    else return u < 0 ? ld_keep_f32(hot + ~u) : ld_stream_f32(op.hot_source() + u);
+  }
+};
+
+template <class Op, int kBlock, int kMode>
+__device__ __forceinline__ void stage_batch(const Gather<Op, kMode> &G, const int32_t *__restrict__ idx,
+                                            int32_t e0, int32_t k0, int32_t ne, typename Op::V *vals) {
   int32_t u[kBatch];
 #pragma unroll
   for (int j = 0; j < kBatch; ++j) {
     const int32_t k = k0 + j * kBlock;
-    u[j] = k < ne ? __ldg(idx + e0 + k) : -1;
+    u[j] = k < ne ? G.src(idx + e0 + k) : -1;
   }
 #pragma unroll
   for (int j = 0; j < kBatch; ++j) {
     const int32_t k = k0 + j * kBlock;
-    if (k < ne) vals[k] = (u[j] >= 0 && in_set(F, u[j])) ? op.edge_val(u[j], e0 + k) : Op::identity();
+    if constexpr (kMode != kGatherPlain) {
+      if (k < ne) vals[k] = G.hot_val(u[j], e0 + k);
+    } else {
+      if (k < ne) vals[k] = (u[j] >= 0 && in_set(G.F, u[j])) ? G.op.edge_val(u[j], e0 + k) : Op::identity();
+    }
   }
 }
 
-template <class Op, int kBlock, int kTE>
+struct BlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// Named barrier over the kThreads threads of one group (ids 1..15; 0 is __syncthreads).
+template <int kThreads>
+struct GroupSync {
+  int id;
+  __device__ __forceinline__ void operator()() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kThreads) : "memory"); }
+};
+
+// Reduction of tile t by the kBlock threads that call it (tid in [0, kBlock)),
+// with `sync` a barrier over exactly those threads.  vals/rp: the group's
+// staging area (pull_stage_bytes), s_red: kBlock/32 values.
+template <class Op, int kBlock, int kMode, class Sync>
+__device__ __forceinline__ void pull_tile(const Gather<Op, kMode> &G, const int4 T, int32_t t,
+                                          const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                          const uint32_t *__restrict__ to, const OutSet &out,
+                                          typename Op::V *partial, typename Op::V *vals, int32_t *rp,
+                                          typename Op::V *s_red, const int tid, const Sync &sync) {
+  using V = typename Op::V;
+  const Op &op = G.op;
+  const int lane = tid & 31, warp = tid >> 5;
+  if (T.y > T.x) {
+    // short tile: rows [r0, r0+R), arcs [T.z, T.w) = [ptr[r0], ptr[r0+R]).  The
+    // row pointers and the arc sources are loaded together (one round trip),
+    // then the gathers; one barrier before the row reductions.
+    const int32_t r0 = T.x, R = T.y - T.x, e0 = T.z, ne = T.w - T.z;
+    constexpr int kRp = (kTileRows + 1 + kBlock - 1) / kBlock;
+    int32_t p[kRp];
+#pragma unroll
+    for (int j = 0; j < kRp; ++j) {
+      const int i = tid + j * kBlock;
+      p[j] = i <= R ? __ldg(ptr + r0 + i) : 0;
+    }
+    for (int32_t k0 = tid; k0 < ne; k0 += kBatch * kBlock) stage_batch<Op, kBlock, kMode>(G, idx, e0, k0, ne, vals);
+#pragma unroll
+    for (int j = 0; j < kRp; ++j) {
+      const int i = tid + j * kBlock;
+      if (i <= R) rp[i] = p[j];
+    }
+    sync();
+    for (int i0 = 0; i0 < R; i0 += kBlock) {
+      const int i = i0 + tid;
+      const bool valid = i < R;
+      int32_t a = 0, b = 0;
+      if (valid) {
+        a = rp[i] - e0;
+        b = rp[i + 1] - e0;
+      }
+      const bool big = valid && (b - a) >= 32;
+      V acc = Op::identity();
+      if (valid && !big)
+        for (int32_t k = a; k < b; ++k) acc = Op::combine(acc, vals[k]);
+      unsigned bal = __ballot_sync(0xffffffffu, big);
+      while (bal) {
+        const int l = __ffs(bal) - 1;
+        bal &= bal - 1;
+        const int32_t la = __shfl_sync(0xffffffffu, a, l), lb = __shfl_sync(0xffffffffu, b, l);
+        V x = Op::identity();
+        for (int32_t k = la + lane; k < lb; k += 32) x = Op::combine(x, vals[k]);
+        x = warp_reduce<V, Op>(x);
+        if (lane == l) acc = x;
+      }
+      const int32_t v = r0 + i;
+      bool mod = false;
+      if (valid && in_set(to, v) && op.dst_ok(v)) mod = op.finish(v, acc);
+      if (out.enabled()) mark_consecutive(out, r0 + i0 + (tid & ~31), mod);
+    }
+    sync();
+  } else {
+    const int32_t r = T.x, e0 = T.z, ne = T.w - T.z;
+    V x = Op::identity();
+    for (int32_t k0 = tid; k0 < ne; k0 += kBatch * kBlock) {
+      int32_t u[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int32_t k = k0 + j * kBlock;
+        u[j] = k < ne ? G.src(idx + e0 + k) : -1;
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        if constexpr (kMode != kGatherPlain) {
+          if (k0 + j * kBlock < ne) x = Op::combine(x, G.hot_val(u[j], e0 + k0 + j * kBlock));
+        } else {
+          if (u[j] >= 0 && in_set(G.F, u[j])) x = Op::combine(x, op.edge_val(u[j], e0 + k0 + j * kBlock));
+        }
+      }
+    }
+    x = warp_reduce<V, Op>(x);
+    if (lane == 0) s_red[warp] = x;
+    sync();
+    if (tid == 0) {
+      V y = Op::identity();
+      for (int w = 0; w < kBlock / 32; ++w) y = Op::combine(y, s_red[w]);
+      if (T.y == r) {
+        if (in_set(to, r) && op.dst_ok(r) && op.finish(r, y) && out.enabled()) out_mark(out, r);
+      } else {
+        partial[t] = y;
+      }
+    }
+    sync();
+  }
+}
+
+template <class Op, int kBlock, int kTE, int kMode = kGatherPlain>
 __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__restrict__ ptr,
                                                        const int32_t *__restrict__ idx, const int4 *__restrict__ tiles,
                                                        int32_t num_tiles, FSet F,
                                                        const uint32_t *__restrict__ to, OutSet out,
-                                                       typename Op::V *partial) {
+                                                       typename Op::V *partial, const float *__restrict__ hot) {
   using V = typename Op::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *vals = reinterpret_cast<V *>(smem_raw);
   int32_t *rp = reinterpret_cast<int32_t *>(smem_raw + sizeof(V) * (size_t)(kTE + kTE / kLongRowDiv));
   __shared__ V s_red[kBlock / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
-    const int4 T = tiles[t];
-    if (T.y > T.x) {
-      const int32_t r0 = T.x, R = T.y - T.x;
-      {
-        constexpr int kRp = (kTileRows + 1 + kBlock - 1) / kBlock;
-        int32_t p[kRp];
-#pragma unroll
-        for (int j = 0; j < kRp; ++j) {
-          const int i = tid + j * kBlock;
-          p[j] = i <= R ? __ldg(ptr + r0 + i) : 0;
-        }
-#pragma unroll
-        for (int j = 0; j < kRp; ++j) {
-          const int i = tid + j * kBlock;
-          if (i <= R) rp[i] = p[j];
-        }
-      }
-      __syncthreads();
-      const int32_t e0 = rp[0], ne = rp[R] - e0;
-      for (int32_t k0 = tid; k0 < ne; k0 += kBatch * kBlock) stage_batch<Op, kBlock>(op, idx, F, e0, k0, ne, vals);
-      __syncthreads();
-      for (int i0 = 0; i0 < R; i0 += kBlock) {
-        const int i = i0 + tid;
-        const bool valid = i < R;
-        int32_t a = 0, b = 0;
-        if (valid) {
-          a = rp[i] - e0;
-          b = rp[i + 1] - e0;
-        }
-        const bool big = valid && (b - a) >= 32;
-        V acc = Op::identity();
-        if (valid && !big)
-          for (int32_t k = a; k < b; ++k) acc = Op::combine(acc, vals[k]);
-        unsigned bal = __ballot_sync(0xffffffffu, big);
-        while (bal) {
-          const int l = __ffs(bal) - 1;
-          bal &= bal - 1;
-          const int32_t la = __shfl_sync(0xffffffffu, a, l), lb = __shfl_sync(0xffffffffu, b, l);
-          V x = Op::identity();
-          for (int32_t k = la + lane; k < lb; k += 32) x = Op::combine(x, vals[k]);
-          x = warp_reduce<V, Op>(x);
-          if (lane == l) acc = x;
-        }
-        const int32_t v = r0 + i;
-        bool mod = false;
-        if (valid && in_set(to, v) && op.dst_ok(v)) mod = op.finish(v, acc);
-        if (out.enabled()) mark_consecutive(out, r0 + i0 + (tid & ~31), mod);
-      }
-      __syncthreads();
-    } else {
-      const int32_t r = T.x, e0 = T.z, ne = T.w - T.z;
-      V x = Op::identity();
-      for (int32_t k0 = tid; k0 < ne; k0 += kBatch * kBlock) {
-        int32_t u[kBatch];
-#pragma unroll
-        for (int j = 0; j < kBatch; ++j) {
-          const int32_t k = k0 + j * kBlock;
-          u[j] = k < ne ? __ldg(idx + e0 + k) : -1;
-        }
-#pragma unroll
-        for (int j = 0; j < kBatch; ++j)
-          if (u[j] >= 0 && in_set(F, u[j])) x = Op::combine(x, op.edge_val(u[j], e0 + k0 + j * kBlock));
-      }
-      x = warp_reduce<V, Op>(x);
-      if (lane == 0) s_red[warp] = x;
-      __syncthreads();
-      if (tid == 0) {
-        V y = Op::identity();
-        for (int w = 0; w < kBlock / 32; ++w) y = Op::combine(y, s_red[w]);
-        if (T.y == r) {
-          if (in_set(to, r) && op.dst_ok(r) && op.finish(r, y) && out.enabled()) out_mark(out, r);
-        } else {
-          partial[t] = y;
-        }
-      }
-      __syncthreads();
-    }
+  static_assert(kMode == kGatherPlain || kMode == kGatherHotL1, "k_pull_tiled: plain or L1-hot gathers");
+  const Gather<Op, kMode> G{op, F, hot};
+  for (int32_t t = blockIdx.x; t < num_tiles; t += gridDim.x)
+    pull_tile<Op, kBlock, kMode>(G, tiles[t], t, ptr, idx, to, out, partial, vals, rp, s_red, threadIdx.x,
+                                 BlockSync{});
+}
+
+// Hot-source pull (GPU form of the cache partitioning of Sec. 5): one
+// persistent block of kGroups x 256 threads per SM first copies the values of
+// the graph's hot sources (the HotSet, up to 160 KB) into shared memory, then
+// each 256-thread group reduces every (gridDim.x*kGroups)-th tile with the
+// same tile algorithm as k_pull_tiled, synchronised by its own named barrier.
+// Arcs from hot sources read shared memory instead of gathering a 32-byte L2
+// sector each.  The tiles and the order of every reduction are those of
+// k_pull_tiled, so the results are bit-identical to it.
+template <class Op, int kTE, int kGroups>
+__global__ void __launch_bounds__(256 * kGroups, 1) k_pull_hot(Op op, const int32_t *__restrict__ ptr,
+                                                               const int32_t *__restrict__ hidx,
+                                                               const int4 *__restrict__ tiles, int32_t num_tiles,
+                                                               const float *__restrict__ hot_vals, int32_t hot_k4,
+                                                               const uint32_t *__restrict__ to, OutSet out,
+                                                               float *partial) {
+  static_assert(std::is_same<typename Op::V, float>::value, "hot pull gathers fp32 values");
+  static_assert(kGroups >= 1 && kGroups <= 4, "named barriers 1..kGroups");
+  constexpr int kB = 256;
+  constexpr size_t kStage = (pull_stage_bytes<float>(kTE) + 15) & ~(size_t)15;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *s_hot = reinterpret_cast<float *>(smem_raw);
+  {
+    const float4 *src4 = reinterpret_cast<const float4 *>(hot_vals);
+    float4 *dst4 = reinterpret_cast<float4 *>(s_hot);
+    for (int i = threadIdx.x; i < hot_k4 / 4; i += blockDim.x) dst4[i] = __ldg(src4 + i);
   }
+  __syncthreads();
+  __shared__ float s_red[kGroups][kB / 32];
+  const int grp = threadIdx.x / kB;
+  unsigned char *stage = smem_raw + sizeof(float) * (size_t)hot_k4 + kStage * grp;
+  float *vals = reinterpret_cast<float *>(stage);
+  int32_t *rp = reinterpret_cast<int32_t *>(stage + sizeof(float) * (size_t)(kTE + kTE / kLongRowDiv));
+  const Gather<Op, kGatherHotSmem> G{op, FSet(), s_hot};
+  const GroupSync<kB> sync{1 + grp};
+  const int32_t stride = (int32_t)gridDim.x * kGroups;
+  for (int32_t t = (int32_t)blockIdx.x * kGroups + grp; t < num_tiles; t += stride)
+    pull_tile<Op, kB, kGatherHotSmem>(G, tiles[t], t, ptr, hidx, to, out, partial, vals, rp, s_red[grp],
+                            (int)(threadIdx.x % kB), sync);
+}
+
+// hot_vals[s] = contrib[src[s]]: the hot sources' values for one launch
+static __global__ void k_hot_gather(const float *__restrict__ contrib, const int32_t *__restrict__ src, int32_t k,
+                             float *__restrict__ vals) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) vals[i] = __ldg(contrib + __ldg(src + i));
 }
 
 // Warp tiles (tile_edges = 256): every warp owns whole tiles and no block
@@ -878,27 +1010,101 @@ namespace gi {
 
 template <class Op>
 size_t pull_smem_bytes(int32_t tile_edges) {
-  return sizeof(typename Op::V) * (size_t)(tile_edges + tile_edges / kLongRowDiv) + sizeof(int32_t) * (kTileRows + 1);
+  return pull_stage_bytes<typename Op::V>(tile_edges);
 }
 
+// Ops whose arc value is a per-source fp32 value (hot_source()[u]) can use the hot-source pull.
+template <class Op, class = void>
+struct HotGatherable : std::false_type {};
+template <class Op>
+struct HotGatherable<Op, std::void_t<decltype(std::declval<const Op &>().hot_source())>> : std::true_type {};
+
 template <class Op, int kTE>
-int launch_pull_tiled_te(const Op &op, const Csr &c, const TileSet &ts, FSet F, const uint32_t *to,
-                         const OutSet &out, cudaStream_t s) {
+int launch_pull_hot_te(gi_graph *g, const Op &op, const TileSet &ts, const uint32_t *to, const OutSet &out,
+                       cudaStream_t s) {
+  constexpr int kGroups = 4;
+  const int32_t k4 = (g->hot.k + 3) & ~3;
+  const size_t stage = (pull_stage_bytes<float>(kTE) + 15) & ~(size_t)15;
+  const size_t smem = sizeof(float) * (size_t)k4 + stage * kGroups;
+  GI_CUDA(cudaFuncSetAttribute(k_pull_hot<Op, kTE, kGroups>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = ts.num_tiles < g->num_sms * kGroups ? div_up(ts.num_tiles, kGroups) : g->num_sms;
+  k_pull_hot<Op, kTE, kGroups><<<grid, 256 * kGroups, smem, s>>>(op, g->in.ptr, g->hot.idx, ts.tiles, ts.num_tiles,
+                                                                 g->hot.vals, k4, to, out,
+                                                                 reinterpret_cast<float *>(ts.partial));
+  return GI_OK;
+}
+
+template <class Op, int kTE, int kMode = kGatherPlain>
+int launch_pull_tiled_te(const Op &op, const int32_t *ptr, const int32_t *idx, const TileSet &ts, FSet F,
+                         const uint32_t *to, const OutSet &out, const float *hot, cudaStream_t s) {
   constexpr int kB = 256;
   const size_t smem = pull_smem_bytes<Op>(kTE);
   if (smem > 48 * 1024) {
-    GI_CUDA(cudaFuncSetAttribute(k_pull_tiled<Op, kB, kTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GI_CUDA(cudaFuncSetAttribute(k_pull_tiled<Op, kB, kTE, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
   }
-  k_pull_tiled<Op, kB, kTE><<<ts.num_tiles, kB, smem, s>>>(op, c.ptr, c.idx, ts.tiles, ts.num_tiles, F, to, out,
-                                                           reinterpret_cast<typename Op::V *>(ts.partial));
+  k_pull_tiled<Op, kB, kTE, kMode><<<ts.num_tiles, kB, smem, s>>>(op, ptr, idx, ts.tiles, ts.num_tiles, F, to, out,
+                                                                  reinterpret_cast<typename Op::V *>(ts.partial), hot);
+  return GI_OK;
+}
+
+// Hot-source pull (hot_mode 1: shared-memory cache, block tiles of 512..2048
+// arcs; 2: L1-resident hot array, block tiles of 512..8192 arcs).  Returns
+// false (nothing launched) where it does not apply.
+template <class Op>
+int launch_pull_hot(gi_graph *g, const Op &op, const TileSet &ts, const uint32_t *to, const OutSet &out,
+                    cudaStream_t s, int kclass, int hot_mode, bool *done) {
+  *done = false;
+  const int te = ts.tile_edges;
+  if (ts.num_tiles == 0 || te < 512 || (hot_mode == 1 && te > 2048)) return GI_OK;
+  GI_TRY(hot_get(g, s));
+  if (g->hot.k == 0) return GI_OK;
+  const int tok = timing_begin(kclass, s);
+  k_hot_gather<<<div_up(g->hot.k, 256), 256, 0, s>>>(op.hot_source(), g->hot.src, g->hot.k, g->hot.vals);
+  GI_LAUNCH_CHECK();
+  const float *hv = g->hot.vals;
+  const int32_t *hp = g->in.ptr, *hi = g->hot.idx;
+  if (hot_mode == 1) {
+    switch (te) {
+      case 512: GI_TRY((launch_pull_hot_te<Op, 512>(g, op, ts, to, out, s))); break;
+      case 1024: GI_TRY((launch_pull_hot_te<Op, 1024>(g, op, ts, to, out, s))); break;
+      default: GI_TRY((launch_pull_hot_te<Op, 2048>(g, op, ts, to, out, s))); break;
+    }
+  } else {
+    switch (te) {
+      case 512: GI_TRY((launch_pull_tiled_te<Op, 512, kGatherHotL1>(op, hp, hi, ts, FSet(), to, out, hv, s))); break;
+      case 1024: GI_TRY((launch_pull_tiled_te<Op, 1024, kGatherHotL1>(op, hp, hi, ts, FSet(), to, out, hv, s))); break;
+      case 2048: GI_TRY((launch_pull_tiled_te<Op, 2048, kGatherHotL1>(op, hp, hi, ts, FSet(), to, out, hv, s))); break;
+      case 4096: GI_TRY((launch_pull_tiled_te<Op, 4096, kGatherHotL1>(op, hp, hi, ts, FSet(), to, out, hv, s))); break;
+      default: GI_TRY((launch_pull_tiled_te<Op, 8192, kGatherHotL1>(op, hp, hi, ts, FSet(), to, out, hv, s))); break;
+    }
+  }
+  timing_end(tok, s);
+  GI_LAUNCH_CHECK();
+  if (ts.num_splits > 0) {
+    k_pull_fixup<Op><<<div_up(ts.num_splits, 128), 128, 0, s>>>(
+        op, ts.splits, ts.num_splits, reinterpret_cast<const typename Op::V *>(ts.partial), to, out);
+    GI_LAUNCH_CHECK();
+  }
+  *done = true;
   return GI_OK;
 }
 
 // Tiled pull over the in-edges `c` with tiles `ts` (the whole graph or one segment).
+// hot_mode (gi_schedule.hot_cache) applies to whole-graph pulls from all sources
+// of Ops with per-source fp32 values.
 template <class Op>
 int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts, FSet F,
                       const uint32_t *to, const OutSet &out, cudaStream_t s, int kclass = kClassOtherPull,
-                      bool vertex_parallel = false) {
+                      bool vertex_parallel = false, int hot_mode = 0) {
+  if constexpr (HotGatherable<Op>::value) {
+    if (hot_mode != 0 && !vertex_parallel && F.bm == nullptr && F.bytes == nullptr && c.idx == g->in.idx &&
+        ts.tiles == g->in_tiles.tiles) {
+      bool done = false;
+      GI_TRY(launch_pull_hot(g, op, ts, to, out, s, kclass, hot_mode, &done));
+      if (done) return GI_OK;
+    }
+  }
   if (vertex_parallel) {
     const int tok = timing_begin(kclass, s);
     k_pull_vertex<Op><<<grid_for(g, g->n, 256), 256, 0, s>>>(op, c.ptr, c.idx, g->n, F, to, out);
@@ -919,11 +1125,11 @@ int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts
                                                               reinterpret_cast<typename Op::V *>(ts.partial));
       break;
     }
-    case 512: GI_TRY((launch_pull_tiled_te<Op, 512>(op, c, ts, F, to, out, s))); break;
-    case 1024: GI_TRY((launch_pull_tiled_te<Op, 1024>(op, c, ts, F, to, out, s))); break;
-    case 2048: GI_TRY((launch_pull_tiled_te<Op, 2048>(op, c, ts, F, to, out, s))); break;
-    case 4096: GI_TRY((launch_pull_tiled_te<Op, 4096>(op, c, ts, F, to, out, s))); break;
-    case 8192: GI_TRY((launch_pull_tiled_te<Op, 8192>(op, c, ts, F, to, out, s))); break;
+    case 512: GI_TRY((launch_pull_tiled_te<Op, 512>(op, c.ptr, c.idx, ts, F, to, out, nullptr, s))); break;
+    case 1024: GI_TRY((launch_pull_tiled_te<Op, 1024>(op, c.ptr, c.idx, ts, F, to, out, nullptr, s))); break;
+    case 2048: GI_TRY((launch_pull_tiled_te<Op, 2048>(op, c.ptr, c.idx, ts, F, to, out, nullptr, s))); break;
+    case 4096: GI_TRY((launch_pull_tiled_te<Op, 4096>(op, c.ptr, c.idx, ts, F, to, out, nullptr, s))); break;
+    case 8192: GI_TRY((launch_pull_tiled_te<Op, 8192>(op, c.ptr, c.idx, ts, F, to, out, nullptr, s))); break;
     default:
       set_error("unsupported tile size %d", ts.tile_edges);
       return GI_ERR_UNSUPPORTED;
