@@ -186,7 +186,7 @@ typedef struct gi_schedule {
 } gi_schedule;
 
 /* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment, 256 threads, t_warp 32,
- * t_cta 1024, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 16384, not persistent,
+ * t_cta 256, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 256, not persistent,
  * hot_cache 0. */
 void gi_schedule_default(gi_schedule *s);
 

@@ -120,11 +120,10 @@ void dev_free(void *p, cudaStream_t s) {
 }
 
 int heavy_get(gi_graph *g, cudaStream_t s) {
-  if (g->heavy_q) return GI_OK;
-  // queue of n entries, then its count and the finishing-block ticket; the
-  // expansion kernel returns both to zero after each use
-  GI_TRY(dev_alloc_n(&g->heavy_q, g->n + 2, s));
-  GI_CUDA(cudaMemsetAsync(g->heavy_q + g->n, 0, 2 * sizeof(int32_t), s));
+  if (g->heavy_mem) return GI_OK;
+  // the expansion kernel returns counter and ticket to zero after each use
+  GI_TRY(dev_alloc(&g->heavy_mem, 16 + 8 * (size_t)(g->n > 0 ? g->n : 1), s));
+  GI_CUDA(cudaMemsetAsync(g->heavy_mem, 0, 16, s));
   return GI_OK;
 }
 
@@ -420,7 +419,7 @@ static void graph_release(gi_graph *g, cudaStream_t s) {
   dev_free(g->out_deg, s);
   dev_free(g->inv_out_deg, s);
   dev_free(g->ctrl, s);
-  dev_free(g->heavy_q, s);
+  dev_free(g->heavy_mem, s);
   ws_free(g, s);
   if (g->ctrl_host) cudaFreeHost(g->ctrl_host);
   delete g;
@@ -1366,12 +1365,12 @@ extern "C" void gi_schedule_default(gi_schedule *s) {
   s->num_segments = 1;
   s->block = 256;
   s->t_warp = 32;
-  s->t_cta = 1024;
+  s->t_cta = 256;
   s->rule = GI_RULE_BEAMER;
   s->alpha = 14.0f;
   s->beta = 24.0f;
   s->tile_edges = 2048;
-  s->t_heavy = 16384;
+  s->t_heavy = 256;
   s->persistent = 0;
   s->hot_cache = 0;
 }

@@ -142,7 +142,7 @@ struct gi_graph {
   gi::Segments segs;
   gi::HotSet hot;                // built on first use of the hot-source pull
   int64_t *ctrl = nullptr;       // device control block (kCtrlWords)
-  int32_t *heavy_q = nullptr;    // sources deferred to the all-block expansion (n entries + count)
+  void *heavy_mem = nullptr;     // HeavyList storage (counter, ticket, 2n entries), allocated on first use
   int64_t *ctrl_host = nullptr;  // pinned mirror
   gi::Workspace *ws = nullptr;
   int device = 0;
@@ -173,7 +173,29 @@ inline int dev_alloc_n(T **p, int64_t n, cudaStream_t s) {
 // --------------------------------------------------------------- utils --
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 int grid_for(const gi_graph *g, int64_t work, int block, int per_sm = 8);
-int heavy_get(gi_graph *g, cudaStream_t s);  // allocates g->heavy_q on first use
+// Sources deferred by k_push to the all-block expansion k_push_heavy.  Each
+// deferred source takes its entry and its range of chunks with one 64-bit
+// atomicAdd on ctr ((entries << 32) | chunks), so base[] grows with the entry
+// index and a chunk's source is found by binary search.  k_push_heavy's last
+// block returns ctr and ticket to zero.
+// Storage (one allocation): 8-byte ctr, 4-byte ticket, 4 bytes padding, then
+// src[n] (deferred sources) and base[n] (first global chunk of src[j]).
+struct HeavyList {
+  unsigned long long *ctr;
+  int32_t *ticket;
+  int32_t *src;
+  int32_t *base;
+};
+__host__ __device__ inline HeavyList heavy_at(void *mem, int64_t n) {
+  unsigned char *b = static_cast<unsigned char *>(mem);
+  HeavyList h;
+  h.ctr = reinterpret_cast<unsigned long long *>(b);
+  h.ticket = reinterpret_cast<int32_t *>(b + 8);
+  h.src = reinterpret_cast<int32_t *>(b + 16);
+  h.base = h.src + (n > 0 ? n : 1);
+  return h;
+}
+int heavy_get(gi_graph *g, cudaStream_t s);  // allocates g->heavy_mem on first use
 
 // exclusive scan of n int32 counts into out[n+1] (out[n] = total); scratch owned by g's workspace
 int scan_exclusive(gi_graph *g, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);

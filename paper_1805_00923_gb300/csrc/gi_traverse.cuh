@@ -809,6 +809,7 @@ __device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *total, in
 // arcs serially in its own thread.
 enum SrcMode { kSrcQueue = 0, kSrcBitmap = 1, kSrcAll = 2 };
 constexpr int kPushBlock = 256;
+constexpr int32_t kHeavyChunk = 4096;  // arcs per chunk of a deferred high-degree source
 constexpr int kMaxTWarp = 64;  // owner table holds kPushBlock * (kMaxTWarp - 1) arcs
 
 template <class Op, int kMode>
@@ -816,7 +817,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__res
                                                      const int32_t *__restrict__ idx, const int32_t *__restrict__ q,
                                                      const int32_t *__restrict__ qcount, FSet Fbm, int64_t n,
                                                      const uint32_t *__restrict__ to, OutSet out, int32_t t_warp,
-                                                     int32_t t_cta, int32_t t_heavy, int32_t *heavy_q) {
+                                                     int32_t t_cta, int32_t t_heavy, void *heavy_mem) {
   __shared__ int32_t s_owner, s_u, s_a, s_deg;
   __shared__ int32_t s_src[kPushBlock], s_beg[kPushBlock], s_off[kPushBlock], s_sw[32];
   __shared__ uint8_t s_own[kPushBlock * (kMaxTWarp - 1)];
@@ -837,7 +838,12 @@ __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__res
     }
     // the largest sources are expanded afterwards by every block (k_push_heavy)
     if (deg >= t_heavy) {
-      heavy_q[atomicAdd(heavy_q + n, 1)] = u;
+      const HeavyList heavy = heavy_at(heavy_mem, n);
+      const unsigned nch = (unsigned)((deg + kHeavyChunk - 1) / kHeavyChunk);
+      const unsigned long long old = atomicAdd(heavy.ctr, (1ull << 32) | nch);
+      const int32_t j = (int32_t)(old >> 32);
+      heavy.src[j] = u;
+      heavy.base[j] = (int32_t)(old & 0xffffffffull);
       deg = 0;
     }
     // block-cooperative expansion of very high-degree sources
@@ -906,39 +912,39 @@ __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__res
 
 namespace gi {
 
-// Sources with >= t_heavy arcs, collected by k_push: their arcs are cut into
-// chunks of kHeavyChunk and chunk c (numbered across all deferred sources) is
-// expanded by block c mod gridDim, so one hub no longer serialises a block.
-constexpr int32_t kHeavyChunk = 4096;
-
+// Sources with >= t_heavy arcs, deferred by k_push: their arcs are cut into
+// chunks of kHeavyChunk, numbered across all deferred sources, and chunk c is
+// expanded by block c mod gridDim (its source found by binary search over the
+// entries' first chunks), so one hub no longer serialises a block and the
+// work per block does not grow with the number of deferred sources.
 template <class Op>
 __global__ void __launch_bounds__(kPushBlock) k_push_heavy(Op op, const int32_t *__restrict__ ptr,
-                                                           const int32_t *__restrict__ idx,
-                                                           int32_t *heavy_q, int64_t n,
-                                                           const uint32_t *__restrict__ to, OutSet out) {
-  const int32_t H = *(volatile int32_t *)(heavy_q + n);
-  int64_t first = 0;  // global index of source i's first chunk
-  for (int32_t i = 0; i < H; ++i) {
-    const int32_t u = heavy_q[i];
-    const int32_t a = __ldg(ptr + u), deg = __ldg(ptr + u + 1) - a;
-    const int64_t nch = (deg + kHeavyChunk - 1) / kHeavyChunk;
-    int64_t c = ((int64_t)blockIdx.x - first) % gridDim.x;
-    if (c < 0) c += gridDim.x;
-    for (; c < nch; c += gridDim.x) {
-      const int32_t k0 = (int32_t)c * kHeavyChunk;
-      const int32_t len = min(kHeavyChunk, deg - k0);
-      push_strided(op, u, a + k0, len, (int32_t)threadIdx.x, kPushBlock, idx, to, out);
+                                                           const int32_t *__restrict__ idx, void *heavy_mem,
+                                                           int64_t n, const uint32_t *__restrict__ to, OutSet out) {
+  const HeavyList heavy = heavy_at(heavy_mem, n);
+  const unsigned long long c64 = *(volatile unsigned long long *)heavy.ctr;
+  const int32_t H = (int32_t)(c64 >> 32), C = (int32_t)(c64 & 0xffffffffull);
+  for (int32_t c = blockIdx.x; c < C; c += gridDim.x) {
+    int32_t lo = 0, hi = H - 1;  // last entry whose first chunk is <= c
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (heavy.base[mid] <= c) lo = mid;
+      else hi = mid - 1;
     }
-    first += nch;
+    const int32_t u = heavy.src[lo];
+    const int32_t a = __ldg(ptr + u), deg = __ldg(ptr + u + 1) - a;
+    const int32_t k0 = (c - heavy.base[lo]) * kHeavyChunk;
+    const int32_t len = min(kHeavyChunk, deg - k0);
+    push_strided(op, u, a + k0, len, (int32_t)threadIdx.x, kPushBlock, idx, to, out);
   }
   // the last block to finish empties the list for the next push (every block
-  // has read H before it takes its ticket)
+  // has read the counter before it takes its ticket)
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(heavy_q + n + 1, 1) == (int32_t)gridDim.x - 1) {
-      heavy_q[n] = 0;
-      heavy_q[n + 1] = 0;
+    if (atomicAdd(heavy.ticket, 1) == (int32_t)gridDim.x - 1) {
+      *heavy.ctr = 0ull;
+      *heavy.ticket = 0;
       __threadfence();
     }
   }
@@ -1155,28 +1161,29 @@ int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const 
   if (tc < tw) tc = tw;
   const int32_t th = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_heavy > 0 ? max(sc.t_heavy, tc) : INT32_MAX);
   if (th != INT32_MAX) GI_TRY(heavy_get(g, s));
+  void *heavy = g->heavy_mem;
   const int block = kPushBlock;
   int grid;
   const int tok = timing_begin(kClassPush, s);
   if (mode == kSrcQueue) {
     grid = g->num_sms * (2048 / block);
     k_push<Op, kSrcQueue><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, from->queue, from->count, nullptr, g->n,
-                                                 to, out, tw, tc, th, g->heavy_q);
+                                                 to, out, tw, tc, th, heavy);
   } else if (mode == kSrcBitmap) {
     grid = grid_for(g, g->n, block, 2048 / block);
     const FSet fs = (sc.dense_rep == GI_REP_BOOL && from->boolmap && (from->reps & GI_REP_BOOL))
                         ? FSet(static_cast<const uint8_t *>(from->boolmap))
                         : FSet(static_cast<const uint32_t *>(from->bitmap));
     k_push<Op, kSrcBitmap><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, fs, g->n, to, out, tw,
-                                                  tc, th, g->heavy_q);
+                                                  tc, th, heavy);
   } else {
     grid = grid_for(g, g->n, block, 2048 / block);
     k_push<Op, kSrcAll><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, nullptr, g->n, to, out,
-                                               tw, tc, th, g->heavy_q);
+                                               tw, tc, th, heavy);
   }
   GI_LAUNCH_CHECK();
   if (th != INT32_MAX) {
-    k_push_heavy<Op><<<g->num_sms * 4, block, 0, s>>>(op, g->out.ptr, g->out.idx, g->heavy_q, g->n, to, out);
+    k_push_heavy<Op><<<g->num_sms * 4, block, 0, s>>>(op, g->out.ptr, g->out.idx, heavy, g->n, to, out);
     GI_LAUNCH_CHECK();
   }
   timing_end(tok, s);

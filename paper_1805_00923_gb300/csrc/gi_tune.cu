@@ -130,7 +130,7 @@ extern "C" int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_sche
       {&gi_schedule::tile_edges, {256, 512, 1024, 2048, 4096, 8192}},
       {&gi_schedule::t_warp, {8, 16, 32, 64}},
       {&gi_schedule::t_cta, {256, 512, 1024, 2048, 4096}},
-      {&gi_schedule::t_heavy, {4096, 8192, 16384, 32768, 65536, INT32_MAX}},
+      {&gi_schedule::t_heavy, {256, 512, 1024, 2048, 4096, 16384, INT32_MAX}},
   };
   if (algo == GI_ALGO_PAGERANK && start->direction == GI_DIR_DENSE_PULL)
     knobs.push_back({&gi_schedule::num_segments, {1, 2, 4, 8}});

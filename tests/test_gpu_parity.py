@@ -52,14 +52,18 @@ def test_bfs_rmat16_all_schedules(gi, direction, balance):
         assert np.array_equal(t["frontier"], levels)
 
 
+@pytest.mark.parametrize("expand", ["block", "all_blocks"])
 @pytest.mark.parametrize("name", ADVERSARIAL)
 @pytest.mark.parametrize("direction", DIRS)
-def test_bfs_adversarial(gi, name, direction):
+def test_bfs_adversarial(gi, name, direction, expand):
+    """Sources of degree >= 256 are expanded by one block (t_heavy off) or
+    split over all blocks (the default t_heavy)."""
     hg = adversarial(name)
     g = _load(gi, hg)
+    kw = dict(t_cta=256, t_heavy=INT_MAX) if expand == "block" else {}
     for src in sorted({0, hg.n // 2, hg.n - 1}):
         want_d, want_p, _ = oracle.bfs(hg, src)
-        d, p = gi.bfs(g, src, sched=gi.schedule(direction, t_cta=256))
+        d, p = gi.bfs(g, src, sched=gi.schedule(direction, **kw))
         assert np.array_equal(_np(d), want_d), (name, src)
         assert np.array_equal(_np(p), want_p), (name, src)
 
@@ -123,6 +127,8 @@ def test_sssp_adversarial(gi, name, direction):
     g = _load(gi, hg)
     want, _ = oracle.sssp(hg, 0)
     assert np.array_equal(_np(gi.sssp(g, 0, sched=gi.schedule(direction))), want)
+    # block-cooperative expansion instead of the all-block split
+    assert np.array_equal(_np(gi.sssp(g, 0, sched=gi.schedule(direction, t_cta=256, t_heavy=INT_MAX))), want)
 
 
 def test_sssp_grid(gi):
