@@ -81,11 +81,12 @@ int gi_graph_free(gi_graph *g);
 int gi_graph_info(const gi_graph *g, int64_t *n, int64_t *m, int32_t *max_deg);
 
 /*
- * The hot-source set of the shared-memory pull (gi_schedule.hot_cache), built
- * on first use from the in-edges (this call builds it, syncing `stream`): *k
+ * The hot-source set of the on-chip pull (gi_schedule.hot_cache), built on
+ * first use from the in-edges (this call builds it, syncing `stream`): *k
  * sources, those of out-degree >= *min_deg, where min_deg is the smallest
  * threshold with at most 40,960 sources (k = 0, min_deg = 0 for a graph
- * without arcs).  Errors: GI_ERR_UNSUPPORTED without in-edges, GI_ERR_OOM.
+ * without arcs); their slots follow descending degree.  Errors:
+ * GI_ERR_UNSUPPORTED without in-edges, GI_ERR_OOM.
  */
 int gi_graph_hot_info(gi_graph *g, int32_t *k, int32_t *min_deg, void *stream);
 
@@ -180,7 +181,7 @@ typedef struct gi_schedule {
                         /* are read from on-chip memory instead of one L2 sector per     */
                         /* arc (the GPU form of the cache partitioning of Sec. 5).       */
                         /* 1 = in shared memory, one persistent block per SM (tiles of   */
-                        /* 512..2048 arcs); 2 = a dense array kept in L1 (tiles of       */
+                        /* 512..2048 arcs); 2 = a dense array cached in L1 (tiles of     */
                         /* 512..8192 arcs); 0 = off.  Results are bit-identical to 0.    */
                         /* Ignored elsewhere.  Built once per graph (4m bytes).          */
 } gi_schedule;

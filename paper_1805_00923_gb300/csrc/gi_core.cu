@@ -694,11 +694,13 @@ void free_tiles(TileSet *ts, cudaStream_t s) {
 }
 
 // =========================================================== hot sources ==
-// Selection of the hot sources for the shared-memory cache of the dense pull:
-// a histogram of out-degrees (65,536 bins, the last one open-ended) gives the
+// Selection of the hot sources for the on-chip cache of the dense pull: a
+// histogram of out-degrees (65,536 bins, the last one open-ended) gives the
 // smallest degree threshold whose count of sources does not exceed kHotMax.
 // Since m < 2^31, fewer than 32,768 vertices have degree >= 65,535, so the
-// threshold always exists.  Slots follow vertex-id order (exclusive scan).
+// threshold always exists.  Slots follow descending degree (bin by bin from
+// the top; the order inside a bin is immaterial), so the most-gathered values
+// share the first cache lines.
 constexpr int kHotBins = 65536, kHotSmemBins = 4096;
 
 __global__ void k_hot_hist(const int32_t *__restrict__ deg, int64_t n, int32_t *hist) {
@@ -715,8 +717,10 @@ __global__ void k_hot_hist(const int32_t *__restrict__ deg, int64_t n, int32_t *
     if (sh[i]) atomicAdd(hist + i, sh[i]);
 }
 
-// One block of 1024 threads; thread t owns bins [64t, 64t+64).  out = {threshold, count}.
-__global__ void __launch_bounds__(1024) k_hot_pick(const int32_t *__restrict__ hist, int32_t cap, int32_t *out) {
+// One block of 1024 threads; thread t owns bins [64t, 64t+64).  start[d] =
+// number of vertices in bins above d; out = {threshold, count}.
+__global__ void __launch_bounds__(1024) k_hot_pick(const int32_t *__restrict__ hist, int32_t cap, int32_t *start,
+                                                   int32_t *out) {
   constexpr int kPer = kHotBins / 1024;
   __shared__ int64_t s_warp[32];
   __shared__ int32_t s_best;
@@ -737,8 +741,13 @@ __global__ void __launch_bounds__(1024) k_hot_pick(const int32_t *__restrict__ h
   __syncthreads();
   int64_t before = 0;  // totals of the warps with larger t
   for (int w = 0; w < rw; ++w) before += s_warp[w];
-  const int64_t after = before + x - own;  // sources with degree in bins above this thread's range
+  const int64_t after = before + x - own;  // vertices in bins above this thread's range
   int64_t run = after;
+  for (int d = t * kPer + kPer - 1; d >= t * kPer; --d) {
+    start[d] = (int32_t)(run < INT32_MAX ? run : INT32_MAX);
+    run += hist[d];
+  }
+  run = after;
   int32_t cand = kHotBins;
   for (int d = t * kPer + kPer - 1; d >= t * kPer && d >= 1; --d) {
     run += hist[d];
@@ -759,15 +768,18 @@ __global__ void __launch_bounds__(1024) k_hot_pick(const int32_t *__restrict__ h
   }
 }
 
-__global__ void k_hot_flags(const int32_t *__restrict__ deg, int64_t n, int32_t min_deg, int32_t *flag) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    flag[v] = deg[v] >= min_deg ? 1 : 0;
-}
-
-__global__ void k_hot_src(const int32_t *__restrict__ deg, int64_t n, int32_t min_deg,
-                          const int32_t *__restrict__ slot, int32_t *src) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    if (deg[v] >= min_deg) src[slot[v]] = (int32_t)v;
+// slot[v] and src[slot] for the hot vertices: bin start + arrival order in the bin
+__global__ void k_hot_slots(const int32_t *__restrict__ deg, int64_t n, int32_t min_deg,
+                            const int32_t *__restrict__ start, int32_t *fill, int32_t *slot, int32_t *src) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = deg[v];
+    if (d >= min_deg) {
+      const int32_t b = min(d, kHotBins - 1);
+      const int32_t s = start[b] + atomicAdd(fill + b, 1);
+      slot[v] = s;
+      src[s] = (int32_t)v;
+    }
+  }
 }
 
 __global__ void k_hot_remap(const int32_t *__restrict__ idx, int64_t m, const int32_t *__restrict__ deg,
@@ -785,24 +797,25 @@ int hot_get(gi_graph *g, cudaStream_t s) {
   const int64_t n = g->n, m = g->m;
   int st = GI_OK;
   if (n > 0 && m > 0 && g->has_csc) {
+    // hist[kHotBins] | start[kHotBins] | fill[kHotBins] | {threshold, count}
     int32_t *hist = nullptr;
-    st = dev_alloc_n(&hist, kHotBins + 2, s);
-    if (st == GI_OK && cudaMemsetAsync(hist, 0, sizeof(int32_t) * (kHotBins + 2), s) != cudaSuccess)
+    st = dev_alloc_n(&hist, 3 * kHotBins + 2, s);
+    int32_t *start = hist + kHotBins, *fill = hist + 2 * kHotBins, *pick_out = hist + 3 * kHotBins;
+    if (st == GI_OK && cudaMemsetAsync(hist, 0, sizeof(int32_t) * (3 * kHotBins + 2), s) != cudaSuccess)
       st = cuda_fail(cudaGetLastError(), "hot histogram", __FILE__, __LINE__);
     if (st == GI_OK) {
       k_hot_hist<<<grid_for(g, n, 256, 2), 256, 0, s>>>(g->out_deg, n, hist);
-      k_hot_pick<<<1, 1024, 0, s>>>(hist, kHotMax, hist + kHotBins);
+      k_hot_pick<<<1, 1024, 0, s>>>(hist, kHotMax, start, pick_out);
       st = launch_status(2);
     }
     int32_t pick[2] = {kHotBins, 0};
-    if (st == GI_OK && (cudaMemcpyAsync(pick, hist + kHotBins, sizeof(pick), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (st == GI_OK && (cudaMemcpyAsync(pick, pick_out, sizeof(pick), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                         cudaStreamSynchronize(s) != cudaSuccess))
       st = cuda_fail(cudaGetLastError(), "hot threshold", __FILE__, __LINE__);
-    dev_free(hist, s);
     h.min_deg = pick[0];
     h.k = pick[1];
     if (st == GI_OK && h.k > 0) {
-      int32_t *flag = g->ws->tmp_i32, *slot = g->ws->tmp2_i32;
+      int32_t *slot = g->ws->tmp_i32;
       const int k4 = (h.k + 3) & ~3;
       st = dev_alloc_n(&h.src, h.k, s);
       if (st == GI_OK) st = dev_alloc_n(&h.vals, k4, s);
@@ -810,12 +823,7 @@ int hot_get(gi_graph *g, cudaStream_t s) {
       if (st == GI_OK && cudaMemsetAsync(h.vals, 0, sizeof(float) * k4, s) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "hot values", __FILE__, __LINE__);
       if (st == GI_OK) {
-        k_hot_flags<<<grid_for(g, n, 256), 256, 0, s>>>(g->out_deg, n, h.min_deg, flag);
-        st = launch_status(1);
-      }
-      if (st == GI_OK) st = scan_exclusive(g, flag, slot, n, s);
-      if (st == GI_OK) {
-        k_hot_src<<<grid_for(g, n, 256), 256, 0, s>>>(g->out_deg, n, h.min_deg, slot, h.src);
+        k_hot_slots<<<grid_for(g, n, 256), 256, 0, s>>>(g->out_deg, n, h.min_deg, start, fill, slot, h.src);
         k_hot_remap<<<grid_for(g, m, 256), 256, 0, s>>>(g->in.idx, m, g->out_deg, h.min_deg, slot, h.idx);
         st = launch_status(2);
       }
@@ -823,9 +831,9 @@ int hot_get(gi_graph *g, cudaStream_t s) {
         dev_free(h.src, s);
         dev_free(h.vals, s);
         dev_free(h.idx, s);
-        return st;
       }
     }
+    dev_free(hist, s);
   }
   if (st != GI_OK) return st;
   h.built = true;
