@@ -2,8 +2,8 @@
 
 ctypes wrapper around oracle.c: plain single-threaded CPU implementations of
 the edgeset-apply path (selection, BFS, Bellman-Ford SSSP, label-propagation
-CC, PageRank, PageRankDelta, frontier statistics, the direction rules and the
-schedule-selector MLP).  Only tests/, the smoke check and the benchmark's CPU
+CC, PageRank, PageRankDelta, single-source betweenness dependencies, frontier
+statistics, the direction rules and the schedule-selector MLP).  Only tests/, the smoke check and the benchmark's CPU
 baseline may import this package; the library under paper_1805_00923_gb300/
 never does, and the two share no code.
 """
@@ -58,6 +58,7 @@ def _load():
             "or_bfs": (_i32, [_i64, _I32, _I32, _I32, _I32, _i32, _I32, _I32, _I64, _i32]),
             "or_sssp": (_i32, [_i64, _I32, _I32, _I32, _i32, _I32, _I64, _i32]),
             "or_cc": (_i32, [_i64, _I32, _I32, _I32, _I64, _i32]),
+            "or_bc": (_i32, [_i64, _I32, _I32, _I32, _I32, _i32, _F64, _F64]),
             "or_pagerank": (None, [_i64, _I32, _I32, _I32, _f64, _i32, _i32, _F64]),
             "or_prdelta": (None, [_i64, _I32, _I32, _f64, _f64, _i32, _F64, _I64]),
             "or_frontier_stats": (None, [_i64, _I32, _U8, _U8, _I64]),
@@ -153,6 +154,16 @@ def cc(g, round_cap: int = 1 << 16):
     fs = np.zeros(round_cap, np.int64)
     r = int(_load().or_cc(G.n, _ptr(G.rp, _I32), _ptr(G.ci, _I32), _ptr(label, _I32), _ptr(fs, _I64), round_cap))
     return label, fs[:min(r, round_cap)].copy()
+
+
+def bc(g, src: int, in_edges=None):
+    """(delta, sigma, levels): Brandes' single-source dependencies and path counts."""
+    G = _G(g, in_edges)
+    delta = np.empty(G.n, np.float64)
+    sigma = np.empty(G.n, np.float64)
+    nl = int(_load().or_bc(G.n, _ptr(G.rp, _I32), _ptr(G.ci, _I32), _ptr(G.in_rp, _I32), _ptr(G.in_ci, _I32),
+                           int(src), _ptr(delta, _F64), _ptr(sigma, _F64)))
+    return delta, sigma, nl
 
 
 def pagerank(g, damping=0.85, iters=20, normalize=True, in_edges=None):

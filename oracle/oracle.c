@@ -14,7 +14,10 @@
  * textbook routines (BFS order, Dijkstra, connected components), closed forms
  * (grid Manhattan distances, uniform PageRank on regular graphs, the PageRank
  * mass recurrence), the worked from() example of Sec. 5, and central finite
- * differences for the MLP gradient.  The schedule *choice* of the learned
+ * differences for the MLP gradient, and for BC the pair-dependency definition
+ * evaluated from all-pairs BFS on tiny graphs, path/star/cycle/complete-graph
+ * closed forms, grid path counts (binomials) and NetworkX's betweenness.  The
+ * schedule *choice* of the learned
  * selector is timing-dependent and has no pin ("parity unpinned"); only its
  * features and the outputs of whatever schedule it picks are pinned.
  */
@@ -219,6 +222,60 @@ int32_t or_cc(int64_t n, const int32_t *rp, const int32_t *ci, int32_t *label, i
   }
   free(front); free(front_l); free(next); free(in_next);
   return rounds;
+}
+
+/* ------------------------------------------------------------------ BC --- */
+
+/*
+ * Single-source betweenness dependencies, the per-source term of Betweenness
+ * Centrality (Sec. 7 runs BC from single starting points, synchronously, as
+ * two edgeset applies: a forward path-counting BFS and a backward dependency
+ * accumulation).  The paper prints no formula; this is Brandes' algorithm
+ * (2001) as published:
+ *   forward: BFS from src over out-arcs; sigma[w] = number of shortest
+ *     src-w paths = sum of sigma[v] over the predecessors v of w (arcs (v,w)
+ *     with d(v) = d(w) - 1); sigma[src] = 1;
+ *   backward: every w in order of non-increasing distance (reverse BFS
+ *     order) passes to each predecessor v the share
+ *     delta[v] += sigma[v] / sigma[w] * (1 + delta[w]).
+ * Predecessors are read from the in-arcs (in_rp, in_ci; the CSR twice for a
+ * symmetric graph).  delta[src] = 0; unreached vertices have sigma = delta = 0.
+ * Returns the number of BFS levels (0 if src is invalid).
+ */
+int32_t or_bc(int64_t n, const int32_t *rp, const int32_t *ci, const int32_t *in_rp, const int32_t *in_ci,
+              int32_t src, double *delta, double *sigma) {
+  for (int64_t v = 0; v < n; ++v) { delta[v] = 0.0; sigma[v] = 0.0; }
+  if (src < 0 || src >= n) return 0;
+  int32_t *d = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  for (int64_t v = 0; v < n; ++v) d[v] = -1;
+  int64_t head = 0, tail = 0;
+  order[tail++] = src;
+  d[src] = 0;
+  sigma[src] = 1.0;
+  while (head < tail) {
+    int32_t v = order[head++];
+    for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+      int32_t w = ci[e];
+      if (d[w] < 0) {
+        d[w] = d[v] + 1;
+        order[tail++] = w;
+      }
+      if (d[w] == d[v] + 1) sigma[w] += sigma[v];
+    }
+  }
+  for (int64_t i = tail - 1; i >= 0; --i) {
+    int32_t w = order[i];
+    for (int64_t e = in_rp[w]; e < in_rp[w + 1]; ++e) {
+      int32_t v = in_ci[e];
+      if (d[v] >= 0 && d[v] == d[w] - 1) delta[v] += sigma[v] / sigma[w] * (1.0 + delta[w]);
+    }
+  }
+  delta[src] = 0.0;
+  int32_t levels = d[order[tail - 1]] + 1;
+  free(d);
+  free(order);
+  return levels;
 }
 
 /* ------------------------------------------------------------ PageRank --- */
