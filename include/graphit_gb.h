@@ -328,6 +328,28 @@ int gi_pagerank_static(const int32_t *in_offsets, const int32_t *in_indices, con
 int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t iters, float *rank_dev,
                       const gi_schedule *sched, gi_trace *trace, void *stream);
 
+/*
+ * Betweenness Centrality from one source (Sec. 7 runs BC from single starting
+ * points, synchronously, as two edgeset applies per level).  Brandes'
+ * single-source dependencies:
+ *   sigma[v] = number of shortest src-v paths (forward apply s1, level by
+ *              level; sigma[src] = 1);
+ *   delta[u] = sum over out-arcs (u,v) with d(v) = d(u)+1 of
+ *              sigma[u] / sigma[v] * (1 + delta[v])  (backward apply s2).
+ * dependency_dev[n] (device, FP64) receives delta (0 at src and at unreached
+ * vertices); with accumulate != 0 it is added to what the array holds, so
+ * summing calls over all sources gives BC.  sigma_dev[n] (FP64, may be NULL)
+ * receives sigma (exact integers below 2^53).  s1 follows sched->direction
+ * like gi_bfs; s2 gathers each level's vertices in a degree-balanced pass
+ * (t_warp, t_cta), or, on symmetric graphs, runs the tiled pull over all rows
+ * when sched->direction is DENSE_PULL or, for hybrid and learned directions,
+ * when the level's |F| + m_f exceeds m/20; push directions keep the gather.
+ * Trace: the forward levels.  Errors: GI_ERR_INVALID_ARG, GI_ERR_UNSUPPORTED
+ * (DENSE_PULL without in-edges), GI_ERR_OOM, GI_ERR_CUDA.  Syncs the stream.
+ */
+int gi_bc(gi_graph *g, int32_t src, double *dependency_dev, double *sigma_dev, int32_t accumulate,
+          const gi_schedule *sched, gi_trace *trace, void *stream);
+
 /* ------------------------------------------------------------ selector -- */
 /*
  * Load the learned direction selector: a 16-64-64-3 ReLU perceptron, params as

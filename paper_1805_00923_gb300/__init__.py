@@ -241,6 +241,17 @@ def pagerank_delta(g: Graph, damping=0.85, eps=1e-7, iters=10, sched=None, trace
     return rank[:g.n]
 
 
+def bc(g: Graph, src: int, sched=None, trace: Trace | None = None, stream=None, out=None, accumulate=False,
+       want_sigma=False):
+    """gi_bc: single-source betweenness dependencies (FP64 CUDA tensor), and
+    the shortest-path counts if want_sigma.  With accumulate, adds into out."""
+    dep = out if out is not None else torch.zeros(max(g.n, 1), dtype=torch.float64, device="cuda")
+    sig = torch.empty(max(g.n, 1), dtype=torch.float64, device="cuda") if want_sigma else None
+    check(_C.gi_bc(g.handle, int(src), _vp(dep), _vp(sig), int(bool(accumulate)), ctypes.byref(_sched(sched)),
+                   _tr(trace), _stream(stream)))
+    return (dep[:g.n], sig[:g.n]) if want_sigma else dep[:g.n]
+
+
 def edgeset_apply(g: Graph, frm: VertexSet | None, to: VertexSet | None, sched, kernel_id: int, args,
                   out: VertexSet | None = None, flags: int = 0, stream=None):
     """gi_edgeset_apply: args is one of the gi_*_args ctypes structs."""

@@ -97,6 +97,7 @@ SIGNATURES = {
     "gi_cc": (ctypes.c_int, [_vp, _vp, _P(gi_schedule), _P(gi_trace), _vp]),
     "gi_pagerank": (ctypes.c_int, [_vp, _f32, _i32, _vp, _P(gi_schedule), _vp]),
     "gi_pagerank_delta": (ctypes.c_int, [_vp, _f32, _f32, _i32, _vp, _P(gi_schedule), _P(gi_trace), _vp]),
+    "gi_bc": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _P(gi_schedule), _P(gi_trace), _vp]),
     "gi_pagerank_static": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _f32, _i32, _vp, _vp]),
     "gi_selector_load": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
     "gi_selector_num_params": (ctypes.c_int, []),

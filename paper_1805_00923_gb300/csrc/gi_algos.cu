@@ -1,7 +1,8 @@
 // Algorithm drivers built on the edgeset apply kernels: BFS, Bellman-Ford
-// SSSP, label-propagation CC, PageRank and PageRankDelta (Sec. 7's
-// benchmarks).  Each iteration: fused frontier statistics + direction choice,
+// SSSP, label-propagation CC, PageRank, PageRankDelta and single-source
+// Betweenness Centrality (Sec. 7's benchmarks).  Each iteration: fused frontier statistics + direction choice,
 // one traversal, and (where the algorithm needs one) a vertex epilogue.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -633,6 +634,283 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "prdelta", __FILE__, __LINE__);
+  return st;
+}
+
+// ==================================================== Betweenness Centrality ==
+// Single-source dependencies (Brandes), run as the paper runs BC (Sec. 7):
+// synchronously, with two edgeset applies per level.
+//   s1 (forward): path-counting BFS; a vertex found at level d+1 receives
+//     sigma[v] = sum of sigma[u] over its in-neighbours u in F_d.  Push adds
+//     with FP64 atomics (sums of integers: exact below 2^53), pull gathers.
+//   s2 (backward): levels from the deepest up; w[v] = (1 + delta[v]) / sigma[v]
+//     is set on level d+1 and zero everywhere else, so for u in level d
+//     delta[u] = sigma[u] * sum of w over u's out-neighbours.  Either a
+//     degree-balanced gather over level d's queue (thread / warp / block per
+//     vertex) or, for large levels of symmetric graphs, the tiled pull over
+//     all rows with the level as destination filter.  Both sum in a fixed
+//     order, without atomics.
+namespace gi {
+
+struct OpBCFwd {
+  using V = double;
+  int32_t *depth;
+  double *sigma;
+  int32_t level;  // depth of the vertices found in this step
+  __device__ static V identity() { return 0.0; }
+  __device__ static V combine(V a, V b) { return a + b; }
+  __device__ V edge_val(int32_t u, int32_t) const { return sigma[u]; }
+  __device__ bool dst_ok(int32_t v) const { return depth[v] == -1; }
+  __device__ bool finish(int32_t v, V s) const {
+    if (s > 0.0) {
+      depth[v] = level;
+      sigma[v] = s;
+      return true;
+    }
+    return false;
+  }
+  __device__ bool push(int32_t u, int32_t v, int32_t) const {
+    const int32_t d = *(volatile int32_t *)(depth + v);
+    if (d != -1 && d != level) return false;
+    bool won = false;
+    if (d == -1) {
+      const int32_t old = atomicCAS(depth + v, -1, level);
+      won = (old == -1);
+      if (!won && old != level) return false;
+    }
+    atomicAdd(sigma + v, sigma[u]);
+    return won;
+  }
+};
+
+struct OpBCBack {
+  using V = double;
+  const double *w;
+  double *delta;
+  const double *sigma;
+  const int32_t *depth;
+  int32_t level;  // rows (sources of the out-arcs) being accumulated
+  __device__ static V identity() { return 0.0; }
+  __device__ static V combine(V a, V b) { return a + b; }
+  __device__ V edge_val(int32_t v, int32_t) const { return __ldg(w + v); }
+  __device__ bool dst_ok(int32_t u) const { return depth[u] == level; }
+  __device__ bool finish(int32_t u, V s) const {
+    delta[u] = sigma[u] * s;
+    return false;
+  }
+  __device__ bool push(int32_t, int32_t, int32_t) const { return false; }
+};
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Sum of w[idx[a + k]] for k = k0, k0 + step, ... < deg, 8 loads in flight.
+__device__ __forceinline__ double bc_row_sum(const int32_t *__restrict__ idx, const double *__restrict__ w,
+                                             int32_t a, int32_t deg, int32_t k0, int32_t step) {
+  double x = 0.0;
+  for (int32_t k = k0; k < deg; k += 8 * step) {
+    int32_t v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = k + j * step < deg ? __ldg(idx + a + k + j * step) : -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (v[j] >= 0) x += __ldg(w + v[j]);
+  }
+  return x;
+}
+
+constexpr int kBcBlock = 256;
+
+// delta[u] = sigma[u] * sum_{v in out(u)} w[v] for every u of the queue: rows
+// of >= t_cta arcs by the whole block, >= t_warp by a warp, the rest by their
+// own thread.
+__global__ void __launch_bounds__(kBcBlock) k_bc_gather(const int32_t *__restrict__ q, int64_t cnt,
+                                                        const int32_t *__restrict__ ptr,
+                                                        const int32_t *__restrict__ idx,
+                                                        const double *__restrict__ w,
+                                                        const double *__restrict__ sigma, double *delta,
+                                                        int32_t t_warp, int32_t t_cta) {
+  __shared__ int32_t s_owner, s_a, s_deg;
+  __shared__ double s_red[kBcBlock / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t base = (int64_t)blockIdx.x * kBcBlock; base < cnt; base += (int64_t)gridDim.x * kBcBlock) {
+    const int64_t i = base + tid;
+    int32_t u = -1, a = 0, deg = 0;
+    if (i < cnt) {
+      u = q[i];
+      a = __ldg(ptr + u);
+      deg = __ldg(ptr + u + 1) - a;
+    }
+    while (true) {
+      if (tid == 0) s_owner = -1;
+      __syncthreads();
+      if (deg >= t_cta) s_owner = tid;
+      __syncthreads();
+      const int owner = s_owner;
+      if (owner < 0) break;
+      if (tid == owner) {
+        s_a = a;
+        s_deg = deg;
+      }
+      __syncthreads();
+      double x = warp_sum(bc_row_sum(idx, w, s_a, s_deg, tid, kBcBlock));
+      if (lane == 0) s_red[warp] = x;
+      __syncthreads();
+      if (tid == owner) {
+        double y = 0.0;
+        for (int k = 0; k < kBcBlock / 32; ++k) y += s_red[k];
+        delta[u] = sigma[u] * y;
+        deg = 0;
+      }
+      __syncthreads();
+    }
+    while (true) {
+      const unsigned bal = __ballot_sync(0xffffffffu, deg >= t_warp);
+      if (!bal) break;
+      const int l = __ffs(bal) - 1;
+      const int32_t la = __shfl_sync(0xffffffffu, a, l), ld = __shfl_sync(0xffffffffu, deg, l);
+      const double x = warp_sum(bc_row_sum(idx, w, la, ld, lane, 32));
+      if (lane == l) {
+        delta[u] = sigma[u] * x;
+        deg = 0;
+      }
+    }
+    if (deg > 0) delta[u] = sigma[u] * bc_row_sum(idx, w, a, deg, 0, 1);
+  }
+}
+
+// w[v] = (1 + delta[v]) / sigma[v] on the level below the one accumulated
+// next (q_set); w back to 0 on the level that was below it before (q_clear).
+__global__ void k_bc_weights(const int32_t *__restrict__ q_set, int64_t n_set, const int32_t *__restrict__ q_clear,
+                             int64_t n_clear, const double *__restrict__ delta, const double *__restrict__ sigma,
+                             double *w) {
+  const int64_t nmax = n_set > n_clear ? n_set : n_clear;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nmax; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n_clear) w[q_clear[i]] = 0.0;
+    if (i < n_set) {
+      const int32_t v = q_set[i];
+      w[v] = (1.0 + delta[v]) / sigma[v];
+    }
+  }
+}
+
+__global__ void k_bc_init(int32_t *depth, double *sigma, double *delta, double *w, int64_t n, int32_t src) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    depth[i] = i == src ? 0 : -1;
+    sigma[i] = i == src ? 1.0 : 0.0;
+    delta[i] = 0.0;
+    w[i] = 0.0;
+  }
+}
+
+// dependency[v] (+)= delta[v], with delta[src] = 0 (src is no interior vertex)
+__global__ void k_bc_out(const double *__restrict__ delta, double *dep, int64_t n, int32_t src, int32_t accumulate) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = i == src ? 0.0 : delta[i];
+    dep[i] = accumulate ? dep[i] + x : x;
+  }
+}
+
+// one forward step (s1) from F into N at level `level`
+static int bc_forward(gi_graph *g, VsetPair &P, int32_t dir, const gi_schedule &sc, int32_t *depth, double *sigma,
+                      int32_t level, cudaStream_t s) {
+  GI_TRY(vset_clear(P.N, s));
+  const OutSet o = out_of(P.N, true);
+  const OpBCFwd op{depth, sigma, level};
+  if (dir == GI_DIR_DENSE_PULL) {
+    GI_TRY(vset_ensure_bitmap(P.F, s));
+    GI_TRY(launch_pull_tiled(g, op, g->in, g->in_tiles, FSet(static_cast<const uint32_t *>(P.F->bitmap)), nullptr,
+                             o, s, kClassOtherPull, sc.balance == GI_BAL_VERTEX));
+  } else if (dir == GI_DIR_SPARSE_PUSH) {
+    GI_TRY(vset_ensure_queue(P.F, s));
+    GI_TRY(launch_push(g, op, kSrcQueue, P.F, nullptr, o, sc, s));
+  } else {
+    GI_TRY(vset_ensure_bitmap(P.F, s));
+    GI_TRY(launch_push(g, op, kSrcBitmap, P.F, nullptr, o, sc, s));
+  }
+  P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
+  return GI_OK;
+}
+
+}  // namespace gi
+
+extern "C" int gi_bc(gi_graph *g, int32_t src, double *dependency, double *sigma_out, int32_t accumulate,
+                     const gi_schedule *sched, gi_trace *trace, void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_TRY(check_schedule(sched));
+  GI_ARG(src >= 0 && src < g->n, "source out of range");
+  GI_ARG(dependency != nullptr, "dependency is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const gi_schedule sc = *sched;
+  if (sc.direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sc.direction));
+  GI_TRY(ensure_tiles(g, sc, s));
+  const int64_t n = g->n;
+  VsetPair P;
+  int32_t *depth = nullptr, *levels = nullptr;
+  double *sigma = sigma_out, *own_sigma = nullptr, *delta = nullptr, *w = nullptr;
+  int st = pair_alloc(g, P, s);
+  if (st == GI_OK) st = dev_alloc_n(&depth, n, s);
+  if (st == GI_OK) st = dev_alloc_n(&levels, n, s);
+  if (st == GI_OK && !sigma) st = dev_alloc_n(&own_sigma, n, s), sigma = own_sigma;
+  if (st == GI_OK) st = dev_alloc_n(&delta, n, s);
+  if (st == GI_OK) st = dev_alloc_n(&w, n, s);
+  if (st == GI_OK) {
+    k_bc_init<<<grid_for(g, n, 256), 256, 0, s>>>(depth, sigma, delta, w, n, src);
+    st = launch_status(1);
+  }
+  if (st == GI_OK) st = front_init(g, P.F, src, s);
+  if (st == GI_OK) st = ctrl_init(g, g->n, g->m, s);
+  // level d's vertices: levels[off[d] .. off[d+1]); its frontier statistics in nf/mf
+  std::vector<int64_t> off{0}, nf, mf;
+  if (st == GI_OK)
+    st = frontier_loop(g, P, sc, true, trace, s, [&](int32_t it, int32_t dir) -> int {
+      const int64_t k = g->ctrl_host[kNf];
+      nf.push_back(k);
+      mf.push_back(g->ctrl_host[kMf]);
+      GI_TRY(vset_ensure_queue(P.F, s));
+      GI_CUDA(cudaMemcpyAsync(levels + off.back(), P.F->queue, sizeof(int32_t) * (size_t)k,
+                              cudaMemcpyDeviceToDevice, s));
+      off.push_back(off.back() + k);
+      return bc_forward(g, P, dir, sc, depth, sigma, it + 1, s);
+    });
+  const int32_t D = (int32_t)nf.size();
+  const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
+  const int32_t tc = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_cta > 0 ? max(sc.t_cta, tw) : 1024);
+  for (int32_t d = D - 2; d >= 1 && st == GI_OK; --d) {
+    const int64_t n_set = nf[d + 1], n_clear = d + 2 < D ? nf[d + 2] : 0;
+    k_bc_weights<<<grid_for(g, n_set > n_clear ? n_set : n_clear, 256), 256, 0, s>>>(
+        levels + off[d + 1], n_set, levels + off[d + 2 < D ? d + 2 : d + 1], n_clear, delta, sigma, w);
+    st = launch_status(1);
+    if (st != GI_OK) break;
+    // s2's direction: forced by the schedule, else Ligra's rule on level d
+    bool dense = g->symmetric && sc.balance != GI_BAL_VERTEX;
+    if (sc.direction == GI_DIR_SPARSE_PUSH || sc.direction == GI_DIR_DENSE_PUSH) dense = false;
+    else if (sc.direction != GI_DIR_DENSE_PULL) dense = dense && (nf[d] + mf[d]) > g->m / 20;
+    if (dense) {
+      const OpBCBack op{w, delta, sigma, depth, d};
+      st = launch_pull_tiled(g, op, g->in, g->in_tiles, FSet(), nullptr, OutSet(), s, kClassOtherPull);
+    } else {
+      const int grid = (int)std::min<int64_t>((nf[d] + kBcBlock - 1) / kBcBlock, (int64_t)g->num_sms * 8);
+      k_bc_gather<<<grid, kBcBlock, 0, s>>>(levels + off[d], nf[d], g->out.ptr, g->out.idx, w, sigma, delta, tw,
+                                            tc);
+      st = launch_status(1);
+    }
+  }
+  if (st == GI_OK) {
+    k_bc_out<<<grid_for(g, n, 256), 256, 0, s>>>(delta, dependency, n, src, accumulate);
+    st = launch_status(1);
+  }
+  dev_free(depth, s);
+  dev_free(levels, s);
+  dev_free(own_sigma, s);
+  dev_free(delta, s);
+  dev_free(w, s);
+  pair_free(P, s);
+  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "bc", __FILE__, __LINE__);
   return st;
 }
 

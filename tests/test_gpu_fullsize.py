@@ -5,6 +5,8 @@ PageRankDelta (eps 1e-7, 10 rounds, hybrid) and CC (hybrid) against the
 oracle on every vertex.  R-MAT scale 24 (16.8M vertices, ~510M arcs, weights in
 [1,1000)): BFS and SSSP from one sampled source, bit-exact against the oracle,
 plus the per-arc invariants (|depth(u)-depth(v)| <= 1, dist(v) <= dist(u)+w).
+R-MAT scale 22: Betweenness Centrality from one sampled source (path counts
+exact, dependencies within 1e-9 relative).
 """
 import numpy as np
 import pytest
@@ -59,3 +61,18 @@ def test_scale24_bfs_sssp_sampled_source(gi, rmat24):
     assert np.array_equal(dist, want)
     reach = dist[u] < np.iinfo(np.int32).max
     assert (dist[hg.col][reach].astype(np.int64) <= dist[u][reach].astype(np.int64) + hg.wt[reach]).all()
+
+
+def test_scale22_bc_sampled_source(gi, rmat22):
+    hg = rmat22
+    g = gi.Graph.from_host(hg)
+    src = int(gg.pick_sources(hg, 1, seed=22)[0])
+    dep, sig = gi.bc(g, src, sched=gi.schedule("hybrid_pull"), want_sigma=True)
+    want_d, want_s, _ = oracle.bc(hg, src)
+    assert np.array_equal(sig.cpu().numpy(), want_s)
+    dep = dep.cpu().numpy()
+    assert np.array_equal(dep == 0, want_d == 0)
+    assert np.allclose(dep, want_d, rtol=1e-9, atol=0)
+    # sum of dependencies = sum over reached t of (d(s,t) - 1)
+    depth = oracle.bfs(hg, src)[0]
+    assert np.isclose(dep.sum(), float((depth[depth > 0] - 1).sum()), rtol=1e-9)
