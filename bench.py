@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--tune-budget", type=int, default=12, help="autotuner trials per algorithm (untimed)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the untimed autotuning and direction comparison (profiling runs)")
-    p.add_argument("--workload", choices=["rmat22", "rmat24_bfs_sssp", "grid4096", "batch512"], default="rmat22",
+    p.add_argument("--workload", choices=["rmat22", "rmat24_bfs_sssp", "grid4096", "batch512", "bc"], default="rmat22",
                    help="rmat22 (default): the timed PR+PRD+CC step; the others measure the remaining "
                         "configurations and print their own JSON line")
     p.add_argument("--sources", type=int, default=16, help="sources per graph for the BFS/SSSP workloads")
@@ -429,6 +429,50 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def run_bc(args):
+    """R-MAT scale --scale, single-source Betweenness Centrality from 10 sources
+    (the paper averages BC over 10 starting points), per forward/backward schedule."""
+    import time as _time
+    import torch
+    import graphgen as gg
+    import oracle
+    import paper_1805_00923_gb300 as gi
+    from paper_1805_00923_gb300 import selector as sel
+    torch.cuda.set_device(0)
+    sel.install()
+    hg = gg.rmat_graph(args.scale, seed=1)
+    g = gi.Graph.from_host(hg)
+    srcs = [int(x) for x in gg.pick_sources(hg, 10, seed=1)]
+    out = {}
+    dep = torch.zeros(hg.n, dtype=torch.float64, device="cuda")
+    for name, sc in [("hybrid_pull", gi.schedule("hybrid_pull")),
+                     ("hybrid_pull_ligra", gi.schedule("hybrid_pull", rule="ligra")),
+                     ("learned", gi.schedule("learned")),
+                     ("sparse_push", gi.schedule("sparse_push")),
+                     ("dense_pull", gi.schedule("dense_pull"))]:
+        gi.bc(g, srcs[0], sched=sc, out=dep)
+        a, b = _events()
+        a.record()
+        for s_ in srcs:
+            gi.bc(g, s_, sched=sc, out=dep)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / len(srcs)
+        out[name] = {"ms_per_source": ms, "gteps_nominal": hg.m / (ms * 1e-3) / 1e9}
+    oracle.build()
+    t0 = _time.perf_counter()
+    oracle.bc(hg, srcs[0])
+    cpu_ms = (_time.perf_counter() - t0) * 1e3
+    best = min(out.values(), key=lambda r: r["ms_per_source"])
+    print(json.dumps({"metric": METRIC, "workload": f"rmat{args.scale}_bc10", "value": out["hybrid_pull"]["gteps_nominal"],
+                      "unit": "GTEPS", "n": hg.n, "m": hg.m, "sources": len(srcs), "results": out,
+                      "best_ms_per_source": best["ms_per_source"],
+                      "cpu_baseline": {"kind": "oracle", "cores": 1, "ms_per_source": cpu_ms,
+                                       "sample": "oracle Brandes BC from the first source"},
+                      "note": "nominal GTEPS = m / time per source; forward and backward applies per level"}))
+    return 0
+
+
 def run_rmat24(args):
     """R-MAT scale 24, BFS + SSSP from --sources sources: Beamer vs learned vs exhaustive best per level."""
     import numpy as np
@@ -577,7 +621,8 @@ def main():
     if args.only:
         return run_only(args)
     if args.impl == "gi" and args.workload != "rmat22":
-        return {"rmat24_bfs_sssp": run_rmat24, "grid4096": run_grid4096, "batch512": run_batch512}[args.workload](args)
+        return {"rmat24_bfs_sssp": run_rmat24, "grid4096": run_grid4096, "batch512": run_batch512,
+                "bc": run_bc}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gi(args)

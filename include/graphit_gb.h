@@ -153,6 +153,9 @@ int gi_vset_import(gi_vset *s, const int32_t *dev_ids, int64_t k, void *stream);
 /* configApplyParallelization (Table 3) */
 #define GI_BAL_VERTEX 0     /* vertex-parallel: one thread per vertex                     */
 #define GI_BAL_EDGE_AWARE 1 /* edge-aware: thread / warp / CTA by degree (t_warp, t_cta)   */
+#define GI_BAL_EDGE_PARALLEL 2 /* SparsePush one thread per arc (exclusive scan of the     */
+                               /* frontier's degrees; each arc finds its source by binary  */
+                               /* search); other traversals as EDGE_AWARE                  */
 
 /* threshold rule used by the hybrid directions */
 #define GI_RULE_BEAMER 0 /* push->pull when m_f > m_u/alpha; pull->push when |F| < n/beta */

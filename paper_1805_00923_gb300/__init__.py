@@ -54,7 +54,7 @@ def schedule(direction="hybrid_pull", **kw) -> gi_schedule:
     s.direction = direction
     for k, v in kw.items():
         if k == "balance" and isinstance(v, str):
-            v = {"vertex": GI_BAL_VERTEX, "edge_aware": GI_BAL_EDGE_AWARE}[v]
+            v = {"vertex": GI_BAL_VERTEX, "edge_aware": GI_BAL_EDGE_AWARE, "edge_parallel": L.GI_BAL_EDGE_PARALLEL}[v]
         if k == "rule" and isinstance(v, str):
             v = {"beamer": GI_RULE_BEAMER, "ligra": GI_RULE_LIGRA}[v]
         setattr(s, k, v)

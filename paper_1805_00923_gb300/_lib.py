@@ -21,7 +21,7 @@ GI_VSET_EMPTY, GI_VSET_ALL, GI_VSET_SINGLE = 0, 1, 2
 GI_REP_SPARSE, GI_REP_BOOL, GI_REP_BITMAP = 0x1, 0x2, 0x4
 GI_DIR_SPARSE_PUSH, GI_DIR_DENSE_PUSH, GI_DIR_DENSE_PULL = 0, 1, 2
 GI_DIR_HYBRID_PULL, GI_DIR_HYBRID_DPUSH, GI_DIR_LEARNED = 3, 4, 5
-GI_BAL_VERTEX, GI_BAL_EDGE_AWARE = 0, 1
+GI_BAL_VERTEX, GI_BAL_EDGE_AWARE, GI_BAL_EDGE_PARALLEL = 0, 1, 2
 GI_RULE_BEAMER, GI_RULE_LIGRA = 0, 1
 GI_K_BFS, GI_K_SSSP, GI_K_CC, GI_K_SUM, GI_K_PROBE = 1, 2, 3, 4, 5
 GI_NO_DEDUP = 0x1

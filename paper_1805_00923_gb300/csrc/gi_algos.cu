@@ -266,7 +266,12 @@ static int frontier_loop(gi_graph *g, VsetPair &P, const gi_schedule &sc, bool t
     if (dir == GI_DIR_DENSE_PULL && (!g->has_csc || !pull_ok)) dir = GI_DIR_DENSE_PUSH;
     g->ctrl_host[kDecision] = dir;
     trace_put(tr, it, g->ctrl_host);
-    GI_TRY(step(it, dir));
+    g->hint_vset = P.F;
+    g->hint_nf = g->ctrl_host[kNf];
+    const int r = step(it, dir);
+    g->hint_vset = nullptr;
+    g->hint_nf = -1;
+    GI_TRY(r);
     P.swap();
   }
   return GI_OK;
@@ -596,6 +601,8 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
     trace_put(trace, round - 1, g->ctrl_host);
     if ((st = vset_clear(P.N, s)) != GI_OK) break;
     float *cin = cb[cur], *cout = cb[cur ^ 1];
+    g->hint_vset = P.F;
+    g->hint_nf = g->ctrl_host[kNf];
     if (dir == GI_DIR_DENSE_PULL && segmented) {
       // cache-partitioned pull: segments add into seg_sum, then the vertex filter
       for (int sid = 0; sid < g->segs.num && st == GI_OK; ++sid) {
@@ -623,6 +630,8 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
         st = launch_status(1);
       }
     }
+    g->hint_vset = nullptr;
+    g->hint_nf = -1;
     P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
     P.swap();
     cur ^= 1;

@@ -166,6 +166,13 @@ static void ws_free(gi_graph *g, cudaStream_t s) {
   g->ws = nullptr;
 }
 
+int ws_scratch(gi_graph *g, int32_t **a, int32_t **b, cudaStream_t s) {
+  GI_TRY(ws_get(g, s));
+  *a = g->ws->tmp_i32;
+  *b = g->ws->tmp2_i32;
+  return GI_OK;
+}
+
 // ================================================================== scan ==
 // Three-phase exclusive scan of int32 counts: per-block scan of 2048 items,
 // scan of the block totals by one block, then add the block offsets.

@@ -141,6 +141,10 @@ struct gi_graph {
   gi::TileSet tile_cache[6];     // owned tile sets for tile_edges 256, 512, ..., 8192 (built on first use)
   gi::Segments segs;
   gi::HotSet hot;                // built on first use of the hot-source pull
+  // member count of a frontier known on the host (set by the drivers after
+  // their per-round statistics, cleared after the round); -1 = unknown
+  const gi_vset *hint_vset = nullptr;
+  int64_t hint_nf = -1;
   int64_t *ctrl = nullptr;       // device control block (kCtrlWords)
   void *heavy_mem = nullptr;     // HeavyList storage (counter, ticket, 2n entries), allocated on first use
   int64_t *ctrl_host = nullptr;  // pinned mirror
@@ -199,6 +203,8 @@ int heavy_get(gi_graph *g, cudaStream_t s);  // allocates g->heavy_mem on first 
 
 // exclusive scan of n int32 counts into out[n+1] (out[n] = total); scratch owned by g's workspace
 int scan_exclusive(gi_graph *g, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+// the workspace's two (n+2)-entry int32 scratch arrays (transient: valid until the next call that uses them)
+int ws_scratch(gi_graph *g, int32_t **a, int32_t **b, cudaStream_t s);
 
 // tiles
 int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cudaStream_t s);

@@ -133,7 +133,8 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
 int check_schedule(const gi_schedule *sc) {
   GI_ARG(sc != nullptr, "schedule is NULL");
   GI_ARG(sc->direction >= GI_DIR_SPARSE_PUSH && sc->direction <= GI_DIR_LEARNED, "unknown direction");
-  GI_ARG(sc->balance == GI_BAL_VERTEX || sc->balance == GI_BAL_EDGE_AWARE, "unknown balance mode");
+  GI_ARG(sc->balance == GI_BAL_VERTEX || sc->balance == GI_BAL_EDGE_AWARE || sc->balance == GI_BAL_EDGE_PARALLEL,
+         "unknown balance mode");
   GI_ARG(sc->num_segments >= 1 && sc->num_segments <= 1024, "num_segments must be in [1, 1024]");
   GI_ARG(sc->rule == GI_RULE_BEAMER || sc->rule == GI_RULE_LIGRA, "unknown rule");
   GI_ARG(sc->dense_rep == GI_REP_BITMAP || sc->dense_rep == GI_REP_BOOL, "dense_rep must be GI_REP_BITMAP or BOOL");
@@ -199,6 +200,13 @@ extern "C" int gi_edgeset_apply(gi_graph *g, gi_vset *from, gi_vset *to, const g
       dir = (int32_t)g->ctrl_host[kDecision];
     }
     if (dir == GI_DIR_DENSE_PULL && !g->has_csc) dir = GI_DIR_DENSE_PUSH;
+    if (from) {  // |from| was just read back with the statistics
+      g->hint_vset = from;
+      g->hint_nf = g->ctrl_host[kNf];
+    }
   }
-  return apply_dispatch(g, from, to, dir, *sched, kernel_id, kernel_args, out_modified, flags, s);
+  const int r = apply_dispatch(g, from, to, dir, *sched, kernel_id, kernel_args, out_modified, flags, s);
+  g->hint_vset = nullptr;
+  g->hint_nf = -1;
+  return r;
 }

@@ -953,6 +953,74 @@ __global__ void __launch_bounds__(kPushBlock) k_push_heavy(Op op, const int32_t 
   }
 }
 
+// Edge-parallel SparsePush (balance GI_BAL_EDGE_PARALLEL): off[] is the
+// exclusive scan of the frontier's out-degrees (off[nf] = m_f), so arc j of
+// the frontier belongs to entry i = max{i : off[i] <= j}.  Each block takes
+// kEdgeTile consecutive arcs: two threads locate the entry range it spans,
+// the block copies that slice of off[] to shared memory (when it fits) and
+// every thread finds its arcs' entries there; arcs of one source sit in
+// consecutive threads, so the index loads coalesce.
+constexpr int kEdgeTile = 1024;
+
+static __global__ void k_front_deg(const int32_t *__restrict__ q, int64_t nf, const int32_t *__restrict__ ptr,
+                            int32_t *fd) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = q[i];
+    fd[i] = __ldg(ptr + u + 1) - __ldg(ptr + u);
+  }
+}
+
+// largest i in [lo, hi] with off[i] <= j (off[lo] <= j holds)
+__device__ __forceinline__ int32_t entry_of(const int32_t *off, int32_t lo, int32_t hi, int32_t j) {
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(256) k_push_edges(Op op, const int32_t *__restrict__ q,
+                                                    const int32_t *__restrict__ off, int32_t nf,
+                                                    const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                                    const uint32_t *__restrict__ to, OutSet out) {
+  constexpr int kPer = kEdgeTile / 256;
+  __shared__ int32_t s_off[kEdgeTile + 1];
+  __shared__ int32_t s_lo, s_hi;
+  const int32_t total = off[nf];
+  for (int64_t base = (int64_t)blockIdx.x * kEdgeTile; base < total; base += (int64_t)gridDim.x * kEdgeTile) {
+    const int32_t j0 = (int32_t)base;
+    const int32_t j1 = (int32_t)(base + kEdgeTile < (int64_t)total ? base + kEdgeTile : (int64_t)total) - 1;
+    if (threadIdx.x == 0) s_lo = entry_of(off, 0, nf - 1, j0);
+    if (threadIdx.x == 1) s_hi = entry_of(off, 0, nf - 1, j1);
+    __syncthreads();
+    const int32_t lo = s_lo, hi = s_hi, cnt = hi - lo + 1;
+    const bool window = cnt <= kEdgeTile;  // zero-degree entries can widen the range
+    if (window)
+      for (int k = threadIdx.x; k < cnt; k += 256) s_off[k] = off[lo + k];
+    __syncthreads();
+    int32_t u[kPer], e[kPer], v[kPer];
+#pragma unroll
+    for (int p = 0; p < kPer; ++p) {
+      const int32_t j = j0 + (int32_t)threadIdx.x + p * 256;
+      u[p] = -1;
+      e[p] = 0;
+      v[p] = -1;
+      if (j <= j1) {
+        const int32_t i = window ? lo + entry_of(s_off, 0, cnt - 1, j) : entry_of(off, lo, hi, j);
+        const int32_t oi = window ? s_off[i - lo] : off[i];
+        u[p] = q[i];
+        e[p] = __ldg(ptr + u[p]) + (j - oi);
+        v[p] = __ldg(idx + e[p]);
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < kPer; ++p) push_apply(op, u[p], v[p], e[p], to, out);
+    __syncthreads();
+  }
+}
+
 // Canonical BFS parents for vertices discovered by push levels (which set
 // depth only): the smallest-id in-neighbour one level closer, found by
 // scanning the sorted in-neighbours (4 per round trip; a warp 32 at a time
@@ -1153,11 +1221,37 @@ int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts
   return GI_OK;
 }
 
+// Edge-parallel SparsePush over from's queue (nf members, or read back when -1).
+template <class Op>
+int launch_push_edges(gi_graph *g, const Op &op, const gi_vset *from, int64_t nf, const uint32_t *to,
+                      const OutSet &out, cudaStream_t s) {
+  if (nf < 0) {
+    int32_t c = 0;
+    GI_CUDA(cudaMemcpyAsync(&c, from->count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GI_CUDA(cudaStreamSynchronize(s));
+    nf = c;
+  }
+  if (nf == 0) return GI_OK;
+  int32_t *fd = nullptr, *off = nullptr;
+  GI_TRY(ws_scratch(g, &fd, &off, s));
+  k_front_deg<<<grid_for(g, nf, 256), 256, 0, s>>>(from->queue, nf, g->out.ptr, fd);
+  GI_LAUNCH_CHECK();
+  GI_TRY(scan_exclusive(g, fd, off, nf, s));
+  const int tok = timing_begin(kClassPush, s);
+  k_push_edges<Op><<<g->num_sms * 8, 256, 0, s>>>(op, from->queue, off, (int32_t)nf, g->out.ptr, g->out.idx, to,
+                                                   out);
+  timing_end(tok, s);
+  GI_LAUNCH_CHECK();
+  return GI_OK;
+}
+
 // Push along the out-edges.  mode: kSrcQueue (from's queue), kSrcBitmap (scan
 // from's bitmap over all vertices), kSrcAll.
 template <class Op>
 int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const uint32_t *to, const OutSet &out,
                 const gi_schedule &sc, cudaStream_t s) {
+  if (mode == kSrcQueue && sc.balance == GI_BAL_EDGE_PARALLEL)
+    return launch_push_edges(g, op, from, from == g->hint_vset ? g->hint_nf : -1, to, out, s);
   int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
   int32_t tc = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_cta > 0 ? sc.t_cta : 1024);
   if (tw != INT32_MAX && tw > kMaxTWarp) tw = kMaxTWarp;

@@ -60,12 +60,14 @@ def test_bc_adversarial(gi, name):
             _check(gi, g, hg, src, gi.schedule(direction))
 
 
-@pytest.mark.parametrize("balance", ["vertex", "block", "all_blocks"])
+@pytest.mark.parametrize("balance", ["vertex", "block", "all_blocks", "edge_parallel"])
 def test_bc_load_balance_modes(gi, balance):
-    """Thread-per-vertex gathers, block-cooperative rows, all-block push split."""
+    """Thread-per-vertex gathers, block-cooperative rows, all-block push split,
+    one thread per arc."""
     hg = adversarial("hub_tail")
     g = gi.Graph.from_host(hg)
-    kw = {"vertex": dict(balance="vertex"), "block": dict(t_cta=256, t_heavy=IMAX), "all_blocks": {}}[balance]
+    kw = {"vertex": dict(balance="vertex"), "block": dict(t_cta=256, t_heavy=IMAX), "all_blocks": {},
+          "edge_parallel": dict(balance="edge_parallel")}[balance]
     for direction in ("sparse_push", "hybrid_pull"):
         for src in (7, 0, 41_000):
             _check(gi, g, hg, src, gi.schedule(direction, **kw))

@@ -37,7 +37,7 @@ def _max_rel(a, b):
 # ----------------------------------------------------------------------- BFS
 
 @pytest.mark.parametrize("direction", DIRS)
-@pytest.mark.parametrize("balance", ["edge_aware", "vertex"])
+@pytest.mark.parametrize("balance", ["edge_aware", "vertex", "edge_parallel"])
 def test_bfs_rmat16_all_schedules(gi, direction, balance):
     hg = rmat(16)
     g = _load(gi, hg)
@@ -107,14 +107,15 @@ def test_bfs_beamer_decisions_replayed_on_cpu(gi):
 
 # ---------------------------------------------------------------------- SSSP
 
+@pytest.mark.parametrize("balance", ["edge_aware", "edge_parallel"])
 @pytest.mark.parametrize("direction", DIRS)
-def test_sssp_rmat_all_schedules(gi, direction):
+def test_sssp_rmat_all_schedules(gi, direction, balance):
     hg = rmat(14, weights=True)
     g = _load(gi, hg)
     for src in [0, *gg.pick_sources(hg, 2, seed=4)]:
         want, fs = oracle.sssp(hg, int(src))
         tr = gi.Trace(256)
-        d = gi.sssp(g, int(src), sched=gi.schedule(direction), trace=tr)
+        d = gi.sssp(g, int(src), sched=gi.schedule(direction, balance=balance), trace=tr)
         assert np.array_equal(_np(d), want)
         t = tr.as_dict()
         assert np.array_equal(t["frontier"], fs)   # synchronous rounds: same frontiers
@@ -129,6 +130,8 @@ def test_sssp_adversarial(gi, name, direction):
     assert np.array_equal(_np(gi.sssp(g, 0, sched=gi.schedule(direction))), want)
     # block-cooperative expansion instead of the all-block split
     assert np.array_equal(_np(gi.sssp(g, 0, sched=gi.schedule(direction, t_cta=256, t_heavy=INT_MAX))), want)
+    # one thread per arc
+    assert np.array_equal(_np(gi.sssp(g, 0, sched=gi.schedule(direction, balance="edge_parallel"))), want)
 
 
 def test_sssp_grid(gi):
@@ -143,13 +146,14 @@ def test_sssp_grid(gi):
 
 # ------------------------------------------------------------------------ CC
 
+@pytest.mark.parametrize("balance", ["edge_aware", "edge_parallel"])
 @pytest.mark.parametrize("direction", DIRS)
-def test_cc_all_schedules(gi, direction):
+def test_cc_all_schedules(gi, direction, balance):
     for hg in [rmat(14), adversarial("components"), adversarial("path"), grid(40, shortcut_frac=0.0)]:
         g = _load(gi, hg)
         want, fs = oracle.cc(hg)
         tr = gi.Trace(4096)
-        lab = gi.cc(g, sched=gi.schedule(direction), trace=tr)
+        lab = gi.cc(g, sched=gi.schedule(direction, balance=balance), trace=tr)
         assert np.array_equal(_np(lab), want)
         assert np.array_equal(tr.as_dict()["frontier"], fs)
 
@@ -204,14 +208,15 @@ def test_prdelta_rmat16(gi, direction):
     assert np.all(np.abs(t["frontier"] - fs[:len(t["frontier"])]) <= max(10, hg.n // 1000))
 
 
+@pytest.mark.parametrize("balance", ["edge_aware", "edge_parallel"])
 @pytest.mark.parametrize("direction", ["dense_pull", "sparse_push", "hybrid_pull"])
-def test_prdelta_sparse_rounds(gi, direction):
+def test_prdelta_sparse_rounds(gi, direction, balance):
     """eps = 1e-2 makes the active set shrink, exercising sparse rounds."""
     hg = rmat(14)
     g = _load(gi, hg)
     want, fs = oracle.prdelta(hg, 0.85, 1e-2, 10)
     tr = gi.Trace(16)
-    got = _np(gi.pagerank_delta(g, 0.85, 1e-2, 10, sched=gi.schedule(direction), trace=tr))
+    got = _np(gi.pagerank_delta(g, 0.85, 1e-2, 10, sched=gi.schedule(direction, balance=balance), trace=tr))
     rel = np.abs(got - want) / np.maximum(want, 1e-30)
     # a threshold decision that lands within FP32 rounding of eps*Rank may flip
     # and perturb a few neighbours by O(eps); everything else stays within 1e-4
@@ -234,10 +239,12 @@ def _mask_set(gi, g, mask):
     return vs
 
 
+@pytest.mark.parametrize("balance", ["edge_aware", "edge_parallel"])
 @pytest.mark.parametrize("direction", ["sparse_push", "dense_push", "dense_pull", "hybrid_pull"])
 @pytest.mark.parametrize("dedup", [True, False])
-def test_edgeset_apply_selection_probe(gi, direction, dedup):
-    """from/to selection and applyModified output equal the oracle's edge set."""
+def test_edgeset_apply_selection_probe(gi, direction, dedup, balance):
+    """from/to selection and applyModified output equal the oracle's edge set
+    (edge_parallel with a forced direction reads the frontier size back)."""
     hg = rmat(12)
     g = _load(gi, hg)
     rng = np.random.default_rng(11)
@@ -251,8 +258,8 @@ def test_edgeset_apply_selection_probe(gi, direction, dedup):
         count = torch.zeros(hg.n, dtype=torch.int32, device="cuda")
         srcsum = torch.zeros(hg.n, dtype=torch.int64, device="cuda")
         args = gi.gi_probe_args(count.data_ptr(), srcsum.data_ptr())
-        gi.edgeset_apply(g, F, T if p_to < 1 else None, gi.schedule(direction), gi.GI_K_PROBE, args, OUT,
-                         flags=0 if dedup else gi.GI_NO_DEDUP)
+        gi.edgeset_apply(g, F, T if p_to < 1 else None, gi.schedule(direction, balance=balance), gi.GI_K_PROBE,
+                         args, OUT, flags=0 if dedup else gi.GI_NO_DEDUP)
         assert np.array_equal(_np(count), cnt)
         assert np.array_equal(_np(srcsum).astype(np.uint64), ssum)
         mod = _np(OUT.export())
