@@ -184,7 +184,9 @@ def kernel_source_hash():
     b = src.index("// Warp tiles (tile_edges = 256)")
     c = src.index("struct OpPR {")
     d = src.index("};", c)
-    return hashlib.sha256((src[a:b] + src[c:d]).encode()).hexdigest()[:16]
+    # code only: comment lines and blank lines do not change the kernel
+    code = [ln.split("//")[0].rstrip() for ln in (src[a:b] + src[c:d]).splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in code if ln).encode()).hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload):

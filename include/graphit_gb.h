@@ -182,7 +182,7 @@ typedef struct gi_schedule {
   int32_t hot_cache;    /* PageRank / PageRankDelta DensePull over the whole graph:      */
                         /* the values of the (up to 40,960) highest-out-degree sources   */
                         /* are read from on-chip memory instead of one L2 sector per     */
-                        /* arc (the GPU form of the cache partitioning of Sec. 5).       */
+                        /* arc (the GPU form of the cache partitioning of Sec. 2).       */
                         /* 1 = in shared memory, one persistent block per SM (tiles of   */
                         /* 512..2048 arcs); 2 = a dense array cached in L1 (tiles of     */
                         /* 512..8192 arcs); 0 = off.  Results are bit-identical to 0.    */

@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__r
                                  BlockSync{});
 }
 
-// Hot-source pull (GPU form of the cache partitioning of Sec. 5): one
+// Hot-source pull (GPU form of the cache partitioning of Sec. 2): one
 // persistent block of kGroups x 256 threads per SM first copies the values of
 // the graph's hot sources (the HotSet, up to 160 KB) into shared memory, then
 // each 256-thread group reduces every (gridDim.x*kGroups)-th tile with the
