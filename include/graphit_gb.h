@@ -97,11 +97,26 @@ int gi_graph_device_csr(const gi_graph *g, const int32_t **offsets, const int32_
 /*
  * Build the segmented subgraphs (SSGs) used by segmented pull (cache
  * partitioning, Sec. 2 and the SSG code generation of Sec. 6): the in-edges are
- * split into num_segments groups by source range; segment s keeps the arcs whose
- * source lies in [s*ceil(n/S), (s+1)*ceil(n/S)), sorted by destination.
+ * split into num_segments groups by source range, each sorted by destination.
+ * strategy GI_SEG_FVC (fixed vertex count): segment s keeps the sources
+ * [s*ceil(n/S), (s+1)*ceil(n/S)); GI_SEG_EVC (edge-aware vertex count): the
+ * ranges are cut where the prefix sum of the sources' out-degrees crosses
+ * s*m/S, so each segment holds about m/S arcs (one source never splits).
  * num_segments = 1 frees them.  Kept until the next call or gi_graph_free.
+ * Errors: GI_ERR_INVALID_ARG, GI_ERR_UNSUPPORTED (no in-edges), GI_ERR_OOM
+ * (nothing is kept then).
  */
-int gi_graph_build_segments(gi_graph *g, int32_t num_segments, void *stream);
+#define GI_SEG_FVC 0
+#define GI_SEG_EVC 1
+int gi_graph_build_segments(gi_graph *g, int32_t num_segments, int32_t strategy, void *stream);
+
+/*
+ * The current segments: *num (1 without segments), *strategy, bounds[0..num]
+ * (segment s holds sources [bounds[s], bounds[s+1])) and arcs[0..num-1];
+ * bounds/arcs may be NULL, and at most cap segments are written.
+ */
+int gi_graph_segment_info(const gi_graph *g, int32_t *num, int32_t *strategy, int32_t *bounds, int64_t *arcs,
+                          int32_t cap);
 
 /* ------------------------------------------------------------- vertexset -- */
 typedef struct gi_vset gi_vset;
@@ -149,6 +164,10 @@ int gi_vset_import(gi_vset *s, const int32_t *dev_ids, int64_t k, void *stream);
 #define GI_DIR_HYBRID_PULL 3  /* DensePull-SparsePush, chosen per iteration    */
 #define GI_DIR_HYBRID_DPUSH 4 /* DensePush-SparsePush, chosen per iteration    */
 #define GI_DIR_LEARNED 5      /* MLP picks SparsePush/DensePush/DensePull      */
+#define GI_DIR_SPARSE_PULL 6  /* SparsePull: only the destinations of the `to` */
+                              /* set pull, each over its in-edges (thread /   */
+                              /* warp / block by degree); without a `to` set   */
+                              /* and in the drivers it runs as DensePull      */
 
 /* configApplyParallelization (Table 3) */
 #define GI_BAL_VERTEX 0     /* vertex-parallel: one thread per vertex                     */
@@ -187,11 +206,12 @@ typedef struct gi_schedule {
                         /* 512..2048 arcs); 2 = a dense array cached in L1 (tiles of     */
                         /* 512..8192 arcs); 0 = off.  Results are bit-identical to 0.    */
                         /* Ignored elsewhere.  Built once per graph (4m bytes).          */
+  int32_t seg_strategy; /* segmented pull (num_segments > 1): GI_SEG_FVC or GI_SEG_EVC    */
 } gi_schedule;
 
-/* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment, 256 threads, t_warp 32,
- * t_cta 256, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 256, not persistent,
- * hot_cache 0. */
+/* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment (FVC when segmented), 256
+ * threads, t_warp 32, t_cta 256, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 256,
+ * not persistent, hot_cache 0. */
 void gi_schedule_default(gi_schedule *s);
 
 /* ------------------------------------------------------------ edgeset apply -- */
@@ -343,10 +363,11 @@ int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t iters, floa
  * vertices); with accumulate != 0 it is added to what the array holds, so
  * summing calls over all sources gives BC.  sigma_dev[n] (FP64, may be NULL)
  * receives sigma (exact integers below 2^53).  s1 follows sched->direction
- * like gi_bfs; s2 gathers each level's vertices in a degree-balanced pass
- * (t_warp, t_cta), or, on symmetric graphs, runs the tiled pull over all rows
- * when sched->direction is DENSE_PULL or, for hybrid and learned directions,
- * when the level's |F| + m_f exceeds m/20; push directions keep the gather.
+ * like gi_bfs; s2 runs a SparsePull over each level's vertices along their
+ * out-edges (t_warp, t_cta), or, on symmetric graphs, the tiled pull over all
+ * rows when sched->direction is DENSE_PULL or, for hybrid and learned
+ * directions, when the level's |F| + m_f exceeds m/20; push directions and
+ * SPARSE_PULL keep the SparsePull.
  * Trace: the forward levels.  Errors: GI_ERR_INVALID_ARG, GI_ERR_UNSUPPORTED
  * (DENSE_PULL without in-edges), GI_ERR_OOM, GI_ERR_CUDA.  Syncs the stream.
  */

@@ -55,6 +55,8 @@ def schedule(direction="hybrid_pull", **kw) -> gi_schedule:
     for k, v in kw.items():
         if k == "balance" and isinstance(v, str):
             v = {"vertex": GI_BAL_VERTEX, "edge_aware": GI_BAL_EDGE_AWARE, "edge_parallel": L.GI_BAL_EDGE_PARALLEL}[v]
+        if k == "seg_strategy" and isinstance(v, str):
+            v = {"fvc": L.GI_SEG_FVC, "evc": L.GI_SEG_EVC}[v]
         if k == "rule" and isinstance(v, str):
             v = {"beamer": GI_RULE_BEAMER, "ligra": GI_RULE_LIGRA}[v]
         setattr(s, k, v)
@@ -112,8 +114,19 @@ class Graph:
         check(_C.gi_graph_hot_info(self.handle, ctypes.byref(k), ctypes.byref(d), _stream(stream)))
         return k.value, d.value
 
-    def build_segments(self, num_segments: int, stream=None):
-        check(_C.gi_graph_build_segments(self.handle, int(num_segments), _stream(stream)))
+    def build_segments(self, num_segments: int, strategy="fvc", stream=None):
+        """gi_graph_build_segments; strategy "fvc" (equal source ranges) or "evc" (about m/S arcs each)."""
+        st = {"fvc": L.GI_SEG_FVC, "evc": L.GI_SEG_EVC}.get(strategy, strategy)
+        check(_C.gi_graph_build_segments(self.handle, int(num_segments), int(st), _stream(stream)))
+
+    def segment_info(self):
+        """(strategy, bounds[S+1], arcs[S]) of the current segments."""
+        num, strat = ctypes.c_int32(), ctypes.c_int32()
+        check(_C.gi_graph_segment_info(self.handle, ctypes.byref(num), ctypes.byref(strat), None, None, 0))
+        b = np.zeros(num.value + 1, np.int32)
+        a = np.zeros(num.value, np.int64)
+        check(_C.gi_graph_segment_info(self.handle, None, None, _vp(b), _vp(a), num.value))
+        return strat.value, b, a
 
     def free(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

@@ -20,8 +20,9 @@ GI_HOST_PTRS, GI_DEV_PTRS, GI_SYMMETRIC, GI_VALIDATE = 0x1, 0x2, 0x4, 0x8
 GI_VSET_EMPTY, GI_VSET_ALL, GI_VSET_SINGLE = 0, 1, 2
 GI_REP_SPARSE, GI_REP_BOOL, GI_REP_BITMAP = 0x1, 0x2, 0x4
 GI_DIR_SPARSE_PUSH, GI_DIR_DENSE_PUSH, GI_DIR_DENSE_PULL = 0, 1, 2
-GI_DIR_HYBRID_PULL, GI_DIR_HYBRID_DPUSH, GI_DIR_LEARNED = 3, 4, 5
+GI_DIR_HYBRID_PULL, GI_DIR_HYBRID_DPUSH, GI_DIR_LEARNED, GI_DIR_SPARSE_PULL = 3, 4, 5, 6
 GI_BAL_VERTEX, GI_BAL_EDGE_AWARE, GI_BAL_EDGE_PARALLEL = 0, 1, 2
+GI_SEG_FVC, GI_SEG_EVC = 0, 1
 GI_RULE_BEAMER, GI_RULE_LIGRA = 0, 1
 GI_K_BFS, GI_K_SSSP, GI_K_CC, GI_K_SUM, GI_K_PROBE = 1, 2, 3, 4, 5
 GI_NO_DEDUP = 0x1
@@ -29,7 +30,7 @@ GI_STATIC_PR_MAX_N = 1 << 20
 GI_ALGO_BFS, GI_ALGO_SSSP, GI_ALGO_CC, GI_ALGO_PAGERANK, GI_ALGO_PAGERANK_DELTA = 1, 2, 3, 4, 5
 
 DIRECTIONS = {"sparse_push": 0, "dense_push": 1, "dense_pull": 2, "hybrid_pull": 3, "hybrid_dpush": 4,
-              "learned": 5}
+              "learned": 5, "sparse_pull": 6}
 
 _vp = ctypes.c_void_p
 _i32, _i64, _u32, _f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float
@@ -40,7 +41,7 @@ class gi_schedule(ctypes.Structure):
     _fields_ = [("direction", _i32), ("dense_rep", _u32), ("balance", _i32), ("num_segments", _i32),
                 ("block", _i32), ("t_warp", _i32), ("t_cta", _i32), ("rule", _i32), ("alpha", _f32),
                 ("beta", _f32), ("tile_edges", _i32), ("t_heavy", _i32), ("persistent", _i32),
-                ("hot_cache", _i32)]
+                ("hot_cache", _i32), ("seg_strategy", _i32)]
 
 
 class gi_trace(ctypes.Structure):
@@ -81,7 +82,8 @@ SIGNATURES = {
     "gi_graph_free": (ctypes.c_int, [_vp]),
     "gi_graph_info": (ctypes.c_int, [_vp, _P(_i64), _P(_i64), _P(_i32)]),
     "gi_graph_device_csr": (ctypes.c_int, [_vp, _P(_vp), _P(_vp), _P(_vp)]),
-    "gi_graph_build_segments": (ctypes.c_int, [_vp, _i32, _vp]),
+    "gi_graph_build_segments": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
+    "gi_graph_segment_info": (ctypes.c_int, [_vp, _P(_i32), _P(_i32), _vp, _vp, _i32]),
     "gi_vset_create": (ctypes.c_int, [_vp, _i32, _i32, _vp, _P(_vp)]),
     "gi_vset_free": (ctypes.c_int, [_vp]),
     "gi_vset_size": (ctypes.c_int, [_vp, _P(_i64), _vp]),

@@ -316,7 +316,7 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
   GI_ARG(depth != nullptr, "depth is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const gi_schedule sc = *sched;
-  if (sc.direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sc.direction));
+  if (forced_direction(sc.direction) >= 0) GI_TRY(pull_available(g, forced_direction(sc.direction)));
   if (sc.persistent && (!parent || g->has_csc)) {
     // depths in one persistent launch; canonical parents by the in-edge pass
     GI_TRY(run_persistent(g, GI_ALGO_BFS, src, depth, sc, trace, s));
@@ -375,7 +375,8 @@ static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src,
   int st = pair_alloc(g, P, s);
   if (st == GI_OK) st = dev_alloc_n(&snap, g->n, s);
   if (st == GI_OK && sc.num_segments > 1 && g->has_csc) {
-    if (g->segs.num != sc.num_segments) st = gi_graph_build_segments(g, sc.num_segments, s);
+    if (g->segs.num != sc.num_segments || g->segs.strategy != sc.seg_strategy)
+      st = gi_graph_build_segments(g, sc.num_segments, sc.seg_strategy, s);
     if (st == GI_OK) st = dev_alloc_n(&seg_acc, g->n, s);
     if (st == GI_OK) {
       k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(seg_acc, g->n, INT32_MAX);
@@ -447,8 +448,8 @@ extern "C" int gi_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedul
   GI_ARG(src >= 0 && src < g->n, "source out of range");
   GI_ARG(dist != nullptr, "dist is NULL");
   GI_ARG(g->out.wt != nullptr, "SSSP needs edge weights");
-  if (sched->direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sched->direction));
-  if (sched->direction == GI_DIR_DENSE_PULL || sched->direction == GI_DIR_HYBRID_PULL) {
+  if (forced_direction(sched->direction) >= 0) GI_TRY(pull_available(g, forced_direction(sched->direction)));
+  if (forced_direction(sched->direction) == GI_DIR_DENSE_PULL || sched->direction == GI_DIR_HYBRID_PULL) {
     GI_ARG(g->symmetric || g->in.wt != nullptr, "pull SSSP needs in-edge weights (gi_load_csc with weights)");
   }
   if (sched->persistent) return run_persistent(g, GI_ALGO_SSSP, src, dist, *sched, trace, (cudaStream_t)stream);
@@ -459,7 +460,7 @@ extern "C" int gi_cc(gi_graph *g, int32_t *label, const gi_schedule *sched, gi_t
   GI_ARG(g != nullptr, "graph is NULL");
   GI_TRY(check_schedule(sched));
   GI_ARG(label != nullptr, "label is NULL");
-  if (sched->direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sched->direction));
+  if (forced_direction(sched->direction) >= 0) GI_TRY(pull_available(g, forced_direction(sched->direction)));
   if (g->n == 0) return GI_OK;
   return minlabel_run(g, label, GI_K_CC, 0, *sched, trace, (cudaStream_t)stream);
 }
@@ -490,7 +491,8 @@ extern "C" int gi_pagerank(gi_graph *g, float damping, int32_t iters, float *ran
   if (!push) GI_TRY(pull_available(g, GI_DIR_DENSE_PULL));
   GI_TRY(ensure_tiles(g, sc, s));
   const bool segmented = !push && sc.num_segments > 1;
-  if (segmented && g->segs.num != sc.num_segments) GI_TRY(gi_graph_build_segments(g, sc.num_segments, s));
+  if (segmented && (g->segs.num != sc.num_segments || g->segs.strategy != sc.seg_strategy))
+    GI_TRY(gi_graph_build_segments(g, sc.num_segments, sc.seg_strategy, s));
   const float base = (1.0f - damping) / (float)g->n, init = 1.0f / (float)g->n;
   float *buf[2] = {nullptr, nullptr}, *acc = nullptr;
   double *acc64 = nullptr;
@@ -561,7 +563,7 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
   if (g->n == 0) return GI_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const gi_schedule sc = *sched;
-  if (sc.direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sc.direction));
+  if (forced_direction(sc.direction) >= 0) GI_TRY(pull_available(g, forced_direction(sc.direction)));
   GI_TRY(ensure_tiles(g, sc, s));
   const float inv_n = 1.0f / (float)g->n, first_base = (1.0f - damping) / (float)g->n;
   VsetPair P;
@@ -573,7 +575,8 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
   if (st == GI_OK) st = dev_alloc_n(&dsum, g->n, s);
   const bool segmented = sc.num_segments > 1 && g->has_csc;
   if (st == GI_OK && segmented) {
-    if (g->segs.num != sc.num_segments) st = gi_graph_build_segments(g, sc.num_segments, s);
+    if (g->segs.num != sc.num_segments || g->segs.strategy != sc.seg_strategy)
+      st = gi_graph_build_segments(g, sc.num_segments, sc.seg_strategy, s);
     if (st == GI_OK) st = dev_alloc_n(&seg_sum, g->n, s);
     if (st == GI_OK && cudaMemsetAsync(seg_sum, 0, sizeof(float) * g->n, s) != cudaSuccess)
       st = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__);
@@ -655,10 +658,10 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
 //   s2 (backward): levels from the deepest up; w[v] = (1 + delta[v]) / sigma[v]
 //     is set on level d+1 and zero everywhere else, so for u in level d
 //     delta[u] = sigma[u] * sum of w over u's out-neighbours.  Either a
-//     degree-balanced gather over level d's queue (thread / warp / block per
-//     vertex) or, for large levels of symmetric graphs, the tiled pull over
-//     all rows with the level as destination filter.  Both sum in a fixed
-//     order, without atomics.
+//     SparsePull over level d's queue along the out-edges (thread / warp /
+//     block per vertex) or, for large levels of symmetric graphs, the tiled
+//     pull over all rows with the level as destination filter.  Both sum in
+//     a fixed order, without atomics.
 namespace gi {
 
 struct OpBCFwd {
@@ -709,87 +712,6 @@ struct OpBCBack {
   }
   __device__ bool push(int32_t, int32_t, int32_t) const { return false; }
 };
-
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
-
-// Sum of w[idx[a + k]] for k = k0, k0 + step, ... < deg, 8 loads in flight.
-__device__ __forceinline__ double bc_row_sum(const int32_t *__restrict__ idx, const double *__restrict__ w,
-                                             int32_t a, int32_t deg, int32_t k0, int32_t step) {
-  double x = 0.0;
-  for (int32_t k = k0; k < deg; k += 8 * step) {
-    int32_t v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = k + j * step < deg ? __ldg(idx + a + k + j * step) : -1;
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (v[j] >= 0) x += __ldg(w + v[j]);
-  }
-  return x;
-}
-
-constexpr int kBcBlock = 256;
-
-// delta[u] = sigma[u] * sum_{v in out(u)} w[v] for every u of the queue: rows
-// of >= t_cta arcs by the whole block, >= t_warp by a warp, the rest by their
-// own thread.
-__global__ void __launch_bounds__(kBcBlock) k_bc_gather(const int32_t *__restrict__ q, int64_t cnt,
-                                                        const int32_t *__restrict__ ptr,
-                                                        const int32_t *__restrict__ idx,
-                                                        const double *__restrict__ w,
-                                                        const double *__restrict__ sigma, double *delta,
-                                                        int32_t t_warp, int32_t t_cta) {
-  __shared__ int32_t s_owner, s_a, s_deg;
-  __shared__ double s_red[kBcBlock / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int64_t base = (int64_t)blockIdx.x * kBcBlock; base < cnt; base += (int64_t)gridDim.x * kBcBlock) {
-    const int64_t i = base + tid;
-    int32_t u = -1, a = 0, deg = 0;
-    if (i < cnt) {
-      u = q[i];
-      a = __ldg(ptr + u);
-      deg = __ldg(ptr + u + 1) - a;
-    }
-    while (true) {
-      if (tid == 0) s_owner = -1;
-      __syncthreads();
-      if (deg >= t_cta) s_owner = tid;
-      __syncthreads();
-      const int owner = s_owner;
-      if (owner < 0) break;
-      if (tid == owner) {
-        s_a = a;
-        s_deg = deg;
-      }
-      __syncthreads();
-      double x = warp_sum(bc_row_sum(idx, w, s_a, s_deg, tid, kBcBlock));
-      if (lane == 0) s_red[warp] = x;
-      __syncthreads();
-      if (tid == owner) {
-        double y = 0.0;
-        for (int k = 0; k < kBcBlock / 32; ++k) y += s_red[k];
-        delta[u] = sigma[u] * y;
-        deg = 0;
-      }
-      __syncthreads();
-    }
-    while (true) {
-      const unsigned bal = __ballot_sync(0xffffffffu, deg >= t_warp);
-      if (!bal) break;
-      const int l = __ffs(bal) - 1;
-      const int32_t la = __shfl_sync(0xffffffffu, a, l), ld = __shfl_sync(0xffffffffu, deg, l);
-      const double x = warp_sum(bc_row_sum(idx, w, la, ld, lane, 32));
-      if (lane == l) {
-        delta[u] = sigma[u] * x;
-        deg = 0;
-      }
-    }
-    if (deg > 0) delta[u] = sigma[u] * bc_row_sum(idx, w, a, deg, 0, 1);
-  }
-}
 
 // w[v] = (1 + delta[v]) / sigma[v] on the level below the one accumulated
 // next (q_set); w back to 0 on the level that was below it before (q_clear).
@@ -854,7 +776,7 @@ extern "C" int gi_bc(gi_graph *g, int32_t src, double *dependency, double *sigma
   GI_ARG(dependency != nullptr, "dependency is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const gi_schedule sc = *sched;
-  if (sc.direction <= GI_DIR_DENSE_PULL) GI_TRY(pull_available(g, sc.direction));
+  if (forced_direction(sc.direction) >= 0) GI_TRY(pull_available(g, forced_direction(sc.direction)));
   GI_TRY(ensure_tiles(g, sc, s));
   const int64_t n = g->n;
   VsetPair P;
@@ -886,27 +808,25 @@ extern "C" int gi_bc(gi_graph *g, int32_t src, double *dependency, double *sigma
       return bc_forward(g, P, dir, sc, depth, sigma, it + 1, s);
     });
   const int32_t D = (int32_t)nf.size();
-  const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
-  const int32_t tc = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_cta > 0 ? max(sc.t_cta, tw) : 1024);
   for (int32_t d = D - 2; d >= 1 && st == GI_OK; --d) {
     const int64_t n_set = nf[d + 1], n_clear = d + 2 < D ? nf[d + 2] : 0;
     k_bc_weights<<<grid_for(g, n_set > n_clear ? n_set : n_clear, 256), 256, 0, s>>>(
         levels + off[d + 1], n_set, levels + off[d + 2 < D ? d + 2 : d + 1], n_clear, delta, sigma, w);
     st = launch_status(1);
     if (st != GI_OK) break;
-    // s2's direction: forced by the schedule, else Ligra's rule on level d
-    bool dense = g->symmetric && sc.balance != GI_BAL_VERTEX;
-    if (sc.direction == GI_DIR_SPARSE_PUSH || sc.direction == GI_DIR_DENSE_PUSH) dense = false;
-    else if (sc.direction != GI_DIR_DENSE_PULL) dense = dense && (nf[d] + mf[d]) > g->m / 20;
-    if (dense) {
-      const OpBCBack op{w, delta, sigma, depth, d};
+    // s2's direction: SparsePull over level d's queue, or the dense pull over
+    // all rows; forced by the schedule, else Ligra's rule on level d
+    const int32_t fd = forced_direction(sc.direction);
+    bool dense;
+    if (sc.direction == GI_DIR_SPARSE_PULL || fd == GI_DIR_SPARSE_PUSH || fd == GI_DIR_DENSE_PUSH) dense = false;
+    else if (fd == GI_DIR_DENSE_PULL) dense = true;
+    else dense = (nf[d] + mf[d]) > g->m / 20;
+    dense = dense && g->symmetric && sc.balance != GI_BAL_VERTEX;
+    const OpBCBack op{w, delta, sigma, depth, d};
+    if (dense)
       st = launch_pull_tiled(g, op, g->in, g->in_tiles, FSet(), nullptr, OutSet(), s, kClassOtherPull);
-    } else {
-      const int grid = (int)std::min<int64_t>((nf[d] + kBcBlock - 1) / kBcBlock, (int64_t)g->num_sms * 8);
-      k_bc_gather<<<grid, kBcBlock, 0, s>>>(levels + off[d], nf[d], g->out.ptr, g->out.idx, w, sigma, delta, tw,
-                                            tc);
-      st = launch_status(1);
-    }
+    else
+      st = launch_pull_sparse(g, op, g->out, levels + off[d], nullptr, nf[d], FSet(), OutSet(), sc, s);
   }
   if (st == GI_OK) {
     k_bc_out<<<grid_for(g, n, 256), 256, 0, s>>>(delta, dependency, n, src, accumulate);

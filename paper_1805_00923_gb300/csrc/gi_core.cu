@@ -402,19 +402,14 @@ extern "C" int gi_stats_read(int32_t kclass, int64_t *launches, int64_t *timed_l
 }
 extern "C" int gi_version(void) { return 100; }
 
+namespace gi {
+static void segs_free(gi_graph *g, cudaStream_t s);
+}
+
 static void graph_release(gi_graph *g, cudaStream_t s) {
   if (!g) return;
   free_tile_cache(g, s);
-  if (g->segs.seg) {
-    for (int i = 0; i < g->segs.num; ++i) {
-      dev_free(g->segs.seg[i].ptr, s);
-      dev_free(g->segs.seg[i].idx, s);
-      dev_free(g->segs.seg[i].wt, s);
-      free_tiles(&g->segs.tiles[i], s);
-    }
-    delete[] g->segs.seg;
-    delete[] g->segs.tiles;
-  }
+  segs_free(g, s);
   if (!g->symmetric) {
     dev_free(g->in.ptr, s);
     dev_free(g->in.idx, s);
@@ -875,12 +870,15 @@ void hot_free(gi_graph *g, cudaStream_t s) {
 }
 
 // ============================================================== segments ==
-// Segment s keeps in-arcs whose source lies in [s*seg, (s+1)*seg), rows kept
-// in destination order and sources ascending (a stable filter of the CSC).
+// Segment s keeps in-arcs whose source lies in [lo, hi) = [bounds[s],
+// bounds[s+1]), rows kept in destination order and sources ascending (a stable
+// filter of the CSC).  Fixed vertex count (FVC): equal source ranges;
+// edge-aware vertex count (EVC): ranges holding about m/S arcs each, found in
+// the prefix sum of the sources' out-degrees (the CSR offsets).
 __global__ void k_seg_count(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t n,
-                            int32_t seg_size, int32_t sid, int32_t *cnt) {
+                            int32_t lo, int32_t hi, int32_t *cnt) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    int32_t lo = sid * seg_size, hi = lo + seg_size, c = 0;
+    int32_t c = 0;
     for (int32_t e = ptr[r]; e < ptr[r + 1]; ++e) {
       int32_t u = idx[e];
       c += (u >= lo && u < hi);
@@ -890,10 +888,10 @@ __global__ void k_seg_count(const int32_t *__restrict__ ptr, const int32_t *__re
 }
 
 __global__ void k_seg_fill(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                           const int32_t *__restrict__ wt, int64_t n, int32_t seg_size, int32_t sid,
+                           const int32_t *__restrict__ wt, int64_t n, int32_t lo, int32_t hi,
                            const int32_t *__restrict__ sptr, int32_t *sidx, int32_t *swt) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    int32_t lo = sid * seg_size, hi = lo + seg_size, o = sptr[r];
+    int32_t o = sptr[r];
     for (int32_t e = ptr[r]; e < ptr[r + 1]; ++e) {
       int32_t u = idx[e];
       if (u >= lo && u < hi) {
@@ -905,16 +903,26 @@ __global__ void k_seg_fill(const int32_t *__restrict__ ptr, const int32_t *__res
   }
 }
 
-}  // namespace gi
-
-extern "C" int gi_graph_build_segments(gi_graph *g, int32_t num_segments, void *stream) {
-  GI_ARG(g != nullptr, "graph is NULL");
-  GI_ARG(num_segments >= 1 && num_segments <= 1024, "num_segments must be in [1, 1024]");
-  if (!g->has_csc) {
-    set_error("segmented pull needs the in-edges: load a symmetric graph or call gi_load_csc");
-    return GI_ERR_UNSUPPORTED;
+// EVC bounds: bounds[s] = smallest v with optr[v] >= s*m/S (bounds[0] = 0, bounds[S] = n)
+__global__ void k_seg_bounds_evc(const int32_t *__restrict__ optr, int64_t n, int64_t m, int32_t S,
+                                 int32_t *bounds) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > S) return;
+  if (s == 0 || s == S) {
+    bounds[s] = s == 0 ? 0 : (int32_t)n;
+    return;
   }
-  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t target = m * (int64_t)s / S;
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)optr[mid] >= target) hi = mid;
+    else lo = mid + 1;
+  }
+  bounds[s] = (int32_t)lo;
+}
+
+static void segs_free(gi_graph *g, cudaStream_t s) {
   if (g->segs.seg) {
     for (int i = 0; i < g->segs.num; ++i) {
       dev_free(g->segs.seg[i].ptr, s);
@@ -922,35 +930,102 @@ extern "C" int gi_graph_build_segments(gi_graph *g, int32_t num_segments, void *
       dev_free(g->segs.seg[i].wt, s);
       free_tiles(&g->segs.tiles[i], s);
     }
-    delete[] g->segs.seg;
-    delete[] g->segs.tiles;
-    g->segs = Segments();
   }
+  delete[] g->segs.seg;
+  delete[] g->segs.tiles;
+  delete[] g->segs.bounds;
+  delete[] g->segs.arcs;
+  g->segs = Segments();
+}
+
+}  // namespace gi
+
+extern "C" int gi_graph_build_segments(gi_graph *g, int32_t num_segments, int32_t strategy, void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_ARG(num_segments >= 1 && num_segments <= 1024, "num_segments must be in [1, 1024]");
+  GI_ARG(strategy == GI_SEG_FVC || strategy == GI_SEG_EVC, "strategy must be GI_SEG_FVC or GI_SEG_EVC");
+  if (!g->has_csc) {
+    set_error("segmented pull needs the in-edges: load a symmetric graph or call gi_load_csc");
+    return GI_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  segs_free(g, s);
   if (num_segments == 1) return GI_OK;
   GI_TRY(ws_get(g, s));
-  int64_t n = g->n;
-  int32_t seg_size = (int32_t)((n + num_segments - 1) / num_segments);
-  g->segs.num = num_segments;
-  g->segs.seg_size = seg_size;
-  g->segs.seg = new Csr[num_segments];
-  g->segs.tiles = new TileSet[num_segments];
-  for (int sid = 0; sid < num_segments; ++sid) {
-    Csr &c = g->segs.seg[sid];
-    GI_TRY(dev_alloc_n(&c.ptr, n + 1, s));
-    k_seg_count<<<grid_for(g, n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, n, seg_size, sid, g->ws->tmp_i32);
-    GI_LAUNCH_CHECK();
-    GI_TRY(scan_exclusive(g, g->ws->tmp_i32, c.ptr, n, s));
+  const int64_t n = g->n;
+  const int S = num_segments;
+  Segments sg;
+  sg.num = S;
+  sg.strategy = strategy;
+  sg.bounds = new int32_t[S + 1];
+  sg.arcs = new int64_t[S];
+  sg.seg = new Csr[S];
+  sg.tiles = new TileSet[S];
+  int st = GI_OK;
+  if (strategy == GI_SEG_FVC) {
+    const int64_t seg_size = (n + S - 1) / S;
+    for (int k = 0; k <= S; ++k) sg.bounds[k] = (int32_t)(k * seg_size < n ? k * seg_size : n);
+  } else {
+    int32_t *db = nullptr;
+    st = dev_alloc_n(&db, S + 1, s);
+    if (st == GI_OK) {
+      k_seg_bounds_evc<<<div_up(S + 1, 256), 256, 0, s>>>(g->out.ptr, n, g->m, S, db);
+      st = launch_status(1);
+    }
+    if (st == GI_OK && (cudaMemcpyAsync(sg.bounds, db, sizeof(int32_t) * (S + 1), cudaMemcpyDeviceToHost, s) !=
+                            cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+      st = cuda_fail(cudaGetLastError(), "segment bounds", __FILE__, __LINE__);
+    dev_free(db, s);
+  }
+  for (int sid = 0; sid < S && st == GI_OK; ++sid) {
+    Csr &c = sg.seg[sid];
+    const int32_t lo = sg.bounds[sid], hi = sg.bounds[sid + 1];
+    st = dev_alloc_n(&c.ptr, n + 1, s);
+    if (st == GI_OK) {
+      k_seg_count<<<grid_for(g, n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, n, lo, hi, g->ws->tmp_i32);
+      st = launch_status(1);
+    }
+    if (st == GI_OK) st = scan_exclusive(g, g->ws->tmp_i32, c.ptr, n, s);
     int32_t cnt = 0;
-    GI_CUDA(cudaMemcpyAsync(&cnt, c.ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    GI_CUDA(cudaStreamSynchronize(s));
-    GI_TRY(dev_alloc_n(&c.idx, cnt, s));
-    if (g->in.wt) GI_TRY(dev_alloc_n(&c.wt, cnt, s));
-    k_seg_fill<<<grid_for(g, n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->in.wt, n, seg_size, sid, c.ptr, c.idx,
-                                                   c.wt);
-    GI_LAUNCH_CHECK();
-    GI_TRY(build_tiles(g, c, g->in_tiles.tile_edges > 0 ? g->in_tiles.tile_edges : 2048, &g->segs.tiles[sid], s));
+    if (st == GI_OK && (cudaMemcpyAsync(&cnt, c.ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+      st = cuda_fail(cudaGetLastError(), "segment size", __FILE__, __LINE__);
+    sg.arcs[sid] = cnt;
+    if (st == GI_OK) st = dev_alloc_n(&c.idx, cnt, s);
+    if (st == GI_OK && g->in.wt) st = dev_alloc_n(&c.wt, cnt, s);
+    if (st == GI_OK) {
+      k_seg_fill<<<grid_for(g, n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->in.wt, n, lo, hi, c.ptr, c.idx, c.wt);
+      st = launch_status(1);
+    }
+    if (st == GI_OK)
+      st = build_tiles(g, c, g->in_tiles.tile_edges > 0 ? g->in_tiles.tile_edges : 2048, &sg.tiles[sid], s);
+  }
+  g->segs = sg;  // owned by the graph from here; freed whole on failure
+  if (st != GI_OK) {
+    segs_free(g, s);
+    return st;
   }
   GI_CUDA(cudaStreamSynchronize(s));
+  return GI_OK;
+}
+
+extern "C" int gi_graph_segment_info(const gi_graph *g, int32_t *num, int32_t *strategy, int32_t *bounds,
+                                     int64_t *arcs, int32_t cap) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  const int S = g->segs.seg ? g->segs.num : 1;
+  if (num) *num = S;
+  if (strategy) *strategy = g->segs.strategy;
+  if (g->segs.seg) {
+    for (int k = 0; k <= S && bounds && k < cap + 1; ++k) bounds[k] = g->segs.bounds[k];
+    for (int k = 0; k < S && arcs && k < cap; ++k) arcs[k] = g->segs.arcs[k];
+  } else {
+    if (bounds && cap >= 1) {
+      bounds[0] = 0;
+      bounds[1] = (int32_t)g->n;
+    }
+    if (arcs && cap >= 1) arcs[0] = g->m;
+  }
   return GI_OK;
 }
 
@@ -1388,4 +1463,5 @@ extern "C" void gi_schedule_default(gi_schedule *s) {
   s->t_heavy = 256;
   s->persistent = 0;
   s->hot_cache = 0;
+  s->seg_strategy = GI_SEG_FVC;
 }

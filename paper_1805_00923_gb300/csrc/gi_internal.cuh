@@ -103,7 +103,9 @@ struct TileSet {
 
 struct Segments {
   int32_t num = 1;
-  int32_t seg_size = 0;       // vertices per source segment
+  int32_t strategy = 0;       // GI_SEG_FVC or GI_SEG_EVC
+  int32_t *bounds = nullptr;  // host array [num+1]: segment s holds sources [bounds[s], bounds[s+1])
+  int64_t *arcs = nullptr;    // host array [num]: arcs of each segment
   Csr *seg = nullptr;         // host array of per-segment CSCs (device pointers)
   TileSet *tiles = nullptr;   // host array: tiles of each segment
 };
@@ -235,6 +237,13 @@ struct DecideParams {
 int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s);
 int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s);
 int ctrl_fetch(gi_graph *g, cudaStream_t s);  // copies ctrl to pinned host + syncs
+
+// The traversal a schedule's direction forces (SparsePull needs a `to` set;
+// the drivers have none and run it as DensePull), or -1 when it is chosen
+// per round (hybrids, learned).
+inline int32_t forced_direction(int32_t d) {
+  return d <= GI_DIR_DENSE_PULL ? d : (d == GI_DIR_SPARSE_PULL ? GI_DIR_DENSE_PULL : -1);
+}
 
 // selector weights (device memory) and state; the batched engine keeps its
 // own copy of the weights, uploaded by gi_selector_load

@@ -17,7 +17,59 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
     GI_TRY(vset_ensure_bitmap(to, s));
     to_bm = to->bitmap;
   }
-  if (is_pull(dir)) {
+  if (dir == GI_DIR_SPARSE_PULL) {
+    // only the destinations of `to` pull (gi_edgeset_apply passes a non-NULL to)
+    GI_TRY(vset_ensure_queue(to, s));
+    FSet F;
+    if (from) {
+      if (sc.dense_rep == GI_REP_BOOL) {
+        GI_TRY(vset_ensure_bool(from, s));
+        F = FSet(static_cast<const uint8_t *>(from->boolmap));
+      } else {
+        GI_TRY(vset_ensure_bitmap(from, s));
+        F = FSet(static_cast<const uint32_t *>(from->bitmap));
+      }
+    }
+    switch (kernel_id) {
+      case GI_K_BFS: {
+        const gi_bfs_args *a = static_cast<const gi_bfs_args *>(args);
+        OpBFSPull op{a->depth, a->parent, a->level};
+        GI_TRY(launch_pull_sparse(g, op, g->in, to->queue, to->count, 0, F, o, sc, s, kClassBfsPull));
+        break;
+      }
+      case GI_K_SSSP: {
+        const gi_sssp_args *a = static_cast<const gi_sssp_args *>(args);
+        if (!g->symmetric && g->in.wt == nullptr) {
+          gi::set_error("pull SSSP needs in-edge weights (gi_load_csc with weights)");
+          return GI_ERR_UNSUPPORTED;
+        }
+        OpMinInt op{a->dist, a->snap, g->in.wt};
+        GI_TRY(launch_pull_sparse(g, op, g->in, to->queue, to->count, 0, F, o, sc, s, kClassMinPull));
+        break;
+      }
+      case GI_K_CC: {
+        const gi_cc_args *a = static_cast<const gi_cc_args *>(args);
+        OpMinInt op{a->label, a->snap, nullptr};
+        GI_TRY(launch_pull_sparse(g, op, g->in, to->queue, to->count, 0, F, o, sc, s, kClassMinPull));
+        break;
+      }
+      case GI_K_SUM: {
+        const gi_sum_args *a = static_cast<const gi_sum_args *>(args);
+        OpSum op{a->contrib, a->acc};
+        GI_TRY(launch_pull_sparse(g, op, g->in, to->queue, to->count, 0, F, o, sc, s));
+        break;
+      }
+      case GI_K_PROBE: {
+        const gi_probe_args *a = static_cast<const gi_probe_args *>(args);
+        OpProbe op{a->count, a->srcsum};
+        GI_TRY(launch_pull_sparse(g, op, g->in, to->queue, to->count, 0, F, o, sc, s));
+        break;
+      }
+      default:
+        gi::set_error("unknown kernel_id %d", kernel_id);
+        return GI_ERR_INVALID_ARG;
+    }
+  } else if (is_pull(dir)) {
     if (!g->has_csc) {
       gi::set_error("pull traversal needs the in-edges: load a symmetric graph or call gi_load_csc");
       return GI_ERR_UNSUPPORTED;
@@ -132,7 +184,7 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
 
 int check_schedule(const gi_schedule *sc) {
   GI_ARG(sc != nullptr, "schedule is NULL");
-  GI_ARG(sc->direction >= GI_DIR_SPARSE_PUSH && sc->direction <= GI_DIR_LEARNED, "unknown direction");
+  GI_ARG(sc->direction >= GI_DIR_SPARSE_PUSH && sc->direction <= GI_DIR_SPARSE_PULL, "unknown direction");
   GI_ARG(sc->balance == GI_BAL_VERTEX || sc->balance == GI_BAL_EDGE_AWARE || sc->balance == GI_BAL_EDGE_PARALLEL,
          "unknown balance mode");
   GI_ARG(sc->num_segments >= 1 && sc->num_segments <= 1024, "num_segments must be in [1, 1024]");
@@ -142,6 +194,7 @@ int check_schedule(const gi_schedule *sc) {
                                  (sc->tile_edges & (sc->tile_edges - 1)) == 0),
          "tile_edges must be a power of two in [256, 8192]");
   GI_ARG(sc->hot_cache >= 0 && sc->hot_cache <= 2, "hot_cache must be 0, 1 or 2");
+  GI_ARG(sc->seg_strategy == GI_SEG_FVC || sc->seg_strategy == GI_SEG_EVC, "seg_strategy must be FVC or EVC");
   return GI_OK;
 }
 
@@ -153,9 +206,9 @@ DecideParams decide_params(const gi_schedule &sc, int32_t level, bool track_unvi
   p.beta = sc.beta > 0 ? sc.beta : 24.0f;
   p.track_unvisited = track_unvisited ? 1 : 0;
   p.hybrid_kind = sc.direction == GI_DIR_HYBRID_DPUSH ? GI_DIR_HYBRID_DPUSH : GI_DIR_HYBRID_PULL;
-  if (sc.direction <= GI_DIR_DENSE_PULL) {
+  if (forced_direction(sc.direction) >= 0) {
     p.mode = 0;
-    p.forced = sc.direction;
+    p.forced = forced_direction(sc.direction);
   } else if (sc.direction == GI_DIR_LEARNED) {
     p.mode = 2;
   } else {
@@ -189,7 +242,13 @@ extern "C" int gi_edgeset_apply(gi_graph *g, gi_vset *from, gi_vset *to, const g
   cudaStream_t s = (cudaStream_t)stream;
   GI_TRY(ensure_tiles(g, *sched, s));
   int32_t dir = sched->direction;
-  if (dir > GI_DIR_DENSE_PULL) {
+  if (dir == GI_DIR_SPARSE_PULL) {
+    if (!to) dir = GI_DIR_DENSE_PULL;  // every destination: the dense form
+    if (!g->has_csc) {
+      gi::set_error("pull traversal needs the in-edges: load a symmetric graph or call gi_load_csc");
+      return GI_ERR_UNSUPPORTED;
+    }
+  } else if (dir > GI_DIR_DENSE_PULL) {
     if (!from) {
       dir = GI_DIR_DENSE_PULL;
     } else {

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstddef>
 #include <type_traits>
 
@@ -1021,6 +1022,111 @@ __global__ void __launch_bounds__(256) k_push_edges(Op op, const int32_t *__rest
   }
 }
 
+// SparsePull (Table 3's pull into a sparse output set): every destination v
+// of a queue gathers over its in-arcs, combine over sources in F of
+// op.edge_val, then op.finish(v, .) where op.dst_ok(v).  Rows of >= t_cta
+// arcs are reduced by the whole block, >= t_warp by a warp, the rest by their
+// own thread; each row's order of combination is fixed, so results do not
+// depend on scheduling.  The queue's length is *qcount (device) or, when
+// qcount is NULL, qn.
+template <class Op>
+__device__ __forceinline__ typename Op::V sparse_row(const Op &op, const int32_t *__restrict__ idx, const FSet &F,
+                                                     int32_t a, int32_t deg, int32_t k0, int32_t step) {
+  using V = typename Op::V;
+  V x = Op::identity();
+  for (int32_t k = k0; k < deg; k += 8 * step) {
+    int32_t u[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) u[j] = k + j * step < deg ? __ldg(idx + a + k + j * step) : -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (u[j] >= 0 && in_set(F, u[j])) x = Op::combine(x, op.edge_val(u[j], a + k + j * step));
+  }
+  return x;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(256) k_pull_sparse(Op op, const int32_t *__restrict__ q,
+                                                     const int32_t *__restrict__ qcount, int64_t qn,
+                                                     const int32_t *__restrict__ ptr,
+                                                     const int32_t *__restrict__ idx, FSet F, OutSet out,
+                                                     int32_t t_warp, int32_t t_cta) {
+  using V = typename Op::V;
+  constexpr int kB = 256;
+  __shared__ int32_t s_owner, s_a, s_deg;
+  __shared__ V s_red[kB / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t cnt = qcount ? (int64_t)(*qcount) : qn;
+  for (int64_t base = (int64_t)blockIdx.x * kB; base < cnt; base += (int64_t)gridDim.x * kB) {
+    const int64_t i = base + tid;
+    int32_t v = -1, a = 0, deg = 0;
+    bool pending = false;
+    V acc = Op::identity();
+    if (i < cnt) {
+      v = q[i];
+      a = __ldg(ptr + v);
+      deg = __ldg(ptr + v + 1) - a;
+      pending = true;
+    }
+    while (true) {  // block-cooperative rows
+      if (tid == 0) s_owner = -1;
+      __syncthreads();
+      if (deg >= t_cta) s_owner = tid;
+      __syncthreads();
+      const int owner = s_owner;
+      if (owner < 0) break;
+      if (tid == owner) {
+        s_a = a;
+        s_deg = deg;
+      }
+      __syncthreads();
+      V x = warp_reduce<V, Op>(sparse_row(op, idx, F, s_a, s_deg, tid, kB));
+      if (lane == 0) s_red[warp] = x;
+      __syncthreads();
+      if (tid == owner) {
+        V y = Op::identity();
+        for (int k = 0; k < kB / 32; ++k) y = Op::combine(y, s_red[k]);
+        acc = y;
+        deg = 0;
+      }
+      __syncthreads();
+    }
+    while (true) {  // warp-cooperative rows
+      const unsigned bal = __ballot_sync(0xffffffffu, deg >= t_warp);
+      if (!bal) break;
+      const int l = __ffs(bal) - 1;
+      const int32_t la = __shfl_sync(0xffffffffu, a, l), ld = __shfl_sync(0xffffffffu, deg, l);
+      const V x = warp_reduce<V, Op>(sparse_row(op, idx, F, la, ld, lane, 32));
+      if (lane == l) {
+        acc = x;
+        deg = 0;
+      }
+    }
+    if (deg > 0) acc = sparse_row(op, idx, F, a, deg, 0, 1);
+    if (pending && op.dst_ok(v) && op.finish(v, acc) && out.enabled()) out_mark(out, v);
+  }
+}
+
+// BFS as a pull edge function (SparsePull): an unvisited destination with an
+// in-neighbour in F takes depth = level and parent = the smallest such
+// in-neighbour (the canonical parent).
+struct OpBFSPull {
+  using V = int32_t;
+  int32_t *depth;
+  int32_t *parent;
+  int32_t level;
+  __device__ static V identity() { return INT32_MAX; }
+  __device__ static V combine(V a, V b) { return a < b ? a : b; }
+  __device__ V edge_val(int32_t u, int32_t) const { return u; }
+  __device__ bool dst_ok(int32_t v) const { return depth[v] == -1; }
+  __device__ bool finish(int32_t v, V m) const {
+    if (m == INT32_MAX) return false;
+    depth[v] = level;
+    if (parent) parent[v] = m;
+    return true;
+  }
+};
+
 // Canonical BFS parents for vertices discovered by push levels (which set
 // depth only): the smallest-id in-neighbour one level closer, found by
 // scanning the sorted in-neighbours (4 per round trip; a warp 32 at a time
@@ -1240,6 +1346,25 @@ int launch_push_edges(gi_graph *g, const Op &op, const gi_vset *from, int64_t nf
   const int tok = timing_begin(kClassPush, s);
   k_push_edges<Op><<<g->num_sms * 8, 256, 0, s>>>(op, from->queue, off, (int32_t)nf, g->out.ptr, g->out.idx, to,
                                                    out);
+  timing_end(tok, s);
+  GI_LAUNCH_CHECK();
+  return GI_OK;
+}
+
+// SparsePull over the queue q (length *qcount on the device, or qn when
+// qcount is NULL), gathering along c's rows.
+template <class Op>
+int launch_pull_sparse(gi_graph *g, const Op &op, const Csr &c, const int32_t *q, const int32_t *qcount, int64_t qn,
+                       FSet F, const OutSet &out, const gi_schedule &sc, cudaStream_t s, int kclass = kClassOtherPull) {
+  const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
+  const int32_t tc = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_cta > 0 ? max(sc.t_cta, tw) : 1024);
+  int grid = g->num_sms * 8;
+  if (!qcount) {
+    if (qn == 0) return GI_OK;
+    grid = (int)std::min<int64_t>((qn + 255) / 256, (int64_t)grid);
+  }
+  const int tok = timing_begin(kclass, s);
+  k_pull_sparse<Op><<<grid, 256, 0, s>>>(op, q, qcount, qn, c.ptr, c.idx, F, out, tw, tc);
   timing_end(tok, s);
   GI_LAUNCH_CHECK();
   return GI_OK;

@@ -132,8 +132,10 @@ extern "C" int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_sche
       {&gi_schedule::t_cta, {256, 512, 1024, 2048, 4096}},
       {&gi_schedule::t_heavy, {256, 512, 1024, 2048, 4096, 16384, INT32_MAX}},
   };
-  if (algo == GI_ALGO_PAGERANK && start->direction == GI_DIR_DENSE_PULL)
+  if (algo == GI_ALGO_PAGERANK && start->direction == GI_DIR_DENSE_PULL) {
     knobs.push_back({&gi_schedule::num_segments, {1, 2, 4, 8}});
+    knobs.push_back({&gi_schedule::seg_strategy, {GI_SEG_FVC, GI_SEG_EVC}});
+  }
   if (algo == GI_ALGO_PAGERANK || algo == GI_ALGO_PAGERANK_DELTA)
     knobs.push_back({&gi_schedule::hot_cache, {0, 1, 2}});
   std::mt19937_64 rng(seed);

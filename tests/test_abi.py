@@ -77,7 +77,7 @@ def test_schedule_defaults(lib):
     assert s.balance == L.GI_BAL_EDGE_AWARE and s.num_segments == 1 and s.block == 256
     assert (s.t_warp, s.t_cta, s.rule, s.alpha, s.beta, s.tile_edges) == (32, 256, L.GI_RULE_BEAMER, 14.0, 24.0,
                                                                           2048)
-    assert (s.t_heavy, s.persistent, s.hot_cache) == (256, 0, 0)
+    assert (s.t_heavy, s.persistent, s.hot_cache, s.seg_strategy) == (256, 0, 0, 0)
 
 
 def test_selector_param_count_matches_oracle(lib):

@@ -39,7 +39,7 @@ def _sources(hg):
     return sorted({0, hg.n // 2, hg.n - 1, int(gg.pick_sources(hg, 1, seed=7)[0]) if hg.m else 0})
 
 
-DIRS = ["sparse_push", "dense_push", "dense_pull", "hybrid_pull", "hybrid_dpush"]
+DIRS = ["sparse_push", "dense_push", "dense_pull", "hybrid_pull", "hybrid_dpush", "sparse_pull"]
 
 
 @pytest.mark.parametrize("direction", DIRS)

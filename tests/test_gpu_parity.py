@@ -240,7 +240,7 @@ def _mask_set(gi, g, mask):
 
 
 @pytest.mark.parametrize("balance", ["edge_aware", "edge_parallel"])
-@pytest.mark.parametrize("direction", ["sparse_push", "dense_push", "dense_pull", "hybrid_pull"])
+@pytest.mark.parametrize("direction", ["sparse_push", "dense_push", "dense_pull", "hybrid_pull", "sparse_pull"])
 @pytest.mark.parametrize("dedup", [True, False])
 def test_edgeset_apply_selection_probe(gi, direction, dedup, balance):
     """from/to selection and applyModified output equal the oracle's edge set
@@ -405,12 +405,13 @@ def test_directed_graph_without_in_edges_rejects_pull(gi):
     assert np.array_equal(_np(d), oracle.bfs(hg, 0, in_edges=gg.transpose(hg)[:2])[0])
 
 
+@pytest.mark.parametrize("strategy", ["fvc", "evc"])
 @pytest.mark.parametrize("segs", [2, 5])
-def test_segmented_pull_all_algorithms(gi, segs):
+def test_segmented_pull_all_algorithms(gi, segs, strategy):
     """Cache-partitioned (segmented) pull for PR, PRD, CC and SSSP matches the oracle."""
     hg = rmat(14, weights=True)
     g = _load(gi, hg)
-    sc = gi.schedule("dense_pull", num_segments=segs)
+    sc = gi.schedule("dense_pull", num_segments=segs, seg_strategy=strategy)
     assert _max_rel(_np(gi.pagerank(g, 0.85, 20, sched=sc)), oracle.pagerank(hg, 0.85, 20)) < PR_TOL
     want, _ = oracle.prdelta(hg, 0.85, 1e-7, 10)
     assert _max_rel(_np(gi.pagerank_delta(g, 0.85, 1e-7, 10, sched=sc)), want) < PR_TOL
@@ -442,3 +443,74 @@ def test_boolean_map_frontier(gi, direction):
     gi.edgeset_apply(g, _mask_set(gi, g, fm), None, sc, gi.GI_K_PROBE,
                      gi.gi_probe_args(count.data_ptr(), srcsum.data_ptr()))
     assert np.array_equal(_np(count), np.bincount(v, minlength=hg.n))
+
+
+@pytest.mark.parametrize("strategy", ["fvc", "evc"])
+def test_segment_bounds_and_arc_counts(gi, strategy):
+    """Segments partition the sources; EVC cuts the out-degree prefix at s*m/S."""
+    hg = rmat(16)
+    g = _load(gi, hg)
+    S = 8
+    g.build_segments(S, strategy)
+    st, b, arcs = g.segment_info()
+    assert st == (0 if strategy == "fvc" else 1)
+    assert b[0] == 0 and b[-1] == hg.n and (np.diff(b) >= 0).all()
+    deg = np.diff(hg.row_ptr).astype(np.int64)
+    want = np.array([deg[b[k]:b[k + 1]].sum() for k in range(S)])   # symmetric: in-arcs per source = out-degree
+    assert np.array_equal(arcs, want) and arcs.sum() == hg.m
+    if strategy == "fvc":
+        size = -(-hg.n // S)
+        assert np.array_equal(b[:-1], np.arange(S) * size)
+    else:
+        for k in range(1, S):
+            assert hg.row_ptr[b[k]] >= hg.m * k // S and (b[k] == 0 or hg.row_ptr[b[k] - 1] < hg.m * k // S)
+        assert arcs.max() <= hg.m // S + deg.max() + 1
+    g.build_segments(1)
+    assert g.segment_info()[1].tolist() == [0, hg.n]
+
+
+@pytest.mark.parametrize("bal", ["edge_aware", "vertex"])
+def test_sparse_pull_matches_dense_pull_with_to_set(gi, bal):
+    """SparsePull (only the `to` destinations pull) computes what DensePull
+    with the same `to` filter computes, for every edge function."""
+    hg = rmat(13, weights=True)
+    g = _load(gi, hg)
+    rng = np.random.default_rng(21)
+    fm = (rng.random(hg.n) < 0.2).astype(np.uint8)
+    fm[7] = 1  # a hub of R-MAT
+    tm = (rng.random(hg.n) < 0.05).astype(np.uint8)
+    tm[np.argsort(np.diff(hg.row_ptr))[-3:]] = 1  # the highest in-degree rows: block-cooperative path
+    F, T = _mask_set(gi, g, fm), _mask_set(gi, g, tm)
+    u, v = oracle.edgeset_select(hg, fm, tm)
+    snap_h = rng.integers(0, 1000, hg.n)
+    results = {}
+    for d in ("dense_pull", "sparse_pull"):
+        sc = gi.schedule(d, balance=bal)
+        # BFS step: unvisited = everything but a few; canonical parent = min frontier in-neighbour
+        depth = torch.full((hg.n,), -1, dtype=torch.int32, device="cuda")
+        depth[:50] = 0
+        parent = torch.full((hg.n,), 2**31 - 1, dtype=torch.int32, device="cuda")
+        OUT = gi.VertexSet(g)
+        gi.edgeset_apply(g, F, T, sc, gi.GI_K_BFS, gi.gi_bfs_args(depth.data_ptr(), parent.data_ptr(), 1), OUT)
+        # CC / SSSP min relaxations from snap
+        snap = torch.tensor(snap_h, dtype=torch.int32, device="cuda")
+        lab = torch.full((hg.n,), 500, dtype=torch.int32, device="cuda")
+        gi.edgeset_apply(g, F, T, sc, gi.GI_K_CC, gi.gi_cc_args(lab.data_ptr(), snap.data_ptr()))
+        dist = torch.full((hg.n,), 900, dtype=torch.int32, device="cuda")
+        gi.edgeset_apply(g, F, T, sc, gi.GI_K_SSSP, gi.gi_sssp_args(dist.data_ptr(), snap.data_ptr()))
+        contrib = torch.linspace(0.1, 1.0, hg.n, dtype=torch.float32, device="cuda")
+        acc = torch.zeros(hg.n, dtype=torch.float32, device="cuda")
+        gi.edgeset_apply(g, F, T, sc, gi.GI_K_SUM, gi.gi_sum_args(contrib.data_ptr(), acc.data_ptr()))
+        results[d] = (_np(depth), _np(parent), _np(OUT.export()), _np(lab), _np(dist), _np(acc))
+    a, b = results["dense_pull"], results["sparse_pull"]
+    for k in range(5):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.allclose(a[5], b[5], rtol=1e-5, atol=0)
+    # and the sums are the oracle's selected edges
+    want = np.bincount(v, weights=np.linspace(0.1, 1.0, hg.n, dtype=np.float32)[u].astype(np.float64),
+                       minlength=hg.n)
+    assert np.allclose(b[5], want, rtol=1e-5, atol=1e-6)
+    # CC relaxation: the oracle's selected edges give the minimum snap per destination
+    lab_want = np.full(hg.n, 500)
+    np.minimum.at(lab_want, v, snap_h[u])
+    assert np.array_equal(b[3], lab_want)
