@@ -666,6 +666,7 @@ namespace gi {
 
 struct OpBCFwd {
   using V = double;
+  static constexpr bool kSkipZeroTerms = true;
   int32_t *depth;
   double *sigma;
   int32_t level;  // depth of the vertices found in this step
@@ -697,6 +698,7 @@ struct OpBCFwd {
 
 struct OpBCBack {
   using V = double;
+  static constexpr bool kSkipZeroTerms = true;
   const double *w;
   double *delta;
   const double *sigma;

@@ -366,6 +366,24 @@ __device__ __forceinline__ void stage_batch(const Gather<Op, kMode> &G, const in
   }
 }
 
+// Ops with FP64 sums (kSkipZeroTerms) skip terms whose bits are zero: on
+// GB300 an FP64 add costs a slot of the narrow FP64 pipe while the integer
+// test does not, and x + 0.0 == x for the non-negative sums they build.
+template <class Op, class = void>
+struct SkipZeroTerms : std::false_type {};
+template <class Op>
+struct SkipZeroTerms<Op, std::void_t<decltype(Op::kSkipZeroTerms)>> : std::bool_constant<Op::kSkipZeroTerms> {};
+
+template <class Op>
+__device__ __forceinline__ typename Op::V combine_term(typename Op::V acc, typename Op::V x) {
+  if constexpr (SkipZeroTerms<Op>::value) {
+    static_assert(sizeof(typename Op::V) == 8, "zero-term skipping is for FP64 sums");
+    return __double_as_longlong(x) == 0 ? acc : Op::combine(acc, x);
+  } else {
+    return Op::combine(acc, x);
+  }
+}
+
 struct BlockSync {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
@@ -410,34 +428,37 @@ __device__ __forceinline__ void pull_tile(const Gather<Op, kMode> &G, const int4
     sync();
     for (int i0 = 0; i0 < R; i0 += kBlock) {
       const int i = i0 + tid;
-      const bool valid = i < R;
+      const int32_t v = r0 + i;
+      // rows the destination filters reject are not reduced at all
+      const bool want = i < R && in_set(to, v) && op.dst_ok(v);
       int32_t a = 0, b = 0;
-      if (valid) {
+      if (want) {
         a = rp[i] - e0;
         b = rp[i + 1] - e0;
       }
-      const bool big = valid && (b - a) >= 32;
+      const bool big = want && (b - a) >= 32;
       V acc = Op::identity();
-      if (valid && !big)
-        for (int32_t k = a; k < b; ++k) acc = Op::combine(acc, vals[k]);
+      if (want && !big)
+        for (int32_t k = a; k < b; ++k) acc = combine_term<Op>(acc, vals[k]);
       unsigned bal = __ballot_sync(0xffffffffu, big);
       while (bal) {
         const int l = __ffs(bal) - 1;
         bal &= bal - 1;
         const int32_t la = __shfl_sync(0xffffffffu, a, l), lb = __shfl_sync(0xffffffffu, b, l);
         V x = Op::identity();
-        for (int32_t k = la + lane; k < lb; k += 32) x = Op::combine(x, vals[k]);
+        for (int32_t k = la + lane; k < lb; k += 32) x = combine_term<Op>(x, vals[k]);
         x = warp_reduce<V, Op>(x);
         if (lane == l) acc = x;
       }
-      const int32_t v = r0 + i;
       bool mod = false;
-      if (valid && in_set(to, v) && op.dst_ok(v)) mod = op.finish(v, acc);
+      if (want) mod = op.finish(v, acc);
       if (out.enabled()) mark_consecutive(out, r0 + i0 + (tid & ~31), mod);
     }
     sync();
   } else {
-    const int32_t r = T.x, e0 = T.z, ne = T.w - T.z;
+    // one long row (or a piece of it): nothing to gather when its destination is filtered out
+    const int32_t r = T.x, e0 = T.z;
+    const int32_t ne = (in_set(to, r) && op.dst_ok(r)) ? T.w - T.z : 0;
     V x = Op::identity();
     for (int32_t k0 = tid; k0 < ne; k0 += kBatch * kBlock) {
       int32_t u[kBatch];
@@ -451,7 +472,7 @@ __device__ __forceinline__ void pull_tile(const Gather<Op, kMode> &G, const int4
         if constexpr (kMode != kGatherPlain) {
           if (k0 + j * kBlock < ne) x = Op::combine(x, G.hot_val(u[j], e0 + k0 + j * kBlock));
         } else {
-          if (u[j] >= 0 && in_set(G.F, u[j])) x = Op::combine(x, op.edge_val(u[j], e0 + k0 + j * kBlock));
+          if (u[j] >= 0 && in_set(G.F, u[j])) x = combine_term<Op>(x, op.edge_val(u[j], e0 + k0 + j * kBlock));
         }
       }
     }
@@ -462,7 +483,7 @@ __device__ __forceinline__ void pull_tile(const Gather<Op, kMode> &G, const int4
       V y = Op::identity();
       for (int w = 0; w < kBlock / 32; ++w) y = Op::combine(y, s_red[w]);
       if (T.y == r) {
-        if (in_set(to, r) && op.dst_ok(r) && op.finish(r, y) && out.enabled()) out_mark(out, r);
+        if (ne > 0 && op.finish(r, y) && out.enabled()) out_mark(out, r);
       } else {
         partial[t] = y;
       }
@@ -1040,7 +1061,7 @@ __device__ __forceinline__ typename Op::V sparse_row(const Op &op, const int32_t
     for (int j = 0; j < 8; ++j) u[j] = k + j * step < deg ? __ldg(idx + a + k + j * step) : -1;
 #pragma unroll
     for (int j = 0; j < 8; ++j)
-      if (u[j] >= 0 && in_set(F, u[j])) x = Op::combine(x, op.edge_val(u[j], a + k + j * step));
+      if (u[j] >= 0 && in_set(F, u[j])) x = combine_term<Op>(x, op.edge_val(u[j], a + k + j * step));
   }
   return x;
 }
