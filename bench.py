@@ -50,7 +50,7 @@ def parse():
                    help="rmat22 (default): the timed PR+PRD+CC step; the others measure the remaining "
                         "configurations and print their own JSON line")
     p.add_argument("--sources", type=int, default=16, help="sources per graph for the BFS/SSSP workloads")
-    p.add_argument("--only", choices=["pagerank", "pagerank_delta", "cc", "bfs", "sssp"], default=None,
+    p.add_argument("--only", choices=["pagerank", "pagerank_delta", "cc", "bfs", "sssp", "bc"], default=None,
                    help="profiling case: run just this algorithm --steps times on the workload graph")
     p.add_argument("--hot-cache", type=int, choices=[0, 1, 2], default=0,
                    help="profiling case: PageRank / PageRankDelta pulls with the hot-source cache")
@@ -419,6 +419,8 @@ def run_only(args):
             gi.cc(g)
         elif args.only == "bfs":
             gi.bfs(g, 0)
+        elif args.only == "bc":
+            gi.bc(g, int(gg.pick_sources(hg, 10, seed=1)[0]), sched=gi.schedule("hybrid_pull", rule="ligra"))
         else:
             gi.sssp(g, 0)
     torch.cuda.synchronize()
