@@ -70,8 +70,8 @@ def workload_config(hg, scale):
             "pagerank": {"iters": PR_ITERS, "damping": DAMPING,
                          "schedule": "DensePull, autotuned from the hot-source L1 pull"},
             "pagerank_delta": {"iters": PRD_ITERS, "eps": PRD_EPS,
-                               "schedule": "DensePull-SparsePush (Ligra rule), autotuned"},
-            "cc": {"schedule": "DensePull-SparsePush (Ligra rule), autotuned"},
+                               "schedule": "DensePull-SparsePush (Ligra rule), autotuned from the hot-source L1 pull"},
+            "cc": {"schedule": "DensePull-SparsePush (Ligra rule), autotuned from the hot-source L1 pull"},
             "l2": "inputs larger than L2 (CSR %.0f MB vs 126 MB L2); no flush" % ((4 * (hg.n + 1) + 4 * hg.m) / 1e6)}
 
 
@@ -238,8 +238,8 @@ def run_gi(args):
     prd_s, prd_tuned_ms, prd_start_ms = gi.autotune(g, "pagerank_delta",
                                                     start=gi.schedule("hybrid_pull", hot_cache=2),
                                                     budget=args.tune_budget, seed=2)
-    cc_s, cc_tuned_ms, cc_start_ms = gi.autotune(g, "cc", start=gi.schedule("hybrid_pull"), budget=args.tune_budget,
-                                                 seed=3)
+    cc_s, cc_tuned_ms, cc_start_ms = gi.autotune(g, "cc", start=gi.schedule("hybrid_pull", hot_cache=2),
+                                                 budget=args.tune_budget, seed=3)
     tuned = {"pagerank": dict(gi.schedule_dict(pr_s), tuned_ms=pr_tuned_ms, default_ms=pr_start_ms),
              "pagerank_delta": dict(gi.schedule_dict(prd_s), tuned_ms=prd_tuned_ms, default_ms=prd_start_ms),
              "cc": dict(gi.schedule_dict(cc_s), tuned_ms=cc_tuned_ms, default_ms=cc_start_ms)}

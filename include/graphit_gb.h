@@ -198,7 +198,8 @@ typedef struct gi_schedule {
                         /* direction chosen on the device (LEARNED: the MLP; SPARSE_PUSH */
                         /* or DENSE_PUSH: push only; otherwise Beamer's rule); the trace */
                         /* then records only the level count.  0 = one launch per level. */
-  int32_t hot_cache;    /* PageRank / PageRankDelta DensePull over the whole graph:      */
+  int32_t hot_cache;    /* PageRank / PageRankDelta / CC / SSSP DensePull over the whole */
+                        /* graph (CC and SSSP: their driver rounds; always form 2):    */
                         /* the values of the (up to 40,960) highest-out-degree sources   */
                         /* are read from on-chip memory instead of one L2 sector per     */
                         /* arc (the GPU form of the cache partitioning of Sec. 2).       */

@@ -418,7 +418,7 @@ static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src,
         GI_TRY(vset_clear(P.N, s));
         OpMinInt op{x, snap, kernel_id == GI_K_CC ? nullptr : g->in.wt};
         r = launch_pull_tiled(g, op, g->in, g->in_tiles, nullptr, nullptr, out_of(P.N), s, kClassMinPull,
-                              sc.balance == GI_BAL_VERTEX);
+                              sc.balance == GI_BAL_VERTEX, sc.hot_cache);
         P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
       } else if (kernel_id == GI_K_CC) {
         gi_cc_args a{x, snap};

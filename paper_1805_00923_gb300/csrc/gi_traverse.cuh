@@ -98,12 +98,13 @@ struct OpMinInt {  // CC (no weights) and SSSP (weights): x[v] = min(x[v], snap[
   const int32_t *wt;  // pull: in-edge weights; push: out-edge weights (same array for symmetric graphs)
   __device__ static V identity() { return INT32_MAX; }
   __device__ static V combine(V a, V b) { return a < b ? a : b; }
-  __device__ V edge_val(int32_t u, int32_t e) const {
-    int32_t s = __ldg(snap + u);
+  __device__ V from_src(int32_t s, int32_t e) const {
     if (s == INT32_MAX) return INT32_MAX;
     long long t = (long long)s + (wt ? __ldg(wt + e) : 0);
     return t < INT32_MAX ? (int32_t)t : INT32_MAX;
   }
+  __device__ V edge_val(int32_t u, int32_t e) const { return from_src(__ldg(snap + u), e); }
+  __host__ __device__ const int32_t *hot_source() const { return snap; }
   __device__ bool dst_ok(int32_t) const { return true; }
   __device__ bool finish(int32_t v, V acc) const {
     if (acc < x[v]) {
@@ -194,6 +195,7 @@ struct OpPR {
   __device__ static V combine(V a, V b) { return a + b; }
   __device__ V edge_val(int32_t u, int32_t) const { return __ldg(contrib + u); }
   __host__ __device__ const float *hot_source() const { return contrib; }
+  __device__ V from_src(float x, int32_t) const { return x; }
   __device__ bool dst_ok(int32_t) const { return true; }
   __device__ bool finish(int32_t v, V s) const {
     float r = fmaf(damping, s, base);
@@ -219,6 +221,7 @@ struct OpPRD {
   __device__ static V combine(V a, V b) { return a + b; }
   __device__ V edge_val(int32_t u, int32_t) const { return __ldg(contrib + u); }
   __host__ __device__ const float *hot_source() const { return contrib; }
+  __device__ V from_src(float x, int32_t) const { return x; }
   __device__ bool dst_ok(int32_t) const { return true; }
   __device__ bool finish(int32_t v, V s) const {
     float delta, r = rank[v];
@@ -306,15 +309,23 @@ __host__ __device__ constexpr size_t pull_stage_bytes(int tile_edges) {
 // stream is marked evict-first (ld.global.cs), so neither displaces the hot
 // lines.  (Measured on R-MAT 22: 0.424 ms against 0.433 ms with
 // L1::evict_last / L1::no_allocate hints and 0.457 ms with plain loads.)
-__device__ __forceinline__ float ld_hot_f32(const float *p) {
-  float v;
-  asm("ld.global.ca.f32 %0, [%1];" : "=f"(v) : "l"(p));
-  return v;
+template <class T>
+__device__ __forceinline__ T ld_hot(const T *p) {
+  static_assert(sizeof(T) == 4, "hot values are 4-byte");
+  uint32_t v;
+  asm("ld.global.ca.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  T t;
+  __builtin_memcpy(&t, &v, 4);
+  return t;
 }
-__device__ __forceinline__ float ld_cold_f32(const float *p) {
-  float v;
-  asm("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
-  return v;
+template <class T>
+__device__ __forceinline__ T ld_cold(const T *p) {
+  static_assert(sizeof(T) == 4, "hot values are 4-byte");
+  uint32_t v;
+  asm("ld.global.cg.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  T t;
+  __builtin_memcpy(&t, &v, 4);
+  return t;
 }
 __device__ __forceinline__ int32_t ld_stream_i32(const int32_t *p) {
   int32_t v;
@@ -327,22 +338,32 @@ __device__ __forceinline__ int32_t ld_stream_i32(const int32_t *p) {
 //   kGatherHotSmem / kGatherHotL1: F is all vertices and the in-edge sources
 //   were remapped by the graph's HotSet; a negative entry ~s reads slot s of
 //   the hot sources' values -- the block's shared-memory copy (s_hot), or the
-//   dense global array hot (kept in L1 with evict_last; the other loads
-//   bypass L1 so they do not evict it).
+//   dense global array hot (cached in L1; the other loads bypass L1 or are
+//   marked evict-first so they do not evict it).  An Op with a hot form
+//   exposes its per-source 4-byte values (hot_source()) and builds the arc
+//   value from one (from_src(value, e)).
 constexpr int kGatherPlain = 0, kGatherHotSmem = 1, kGatherHotL1 = 2;
+
+template <class Op>
+using hot_src_t = std::remove_cv_t<std::remove_pointer_t<decltype(std::declval<const Op &>().hot_source())>>;
 
 template <class Op, int kMode>
 struct Gather {
   const Op &op;
   FSet F;
-  const float *hot;  // shared memory (kGatherHotSmem) or global (kGatherHotL1)
+  const float *hot;  // 4-byte slots: shared memory (kGatherHotSmem) or global (kGatherHotL1)
   __device__ __forceinline__ int32_t src(const int32_t *p) const {
     if constexpr (kMode == kGatherHotL1) return ld_stream_i32(p);
     else return __ldg(p);
   }
   __device__ __forceinline__ typename Op::V hot_val(int32_t u, int32_t e) const {
-    if constexpr (kMode == kGatherHotSmem) return u < 0 ? hot[~u] : op.edge_val(u, e);
-    else return u < 0 ? ld_hot_f32(hot + ~u) : ld_cold_f32(op.hot_source() + u);
+    if constexpr (kMode == kGatherHotSmem) {
+      return u < 0 ? hot[~u] : op.edge_val(u, e);
+    } else {
+      using S = hot_src_t<Op>;
+      const S sv = u < 0 ? ld_hot(reinterpret_cast<const S *>(hot) + ~u) : ld_cold(op.hot_source() + u);
+      return op.from_src(sv, e);
+    }
   }
 };
 
@@ -550,9 +571,10 @@ __global__ void __launch_bounds__(256 * kGroups, 1) k_pull_hot(Op op, const int3
                             (int)(threadIdx.x % kB), sync);
 }
 
-// hot_vals[s] = contrib[src[s]]: the hot sources' values for one launch
-static __global__ void k_hot_gather(const float *__restrict__ contrib, const int32_t *__restrict__ src, int32_t k,
-                             float *__restrict__ vals) {
+// hot_vals[s] = values[src[s]]: the hot sources' values for one launch
+template <class S>
+static __global__ void k_hot_gather(const S *__restrict__ contrib, const int32_t *__restrict__ src, int32_t k,
+                                    S *__restrict__ vals) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < k) vals[i] = __ldg(contrib + __ldg(src + i));
 }
@@ -1217,7 +1239,7 @@ size_t pull_smem_bytes(int32_t tile_edges) {
   return pull_stage_bytes<typename Op::V>(tile_edges);
 }
 
-// Ops whose arc value is a per-source fp32 value (hot_source()[u]) can use the hot-source pull.
+// Ops whose arc value is built from a per-source 4-byte value (hot_source()[u]) can use the hot-source pull.
 template <class Op, class = void>
 struct HotGatherable : std::false_type {};
 template <class Op>
@@ -1260,19 +1282,25 @@ int launch_pull_hot(gi_graph *g, const Op &op, const TileSet &ts, const uint32_t
                     cudaStream_t s, int kclass, int hot_mode, bool *done) {
   *done = false;
   const int te = ts.tile_edges;
-  if (ts.num_tiles == 0 || te < 512 || (hot_mode == 1 && te > 2048)) return GI_OK;
+  // the shared-memory form holds fp32 values and block tiles of <= 2048 arcs
+  constexpr bool kSmemOk = std::is_same<typename Op::V, float>::value && std::is_same<hot_src_t<Op>, float>::value;
+  if (ts.num_tiles == 0 || te < 512 || (hot_mode == 1 && kSmemOk && te > 2048)) return GI_OK;
   GI_TRY(hot_get(g, s));
   if (g->hot.k == 0) return GI_OK;
   const int tok = timing_begin(kclass, s);
-  k_hot_gather<<<div_up(g->hot.k, 256), 256, 0, s>>>(op.hot_source(), g->hot.src, g->hot.k, g->hot.vals);
+  using S = hot_src_t<Op>;
+  k_hot_gather<S><<<div_up(g->hot.k, 256), 256, 0, s>>>(op.hot_source(), g->hot.src, g->hot.k,
+                                                        reinterpret_cast<S *>(g->hot.vals));
   GI_LAUNCH_CHECK();
   const float *hv = g->hot.vals;
   const int32_t *hp = g->in.ptr, *hi = g->hot.idx;
-  if (hot_mode == 1) {
-    switch (te) {
-      case 512: GI_TRY((launch_pull_hot_te<Op, 512>(g, op, ts, to, out, s))); break;
-      case 1024: GI_TRY((launch_pull_hot_te<Op, 1024>(g, op, ts, to, out, s))); break;
-      default: GI_TRY((launch_pull_hot_te<Op, 2048>(g, op, ts, to, out, s))); break;
+  if (kSmemOk && hot_mode == 1) {
+    if constexpr (kSmemOk) {
+      switch (te) {
+        case 512: GI_TRY((launch_pull_hot_te<Op, 512>(g, op, ts, to, out, s))); break;
+        case 1024: GI_TRY((launch_pull_hot_te<Op, 1024>(g, op, ts, to, out, s))); break;
+        default: GI_TRY((launch_pull_hot_te<Op, 2048>(g, op, ts, to, out, s))); break;
+      }
     }
   } else {
     switch (te) {
@@ -1296,7 +1324,8 @@ int launch_pull_hot(gi_graph *g, const Op &op, const TileSet &ts, const uint32_t
 
 // Tiled pull over the in-edges `c` with tiles `ts` (the whole graph or one segment).
 // hot_mode (gi_schedule.hot_cache) applies to whole-graph pulls from all sources
-// of Ops with per-source fp32 values.
+// of Ops whose arc values come from per-source 4-byte values; Ops with other
+// than fp32 values use the L1 form for both modes.
 template <class Op>
 int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts, FSet F,
                       const uint32_t *to, const OutSet &out, cudaStream_t s, int kclass = kClassOtherPull,

@@ -136,8 +136,7 @@ extern "C" int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_sche
     knobs.push_back({&gi_schedule::num_segments, {1, 2, 4, 8}});
     knobs.push_back({&gi_schedule::seg_strategy, {GI_SEG_FVC, GI_SEG_EVC}});
   }
-  if (algo == GI_ALGO_PAGERANK || algo == GI_ALGO_PAGERANK_DELTA)
-    knobs.push_back({&gi_schedule::hot_cache, {0, 1, 2}});
+  if (algo != GI_ALGO_BFS) knobs.push_back({&gi_schedule::hot_cache, {0, 1, 2}});
   std::mt19937_64 rng(seed);
   const int reps = 2;
   gi_schedule cur = *start, top = *start;

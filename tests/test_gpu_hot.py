@@ -129,3 +129,32 @@ def test_hot_set_rebuilt_after_new_in_edges(gi):
     again = _np(gi.pagerank(g, 0.85, 10, sched=gi.schedule("dense_pull", hot_cache=1)))
     assert np.array_equal(first.view(np.uint32), again.view(np.uint32))
     assert _max_rel(again, oracle.pagerank(hg, 0.85, 10, in_edges=(in_ptr, in_col))) < PR_TOL
+
+
+WEIGHTED = {
+    "rmat14_all_hot": lambda: rmat(14, weights=True),
+    "rmat18_head_hot": lambda: rmat(18, weights=True),
+    "grid300_ties": lambda: grid(300, weights=True),
+    "hub_tail_split_row": lambda: adversarial("hub_tail", weights=True),
+}
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("name", list(WEIGHTED))
+def test_hot_cc_sssp_exact(gi, name, mode):
+    """Min-label pulls (CC, SSSP) read snap[u] of hot sources from the hot
+    array (both modes run the L1 form for integer values): labels, distances
+    and per-round frontiers equal the oracle's."""
+    hg = WEIGHTED[name]()
+    g = gi.Graph.from_host(hg)
+    for direction in ("dense_pull", "hybrid_pull"):
+        sc = gi.schedule(direction, hot_cache=mode)
+        want, fs = oracle.cc(hg)
+        tr = gi.Trace(1 << 12)
+        assert np.array_equal(_np(gi.cc(g, sched=sc, trace=tr)), want)
+        assert np.array_equal(tr.as_dict()["frontier"], fs)
+        src = int(gg.pick_sources(hg, 1, seed=3)[0])
+        want, fs = oracle.sssp(hg, src)
+        tr = gi.Trace(1 << 14)
+        assert np.array_equal(_np(gi.sssp(g, src, sched=sc, trace=tr)), want)
+        assert np.array_equal(tr.as_dict()["frontier"], fs)
