@@ -360,7 +360,9 @@ def run_gi(args):
             selector["bfs_" + ("beamer" if pol == "hybrid_pull" else "learned") + "_gteps"] = ed / (ms * 1e-3) / 1e9
 
     peak, peak_kind = measured_hbm()
-    bytes_per_launch = 4 * m + 16 * n + 4
+    # algorithmic bytes of one PageRank DensePull launch: offsets 4(n+1), indices 4m,
+    # one gathered 4-byte contribution per arc 4m, 1/outdeg 4n, one output vector 4n
+    bytes_per_launch = 8 * m + 12 * n + 4
     avg_ms = pr_ms / max(pr_launches, 1)
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     hot = int(pr_s.hot_cache) if pr_s.direction == gi.GI_DIR_DENSE_PULL and pr_s.num_segments == 1 else 0
@@ -383,7 +385,8 @@ def run_gi(args):
                                        "in shared memory)",
                                     2: "k_hot_gather + k_pull_tiled<OpPR, hot L1> (PageRank DensePull iteration, hot "
                                        "sources kept in L1)"}[hot],
-                         "bytes_model": "4m + 16n + 4 per launch", "launches_timed": pr_launches,
+                         "bytes_model": "8m + 12n + 4 per launch (offsets, indices, one gathered contribution "
+                                        "per arc, 1/outdeg, output vector)", "launches_timed": pr_launches,
                          "avg_launch_ms": avg_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": sum(e2e_ms) / max(len(e2e_ms), 1)},
