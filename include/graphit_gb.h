@@ -197,7 +197,12 @@ typedef struct gi_schedule {
                         /* persistent kernel (the batched engine's whole-GPU mode), the */
                         /* direction chosen on the device (LEARNED: the MLP; SPARSE_PUSH */
                         /* or DENSE_PUSH: push only; otherwise Beamer's rule); the trace */
-                        /* then records only the level count.  0 = one launch per level. */
+                        /* then records only the level count.  2 (gi_bfs only; gi_sssp  */
+                        /* runs host-driven) = the level loop is a CUDA graph (a WHILE */
+                        /* node over the library's per-level kernels, direction and     */
+                        /* loop condition set on the device, no host round trip per     */
+                        /* level), built on first use and cached per graph and schedule; */
+                        /* trace: level count only.  0 = one host-driven round per level. */
   int32_t hot_cache;    /* PageRank / PageRankDelta / CC / SSSP DensePull over the whole */
                         /* graph (CC and SSSP: their driver rounds; always form 2):    */
                         /* the values of the (up to 40,960) highest-out-degree sources   */

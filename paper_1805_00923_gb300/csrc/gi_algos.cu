@@ -4,6 +4,7 @@
 // one traversal, and (where the algorithm needs one) a vertex epilogue.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "gi_traverse.cuh"
@@ -307,6 +308,166 @@ static int run_persistent(gi_graph *g, int32_t algo, int32_t src, int32_t *out, 
   return st != GI_OK ? st : st2;
 }
 
+// ========================================================= graph-driven BFS ==
+// gi_schedule.persistent = 2: the level loop runs on the device as a CUDA
+// graph.  One WHILE node repeats a body of two levels (the frontier sets
+// alternate roles); each level is the statistics + direction kernel, which
+// empties the next frontier, writes the level's control words and sets the
+// loop condition, then the push (with the all-block expansion of deferred
+// sources) and the early-exit pull, each a no-op unless the level uses it.
+// No host round trip per level.
+// The graph is built once per graph and schedule; depths go to an internal
+// buffer that is copied out after the launch.
+namespace gi {
+
+struct OpBFSDev {  // BFS claim with the level read from the control words
+  int32_t *depth;
+  const int32_t *gm;
+  __device__ bool push(int32_t, int32_t v, int32_t) const {
+    if (*(volatile int32_t *)(depth + v) != -1) return false;
+    return atomicCAS(depth + v, -1, gm[kGmLevel] + 1) == -1;
+  }
+};
+
+struct GraphLoop {
+  gi_schedule sc{};
+  int use_selector = -1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int32_t *depth = nullptr;
+  int32_t *gm = nullptr;
+  gi_vset a, b;
+};
+
+__global__ void k_gm_init(int32_t *gm, int32_t cap) {
+  if (threadIdx.x < kGmWords) gm[threadIdx.x] = threadIdx.x == kGmCap ? cap : 0;
+}
+
+void graph_loop_free(gi_graph *g) {
+  GraphLoop *L = static_cast<GraphLoop *>(g->graph_loop);
+  if (!L) return;
+  if (L->exec) cudaGraphExecDestroy(L->exec);
+  if (L->graph) cudaGraphDestroy(L->graph);
+  for (gi_vset *v : {&L->a, &L->b}) {
+    dev_free(v->queue, nullptr);
+    dev_free(v->count, nullptr);
+    dev_free(v->bitmap, nullptr);
+    dev_free(v->boolmap, nullptr);
+  }
+  dev_free(L->depth, nullptr);
+  dev_free(L->gm, nullptr);
+  delete L;
+  g->graph_loop = nullptr;
+}
+
+// one level, F -> N, captured into the loop body: the statistics kernel
+// (which also empties N and writes the level's control words), the push
+// (queue length 0 unless this level pushes) and the early-exit pull (returns
+// at once unless this level pulls).  Kernels that exit at once measured
+// cheaper than IF nodes around them (grid 4096^2: 82 vs 103 ms per BFS).
+static int graph_level(gi_graph *g, const gi_schedule &sc, GraphLoop *L, gi_vset *F, gi_vset *N,
+                       cudaGraphConditionalHandle h, cudaStream_t cs) {
+  DecideParams p = decide_params(sc, 0, true);
+  p.gm = L->gm;
+  p.cond_handle = (unsigned long long)h;
+  p.clear_bm = N->bitmap;  // N holds the frontier of two levels before: its queue lists its bits
+  p.clear_q = N->queue;
+  p.clear_qc = N->count;
+  GI_TRY(frontier_decide(g, F, p, cs));
+  gi_vset Fp = *F;  // the push sees |F| only when this level pushes
+  Fp.count = L->gm + kGmPush;
+  const OpBFSDev op{L->depth, L->gm};
+  GI_TRY(launch_push(g, op, kSrcQueue, &Fp, nullptr, out_of(N, false), sc, cs));
+  if (g->has_csc) {
+    const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
+    k_pull_bfs<<<grid_for(g, g->n, 256), 256, 0, cs>>>(g->in.ptr, g->in.idx, g->n,
+                                                      FSet(static_cast<const uint32_t *>(F->bitmap)), nullptr,
+                                                      L->depth, nullptr, 0, tw, N->bitmap, N->queue, N->count, L->gm);
+    GI_LAUNCH_CHECK();
+  }
+  N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
+  return GI_OK;
+}
+
+static int graph_loop_build(gi_graph *g, const gi_schedule &sc, GraphLoop *L, cudaStream_t s) {
+  GI_TRY(heavy_get(g, s));
+  GI_TRY(dev_alloc_n(&L->depth, g->n, s));
+  GI_TRY(dev_alloc_n(&L->gm, kGmWords, s));
+  GI_TRY(vset_alloc(g, &L->a, s));
+  GI_TRY(vset_alloc(g, &L->b, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  GI_CUDA(cudaGraphCreate(&L->graph, 0));
+  cudaGraphConditionalHandle h;
+  GI_CUDA(cudaGraphConditionalHandleCreate(&h, L->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  GI_CUDA(cudaGraphAddNode(&loop, L->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs;
+  GI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  int st = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess
+               ? GI_OK
+               : cuda_fail(cudaGetLastError(), "begin capture", __FILE__, __LINE__);
+  L->a.reps = L->b.reps = GI_REP_SPARSE | GI_REP_BITMAP;
+  if (st == GI_OK) st = graph_level(g, sc, L, &L->a, &L->b, h, cs);
+  if (st == GI_OK) st = graph_level(g, sc, L, &L->b, &L->a, h, cs);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
+  cudaStreamDestroy(cs);
+  if (st == GI_OK && ec != cudaSuccess) st = cuda_fail(ec, "end capture", __FILE__, __LINE__);
+  if (st == GI_OK && cudaGraphInstantiate(&L->exec, L->graph, 0) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "graph instantiate", __FILE__, __LINE__);
+  return st;
+}
+
+// BFS depths by the graph-driven loop; levels = number of levels
+static int run_graph_bfs(gi_graph *g, int32_t src, int32_t *depth, const gi_schedule &sched, int32_t *levels,
+                         cudaStream_t s) {
+  gi_schedule sc = sched;
+  sc.balance = sc.balance == GI_BAL_EDGE_PARALLEL ? GI_BAL_EDGE_AWARE : sc.balance;  // needs a host-known |F|
+  if (!g->has_csc) sc.direction = GI_DIR_SPARSE_PUSH;
+  const int use_sel = selector_loaded() ? 1 : 0;
+  GraphLoop *L = static_cast<GraphLoop *>(g->graph_loop);
+  if (L && (std::memcmp(&L->sc, &sc, sizeof(sc)) != 0 || L->use_selector != use_sel)) {
+    graph_loop_free(g);
+    L = nullptr;
+  }
+  if (!L) {
+    L = new GraphLoop();
+    L->sc = sc;
+    L->use_selector = use_sel;
+    g->graph_loop = L;
+    const int st = graph_loop_build(g, sc, L, s);
+    if (st != GI_OK) {
+      graph_loop_free(g);
+      return st;
+    }
+  }
+  k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(L->depth, nullptr, g->n, src);
+  k_gm_init<<<1, 32, 0, s>>>(L->gm, (int32_t)(g->n + 1 < INT32_MAX ? g->n + 1 : INT32_MAX));
+  GI_TRY(launch_status(2));
+  GI_TRY(front_init(g, &L->a, src, s));
+  GI_TRY(vset_clear(&L->b, s));  // the loop empties b through its queue from then on
+  GI_TRY(ctrl_init(g, g->n, g->m, s));
+  GI_CUDA(cudaGraphLaunch(L->exec, s));
+  GI_CUDA(cudaMemcpyAsync(depth, L->depth, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
+  int32_t gm[kGmWords];
+  GI_CUDA(cudaMemcpyAsync(gm, L->gm, sizeof(gm), cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  if (gm[kGmErr]) {
+    set_error("graph-driven BFS reached its level cap");
+    return GI_ERR_TIMEOUT;
+  }
+  *levels = gm[kGmNext];
+  return GI_OK;
+}
+
+}  // namespace gi
+
 // ===================================================================== BFS ==
 extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent, const gi_schedule *sched,
                       gi_trace *trace, void *stream) {
@@ -318,8 +479,15 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
   const gi_schedule sc = *sched;
   if (forced_direction(sc.direction) >= 0) GI_TRY(pull_available(g, forced_direction(sc.direction)));
   if (sc.persistent && (!parent || g->has_csc)) {
-    // depths in one persistent launch; canonical parents by the in-edge pass
-    GI_TRY(run_persistent(g, GI_ALGO_BFS, src, depth, sc, trace, s));
+    // depths in one persistent launch or the graph-driven loop; canonical
+    // parents by the in-edge pass
+    if (sc.persistent == 2) {
+      int32_t levels = 0;
+      GI_TRY(run_graph_bfs(g, src, depth, sc, &levels, s));
+      if (trace) trace->iterations = levels;
+    } else {
+      GI_TRY(run_persistent(g, GI_ALGO_BFS, src, depth, sc, trace, s));
+    }
     if (!parent) return GI_OK;
     k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n, INT32_MAX);
     k_set_one<<<1, 1, 0, s>>>(parent, src, src);
@@ -452,7 +620,7 @@ extern "C" int gi_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedul
   if (forced_direction(sched->direction) == GI_DIR_DENSE_PULL || sched->direction == GI_DIR_HYBRID_PULL) {
     GI_ARG(g->symmetric || g->in.wt != nullptr, "pull SSSP needs in-edge weights (gi_load_csc with weights)");
   }
-  if (sched->persistent) return run_persistent(g, GI_ALGO_SSSP, src, dist, *sched, trace, (cudaStream_t)stream);
+  if (sched->persistent == 1) return run_persistent(g, GI_ALGO_SSSP, src, dist, *sched, trace, (cudaStream_t)stream);
   return minlabel_run(g, dist, GI_K_SSSP, src, *sched, trace, (cudaStream_t)stream);
 }
 

@@ -65,6 +65,8 @@ static cudaEvent_t pool_event() {
 
 int timing_begin(int kclass, cudaStream_t s) {
   if (!g_timing.load(std::memory_order_relaxed)) return -1;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return -1;  // graph capture
   std::lock_guard<std::mutex> lk(g_timing_mu);
   TimedRec r{kclass, pool_event(), pool_event()};
   if (!r.a || !r.b) return -1;
@@ -408,6 +410,7 @@ static void segs_free(gi_graph *g, cudaStream_t s);
 
 static void graph_release(gi_graph *g, cudaStream_t s) {
   if (!g) return;
+  graph_loop_free(g);
   free_tile_cache(g, s);
   segs_free(g, s);
   if (!g->symmetric) {
@@ -1336,6 +1339,10 @@ __global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *
   unsigned long long local = 0;
   // 8 independent queue loads, then 8 independent degree gathers, per round trip
   const int32_t stride = gridDim.x * blockDim.x;
+  if (p.clear_bm) {  // graph-driven: empty the set this level fills
+    const int32_t cc = *p.clear_qc;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cc; i += stride) p.clear_bm[p.clear_q[i] >> 5] = 0u;
+  }
   for (int32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < c; i0 += 8 * stride) {
     int32_t v[8];
 #pragma unroll
@@ -1350,7 +1357,7 @@ __global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *
   if (threadIdx.x == 0) {
     unsigned long long b = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_sum[w];
-    atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kMf), b);
+    atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kMfAcc), b);
     __threadfence();
     unsigned long long t = atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kTicket), 1ull);
     last = (t == gridDim.x - 1);
@@ -1359,7 +1366,7 @@ __global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *
   if (!last) return;
   __threadfence();
   int64_t nf = c;
-  int64_t mf = *(volatile int64_t *)(ctrl + kMf);
+  int64_t mf = *(volatile int64_t *)(ctrl + kMfAcc);
   int64_t nu = ctrl[kNu], mu = ctrl[kMu];
   if (p.track_unvisited) {
     nu -= nf;
@@ -1367,7 +1374,8 @@ __global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *
   }
   int32_t was_pull = (int32_t)ctrl[kWasPull];
   int64_t nf_prev = ctrl[kNfPrev];
-  if (threadIdx.x == 0) level_features(feat, n, m, maxdeg, nf, mf, nu, mu, p.level, was_pull, nf_prev);
+  const int32_t level = p.gm ? *(volatile int32_t *)(p.gm + kGmNext) : p.level;
+  if (threadIdx.x == 0) level_features(feat, n, m, maxdeg, nf, mf, nu, mu, level, was_pull, nf_prev);
   __syncthreads();
   int32_t dir;
   if (p.mode == 0) {
@@ -1395,9 +1403,20 @@ __global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *
     ctrl[kMu] = mu;
     ctrl[kDecision] = dir;
     ctrl[kWasPull] = (dir == GI_DIR_DENSE_PULL) ? 1 : 0;
-    ctrl[kLevel] = p.level;
+    ctrl[kLevel] = level;
     ctrl[kNfPrev] = nf;
     ctrl[kTicket] = 0;
+    ctrl[kMfAcc] = 0;
+    if (p.clear_qc) *p.clear_qc = 0;  // every block has passed its clearing loop
+    if (p.gm) {  // graph-driven: both traversals of the level read their part
+      const bool go = nf > 0 && level < p.gm[kGmCap];
+      if (nf > 0 && !go) p.gm[kGmErr] = 1;
+      p.gm[kGmPush] = (go && dir != GI_DIR_DENSE_PULL) ? (int32_t)nf : 0;
+      p.gm[kGmPull] = (go && dir == GI_DIR_DENSE_PULL) ? 1 : 0;
+      p.gm[kGmLevel] = level;
+      if (go) p.gm[kGmNext] = level + 1;
+      cudaGraphSetConditional((cudaGraphConditionalHandle)p.cond_handle, go ? 1u : 0u);
+    }
   }
 }
 
@@ -1418,7 +1437,6 @@ int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s) {
 
 int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s) {
   GI_TRY(vset_ensure_queue(F, s));
-  GI_CUDA(cudaMemsetAsync(g->ctrl + kMf, 0, sizeof(int64_t), s));
   int blocks = g->num_sms * 2;
   k_frontier_decide<<<blocks, 256, 0, s>>>(F->queue, F->count, g->out_deg, g->ctrl, p, g->n, g->m, g->max_deg,
                                            g_sel_loaded ? 1 : 0);

@@ -77,6 +77,7 @@ enum CtrlSlot {
   kNfPrev = 7,
   kTicket = 8,    // last-block ticket of the statistics kernel
   kErr = 9,       // device-side error flag (bounded waits, bounds checks)
+  kMfAcc = 10,    // m_f accumulator of the statistics kernel (its last block returns it to 0)
   kFeat = 16,     // 16 float features stored as float bits in 8 int64 words (slots 16..23)
 };
 
@@ -147,6 +148,7 @@ struct gi_graph {
   // their per-round statistics, cleared after the round); -1 = unknown
   const gi_vset *hint_vset = nullptr;
   int64_t hint_nf = -1;
+  void *graph_loop = nullptr;    // cached CUDA graph of the graph-driven BFS (gi_schedule.persistent = 2)
   int64_t *ctrl = nullptr;       // device control block (kCtrlWords)
   void *heavy_mem = nullptr;     // HeavyList storage (counter, ticket, 2n entries), allocated on first use
   int64_t *ctrl_host = nullptr;  // pinned mirror
@@ -212,6 +214,7 @@ int ws_scratch(gi_graph *g, int32_t **a, int32_t **b, cudaStream_t s);
 int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cudaStream_t s);
 int use_tiles(gi_graph *g, int32_t tile_edges, cudaStream_t s);  // select (building once) the in-edge tiles
 void free_tile_cache(gi_graph *g, cudaStream_t s);
+void graph_loop_free(gi_graph *g);  // the cached graph-driven BFS (gi_algos.cu)
 void free_tiles(TileSet *ts, cudaStream_t s);
 int hot_get(gi_graph *g, cudaStream_t s);  // build (once) g->hot from the in-edges
 void hot_free(gi_graph *g, cudaStream_t s);
@@ -225,6 +228,19 @@ int vset_ensure_bool(gi_vset *v, cudaStream_t s);
 
 // frontier statistics + direction decision (fused); reads F's queue.
 // mode: 0 = forced direction `forced`, 1 = rule (hybrid), 2 = learned.
+// Device-side level control of the graph-driven drivers (int32 words): the
+// statistics kernel reads the level from kGmNext, writes what each traversal
+// kernel of the level needs, and sets the WHILE condition of the graph.
+enum GmSlot {
+  kGmPush = 0,   // queue length the push kernel sees (|F| if this level pushes, else 0)
+  kGmPull = 1,   // 1 if this level pulls
+  kGmLevel = 2,  // index of the level being expanded (its new vertices get depth kGmLevel + 1)
+  kGmNext = 3,   // index of the next level
+  kGmCap = 4,    // level cap: reaching it stops the loop with kGmErr set
+  kGmErr = 5,
+  kGmWords = 8
+};
+
 struct DecideParams {
   int32_t mode;
   int32_t forced;      // GI_DIR_* when mode == 0
@@ -233,6 +249,13 @@ struct DecideParams {
   float alpha, beta;
   int32_t track_unvisited;  // subtract |F|, m_f from n_u, m_u after deciding (BFS)
   int32_t level;
+  int32_t *gm = nullptr;                     // graph-driven mode: GmSlot words (level read from there)
+  unsigned long long cond_handle = 0;        // graph-driven mode: cudaGraphConditionalHandle of the loop
+  // graph-driven mode: the set the level fills, emptied here (its bits are
+  // exactly its queue's members: the frontier of two levels before)
+  uint32_t *clear_bm = nullptr;
+  const int32_t *clear_q = nullptr;
+  int32_t *clear_qc = nullptr;
 };
 int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s);
 int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s);

@@ -195,6 +195,7 @@ int check_schedule(const gi_schedule *sc) {
          "tile_edges must be a power of two in [256, 8192]");
   GI_ARG(sc->hot_cache >= 0 && sc->hot_cache <= 2, "hot_cache must be 0, 1 or 2");
   GI_ARG(sc->seg_strategy == GI_SEG_FVC || sc->seg_strategy == GI_SEG_EVC, "seg_strategy must be FVC or EVC");
+  GI_ARG(sc->persistent >= 0 && sc->persistent <= 2, "persistent must be 0, 1 or 2");
   return GI_OK;
 }
 

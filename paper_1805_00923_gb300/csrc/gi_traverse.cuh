@@ -720,7 +720,11 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
                                                   int64_t n, FSet F,
                                                   const uint32_t *__restrict__ to, int32_t *depth, int32_t *parent,
                                                   int32_t level, int32_t t_warp, uint32_t *out_bm, int32_t *out_q,
-                                                  int32_t *out_qc) {
+                                                  int32_t *out_qc, const int32_t *gm = nullptr) {
+  if (gm) {  // graph-driven level: run only when this level pulls
+    if (gm[kGmPull] == 0) return;
+    level = gm[kGmLevel] + 1;
+  }
   const int lane = threadIdx.x & 31;
   const int64_t nw = (n + 31) >> 5;
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
@@ -1454,7 +1458,7 @@ int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const 
                                                tw, tc, th, heavy);
   }
   GI_LAUNCH_CHECK();
-  if (th != INT32_MAX) {
+  if (th != INT32_MAX && g->max_deg >= th) {  // otherwise no source can have been deferred
     k_push_heavy<Op><<<g->num_sms * 4, block, 0, s>>>(op, g->out.ptr, g->out.idx, heavy, g->n, to, out);
     GI_LAUNCH_CHECK();
   }

@@ -120,9 +120,11 @@ def test_batch_sssp_threshold_orders(gi, delta):
     _check(hgs, qs, res)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("selector", ["sparse_push", "hybrid_pull", "learned"])
-def test_persistent_single_queries(gi, selector):
-    """BFS (depth + canonical parent) and SSSP in the whole-GPU persistent mode."""
+def test_persistent_single_queries(gi, selector, mode):
+    """BFS (depth + canonical parent) and SSSP in the whole-GPU persistent mode
+    (1) and with the level loop as a CUDA graph (2; SSSP then runs host-driven)."""
     if selector == "learned":
         if not os.path.exists(WEIGHTS):
             pytest.skip("no trained selector weights committed")
@@ -131,7 +133,7 @@ def test_persistent_single_queries(gi, selector):
     for hg in [rmat(14, weights=True), grid(64, weights=True), adversarial("path", True),
                adversarial("components", True), adversarial("single", True)]:
         g = gi.Graph.from_host(hg)
-        sc = gi.schedule(selector, persistent=1)
+        sc = gi.schedule(selector, persistent=mode)
         for src in sorted({0, hg.n // 3, hg.n - 1}):
             wd, wp, levels = oracle.bfs(hg, src)
             tr = gi.Trace(16)
@@ -156,3 +158,34 @@ def test_grid_barrier_wait_runs_out(gi):
         lib.gi_debug_barrier_phantoms(0)
     res, _ = gi.batch_run([g], [(0, 0, "bfs"), (0, 3, "bfs")], opts=gi.batch_opts(cluster_size=0))
     _check([hg], [(0, 0, "bfs"), (0, 3, "bfs")], res)
+
+
+def test_graph_driven_bfs_cache_and_reuse(gi):
+    """The cached graph is rebuilt when the schedule changes and reused across
+    sources and output buffers; results stay the oracle's."""
+    import torch
+    hg = rmat(13)
+    g = gi.Graph.from_host(hg)
+    for k, sc in enumerate([gi.schedule("hybrid_pull", persistent=2), gi.schedule("hybrid_pull", persistent=2),
+                            gi.schedule("sparse_push", persistent=2), gi.schedule("hybrid_pull", persistent=2,
+                                                                                   alpha=4.0)]):
+        for src in (0, 100 + k, hg.n - 1):
+            out = (torch.full((hg.n,), 77, dtype=torch.int32, device="cuda"),
+                   torch.full((hg.n,), 77, dtype=torch.int32, device="cuda"))
+            tr = gi.Trace(8)
+            d, p = gi.bfs(g, src, sched=sc, trace=tr, out=out)
+            wd, wp, levels = oracle.bfs(hg, src)
+            assert np.array_equal(d.cpu().numpy(), wd) and np.array_equal(p.cpu().numpy(), wp)
+            assert tr.iterations == len(levels)
+
+
+def test_graph_driven_bfs_directed_without_in_edges(gi):
+    """Without in-edges the graph-driven loop pushes every level."""
+    rng = np.random.default_rng(2)
+    n = 2000
+    e = rng.integers(0, n, (10_000, 2))
+    hg = gg.from_edge_list(n, map(tuple, e), symmetrize=False)
+    g = gi.Graph(hg.row_ptr, hg.col, symmetric=False)
+    d, _ = gi.bfs(g, 5, want_parent=False, sched=gi.schedule("hybrid_pull", persistent=2))
+    want = oracle.bfs(hg, 5, in_edges=gg.transpose(hg)[:2])[0]
+    assert np.array_equal(d.cpu().numpy(), want)
