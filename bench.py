@@ -510,6 +510,16 @@ def run_rmat24(args):
                 ms += a.elapsed_time(b)
                 edges += int(tr.as_dict()["edges"].sum())
             res[pol] = {"gteps": edges / (ms * 1e-3) / 1e9, "ms_per_query": ms / len(srcs)}
+        if algo == "bfs":  # the same queries with the level loop as a CUDA graph
+            gsc = gi.schedule("hybrid_pull", persistent=2)
+            gi.bfs(g, int(srcs[0]), want_parent=False, sched=gsc)
+            a, b = _events()
+            a.record()
+            for s_ in srcs:
+                gi.bfs(g, int(s_), want_parent=False, sched=gsc)
+            b.record()
+            torch.cuda.synchronize()
+            res["graph_driven_ms_per_query"] = a.elapsed_time(b) / len(srcs)
         best_ms = 0.0
         for s_ in srcs[:max(1, len(srcs) // 4)]:
             f, t = sel.profile(g, gi.GI_K_BFS if algo == "bfs" else gi.GI_K_SSSP, int(s_))
@@ -557,6 +567,17 @@ def run_grid4096(args):
         b.record()
         torch.cuda.synchronize()
         pers_ms = a.elapsed_time(b) / 4
+        graph_ms = None
+        if algo == "bfs":  # the level loop as a CUDA graph (BFS)
+            gsc = gi.schedule("hybrid_pull", persistent=2)
+            gi.bfs(g, int(srcs[0]), want_parent=False, sched=gsc)
+            a, b = _events()
+            a.record()
+            for s_ in srcs[:4]:
+                gi.bfs(g, int(s_), want_parent=False, sched=gsc)
+            b.record()
+            torch.cuda.synchronize()
+            graph_ms = a.elapsed_time(b) / 4
         qs = [(0, int(s_), algo) for s_ in srcs]
         plan = gi.BatchPlan([g], qs, opts=gi.batch_opts(cluster_size=8, selector="learned"))
         plan.launch()
@@ -569,7 +590,8 @@ def run_grid4096(args):
         res, ns, lev = plan.results()
         plan.free()
         bms = a.elapsed_time(b)
-        out[algo] = {"host_driven_ms_per_query": host_ms, "persistent_ms_per_query": pers_ms, "batch_ms_total": bms,
+        out[algo] = {"host_driven_ms_per_query": host_ms, "persistent_ms_per_query": pers_ms,
+                     "graph_driven_ms_per_query": graph_ms, "batch_ms_total": bms,
                      "batch_gteps_nominal": len(qs) * hg.m / (bms * 1e-3) / 1e9,
                      "p50_ms": float(np.percentile(ns, 50) / 1e6), "p99_ms": float(np.percentile(ns, 99) / 1e6),
                      "levels_mean": float(lev.mean())}
