@@ -518,6 +518,7 @@ extern "C" int gi_load_csc(gi_graph *g, const int32_t *in_offsets, const int32_t
   GI_ARG(((flags & GI_HOST_PTRS) != 0) != ((flags & GI_DEV_PTRS) != 0), "exactly one of GI_HOST_PTRS/GI_DEV_PTRS");
   cudaStream_t s = (cudaStream_t)stream;
   if (g->symmetric) return GI_OK;  // the CSR already is the in-edge view
+  graph_loop_free(g);              // its kernels hold the in-edge arrays
   if (g->has_csc) {
     free_tile_cache(g, s);
     dev_free(g->in.ptr, s);

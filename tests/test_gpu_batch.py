@@ -189,3 +189,18 @@ def test_graph_driven_bfs_directed_without_in_edges(gi):
     d, _ = gi.bfs(g, 5, want_parent=False, sched=gi.schedule("hybrid_pull", persistent=2))
     want = oracle.bfs(hg, 5, in_edges=gg.transpose(hg)[:2])[0]
     assert np.array_equal(d.cpu().numpy(), want)
+
+
+def test_graph_driven_bfs_follows_new_in_edges(gi):
+    """gi_load_csc drops the cached graph (its kernels hold the in-edge arrays)."""
+    rng = np.random.default_rng(6)
+    n = 3000
+    e = rng.integers(0, n, (12_000, 2))
+    hg = gg.from_edge_list(n, map(tuple, e), symmetrize=False)
+    ip, ic, _ = gg.transpose(hg)
+    g = gi.Graph(hg.row_ptr, hg.col, symmetric=False, in_edges=(ip, ic, None))
+    sc = gi.schedule("dense_pull", persistent=2)
+    want = oracle.bfs(hg, 1, in_edges=(ip, ic))[0]
+    assert np.array_equal(gi.bfs(g, 1, want_parent=False, sched=sc)[0].cpu().numpy(), want)
+    g.load_in_edges(ip.copy(), ic.copy())
+    assert np.array_equal(gi.bfs(g, 1, want_parent=False, sched=sc)[0].cpu().numpy(), want)
