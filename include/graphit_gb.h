@@ -41,7 +41,7 @@ extern "C" {
 
 /* Message of the calling thread's last failure ("" if none).  Never NULL. */
 const char *gi_last_error(void);
-/* Library version as major*10000 + minor*100 + patch. */
+/* Library version as major*10000 + minor*100 + patch (never fails). */
 int gi_version(void);
 
 /* ----------------------------------------------------------------- graph -- */
@@ -75,9 +75,11 @@ int gi_load_csr(const int32_t *offsets, const int32_t *indices, const int32_t *w
 int gi_load_csc(gi_graph *g, const int32_t *in_offsets, const int32_t *in_indices, const int32_t *in_weights,
                 uint32_t flags, void *stream);
 
+/* Releases g and everything built on it (tiles, segments, caches); NULL is a no-op. */
 int gi_graph_free(gi_graph *g);
 
-/* n, m and the maximum out-degree.  Any output pointer may be NULL. */
+/* n, m and the maximum out-degree (host outputs).  Any output pointer may be
+ * NULL.  Errors: GI_ERR_INVALID_ARG (g NULL). */
 int gi_graph_info(const gi_graph *g, int64_t *n, int64_t *m, int32_t *max_deg);
 
 /*
@@ -90,7 +92,8 @@ int gi_graph_info(const gi_graph *g, int64_t *n, int64_t *m, int32_t *max_deg);
  */
 int gi_graph_hot_info(gi_graph *g, int32_t *k, int32_t *min_deg, void *stream);
 
-/* Device pointers of the library's copy: out-offsets, out-indices, out-weights (NULL if none). */
+/* Device pointers of the library's copy: out-offsets, out-indices, out-weights (NULL if none);
+ * owned by g, valid until gi_graph_free.  Errors: GI_ERR_INVALID_ARG (g NULL). */
 int gi_graph_device_csr(const gi_graph *g, const int32_t **offsets, const int32_t **indices,
                         const int32_t **weights);
 
@@ -111,9 +114,10 @@ int gi_graph_device_csr(const gi_graph *g, const int32_t **offsets, const int32_
 int gi_graph_build_segments(gi_graph *g, int32_t num_segments, int32_t strategy, void *stream);
 
 /*
- * The current segments: *num (1 without segments), *strategy, bounds[0..num]
- * (segment s holds sources [bounds[s], bounds[s+1])) and arcs[0..num-1];
- * bounds/arcs may be NULL, and at most cap segments are written.
+ * The current segments (host memory outputs): *num (1 without segments),
+ * *strategy, bounds[0..num] (segment s holds sources [bounds[s], bounds[s+1]))
+ * and arcs[0..num-1]; any output may be NULL, and at most cap segments are
+ * written.  Does not touch the device.  Errors: GI_ERR_INVALID_ARG (g NULL).
  */
 int gi_graph_segment_info(const gi_graph *g, int32_t *num, int32_t *strategy, int32_t *bounds, int64_t *arcs,
                           int32_t cap);
@@ -130,20 +134,27 @@ typedef struct gi_vset gi_vset;
 #define GI_REP_BOOL 0x2u   /* one byte per vertex (boolean map)                      */
 #define GI_REP_BITMAP 0x4u /* one bit per vertex, uint32 words (bitvector)           */
 
-/* Create a vertexset over g's vertices; it stays valid until gi_vset_free. */
+/* Create a vertexset over g's vertices (init GI_VSET_*, v for SINGLE); it stays
+ * valid until gi_vset_free and must be freed before g.  Errors:
+ * GI_ERR_INVALID_ARG (NULL g/out, unknown init, v out of range), GI_ERR_OOM. */
 int gi_vset_create(gi_graph *g, int32_t init, int32_t v, void *stream, gi_vset **out);
+/* Releases s (NULL is a no-op). */
 int gi_vset_free(gi_vset *s);
 
-/* size() of Table 2.  Syncs the stream. */
+/* size() of Table 2 into *out (host).  Syncs the stream.  Errors:
+ * GI_ERR_INVALID_ARG (NULL), GI_ERR_CUDA. */
 int gi_vset_size(gi_vset *s, int64_t *out, void *stream);
 
-/* Which representations currently hold the set (a mask of GI_REP_*). */
+/* Which representations currently hold the set (a mask of GI_REP_*).
+ * Errors: GI_ERR_INVALID_ARG (NULL). */
 int gi_vset_reps(const gi_vset *s, uint32_t *reps);
 
-/* Make the sparse representation valid (bitmap/bool -> ids, ascending order). */
+/* Make the sparse representation valid (bitmap/bool -> ids, ascending order).
+ * Errors: GI_ERR_INVALID_ARG (NULL), GI_ERR_OOM, GI_ERR_CUDA. */
 int gi_vset_to_sparse(gi_vset *s, void *stream);
 
-/* Make a dense representation valid: rep = GI_REP_BOOL or GI_REP_BITMAP. */
+/* Make a dense representation valid: rep = GI_REP_BOOL or GI_REP_BITMAP.
+ * Errors: GI_ERR_INVALID_ARG (NULL or another rep), GI_ERR_OOM, GI_ERR_CUDA. */
 int gi_vset_to_dense(gi_vset *s, uint32_t rep, void *stream);
 
 /*
@@ -153,7 +164,9 @@ int gi_vset_to_dense(gi_vset *s, uint32_t rep, void *stream);
  */
 int gi_vset_export(gi_vset *s, int32_t *dev_out, int64_t cap, int64_t *count, void *stream);
 
-/* Replace the members by k device-resident ids (each in [0,n); duplicates removed). */
+/* Replace the members by k device-resident ids (each in [0,n); duplicates removed).
+ * Syncs the stream.  Errors: GI_ERR_INVALID_ARG (NULL, k < 0 or an id out of
+ * range: the set is then left empty), GI_ERR_CUDA. */
 int gi_vset_import(gi_vset *s, const int32_t *dev_ids, int64_t k, void *stream);
 
 /* --------------------------------------------------------------- schedule -- */
@@ -217,7 +230,8 @@ typedef struct gi_schedule {
 
 /* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment (FVC when segmented), 256
  * threads, t_warp 32, t_cta 256, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 256,
- * not persistent, hot_cache 0. */
+ * not persistent, hot_cache 0.  Every driver rejects a schedule with a field out of
+ * range with GI_ERR_INVALID_ARG. */
 void gi_schedule_default(gi_schedule *s);
 
 /* ------------------------------------------------------------ edgeset apply -- */
@@ -284,7 +298,11 @@ typedef struct gi_trace {
  * bitvector frontier and early exit, DensePush, or a hybrid).  depth_dev[n]:
  * hops from src, -1 if unreached.  parent_dev[n] (may be NULL): the smallest-id
  * in-neighbour one level closer to src (parent[src] = src, -1 if unreached);
- * the rule makes parents identical under every schedule.
+ * the rule makes parents identical under every schedule.  Syncs the stream.
+ * Errors: GI_ERR_INVALID_ARG (NULL, src out of range, bad schedule),
+ * GI_ERR_UNSUPPORTED (DENSE_PULL without in-edges), GI_ERR_TIMEOUT (a level
+ * cap or bounded wait of the persistent / graph-driven modes), GI_ERR_OOM,
+ * GI_ERR_CUDA.
  */
 int gi_bfs(gi_graph *g, int32_t src, int32_t *depth_dev, int32_t *parent_dev, const gi_schedule *sched,
            gi_trace *trace, void *stream);
@@ -301,6 +319,8 @@ int gi_sssp(gi_graph *g, int32_t src, int32_t *dist_dev, const gi_schedule *sche
 /*
  * Connected components by synchronous min-label propagation (Sec. 7's CC):
  * label_dev[n] = smallest vertex id of v's component (symmetric graphs).
+ * Syncs the stream.  Errors: GI_ERR_INVALID_ARG, GI_ERR_UNSUPPORTED (DENSE_PULL
+ * without in-edges), GI_ERR_OOM, GI_ERR_CUDA.
  */
 int gi_cc(gi_graph *g, int32_t *label_dev, const gi_schedule *sched, gi_trace *trace, void *stream);
 
@@ -309,7 +329,9 @@ int gi_cc(gi_graph *g, int32_t *label_dev, const gi_schedule *sched, gi_trace *t
  * PR[v] = (1-d)/n + d * sum_{u in in(v)} PR[u]/outdeg(u) from PR = 1/n in FP32
  * (FP32 accumulation), then division by the FP64 sum of all ranks.
  * sched->direction: DENSE_PULL (default; segmented when num_segments > 1) or
- * DENSE_PUSH.  rank_dev[n] receives the normalised ranks.
+ * DENSE_PUSH.  rank_dev[n] receives the normalised ranks.  Syncs the stream.
+ * Errors: GI_ERR_INVALID_ARG (NULL, iters < 0, damping outside [0,1]),
+ * GI_ERR_UNSUPPORTED (pull without in-edges), GI_ERR_OOM, GI_ERR_CUDA.
  */
 int gi_pagerank(gi_graph *g, float damping, int32_t iters, float *rank_dev, const gi_schedule *sched,
                 void *stream);
@@ -353,6 +375,8 @@ int gi_pagerank_static(const int32_t *in_offsets, const int32_t *in_indices, con
  * those with |Delta| > eps*Rank stay active.  iters rounds, FP32.  rank_dev[n]
  * receives Rank (not normalised).  The edge traversal per round follows sched
  * (hybrid by default: DensePull when the active set is large, SparsePush else).
+ * Syncs the stream.  Errors: GI_ERR_INVALID_ARG (NULL, iters < 0, eps < 0),
+ * GI_ERR_UNSUPPORTED (DENSE_PULL without in-edges), GI_ERR_OOM, GI_ERR_CUDA.
  */
 int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t iters, float *rank_dev,
                       const gi_schedule *sched, gi_trace *trace, void *stream);
@@ -386,10 +410,11 @@ int gi_bc(gi_graph *g, int32_t src, double *dependency_dev, double *sigma_dev, i
  * float32 W1[64][16], b1[64], W2[64][64], b2[64], W3[3][64], b3[3] (host memory,
  * `count` = 5443 floats), plus feature normalisation mean[16] and inv_std[16].
  * Used by GI_DIR_LEARNED; until loaded, LEARNED falls back to the Beamer rule.
+ * Errors: GI_ERR_INVALID_ARG (NULL or count != 5443), GI_ERR_CUDA.
  */
 int gi_selector_load(const float *params, int32_t count, const float *mean, const float *inv_std);
 
-/* Number of parameters of the selector network (5443). */
+/* Number of parameters of the selector network (5443; never fails). */
 int gi_selector_num_params(void);
 
 /*
@@ -400,7 +425,9 @@ int gi_selector_num_params(void);
  * gi_mlp_loss_grad writes grad[5443] (overwritten) and loss[2] = {masked MSE
  * sum_{b,j} M (Y-T)^2 / sum M, sum M}.  gi_mlp_forward writes Y[B][3].
  * gi_mlp_adam applies one Adam step (Kingma & Ba) with step number t >= 1,
- * updating params and the moment vectors m, v in place.
+ * updating params and the moment vectors m, v in place.  Asynchronous on
+ * `stream`.  Errors: GI_ERR_INVALID_ARG (NULL, B < 1, t < 1), GI_ERR_OOM,
+ * GI_ERR_CUDA.
  */
 int gi_mlp_loss_grad(const float *params, const float *X, const float *T, const float *M, int64_t B, float *grad,
                      float *loss, void *stream);
@@ -416,6 +443,8 @@ int gi_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t t,
  * (host) receive the level's 16 selector features and times_ms[3*i..] (host)
  * the three durations in milliseconds; *levels the number of levels recorded.
  * Syncs the stream.  Needs the in-edges (symmetric graph or gi_load_csc).
+ * Errors: GI_ERR_INVALID_ARG (NULL, other kernel_id, src out of range, cap < 0),
+ * GI_ERR_UNSUPPORTED (no in-edges), GI_ERR_OOM, GI_ERR_CUDA.
  */
 int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, const gi_schedule *sched, int32_t cap,
                         float *features, float *times_ms, int32_t *levels, void *stream);
@@ -446,6 +475,8 @@ typedef struct gi_batch_opts {
                         /* < 0: no threshold, every frontier source relaxed each round)    */
 } gi_batch_opts;
 
+/* Defaults: cluster_size 4, clusters 0, HYBRID_PULL, alpha 14, beta 24, level_cap 0,
+ * levels NULL, sssp_delta 0 (never fails). */
 void gi_batch_opts_default(gi_batch_opts *o);
 
 /*
@@ -470,8 +501,10 @@ int gi_batch_run(gi_graph *const *graphs, int32_t n_graphs, const int32_t *q_gra
  * on `stream` (no allocation, no host synchronisation: capturable);
  * gi_batch_plan_results copies per-query times and level counts (either may be
  * NULL) and reports GI_ERR_TIMEOUT if a query hit the level cap (syncs);
- * gi_batch_plan_free releases everything.  Outputs go to the out_dev pointers
- * given at creation, which must stay valid while the plan is used.
+ * gi_batch_plan_free releases everything (NULL is a no-op).  Outputs go to the
+ * out_dev pointers given at creation, which must stay valid while the plan is
+ * used.  Errors: as gi_batch_run (create), GI_ERR_INVALID_ARG (NULL plan),
+ * GI_ERR_TIMEOUT and GI_ERR_CUDA (results).
  */
 typedef struct gi_batch_plan gi_batch_plan;
 int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, const int32_t *q_graph, const int32_t *q_src,
@@ -499,6 +532,9 @@ int gi_batch_plan_free(gi_batch_plan *p);
  * whose output differs from start's (integers bit-exact, ranks beyond 1e-4
  * relative) is rejected.  *best receives the fastest valid schedule, *best_ms
  * and *start_ms (may be NULL) its time and start's.  Syncs the stream.
+ * Errors: GI_ERR_INVALID_ARG (NULL, unknown algo, budget outside [1, 100000],
+ * src out of range, SSSP without weights), GI_ERR_OOM, GI_ERR_CUDA, or a
+ * driver's error for a candidate.
  */
 int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_schedule *start, int32_t budget, uint64_t seed,
                 gi_schedule *best, double *best_ms, double *start_ms, void *stream);
@@ -518,14 +554,15 @@ int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_schedule *start
 #define GI_KCLASS_OTHER_PULL 5 /* other tiled pulls (sum, probe, segments)                 */
 #define GI_KCLASS_BATCH 6      /* the batched persistent engine                            */
 
-/* Turn per-launch event timing on (1) or off (0); counting is always on. */
+/* Turn per-launch event timing on (1) or off (0); counting is always on (never fails). */
 int gi_stats_enable(int timing_on);
-/* Zero the launch counter and drop recorded timings. */
+/* Zero the launch counter and drop recorded timings (never fails). */
 int gi_stats_reset(void);
 /*
  * Launches since the last reset (*launches), and for kernel class `kclass`
  * (-1 = all timed classes) the number of timed launches and their summed
- * device time in milliseconds.  Waits for the recorded events.
+ * device time in milliseconds.  Waits for the recorded events.  Errors:
+ * GI_ERR_INVALID_ARG (unknown class), GI_ERR_CUDA.
  */
 int gi_stats_read(int32_t kclass, int64_t *launches, int64_t *timed_launches, double *timed_ms);
 
