@@ -86,7 +86,7 @@ int gi_graph_info(const gi_graph *g, int64_t *n, int64_t *m, int32_t *max_deg);
  * The hot-source set of the on-chip pull (gi_schedule.hot_cache), built on
  * first use from the in-edges (this call builds it, syncing `stream`): *k
  * sources, those of out-degree >= *min_deg, where min_deg is the smallest
- * threshold with at most 40,960 sources (k = 0, min_deg = 0 for a graph
+ * threshold with at most 24,576 sources (k = 0, min_deg = 0 for a graph
  * without arcs); their slots follow descending degree.  Errors:
  * GI_ERR_UNSUPPORTED without in-edges, GI_ERR_OOM.
  */
@@ -218,7 +218,7 @@ typedef struct gi_schedule {
                         /* trace: level count only.  0 = one host-driven round per level. */
   int32_t hot_cache;    /* PageRank / PageRankDelta / CC / SSSP DensePull over the whole */
                         /* graph (CC and SSSP: their driver rounds; always form 2):    */
-                        /* the values of the (up to 40,960) highest-out-degree sources   */
+                        /* the values of the (up to 24,576) highest-out-degree sources   */
                         /* are read from on-chip memory instead of one L2 sector per     */
                         /* arc (the GPU form of the cache partitioning of Sec. 2).       */
                         /* 1 = in shared memory, one persistent block per SM (tiles of   */

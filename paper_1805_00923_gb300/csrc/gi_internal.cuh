@@ -116,7 +116,7 @@ struct Segments {
 // in vertex-id order; `idx` is the in-edge column array with each hot source
 // u replaced by ~slot(u) (negative), so a pull kernel that holds the hot
 // sources' values in shared memory reads them there without a lookup.
-constexpr int kHotMax = 40960;  // 160 KB of fp32 values per block
+constexpr int kHotMax = 24576;  // 96 KB of 4-byte values (fits beside the pull's staging in L1)
 struct HotSet {
   bool built = false;
   int32_t k = 0;              // hot sources (0: the cache does not apply)

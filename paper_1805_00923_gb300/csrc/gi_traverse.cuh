@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__r
 
 // Hot-source pull (GPU form of the cache partitioning of Sec. 2): one
 // persistent block of kGroups x 256 threads per SM first copies the values of
-// the graph's hot sources (the HotSet, up to 160 KB) into shared memory, then
+// the graph's hot sources (the HotSet, up to 96 KB) into shared memory, then
 // each 256-thread group reduces every (gridDim.x*kGroups)-th tile with the
 // same tile algorithm as k_pull_tiled, synchronised by its own named barrier.
 // Arcs from hot sources read shared memory instead of gathering a 32-byte L2

@@ -3,7 +3,7 @@
 The shared-memory source cache changes only where an arc's value is read, not
 the tiles or the order of any reduction, so PageRank and PageRankDelta must
 equal the plain tiled pull bit for bit, and the oracle within the fp32
-tolerance.  Cases: every source hot (n <= 40,960), only the high-degree head
+tolerance.  Cases: every source hot (n <= 24,576), only the high-degree head
 hot (R-MAT 18, 2-D grid with ties at the threshold degree), a hub row split
 over tiles, a graph without arcs (no hot set), a directed graph with separate
 in-edges, and every block tile size (mode 1 covers 512..2048 arcs and falls
@@ -18,7 +18,7 @@ from _graphs import adversarial, grid, rmat
 
 pytestmark = pytest.mark.gpu
 PR_TOL = 1e-4
-HOT_MAX = 40960
+HOT_MAX = 24576
 
 
 def _np(t):
@@ -48,7 +48,7 @@ CASES = {
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_hot_set_is_the_degree_head(gi, name):
-    """k sources of out-degree >= min_deg, min_deg the smallest threshold with <= 40,960 sources."""
+    """k sources of out-degree >= min_deg, min_deg the smallest threshold with <= 24,576 sources."""
     hg = CASES[name]()
     g = gi.Graph.from_host(hg)
     k, d = _hot_info(gi, g)
