@@ -175,9 +175,9 @@ class ClockSampler:
 
 
 def kernel_source_hash():
-    """Hash of the source text of the timed kernel (k_pull_tiled with its staging
-    helper and the PageRank edge function), so a recorded ncu traffic figure is
-    used only while that code is unchanged."""
+    """Hash of the code of the timed kernel (k_pull_tiled with its staging
+    helpers, the PageRank edge function and the hot-source cap), so a recorded
+    ncu traffic figure is used only while that code is unchanged."""
     with open(os.path.join(ROOT, "paper_1805_00923_gb300", "csrc", "gi_traverse.cuh")) as fh:
         src = fh.read()
     a = src.index("constexpr int kBatch = 8;")
@@ -186,6 +186,9 @@ def kernel_source_hash():
     d = src.index("};", c)
     # code only: comment lines and blank lines do not change the kernel
     code = [ln.split("//")[0].rstrip() for ln in (src[a:b] + src[c:d]).splitlines()]
+    # the hot-source cap (a constant of the shared header) changes what the kernel reads
+    with open(os.path.join(ROOT, "paper_1805_00923_gb300", "csrc", "gi_internal.cuh")) as fh:
+        code += [ln.split("//")[0].rstrip() for ln in fh if ln.startswith("constexpr int kHotMax")]
     return hashlib.sha256("\n".join(ln for ln in code if ln).encode()).hexdigest()[:16]
 
 
