@@ -629,8 +629,8 @@ def run_batch512(args):
         qs.append((k, int(gg.pick_sources(hgs[k], 1, seed=1000 + i)[0]), "bfs" if i % 2 == 0 else "sssp"))
     edges = sum(hgs[q[0]].m for q in qs)
     out = {}
-    for cs in (2, 4):
-        plan = gi.BatchPlan(gs, qs, opts=gi.batch_opts(cluster_size=cs, selector="learned"))
+    for cs, order in ((2, 1), (4, 1), (4, 0), (8, 1)):
+        plan = gi.BatchPlan(gs, qs, opts=gi.batch_opts(cluster_size=cs, selector="learned", order=order))
         plan.launch()
         plan.results()
         a, b = _events()
@@ -641,7 +641,7 @@ def run_batch512(args):
         _, ns, lev = plan.results()
         plan.free()
         ms = a.elapsed_time(b)
-        out[f"cluster{cs}"] = {"ms": ms, "gteps_nominal": edges / (ms * 1e-3) / 1e9,
+        out[f"cluster{cs}" + ("" if order == 1 else "_as_given")] = {"ms": ms, "gteps_nominal": edges / (ms * 1e-3) / 1e9,
                                "p50_ms": float(np.percentile(ns, 50) / 1e6),
                                "p99_ms": float(np.percentile(ns, 99) / 1e6)}
     best = max(out.values(), key=lambda r: r["gteps_nominal"])

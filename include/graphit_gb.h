@@ -473,10 +473,12 @@ typedef struct gi_batch_opts {
   int32_t *levels;      /* host, n_q entries or NULL: levels (BFS) / rounds (SSSP) run     */
   float sssp_delta;     /* SSSP threshold step = sssp_delta x mean arc weight (0: 2.0;     */
                         /* < 0: no threshold, every frontier source relaxed each round)    */
+  int32_t order;        /* order in which clusters claim queries: 0 = as given, 1 =        */
+                        /* largest graph first, SSSP before BFS (shorter makespan)          */
 } gi_batch_opts;
 
 /* Defaults: cluster_size 4, clusters 0, HYBRID_PULL, alpha 14, beta 24, level_cap 0,
- * levels NULL, sssp_delta 0 (never fails). */
+ * levels NULL, sssp_delta 0, order 1 (never fails). */
 void gi_batch_opts_default(gi_batch_opts *o);
 
 /*

@@ -51,7 +51,7 @@ class gi_trace(ctypes.Structure):
 
 class gi_batch_opts(ctypes.Structure):
     _fields_ = [("cluster_size", _i32), ("clusters", _i32), ("selector", _i32), ("alpha", _f32), ("beta", _f32),
-                ("level_cap", _i64), ("levels", _P(_i32)), ("sssp_delta", _f32)]
+                ("level_cap", _i64), ("levels", _P(_i32)), ("sssp_delta", _f32), ("order", _i32)]
 
 
 class gi_bfs_args(ctypes.Structure):

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <vector>
 
 #include "gi_features.cuh"
@@ -47,6 +48,7 @@ struct BatchGraph {
 struct BatchQuery {
   int32_t graph, src, algo;
   int32_t *out;
+  int32_t index;  // position in the caller's query arrays (times and levels are reported there)
 };
 
 struct ClusterWs {  // per-cluster working memory (device pointers)
@@ -493,8 +495,8 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
           theta = *(volatile int64_t *)(W.cnt + 12 + L % 4) + G.delta;  // nothing was near: move past the nearest
       }
     }
-    if (gtid == 0 && q_ns) q_ns[qi] = (int64_t)(global_ns() - t0);
-    if (gtid == 0 && q_levels) q_levels[qi] = levels;
+    if (gtid == 0 && q_ns) q_ns[Q.index] = (int64_t)(global_ns() - t0);
+    if (gtid == 0 && q_levels) q_levels[Q.index] = levels;
     if (!bar()) return;
   }
 }
@@ -554,6 +556,7 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
          "cluster_size must be 0 (whole GPU), 1, 2, 4 or 8");
   GI_ARG(o.selector == GI_DIR_SPARSE_PUSH || o.selector == GI_DIR_HYBRID_PULL || o.selector == GI_DIR_LEARNED,
          "selector must be GI_DIR_SPARSE_PUSH, GI_DIR_HYBRID_PULL or GI_DIR_LEARNED");
+  GI_ARG(o.order == 0 || o.order == 1, "order must be 0 (as given) or 1 (largest first)");
   std::vector<BatchGraph> hg(n_graphs);
   int64_t nmax = 1;
   for (int i = 0; i < n_graphs; ++i) {
@@ -578,7 +581,17 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
     if (q_algo[i] == GI_ALGO_BFS && o.selector != GI_DIR_SPARSE_PUSH)
       GI_ARG(g->has_csc, "pull levels need the in-edges (symmetric graph or gi_load_csc)");
     GI_ARG(out_dev[i] != nullptr, "NULL output");
-    hq[i] = BatchQuery{q_graph[i], q_src[i], q_algo[i], out_dev[i]};
+    hq[i] = BatchQuery{q_graph[i], q_src[i], q_algo[i], out_dev[i], i};
+  }
+  if (o.order == 1) {
+    // largest first (longest-processing-time order): vertex count is the proxy
+    // for both the work and, on road-like graphs, the number of levels; SSSP
+    // before BFS on the same graph; ties keep the caller's order
+    std::stable_sort(hq.begin(), hq.end(), [&](const BatchQuery &x, const BatchQuery &y) {
+      const int64_t nx = graphs[x.graph]->n, ny = graphs[y.graph]->n;
+      if (nx != ny) return nx > ny;
+      return x.algo == GI_ALGO_SSSP && y.algo != GI_ALGO_SSSP;
+    });
   }
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, sms = 0;
@@ -728,4 +741,5 @@ extern "C" void gi_batch_opts_default(gi_batch_opts *o) {
   o->level_cap = 0;
   o->levels = nullptr;
   o->sssp_delta = 0.0f;
+  o->order = 1;
 }

@@ -1,6 +1,7 @@
 """Batched persistent engine: every query's result equals the oracle's
 (bit-exact BFS depths and SSSP distances) for all cluster sizes and
 direction selectors; the level cap ends a run cleanly with GI_ERR_TIMEOUT."""
+import ctypes
 import os
 
 import numpy as np
@@ -204,3 +205,23 @@ def test_graph_driven_bfs_follows_new_in_edges(gi):
     assert np.array_equal(gi.bfs(g, 1, want_parent=False, sched=sc)[0].cpu().numpy(), want)
     g.load_in_edges(ip.copy(), ic.copy())
     assert np.array_equal(gi.bfs(g, 1, want_parent=False, sched=sc)[0].cpu().numpy(), want)
+
+
+def test_batch_claim_order_does_not_change_results(gi):
+    """Largest-first and as-given claim orders give the same per-query results,
+    the same BFS level counts (SSSP's asynchronous rounds vary with timing) and
+    a time for every query."""
+    hgs = _graphs()
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    qs = _queries(hgs, 40, seed=17)
+    levels = {}
+    for order in (0, 1):
+        lv = np.zeros(len(qs), np.int32)
+        opts = gi.batch_opts(cluster_size=2, order=order,
+                             levels=lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        res, ns = gi.batch_run(gs, qs, opts=opts)
+        _check(hgs, qs, res)
+        assert (ns > 0).all()
+        levels[order] = lv
+    bfs = np.array([q[2] == "bfs" for q in qs])
+    assert np.array_equal(levels[0][bfs], levels[1][bfs]) and (levels[1] > 0).all()
