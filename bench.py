@@ -305,6 +305,9 @@ def run_gi(args):
         edges += step(g, evs[k])
     stop.record()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     gi.stats_enable(False)
     launches, pr_launches, pr_ms = gi.stats_read("pr_pull")
     clocks = sampler.stop()
@@ -339,7 +342,11 @@ def run_gi(args):
         if k > 0:  # first one warms the allocator pool
             e2e_ms.append(dt)
             e2e_edges += sum(ed)
-    e2e_value = world * e2e_edges / (sum(e2e_ms) * 1e-3) / 1e9
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        from paper_1805_00923_gb300 import replicas
+        e2e_total = replicas.max_over_ranks(e2e_total, device="cuda")
+    e2e_value = world * e2e_edges / (e2e_total * 1e-3) / 1e9
 
     # learned vs heuristic direction selection on the same graph (BFS from 8 sources; untimed extra)
     selector = None
