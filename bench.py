@@ -326,12 +326,14 @@ def run_gi(args):
     out_h = [torch.empty(n, dtype=torch.float32).pin_memory(), torch.empty(n, dtype=torch.float32).pin_memory(),
              torch.empty(n, dtype=torch.int32).pin_memory()]
     h2d = 4 * (n + 1) + 4 * m
+    # the hot-source set is built while the indices arrive when a schedule uses it
+    want_hot = any(int(x.hot_cache) > 0 for x in (pr_s, hyb, cc_s))
     d2h = 3 * 4 * n
     e2e_ms, e2e_edges = [], 0.0
     for k in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ge = gi.Graph(rp_h.numpy(), col_h.numpy(), symmetric=True)
+        ge = gi.Graph(rp_h.numpy(), col_h.numpy(), symmetric=True, hot_sources=want_hot)
         ed = step(ge)
         out_h[0].copy_(rank_buf, non_blocking=True)
         out_h[1].copy_(prd_buf, non_blocking=True)

@@ -51,6 +51,7 @@ typedef struct gi_graph gi_graph;
 #define GI_DEV_PTRS 0x2u  /* input arrays are device memory (copied device-to-device)        */
 #define GI_SYMMETRIC 0x4u /* every arc (u,v) has its reverse: the in-edge view aliases CSR   */
 #define GI_VALIDATE 0x8u  /* check offsets/indices on the device; GI_ERR_BAD_GRAPH if bad    */
+#define GI_HOT_SOURCES 0x10u /* also build the hot-source set of the dense pull during the load */
 
 /*
  * Load a graph's out-edges in CSR form (the edgeset of Sec. 3; getOutNghs of the
@@ -60,6 +61,12 @@ typedef struct gi_graph gi_graph;
  * returns (the stream is synchronised before return).  Also builds out-degrees,
  * 1/out-degree and the pull tiles.  For GI_SYMMETRIC graphs the in-edge (CSC)
  * view is the CSR itself; otherwise call gi_load_csc before any pull traversal.
+ * The indices (and weights) are copied on an internal stream in pieces, so
+ * that the degree and tile work runs under the copy.  GI_HOT_SOURCES also
+ * builds the hot-source set of the on-chip pull (gi_schedule.hot_cache,
+ * otherwise built on first use) while the in-edges arrive, each piece
+ * remapped as soon as it has landed; it takes effect on the call that loads
+ * the in-edges (this one for GI_SYMMETRIC graphs, gi_load_csc otherwise).
  * Errors: GI_ERR_INVALID_ARG (n < 0, m < 0, NULL pointers with m > 0, both or
  * neither of HOST/DEV flags), GI_ERR_UNSUPPORTED (n or m >= 2^31),
  * GI_ERR_BAD_GRAPH (GI_VALIDATE and a check failed), GI_ERR_OOM, GI_ERR_CUDA.

@@ -67,10 +67,12 @@ class Graph:
     """A graph loaded into the library (gi_load_csr / gi_load_csc).
 
     row_ptr/col/wt are host numpy arrays (copied host-to-device) or CUDA
-    tensors (copied device-to-device), int32.
+    tensors (copied device-to-device), int32.  hot_sources=True builds the
+    hot-source set of the on-chip pull during the load (GI_HOT_SOURCES).
     """
 
-    def __init__(self, row_ptr, col, wt=None, symmetric=True, validate=False, in_edges=None, stream=None):
+    def __init__(self, row_ptr, col, wt=None, symmetric=True, validate=False, in_edges=None, stream=None,
+                 hot_sources=False):
         on_dev = isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda
         if not on_dev:
             row_ptr = np.ascontiguousarray(row_ptr, np.int32)
@@ -80,32 +82,34 @@ class Graph:
         n = int(row_ptr.shape[0]) - 1
         m = int(col.shape[0])
         flags = (L.GI_DEV_PTRS if on_dev else L.GI_HOST_PTRS) | (L.GI_SYMMETRIC if symmetric else 0) | \
-            (L.GI_VALIDATE if validate else 0)
+            (L.GI_VALIDATE if validate else 0) | (L.GI_HOT_SOURCES if hot_sources else 0)
         h = ctypes.c_void_p()
         check(_C.gi_load_csr(_vp(row_ptr), _vp(col), _vp(wt), n, m, flags, _stream(stream), ctypes.byref(h)))
         self.handle = h
         self._keep = None
         if in_edges is not None and not symmetric:
-            self.load_in_edges(*(list(in_edges) + [None])[:3], validate=validate, stream=stream)
+            self.load_in_edges(*(list(in_edges) + [None])[:3], validate=validate, stream=stream,
+                               hot_sources=hot_sources)
         n_, m_, md = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         check(_C.gi_graph_info(h, ctypes.byref(n_), ctypes.byref(m_), ctypes.byref(md)))
         self.n, self.m, self.max_deg = n_.value, m_.value, md.value
         self.weighted = wt is not None
 
     @classmethod
-    def from_host(cls, hg, validate=False, stream=None, in_edges=None):
+    def from_host(cls, hg, validate=False, stream=None, in_edges=None, hot_sources=False):
         """From a graphgen.HostGraph-like object (n, row_ptr, col, wt, symmetric)."""
         return cls(hg.row_ptr, hg.col, getattr(hg, "wt", None), symmetric=getattr(hg, "symmetric", True),
-                   validate=validate, in_edges=in_edges, stream=stream)
+                   validate=validate, in_edges=in_edges, stream=stream, hot_sources=hot_sources)
 
-    def load_in_edges(self, in_ptr, in_col, in_wt=None, validate=False, stream=None):
+    def load_in_edges(self, in_ptr, in_col, in_wt=None, validate=False, stream=None, hot_sources=False):
         """gi_load_csc: attach (or replace) the in-edges of a non-symmetric graph."""
         on_dev = isinstance(in_ptr, torch.Tensor) and in_ptr.is_cuda
         if not on_dev:
             in_ptr, in_col = np.ascontiguousarray(in_ptr, np.int32), np.ascontiguousarray(in_col, np.int32)
             in_wt = None if in_wt is None else np.ascontiguousarray(in_wt, np.int32)
         check(_C.gi_load_csc(self.handle, _vp(in_ptr), _vp(in_col), _vp(in_wt),
-                             (L.GI_DEV_PTRS if on_dev else L.GI_HOST_PTRS) | (L.GI_VALIDATE if validate else 0),
+                             (L.GI_DEV_PTRS if on_dev else L.GI_HOST_PTRS) | (L.GI_VALIDATE if validate else 0) |
+                             (L.GI_HOT_SOURCES if hot_sources else 0),
                              _stream(stream)))
 
     def hot_info(self, stream=None):

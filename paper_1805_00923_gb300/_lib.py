@@ -16,7 +16,7 @@ GI_ERR_UNSUPPORTED = -6
 ERR_NAMES = {0: "GI_OK", -1: "GI_ERR_INVALID_ARG", -2: "GI_ERR_BAD_GRAPH", -3: "GI_ERR_OOM",
              -4: "GI_ERR_CUDA", -5: "GI_ERR_TIMEOUT", -6: "GI_ERR_UNSUPPORTED"}
 
-GI_HOST_PTRS, GI_DEV_PTRS, GI_SYMMETRIC, GI_VALIDATE = 0x1, 0x2, 0x4, 0x8
+GI_HOST_PTRS, GI_DEV_PTRS, GI_SYMMETRIC, GI_VALIDATE, GI_HOT_SOURCES = 0x1, 0x2, 0x4, 0x8, 0x10
 GI_VSET_EMPTY, GI_VSET_ALL, GI_VSET_SINGLE = 0, 1, 2
 GI_REP_SPARSE, GI_REP_BOOL, GI_REP_BITMAP = 0x1, 0x2, 0x4
 GI_DIR_SPARSE_PUSH, GI_DIR_DENSE_PUSH, GI_DIR_DENSE_PULL = 0, 1, 2

@@ -322,6 +322,75 @@ static int copy_in(int32_t **dst, const int32_t *src, int64_t count, uint32_t fl
   return GI_OK;
 }
 
+// The index and weight arrays of a load are copied on a side stream in up to
+// kChunks pieces, one event per piece, so that the degree, tile and hot-set
+// work on the caller's stream runs under the copy (host-to-device copies are
+// bound by the host link, ~210 GB/s on a GB300 node, not by the SMs), and
+// the hot-set remap of each piece starts as soon as the piece has landed.
+struct SideCopy {
+  static constexpr int kChunks = 8;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t done[kChunks] = {}, wt_done = nullptr;
+  int64_t cut[kChunks + 1] = {};
+  int chunks = 0, waited = 0;
+
+  int start(gi_graph *g, Csr *c, const int32_t *idx, const int32_t *wt, uint32_t flags, cudaStream_t s) {
+    const int64_t m = g->m;
+    GI_TRY(dev_alloc_n(&c->idx, m, s));
+    if (wt) GI_TRY(dev_alloc_n(&c->wt, m, s));
+    if (m == 0) return GI_OK;
+    const cudaMemcpyKind kind = (flags & GI_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaEvent_t ready = nullptr;
+    GI_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ready, s);  // the allocations above, and any producer of device inputs
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
+    cudaEventDestroy(ready);
+    if (e != cudaSuccess) return cuda_fail(e, "side copy stream", __FILE__, __LINE__);
+    const int64_t want = m >> 22;  // pieces of at least 4M arcs
+    chunks = want < 1 ? 1 : (want > kChunks ? kChunks : (int)want);
+    for (int i = 0; i <= chunks; ++i) cut[i] = m * i / chunks;
+    for (int i = 0; i < chunks; ++i) {
+      GI_CUDA(cudaMemcpyAsync(c->idx + cut[i], idx + cut[i], sizeof(int32_t) * (size_t)(cut[i + 1] - cut[i]), kind,
+                              cs));
+      GI_CUDA(cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming));
+      GI_CUDA(cudaEventRecord(done[i], cs));
+    }
+    if (wt) {
+      GI_CUDA(cudaMemcpyAsync(c->wt, wt, sizeof(int32_t) * (size_t)m, kind, cs));
+      GI_CUDA(cudaEventCreateWithFlags(&wt_done, cudaEventDisableTiming));
+      GI_CUDA(cudaEventRecord(wt_done, cs));
+    }
+    return GI_OK;
+  }
+  // s waits for pieces [0, upto)
+  int wait(int upto, cudaStream_t s) {
+    for (; waited < upto && waited < chunks; ++waited) GI_CUDA(cudaStreamWaitEvent(s, done[waited], 0));
+    return GI_OK;
+  }
+  int wait_weights(cudaStream_t s) {
+    if (wt_done) GI_CUDA(cudaStreamWaitEvent(s, wt_done, 0));
+    return GI_OK;
+  }
+  int wait_all(cudaStream_t s) {
+    if (wt_done) GI_CUDA(cudaStreamWaitEvent(s, wt_done, 0));
+    return wait(chunks, s);
+  }
+  // the copies have finished (or never started) when this returns
+  void release() {
+    if (cs) cudaStreamSynchronize(cs);
+    for (auto &ev : done)
+      if (ev) cudaEventDestroy(ev);
+    if (wt_done) cudaEventDestroy(wt_done);
+    if (cs) cudaStreamDestroy(cs);
+    cs = nullptr;
+    wt_done = nullptr;
+    for (auto &ev : done) ev = nullptr;
+  }
+};
+
+static int hot_build_overlapped(gi_graph *g, SideCopy &sc, cudaStream_t s);
+
 static int validate_csr_dev(gi_graph *g, const Csr &c, cudaStream_t s) {
   GI_CUDA(cudaMemsetAsync(g->ctrl + kErr, 0, sizeof(int64_t), s));
   k_validate<<<grid_for(g, g->n, 256), 256, 0, s>>>(c.ptr, c.idx, g->n, g->m, g->ctrl + kErr);
@@ -448,6 +517,7 @@ extern "C" int gi_load_csr(const int32_t *offsets, const int32_t *indices, const
   g->m = m;
   g->symmetric = (flags & GI_SYMMETRIC) != 0;
   int st = GI_OK;
+  SideCopy side;
   do {
     if (cudaGetDevice(&g->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
@@ -463,9 +533,9 @@ extern "C" int gi_load_csr(const int32_t *offsets, const int32_t *indices, const
       break;
     }
     if ((st = copy_in(&g->out.ptr, offsets, n + 1, flags, s)) != GI_OK) break;
-    if ((st = copy_in(&g->out.idx, indices, m, flags, s)) != GI_OK) break;
-    if (weights && (st = copy_in(&g->out.wt, weights, m, flags, s)) != GI_OK) break;
-    if ((flags & GI_VALIDATE) && (st = validate_csr_dev(g, g->out, s)) != GI_OK) break;
+    if ((st = side.start(g, &g->out, indices, weights, flags, s)) != GI_OK) break;
+    if ((flags & GI_VALIDATE) && ((st = side.wait_all(s)) != GI_OK || (st = validate_csr_dev(g, g->out, s)) != GI_OK))
+      break;
     if ((st = dev_alloc_n(&g->out_deg, n, s)) != GI_OK) break;
     if ((st = dev_alloc_n(&g->inv_out_deg, n, s)) != GI_OK) break;
     if (cudaMemsetAsync(g->ctrl + kErr, 0, sizeof(int64_t), s) != cudaSuccess) { st = GI_ERR_CUDA; break; }
@@ -479,8 +549,15 @@ extern "C" int gi_load_csr(const int32_t *offsets, const int32_t *indices, const
       break;
     }
     g->max_deg = (int32_t)(md & 0xffffffff);
+    if (g->symmetric) {
+      g->in = g->out;
+      g->has_csc = true;
+      if ((st = use_tiles(g, 2048, s)) != GI_OK) break;
+      if ((flags & GI_HOT_SOURCES) && (st = hot_build_overlapped(g, side, s)) != GI_OK) break;
+    }
     if (weights && m > 0) {
       unsigned long long wsum = 0;
+      if ((st = side.wait_weights(s)) != GI_OK) break;
       if (cudaMemsetAsync(g->ctrl + kErr, 0, sizeof(int64_t), s) != cudaSuccess) { st = GI_ERR_CUDA; break; }
       k_sum_weights<<<grid_for(g, m, 256), 256, 0, s>>>(g->out.wt, m,
                                                         reinterpret_cast<unsigned long long *>(g->ctrl + kErr));
@@ -492,16 +569,13 @@ extern "C" int gi_load_csr(const int32_t *offsets, const int32_t *indices, const
       }
       g->wt_mean = (double)(long long)wsum / (double)m;
     }
-    if (g->symmetric) {
-      g->in = g->out;
-      g->has_csc = true;
-      if ((st = use_tiles(g, 2048, s)) != GI_OK) break;
-    }
+    if ((st = side.wait_all(s)) != GI_OK) break;
     if (cudaStreamSynchronize(s) != cudaSuccess) {
       st = cuda_fail(cudaGetLastError(), "load sync", __FILE__, __LINE__);
       break;
     }
   } while (0);
+  side.release();  // no copy may still write into memory that graph_release frees
   if (st != GI_OK) {
     cudaStreamSynchronize(s);
     graph_release(g, s);
@@ -528,13 +602,19 @@ extern "C" int gi_load_csc(gi_graph *g, const int32_t *in_offsets, const int32_t
     g->has_csc = false;
   }
   GI_TRY(copy_in(&g->in.ptr, in_offsets, g->n + 1, flags, s));
-  GI_TRY(copy_in(&g->in.idx, in_indices, g->m, flags, s));
-  if (in_weights) GI_TRY(copy_in(&g->in.wt, in_weights, g->m, flags, s));
-  if (flags & GI_VALIDATE) GI_TRY(validate_csr_dev(g, g->in, s));
-  g->has_csc = true;
-  GI_TRY(use_tiles(g, 2048, s));
-  GI_CUDA(cudaStreamSynchronize(s));
-  return GI_OK;
+  SideCopy side;
+  int st = side.start(g, &g->in, in_indices, in_weights, flags, s);
+  if (st == GI_OK && (flags & GI_VALIDATE) && (st = side.wait_all(s)) == GI_OK) st = validate_csr_dev(g, g->in, s);
+  if (st == GI_OK) {
+    g->has_csc = true;
+    st = use_tiles(g, 2048, s);
+  }
+  if (st == GI_OK && (flags & GI_HOT_SOURCES)) st = hot_build_overlapped(g, side, s);
+  if (st == GI_OK) st = side.wait_all(s);
+  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "load sync", __FILE__, __LINE__);
+  side.release();
+  return st;
 }
 
 extern "C" int gi_graph_free(gi_graph *g) {
@@ -774,77 +854,117 @@ __global__ void __launch_bounds__(1024) k_hot_pick(const int32_t *__restrict__ h
   }
 }
 
-// slot[v] and src[slot] for the hot vertices: bin start + arrival order in the bin
+// code[v] = ~slot for hot vertices (slot = bin start + arrival order in the
+// bin; src[slot] = v), v for the others
 __global__ void k_hot_slots(const int32_t *__restrict__ deg, int64_t n, int32_t min_deg,
-                            const int32_t *__restrict__ start, int32_t *fill, int32_t *slot, int32_t *src) {
+                            const int32_t *__restrict__ start, int32_t *fill, int32_t *code, int32_t *src) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t d = deg[v];
+    int32_t c = (int32_t)v;
     if (d >= min_deg) {
       const int32_t b = min(d, kHotBins - 1);
       const int32_t s = start[b] + atomicAdd(fill + b, 1);
-      slot[v] = s;
       src[s] = (int32_t)v;
+      c = ~s;
     }
+    code[v] = c;
   }
 }
 
-__global__ void k_hot_remap(const int32_t *__restrict__ idx, int64_t m, const int32_t *__restrict__ deg,
-                            int32_t min_deg, const int32_t *__restrict__ slot, int32_t *hidx) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = idx[e];
-    hidx[e] = deg[u] >= min_deg ? ~slot[u] : u;
+// the in-edge sources with hot ones replaced by ~slot: one gather per arc
+__global__ void k_hot_remap(const int32_t *__restrict__ idx, int64_t m, const int32_t *__restrict__ code,
+                            int32_t *hidx) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    hidx[e] = __ldg(code + idx[e]);
+}
+
+// Threshold, slots and code[] (in the workspace) of the hot set; h.src,
+// h.vals and h.idx are allocated, h.idx not yet written (hot_remap).
+static int hot_select(gi_graph *g, HotSet &h, cudaStream_t s) {
+  const int64_t n = g->n, m = g->m;
+  if (n == 0 || m == 0 || !g->has_csc) return GI_OK;
+  // hist[kHotBins] | start[kHotBins] | fill[kHotBins] | {threshold, count}
+  int32_t *hist = nullptr;
+  int st = dev_alloc_n(&hist, 3 * kHotBins + 2, s);
+  int32_t *start = hist + kHotBins, *fill = hist + 2 * kHotBins, *pick_out = hist + 3 * kHotBins;
+  if (st == GI_OK && cudaMemsetAsync(hist, 0, sizeof(int32_t) * (3 * kHotBins + 2), s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "hot histogram", __FILE__, __LINE__);
+  if (st == GI_OK) {
+    k_hot_hist<<<grid_for(g, n, 256, 2), 256, 0, s>>>(g->out_deg, n, hist);
+    k_hot_pick<<<1, 1024, 0, s>>>(hist, kHotMax, start, pick_out);
+    st = launch_status(2);
   }
+  int32_t pick[2] = {kHotBins, 0};
+  if (st == GI_OK && (cudaMemcpyAsync(pick, pick_out, sizeof(pick), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                      cudaStreamSynchronize(s) != cudaSuccess))
+    st = cuda_fail(cudaGetLastError(), "hot threshold", __FILE__, __LINE__);
+  h.min_deg = pick[0];
+  h.k = pick[1];
+  if (st == GI_OK && h.k > 0) {
+    const int k4 = (h.k + 3) & ~3;
+    st = dev_alloc_n(&h.src, h.k, s);
+    if (st == GI_OK) st = dev_alloc_n(&h.vals, k4, s);
+    if (st == GI_OK) st = dev_alloc_n(&h.idx, m, s);
+    if (st == GI_OK && cudaMemsetAsync(h.vals, 0, sizeof(float) * k4, s) != cudaSuccess)
+      st = cuda_fail(cudaGetLastError(), "hot values", __FILE__, __LINE__);
+    if (st == GI_OK) {
+      k_hot_slots<<<grid_for(g, n, 256), 256, 0, s>>>(g->out_deg, n, h.min_deg, start, fill, g->ws->tmp_i32, h.src);
+      st = launch_status(1);
+    }
+  }
+  dev_free(hist, s);
+  return st;
+}
+
+// h.idx[e0, e1) from the in-edge sources (needs hot_select's code[] intact)
+static int hot_remap(gi_graph *g, const HotSet &h, int64_t e0, int64_t e1, cudaStream_t s) {
+  if (h.k == 0 || e1 <= e0) return GI_OK;
+  k_hot_remap<<<grid_for(g, e1 - e0, 256), 256, 0, s>>>(g->in.idx + e0, e1 - e0, g->ws->tmp_i32, h.idx + e0);
+  return launch_status(1);
+}
+
+static void hot_discard(HotSet &h, cudaStream_t s) {
+  dev_free(h.src, s);
+  dev_free(h.vals, s);
+  dev_free(h.idx, s);
+  h = HotSet();
+}
+
+static void hot_commit(gi_graph *g, HotSet &h) {
+  h.built = true;
+  if (h.k == 0) h.min_deg = 0;
+  g->hot = h;
 }
 
 int hot_get(gi_graph *g, cudaStream_t s) {
   if (g->hot.built) return GI_OK;
   GI_TRY(ws_get(g, s));
   HotSet h;
-  const int64_t n = g->n, m = g->m;
-  int st = GI_OK;
-  if (n > 0 && m > 0 && g->has_csc) {
-    // hist[kHotBins] | start[kHotBins] | fill[kHotBins] | {threshold, count}
-    int32_t *hist = nullptr;
-    st = dev_alloc_n(&hist, 3 * kHotBins + 2, s);
-    int32_t *start = hist + kHotBins, *fill = hist + 2 * kHotBins, *pick_out = hist + 3 * kHotBins;
-    if (st == GI_OK && cudaMemsetAsync(hist, 0, sizeof(int32_t) * (3 * kHotBins + 2), s) != cudaSuccess)
-      st = cuda_fail(cudaGetLastError(), "hot histogram", __FILE__, __LINE__);
-    if (st == GI_OK) {
-      k_hot_hist<<<grid_for(g, n, 256, 2), 256, 0, s>>>(g->out_deg, n, hist);
-      k_hot_pick<<<1, 1024, 0, s>>>(hist, kHotMax, start, pick_out);
-      st = launch_status(2);
-    }
-    int32_t pick[2] = {kHotBins, 0};
-    if (st == GI_OK && (cudaMemcpyAsync(pick, pick_out, sizeof(pick), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                        cudaStreamSynchronize(s) != cudaSuccess))
-      st = cuda_fail(cudaGetLastError(), "hot threshold", __FILE__, __LINE__);
-    h.min_deg = pick[0];
-    h.k = pick[1];
-    if (st == GI_OK && h.k > 0) {
-      int32_t *slot = g->ws->tmp_i32;
-      const int k4 = (h.k + 3) & ~3;
-      st = dev_alloc_n(&h.src, h.k, s);
-      if (st == GI_OK) st = dev_alloc_n(&h.vals, k4, s);
-      if (st == GI_OK) st = dev_alloc_n(&h.idx, m, s);
-      if (st == GI_OK && cudaMemsetAsync(h.vals, 0, sizeof(float) * k4, s) != cudaSuccess)
-        st = cuda_fail(cudaGetLastError(), "hot values", __FILE__, __LINE__);
-      if (st == GI_OK) {
-        k_hot_slots<<<grid_for(g, n, 256), 256, 0, s>>>(g->out_deg, n, h.min_deg, start, fill, slot, h.src);
-        k_hot_remap<<<grid_for(g, m, 256), 256, 0, s>>>(g->in.idx, m, g->out_deg, h.min_deg, slot, h.idx);
-        st = launch_status(2);
-      }
-      if (st != GI_OK) {
-        dev_free(h.src, s);
-        dev_free(h.vals, s);
-        dev_free(h.idx, s);
-      }
-    }
-    dev_free(hist, s);
+  int st = hot_select(g, h, s);
+  if (st == GI_OK) st = hot_remap(g, h, 0, g->m, s);
+  if (st != GI_OK) {
+    hot_discard(h, s);
+    return st;
   }
-  if (st != GI_OK) return st;
-  h.built = true;
-  if (h.k == 0) h.min_deg = 0;
-  g->hot = h;
+  hot_commit(g, h);
+  return GI_OK;
+}
+
+// Hot set built during a load: select on the caller's stream while the
+// indices are still arriving, then remap each piece once it has landed.
+static int hot_build_overlapped(gi_graph *g, SideCopy &sc, cudaStream_t s) {
+  GI_TRY(ws_get(g, s));
+  HotSet h;
+  int st = hot_select(g, h, s);
+  for (int i = 0; st == GI_OK && i < sc.chunks; ++i) {
+    st = sc.wait(i + 1, s);
+    if (st == GI_OK) st = hot_remap(g, h, sc.cut[i], sc.cut[i + 1], s);
+  }
+  if (st != GI_OK) {
+    hot_discard(h, s);
+    return st;
+  }
+  hot_commit(g, h);
   return GI_OK;
 }
 

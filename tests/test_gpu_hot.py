@@ -158,3 +158,62 @@ def test_hot_cc_sssp_exact(gi, name, mode):
         tr = gi.Trace(1 << 14)
         assert np.array_equal(_np(gi.sssp(g, src, sched=sc, trace=tr)), want)
         assert np.array_equal(tr.as_dict()["frontier"], fs)
+
+
+LOAD_CASES = {
+    "rmat14_all_hot": lambda: rmat(14),
+    "rmat19_three_pieces": lambda: rmat(19),
+    "grid300_ties_weighted": lambda: grid(300, weights=True),
+    "hub_tail_split_row": lambda: adversarial("hub_tail"),
+    "isolated_no_arcs": lambda: adversarial("isolated"),
+}
+
+
+@pytest.mark.parametrize("source", ["host", "pinned", "device"])
+@pytest.mark.parametrize("validate", [False, True])
+@pytest.mark.parametrize("name", list(LOAD_CASES))
+def test_hot_set_built_during_load(gi, name, validate, source):
+    """GI_HOT_SOURCES: the hot set remapped piece by piece while the indices
+    arrive equals the one built on first use (same threshold and count, and
+    the hot pulls give the plain pull's ranks bit for bit)."""
+    import torch
+    hg = LOAD_CASES[name]()
+    wt = getattr(hg, "wt", None)
+    arrs = [hg.row_ptr, hg.col] + ([wt] if wt is not None else [])
+    if source == "pinned":
+        arrs = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in arrs]
+    elif source == "device":
+        arrs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+    g_load = gi.Graph(arrs[0], arrs[1], arrs[2] if wt is not None else None, symmetric=True, validate=validate,
+                      hot_sources=True)
+    g_lazy = gi.Graph.from_host(hg)
+    assert g_load.hot_info() == g_lazy.hot_info()
+    plain = _np(gi.pagerank(g_lazy, 0.85, 10, sched=gi.schedule("dense_pull")))
+    for mode in (1, 2):
+        for g in (g_load, g_lazy):
+            hot = _np(gi.pagerank(g, 0.85, 10, sched=gi.schedule("dense_pull", hot_cache=mode)))
+            assert np.array_equal(plain.view(np.uint32), hot.view(np.uint32))
+    if wt is not None and hg.m:
+        src = int(gg.pick_sources(hg, 1, seed=5)[0])
+        want, _ = oracle.sssp(hg, src)
+        assert np.array_equal(_np(gi.sssp(g_load, src, sched=gi.schedule("hybrid_pull", hot_cache=2))), want)
+    g_load.free()
+    g_lazy.free()
+
+
+def test_hot_set_built_with_separate_in_edges(gi):
+    """On a directed graph the flag acts on the call that loads the in-edges."""
+    rng = np.random.default_rng(21)
+    n = 70_000
+    src = np.concatenate([rng.integers(0, 40, 300_000), rng.integers(0, n, 9_000_000)]).astype(np.int32)
+    dst = rng.integers(0, n, src.size).astype(np.int32)
+    row_ptr, col = gg.csr_from_edges(n, src, dst, False)
+    hg = gg.HostGraph(n, row_ptr, col, None, False, "directed_two_pieces", {})
+    in_ptr, in_col, _ = gg.transpose(hg)
+    g_load = gi.Graph(hg.row_ptr, hg.col, symmetric=False, in_edges=(in_ptr, in_col, None), hot_sources=True)
+    g_lazy = gi.Graph(hg.row_ptr, hg.col, symmetric=False, in_edges=(in_ptr, in_col, None))
+    assert g_load.hot_info() == g_lazy.hot_info() and g_load.hot_info()[0] > 0
+    plain = _np(gi.pagerank(g_lazy, 0.85, 20, sched=gi.schedule("dense_pull")))
+    hot = _np(gi.pagerank(g_load, 0.85, 20, sched=gi.schedule("dense_pull", hot_cache=2)))
+    assert np.array_equal(plain.view(np.uint32), hot.view(np.uint32))
+    assert _max_rel(hot, oracle.pagerank(hg, 0.85, 20, in_edges=(in_ptr, in_col))) < PR_TOL
