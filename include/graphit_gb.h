@@ -224,11 +224,12 @@ typedef struct gi_schedule {
                         /* level), built on first use and cached per graph and schedule; */
                         /* trace: level count only.  0 = one host-driven round per level. */
   int32_t hot_cache;    /* PageRank / PageRankDelta / CC / SSSP DensePull over the whole */
-                        /* graph (CC and SSSP: their driver rounds; always form 2):    */
+                        /* graph (CC and SSSP: their driver rounds):                   */
                         /* the values of the (up to 24,576) highest-out-degree sources   */
                         /* are read from on-chip memory instead of one L2 sector per     */
                         /* arc (the GPU form of the cache partitioning of Sec. 2).       */
-                        /* 1 = in shared memory, one persistent block per SM (tiles of   */
+                        /* 1 = the hottest (up to 8,192) in shared memory, the rest in   */
+                        /* L1, two persistent blocks per SM (tiles of                    */
                         /* 512..2048 arcs); 2 = a dense array cached in L1 (tiles of     */
                         /* 512..8192 arcs); 0 = off.  Results are bit-identical to 0.    */
                         /* Ignored elsewhere.  Built once per graph (4m bytes).          */

@@ -113,10 +113,16 @@ struct Segments {
 
 // Hot-source cache for dense pulls over the whole graph: the sources of
 // highest out-degree (out_deg >= min_deg, at most kHotMax of them) get slots
-// in vertex-id order; `idx` is the in-edge column array with each hot source
-// u replaced by ~slot(u) (negative), so a pull kernel that holds the hot
-// sources' values in shared memory reads them there without a lookup.
+// in descending degree; `idx` is the in-edge column array with each hot
+// source u replaced by ~slot(u) (negative), so a pull kernel that holds the
+// hot sources' values on chip reads them there without a lookup.
 constexpr int kHotMax = 24576;  // 96 KB of 4-byte values (fits beside the pull's staging in L1)
+// cap on the slots the shared-memory form keeps in shared memory (the rest
+// of the hot set is read through L1).  A larger shared-memory share shrinks
+// L1, which the cold gathers need for their misses in flight: on R-MAT 22
+// (2048-arc tiles) caps of 8,192 / 12,288 / 14,544 slots ran 0.479 / 0.649 /
+// 0.635 ms per PageRank pull.
+constexpr int kHotSmemSlots = 8192;
 struct HotSet {
   bool built = false;
   int32_t k = 0;              // hot sources (0: the cache does not apply)

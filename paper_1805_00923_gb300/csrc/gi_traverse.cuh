@@ -337,11 +337,13 @@ __device__ __forceinline__ int32_t ld_stream_i32(const int32_t *p) {
 //   kGatherPlain: op.edge_val(u, e) for sources u in F;
 //   kGatherHotSmem / kGatherHotL1: F is all vertices and the in-edge sources
 //   were remapped by the graph's HotSet; a negative entry ~s reads slot s of
-//   the hot sources' values -- the block's shared-memory copy (s_hot), or the
-//   dense global array hot (cached in L1; the other loads bypass L1 or are
-//   marked evict-first so they do not evict it).  An Op with a hot form
-//   exposes its per-source 4-byte values (hot_source()) and builds the arc
-//   value from one (from_src(value, e)).
+//   the hot sources' values.  kGatherHotL1 reads them from the dense global
+//   array hot_g (cached in L1; the other loads bypass L1 or are marked
+//   evict-first so they do not evict it).  kGatherHotSmem reads slots below
+//   k1 (the hottest, slots being in descending degree) from the block's
+//   shared-memory copy hot and the rest from hot_g as kGatherHotL1 does.  An
+//   Op with a hot form exposes its per-source 4-byte values (hot_source())
+//   and builds the arc value from one (from_src(value, e)).
 constexpr int kGatherPlain = 0, kGatherHotSmem = 1, kGatherHotL1 = 2;
 
 template <class Op>
@@ -351,19 +353,20 @@ template <class Op, int kMode>
 struct Gather {
   const Op &op;
   FSet F;
-  const float *hot;  // 4-byte slots: shared memory (kGatherHotSmem) or global (kGatherHotL1)
+  const float *hot_g;         // 4-byte slots in global memory (the hot modes)
+  const float *hot = nullptr; // kGatherHotSmem: slots [0, k1) in shared memory
+  int32_t k1 = 0;
   __device__ __forceinline__ int32_t src(const int32_t *p) const {
-    if constexpr (kMode == kGatherHotL1) return ld_stream_i32(p);
+    if constexpr (kMode != kGatherPlain) return ld_stream_i32(p);
     else return __ldg(p);
   }
   __device__ __forceinline__ typename Op::V hot_val(int32_t u, int32_t e) const {
-    if constexpr (kMode == kGatherHotSmem) {
-      return u < 0 ? hot[~u] : op.edge_val(u, e);
-    } else {
-      using S = hot_src_t<Op>;
-      const S sv = u < 0 ? ld_hot(reinterpret_cast<const S *>(hot) + ~u) : ld_cold(op.hot_source() + u);
-      return op.from_src(sv, e);
-    }
+    using S = hot_src_t<Op>;
+    S sv;
+    if (u >= 0) sv = ld_cold(op.hot_source() + u);
+    else if (kMode == kGatherHotSmem && ~u < k1) sv = reinterpret_cast<const S *>(hot)[~u];
+    else sv = ld_hot(reinterpret_cast<const S *>(hot_g) + ~u);
+    return op.from_src(sv, e);
   }
 };
 
@@ -531,44 +534,49 @@ __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__r
                                  BlockSync{});
 }
 
-// Hot-source pull (GPU form of the cache partitioning of Sec. 2): one
-// persistent block of kGroups x 256 threads per SM first copies the values of
-// the graph's hot sources (the HotSet, up to 96 KB) into shared memory, then
-// each 256-thread group reduces every (gridDim.x*kGroups)-th tile with the
-// same tile algorithm as k_pull_tiled, synchronised by its own named barrier.
-// Arcs from hot sources read shared memory instead of gathering a 32-byte L2
-// sector each.  The tiles and the order of every reduction are those of
-// k_pull_tiled, so the results are bit-identical to it.
+// Hot-source pull (GPU form of the cache partitioning of Sec. 2) with a
+// two-level cache: two persistent blocks of kGroups x 256 threads per SM
+// (the plain kernel's warp count) each copy the k1 hottest slots of the
+// HotSet (as many as fit beside the groups' staging areas) into shared
+// memory; the remaining hot slots are read through L1 from the dense hot
+// array and the cold sources from L2, as in the L1 form.  Each 256-thread
+// group reduces every (gridDim.x*kGroups)-th tile with the same tile
+// algorithm as k_pull_tiled, synchronised by its own named barrier, so the
+// tiles and the order of every reduction are those of k_pull_tiled and the
+// results are bit-identical to it.
 template <class Op, int kTE, int kGroups>
-__global__ void __launch_bounds__(256 * kGroups, 1) k_pull_hot(Op op, const int32_t *__restrict__ ptr,
+__global__ void __launch_bounds__(256 * kGroups, 2) k_pull_hot(Op op, const int32_t *__restrict__ ptr,
                                                                const int32_t *__restrict__ hidx,
                                                                const int4 *__restrict__ tiles, int32_t num_tiles,
-                                                               const float *__restrict__ hot_vals, int32_t hot_k4,
+                                                               const float *__restrict__ hot_vals, int32_t k1,
                                                                const uint32_t *__restrict__ to, OutSet out,
-                                                               float *partial) {
-  static_assert(std::is_same<typename Op::V, float>::value, "hot pull gathers fp32 values");
+                                                               typename Op::V *partial) {
+  using V = typename Op::V;
+  static_assert(sizeof(hot_src_t<Op>) == 4, "hot slots are 4-byte");
   static_assert(kGroups >= 1 && kGroups <= 4, "named barriers 1..kGroups");
   constexpr int kB = 256;
-  constexpr size_t kStage = (pull_stage_bytes<float>(kTE) + 15) & ~(size_t)15;
+  constexpr size_t kStage = (pull_stage_bytes<V>(kTE) + 15) & ~(size_t)15;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *s_hot = reinterpret_cast<float *>(smem_raw);
   {
     const float4 *src4 = reinterpret_cast<const float4 *>(hot_vals);
     float4 *dst4 = reinterpret_cast<float4 *>(s_hot);
-    for (int i = threadIdx.x; i < hot_k4 / 4; i += blockDim.x) dst4[i] = __ldg(src4 + i);
+    for (int i = threadIdx.x; i < k1 / 4; i += blockDim.x) dst4[i] = __ldg(src4 + i);
   }
   __syncthreads();
-  __shared__ float s_red[kGroups][kB / 32];
+  __shared__ V s_red[kGroups][kB / 32];
   const int grp = threadIdx.x / kB;
-  unsigned char *stage = smem_raw + sizeof(float) * (size_t)hot_k4 + kStage * grp;
-  float *vals = reinterpret_cast<float *>(stage);
-  int32_t *rp = reinterpret_cast<int32_t *>(stage + sizeof(float) * (size_t)(kTE + kTE / kLongRowDiv));
-  const Gather<Op, kGatherHotSmem> G{op, FSet(), s_hot};
+  unsigned char *stage = smem_raw + sizeof(float) * (size_t)k1 + kStage * grp;
+  V *vals = reinterpret_cast<V *>(stage);
+  int32_t *rp = reinterpret_cast<int32_t *>(stage + sizeof(V) * (size_t)(kTE + kTE / kLongRowDiv));
+  Gather<Op, kGatherHotSmem> G{op, FSet(), hot_vals};
+  G.hot = s_hot;
+  G.k1 = k1;
   const GroupSync<kB> sync{1 + grp};
   const int32_t stride = (int32_t)gridDim.x * kGroups;
   for (int32_t t = (int32_t)blockIdx.x * kGroups + grp; t < num_tiles; t += stride)
     pull_tile<Op, kB, kGatherHotSmem>(G, tiles[t], t, ptr, hidx, to, out, partial, vals, rp, s_red[grp],
-                            (int)(threadIdx.x % kB), sync);
+                                      (int)(threadIdx.x % kB), sync);
 }
 
 // hot_vals[s] = values[src[s]]: the hot sources' values for one launch
@@ -1252,15 +1260,28 @@ struct HotGatherable<Op, std::void_t<decltype(std::declval<const Op &>().hot_sou
 template <class Op, int kTE>
 int launch_pull_hot_te(gi_graph *g, const Op &op, const TileSet &ts, const uint32_t *to, const OutSet &out,
                        cudaStream_t s) {
-  constexpr int kGroups = 4;
+  using V = typename Op::V;
+  constexpr int kGroups = 4, kBlocksPerSm = 2;
+  auto kern = k_pull_hot<Op, kTE, kGroups>;
   const int32_t k4 = (g->hot.k + 3) & ~3;
-  const size_t stage = (pull_stage_bytes<float>(kTE) + 15) & ~(size_t)15;
-  const size_t smem = sizeof(float) * (size_t)k4 + stage * kGroups;
-  GI_CUDA(cudaFuncSetAttribute(k_pull_hot<Op, kTE, kGroups>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int grid = ts.num_tiles < g->num_sms * kGroups ? div_up(ts.num_tiles, kGroups) : g->num_sms;
-  k_pull_hot<Op, kTE, kGroups><<<grid, 256 * kGroups, smem, s>>>(op, g->in.ptr, g->hot.idx, ts.tiles, ts.num_tiles,
-                                                                 g->hot.vals, k4, to, out,
-                                                                 reinterpret_cast<float *>(ts.partial));
+  const size_t stage = (pull_stage_bytes<V>(kTE) + 15) & ~(size_t)15;
+  // shared memory for two blocks per SM: the per-SM capacity less the 1 KB
+  // the runtime reserves per block and the kernel's static arrays
+  int per_sm = 0, optin = 0;
+  cudaFuncAttributes fa;
+  GI_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, g->device));
+  GI_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
+  GI_CUDA(cudaFuncGetAttributes(&fa, kern));
+  const int64_t budget = std::min<int64_t>(optin, per_sm / kBlocksPerSm - 1024) - (int64_t)fa.sharedSizeBytes;
+  int64_t room = (budget - (int64_t)stage * kGroups) / (int64_t)sizeof(float);
+  room = room < 0 ? 0 : (room & ~(int64_t)3);
+  const int32_t k1 = (int32_t)std::min<int64_t>({(int64_t)k4, room, (int64_t)kHotSmemSlots});
+  const size_t smem = sizeof(float) * (size_t)k1 + stage * kGroups;
+  GI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t full = (int64_t)g->num_sms * kBlocksPerSm;
+  const int grid = (int)std::min<int64_t>(full, div_up(ts.num_tiles, kGroups));
+  kern<<<grid, 256 * kGroups, smem, s>>>(op, g->in.ptr, g->hot.idx, ts.tiles, ts.num_tiles, g->hot.vals, k1, to, out,
+                                         reinterpret_cast<V *>(ts.partial));
   return GI_OK;
 }
 
@@ -1286,9 +1307,8 @@ int launch_pull_hot(gi_graph *g, const Op &op, const TileSet &ts, const uint32_t
                     cudaStream_t s, int kclass, int hot_mode, bool *done) {
   *done = false;
   const int te = ts.tile_edges;
-  // the shared-memory form holds fp32 values and block tiles of <= 2048 arcs
-  constexpr bool kSmemOk = std::is_same<typename Op::V, float>::value && std::is_same<hot_src_t<Op>, float>::value;
-  if (ts.num_tiles == 0 || te < 512 || (hot_mode == 1 && kSmemOk && te > 2048)) return GI_OK;
+  // the shared-memory form takes block tiles of <= 2048 arcs
+  if (ts.num_tiles == 0 || te < 512 || (hot_mode == 1 && te > 2048)) return GI_OK;
   GI_TRY(hot_get(g, s));
   if (g->hot.k == 0) return GI_OK;
   const int tok = timing_begin(kclass, s);
@@ -1298,13 +1318,11 @@ int launch_pull_hot(gi_graph *g, const Op &op, const TileSet &ts, const uint32_t
   GI_LAUNCH_CHECK();
   const float *hv = g->hot.vals;
   const int32_t *hp = g->in.ptr, *hi = g->hot.idx;
-  if (kSmemOk && hot_mode == 1) {
-    if constexpr (kSmemOk) {
-      switch (te) {
-        case 512: GI_TRY((launch_pull_hot_te<Op, 512>(g, op, ts, to, out, s))); break;
-        case 1024: GI_TRY((launch_pull_hot_te<Op, 1024>(g, op, ts, to, out, s))); break;
-        default: GI_TRY((launch_pull_hot_te<Op, 2048>(g, op, ts, to, out, s))); break;
-      }
+  if (hot_mode == 1) {
+    switch (te) {
+      case 512: GI_TRY((launch_pull_hot_te<Op, 512>(g, op, ts, to, out, s))); break;
+      case 1024: GI_TRY((launch_pull_hot_te<Op, 1024>(g, op, ts, to, out, s))); break;
+      default: GI_TRY((launch_pull_hot_te<Op, 2048>(g, op, ts, to, out, s))); break;
     }
   } else {
     switch (te) {

@@ -1,4 +1,4 @@
-"""Hot-source DensePull (gi_schedule.hot_cache = 1: shared memory, 2: L1 array).
+"""Hot-source DensePull (gi_schedule.hot_cache = 1: shared memory + L1, 2: L1 array).
 
 The shared-memory source cache changes only where an arc's value is read, not
 the tiles or the order of any reduction, so PageRank and PageRankDelta must
@@ -143,8 +143,8 @@ WEIGHTED = {
 @pytest.mark.parametrize("name", list(WEIGHTED))
 def test_hot_cc_sssp_exact(gi, name, mode):
     """Min-label pulls (CC, SSSP) read snap[u] of hot sources from the hot
-    array (both modes run the L1 form for integer values): labels, distances
-    and per-round frontiers equal the oracle's."""
+    set (shared memory and L1 in mode 1, L1 in mode 2): labels, distances and
+    per-round frontiers equal the oracle's."""
     hg = WEIGHTED[name]()
     g = gi.Graph.from_host(hg)
     for direction in ("dense_pull", "hybrid_pull"):
