@@ -46,7 +46,8 @@ def parse():
     p.add_argument("--tune-budget", type=int, default=12, help="autotuner trials per algorithm (untimed)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the untimed autotuning and direction comparison (profiling runs)")
-    p.add_argument("--workload", choices=["rmat22", "rmat24_bfs_sssp", "grid4096", "batch512", "bc"], default="rmat22",
+    p.add_argument("--workload", choices=["rmat22", "rmat24_bfs_sssp", "rmat24_levels", "grid4096", "batch512", "bc"],
+                   default="rmat22",
                    help="rmat22 (default): the timed PR+PRD+CC step; the others measure the remaining "
                         "configurations and print their own JSON line")
     p.add_argument("--sources", type=int, default=16, help="sources per graph for the BFS/SSSP workloads")
@@ -271,18 +272,25 @@ def run_gi(args):
         t = tr.as_dict()
         return int(sum(m if d == gi.GI_DIR_DENSE_PULL else e for d, e in zip(t["direction"], t["edges"])))
 
-    def step(graph, ev=None):
+    def step(graph, ev=None, after=None):
+        """One pass of the workload; after(i), if given, runs once algorithm i is enqueued."""
         if ev:
             ev[0].record()
         gi.pagerank(graph, DAMPING, PR_ITERS, sched=pr_s, out=rank_buf)
         if ev:
             ev[1].record()
+        if after:
+            after(0)
         gi.pagerank_delta(graph, DAMPING, PRD_EPS, PRD_ITERS, sched=hyb, trace=tr_p, out=prd_buf)
         if ev:
             ev[2].record()
+        if after:
+            after(1)
         gi.cc(graph, sched=cc_s, trace=tr_c, out=lab_buf)
         if ev:
             ev[3].record()
+        if after:
+            after(2)
         return PR_ITERS * m, traversed(tr_p), traversed(tr_c)
 
     for _ in range(args.warmup):
@@ -329,15 +337,25 @@ def run_gi(args):
     # the hot-source set is built while the indices arrive when a schedule uses it
     want_hot = any(int(x.hot_cache) > 0 for x in (pr_s, hyb, cc_s))
     d2h = 3 * 4 * n
+    # each result vector goes back on a side stream as soon as its algorithm
+    # is done, under the next algorithm's kernels
+    side = torch.cuda.Stream()
+    res_dev = (rank_buf, prd_buf, lab_buf)
+
+    def fetch(i):
+        done = torch.cuda.Event()
+        done.record()
+        side.wait_event(done)
+        with torch.cuda.stream(side):
+            out_h[i].copy_(res_dev[i], non_blocking=True)
+
     e2e_ms, e2e_edges = [], 0.0
     for k in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ge = gi.Graph(rp_h.numpy(), col_h.numpy(), symmetric=True, hot_sources=want_hot)
-        ed = step(ge)
-        out_h[0].copy_(rank_buf, non_blocking=True)
-        out_h[1].copy_(prd_buf, non_blocking=True)
-        out_h[2].copy_(lab_buf, non_blocking=True)
+        ed = step(ge, after=fetch)
+        torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
         ge.free()
         dt = (time.perf_counter() - t0) * 1e3
@@ -548,6 +566,102 @@ def run_rmat24(args):
     return 0
 
 
+def _bfs_level_bytes(depth, col, row, row_ptr, deg, levels):
+    """Per BFS level d (frontier = depth d): |F|, m_f, |F_next|, n_u and the
+    arcs an early-exit pull scans (E_scanned: for each vertex not yet reached,
+    its in-arcs up to and including the first one from the frontier, all of
+    them if none), from the run's own depths; measurement plumbing in torch."""
+    import torch
+    m = col.numel()
+    local = torch.arange(m, device=col.device, dtype=torch.int32) - row_ptr[row.long()]  # position in the row
+    dsrc = depth[col.long()]
+    out = []
+    for d in range(levels):
+        front = depth == d
+        unv = (depth > d) | (depth < 0)
+        first = deg.clone()
+        hit = dsrc == d
+        first.scatter_reduce_(0, row[hit].long(), local[hit] + 1, reduce="amin", include_self=True)
+        out.append(dict(frontier=int(front.sum()), m_f=int(deg[front].sum()), next=int((depth == d + 1).sum()),
+                        n_u=int(unv.sum()), e_scanned=int(first[unv].sum())))
+    return out
+
+
+def run_levels(args):
+    """R-MAT scale 24: every BFS level and SSSP round from one source, each of
+    SparsePush / DensePush / DensePull timed alone from the same state
+    (gi_selector_profile), with the algorithmic bytes of that direction at that
+    level and the bandwidth they imply against the measured copy peak."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import paper_1805_00923_gb300 as gi
+    from paper_1805_00923_gb300 import selector as sel
+    torch.cuda.set_device(0)
+    hg = gg.rmat_graph(24, seed=1, weights=(1, 1000))
+    n, m = hg.n, hg.m
+    g = gi.Graph.from_host(hg)
+    src = int(gg.pick_sources(hg, 1, seed=1)[0])
+    peak, peak_kind = measured_hbm()
+    deg = torch.from_numpy(np.diff(hg.row_ptr).astype(np.int32)).cuda()
+    col = torch.from_numpy(hg.col).cuda()
+    row_ptr = torch.from_numpy(hg.row_ptr).cuda()
+    row = torch.repeat_interleave(torch.arange(n, device="cuda", dtype=torch.int32), deg.long(), output_size=m)
+    names = ("sparse_push", "dense_push", "dense_pull")
+
+    def rows(t, bytes_of):
+        res = []
+        for i in range(t.shape[0]):
+            b = bytes_of(i)
+            r = {"level": i}
+            r.update(b["sizes"])
+            for j, nm in enumerate(names):
+                ms = float(t[i, j])
+                gbs = b[nm] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+                r[nm] = {"ms": ms, "bytes": b[nm], "gbs": gbs, "frac": gbs / peak}
+            res.append(r)
+        return res
+
+    depth, _ = gi.bfs(g, src, want_parent=False)
+    _, tb = sel.profile(g, gi.GI_K_BFS, src)
+    lv = _bfs_level_bytes(depth, col, row, row_ptr, deg, tb.shape[0])
+
+    def bfs_bytes(i):
+        x = lv[i]
+        push = 12 * x["frontier"] + 8 * x["m_f"] + 8 * x["next"]
+        pull = 4 * (x["n_u"] + 1) + 8 * x["e_scanned"] + n // 4 + 8 * x["next"]
+        return {"sizes": x, "sparse_push": push, "dense_push": push + n // 8, "dense_pull": pull}
+
+    tr = gi.Trace(1 << 14)
+    gi.sssp(g, src, trace=tr)
+    d = tr.as_dict()
+    _, ts = sel.profile(g, gi.GI_K_SSSP, src)
+
+    def sssp_bytes(i):
+        f, mf = int(d["frontier"][i]), int(d["edges"][i])
+        nxt = int(d["frontier"][i + 1]) if i + 1 < len(d["frontier"]) else 0
+        push = 12 * f + 12 * mf + 8 * nxt
+        pull = 4 * (n + 1) + 8 * m + 8 * mf + n // 4 + 4 * nxt
+        return {"sizes": {"frontier": f, "m_f": mf, "next": nxt}, "sparse_push": push, "dense_push": push + n // 8,
+                "dense_pull": pull}
+
+    bfs_rows = rows(tb, bfs_bytes)
+    sssp_rows = rows(ts[:len(d["frontier"])], sssp_bytes)
+
+    def best(rs):
+        return max((r[nm]["frac"], r["level"], nm) for r in rs for nm in names)
+
+    print(json.dumps({"metric": METRIC, "workload": "rmat24_levels", "n": n, "m": m, "source": src,
+                      "peak_gbs": peak, "peak_kind": peak_kind, "bfs_levels": bfs_rows, "sssp_rounds": sssp_rows,
+                      "best_frac": {"bfs": best(bfs_rows), "sssp": best(sssp_rows)},
+                      "bytes_model": {
+                          "sparse_push": "12|F| + 8 m_f + 8|F_next| (BFS; SSSP adds 4 m_f of weights)",
+                          "dense_push": "sparse_push + V/8 (bitmap scan)",
+                          "dense_pull_bfs": "4(n_u + 1) + 8 E_scanned + V/4 + 8|F_next|",
+                          "dense_pull_sssp": "4(V + 1) + 8m + 8 m_f + V/4 + 4|F_next|"}}))
+    return 0
+
+
 def run_grid4096(args):
     """4096x4096 grid, BFS + SSSP from --sources sources: host-driven drivers vs the batched engine."""
     import numpy as np
@@ -665,8 +779,8 @@ def main():
     if args.only:
         return run_only(args)
     if args.impl == "gi" and args.workload != "rmat22":
-        return {"rmat24_bfs_sssp": run_rmat24, "grid4096": run_grid4096, "batch512": run_batch512,
-                "bc": run_bc}[args.workload](args)
+        return {"rmat24_bfs_sssp": run_rmat24, "rmat24_levels": run_levels, "grid4096": run_grid4096,
+                "batch512": run_batch512, "bc": run_bc}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gi(args)

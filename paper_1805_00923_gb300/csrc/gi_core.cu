@@ -121,6 +121,62 @@ void dev_free(void *p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
 
+// Pinned host control blocks (kCtrlWords int64 each, one per graph), carved
+// from 64 KB slabs that live as long as the process: pinning and unpinning
+// host memory per graph costs more than the rest of a small graph's load,
+// and cudaFreeHost synchronises the device.
+static std::mutex g_pinned_mu;
+static std::vector<int64_t *> g_pinned_free;
+
+static int pinned_ctrl_get(int64_t **out) {
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  if (g_pinned_free.empty()) {
+    constexpr size_t kSlab = 64 * 1024, kBlock = sizeof(int64_t) * kCtrlWords;
+    void *slab = nullptr;
+    if (cudaHostAlloc(&slab, kSlab, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("pinned host allocation failed");
+      return GI_ERR_OOM;
+    }
+    for (size_t off = 0; off + kBlock <= kSlab; off += kBlock)
+      g_pinned_free.push_back(reinterpret_cast<int64_t *>(static_cast<char *>(slab) + off));
+  }
+  *out = g_pinned_free.back();
+  g_pinned_free.pop_back();
+  memset(*out, 0, sizeof(int64_t) * kCtrlWords);
+  return GI_OK;
+}
+
+static void pinned_ctrl_put(int64_t *p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  g_pinned_free.push_back(p);
+}
+
+// One non-blocking stream per device for the side copies of graph loads,
+// created on first use and kept: the loads order their work on it with events.
+static std::once_flag g_side_once[64];
+static cudaStream_t g_side_stream[64];
+
+static int side_stream(int dev, cudaStream_t *out) {
+  if (dev < 0 || dev >= 64) {
+    set_error("device %d out of range", dev);
+    return GI_ERR_UNSUPPORTED;
+  }
+  std::call_once(g_side_once[dev], [dev]() {
+    if (cudaStreamCreateWithFlags(&g_side_stream[dev], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      g_side_stream[dev] = nullptr;
+    }
+  });
+  if (!g_side_stream[dev]) {
+    set_error("side copy stream could not be created");
+    return GI_ERR_CUDA;
+  }
+  *out = g_side_stream[dev];
+  return GI_OK;
+}
+
 int heavy_get(gi_graph *g, cudaStream_t s) {
   if (g->heavy_mem) return GI_OK;
   // the expansion kernel returns counter and ticket to zero after each use
@@ -333,6 +389,7 @@ struct SideCopy {
   cudaEvent_t done[kChunks] = {}, wt_done = nullptr;
   int64_t cut[kChunks + 1] = {};
   int chunks = 0, waited = 0;
+  bool recorded = true;  // every copy enqueued so far is covered by an event
 
   int start(gi_graph *g, Csr *c, const int32_t *idx, const int32_t *wt, uint32_t flags, cudaStream_t s) {
     const int64_t m = g->m;
@@ -340,10 +397,11 @@ struct SideCopy {
     if (wt) GI_TRY(dev_alloc_n(&c->wt, m, s));
     if (m == 0) return GI_OK;
     const cudaMemcpyKind kind = (flags & GI_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    GI_TRY(side_stream(g->device, &cs));
+    recorded = false;
     cudaEvent_t ready = nullptr;
     GI_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     cudaError_t e = cudaEventRecord(ready, s);  // the allocations above, and any producer of device inputs
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
     cudaEventDestroy(ready);
     if (e != cudaSuccess) return cuda_fail(e, "side copy stream", __FILE__, __LINE__);
@@ -361,6 +419,7 @@ struct SideCopy {
       GI_CUDA(cudaEventCreateWithFlags(&wt_done, cudaEventDisableTiming));
       GI_CUDA(cudaEventRecord(wt_done, cs));
     }
+    recorded = true;
     return GI_OK;
   }
   // s waits for pieces [0, upto)
@@ -376,13 +435,15 @@ struct SideCopy {
     if (wt_done) GI_CUDA(cudaStreamWaitEvent(s, wt_done, 0));
     return wait(chunks, s);
   }
-  // the copies have finished (or never started) when this returns
+  // this load's copies have finished (or never started) when this returns
   void release() {
-    if (cs) cudaStreamSynchronize(cs);
+    if (cs && !recorded) cudaStreamSynchronize(cs);  // a start() that failed half way
+    for (auto &ev : done)
+      if (ev) cudaEventSynchronize(ev);
+    if (wt_done) cudaEventSynchronize(wt_done);
     for (auto &ev : done)
       if (ev) cudaEventDestroy(ev);
     if (wt_done) cudaEventDestroy(wt_done);
-    if (cs) cudaStreamDestroy(cs);
     cs = nullptr;
     wt_done = nullptr;
     for (auto &ev : done) ev = nullptr;
@@ -495,7 +556,7 @@ static void graph_release(gi_graph *g, cudaStream_t s) {
   dev_free(g->ctrl, s);
   dev_free(g->heavy_mem, s);
   ws_free(g, s);
-  if (g->ctrl_host) cudaFreeHost(g->ctrl_host);
+  pinned_ctrl_put(g->ctrl_host);
   delete g;
 }
 
@@ -526,12 +587,7 @@ extern "C" int gi_load_csr(const int32_t *offsets, const int32_t *indices, const
     }
     if ((st = dev_alloc_n(&g->ctrl, kCtrlWords, s)) != GI_OK) break;
     if (cudaMemsetAsync(g->ctrl, 0, sizeof(int64_t) * kCtrlWords, s) != cudaSuccess) { st = GI_ERR_CUDA; break; }
-    if (cudaHostAlloc((void **)&g->ctrl_host, sizeof(int64_t) * kCtrlWords, cudaHostAllocDefault) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("pinned host allocation failed");
-      st = GI_ERR_OOM;
-      break;
-    }
+    if ((st = pinned_ctrl_get(&g->ctrl_host)) != GI_OK) break;
     if ((st = copy_in(&g->out.ptr, offsets, n + 1, flags, s)) != GI_OK) break;
     if ((st = side.start(g, &g->out, indices, weights, flags, s)) != GI_OK) break;
     if ((flags & GI_VALIDATE) && ((st = side.wait_all(s)) != GI_OK || (st = validate_csr_dev(g, g->out, s)) != GI_OK))

@@ -738,34 +738,40 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
        w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t v = w * 32 + lane;
-    bool active = v < n && depth[v] == -1 && in_set(to, (int32_t)v);
-    int32_t a = 0, b = 0;
-    if (active) {
+    // the row bounds are loaded with the depth word (one round trip, not two)
+    int32_t a = 0, b = 0, dv = 0;
+    if (v < n) {
+      dv = depth[v];
       a = __ldg(ptr + v);
       b = __ldg(ptr + v + 1);
     }
+    const bool active = v < n && dv == -1 && in_set(to, (int32_t)v);
+    if (!active) b = a;
     int32_t found = -1;
-    const bool big = active && (b - a) >= t_warp;
-    if (active && !big) {
-      // 4 neighbours per round trip: 4 independent index loads, then 4
-      // independent frontier-bit loads; the first hit in order is the min id
-      for (int32_t e = a; e < b && found < 0; e += 4) {
-        int32_t u[4];
+    // every lane first probes the first 4 arcs of its own row: 4 independent
+    // index loads, then 4 independent frontier-bit loads; the first hit in
+    // order is the min id.  Rows of fewer than t_warp arcs go on 4 at a time;
+    // longer rows without a hit in the probe are scanned by the whole warp.
+    for (int32_t e = a; e < b && found < 0; e += 4) {
+      int32_t u[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) u[j] = e + j < b ? __ldg(idx + e + j) : -1;
-        bool h[4];
+      for (int j = 0; j < 4; ++j) u[j] = e + j < b ? __ldg(idx + e + j) : -1;
+      bool h[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) h[j] = u[j] >= 0 && in_set(F, u[j]);
+      for (int j = 0; j < 4; ++j) h[j] = u[j] >= 0 && in_set(F, u[j]);
 #pragma unroll
-        for (int j = 3; j >= 0; --j)
-          if (h[j]) found = u[j];
-      }
+      for (int j = 3; j >= 0; --j)
+        if (h[j]) found = u[j];
+      if (b - a >= t_warp) break;
     }
+    const bool big = active && found < 0 && (b - a) >= t_warp;
     unsigned bal = __ballot_sync(0xffffffffu, big);
     while (bal) {
       const int l = __ffs(bal) - 1;
       bal &= bal - 1;
-      const int32_t la = __shfl_sync(0xffffffffu, a, l), lb = __shfl_sync(0xffffffffu, b, l);
+      // the probe covered [a, a + 4)
+      const int32_t lb = __shfl_sync(0xffffffffu, b, l), la0 = __shfl_sync(0xffffffffu, a, l);
+      const int32_t la = la0 + (lb - la0 < 4 ? lb - la0 : 4);
       int32_t hit = -1;
       for (int32_t base = la; base < lb; base += 32) {
         const int32_t e = base + lane;
