@@ -269,9 +269,11 @@ static int frontier_loop(gi_graph *g, VsetPair &P, const gi_schedule &sc, bool t
     trace_put(tr, it, g->ctrl_host);
     g->hint_vset = P.F;
     g->hint_nf = g->ctrl_host[kNf];
+    g->hint_mf = g->ctrl_host[kMf];
     const int r = step(it, dir);
     g->hint_vset = nullptr;
     g->hint_nf = -1;
+    g->hint_mf = -1;
     GI_TRY(r);
     P.swap();
   }
@@ -774,6 +776,7 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
     float *cin = cb[cur], *cout = cb[cur ^ 1];
     g->hint_vset = P.F;
     g->hint_nf = g->ctrl_host[kNf];
+    g->hint_mf = g->ctrl_host[kMf];
     if (dir == GI_DIR_DENSE_PULL && segmented) {
       // cache-partitioned pull: segments add into seg_sum, then the vertex filter
       for (int sid = 0; sid < g->segs.num && st == GI_OK; ++sid) {
@@ -803,6 +806,7 @@ extern "C" int gi_pagerank_delta(gi_graph *g, float damping, float eps, int32_t 
     }
     g->hint_vset = nullptr;
     g->hint_nf = -1;
+    g->hint_mf = -1;
     P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
     P.swap();
     cur ^= 1;

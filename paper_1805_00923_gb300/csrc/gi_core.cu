@@ -177,6 +177,14 @@ static int side_stream(int dev, cudaStream_t *out) {
   return GI_OK;
 }
 
+int bfs_defer_get(gi_graph *g, cudaStream_t s) {
+  if (g->bfs_defer) return GI_OK;
+  // the deferred-scan kernel returns counter and ticket to zero after each use
+  GI_TRY(dev_alloc(&g->bfs_defer, 16 + 16 * (size_t)bfs_defer_cap(g->m), s));
+  GI_CUDA(cudaMemsetAsync(g->bfs_defer, 0, 16, s));
+  return GI_OK;
+}
+
 int heavy_get(gi_graph *g, cudaStream_t s) {
   if (g->heavy_mem) return GI_OK;
   // the expansion kernel returns counter and ticket to zero after each use
@@ -555,6 +563,7 @@ static void graph_release(gi_graph *g, cudaStream_t s) {
   dev_free(g->inv_out_deg, s);
   dev_free(g->ctrl, s);
   dev_free(g->heavy_mem, s);
+  dev_free(g->bfs_defer, s);
   ws_free(g, s);
   pinned_ctrl_put(g->ctrl_host);
   delete g;

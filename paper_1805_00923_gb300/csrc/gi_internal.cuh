@@ -150,13 +150,15 @@ struct gi_graph {
   gi::TileSet tile_cache[6];     // owned tile sets for tile_edges 256, 512, ..., 8192 (built on first use)
   gi::Segments segs;
   gi::HotSet hot;                // built on first use of the hot-source pull
-  // member count of a frontier known on the host (set by the drivers after
-  // their per-round statistics, cleared after the round); -1 = unknown
+  // member count and out-degree sum of a frontier known on the host (set by
+  // the drivers after their per-round statistics, cleared after the round);
+  // -1 = unknown
   const gi_vset *hint_vset = nullptr;
-  int64_t hint_nf = -1;
+  int64_t hint_nf = -1, hint_mf = -1;
   void *graph_loop = nullptr;    // cached CUDA graph of the graph-driven BFS (gi_schedule.persistent = 2)
   int64_t *ctrl = nullptr;       // device control block (kCtrlWords)
   void *heavy_mem = nullptr;     // HeavyList storage (counter, ticket, 2n entries), allocated on first use
+  void *bfs_defer = nullptr;     // BfsDefer storage of the early-exit BFS pull, allocated on first use
   int64_t *ctrl_host = nullptr;  // pinned mirror
   gi::Workspace *ws = nullptr;
   int device = 0;
@@ -210,6 +212,35 @@ __host__ __device__ inline HeavyList heavy_at(void *mem, int64_t n) {
   return h;
 }
 int heavy_get(gi_graph *g, cudaStream_t s);  // allocates g->heavy_mem on first use
+
+// Rows of the early-exit BFS pull that a warp scanned for kBfsScanCap arcs
+// without meeting a frontier source, with more than kBfsDeferChunk arcs
+// left, are queued here and finished by every block in chunks of
+// kBfsDeferChunk arcs (k_pull_bfs_deferred); best[j] receives the position
+// of the first frontier source in the rest of row j.  Each queued row has
+// more than kBfsScanCap + kBfsDeferChunk arcs, so m / that + 1 entries hold
+// them all.
+constexpr int kBfsScanCap = 1024, kBfsDeferChunk = 2048;
+struct BfsDefer {
+  unsigned long long *ctr;  // (entries << 32) | chunks
+  int32_t *ticket;
+  int32_t *row, *from, *base, *best;
+};
+__host__ __device__ inline int32_t bfs_defer_cap(int64_t m) {
+  return (int32_t)(m / (kBfsScanCap + kBfsDeferChunk) + 1);
+}
+__host__ __device__ inline BfsDefer bfs_defer_at(void *mem, int32_t cap) {
+  unsigned char *b = static_cast<unsigned char *>(mem);
+  BfsDefer d;
+  d.ctr = reinterpret_cast<unsigned long long *>(b);
+  d.ticket = reinterpret_cast<int32_t *>(b + 8);
+  d.row = reinterpret_cast<int32_t *>(b + 16);
+  d.from = d.row + cap;
+  d.base = d.from + cap;
+  d.best = d.base + cap;
+  return d;
+}
+int bfs_defer_get(gi_graph *g, cudaStream_t s);  // allocates g->bfs_defer on first use
 
 // exclusive scan of n int32 counts into out[n+1] (out[n] = total); scratch owned by g's workspace
 int scan_exclusive(gi_graph *g, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);

@@ -89,9 +89,25 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
       case GI_K_BFS: {
         const gi_bfs_args *a = static_cast<const gi_bfs_args *>(args);
         int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
+        // rows long enough to be deferred exist only above this degree; and
+        // once 1/64 of the arcs leave the frontier, a row's first kBfsScanCap
+        // arcs all miss it with probability about e^-16, so the deferred pass
+        // (one more launch) is left out
+        const bool long_rows = (g->symmetric ? (int64_t)g->max_deg : g->m) > kBfsScanCap + kBfsDeferChunk + 4;
+        const int64_t mf = from == g->hint_vset ? g->hint_mf : -1;
+        const bool sparse_front = mf < 0 || mf * 64 < g->m;
+        void *defer = nullptr;
+        const int32_t dcap = bfs_defer_cap(g->m);
+        if (tw != INT32_MAX && long_rows && sparse_front) {
+          GI_TRY(bfs_defer_get(g, s));
+          defer = g->bfs_defer;
+        }
         const int tok = timing_begin(kClassBfsPull, s);
         k_pull_bfs<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->n, F, to_bm, a->depth, a->parent,
-                                                          a->level, tw, o.bm, o.q, o.qc);
+                                                          a->level, tw, o.bm, o.q, o.qc, nullptr, defer, dcap);
+        if (defer)
+          k_pull_bfs_deferred<<<g->num_sms * 8, 256, 0, s>>>(g->in.ptr, g->in.idx, F, defer, dcap, a->depth,
+                                                              a->parent, a->level, o.bm, o.q, o.qc);
         timing_end(tok, s);
         GI_LAUNCH_CHECK();
         break;
@@ -263,10 +279,12 @@ extern "C" int gi_edgeset_apply(gi_graph *g, gi_vset *from, gi_vset *to, const g
     if (from) {  // |from| was just read back with the statistics
       g->hint_vset = from;
       g->hint_nf = g->ctrl_host[kNf];
+      g->hint_mf = g->ctrl_host[kMf];
     }
   }
   const int r = apply_dispatch(g, from, to, dir, *sched, kernel_id, kernel_args, out_modified, flags, s);
   g->hint_vset = nullptr;
   g->hint_nf = -1;
+  g->hint_mf = -1;
   return r;
 }

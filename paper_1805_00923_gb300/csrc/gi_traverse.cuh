@@ -728,7 +728,8 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
                                                   int64_t n, FSet F,
                                                   const uint32_t *__restrict__ to, int32_t *depth, int32_t *parent,
                                                   int32_t level, int32_t t_warp, uint32_t *out_bm, int32_t *out_q,
-                                                  int32_t *out_qc, const int32_t *gm = nullptr) {
+                                                  int32_t *out_qc, const int32_t *gm = nullptr,
+                                                  void *defer = nullptr, int32_t defer_cap = 0) {
   if (gm) {  // graph-driven level: run only when this level pulls
     if (gm[kGmPull] == 0) return;
     level = gm[kGmLevel] + 1;
@@ -772,14 +773,29 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
       // the probe covered [a, a + 4)
       const int32_t lb = __shfl_sync(0xffffffffu, b, l), la0 = __shfl_sync(0xffffffffu, a, l);
       const int32_t la = la0 + (lb - la0 < 4 ? lb - la0 : 4);
+      // a long row is scanned here for kBfsScanCap arcs at most; the rest,
+      // if no frontier source turned up, is left to every block
+      const int32_t stop = (defer != nullptr && lb - la > kBfsScanCap + kBfsDeferChunk) ? la + kBfsScanCap : lb;
       int32_t hit = -1;
-      for (int32_t base = la; base < lb; base += 32) {
+      for (int32_t base = la; base < stop; base += 32) {
         const int32_t e = base + lane;
-        int32_t u = e < lb ? __ldg(idx + e) : 0;
-        unsigned h = __ballot_sync(0xffffffffu, e < lb && in_set(F, u));
+        int32_t u = e < stop ? __ldg(idx + e) : 0;
+        unsigned h = __ballot_sync(0xffffffffu, e < stop && in_set(F, u));
         if (h) {
           hit = __shfl_sync(0xffffffffu, u, __ffs(h) - 1);
           break;
+        }
+      }
+      if (hit < 0 && stop < lb && lane == l) {
+        const BfsDefer D = bfs_defer_at(defer, defer_cap);
+        const unsigned nch = (unsigned)((lb - stop + kBfsDeferChunk - 1) / kBfsDeferChunk);
+        const unsigned long long old = atomicAdd(D.ctr, (1ull << 32) | nch);
+        const int32_t j = (int32_t)(old >> 32);
+        if (j < defer_cap) {  // always: each queued row holds more than m / defer_cap arcs
+          D.row[j] = (int32_t)v;
+          D.from[j] = stop;
+          D.base[j] = (int32_t)(old & 0xffffffffull);
+          D.best[j] = INT32_MAX;
         }
       }
       if (lane == l) found = hit;
@@ -798,6 +814,90 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
       base = __shfl_sync(0xffffffffu, base, 0);
       if (got) out_q[base + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
     }
+  }
+}
+
+// The deferred rows of k_pull_bfs: block task c is chunk c of the queue (the
+// last entry whose first chunk is <= c), kBfsDeferChunk arcs, 8 per thread.
+// A chunk that starts after a hit already recorded for its row is skipped;
+// otherwise the chunk's first frontier source (lowest position) goes into
+// best[row] by atomicMin, so best ends as the row's first hit in order, the
+// min-id parent.  The last block to finish writes depth / parent / output
+// set for the rows that hit and empties the queue for the next level (every
+// block has read the counter before it takes its ticket).
+static __global__ void __launch_bounds__(256) k_pull_bfs_deferred(const int32_t *__restrict__ ptr,
+                                                           const int32_t *__restrict__ idx, FSet F, void *defer,
+                                                           int32_t defer_cap, int32_t *depth, int32_t *parent,
+                                                           int32_t level, uint32_t *out_bm, int32_t *out_q,
+                                                           int32_t *out_qc) {
+  constexpr int kPer = kBfsDeferChunk / 256;
+  const BfsDefer D = bfs_defer_at(defer, defer_cap);
+  const unsigned long long c64 = *(volatile unsigned long long *)D.ctr;
+  const int32_t H = (int32_t)(c64 >> 32) < defer_cap ? (int32_t)(c64 >> 32) : defer_cap;
+  const int32_t C = (int32_t)(c64 & 0xffffffffull);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int32_t s_j, s_from, s_end, s_min[8];
+  __shared__ bool s_last;
+  for (int32_t c = blockIdx.x; c < C; c += gridDim.x) {
+    if (tid == 0) {
+      int32_t lo = 0, hi = H - 1;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (D.base[mid] <= c) lo = mid;
+        else hi = mid - 1;
+      }
+      const int32_t from = D.from[lo] + (c - D.base[lo]) * kBfsDeferChunk;
+      const int32_t end = __ldg(ptr + D.row[lo] + 1);
+      s_j = lo;
+      s_from = from;
+      s_end = *(volatile int32_t *)(D.best + lo) < from ? from : min(from + kBfsDeferChunk, end);
+    }
+    __syncthreads();
+    const int32_t from = s_from, end = s_end;
+    int32_t u[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int32_t e = from + tid + 256 * k;
+      u[k] = e < end ? __ldg(idx + e) : -1;
+    }
+    int32_t mine = INT32_MAX;
+#pragma unroll
+    for (int k = kPer - 1; k >= 0; --k)
+      if (u[k] >= 0 && in_set(F, u[k])) mine = from + tid + 256 * k;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine = min(mine, __shfl_xor_sync(0xffffffffu, mine, o));
+    if (lane == 0) s_min[warp] = mine;
+    __syncthreads();
+    if (tid == 0) {
+      int32_t y = s_min[0];
+      for (int w = 1; w < 8; ++w) y = min(y, s_min[w]);
+      if (y < INT32_MAX) atomicMin(D.best + s_j, y);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(D.ticket, 1) == (int32_t)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int32_t j = tid; j < H; j += blockDim.x) {
+    const int32_t pos = *(volatile int32_t *)(D.best + j);
+    if (pos == INT32_MAX) continue;
+    const int32_t v = D.row[j], u = __ldg(idx + pos);
+    depth[v] = level;
+    if (parent) parent[v] = u;
+    if (out_bm) {
+      atomicOr(out_bm + (v >> 5), 1u << (v & 31));
+      out_q[atomicAdd(out_qc, 1)] = v;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    *D.ctr = 0ull;
+    *D.ticket = 0;
+    __threadfence();
   }
 }
 

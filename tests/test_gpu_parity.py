@@ -514,3 +514,24 @@ def test_sparse_pull_matches_dense_pull_with_to_set(gi, bal):
     lab_want = np.full(hg.n, 500)
     np.minimum.at(lab_want, v, snap_h[u])
     assert np.array_equal(b[3], lab_want)
+
+
+@pytest.mark.parametrize("direction", ["dense_pull", "hybrid_pull"])
+def test_bfs_pull_deferred_long_rows(gi, direction):
+    """Rows whose first 1,028 in-arcs hold no frontier source and that have
+    more than 2,048 arcs left are finished by every block in 2,048-arc
+    chunks.  A hub of 20,000 leaves is pulled with its only frontier source
+    deep in the row, with frontier sources in two different chunks (the
+    parent must be the lower id), and with none at all."""
+    N = 20_000
+    S = N + 1
+    edges = [(0, i) for i in range(1, N + 1)] + [(S, 9_000), (S, 17_000)]
+    hg = gg.from_edge_list(N + 2, edges)
+    g = _load(gi, hg)
+    # S: hits at positions 8,999 and 16,999 (two chunks); 15,000 and 1,500:
+    # one deferred hit; 500: a hit inside the warp's own scan; 0: the hub
+    for src in (S, 15_000, 1_500, 500, 0):
+        want_d, want_p, _ = oracle.bfs(hg, src)
+        d, p = gi.bfs(g, src, sched=gi.schedule(direction))
+        assert np.array_equal(_np(d), want_d), src
+        assert np.array_equal(_np(p), want_p), src
