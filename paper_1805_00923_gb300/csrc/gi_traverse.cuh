@@ -738,18 +738,43 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
     if (gm[kGmPull] == 0) return;
     level = gm[kGmLevel] + 1;
   }
+  // found vertices are staged per warp in shared memory and appended to the
+  // queue kQBuf - 32 or more at a time: one atomic per flush, not one per
+  // 32 vertices, and no wait on its return in every iteration
+  constexpr int kQBuf = 128;
+  __shared__ int32_t s_q[8][kQBuf];  // blockDim.x == 256
   const int lane = threadIdx.x & 31;
+  int32_t *wq = s_q[threadIdx.x >> 5];
+  int32_t qn = 0;  // staged entries (warp-uniform)
+  const auto flush = [&]() {
+    __syncwarp();
+    int32_t base = 0;
+    if (lane == 0) base = atomicAdd(out_qc, qn);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int32_t j = lane; j < qn; j += 32) out_q[base + j] = wq[j];
+    __syncwarp();
+    qn = 0;
+  };
   const int64_t nw = (n + 31) >> 5;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
-       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int64_t v = w * 32 + lane;
-    // the row bounds are loaded with the depth word (one round trip, not two)
-    int32_t a = 0, b = 0, dv = 0;
-    if (v < n) {
-      dv = depth[v];
-      a = __ldg(ptr + v);
-      b = __ldg(ptr + v + 1);
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // the depth word and row bounds of the warp's next 32 vertices are loaded
+  // while the current ones are probed (one round trip per iteration fewer)
+  int32_t ndv = 0, na = 0, nb = 0;
+  const auto fetch = [&](int64_t ww) {
+    const int64_t vv = ww * 32 + lane;
+    if (ww < nw && vv < n) {
+      ndv = depth[vv];
+      na = __ldg(ptr + vv);
+      nb = __ldg(ptr + vv + 1);
     }
+  };
+  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  fetch(w);
+  for (; w < nw; w += wstride) {
+    const int64_t v = w * 32 + lane;
+    const int32_t dv = ndv;
+    int32_t a = na, b = nb;
+    fetch(w + wstride);
     const bool active = v < n && dv == -1 && in_set(to, (int32_t)v);
     if (!active) b = a;
     int32_t found = -1;
@@ -813,12 +838,12 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
     if (out_bm == nullptr) continue;
     if (lane == 0 && word) out_bm[w] |= word;
     if (word) {
-      int32_t base = 0;
-      if (lane == 0) base = atomicAdd(out_qc, __popc(word));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (got) out_q[base + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
+      if (got) wq[qn + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
+      qn += __popc(word);
+      if (qn > kQBuf - 32) flush();
     }
   }
+  if (out_bm != nullptr && qn > 0) flush();
 }
 
 // The deferred rows of k_pull_bfs: block task c is chunk c of the queue (the
