@@ -33,7 +33,7 @@ def workloads(seed_base: int, quick: bool):
     for sc in scales:
         for ef in (8, 16, 32):
             out.append(("bfs", f"rmat{sc}_ef{ef}", lambda sc=sc, ef=ef: gg.rmat_graph(sc, ef, seed=seed_base + sc)))
-    for sc in scales[:-1]:
+    for sc in scales:
         out.append(("sssp", f"rmat{sc}_w", lambda sc=sc: gg.rmat_graph(sc, 16, seed=seed_base + 50 + sc,
                                                                          weights=(1, 1000))))
     sides = [128, 256, 512] if quick else [128, 256, 512, 1024, 2048]
