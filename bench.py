@@ -40,7 +40,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gi", "reference"], default="gi")
     p.add_argument("--scale", type=int, default=22)
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=16)
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--tune-budget", type=int, default=12, help="autotuner trials per algorithm (untimed)")
@@ -349,20 +349,53 @@ def run_gi(args):
         with torch.cuda.stream(side):
             out_h[i].copy_(res_dev[i], non_blocking=True)
 
-    e2e_ms, e2e_edges = [], 0.0
-    for k in range(args.e2e_steps + 1):
+    # serial form: load, step, copy back, free, one after another
+    serial_ms = []
+    for k in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ge = gi.Graph(rp_h.numpy(), col_h.numpy(), symmetric=True, hot_sources=want_hot)
-        ed = step(ge, after=fetch)
+        step(ge, after=fetch)
         torch.cuda.current_stream().wait_stream(side)
-        torch.cuda.synchronize()
+        torch.cuda.current_stream().synchronize()
         ge.free()
-        dt = (time.perf_counter() - t0) * 1e3
-        if k > 0:  # first one warms the allocator pool
-            e2e_ms.append(dt)
-            e2e_edges += sum(ed)
-    e2e_total = sum(e2e_ms)
+        if k > 0:  # the first one warms the allocator pool
+            serial_ms.append((time.perf_counter() - t0) * 1e3)
+
+    # pipelined form (the reported number): like a data loader, a second host
+    # thread loads step k+1's graph (host-to-device copy on its own stream,
+    # tiles, hot-source set) while step k runs.  Every step's copy in, from the
+    # first load on, and every result copy out lie inside the timed region.
+    load_stream = torch.cuda.Stream()
+    dev = torch.cuda.current_device()
+
+    def load_graph(box):
+        torch.cuda.set_device(dev)
+        box["g"] = gi.Graph(rp_h.numpy(), col_h.numpy(), symmetric=True, hot_sources=want_hot, stream=load_stream)
+
+    def pipelined(K):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        box = {}
+        load_graph(box)
+        edges = 0.0
+        for k in range(K):
+            cur, box = box["g"], {}
+            th = threading.Thread(target=load_graph, args=(box,)) if k + 1 < K else None
+            if th:
+                th.start()
+            edges += sum(step(cur, after=fetch))
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.current_stream().synchronize()
+            if th:
+                th.join()
+                if "g" not in box:
+                    raise RuntimeError("graph load in the loader thread failed")
+            cur.free()  # after the join: its device-wide sync waits for nothing
+        return (time.perf_counter() - t0) * 1e3, edges
+
+    pipelined(2)  # warm-up
+    e2e_total, e2e_edges = pipelined(args.e2e_steps)
     if world > 1:
         from paper_1805_00923_gb300 import replicas
         e2e_total = replicas.max_over_ranks(e2e_total, device="cuda")
@@ -420,7 +453,10 @@ def run_gi(args):
                                         "per arc, 1/outdeg, output vector)", "launches_timed": pr_launches,
                          "avg_launch_ms": avg_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": sum(e2e_ms) / max(len(e2e_ms), 1)},
+                    "ms_per_step": e2e_total / args.e2e_steps, "steps": args.e2e_steps,
+                    "form": "next step's graph loaded by a second host thread on its own stream under the "
+                            "current step; first load and every copy in the timed region",
+                    "serial_ms_per_step": statistics.median(serial_ms)},
             "gpu_launches": launches, "clocks": clocks,
             "autotuned": tuned, "pagerank_direction_gteps": compare, "selector": selector}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
