@@ -932,21 +932,50 @@ static __global__ void __launch_bounds__(256) k_pull_bfs_deferred(const int32_t 
 
 // ------------------------------------------------------------------- push ------
 
-template <class Op>
-__device__ __forceinline__ void push_apply(const Op &op, int32_t u, int32_t v, int32_t e,
-                                           const uint32_t *__restrict__ to, const OutSet &out) {
-  const bool mod = v >= 0 && in_set(to, v) && op.push(u, v, e);
-  if (out.enabled()) {
-    bool fresh = false;
-    if (mod) {
+// A batch of N candidate arcs (u[j] -> v[j], arc e[j]; v[j] < 0: none): all
+// N updates first, then all dedup tests, then one warp-aggregated append to
+// the output queue.  Taken arc by arc, a ballot and two atomics whose results
+// are waited for stood between consecutive updates, so the updates of one
+// batch never overlapped.
+template <int N, class Op>
+__device__ __forceinline__ void push_batch(const Op &op, const int32_t (&u)[N], const int32_t (&v)[N],
+                                           const int32_t (&e)[N], const uint32_t *__restrict__ to,
+                                           const OutSet &out) {
+  bool mod[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) mod[j] = v[j] >= 0 && in_set(to, v[j]) && op.push(u[j], v[j], e[j]);
+  if (!out.enabled()) return;
+  bool fresh[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    fresh[j] = false;
+    if (mod[j]) {
       if (out.dedup) {
-        fresh = bit_test_and_set(out.bm, v);
+        fresh[j] = bit_test_and_set(out.bm, v[j]);
       } else {
-        atomicOr(out.bm + (v >> 5), 1u << (v & 31));
-        fresh = true;
+        atomicOr(out.bm + (v[j] >> 5), 1u << (v[j] & 31));
+        fresh[j] = true;
       }
     }
-    warp_append(out.q, out.qc, fresh, v);
+  }
+  const unsigned act = __activemask();
+  unsigned ball[N];
+  int32_t tot = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    ball[j] = __ballot_sync(act, fresh[j]);
+    tot += __popc(ball[j]);
+  }
+  if (tot == 0) return;
+  const int lane = lane_id(), leader = __ffs(act) - 1;
+  int32_t base = 0;
+  if (lane == leader) base = atomicAdd(out.qc, tot);
+  base = __shfl_sync(act, base, leader);
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (fresh[j]) out.q[base + __popc(ball[j] & lt)] = v[j];
+    base += __popc(ball[j]);
   }
 }
 
@@ -959,11 +988,14 @@ __device__ __forceinline__ void push_strided(const Op &op, int32_t u, int32_t a,
                                              int32_t step, const int32_t *__restrict__ idx,
                                              const uint32_t *__restrict__ to, const OutSet &out) {
   for (int32_t k = k0; k < deg; k += kPushBatch * step) {
-    int32_t v[kPushBatch];
+    int32_t uu[kPushBatch], v[kPushBatch], e[kPushBatch];
 #pragma unroll
-    for (int j = 0; j < kPushBatch; ++j) v[j] = (k + j * step < deg) ? __ldg(idx + a + k + j * step) : -1;
-#pragma unroll
-    for (int j = 0; j < kPushBatch; ++j) push_apply(op, u, v[j], a + k + j * step, to, out);
+    for (int j = 0; j < kPushBatch; ++j) {
+      uu[j] = u;
+      e[j] = a + k + j * step;
+      v[j] = (k + j * step < deg) ? __ldg(idx + e[j]) : -1;
+    }
+    push_batch(op, uu, v, e, to, out);
   }
 }
 
@@ -1092,8 +1124,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__res
             vv[b] = -1;
           }
         }
-#pragma unroll
-        for (int b = 0; b < kPushBatch; ++b) push_apply(op, uu[b], vv[b], ee[b], to, out);
+        push_batch(op, uu, vv, ee, to, out);
       }
       __syncthreads();
     } else {
@@ -1206,8 +1237,7 @@ __global__ void __launch_bounds__(256) k_push_edges(Op op, const int32_t *__rest
         v[p] = __ldg(idx + e[p]);
       }
     }
-#pragma unroll
-    for (int p = 0; p < kPer; ++p) push_apply(op, u[p], v[p], e[p], to, out);
+    push_batch(op, u, v, e, to, out);
     __syncthreads();
   }
 }
