@@ -337,16 +337,5 @@ __device__ __forceinline__ bool bit_test_and_set(uint32_t *bm, int32_t v) {
   return (old & mask) == 0;
 }
 
-// warp-aggregated append of `v` (for lanes with `want`) to queue/count
-__device__ __forceinline__ void warp_append(int32_t *queue, int32_t *count, bool want, int32_t v) {
-  unsigned active = __activemask();
-  unsigned ball = __ballot_sync(active, want);
-  if (!ball) return;
-  int leader = __ffs(ball) - 1;
-  int base = 0;
-  if (lane_id() == leader) base = atomicAdd(count, __popc(ball));
-  base = __shfl_sync(active, base, leader);
-  if (want) queue[base + __popc(ball & ((1u << lane_id()) - 1))] = v;
-}
 
 }  // namespace gi
