@@ -181,11 +181,14 @@ template <class Fn>
 __device__ __forceinline__ void strided_arcs(int32_t du, int32_t a, int32_t d, int32_t k0, int32_t step,
                                              const int32_t *__restrict__ idx, Fn &fn) {
   for (int32_t k = k0; k < d; k += kBatchArcs * step) {
-    int32_t v[kBatchArcs];
+    int32_t dd[kBatchArcs], e[kBatchArcs], v[kBatchArcs];
 #pragma unroll
-    for (int j = 0; j < kBatchArcs; ++j) v[j] = k + j * step < d ? __ldg(idx + a + k + j * step) : -1;
-#pragma unroll
-    for (int j = 0; j < kBatchArcs; ++j) fn(du, a + k + j * step, v[j]);
+    for (int j = 0; j < kBatchArcs; ++j) {
+      dd[j] = du;
+      e[j] = a + k + j * step;
+      v[j] = k + j * step < d ? __ldg(idx + e[j]) : -1;
+    }
+    fn(dd, e, v);
   }
 }
 
@@ -262,8 +265,7 @@ __device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_
           v[b2] = -1;
         }
       }
-#pragma unroll
-      for (int b2 = 0; b2 < kBatchArcs; ++b2) fn(dd[b2], e[b2], v[b2]);
+      fn(dd, e, v);
     }
     __syncthreads();
   }
@@ -281,17 +283,54 @@ __device__ __forceinline__ void append_warp(bool want, int32_t v, int32_t *next,
   if (want) next[base + __popc(ball & ((1u << lane) - 1u))] = v;
 }
 
+// One warp-aggregated append of a batch (v[j] where want[j]): one atomic for
+// the batch instead of one per arc.
+__device__ __forceinline__ void append_batch(const bool (&want)[kBatchArcs], const int32_t (&v)[kBatchArcs],
+                                             int32_t *next, int64_t *ncnt) {
+  const int lane = threadIdx.x & 31;
+  const unsigned active = __activemask();
+  unsigned ball[kBatchArcs];
+  int32_t tot = 0;
+#pragma unroll
+  for (int j = 0; j < kBatchArcs; ++j) {
+    ball[j] = __ballot_sync(active, want[j]);
+    tot += __popc(ball[j]);
+  }
+  if (tot == 0) return;
+  const int leader = __ffs(active) - 1;
+  long long base = 0;
+  if (lane == leader) base = atomicAdd(reinterpret_cast<unsigned long long *>(ncnt), (unsigned long long)tot);
+  base = __shfl_sync(active, base, leader);
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < kBatchArcs; ++j) {
+    if (want[j]) next[base + __popc(ball[j] & lt)] = v[j];
+    base += __popc(ball[j]);
+  }
+}
+
 // BFS SparsePush of this level's queue: newly reached vertices get depth L+1
 // and join the next queue (their out-degrees summed into the edge count).
 __device__ void batch_bfs_push(const BatchGraph &G, int32_t *depth, const int32_t *cur, int64_t nf, int32_t *next,
                                int64_t *ncnt, int64_t *necnt, int32_t L, int rank, int csize) {
-  auto fn = [&](int32_t, int32_t, int32_t v) {
-    bool won = false;
-    if (v >= 0 && *(volatile int32_t *)(depth + v) == -1) won = atomicCAS(depth + v, -1, L + 1) == -1;
-    append_warp(won, v, next, ncnt);
-    if (won)
-      atomicAdd(reinterpret_cast<unsigned long long *>(necnt), (unsigned long long)(__ldg(G.ptr + v + 1) -
-                                                                                   __ldg(G.ptr + v)));
+  // a batch's claims first, then one append and one edge-count add per warp
+  auto fn = [&](const int32_t (&)[kBatchArcs], const int32_t (&)[kBatchArcs], const int32_t (&v)[kBatchArcs]) {
+    bool won[kBatchArcs];
+#pragma unroll
+    for (int j = 0; j < kBatchArcs; ++j) {
+      won[j] = false;
+      if (v[j] >= 0 && *(volatile int32_t *)(depth + v[j]) == -1) won[j] = atomicCAS(depth + v[j], -1, L + 1) == -1;
+    }
+    append_batch(won, v, next, ncnt);
+    // the won vertices are distinct, so a warp's degree sum is below m < 2^31
+    uint32_t deg = 0;
+#pragma unroll
+    for (int j = 0; j < kBatchArcs; ++j)
+      if (won[j]) deg += (uint32_t)(__ldg(G.ptr + v[j] + 1) - __ldg(G.ptr + v[j]));
+    const unsigned active = __activemask();
+    const uint32_t wdeg = __reduce_add_sync(active, deg);
+    if (wdeg && (threadIdx.x & 31) == __ffs(active) - 1)
+      atomicAdd(reinterpret_cast<unsigned long long *>(necnt), (unsigned long long)wdeg);
   };
   cta_expand(G, cur, nullptr, nullptr, nf, rank, csize, fn);
 }
@@ -378,19 +417,26 @@ __device__ void batch_sssp_push(const BatchGraph &G, int32_t *dist, const int32_
       atomicAdd(reinterpret_cast<unsigned long long *>(relaxed), (unsigned long long)__popc(ball));
     return near;
   };
-  auto fn = [&](int32_t du, int32_t e, int32_t v) {
-    bool fresh = false;
-    if (v >= 0) {
-      const long long nd = (long long)du + __ldg(G.wt + e);
-      if (nd < *(volatile int32_t *)(dist + v)) {
-        const int32_t old = atomicMin(dist + v, (int32_t)nd);
-        if (nd < old) {
-          const uint32_t mask = 1u << (v & 31);
-          fresh = (atomicOr(inq + (v >> 5), mask) & mask) == 0;
-        }
+  // a batch's relaxations first, then its dedup tests, then one append
+  auto fn = [&](const int32_t (&du)[kBatchArcs], const int32_t (&e)[kBatchArcs], const int32_t (&v)[kBatchArcs]) {
+    bool better[kBatchArcs], fresh[kBatchArcs];
+#pragma unroll
+    for (int j = 0; j < kBatchArcs; ++j) {
+      better[j] = false;
+      if (v[j] >= 0) {
+        const long long nd = (long long)du[j] + __ldg(G.wt + e[j]);
+        if (nd < *(volatile int32_t *)(dist + v[j])) better[j] = nd < atomicMin(dist + v[j], (int32_t)nd);
       }
     }
-    append_warp(fresh, v, next, ncnt);
+#pragma unroll
+    for (int j = 0; j < kBatchArcs; ++j) {
+      fresh[j] = false;
+      if (better[j]) {
+        const uint32_t mask = 1u << (v[j] & 31);
+        fresh[j] = (atomicOr(inq + (v[j] >> 5), mask) & mask) == 0;
+      }
+    }
+    append_batch(fresh, v, next, ncnt);
   };
   cta_expand(G, cur, nullptr, dist, nf, rank, csize, fn, keep);
 }
