@@ -338,33 +338,61 @@ __device__ void batch_bfs_push(const BatchGraph &G, int32_t *depth, const int32_
 // BFS DensePull with early exit: the frontier is {u : depth[u] == L}
 __device__ void batch_bfs_pull(const BatchGraph &G, int32_t *depth, int32_t *next, int64_t *ncnt, int64_t *necnt,
                                int32_t L, int rank, int csize) {
+  // as the single-query early-exit pull: each lane probes its row's first 4
+  // arcs before any warp-wide scan, the next rows' depth and bounds are
+  // fetched under the current probe, found vertices are staged per warp and
+  // appended kQBuf - 32 or more at a time, and the edge count is summed per
+  // lane and added once per warp
+  constexpr int kQBuf = 128;
+  __shared__ int32_t s_q[kBT / 32][kQBuf];
   const int lane = threadIdx.x & 31;
+  int32_t *wq = s_q[threadIdx.x >> 5];
+  int32_t qn = 0;
+  unsigned long long edges = 0;
+  const auto flush = [&]() {
+    __syncwarp();
+    long long base = 0;
+    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(ncnt), (unsigned long long)qn);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int32_t j = lane; j < qn; j += 32) next[base + j] = wq[j];
+    __syncwarp();
+    qn = 0;
+  };
   const int64_t nw = (G.n + 31) >> 5;
   const int64_t wstride = (int64_t)csize * (kBT / 32);
-  for (int64_t w = (int64_t)rank * (kBT / 32) + (threadIdx.x >> 5); w < nw; w += wstride) {
+  int32_t ndv = 0, na = 0, nb = 0;
+  const auto fetch = [&](int64_t ww) {
+    const int64_t vv = ww * 32 + lane;
+    if (ww < nw && vv < G.n) {
+      ndv = depth[vv];
+      na = G.iptr[vv];
+      nb = G.iptr[vv + 1];
+    }
+  };
+  int64_t w = (int64_t)rank * (kBT / 32) + (threadIdx.x >> 5);
+  fetch(w);
+  for (; w < nw; w += wstride) {
     const int64_t v = w * 32 + lane;
-    const bool active = v < G.n && depth[v] == -1;
-    int32_t a = 0, b = 0;
-    if (active) {
-      a = G.iptr[v];
-      b = G.iptr[v + 1];
-    }
+    const int32_t dv = ndv;
+    int32_t a = na, b = nb;
+    fetch(w + wstride);
+    const bool active = v < G.n && dv == -1;
+    if (!active) b = a;
     bool found = false;
-    const bool big = active && (b - a) >= 32;
-    if (active && !big) {
-      for (int32_t e = a; e < b && !found; e += 4) {
-        int32_t u[4];
+    for (int32_t e = a; e < b && !found; e += 4) {
+      int32_t u[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) u[j] = e + j < b ? G.iidx[e + j] : -1;
+      for (int j = 0; j < 4; ++j) u[j] = e + j < b ? G.iidx[e + j] : -1;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) found |= u[j] >= 0 && depth[u[j]] == L;
-      }
+      for (int j = 0; j < 4; ++j) found |= u[j] >= 0 && depth[u[j]] == L;
+      if (b - a >= 32) break;
     }
+    const bool big = active && !found && (b - a) >= 32;
     unsigned bal = __ballot_sync(0xffffffffu, big);
     while (bal) {
       const int l = __ffs(bal) - 1;
       bal &= bal - 1;
-      const int32_t la = __shfl_sync(0xffffffffu, a, l), lb = __shfl_sync(0xffffffffu, b, l);
+      const int32_t lb = __shfl_sync(0xffffffffu, b, l), la = __shfl_sync(0xffffffffu, a, l) + 4;
       bool hit = false;
       for (int32_t base = la; base < lb && !hit; base += 32) {
         const int32_t e = base + lane;
@@ -372,18 +400,21 @@ __device__ void batch_bfs_pull(const BatchGraph &G, int32_t *depth, int32_t *nex
       }
       if (lane == l) found = hit;
     }
-    if (found) depth[v] = L + 1;
+    if (found) {
+      depth[v] = L + 1;
+      edges += (unsigned long long)(G.ptr[v + 1] - G.ptr[v]);
+    }
     const unsigned word = __ballot_sync(0xffffffffu, found);
     if (word) {
-      long long base = 0;
-      if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(ncnt), (unsigned long long)__popc(word));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (found) {
-        next[base + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
-        atomicAdd(reinterpret_cast<unsigned long long *>(necnt), (unsigned long long)(G.ptr[v + 1] - G.ptr[v]));
-      }
+      if (found) wq[qn + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
+      qn += __popc(word);
+      if (qn > kQBuf - 32) flush();
     }
   }
+  if (qn > 0) flush();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) edges += __shfl_xor_sync(0xffffffffu, edges, o);
+  if (lane == 0 && edges) atomicAdd(reinterpret_cast<unsigned long long *>(necnt), edges);
 }
 
 // SSSP push relax of this round's queue with asynchronous min updates (the
