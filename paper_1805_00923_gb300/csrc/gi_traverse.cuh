@@ -1511,8 +1511,8 @@ int launch_pull_hot(gi_graph *g, const Op &op, const TileSet &ts, const uint32_t
 
 // Tiled pull over the in-edges `c` with tiles `ts` (the whole graph or one segment).
 // hot_mode (gi_schedule.hot_cache) applies to whole-graph pulls from all sources
-// of Ops whose arc values come from per-source 4-byte values; Ops with other
-// than fp32 values use the L1 form for both modes.
+// of Ops whose arc values come from per-source 4-byte values (both forms
+// take any such value: fp32 contributions, int32 labels or distances).
 template <class Op>
 int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts, FSet F,
                       const uint32_t *to, const OutSet &out, cudaStream_t s, int kclass = kClassOtherPull,
