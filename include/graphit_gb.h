@@ -19,6 +19,10 @@
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *     stream.  Work is enqueued on it; calls documented as "syncs" wait for it.
  *   - Vertex ids and arc offsets are int32 (graphs with fewer than 2^31 arcs).
+ *   - Threads: different graphs may be loaded and traversed from different
+ *     host threads on different streams at the same time.  One graph runs one
+ *     traversal at a time (its scratch lists, tiles and hot-source set are
+ *     per graph); gi_graph_free and gi_vset_free synchronise the device.
  */
 #ifndef GRAPHIT_GB_H
 #define GRAPHIT_GB_H
