@@ -1,0 +1,65 @@
+"""Host-side pieces of bench.py that need no GPU: the per-level byte model of
+the early-exit BFS pull (checked against a brute-force scan) and the JSON line
+of the CPU reference arm."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import torch
+
+import graphgen as gg
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_bfs_level_bytes_match_brute_force():
+    """|F|, m_f, |F_next|, n_u and E_scanned (in-arcs up to and including the
+    first frontier source, all of them if none) per level, from the depths."""
+    hg = gg.rmat_graph(10, seed=3)
+    src = int(gg.pick_sources(hg, 1, seed=1)[0])
+    depth, _, _ = oracle.bfs(hg, src)
+    deg = np.diff(hg.row_ptr)
+    levels = int(depth.max()) + 1
+    got = bench._bfs_level_bytes(torch.from_numpy(depth.astype(np.int32)), torch.from_numpy(hg.col),
+                                 torch.repeat_interleave(torch.arange(hg.n, dtype=torch.int32),
+                                                         torch.from_numpy(deg.astype(np.int64))),
+                                 torch.from_numpy(hg.row_ptr), torch.from_numpy(deg.astype(np.int32)), levels)
+    for d in range(levels):
+        scanned = 0
+        for v in range(hg.n):
+            if 0 <= depth[v] <= d:
+                continue
+            a, b = hg.row_ptr[v], hg.row_ptr[v + 1]
+            k = b - a
+            for j in range(a, b):
+                if depth[hg.col[j]] == d:
+                    k = j - a + 1
+                    break
+            scanned += k
+        front = depth == d
+        assert got[d] == dict(frontier=int(front.sum()), m_f=int(deg[front].sum()),
+                              next=int((depth == d + 1).sum()), n_u=int(((depth > d) | (depth < 0)).sum()),
+                              e_scanned=scanned)
+
+
+def test_reference_arm_json_line():
+    """`--impl reference` prints one JSON line with the contract's keys and
+    exits 0 (oracle PageRank on a small graph)."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--scale", "12",
+                        "--steps", "1", "--warmup", "0", "--cpu-seconds", "0.2"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "dtype", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["kind"] == "oracle"
