@@ -535,3 +535,50 @@ def test_bfs_pull_deferred_long_rows(gi, direction):
         d, p = gi.bfs(g, src, sched=gi.schedule(direction))
         assert np.array_equal(_np(d), want_d), src
         assert np.array_equal(_np(p), want_p), src
+
+
+def test_bfs_pull_deferred_rows_directed_graph(gi):
+    """Deferred long rows on a directed graph whose in-edges are loaded
+    separately: hub H has in-arcs from 20,000 sources, and the BFS reaches two
+    of them (9,000 and 17,000) one level before H."""
+    N = 20_000
+    H, S = N + 1, N + 2
+    src = list(range(1, N + 1)) + [S, S]
+    dst = [H] * N + [9_000, 17_000]
+    row_ptr, col = gg.csr_from_edges(N + 3, np.array(src, np.int32), np.array(dst, np.int32), False)
+    hg = gg.HostGraph(N + 3, row_ptr, col, None, False, "directed_hub", {})
+    in_ptr, in_col, _ = gg.transpose(hg)
+    g = gi.Graph(hg.row_ptr, hg.col, symmetric=False, in_edges=(in_ptr, in_col, None))
+    for direction in ("dense_pull", "hybrid_pull"):
+        for s in (S, 12_345):
+            want_d, want_p, _ = oracle.bfs(hg, s, in_edges=(in_ptr, in_col))
+            d, p = gi.bfs(g, s, sched=gi.schedule(direction))
+            assert np.array_equal(_np(d), want_d), (direction, s)
+            assert np.array_equal(_np(p), want_p), (direction, s)
+
+
+@pytest.mark.parametrize("hub_in_to", [True, False])
+def test_edgeset_apply_bfs_deferred_row_with_to_set(gi, hub_in_to):
+    """The operator form of the early-exit pull: a hub whose frontier sources
+    sit deep in its row is finished by the deferred scan only if the `to` set
+    holds it; the parent is the smallest frontier source."""
+    N = 20_000
+    hg = gg.from_edge_list(N + 1, [(0, i) for i in range(1, N + 1)])
+    g = _load(gi, hg)
+    fm = np.zeros(hg.n, np.uint8)
+    fm[[15_000, 17_500, 19_999]] = 1
+    tm = np.zeros(hg.n, np.uint8)
+    tm[[0, 3, 4]] = 1 if hub_in_to else 0
+    tm[[3, 4]] = 1
+    depth = torch.full((hg.n,), -1, dtype=torch.int32, device="cuda")
+    depth[torch.from_numpy(np.flatnonzero(fm)).cuda()] = 0
+    parent = torch.full((hg.n,), -1, dtype=torch.int32, device="cuda")
+    OUT = gi.VertexSet(g)
+    gi.edgeset_apply(g, _mask_set(gi, g, fm), _mask_set(gi, g, tm), gi.schedule("dense_pull"), gi.GI_K_BFS,
+                     gi.gi_bfs_args(depth.data_ptr(), parent.data_ptr(), 1), OUT)
+    d, p, out = _np(depth), _np(parent), np.sort(_np(OUT.export()))
+    if hub_in_to:
+        assert d[0] == 1 and p[0] == 15_000 and out.tolist() == [0]
+    else:
+        assert d[0] == -1 and out.size == 0
+    assert d[3] == -1 and d[4] == -1  # leaves 3 and 4: their only in-neighbour (the hub) is not in F
