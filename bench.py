@@ -1,17 +1,23 @@
 #!/usr/bin/env python
 """Benchmark of the edgeset-apply hot path on one GB300 (or N replicas).
 
-Workload (one "step"): on a symmetrized R-MAT graph of scale 22 (edge factor
-16, a=.57 b=.19 c=.19, seed 1; ~4.19M vertices, ~128M arcs), run
-  PageRank        20 iterations, damping 0.85, DensePull (FP32, FP64 normalisation)
-  PageRankDelta   10 rounds, eps 1e-7, hybrid DensePull-SparsePush
-  CC              label propagation to convergence, hybrid DensePull-SparsePush
-Value = arcs traversed by the step / step time, in GTEPS (10^9 arcs/s): PR
-counts iters*m, PRD and CC count m for pull rounds and m_f (the frontier's
-out-degree sum) for push rounds.  Inputs (CSR ~0.5 GB) exceed the 126 MB L2.
+Workload (one "step", the default): on a symmetrized R-MAT graph of scale 24
+(edge factor 16, a=.57 b=.19 c=.19, seed 1; 16.8M vertices, ~521M arcs, int32
+arc weights uniform in [1,1000) from the pair hash), run from each of 64 seeded
+sources (uniform among vertices of degree >= 1)
+  BFS    depth + canonical (smallest-id) parent
+  SSSP   Bellman-Ford distances
+with the direction of every level chosen by the learned selector.  Value =
+arcs of the reached components (per query the sum of the reached vertices'
+degrees) / step time, in GTEPS (10^9 arcs/s).  Beside it: Beamer's rule
+(SSSP: Ligra's |F| + m_f > m/20) on the same queries, three interleaved
+repeats of each, the BFS level loop as a CUDA graph, and the exhaustive
+best-direction-per-level sum; the PR + PRD + CC step on R-MAT 22 rides along
+as an extra.  Inputs (CSR + weights ~4.2 GB) exceed the 126 MB L2.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
-bounded sample of the same workload instead.
+bounded sample of the same workload instead.  --workload selects the other
+configurations, each printing its own line.
 """
 from __future__ import annotations
 
@@ -39,18 +45,24 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["gi", "reference"], default="gi")
-    p.add_argument("--scale", type=int, default=22)
-    p.add_argument("--e2e-steps", type=int, default=16)
-    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--scale", type=int, default=24, help="R-MAT scale of the BFS/SSSP workload")
+    p.add_argument("--m-scale", type=int, default=22, help="R-MAT scale of the PR/PRD/CC workload (and BC)")
+    p.add_argument("--m-steps", type=int, default=5, help="timed steps of the PR/PRD/CC extra")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--repeats", type=int, default=3, help="repeats of the learned vs Beamer comparison")
+    p.add_argument("--exhaustive-sources", type=int, default=8)
+    p.add_argument("--cpu-sources", type=int, default=4, help="sources of the CPU oracle sample (BFS + SSSP)")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="PR/PRD/CC workload: CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--tune-budget", type=int, default=12, help="autotuner trials per algorithm (untimed)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the untimed autotuning and direction comparison (profiling runs)")
-    p.add_argument("--workload", choices=["rmat22", "rmat24_bfs_sssp", "rmat24_levels", "grid4096", "batch512", "bc"],
-                   default="rmat22",
-                   help="rmat22 (default): the timed PR+PRD+CC step; the others measure the remaining "
+    p.add_argument("--workload", choices=["rmat24_bfs_sssp", "rmat22", "rmat24_levels", "grid4096", "batch512", "bc"],
+                   default="rmat24_bfs_sssp",
+                   help="rmat24_bfs_sssp (default): BFS + SSSP from 64 sources on R-MAT 24, learned vs Beamer, "
+                        "with the PR+PRD+CC step on R-MAT 22 as an extra; the others measure the remaining "
                         "configurations and print their own JSON line")
-    p.add_argument("--sources", type=int, default=16, help="sources per graph for the BFS/SSSP workloads")
+    p.add_argument("--sources", type=int, default=64, help="sources per graph for the BFS/SSSP workloads")
     p.add_argument("--only", choices=["pagerank", "pagerank_delta", "cc", "bfs", "sssp", "bc"], default=None,
                    help="profiling case: run just this algorithm --steps times on the workload graph")
     p.add_argument("--hot-cache", type=int, choices=[0, 1, 2], default=0,
@@ -91,29 +103,34 @@ def oracle_sample(hg, seconds):
 
 
 def run_reference(args):
+    """The oracle on the BFS/SSSP workload: each step is one oracle query (BFS
+    with parents, then SSSP, alternating over the 64 sources), single-threaded
+    C; the steps run on the host cores at once, so value = arcs of the timed
+    queries / wall time of the timed region on `cores` threads."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
+    import numpy as np
     import graphgen as gg
-    import oracle
-    oracle.build()
-    hg = gg.rmat_graph(args.scale, seed=1)
-    iters = 2
-    times = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        oracle.pagerank(hg, DAMPING, iters)
-        dt = time.perf_counter() - t0
-        if i >= args.warmup:
-            times.append(dt)
-    total = sum(times)
-    value = args.steps * iters * hg.m / total / 1e9
-    sample = f"oracle PageRank, {iters} iterations per step on the full scale-{args.scale} graph (single thread)"
+    hg = gg.rmat_graph(args.scale, seed=1, weights=(1, 1000))
+    srcs = [int(x) for x in gg.pick_sources(hg, args.sources, seed=1)]
+    qs = [("bfs" if i % 2 == 0 else "sssp", srcs[(i // 2) % len(srcs)]) for i in range(args.warmup + args.steps)]
+    cores, model = host_cpu()
+    threads = max(1, min(cores, len(qs)))
+    if args.warmup:
+        oracle_queries(hg, qs[:args.warmup], threads)
+    timed = qs[args.warmup:]
+    secs, arcs = oracle_queries(hg, timed, min(threads, max(1, len(timed))))
+    value = arcs / secs / 1e9
+    used = min(threads, max(1, len(timed)))
+    sample = (f"{len(timed)} oracle queries (BFS with parents / SSSP alternating over the seeded sources) of "
+              f"the scale-{args.scale} workload, one per step, on {used} threads at once")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(hg, args.scale),
-            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": l_config(hg, len(srcs)),
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": used, "kind": "oracle", "sample": sample,
+                             "host": {"nproc": cores, "model": model, "used": f"{used} of {cores} cores"}},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -216,40 +233,45 @@ def measured_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def run_gi(args):
+def run_rmat22(args, extra=False):
+    """The PageRank + PageRankDelta + CC step on R-MAT scale --m-scale.  As the
+    workload of `--workload rmat22` it prints its own line; with extra=True it
+    runs --m-steps timed steps (no end-to-end, comparison or CPU legs) and
+    returns the line for embedding in the BFS/SSSP line."""
     import numpy as np
     import torch
     import torch.distributed as dist
 
     world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
+    if not extra:
+        torch.cuda.set_device(local)
+        if world > 1:
+            dist.init_process_group("nccl")
     import graphgen as gg
     import paper_1805_00923_gb300 as gi
 
-    hg = gg.rmat_graph(args.scale, seed=1)
+    steps = args.m_steps if extra else args.steps
+    hg = gg.rmat_graph(args.m_scale, seed=1)
     n, m = hg.n, hg.m
     stream = torch.cuda.current_stream()
     g = gi.Graph.from_host(hg)
     # the autotuner picks tile shape / thresholds / segment count (untimed setup)
-    if args.no_extras:
-        args.tune_budget = 1
+    tune_budget = 1 if args.no_extras else args.tune_budget
     # PageRank / PageRankDelta start from the L1-resident hot-source pull
     # (faster on R-MAT at these sizes); the tuner may move every knob
     pr_s, pr_tuned_ms, pr_start_ms = gi.autotune(g, "pagerank", start=gi.schedule("dense_pull", hot_cache=2),
-                                                 budget=args.tune_budget, seed=1)
+                                                 budget=tune_budget, seed=1)
     prd_s, prd_tuned_ms, prd_start_ms = gi.autotune(g, "pagerank_delta",
                                                     start=gi.schedule("hybrid_pull", hot_cache=2),
-                                                    budget=args.tune_budget, seed=2)
+                                                    budget=tune_budget, seed=2)
     cc_s, cc_tuned_ms, cc_start_ms = gi.autotune(g, "cc", start=gi.schedule("hybrid_pull", hot_cache=2),
-                                                 budget=args.tune_budget, seed=3)
+                                                 budget=tune_budget, seed=3)
     tuned = {"pagerank": dict(gi.schedule_dict(pr_s), tuned_ms=pr_tuned_ms, default_ms=pr_start_ms),
              "pagerank_delta": dict(gi.schedule_dict(prd_s), tuned_ms=prd_tuned_ms, default_ms=prd_start_ms),
              "cc": dict(gi.schedule_dict(cc_s), tuned_ms=cc_tuned_ms, default_ms=cc_start_ms)}
     # the three PageRank directions of the workload, one timed run each (untimed setup)
     compare = {}
-    for name, sc in ([] if args.no_extras else
+    for name, sc in ([] if (args.no_extras or extra) else
                      [("dense_pull", gi.schedule("dense_pull")),
                       ("dense_pull_hot_cache", gi.schedule("dense_pull", hot_cache=1)),
                       ("segmented_pull_4", gi.schedule("dense_pull", num_segments=4)),
@@ -269,6 +291,7 @@ def run_gi(args):
     tr_p, tr_c = gi.Trace(64), gi.Trace(256)
 
     def traversed(tr):
+        """PageRankDelta's actual work: m per pull round, m_f per push round."""
         t = tr.as_dict()
         return int(sum(m if d == gi.GI_DIR_DENSE_PULL else e for d, e in zip(t["direction"], t["edges"])))
 
@@ -291,12 +314,13 @@ def run_gi(args):
             ev[3].record()
         if after:
             after(2)
-        return PR_ITERS * m, traversed(tr_p), traversed(tr_c)
+        # CC reaches every vertex: sum of degrees = m, counted once
+        return PR_ITERS * m, traversed(tr_p), m
 
     for _ in range(args.warmup):
         step(g)
     torch.cuda.synchronize()
-    if world > 1:
+    if world > 1 and not extra:
         dist.barrier()
     torch.cuda.synchronize()
 
@@ -305,15 +329,15 @@ def run_gi(args):
     time.sleep(0.3)
     gi.stats_reset()
     gi.stats_enable(True)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     edges = np.zeros(3, np.float64)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record()
-    for k in range(args.steps):
+    for k in range(steps):
         edges += step(g, evs[k])
     stop.record()
     torch.cuda.synchronize()
-    if world > 1:
+    if world > 1 and not extra:
         dist.barrier()
     torch.cuda.synchronize()
     gi.stats_enable(False)
@@ -323,10 +347,13 @@ def run_gi(args):
     per_alg_ms = np.zeros(3)
     for ev in evs:
         per_alg_ms += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
-    if world > 1:
+    if world > 1 and not extra:
         from paper_1805_00923_gb300 import replicas
         total_ms = replicas.max_over_ranks(total_ms, device="cuda")
-    value = world * edges.sum() / (total_ms * 1e-3) / 1e9
+    value = (1 if extra else world) * edges.sum() / (total_ms * 1e-3) / 1e9
+    if extra:
+        return rmat22_summary(args, hg, g, steps, value, total_ms, per_alg_ms, edges, launches, pr_launches, pr_ms,
+                              pr_s, tuned, clocks)
 
     # end to end through the C ABI from pinned host buffers
     rp_h = torch.from_numpy(hg.row_ptr).pin_memory()
@@ -430,18 +457,18 @@ def run_gi(args):
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     hot = int(pr_s.hot_cache) if pr_s.direction == gi.GI_DIR_DENSE_PULL and pr_s.num_segments == 1 else 0
     kname = {0: "k_pull_tiled_OpPR", 1: "k_pull_hot_OpPR", 2: "k_pull_tiled_hotL1_OpPR"}[hot]
-    traffic = recorded_traffic(kname, f"rmat{args.scale}")
+    traffic = recorded_traffic(kname, f"rmat{args.m_scale}")
 
-    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(hg, args.scale),
+            "config": workload_config(hg, args.m_scale),
             "per_algorithm": {
-                "pagerank": {"gteps": edges[0] / (per_alg_ms[0] * 1e-3) / 1e9, "ms": per_alg_ms[0] / args.steps},
+                "pagerank": {"gteps": edges[0] / (per_alg_ms[0] * 1e-3) / 1e9, "ms": per_alg_ms[0] / steps},
                 "pagerank_delta": {"gteps": edges[1] / (per_alg_ms[1] * 1e-3) / 1e9,
-                                   "gteps_nominal": PRD_ITERS * m * args.steps / (per_alg_ms[1] * 1e-3) / 1e9,
-                                   "ms": per_alg_ms[1] / args.steps},
-                "cc": {"gteps": edges[2] / (per_alg_ms[2] * 1e-3) / 1e9, "ms": per_alg_ms[2] / args.steps}},
+                                   "gteps_nominal": PRD_ITERS * m * steps / (per_alg_ms[1] * 1e-3) / 1e9,
+                                   "ms": per_alg_ms[1] / steps},
+                "cc": {"gteps": edges[2] / (per_alg_ms[2] * 1e-3) / 1e9, "ms": per_alg_ms[2] / steps}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": {0: "k_pull_tiled<OpPR> (PageRank DensePull iteration)",
@@ -514,7 +541,7 @@ def run_bc(args):
     from paper_1805_00923_gb300 import selector as sel
     torch.cuda.set_device(0)
     sel.install()
-    hg = gg.rmat_graph(args.scale, seed=1)
+    hg = gg.rmat_graph(args.m_scale, seed=1)
     g = gi.Graph.from_host(hg)
     srcs = [int(x) for x in gg.pick_sources(hg, 10, seed=1)]
     out = {}
@@ -538,7 +565,7 @@ def run_bc(args):
     oracle.bc(hg, srcs[0])
     cpu_ms = (_time.perf_counter() - t0) * 1e3
     best = min(out.values(), key=lambda r: r["ms_per_source"])
-    print(json.dumps({"metric": METRIC, "workload": f"rmat{args.scale}_bc10", "value": out["hybrid_pull"]["gteps_nominal"],
+    print(json.dumps({"metric": METRIC, "workload": f"rmat{args.m_scale}_bc10", "value": out["hybrid_pull"]["gteps_nominal"],
                       "unit": "GTEPS", "n": hg.n, "m": hg.m, "sources": len(srcs), "results": out,
                       "best_ms_per_source": best["ms_per_source"],
                       "cpu_baseline": {"kind": "oracle", "cores": 1, "ms_per_source": cpu_ms,
@@ -547,59 +574,333 @@ def run_bc(args):
     return 0
 
 
-def run_rmat24(args):
-    """R-MAT scale 24, BFS + SSSP from --sources sources: Beamer vs learned vs exhaustive best per level."""
+def _sssp_pull_bytes(n, m, tr):
+    """Algorithmic bytes of the SSSP DensePull rounds of one traced query:
+    4(V+1) offsets + 8m (index and frontier test per arc) + 8 m_f (weight and
+    distance per frontier arc) + V/4 (bitmaps) + 4|F_next| per pull round."""
+    t = tr.as_dict()
+    fr, ed, dr = t["frontier"], t["edges"], t["direction"]
+    total, rounds = 0, 0
+    for i in range(len(dr)):
+        if dr[i] == 2:  # GI_DIR_DENSE_PULL
+            nxt = int(fr[i + 1]) if i + 1 < len(fr) else 0
+            total += 4 * (n + 1) + 8 * m + 8 * int(ed[i]) + n // 4 + 4 * nxt
+            rounds += 1
+    return total, rounds
+
+
+def host_cpu():
+    """(nproc, CPU model name) of this host."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model Name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_queries(hg, queries, threads):
+    """Run oracle BFS / SSSP queries [(algo, src)] on `threads` host threads
+    (each oracle call is single-threaded C that releases the interpreter lock);
+    returns (wall seconds, arcs = sum over queries of the reached vertices' degrees)."""
+    import concurrent.futures as cf
+    import numpy as np
+    import oracle
+    oracle.build()
+    deg = np.diff(hg.row_ptr).astype(np.int64)
+
+    def one(q):
+        algo, s = q
+        if algo == "bfs":
+            d = oracle.bfs(hg, s)[0]
+            return int(deg[d >= 0].sum())
+        d = oracle.sssp(hg, s)[0]
+        return int(deg[d < np.iinfo(np.int32).max].sum())
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        arcs = sum(ex.map(one, queries))
+    return time.perf_counter() - t0, arcs
+
+
+def l_config(hg, n_sources):
+    return {"workload": "rmat24_bfs_sssp", "graph": "R-MAT symmetrized, int32 weights uniform in [1,1000)",
+            "scale": max(0, int(hg.n).bit_length() - 1), "edge_factor": 16, "abc": [0.57, 0.19, 0.19],
+            "seed": 1, "n": hg.n, "m": hg.m, "sources": n_sources,
+            "sources_rule": "uniform among vertices of degree >= 1, seeded (pick_sources seed 1)",
+            "step": f"BFS (depth + canonical parent) then SSSP (distance) from each of the {n_sources} sources",
+            "gteps_numerator": "per query the sum of degrees of the reached vertices (arcs of the reached "
+                               "component, both directions); Graph500 count = half",
+            "schedule": "learned selector per level (SparsePush / DensePush / DensePull), library defaults",
+            "l2": "inputs larger than L2 (CSR + weights %.2f GB vs 126 MB L2); no flush"
+                  % ((4 * (hg.n + 1) + 8 * hg.m) / 1e9)}
+
+
+def run_config_l(args):
+    """R-MAT scale 24 (weights [1,1000)), BFS + SSSP from 64 seeded sources:
+    the timed step runs every source under the learned selector; Beamer's rule
+    (Ligra's |F| + m_f > m/20 for SSSP) and the exhaustive per-level optimum are
+    measured beside it."""
     import numpy as np
     import torch
+    import torch.distributed as dist
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
     import graphgen as gg
     import paper_1805_00923_gb300 as gi
     from paper_1805_00923_gb300 import selector as sel
-    torch.cuda.set_device(0)
     sel.install()
-    hg = gg.rmat_graph(24, seed=1, weights=(1, 1000))
+    hg = gg.rmat_graph(args.scale, seed=1, weights=(1, 1000))
+    n, m = hg.n, hg.m
     g = gi.Graph.from_host(hg)
-    srcs = gg.pick_sources(hg, args.sources, seed=1)
-    out = {}
-    for algo in ("bfs", "sssp"):
-        res = {}
-        for pol in ("hybrid_pull", "learned"):
-            ms, edges = 0.0, 0
-            for s_ in srcs:
-                tr = gi.Trace(4096)
-                run = (lambda: gi.bfs(g, int(s_), want_parent=False, sched=gi.schedule(pol), trace=tr)) \
-                    if algo == "bfs" else (lambda: gi.sssp(g, int(s_), sched=gi.schedule(pol), trace=tr))
-                run()
-                a, b = _events()
-                a.record()
-                run()
-                b.record()
-                torch.cuda.synchronize()
-                ms += a.elapsed_time(b)
-                edges += int(tr.as_dict()["edges"].sum())
-            res[pol] = {"gteps": edges / (ms * 1e-3) / 1e9, "ms_per_query": ms / len(srcs)}
-            if algo == "bfs":  # Graph500 counts each undirected edge once
-                res[pol]["gteps_graph500"] = res[pol]["gteps"] / 2
-        if algo == "bfs":  # the same queries with the level loop as a CUDA graph
-            gsc = gi.schedule("hybrid_pull", persistent=2)
-            gi.bfs(g, int(srcs[0]), want_parent=False, sched=gsc)
-            a, b = _events()
-            a.record()
-            for s_ in srcs:
-                gi.bfs(g, int(s_), want_parent=False, sched=gsc)
-            b.record()
+    # replicas: rank r serves its own 64 seeded sources (weak scaling)
+    srcs = [int(x) for x in gg.pick_sources(hg, args.sources, seed=1 + rank)]
+    pols = {"learned": (gi.schedule("learned"), gi.schedule("learned")),
+            "beamer": (gi.schedule("hybrid_pull"), gi.schedule("hybrid_pull"))}
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    dist_ = torch.empty(n, dtype=torch.int32, device="cuda")
+    deg = torch.from_numpy(np.diff(hg.row_ptr).astype(np.int64)).cuda()
+    # per-query GTEPS numerator: arcs of the reached component (BFS and SSSP
+    # reach the same vertices: weights are positive), untimed
+    reach = {}
+    for s_ in srcs:
+        gi.bfs(g, s_, want_parent=False, sched=pols["learned"][0], out=(depth, None))
+        reach[s_] = int(deg[depth >= 0].sum())
+    arcs_per_step = 2 * sum(reach.values())
+    traces = {s_: gi.Trace(4096) for s_ in srcs}
+
+    def one_pass(pol, ev=None):
+        bs, ss = pols[pol]
+        for i, s_ in enumerate(srcs):
+            gi.bfs(g, s_, sched=bs, out=(depth, parent))
+            if ev is not None:
+                ev[i].record()
+            gi.sssp(g, s_, sched=ss, trace=traces[s_], out=dist_)
+        return arcs_per_step
+
+    for _ in range(args.warmup):
+        one_pass("learned")
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    gi.stats_reset()
+    gi.stats_enable(True)
+    start, stop = _events()
+    start.record()
+    for _ in range(args.steps):
+        one_pass("learned")
+    stop.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    gi.stats_enable(False)
+    launches, pull_launches, pull_ms = gi.stats_read("min_pull")
+    clocks = sampler.stop()
+    total_ms = start.elapsed_time(stop)
+    if world > 1:
+        from paper_1805_00923_gb300 import replicas
+        total_ms = replicas.max_over_ranks(total_ms, device="cuda")
+    value = world * args.steps * arcs_per_step / (total_ms * 1e-3) / 1e9
+
+    # roofline: the SSSP DensePull rounds (k_pull_tiled<OpMinInt>), CUDA-event
+    # timed per launch on the launching stream inside the timed region
+    pull_bytes, pull_rounds = 0, 0
+    for s_ in srcs:
+        b_, r_ = _sssp_pull_bytes(n, m, traces[s_])
+        pull_bytes += b_
+        pull_rounds += r_
+    pull_bytes *= args.steps
+    peak, peak_kind = measured_hbm()
+    achieved = pull_bytes / (pull_ms * 1e-3) / 1e9 if pull_ms > 0 else 0.0
+
+    # per algorithm, learned vs Beamer, 3 interleaved repeats each (outside the timed region)
+    def per_alg(pol):
+        bs, ss = pols[pol]
+        a0, a1 = _events()
+        b_ms = s_ms = 0.0
+        for s_ in srcs:
+            a0.record()
+            gi.bfs(g, s_, sched=bs, out=(depth, parent))
+            a1.record()
             torch.cuda.synchronize()
-            res["graph_driven_ms_per_query"] = a.elapsed_time(b) / len(srcs)
-        best_ms = 0.0
-        for s_ in srcs[:max(1, len(srcs) // 4)]:
-            f, t = sel.profile(g, gi.GI_K_BFS if algo == "bfs" else gi.GI_K_SSSP, int(s_))
-            best_ms += float(t.min(axis=1).sum())
-        res["exhaustive_best_ms_per_query"] = best_ms / max(1, len(srcs) // 4)
-        out[algo] = res
-    val = (out["bfs"]["learned"]["gteps"] + out["sssp"]["learned"]["gteps"]) / 2
-    print(json.dumps({"metric": METRIC, "workload": "rmat24_bfs_sssp", "value": val, "unit": "GTEPS",
-                      "n": hg.n, "m": hg.m, "sources": len(srcs), "results": out,
-                      "note": "value = mean of BFS and SSSP GTEPS under the learned selector; edges = sum of m_f"}))
+            b_ms += a0.elapsed_time(a1)
+            a0.record()
+            gi.sssp(g, s_, sched=ss, out=dist_)
+            a1.record()
+            torch.cuda.synchronize()
+            s_ms += a0.elapsed_time(a1)
+        half = arcs_per_step / 2
+        return {"bfs_gteps": half / (b_ms * 1e-3) / 1e9, "sssp_gteps": half / (s_ms * 1e-3) / 1e9,
+                "gteps": arcs_per_step / ((b_ms + s_ms) * 1e-3) / 1e9,
+                "bfs_ms_per_query": b_ms / len(srcs), "sssp_ms_per_query": s_ms / len(srcs)}
+
+    reps = {"learned": [], "beamer": []}
+    for _ in range(args.repeats):
+        for pol in ("learned", "beamer"):
+            reps[pol].append(per_alg(pol))
+    compare = {}
+    for pol, rs in reps.items():
+        d = {}
+        for k in rs[0]:
+            vals = [r[k] for r in rs]
+            d[k] = {"mean": float(np.mean(vals)), "min": float(np.min(vals)), "max": float(np.max(vals))}
+        compare[pol] = d
+    for k in ("bfs_gteps", "sssp_gteps", "gteps"):
+        compare.setdefault("learned_beats_beamer", {})[k] = \
+            compare["learned"][k]["min"] > compare["beamer"][k]["max"]
+    # the same BFS queries with the level loop as a CUDA graph (no host round trip per level)
+    gd = {}
+    for pol, sc in (("graph_driven_rule", gi.schedule("hybrid_pull", persistent=2)),
+                    ("graph_driven_learned", gi.schedule("learned", persistent=2))):
+        gi.bfs(g, srcs[0], sched=sc, out=(depth, parent))
+        a0, a1 = _events()
+        a0.record()
+        for s_ in srcs:
+            gi.bfs(g, s_, sched=sc, out=(depth, parent))
+        a1.record()
+        torch.cuda.synchronize()
+        gd[pol] = {"bfs_ms_per_query": a0.elapsed_time(a1) / len(srcs),
+                   "bfs_gteps": (arcs_per_step / 2) / (a0.elapsed_time(a1) * 1e-3) / 1e9}
+    # exhaustive best direction per level: every level of a query timed under all
+    # three directions from the same state (gi_selector_profile), minima summed
+    nx = max(1, min(len(srcs), args.exhaustive_sources))
+    ex_ms = {"bfs": 0.0, "sssp": 0.0}
+    for s_ in srcs[:nx]:
+        for algo, kid in (("bfs", gi.GI_K_BFS), ("sssp", gi.GI_K_SSSP)):
+            _, t = sel.profile(g, kid, s_)
+            ex_ms[algo] += float(t.min(axis=1).sum())
+    exhaustive = {"sources": nx, "bfs_ms_per_query": ex_ms["bfs"] / nx, "sssp_ms_per_query": ex_ms["sssp"] / nx,
+                  "note": "sum over levels of the fastest direction timed alone, without the per-level statistics "
+                          "kernel and host round trip; BFS without the parent pass"}
+
+    # end to end through the C ABI: CSR + weights from pinned host buffers
+    # (gi_load_csr), every query's depth, parent and distance copied back to
+    # pinned host memory on a side stream as soon as the query ends
+    rp_h = torch.from_numpy(hg.row_ptr).pin_memory()
+    col_h = torch.from_numpy(hg.col).pin_memory()
+    wt_h = torch.from_numpy(hg.wt).pin_memory()
+    slots = 8
+    out_h = [[torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(3)] for _ in range(slots)]
+    side = torch.cuda.Stream()
+    dev_out = [[torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(3)] for _ in range(slots)]
+    slot_free = [None] * slots
+    h2d = 4 * (n + 1) + 8 * m
+    d2h = len(srcs) * 3 * 4 * n
+
+    def e2e_step():
+        ge = gi.Graph(rp_h.numpy(), col_h.numpy(), wt_h.numpy(), symmetric=True)
+        bs, ss = pols["learned"]
+        for i, s_ in enumerate(srcs):
+            k = i % slots
+            if slot_free[k] is not None:
+                slot_free[k].synchronize()  # the host has the slot's previous results
+            dd, pp, ds = dev_out[k]
+            gi.bfs(ge, s_, sched=bs, out=(dd, pp))
+            gi.sssp(ge, s_, sched=ss, out=ds)
+            done = torch.cuda.Event()
+            done.record()
+            side.wait_event(done)
+            with torch.cuda.stream(side):
+                for j in range(3):
+                    out_h[k][j].copy_(dev_out[k][j], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record()
+            slot_free[k] = ev
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.current_stream().synchronize()
+        ge.free()
+
+    e2e_step()  # warm-up (allocator pool, pinned slabs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        from paper_1805_00923_gb300 import replicas
+        e2e_s = replicas.max_over_ranks(e2e_s, device="cuda")
+    e2e_value = world * args.e2e_steps * arcs_per_step / e2e_s / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": l_config(hg, len(srcs)),
+            "per_algorithm": {"learned": compare["learned"], "beamer": compare["beamer"],
+                              "repeats": args.repeats, "learned_beats_beamer_beyond_spread":
+                                  compare["learned_beats_beamer"],
+                              "graph_driven_bfs": gd, "exhaustive_best_per_level": exhaustive,
+                              "gteps_graph500": value / 2},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_pull_tiled<OpMinInt> (SSSP DensePull round, frontier folded into the "
+                                   "gathered start-of-round distances)",
+                         "bytes_model": "per pull round 4(V+1) + 8m + 8 m_f + V/4 + 4|F_next|",
+                         "launches_timed": pull_launches, "pull_rounds_expected": pull_rounds * args.steps,
+                         "avg_launch_ms": pull_ms / max(pull_launches, 1),
+                         "peak_kind": f"{peak_kind} hbm_gbs (burst copy; the kernel runs inside a long step)"},
+            "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1e3 * e2e_s / args.e2e_steps, "steps": args.e2e_steps,
+                    "form": "gi_load_csr from pinned host CSR + weights, then the 64 BFS + SSSP queries; each "
+                            "query's depth, parent and distance copied to pinned host memory on a side stream "
+                            "(8 result slots reused once the host has them); load, queries and copies timed"},
+            "gpu_launches": launches, "clocks": clocks}
+    if not args.no_extras:
+        line["config_m_pr_prd_cc"] = run_rmat22(args, extra=True)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nq = min(args.cpu_sources, len(srcs))
+        qs = [(a_, s_) for s_ in srcs[:nq] for a_ in ("bfs", "sssp")]
+        secs, arcs = oracle_queries(hg, qs, len(qs))
+        cores, model = host_cpu()
+        line["cpu_baseline"] = {"value": arcs / secs / 1e9, "unit": "GTEPS", "cores": len(qs), "kind": "oracle",
+                                "sample": f"oracle BFS (depth + parent) and SSSP from {nq} of the {len(srcs)} "
+                                          f"sources, each query single-threaded, {len(qs)} queries on {len(qs)} "
+                                          f"threads at once ({secs:.1f} s wall)",
+                                "host": {"nproc": cores, "model": model,
+                                         "used": f"{len(qs)} of {cores} cores"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.free()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
+
+
+def rmat22_summary(args, hg, g, steps, value, total_ms, per_alg_ms, edges, launches, pr_launches, pr_ms, pr_s,
+                   tuned, clocks):
+    """The config-M step's numbers, for embedding in the BFS/SSSP line."""
+    import paper_1805_00923_gb300 as gi
+    m, n = hg.m, hg.n
+    peak, peak_kind = measured_hbm()
+    avg_ms = pr_ms / max(pr_launches, 1)
+    achieved = (8 * m + 12 * n + 4) / (avg_ms * 1e-3) / 1e9
+    out = {"workload": workload_config(hg, args.m_scale), "value": value, "unit": "GTEPS", "steps": steps,
+           "ms_per_step": total_ms / steps,
+           "per_algorithm": {
+               "pagerank": {"gteps": edges[0] / (per_alg_ms[0] * 1e-3) / 1e9, "ms": per_alg_ms[0] / steps},
+               "pagerank_delta": {"gteps": edges[1] / (per_alg_ms[1] * 1e-3) / 1e9,
+                                  "gteps_nominal": PRD_ITERS * m * steps / (per_alg_ms[1] * 1e-3) / 1e9,
+                                  "ms": per_alg_ms[1] / steps},
+               "cc": {"gteps": edges[2] / (per_alg_ms[2] * 1e-3) / 1e9, "ms": per_alg_ms[2] / steps}},
+           "numerators": "PR 20m; PRD m per pull round + m_f per push round; CC m (every vertex reached)",
+           "roofline_pr_pull": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                "bytes_model": "8m + 12n + 4 per launch", "avg_launch_ms": avg_ms,
+                                "launches_timed": pr_launches, "peak_kind": f"{peak_kind} hbm_gbs"},
+           "autotuned": tuned, "gpu_launches": launches, "clocks": clocks}
+    g.free()
+    return out
 
 
 def _bfs_level_bytes(depth, col, row, row_ptr, deg, levels):
@@ -814,12 +1115,10 @@ def main():
     args = parse()
     if args.only:
         return run_only(args)
-    if args.impl == "gi" and args.workload != "rmat22":
-        return {"rmat24_bfs_sssp": run_rmat24, "rmat24_levels": run_levels, "grid4096": run_grid4096,
-                "batch512": run_batch512, "bc": run_bc}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
-    return run_gi(args)
+    return {"rmat24_bfs_sssp": run_config_l, "rmat22": run_rmat22, "rmat24_levels": run_levels,
+            "grid4096": run_grid4096, "batch512": run_batch512, "bc": run_bc}[args.workload](args)
 
 
 if __name__ == "__main__":

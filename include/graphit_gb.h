@@ -369,7 +369,11 @@ int gi_pagerank(gi_graph *g, float damping, int32_t iters, float *rank_dev, cons
  * rejected with GI_ERR_INVALID_ARG before any work is queued.  No cudaMalloc,
  * cudaFree or allocating library routine is called.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
+ * device current; make that first call before any stream capture.  Under lazy
+ * module loading (the CUDA default) the driver reserves the array when that
+ * first call loads the library's module on the device, so the first call may
+ * itself need the ~8 MB: make it during set-up, while memory is still
+ * available, and every later call reuses the array.  All calls
  * share the one array and the kernels re-initialise what they read, so
  * results do not depend on earlier calls -- but calls whose work overlaps on
  * the GPU (different streams, or host threads) race on the array and must be

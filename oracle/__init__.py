@@ -60,7 +60,7 @@ def _load():
             "or_cc": (_i32, [_i64, _I32, _I32, _I32, _I64, _i32]),
             "or_bc": (_i32, [_i64, _I32, _I32, _I32, _I32, _i32, _F64, _F64]),
             "or_pagerank": (None, [_i64, _I32, _I32, _I32, _f64, _i32, _i32, _F64]),
-            "or_prdelta": (None, [_i64, _I32, _I32, _f64, _f64, _i32, _F64, _I64]),
+            "or_prdelta": (None, [_i64, _I32, _I32, _f64, _f64, _i32, _F64, _I64, _F64, _F64]),
             "or_frontier_stats": (None, [_i64, _I32, _U8, _U8, _I64]),
             "or_beamer": (_i32, [_i64, _i64, _i64, _i64, _i32, _f64, _f64]),
             "or_ligra_dense": (_i32, [_i64, _i64, _i64]),
@@ -175,13 +175,19 @@ def pagerank(g, damping=0.85, iters=20, normalize=True, in_edges=None):
     return rank
 
 
-def prdelta(g, damping=0.85, eps=1e-7, iters=10):
-    """(rank, frontier_sizes) of PageRankDelta (Fig. 1 / Fig. 3)."""
+def prdelta(g, damping=0.85, eps=1e-7, iters=10, history=False):
+    """(rank, frontier_sizes) of PageRankDelta (Fig. 1 / Fig. 3).  With
+    history=True also (delta_hist, rank_hist), each iters x n: Delta and Rank
+    of every vertex at the end of each round."""
     G = _G(g)
     rank = np.empty(G.n, np.float64)
     fs = np.zeros(max(iters, 1), np.int64)
+    dh = np.empty((max(iters, 1), G.n), np.float64) if history else None
+    rh = np.empty((max(iters, 1), G.n), np.float64) if history else None
     _load().or_prdelta(G.n, _ptr(G.rp, _I32), _ptr(G.ci, _I32), float(damping), float(eps), int(iters),
-                       _ptr(rank, _F64), _ptr(fs, _I64))
+                       _ptr(rank, _F64), _ptr(fs, _I64), _ptr(dh, _F64), _ptr(rh, _F64))
+    if history:
+        return rank, fs[:iters].copy(), dh[:iters], rh[:iters]
     return rank, fs[:iters].copy()
 
 

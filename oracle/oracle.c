@@ -320,9 +320,12 @@ void or_pagerank(int64_t n, const int32_t *in_rp, const int32_t *in_ci, const in
  * In round 1, Rank is updated before 1/V is subtracted (the order of the
  * Fig. 3 code); with eps = 0 this makes Rank after round k equal PR_k.
  * frontier_sizes (optional) receives |Frontier| at the start of each round.
+ * delta_hist / rank_hist (optional, max_iter*n doubles each) receive Delta and
+ * Rank of every vertex at the end of each round (row round-1), i.e. the two
+ * values whose comparison |Delta| > eps*Rank decides the next frontier.
  */
 void or_prdelta(int64_t n, const int32_t *rp, const int32_t *ci, double a, double eps, int32_t max_iter,
-                double *rank, int64_t *frontier_sizes) {
+                double *rank, int64_t *frontier_sizes, double *delta_hist, double *rank_hist) {
   double *delta = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double *dsum = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
   uint8_t *front = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
@@ -348,6 +351,8 @@ void or_prdelta(int64_t n, const int32_t *rp, const int32_t *ci, double a, doubl
       dsum[v] = 0.0;
       front[v] = fabs(delta[v]) > eps * rank[v];
     }
+    if (delta_hist) memcpy(delta_hist + (size_t)(round - 1) * (size_t)n, delta, sizeof(double) * (size_t)n);
+    if (rank_hist) memcpy(rank_hist + (size_t)(round - 1) * (size_t)n, rank, sizeof(double) * (size_t)n);
   }
   free(delta); free(dsum); free(front);
 }

@@ -26,15 +26,16 @@ namespace cg = cooperative_groups;
 
 namespace gi {
 
-// this translation unit's copy of the selector weights (see gi_selector_load)
-__device__ float d_sel_params[64 * 16 + 64 + 64 * 64 + 64 + 3 * 64 + 3];
-__device__ float d_sel_mean[16];
-__device__ float d_sel_istd[16];
+// this translation unit's copy of the selector weights (see gi_selector_load);
+// internal linkage, so it never collides with gi_core.cu's copy
+static __device__ float d_bsel_params[64 * 16 + 64 + 64 * 64 + 64 + 3 * 64 + 3];
+static __device__ float d_bsel_mean[16];
+static __device__ float d_bsel_istd[16];
 
 int batch_selector_upload(const float *params, const float *mean, const float *inv_std) {
-  GI_CUDA(cudaMemcpyToSymbol(d_sel_params, params, sizeof(d_sel_params)));
-  GI_CUDA(cudaMemcpyToSymbol(d_sel_mean, mean, sizeof(d_sel_mean)));
-  GI_CUDA(cudaMemcpyToSymbol(d_sel_istd, inv_std, sizeof(d_sel_istd)));
+  GI_CUDA(cudaMemcpyToSymbol(d_bsel_params, params, sizeof(d_bsel_params)));
+  GI_CUDA(cudaMemcpyToSymbol(d_bsel_mean, mean, sizeof(d_bsel_mean)));
+  GI_CUDA(cudaMemcpyToSymbol(d_bsel_istd, inv_std, sizeof(d_bsel_istd)));
   return GI_OK;
 }
 
@@ -132,13 +133,13 @@ __device__ bool batch_decide_pull(const BatchGraph &G, int64_t nf, int64_t mf, i
                                   int32_t was_pull, int64_t nf_prev, int mode, float alpha, float beta, float *sh) {
   if (mode == 2) {
     float *x = sh, *h1 = sh + 16, *h2 = h1 + 64, *y = h2 + 64;
-    const float *W1 = d_sel_params, *b1 = W1 + 64 * 16, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
+    const float *W1 = d_bsel_params, *b1 = W1 + 64 * 16, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
                 *b3 = W3 + 3 * 64;
     const int t = threadIdx.x;
     if (t == 0) {
       float raw[16];
       level_features(raw, G.n, G.m, G.maxdeg, nf, mf, nu, mu, level, was_pull, nf_prev);
-      for (int i = 0; i < 16; ++i) x[i] = (raw[i] - d_sel_mean[i]) * d_sel_istd[i];
+      for (int i = 0; i < 16; ++i) x[i] = (raw[i] - d_bsel_mean[i]) * d_bsel_istd[i];
     }
     __syncthreads();
     if (t < 64) {

@@ -879,20 +879,24 @@ static __global__ void __launch_bounds__(256) k_pull_bfs_deferred(const int32_t 
       const int32_t end = __ldg(ptr + D.row[lo] + 1);
       s_j = lo;
       s_from = from;
-      s_end = *(volatile int32_t *)(D.best + lo) < from ? from : min(from + kBfsDeferChunk, end);
+      // chunk ends and arc positions in 64 bits: from + kBfsDeferChunk may pass
+      // INT32_MAX on graphs with m close to 2^31
+      s_end = *(volatile int32_t *)(D.best + lo) < from
+                  ? from
+                  : (int32_t)min((int64_t)from + kBfsDeferChunk, (int64_t)end);
     }
     __syncthreads();
     const int32_t from = s_from, end = s_end;
     int32_t u[kPer];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-      const int32_t e = from + tid + 256 * k;
+      const int64_t e = (int64_t)from + tid + 256 * k;
       u[k] = e < end ? __ldg(idx + e) : -1;
     }
     int32_t mine = INT32_MAX;
 #pragma unroll
     for (int k = kPer - 1; k >= 0; --k)
-      if (u[k] >= 0 && in_set(F, u[k])) mine = from + tid + 256 * k;
+      if (u[k] >= 0 && in_set(F, u[k])) mine = (int32_t)((int64_t)from + tid + 256 * k);  // < end <= m
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mine = min(mine, __shfl_xor_sync(0xffffffffu, mine, o));
     if (lane == 0) s_min[warp] = mine;

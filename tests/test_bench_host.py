@@ -47,11 +47,22 @@ def test_bfs_level_bytes_match_brute_force():
                               e_scanned=scanned)
 
 
+def test_sssp_pull_bytes_counts_pull_rounds_only():
+    """Per pull round 4(V+1) + 8m + 8 m_f + V/4 + 4|F_next|; push rounds add nothing."""
+    class T:
+        def as_dict(self):
+            return {"frontier": np.array([1, 40, 900, 50]), "edges": np.array([3, 200, 5000, 300]),
+                    "direction": np.array([0, 2, 2, 0])}
+    n, m = 1000, 20000
+    want = sum(4 * (n + 1) + 8 * m + 8 * e + n // 4 + 4 * nx for e, nx in ((200, 900), (5000, 50)))
+    assert bench._sssp_pull_bytes(n, m, T()) == (want, 2)
+
+
 def test_reference_arm_json_line():
     """`--impl reference` prints one JSON line with the contract's keys and
-    exits 0 (oracle PageRank on a small graph)."""
+    exits 0 (oracle BFS / SSSP queries of the BFS/SSSP workload on a small graph)."""
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--scale", "12",
-                        "--steps", "1", "--warmup", "0", "--cpu-seconds", "0.2"],
+                        "--steps", "2", "--warmup", "1"],
                        capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
@@ -62,4 +73,5 @@ def test_reference_arm_json_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["config"]["workload"] == "rmat24_bfs_sssp" and d["config"]["sources"] == 64

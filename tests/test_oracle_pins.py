@@ -265,6 +265,26 @@ def test_prdelta_eps0_equals_pagerank_iterates():
     assert fs[0] == g.n
 
 
+def test_prdelta_history_matches_pagerank_iterates_and_frontiers():
+    """The per-round history: with eps = 0, Rank after round k is PR_k and
+    Delta after round k is PR_k - PR_{k-1} (PR_0 = 1/V, Fig. 1's Delta), both
+    from the independently pinned power iteration; with eps > 0 the frontier
+    entering round k+1 is {v : |Delta_k(v)| > eps * Rank_k(v)}."""
+    g = gg.rmat_graph(10)
+    k = 6
+    rank, fs, dh, rh = oracle.prdelta(g, 0.85, 0.0, k, history=True)
+    prev = np.full(g.n, 1.0 / g.n)
+    for r in range(k):
+        pr = oracle.pagerank(g, 0.85, r + 1, normalize=False)
+        assert np.allclose(rh[r], pr, rtol=1e-11, atol=1e-15), r
+        assert np.allclose(dh[r], pr - prev, rtol=1e-9, atol=1e-15), r
+        prev = pr
+    assert np.array_equal(rh[-1], rank)
+    rank, fs, dh, rh = oracle.prdelta(g, 0.85, 1e-2, 8, history=True)
+    for r in range(1, 8):
+        assert fs[r] == int(np.sum(np.abs(dh[r - 1]) > 1e-2 * rh[r - 1])), r
+
+
 def test_prdelta_huge_eps_freezes_after_round1():
     g = gg.rmat_graph(9)
     r1, _ = oracle.prdelta(g, 0.85, 0.0, 1)
