@@ -238,11 +238,14 @@ typedef struct gi_schedule {
                         /* 512..8192 arcs); 0 = off.  Results are bit-identical to 0.    */
                         /* Ignored elsewhere.  Built once per graph (4m bytes).          */
   int32_t seg_strategy; /* segmented pull (num_segments > 1): GI_SEG_FVC or GI_SEG_EVC    */
+  int32_t delta;        /* gi_sssp only: 0 = Bellman-Ford in synchronous rounds (Sec. 7);  */
+                        /* > 0 = delta-stepping with buckets of this width in weight units */
+                        /* (see gi_sssp); same distances either way                        */
 } gi_schedule;
 
 /* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment (FVC when segmented), 256
  * threads, t_warp 32, t_cta 256, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 256,
- * not persistent, hot_cache 0.  Every driver rejects a schedule with a field out of
+ * not persistent, hot_cache 0, delta 0.  Every driver rejects a schedule with a field out of
  * range with GI_ERR_INVALID_ARG. */
 void gi_schedule_default(gi_schedule *s);
 

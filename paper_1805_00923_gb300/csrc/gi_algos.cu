@@ -322,12 +322,22 @@ static int run_persistent(gi_graph *g, int32_t algo, int32_t src, int32_t *out, 
 // buffer that is copied out after the launch.
 namespace gi {
 
-struct OpBFSDev {  // BFS claim with the level read from the control words
+struct OpBFSDev {  // BFS claim with the level read from the control words; canonical parent as OpBFS
   int32_t *depth;
+  int32_t *parent;
   const int32_t *gm;
-  __device__ bool push(int32_t, int32_t v, int32_t) const {
-    if (*(volatile int32_t *)(depth + v) != -1) return false;
-    return atomicCAS(depth + v, -1, gm[kGmLevel] + 1) == -1;
+  __device__ bool push(int32_t u, int32_t v, int32_t) const {
+    const int32_t lvl = gm[kGmLevel] + 1;
+    const int32_t d = *(volatile int32_t *)(depth + v);
+    if (d != -1 && d != lvl) return false;
+    bool won = false;
+    if (d == -1) {
+      const int32_t old = atomicCAS(depth + v, -1, lvl);
+      won = (old == -1);
+      if (!won && old != lvl) return false;
+    }
+    if (u < *(volatile int32_t *)(parent + v)) atomicMin(parent + v, u);
+    return won;
   }
 };
 
@@ -337,6 +347,7 @@ struct GraphLoop {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int32_t *depth = nullptr;
+  int32_t *parent = nullptr;  // canonical parents, INT32_MAX until found
   int32_t *gm = nullptr;
   gi_vset a, b;
 };
@@ -357,6 +368,7 @@ void graph_loop_free(gi_graph *g) {
     dev_free(v->boolmap, nullptr);
   }
   dev_free(L->depth, nullptr);
+  dev_free(L->parent, nullptr);
   dev_free(L->gm, nullptr);
   delete L;
   g->graph_loop = nullptr;
@@ -378,13 +390,14 @@ static int graph_level(gi_graph *g, const gi_schedule &sc, GraphLoop *L, gi_vset
   GI_TRY(frontier_decide(g, F, p, cs));
   gi_vset Fp = *F;  // the push sees |F| only when this level pushes
   Fp.count = L->gm + kGmPush;
-  const OpBFSDev op{L->depth, L->gm};
+  const OpBFSDev op{L->depth, L->parent, L->gm};
   GI_TRY(launch_push(g, op, kSrcQueue, &Fp, nullptr, out_of(N, false), sc, cs));
   if (g->has_csc) {
     const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
     k_pull_bfs<<<grid_for(g, g->n, 256), 256, 0, cs>>>(g->in.ptr, g->in.idx, g->n,
                                                       FSet(static_cast<const uint32_t *>(F->bitmap)), nullptr,
-                                                      L->depth, nullptr, 0, tw, N->bitmap, N->queue, N->count, L->gm);
+                                                      L->depth, L->parent, 0, tw, N->bitmap, N->queue, N->count,
+                                                      L->gm);
     GI_LAUNCH_CHECK();
   }
   N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
@@ -394,6 +407,7 @@ static int graph_level(gi_graph *g, const gi_schedule &sc, GraphLoop *L, gi_vset
 static int graph_loop_build(gi_graph *g, const gi_schedule &sc, GraphLoop *L, cudaStream_t s) {
   GI_TRY(heavy_get(g, s));
   GI_TRY(dev_alloc_n(&L->depth, g->n, s));
+  GI_TRY(dev_alloc_n(&L->parent, g->n, s));
   GI_TRY(dev_alloc_n(&L->gm, kGmWords, s));
   GI_TRY(vset_alloc(g, &L->a, s));
   GI_TRY(vset_alloc(g, &L->b, s));
@@ -426,9 +440,10 @@ static int graph_loop_build(gi_graph *g, const gi_schedule &sc, GraphLoop *L, cu
   return st;
 }
 
-// BFS depths by the graph-driven loop; levels = number of levels
-static int run_graph_bfs(gi_graph *g, int32_t src, int32_t *depth, const gi_schedule &sched, int32_t *levels,
-                         cudaStream_t s) {
+// BFS depths (and canonical parents, parent may be NULL) by the graph-driven
+// loop; levels = number of levels
+static int run_graph_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent, const gi_schedule &sched,
+                         int32_t *levels, cudaStream_t s) {
   gi_schedule sc = sched;
   sc.balance = sc.balance == GI_BAL_EDGE_PARALLEL ? GI_BAL_EDGE_AWARE : sc.balance;  // needs a host-known |F|
   if (!g->has_csc) sc.direction = GI_DIR_SPARSE_PUSH;
@@ -449,7 +464,7 @@ static int run_graph_bfs(gi_graph *g, int32_t src, int32_t *depth, const gi_sche
       return st;
     }
   }
-  k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(L->depth, nullptr, g->n, src);
+  k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(L->depth, L->parent, g->n, src);
   k_gm_init<<<1, 32, 0, s>>>(L->gm, (int32_t)(g->n + 1 < INT32_MAX ? g->n + 1 : INT32_MAX));
   GI_TRY(launch_status(2));
   GI_TRY(front_init(g, &L->a, src, s));
@@ -457,6 +472,11 @@ static int run_graph_bfs(gi_graph *g, int32_t src, int32_t *depth, const gi_sche
   GI_TRY(ctrl_init(g, g->n, g->m, s));
   GI_CUDA(cudaGraphLaunch(L->exec, s));
   GI_CUDA(cudaMemcpyAsync(depth, L->depth, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
+  if (parent) {
+    GI_CUDA(cudaMemcpyAsync(parent, L->parent, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
+    k_parent_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n);
+    GI_TRY(launch_status(1));
+  }
   int32_t gm[kGmWords];
   GI_CUDA(cudaMemcpyAsync(gm, L->gm, sizeof(gm), cudaMemcpyDeviceToHost, s));
   GI_CUDA(cudaStreamSynchronize(s));
@@ -480,16 +500,16 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
   cudaStream_t s = (cudaStream_t)stream;
   const gi_schedule sc = *sched;
   if (forced_direction(sc.direction) >= 0) GI_TRY(pull_available(g, forced_direction(sc.direction)));
+  if (sc.persistent == 2) {
+    // the graph-driven loop keeps depths and canonical parents itself
+    int32_t levels = 0;
+    GI_TRY(run_graph_bfs(g, src, depth, parent, sc, &levels, s));
+    if (trace) trace->iterations = levels;
+    return GI_OK;
+  }
   if (sc.persistent && (!parent || g->has_csc)) {
-    // depths in one persistent launch or the graph-driven loop; canonical
-    // parents by the in-edge pass
-    if (sc.persistent == 2) {
-      int32_t levels = 0;
-      GI_TRY(run_graph_bfs(g, src, depth, sc, &levels, s));
-      if (trace) trace->iterations = levels;
-    } else {
-      GI_TRY(run_persistent(g, GI_ALGO_BFS, src, depth, sc, trace, s));
-    }
+    // depths in one persistent launch; canonical parents by the in-edge pass
+    GI_TRY(run_persistent(g, GI_ALGO_BFS, src, depth, sc, trace, s));
     if (!parent) return GI_OK;
     k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n, INT32_MAX);
     k_set_one<<<1, 1, 0, s>>>(parent, src, src);
@@ -511,21 +531,18 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
   if (st == GI_OK) st = ctrl_init(g, g->n, g->m, s);
   if (st == GI_OK)
     st = frontier_loop(g, P, sc, true, trace, s, [&](int32_t it, int32_t dir) {
-      // with in-edges, push levels set depth only (no atomics on parents) and
-      // the canonical parents of their vertices come from k_bfs_parents
-      // afterwards; without in-edges push levels take the min with atomics
-      gi_bfs_args a{depth, (dir == GI_DIR_DENSE_PULL || !g->has_csc) ? parent : nullptr, it + 1};
+      // the canonical parent in every direction: pull levels stop at the
+      // first (smallest-id) frontier in-neighbour; push levels lower parent[v]
+      // with atomicMin from every frontier in-neighbour of a vertex found at
+      // this level (after a plain read shows the id is smaller).  A pass over
+      // the in-edges after the loop instead scanned hub rows serially for
+      // their parent (R-MAT 24: 6.8 ms per query against < 0.1 ms here).
+      gi_bfs_args a{depth, parent, it + 1};
       return apply_dispatch(g, P.F, nullptr, dir, sc, GI_K_BFS, &a, P.N, GI_NO_DEDUP, s);
     });
   if (st == GI_OK && parent) {
-    int launched = 0;
-    if (g->has_csc) {
-      const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
-      k_bfs_parents<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->n, depth, parent, tw);
-      ++launched;
-    }
     k_parent_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n);
-    st = launch_status(launched + 1);
+    st = launch_status(1);
   }
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
@@ -611,6 +628,356 @@ static int minlabel_run(gi_graph *g, int32_t *x, int32_t kernel_id, int32_t src,
   return st;
 }
 
+// ========================================================= delta-stepping ==
+// gi_schedule.delta > 0: SSSP by delta-stepping (Meyer & Sanders) in
+// synchronous rounds, an ordering of the same label-correcting relaxations
+// that Sec. 6's asyncMin leaves free (the final distances do not depend on
+// it).  Arcs lighter than delta ("light") are relaxed inside the bucket
+// [k*delta, (k+1)*delta) until it stops changing; the bucket's vertices are
+// then final and their heavy arcs are relaxed once.  Each row's arcs are split
+// by class into two CSRs, built once per graph and delta, so a round streams
+// only the arcs it relaxes.  Every round is a SparsePush over the round's
+// sources or a DensePull whose per-source values are the start-of-round
+// distances of those sources (INT32_MAX elsewhere); on symmetric graphs the
+// light and heavy CSRs are also their own in-edge views, so both directions
+// relax exactly the same arcs and leave the same state.
+namespace gi {
+
+struct DeltaSplit {
+  int32_t delta = 0;
+  int32_t tile_edges = 0;
+  Csr light, heavy;  // same vertices, arcs split by w < delta
+  int32_t *deg_l = nullptr, *deg_h = nullptr;
+  TileSet tl, th;    // pull tiles (symmetric graphs)
+  int64_t m_light = 0;
+};
+
+void dstep_free(gi_graph *g, cudaStream_t s) {
+  DeltaSplit *D = static_cast<DeltaSplit *>(g->dstep);
+  if (!D) return;
+  for (Csr *c : {&D->light, &D->heavy}) {
+    dev_free(c->ptr, s);
+    dev_free(c->idx, s);
+    dev_free(c->wt, s);
+  }
+  dev_free(D->deg_l, s);
+  dev_free(D->deg_h, s);
+  free_tiles(&D->tl, s);
+  free_tiles(&D->th, s);
+  delete D;
+  g->dstep = nullptr;
+}
+
+// light arcs per row, one warp per row
+__global__ void k_ds_count(const int32_t *__restrict__ ptr, const int32_t *__restrict__ wt, int64_t n, int32_t delta,
+                           int32_t *cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t a = __ldg(ptr + v), b = __ldg(ptr + v + 1);
+    int32_t c = 0;
+    for (int64_t e = a + lane; e < b; e += 32) c += __ldg(wt + e) < delta ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[v] = c;
+  }
+}
+
+// heavy row offsets and both degree arrays: hptr[v] = ptr[v] - lptr[v]
+__global__ void k_ds_offsets(const int32_t *__restrict__ ptr, const int32_t *__restrict__ lptr, int64_t n,
+                             int32_t *hptr, int32_t *deg_l, int32_t *deg_h) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += (int64_t)gridDim.x * blockDim.x) {
+    hptr[v] = ptr[v] - lptr[v];
+    if (v < n) {
+      const int32_t dl = lptr[v + 1] - lptr[v];
+      deg_l[v] = dl;
+      deg_h[v] = (ptr[v + 1] - ptr[v]) - dl;
+    }
+  }
+}
+
+// stable split of each row (one warp per row): light arcs to the light CSR,
+// the others to the heavy CSR, both keeping the row's ascending order
+__global__ void k_ds_fill(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                          const int32_t *__restrict__ wt, int64_t n, int32_t delta, const int32_t *__restrict__ lptr,
+                          const int32_t *__restrict__ hptr, int32_t *lidx, int32_t *lwt, int32_t *hidx, int32_t *hwt) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t a = __ldg(ptr + v), b = __ldg(ptr + v + 1);
+    int64_t lo = __ldg(lptr + v), ho = __ldg(hptr + v);
+    for (int64_t e0 = a; e0 < b; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const bool ok = e < b;
+      const int32_t w = ok ? __ldg(wt + e) : 0, u = ok ? __ldg(idx + e) : 0;
+      const bool li = ok && w < delta, hv = ok && !li;
+      const unsigned bl = __ballot_sync(0xffffffffu, li), bh = __ballot_sync(0xffffffffu, hv);
+      if (li) {
+        const int64_t p = lo + __popc(bl & below);
+        lidx[p] = u;
+        lwt[p] = w;
+      }
+      if (hv) {
+        const int64_t p = ho + __popc(bh & below);
+        hidx[p] = u;
+        hwt[p] = w;
+      }
+      lo += __popc(bl);
+      ho += __popc(bh);
+    }
+  }
+}
+
+static int dstep_get(gi_graph *g, int32_t delta, int32_t tile_edges, cudaStream_t s, DeltaSplit **out) {
+  DeltaSplit *D = static_cast<DeltaSplit *>(g->dstep);
+  const int32_t te = tile_edges > 0 ? tile_edges : 2048;
+  if (D && D->delta == delta && (!g->symmetric || D->tile_edges == te)) {
+    *out = D;
+    return GI_OK;
+  }
+  dstep_free(g, s);
+  D = new DeltaSplit();
+  g->dstep = D;
+  D->delta = delta;
+  D->tile_edges = te;
+  const int64_t n = g->n;
+  int st = dev_alloc_n(&D->light.ptr, n + 1, s);
+  if (st == GI_OK) st = dev_alloc_n(&D->heavy.ptr, n + 1, s);
+  if (st == GI_OK) st = dev_alloc_n(&D->deg_l, n, s);
+  if (st == GI_OK) st = dev_alloc_n(&D->deg_h, n, s);
+  const int wgrid = grid_for(g, n * 32, 256);
+  int32_t *cnt = nullptr;
+  if (st == GI_OK) st = dev_alloc_n(&cnt, n, s);
+  if (st == GI_OK) {
+    k_ds_count<<<wgrid, 256, 0, s>>>(g->out.ptr, g->out.wt, n, delta, cnt);
+    st = launch_status(1);
+  }
+  if (st == GI_OK) st = scan_exclusive(g, cnt, D->light.ptr, n, s);
+  dev_free(cnt, s);
+  int32_t ml = 0;
+  if (st == GI_OK) {
+    k_ds_offsets<<<grid_for(g, n + 1, 256), 256, 0, s>>>(g->out.ptr, D->light.ptr, n, D->heavy.ptr, D->deg_l,
+                                                          D->deg_h);
+    st = launch_status(1);
+  }
+  if (st == GI_OK && (cudaMemcpyAsync(&ml, D->light.ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+                          cudaSuccess ||
+                      cudaStreamSynchronize(s) != cudaSuccess))
+    st = cuda_fail(cudaGetLastError(), "light arc count", __FILE__, __LINE__);
+  D->m_light = ml;
+  const int64_t mh = g->m - ml;
+  if (st == GI_OK) st = dev_alloc_n(&D->light.idx, ml, s);
+  if (st == GI_OK) st = dev_alloc_n(&D->light.wt, ml, s);
+  if (st == GI_OK) st = dev_alloc_n(&D->heavy.idx, mh, s);
+  if (st == GI_OK) st = dev_alloc_n(&D->heavy.wt, mh, s);
+  if (st == GI_OK) {
+    k_ds_fill<<<wgrid, 256, 0, s>>>(g->out.ptr, g->out.idx, g->out.wt, n, delta, D->light.ptr, D->heavy.ptr,
+                                    D->light.idx, D->light.wt, D->heavy.idx, D->heavy.wt);
+    st = launch_status(1);
+  }
+  if (st == GI_OK && g->symmetric) st = build_tiles(g, D->light, te, &D->tl, s);
+  if (st == GI_OK && g->symmetric) st = build_tiles(g, D->heavy, te, &D->th, s);
+  if (st != GI_OK) {
+    dstep_free(g, s);
+    return st;
+  }
+  *out = D;
+  return GI_OK;
+}
+
+// one warp appends the ids of its lanes with pred set to q (count *qc)
+__device__ __forceinline__ void warp_append(int32_t *q, int32_t *qc, bool pred, int32_t v) {
+  const unsigned b = __ballot_sync(0xffffffffu, pred);
+  if (!b) return;
+  const int lane = threadIdx.x & 31;
+  int32_t base = 0;
+  if (lane == 0) base = atomicAdd(qc, __popc(b));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (pred) q[base + __popc(b & ((1u << lane) - 1u))] = v;
+}
+
+// Device words of one delta-stepping round (int32): R, S and far counts and
+// the smallest distance among the far vertices.
+enum DsWord { kDsR = 0, kDsS = 1, kDsFar = 2, kDsFarMin = 3 };
+
+__global__ void k_ds_round_init(int32_t *w) {
+  if (threadIdx.x == 0) {
+    w[kDsR] = 0;
+    w[kDsFar] = 0;
+    w[kDsFarMin] = INT32_MAX;
+  }
+}
+
+// Splits the pending set P (vertices whose distance changed and whose light
+// arcs have not been relaxed at it): those below hi form this round's R
+// (snap = their distance) and join the bucket's settled list S once; the rest
+// go to the far list, whose smallest distance is recorded.
+__global__ void k_ds_split(const int32_t *__restrict__ P, const int32_t *__restrict__ Pc,
+                           const int32_t *__restrict__ x, int32_t hi, int32_t *Rq, int32_t *snap, uint32_t *Sbm,
+                           int32_t *Sq, int32_t *Fq, int32_t *w) {
+  const int lane = threadIdx.x & 31;
+  const int32_t c = *Pc;
+  const int32_t stride = gridDim.x * blockDim.x;
+  int32_t fmin = INT32_MAX;
+  for (int32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < c; i0 += stride) {
+    const int32_t i = i0 + lane;
+    int32_t v = -1, d = INT32_MAX;
+    if (i < c) {
+      v = P[i];
+      d = x[v];
+    }
+    const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
+    if (near) snap[v] = d;
+    if (far) fmin = min(fmin, d);
+    warp_append(Rq, w + kDsR, near, v);
+    warp_append(Fq, w + kDsFar, far, v);
+    warp_append(Sq, w + kDsS, near && bit_test_and_set(Sbm, v), v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
+  if (lane == 0 && fmin < INT32_MAX) atomicMin(w + kDsFarMin, fmin);
+}
+
+// far list -> next pending set N (bitmap test-and-set keeps it duplicate-free)
+__global__ void k_ds_merge(const int32_t *__restrict__ Fq, const int32_t *__restrict__ w, uint32_t *Nbm, int32_t *Nq,
+                           int32_t *Nc) {
+  const int lane = threadIdx.x & 31;
+  const int32_t c = w[kDsFar];
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < c; i0 += stride) {
+    const int32_t i = i0 + lane;
+    const int32_t v = i < c ? Fq[i] : -1;
+    warp_append(Nq, Nc, v >= 0 && bit_test_and_set(Nbm, v), v);
+  }
+  (void)lane;
+}
+
+__global__ void k_ds_clear_s(const int32_t *__restrict__ Sq, int32_t *w, uint32_t *Sbm) {
+  const int32_t c = w[kDsS];
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+    const int32_t v = Sq[i];
+    atomicAnd(Sbm + (v >> 5), ~(1u << (v & 31)));
+  }
+}
+
+__global__ void k_ds_zero_s(int32_t *w) {
+  if (threadIdx.x == 0) w[kDsS] = 0;
+}
+
+}  // namespace gi
+
+static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule &sc, gi_trace *trace,
+                         cudaStream_t s) {
+  DeltaSplit *D = nullptr;
+  GI_TRY(dstep_get(g, sc.delta, sc.tile_edges, s, &D));
+  const int64_t n = g->n;
+  const bool pull_ok = g->symmetric;
+  VsetPair P;
+  gi_vset R{}, S{};
+  int32_t *snap = nullptr, *Rq = nullptr, *Sq = nullptr, *Fq = nullptr;
+  uint32_t *Sbm = nullptr;
+  // the round words live in the graph's control block, so the fetch of the
+  // statistics brings them to the host in the same pinned copy
+  int32_t *w = reinterpret_cast<int32_t *>(g->ctrl + kDsSlots);
+  const int32_t *hw = reinterpret_cast<const int32_t *>(g->ctrl_host + kDsSlots);
+  int st = pair_alloc(g, P, s);
+  if (st == GI_OK) st = dev_alloc_n(&snap, n, s);
+  if (st == GI_OK) st = dev_alloc_n(&Rq, n, s);
+  if (st == GI_OK) st = dev_alloc_n(&Sq, n, s);
+  if (st == GI_OK) st = dev_alloc_n(&Fq, n, s);
+  if (st == GI_OK) st = dev_alloc_n(&Sbm, P.a.words, s);
+  if (st == GI_OK) {
+    k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(x, n, INT32_MAX);
+    k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(snap, n, INT32_MAX);
+    k_set_one<<<1, 1, 0, s>>>(x, src, 0);
+    st = launch_status(3);
+  }
+  if (st == GI_OK && cudaMemsetAsync(Sbm, 0, sizeof(uint32_t) * (size_t)P.a.words, s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "delta-stepping init", __FILE__, __LINE__);
+  if (st == GI_OK) st = front_init(g, P.F, src, s);
+  if (st == GI_OK) st = ctrl_init(g, 0, 0, s);  // also zeroes the round words
+  // R and S are vertex sets with the queue form only; their counters are round words
+  R.g = S.g = g;
+  R.n = S.n = n;
+  R.queue = Rq;
+  R.count = w + kDsR;
+  R.reps = GI_REP_SPARSE;
+  S.queue = Sq;
+  S.count = w + kDsS;
+  S.reps = GI_REP_SPARSE;
+  int64_t hi = sc.delta;  // end of the current bucket (distance of src = 0)
+  const int grid = g->num_sms * 4;
+  int32_t it = 0;
+  while (st == GI_OK) {
+    k_ds_round_init<<<1, 32, 0, s>>>(w);
+    k_ds_split<<<grid, 256, 0, s>>>(P.F->queue, P.F->count, x, (int32_t)(hi < INT32_MAX ? hi : INT32_MAX), Rq, snap,
+                                    Sbm, Sq, Fq, w);
+    if ((st = launch_status(2)) != GI_OK) break;
+    DecideParams p = decide_params(sc, it, false);
+    if ((st = frontier_decide(g, &R, p, s, D->deg_l)) != GI_OK) break;
+    if ((st = ctrl_fetch(g, s)) != GI_OK) break;
+    const bool light = hw[kDsR] > 0;
+    if (!light && hw[kDsS] == 0) {
+      if (hw[kDsFar] == 0) break;  // nothing pending: done
+      // the bucket is finished and its heavy arcs relaxed: next bucket
+      hi = ((int64_t)hw[kDsFarMin] / sc.delta + 1) * sc.delta;
+      continue;
+    }
+    gi_vset *Fr = light ? &R : &S;
+    const Csr &arcs = light ? D->light : D->heavy;
+    if (!light) {
+      // heavy round of the finished bucket: its vertices are final
+      k_snap_set<<<grid, 256, 0, s>>>(Sq, S.count, snap, x);
+      if ((st = launch_status(1)) != GI_OK) break;
+      if ((st = frontier_decide(g, &S, p, s, D->deg_h)) != GI_OK) break;
+      if ((st = ctrl_fetch(g, s)) != GI_OK) break;
+    }
+    int32_t dir = (int32_t)g->ctrl_host[kDecision];
+    if (dir == GI_DIR_DENSE_PUSH || (dir == GI_DIR_DENSE_PULL && !pull_ok)) dir = GI_DIR_SPARSE_PUSH;
+    g->ctrl_host[kDecision] = dir;
+    trace_put(trace, it, g->ctrl_host);
+    if ((st = vset_clear(P.N, s)) != GI_OK) break;
+    if (g->ctrl_host[kMf] > 0) {
+      OpMinInt op{x, snap, arcs.wt};
+      if (dir == GI_DIR_DENSE_PULL) {
+        st = launch_pull_tiled(g, op, arcs, light ? D->tl : D->th, FSet(), nullptr, out_of(P.N), s, kClassMinPull,
+                               sc.balance == GI_BAL_VERTEX);
+      } else {
+        g->hint_vset = Fr;
+        g->hint_nf = g->ctrl_host[kNf];
+        g->hint_mf = g->ctrl_host[kMf];
+        st = launch_push(g, op, kSrcQueue, Fr, nullptr, out_of(P.N), sc, s, &arcs);
+        g->hint_vset = nullptr;
+        g->hint_nf = g->hint_mf = -1;
+      }
+      if (st != GI_OK) break;
+    }
+    k_ds_merge<<<grid, 256, 0, s>>>(Fq, w, P.N->bitmap, P.N->queue, P.N->count);
+    k_snap_reset<<<grid, 256, 0, s>>>(Fr->queue, Fr->count, snap);
+    int launched = 2;
+    if (!light) {  // the bucket's settled list is done with
+      k_ds_clear_s<<<grid, 256, 0, s>>>(Sq, w, Sbm);
+      k_ds_zero_s<<<1, 32, 0, s>>>(w);
+      launched += 2;
+    }
+    if ((st = launch_status(launched)) != GI_OK) break;
+    P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
+    P.swap();
+    ++it;
+  }
+  if (trace) trace->iterations = it;
+  dev_free(snap, s);
+  dev_free(Rq, s);
+  dev_free(Sq, s);
+  dev_free(Fq, s);
+  dev_free(Sbm, s);
+  pair_free(P, s);
+  if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "delta-stepping", __FILE__, __LINE__);
+  return st;
+}
+
 extern "C" int gi_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedule *sched, gi_trace *trace,
                        void *stream) {
   GI_ARG(g != nullptr, "graph is NULL");
@@ -623,6 +990,7 @@ extern "C" int gi_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedul
     GI_ARG(g->symmetric || g->in.wt != nullptr, "pull SSSP needs in-edge weights (gi_load_csc with weights)");
   }
   if (sched->persistent == 1) return run_persistent(g, GI_ALGO_SSSP, src, dist, *sched, trace, (cudaStream_t)stream);
+  if (sched->delta > 0) return deltastep_run(g, dist, src, *sched, trace, (cudaStream_t)stream);
   return minlabel_run(g, dist, GI_K_SSSP, src, *sched, trace, (cudaStream_t)stream);
 }
 

@@ -549,6 +549,7 @@ static void segs_free(gi_graph *g, cudaStream_t s);
 static void graph_release(gi_graph *g, cudaStream_t s) {
   if (!g) return;
   graph_loop_free(g);
+  dstep_free(g, s);
   free_tile_cache(g, s);
   segs_free(g, s);
   if (!g->symmetric) {
@@ -1621,11 +1622,11 @@ int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s) {
   return GI_OK;
 }
 
-int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s) {
+int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s, const int32_t *deg) {
   GI_TRY(vset_ensure_queue(F, s));
   int blocks = g->num_sms * 2;
-  k_frontier_decide<<<blocks, 256, 0, s>>>(F->queue, F->count, g->out_deg, g->ctrl, p, g->n, g->m, g->max_deg,
-                                           g_sel_loaded ? 1 : 0);
+  k_frontier_decide<<<blocks, 256, 0, s>>>(F->queue, F->count, deg ? deg : g->out_deg, g->ctrl, p, g->n, g->m,
+                                           g->max_deg, g_sel_loaded ? 1 : 0);
   GI_LAUNCH_CHECK();
   return GI_OK;
 }
@@ -1668,4 +1669,5 @@ extern "C" void gi_schedule_default(gi_schedule *s) {
   s->persistent = 0;
   s->hot_cache = 0;
   s->seg_strategy = GI_SEG_FVC;
+  s->delta = 0;
 }

@@ -79,6 +79,7 @@ enum CtrlSlot {
   kErr = 9,       // device-side error flag (bounded waits, bounds checks)
   kMfAcc = 10,    // m_f accumulator of the statistics kernel (its last block returns it to 0)
   kFeat = 16,     // 16 float features stored as float bits in 8 int64 words (slots 16..23)
+  kDsSlots = 32,  // delta-stepping SSSP: 8 int32 round words in slots 32..35 (fetched with the rest)
 };
 
 // --------------------------------------------------------------- graph --
@@ -156,6 +157,7 @@ struct gi_graph {
   const gi_vset *hint_vset = nullptr;
   int64_t hint_nf = -1, hint_mf = -1;
   void *graph_loop = nullptr;    // cached CUDA graph of the graph-driven BFS (gi_schedule.persistent = 2)
+  void *dstep = nullptr;         // cached light/heavy arc split of delta-stepping SSSP (gi_schedule.delta)
   int64_t *ctrl = nullptr;       // device control block (kCtrlWords)
   void *heavy_mem = nullptr;     // HeavyList storage (counter, ticket, 2n entries), allocated on first use
   void *bfs_defer = nullptr;     // BfsDefer storage of the early-exit BFS pull, allocated on first use
@@ -252,6 +254,7 @@ int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cuda
 int use_tiles(gi_graph *g, int32_t tile_edges, cudaStream_t s);  // select (building once) the in-edge tiles
 void free_tile_cache(gi_graph *g, cudaStream_t s);
 void graph_loop_free(gi_graph *g);  // the cached graph-driven BFS (gi_algos.cu)
+void dstep_free(gi_graph *g, cudaStream_t s);  // the cached light/heavy split of delta-stepping (gi_algos.cu)
 void free_tiles(TileSet *ts, cudaStream_t s);
 int hot_get(gi_graph *g, cudaStream_t s);  // build (once) g->hot from the in-edges
 void hot_free(gi_graph *g, cudaStream_t s);
@@ -294,7 +297,8 @@ struct DecideParams {
   const int32_t *clear_q = nullptr;
   int32_t *clear_qc = nullptr;
 };
-int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s);
+// deg: per-vertex arc counts summed into m_f (NULL = out-degrees)
+int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s, const int32_t *deg = nullptr);
 int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s);
 int ctrl_fetch(gi_graph *g, cudaStream_t s);  // copies ctrl to pinned host + syncs
 

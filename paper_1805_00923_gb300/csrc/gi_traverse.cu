@@ -212,6 +212,7 @@ int check_schedule(const gi_schedule *sc) {
   GI_ARG(sc->hot_cache >= 0 && sc->hot_cache <= 2, "hot_cache must be 0, 1 or 2");
   GI_ARG(sc->seg_strategy == GI_SEG_FVC || sc->seg_strategy == GI_SEG_EVC, "seg_strategy must be FVC or EVC");
   GI_ARG(sc->persistent >= 0 && sc->persistent <= 2, "persistent must be 0, 1 or 2");
+  GI_ARG(sc->delta >= 0, "delta must be >= 0");
   return GI_OK;
 }
 

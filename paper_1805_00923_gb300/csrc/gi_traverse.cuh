@@ -1571,7 +1571,7 @@ int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts
 // Edge-parallel SparsePush over from's queue (nf members, or read back when -1).
 template <class Op>
 int launch_push_edges(gi_graph *g, const Op &op, const gi_vset *from, int64_t nf, const uint32_t *to,
-                      const OutSet &out, cudaStream_t s) {
+                      const OutSet &out, cudaStream_t s, const Csr &c) {
   if (nf < 0) {
     int32_t c = 0;
     GI_CUDA(cudaMemcpyAsync(&c, from->count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1581,12 +1581,11 @@ int launch_push_edges(gi_graph *g, const Op &op, const gi_vset *from, int64_t nf
   if (nf == 0) return GI_OK;
   int32_t *fd = nullptr, *off = nullptr;
   GI_TRY(ws_scratch(g, &fd, &off, s));
-  k_front_deg<<<grid_for(g, nf, 256), 256, 0, s>>>(from->queue, nf, g->out.ptr, fd);
+  k_front_deg<<<grid_for(g, nf, 256), 256, 0, s>>>(from->queue, nf, c.ptr, fd);
   GI_LAUNCH_CHECK();
   GI_TRY(scan_exclusive(g, fd, off, nf, s));
   const int tok = timing_begin(kClassPush, s);
-  k_push_edges<Op><<<g->num_sms * 8, 256, 0, s>>>(op, from->queue, off, (int32_t)nf, g->out.ptr, g->out.idx, to,
-                                                   out);
+  k_push_edges<Op><<<g->num_sms * 8, 256, 0, s>>>(op, from->queue, off, (int32_t)nf, c.ptr, c.idx, to, out);
   timing_end(tok, s);
   GI_LAUNCH_CHECK();
   return GI_OK;
@@ -1611,13 +1610,16 @@ int launch_pull_sparse(gi_graph *g, const Op &op, const Csr &c, const int32_t *q
   return GI_OK;
 }
 
-// Push along the out-edges.  mode: kSrcQueue (from's queue), kSrcBitmap (scan
-// from's bitmap over all vertices), kSrcAll.
+// Push along the out-edges (csr: another arc set of the same vertices, e.g.
+// the light or heavy arcs of delta-stepping; NULL = the graph's CSR).  mode:
+// kSrcQueue (from's queue), kSrcBitmap (scan from's bitmap over all
+// vertices), kSrcAll.
 template <class Op>
 int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const uint32_t *to, const OutSet &out,
-                const gi_schedule &sc, cudaStream_t s) {
+                const gi_schedule &sc, cudaStream_t s, const Csr *csr = nullptr) {
+  const Csr &c = csr ? *csr : g->out;
   if (mode == kSrcQueue && sc.balance == GI_BAL_EDGE_PARALLEL)
-    return launch_push_edges(g, op, from, from == g->hint_vset ? g->hint_nf : -1, to, out, s);
+    return launch_push_edges(g, op, from, from == g->hint_vset ? g->hint_nf : -1, to, out, s, c);
   int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
   int32_t tc = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_cta > 0 ? sc.t_cta : 1024);
   if (tw != INT32_MAX && tw > kMaxTWarp) tw = kMaxTWarp;
@@ -1630,23 +1632,23 @@ int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const 
   const int tok = timing_begin(kClassPush, s);
   if (mode == kSrcQueue) {
     grid = g->num_sms * (2048 / block);
-    k_push<Op, kSrcQueue><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, from->queue, from->count, nullptr, g->n,
+    k_push<Op, kSrcQueue><<<grid, block, 0, s>>>(op, c.ptr, c.idx, from->queue, from->count, nullptr, g->n,
                                                  to, out, tw, tc, th, heavy);
   } else if (mode == kSrcBitmap) {
     grid = grid_for(g, g->n, block, 2048 / block);
     const FSet fs = (sc.dense_rep == GI_REP_BOOL && from->boolmap && (from->reps & GI_REP_BOOL))
                         ? FSet(static_cast<const uint8_t *>(from->boolmap))
                         : FSet(static_cast<const uint32_t *>(from->bitmap));
-    k_push<Op, kSrcBitmap><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, fs, g->n, to, out, tw,
+    k_push<Op, kSrcBitmap><<<grid, block, 0, s>>>(op, c.ptr, c.idx, nullptr, nullptr, fs, g->n, to, out, tw,
                                                   tc, th, heavy);
   } else {
     grid = grid_for(g, g->n, block, 2048 / block);
-    k_push<Op, kSrcAll><<<grid, block, 0, s>>>(op, g->out.ptr, g->out.idx, nullptr, nullptr, nullptr, g->n, to, out,
+    k_push<Op, kSrcAll><<<grid, block, 0, s>>>(op, c.ptr, c.idx, nullptr, nullptr, nullptr, g->n, to, out,
                                                tw, tc, th, heavy);
   }
   GI_LAUNCH_CHECK();
   if (th != INT32_MAX && g->max_deg >= th) {  // otherwise no source can have been deferred
-    k_push_heavy<Op><<<g->num_sms * 4, block, 0, s>>>(op, g->out.ptr, g->out.idx, heavy, g->n, to, out);
+    k_push_heavy<Op><<<g->num_sms * 4, block, 0, s>>>(op, c.ptr, c.idx, heavy, g->n, to, out);
     GI_LAUNCH_CHECK();
   }
   timing_end(tok, s);

@@ -57,7 +57,9 @@ L_SOURCES = 64   # the scale-24 BFS/SSSP configuration: 64 seeded sources (bench
 BFS_SCHEDULES = {"hybrid_pull": dict(direction="hybrid_pull"), "learned": dict(direction="learned"),
                  "graph_driven": dict(direction="hybrid_pull", persistent=2),
                  "graph_driven_learned": dict(direction="learned", persistent=2)}
-SSSP_SCHEDULES = {"hybrid_pull": dict(direction="hybrid_pull"), "learned": dict(direction="learned")}
+SSSP_SCHEDULES = {"hybrid_pull": dict(direction="hybrid_pull"), "learned": dict(direction="learned"),
+                  "delta_hybrid": dict(direction="hybrid_pull", delta=64),
+                  "delta_learned": dict(direction="learned", delta=64)}
 
 
 @pytest.fixture(scope="module")

@@ -145,6 +145,89 @@ def test_sssp_grid(gi):
     assert np.array_equal(tr.as_dict()["frontier"], fs)
 
 
+# ------------------------------------------------------ SSSP, delta-stepping
+
+DS_DIRS = ["sparse_push", "dense_pull", "dense_push", "hybrid_pull", "learned"]
+
+
+@pytest.mark.parametrize("delta", [1, 7, 64, 333, 1 << 20])
+@pytest.mark.parametrize("direction", DS_DIRS)
+def test_sssp_delta_stepping_rmat(gi, direction, delta):
+    """Delta-stepping (gi_schedule.delta) gives the oracle's distances for bucket
+    widths from one weight unit (every arc heavy) to beyond the largest
+    distance (every arc light, one bucket)."""
+    from paper_1805_00923_gb300 import selector as sel
+    sel.install()
+    hg = rmat(14, weights=True)
+    g = _load(gi, hg)
+    for src in [0, *gg.pick_sources(hg, 2, seed=4)]:
+        want, _ = oracle.sssp(hg, int(src))
+        d = gi.sssp(g, int(src), sched=gi.schedule(direction, delta=delta))
+        assert np.array_equal(_np(d), want), (src, delta)
+
+
+@pytest.mark.parametrize("balance", ["edge_aware", "vertex", "edge_parallel"])
+def test_sssp_delta_stepping_rounds_do_not_depend_on_direction(gi, balance):
+    """Push and pull relax the same arcs of the same sources in every round
+    (the light / heavy split is its own in-edge view on symmetric graphs), so
+    the per-round source counts and arc counts agree across directions."""
+    hg = rmat(14, weights=True)
+    g = _load(gi, hg)
+    src = int(gg.pick_sources(hg, 1, seed=9)[0])
+    want, _ = oracle.sssp(hg, src)
+    traces = []
+    for direction in ["sparse_push", "dense_pull", "hybrid_pull"]:
+        tr = gi.Trace(4096)
+        d = gi.sssp(g, src, sched=gi.schedule(direction, delta=48, balance=balance), trace=tr)
+        assert np.array_equal(_np(d), want)
+        t = tr.as_dict()
+        traces.append((t["frontier"], t["edges"]))
+    for f, e in traces[1:]:
+        assert np.array_equal(f, traces[0][0]) and np.array_equal(e, traces[0][1])
+    # every arc of every reached vertex is relaxed at least once (light arcs in
+    # its bucket's light rounds, heavy arcs once in the bucket's heavy round)
+    deg = np.diff(hg.row_ptr)
+    assert traces[0][1].sum() >= deg[want < INT_MAX].sum()
+
+
+@pytest.mark.parametrize("name", ["path", "components", "hub_tail", "single", "isolated", "star"])
+@pytest.mark.parametrize("direction", ["sparse_push", "dense_pull", "hybrid_pull"])
+def test_sssp_delta_stepping_adversarial(gi, name, direction):
+    hg = adversarial(name, weights=True)
+    g = _load(gi, hg)
+    want, _ = oracle.sssp(hg, 0)
+    for delta in (1, 10, 100):
+        assert np.array_equal(_np(gi.sssp(g, 0, sched=gi.schedule(direction, delta=delta))), want), delta
+        assert np.array_equal(_np(gi.sssp(g, 0, sched=gi.schedule(direction, delta=delta,
+                                                                    balance="edge_parallel"))), want), delta
+
+
+def test_sssp_delta_stepping_grid_and_directed(gi):
+    hg = grid(64, weights=True)
+    g = _load(gi, hg)
+    for delta in (3, 20, 250):
+        assert np.array_equal(_np(gi.sssp(g, 100, sched=gi.schedule("hybrid_pull", delta=delta))),
+                              oracle.sssp(hg, 100)[0])
+    # a directed graph: delta-stepping pushes along the out-edges (pull needs a symmetric graph)
+    hd = _directed(3000, 12000, 4, weights=True)
+    in_ptr, in_col, in_wt = gg.transpose(hd)
+    gd = gi.Graph(hd.row_ptr, hd.col, hd.wt, symmetric=False, in_edges=(in_ptr, in_col, in_wt), validate=True)
+    for direction in ("sparse_push", "dense_pull", "hybrid_pull"):
+        for src in (0, 1234):
+            assert np.array_equal(_np(gi.sssp(gd, src, sched=gi.schedule(direction, delta=40))),
+                                  oracle.sssp(hd, src)[0])
+
+
+def test_sssp_delta_stepping_split_reused_and_rebuilt(gi):
+    """The light/heavy split is cached per graph and delta: alternating deltas
+    rebuilds it each time and keeps every result exact."""
+    hg = rmat(12, weights=True)
+    g = _load(gi, hg)
+    want, _ = oracle.sssp(hg, 5)
+    for delta in (16, 16, 200, 16, 0, 200):
+        assert np.array_equal(_np(gi.sssp(g, 5, sched=gi.schedule("hybrid_pull", delta=delta))), want), delta
+
+
 # ------------------------------------------------------------------------ CC
 
 @pytest.mark.parametrize("balance", ["edge_aware", "edge_parallel"])
