@@ -209,7 +209,8 @@ typedef struct gi_schedule {
   uint32_t dense_rep;   /* frontier rep for dense traversals: GI_REP_BITMAP or BOOL  */
   int32_t balance;      /* GI_BAL_*                                                  */
   int32_t num_segments; /* SSG count for segmented pull (configApplyNumSSG); 1 = off  */
-  int32_t block;        /* reserved (traversal kernels run 256-thread blocks)        */
+  int32_t block;        /* SparsePush block size: 128, 256 or 512 threads (the grid   */
+                        /* keeps 2048 threads per SM); other kernels run 256          */
   int32_t t_warp;       /* edge-aware: degree >= t_warp goes to a warp                */
   int32_t t_cta;        /* edge-aware: degree >= t_cta goes to a whole block          */
   int32_t rule;         /* GI_RULE_*                                                 */
@@ -494,10 +495,17 @@ typedef struct gi_batch_opts {
                         /* < 0: no threshold, every frontier source relaxed each round)    */
   int32_t order;        /* order in which clusters claim queries: 0 = as given, 1 =        */
                         /* largest graph first, SSSP before BFS (shorter makespan)          */
+  int32_t t_warp;       /* expansion bins: frontier sources with >= t_warp arcs are spread */
+                        /* over a warp (1..32; 0 = 32) ...                                 */
+  int32_t t_cta;        /* ... and with >= t_cta arcs over the CTA (>= t_warp; 0 = 1024)   */
+  int32_t *const *parents; /* host array of n_q device pointers, or NULL: a BFS query whose */
+                        /* entry is non-NULL also receives the canonical parents there (n   */
+                        /* of its graph entries; as gi_bfs: parent[src] = src, -1 if        */
+                        /* unreached); entries of SSSP queries are ignored                  */
 } gi_batch_opts;
 
 /* Defaults: cluster_size 4, clusters 0, HYBRID_PULL, alpha 14, beta 24, level_cap 0,
- * levels NULL, sssp_delta 0, order 1 (never fails). */
+ * levels NULL, sssp_delta 0, order 1, t_warp 32, t_cta 1024, parents NULL (never fails). */
 void gi_batch_opts_default(gi_batch_opts *o);
 
 /*
@@ -546,8 +554,11 @@ int gi_batch_plan_free(gi_batch_plan *p);
 /*
  * Schedule autotuner (the paper tunes schedules with OpenTuner, Sec. 6): keeps
  * start->direction/balance/rule and searches tile_edges, t_warp, t_cta,
- * t_heavy, num_segments (PageRank DensePull) and, for rule-based BFS hybrids,
- * Beamer's alpha/beta: random candidates for the first third of `budget`
+ * t_heavy, block, hot_cache (not BFS), the dense frontier representation
+ * dense_rep (not PageRank), num_segments and seg_strategy (PageRank
+ * DensePull), delta (SSSP: Bellman-Ford or delta-stepping bucket widths) and,
+ * for rule-based BFS hybrids, Beamer's alpha/beta: random candidates for the
+ * first third of `budget`
  * trials, then hill climbing around the best.  Each candidate runs once to
  * warm up and is timed (best of 2) with CUDA events on `stream`; a candidate
  * whose output differs from start's (integers bit-exact, ranks beyond 1e-4
@@ -559,6 +570,24 @@ int gi_batch_plan_free(gi_batch_plan *p);
  */
 int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_schedule *start, int32_t budget, uint64_t seed,
                 gi_schedule *best, double *best_ms, double *start_ms, void *stream);
+
+/*
+ * Autotuner of the batched engine (the same search applied to the batched
+ * launch, not in the paper): keeps start's selector and Beamer constants and
+ * searches cluster_size (1, 2, 4, 8), the expansion bins t_warp (8, 16, 32)
+ * and t_cta (128 .. 4096), sssp_delta (0.5 .. 8) and the claim order, each
+ * candidate a plan over the given queries (gi_batch_plan_create) whose
+ * launch is timed with CUDA events on `stream` (best of two after a
+ * warm-up); a candidate whose results differ from start's in any query is
+ * rejected.  start may be NULL (defaults); its levels and parents pointers are
+ * not used while tuning and are copied to *best.  The library allocates the
+ * output buffers of the candidates (the sum of the queried graphs' vertex
+ * counts, twice).  Syncs the stream.  Errors: as gi_batch_plan_create,
+ * GI_ERR_INVALID_ARG (budget outside [1, 100000]), GI_ERR_OOM, GI_ERR_CUDA.
+ */
+int gi_batch_autotune(gi_graph *const *graphs, int32_t n_graphs, const int32_t *q_graph, const int32_t *q_src,
+                      const int32_t *q_algo, int32_t n_q, const gi_batch_opts *start, int32_t budget, uint64_t seed,
+                      gi_batch_opts *best, double *best_ms, double *start_ms, void *stream);
 
 /* -------------------------------------------------------------- profiling -- */
 /*

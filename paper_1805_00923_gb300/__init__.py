@@ -334,8 +334,22 @@ def batch_opts(**kw) -> gi_batch_opts:
     return o
 
 
-def batch_run(graphs, queries, outs=None, opts=None, stream=None):
+def _with_parents(opts, parents, n_q):
+    """A copy of opts whose parents field points at the device tensors in
+    `parents` (one per query, None for no parents); returns (opts, keep-alive)."""
+    o = gi_batch_opts()
+    ctypes.pointer(o)[0] = opts if opts is not None else batch_opts()
+    if parents is None:
+        return o, None
+    arr = (ctypes.c_void_p * max(n_q, 1))(*[None if p is None else p.data_ptr() for p in parents])
+    o.parents = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
+    return o, arr
+
+
+def batch_run(graphs, queries, outs=None, opts=None, stream=None, parents=None):
     """gi_batch_run.  queries: list of (graph index, source, "bfs"|"sssp").
+    parents: optional list (one int32 CUDA tensor or None per query) that BFS
+    queries fill with canonical parents.
     Returns (list of int32 CUDA result tensors, per-query ns as numpy int64)."""
     n_q = len(queries)
     qg = np.array([q[0] for q in queries], np.int32)
@@ -346,15 +360,32 @@ def batch_run(graphs, queries, outs=None, opts=None, stream=None):
     handles = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
     optr = (ctypes.c_void_p * max(n_q, 1))(*[o.data_ptr() for o in outs])
     ns = np.zeros(max(n_q, 1), np.int64)
-    check(_C.gi_batch_run(handles, len(graphs), _vp(qg), _vp(qs), _vp(qa), n_q, optr, _vp(ns),
-                          ctypes.byref(opts if opts is not None else batch_opts()), _stream(stream)))
-    return [o[:graphs[q[0]].n] for o, q in zip(outs, queries)], ns[:n_q]
+    o, keep = _with_parents(opts, parents, n_q)
+    check(_C.gi_batch_run(handles, len(graphs), _vp(qg), _vp(qs), _vp(qa), n_q, optr, _vp(ns), ctypes.byref(o),
+                          _stream(stream)))
+    del keep
+    return [o_[:graphs[q[0]].n] for o_, q in zip(outs, queries)], ns[:n_q]
+
+
+def batch_autotune(graphs, queries, start=None, budget: int = 12, seed: int = 1, stream=None):
+    """gi_batch_autotune: (best gi_batch_opts, best ms, start ms) for the launch of these queries."""
+    n_q = len(queries)
+    qg = np.array([q[0] for q in queries], np.int32)
+    qs = np.array([q[1] for q in queries], np.int32)
+    qa = np.array([ALGOS[q[2]] if isinstance(q[2], str) else q[2] for q in queries], np.int32)
+    handles = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+    best = gi_batch_opts()
+    bms, sms = ctypes.c_double(), ctypes.c_double()
+    check(_C.gi_batch_autotune(handles, len(graphs), _vp(qg), _vp(qs), _vp(qa), n_q,
+                               ctypes.byref(start if start is not None else batch_opts()), int(budget), int(seed),
+                               ctypes.byref(best), ctypes.byref(bms), ctypes.byref(sms), _stream(stream)))
+    return best, bms.value, sms.value
 
 
 class BatchPlan:
     """gi_batch_plan: the batched engine split into create / launch (capturable) / results."""
 
-    def __init__(self, graphs, queries, opts=None, outs=None, stream=None):
+    def __init__(self, graphs, queries, opts=None, outs=None, stream=None, parents=None):
         n_q = len(queries)
         qg = np.array([q[0] for q in queries], np.int32)
         qs = np.array([q[1] for q in queries], np.int32)
@@ -366,9 +397,11 @@ class BatchPlan:
         handles = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
         optr = (ctypes.c_void_p * n_q)(*[o.data_ptr() for o in self.outs])
         h = ctypes.c_void_p()
-        check(_C.gi_batch_plan_create(handles, len(graphs), _vp(qg), _vp(qs), _vp(qa), n_q, optr,
-                                      ctypes.byref(opts if opts is not None else batch_opts()), _stream(stream),
-                                      ctypes.byref(h)))
+        o, keep = _with_parents(opts, parents, n_q)
+        check(_C.gi_batch_plan_create(handles, len(graphs), _vp(qg), _vp(qs), _vp(qa), n_q, optr, ctypes.byref(o),
+                                      _stream(stream), ctypes.byref(h)))
+        del keep
+        self.parents = parents
         self.handle = h
 
     def launch(self, stream=None):

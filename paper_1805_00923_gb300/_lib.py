@@ -51,7 +51,8 @@ class gi_trace(ctypes.Structure):
 
 class gi_batch_opts(ctypes.Structure):
     _fields_ = [("cluster_size", _i32), ("clusters", _i32), ("selector", _i32), ("alpha", _f32), ("beta", _f32),
-                ("level_cap", _i64), ("levels", _P(_i32)), ("sssp_delta", _f32), ("order", _i32)]
+                ("level_cap", _i64), ("levels", _P(_i32)), ("sssp_delta", _f32), ("order", _i32),
+                ("t_warp", _i32), ("t_cta", _i32), ("parents", _P(_vp))]
 
 
 class gi_bfs_args(ctypes.Structure):
@@ -110,6 +111,9 @@ SIGNATURES = {
     "gi_autotune": (ctypes.c_int, [_vp, _i32, _i32, _P(gi_schedule), _i32, ctypes.c_uint64, _P(gi_schedule),
                                    _P(ctypes.c_double), _P(ctypes.c_double), _vp]),
     "gi_batch_opts_default": (None, [_P(gi_batch_opts)]),
+    "gi_batch_autotune": (ctypes.c_int, [_P(_vp), _i32, _vp, _vp, _vp, _i32, _P(gi_batch_opts), _i32,
+                                         ctypes.c_uint64, _P(gi_batch_opts), _P(ctypes.c_double),
+                                         _P(ctypes.c_double), _vp]),
     "gi_batch_run": (ctypes.c_int, [_P(_vp), _i32, _vp, _vp, _vp, _i32, _P(_vp), _vp, _P(gi_batch_opts), _vp]),
     "gi_batch_plan_create": (ctypes.c_int, [_P(_vp), _i32, _vp, _vp, _vp, _i32, _P(_vp), _P(gi_batch_opts), _vp,
                                             _P(_vp)]),

@@ -284,9 +284,10 @@ static int frontier_loop(gi_graph *g, VsetPair &P, const gi_schedule &sc, bool t
 
 using namespace gi;
 
-// Single query in the batched engine's whole-GPU persistent mode.
+// Single query in the batched engine's whole-GPU persistent mode (BFS parents
+// from the engine too when parent is non-NULL).
 static int run_persistent(gi_graph *g, int32_t algo, int32_t src, int32_t *out, const gi_schedule &sc,
-                          gi_trace *trace, cudaStream_t s) {
+                          gi_trace *trace, cudaStream_t s, int32_t *parent = nullptr) {
   gi_batch_opts o;
   gi_batch_opts_default(&o);
   o.cluster_size = 0;
@@ -299,6 +300,8 @@ static int run_persistent(gi_graph *g, int32_t algo, int32_t src, int32_t *out, 
   o.beta = sc.beta > 0 ? sc.beta : 24.0f;
   gi_graph *gs[1] = {g};
   int32_t *outs[1] = {out};
+  int32_t *pars[1] = {parent};
+  if (parent) o.parents = pars;
   const int32_t qg = 0, qs = src, qa = algo;
   gi_batch_plan *p = nullptr;
   GI_TRY(gi_batch_plan_create(gs, 1, &qg, &qs, &qa, 1, outs, &o, s, &p));
@@ -507,18 +510,9 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     if (trace) trace->iterations = levels;
     return GI_OK;
   }
-  if (sc.persistent && (!parent || g->has_csc)) {
-    // depths in one persistent launch; canonical parents by the in-edge pass
-    GI_TRY(run_persistent(g, GI_ALGO_BFS, src, depth, sc, trace, s));
-    if (!parent) return GI_OK;
-    k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n, INT32_MAX);
-    k_set_one<<<1, 1, 0, s>>>(parent, src, src);
-    const int32_t tw = sc.balance == GI_BAL_VERTEX ? INT32_MAX : (sc.t_warp > 0 ? sc.t_warp : 32);
-    k_bfs_parents<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->n, depth, parent, tw);
-    k_parent_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n);
-    GI_TRY(launch_status(4));
-    GI_CUDA(cudaStreamSynchronize(s));
-    return GI_OK;
+  if (sc.persistent == 1) {
+    // depths and canonical parents in one persistent launch of the batched engine
+    return run_persistent(g, GI_ALGO_BFS, src, depth, sc, trace, s, parent);
   }
   GI_TRY(ensure_tiles(g, sc, s));
   VsetPair P;
@@ -797,25 +791,22 @@ __device__ __forceinline__ void warp_append(int32_t *q, int32_t *qc, bool pred, 
   if (pred) q[base + __popc(b & ((1u << lane) - 1u))] = v;
 }
 
-// Device words of one delta-stepping round (int32): R, S and far counts and
-// the smallest distance among the far vertices.
-enum DsWord { kDsR = 0, kDsS = 1, kDsFar = 2, kDsFarMin = 3 };
+// Device words of delta-stepping (int32, in the graph's control block): the
+// round's R and the bucket's S counts, the counts of the two far-pile
+// buffers and the smallest distance in the far pile.
+enum DsWord { kDsR = 0, kDsS = 1, kDsPile0 = 2, kDsPile1 = 3, kDsPileMin = 4 };
 
 __global__ void k_ds_round_init(int32_t *w) {
-  if (threadIdx.x == 0) {
-    w[kDsR] = 0;
-    w[kDsFar] = 0;
-    w[kDsFarMin] = INT32_MAX;
-  }
+  if (threadIdx.x == 0) w[kDsR] = 0;
 }
 
-// Splits the pending set P (vertices whose distance changed and whose light
-// arcs have not been relaxed at it): those below hi form this round's R
-// (snap = their distance) and join the bucket's settled list S once; the rest
-// go to the far list, whose smallest distance is recorded.
+// Splits the vertices whose distance changed last round (P): those below hi
+// form this round's R (snap = their distance), join the bucket's settled list
+// S once and leave the far pile if they were in it; the rest join the far
+// pile once (bitmap fbm) and lower its recorded minimum.
 __global__ void k_ds_split(const int32_t *__restrict__ P, const int32_t *__restrict__ Pc,
                            const int32_t *__restrict__ x, int32_t hi, int32_t *Rq, int32_t *snap, uint32_t *Sbm,
-                           int32_t *Sq, int32_t *Fq, int32_t *w) {
+                           int32_t *Sq, uint32_t *fbm, int32_t *pile, int32_t *pile_count, int32_t *w) {
   const int lane = threadIdx.x & 31;
   const int32_t c = *Pc;
   const int32_t stride = gridDim.x * blockDim.x;
@@ -828,29 +819,59 @@ __global__ void k_ds_split(const int32_t *__restrict__ P, const int32_t *__restr
       d = x[v];
     }
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
-    if (near) snap[v] = d;
+    const uint32_t bit = v >= 0 ? 1u << (v & 31) : 0u;
+    if (near) {
+      snap[v] = d;
+      if (fbm[v >> 5] & bit) atomicAnd(fbm + (v >> 5), ~bit);  // its pile entry is now stale
+    }
     if (far) fmin = min(fmin, d);
     warp_append(Rq, w + kDsR, near, v);
-    warp_append(Fq, w + kDsFar, far, v);
     warp_append(Sq, w + kDsS, near && bit_test_and_set(Sbm, v), v);
+    warp_append(pile, pile_count, far && bit_test_and_set(fbm, v), v);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
-  if (lane == 0 && fmin < INT32_MAX) atomicMin(w + kDsFarMin, fmin);
+  if (lane == 0 && fmin < INT32_MAX) atomicMin(w + kDsPileMin, fmin);
 }
 
-// far list -> next pending set N (bitmap test-and-set keeps it duplicate-free)
-__global__ void k_ds_merge(const int32_t *__restrict__ Fq, const int32_t *__restrict__ w, uint32_t *Nbm, int32_t *Nq,
-                           int32_t *Nc) {
+// Next bucket: the far pile's live entries (bit still set in fbm) below hi
+// leave it for the pending set P (queue + bitmap; P is empty here), the rest
+// are compacted into the other pile buffer, whose minimum is recomputed.
+__global__ void k_ds_pile_split(const int32_t *__restrict__ pile, const int32_t *__restrict__ pile_count,
+                                const int32_t *__restrict__ x, int32_t hi, uint32_t *fbm, int32_t *Pq, int32_t *Pc,
+                                uint32_t *Pbm, int32_t *pile2, int32_t *pile2_count, int32_t *w) {
   const int lane = threadIdx.x & 31;
-  const int32_t c = w[kDsFar];
+  const int32_t c = *pile_count;
   const int32_t stride = gridDim.x * blockDim.x;
+  int32_t fmin = INT32_MAX;
   for (int32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < c; i0 += stride) {
     const int32_t i = i0 + lane;
-    const int32_t v = i < c ? Fq[i] : -1;
-    warp_append(Nq, Nc, v >= 0 && bit_test_and_set(Nbm, v), v);
+    int32_t v = -1, d = INT32_MAX;
+    if (i < c) {
+      v = pile[i];
+      if (!bit_test(fbm, v)) v = -1;  // left the pile after it was queued
+      else d = x[v];
+    }
+    const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
+    if (near) {
+      atomicAnd(fbm + (v >> 5), ~(1u << (v & 31)));
+      atomicOr(Pbm + (v >> 5), 1u << (v & 31));
+    }
+    if (far) fmin = min(fmin, d);
+    warp_append(Pq, Pc, near, v);
+    warp_append(pile2, pile2_count, far, v);
   }
-  (void)lane;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
+  if (lane == 0 && fmin < INT32_MAX) atomicMin(w + kDsPileMin, fmin);
+}
+
+// before a pile split: the target buffer empty, its minimum to be recomputed
+__global__ void k_ds_pile_prep(int32_t *w, int32_t target) {
+  if (threadIdx.x == 0) {
+    w[target] = 0;
+    w[kDsPileMin] = INT32_MAX;
+  }
 }
 
 __global__ void k_ds_clear_s(const int32_t *__restrict__ Sq, int32_t *w, uint32_t *Sbm) {
@@ -867,17 +888,33 @@ __global__ void k_ds_zero_s(int32_t *w) {
 
 }  // namespace gi
 
+// Per-round timing of both directions from the same state (selector training
+// data, gi_selector_profile): for round i < cap, features[16 i..] and
+// times_ms[3 i..] = {SparsePush, -1 (DensePush is not offered), DensePull}.
+struct DsProfile {
+  int32_t cap = 0;
+  float *features = nullptr;
+  float *times_ms = nullptr;
+  int32_t rounds = 0;
+};
+
+// Host loop of delta-stepping.  Each round: split the changed vertices into
+// this bucket's R and the far pile (one kernel), statistics and direction for
+// R (one kernel and one host read-back), then the light relaxation of R.  When
+// R is empty the bucket's settled list S gets its heavy round; when S is empty
+// too, the far pile's entries of the next non-empty bucket become the pending
+// set.  Far vertices wait in the pile instead of being re-read every round.
 static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule &sc, gi_trace *trace,
-                         cudaStream_t s) {
+                         cudaStream_t s, DsProfile *prof = nullptr) {
   DeltaSplit *D = nullptr;
   GI_TRY(dstep_get(g, sc.delta, sc.tile_edges, s, &D));
   const int64_t n = g->n;
   const bool pull_ok = g->symmetric;
   VsetPair P;
   gi_vset R{}, S{};
-  int32_t *snap = nullptr, *Rq = nullptr, *Sq = nullptr, *Fq = nullptr;
-  uint32_t *Sbm = nullptr;
-  // the round words live in the graph's control block, so the fetch of the
+  int32_t *snap = nullptr, *Rq = nullptr, *Sq = nullptr, *pile[2] = {nullptr, nullptr};
+  uint32_t *Sbm = nullptr, *fbm = nullptr;
+  // the words live in the graph's control block, so the fetch of the
   // statistics brings them to the host in the same pinned copy
   int32_t *w = reinterpret_cast<int32_t *>(g->ctrl + kDsSlots);
   const int32_t *hw = reinterpret_cast<const int32_t *>(g->ctrl_host + kDsSlots);
@@ -885,19 +922,33 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
   if (st == GI_OK) st = dev_alloc_n(&snap, n, s);
   if (st == GI_OK) st = dev_alloc_n(&Rq, n, s);
   if (st == GI_OK) st = dev_alloc_n(&Sq, n, s);
-  if (st == GI_OK) st = dev_alloc_n(&Fq, n, s);
+  if (st == GI_OK) st = dev_alloc_n(&pile[0], n, s);
+  if (st == GI_OK) st = dev_alloc_n(&pile[1], n, s);
   if (st == GI_OK) st = dev_alloc_n(&Sbm, P.a.words, s);
+  if (st == GI_OK) st = dev_alloc_n(&fbm, P.a.words, s);
+  int32_t *prof_keep = nullptr;
+  cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+  if (prof) {
+    if (st == GI_OK) st = dev_alloc_n(&prof_keep, n, s);
+    if (st == GI_OK && (cudaEventCreate(&prof_ev[0]) != cudaSuccess || cudaEventCreate(&prof_ev[1]) != cudaSuccess))
+      st = cuda_fail(cudaGetLastError(), "event create", __FILE__, __LINE__);
+  }
   if (st == GI_OK) {
     k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(x, n, INT32_MAX);
     k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(snap, n, INT32_MAX);
     k_set_one<<<1, 1, 0, s>>>(x, src, 0);
     st = launch_status(3);
   }
-  if (st == GI_OK && cudaMemsetAsync(Sbm, 0, sizeof(uint32_t) * (size_t)P.a.words, s) != cudaSuccess)
+  if (st == GI_OK && (cudaMemsetAsync(Sbm, 0, sizeof(uint32_t) * (size_t)P.a.words, s) != cudaSuccess ||
+                      cudaMemsetAsync(fbm, 0, sizeof(uint32_t) * (size_t)P.a.words, s) != cudaSuccess))
     st = cuda_fail(cudaGetLastError(), "delta-stepping init", __FILE__, __LINE__);
   if (st == GI_OK) st = front_init(g, P.F, src, s);
-  if (st == GI_OK) st = ctrl_init(g, 0, 0, s);  // also zeroes the round words
-  // R and S are vertex sets with the queue form only; their counters are round words
+  if (st == GI_OK) st = ctrl_init(g, 0, 0, s);  // also zeroes the words
+  if (st == GI_OK) {
+    k_ds_pile_prep<<<1, 32, 0, s>>>(w, kDsPile0);  // pile minimum = INT32_MAX
+    st = launch_status(1);
+  }
+  // R and S are vertex sets with the queue form only; their counters are words
   R.g = S.g = g;
   R.n = S.n = n;
   R.queue = Rq;
@@ -907,21 +958,31 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
   S.count = w + kDsS;
   S.reps = GI_REP_SPARSE;
   int64_t hi = sc.delta;  // end of the current bucket (distance of src = 0)
+  int cur = 0;            // far-pile buffer in use
   const int grid = g->num_sms * 4;
   int32_t it = 0;
   while (st == GI_OK) {
     k_ds_round_init<<<1, 32, 0, s>>>(w);
     k_ds_split<<<grid, 256, 0, s>>>(P.F->queue, P.F->count, x, (int32_t)(hi < INT32_MAX ? hi : INT32_MAX), Rq, snap,
-                                    Sbm, Sq, Fq, w);
+                                    Sbm, Sq, fbm, pile[cur], w + kDsPile0 + cur, w);
     if ((st = launch_status(2)) != GI_OK) break;
     DecideParams p = decide_params(sc, it, false);
     if ((st = frontier_decide(g, &R, p, s, D->deg_l)) != GI_OK) break;
     if ((st = ctrl_fetch(g, s)) != GI_OK) break;
     const bool light = hw[kDsR] > 0;
     if (!light && hw[kDsS] == 0) {
-      if (hw[kDsFar] == 0) break;  // nothing pending: done
-      // the bucket is finished and its heavy arcs relaxed: next bucket
-      hi = ((int64_t)hw[kDsFarMin] / sc.delta + 1) * sc.delta;
+      if (hw[kDsPile0 + cur] == 0) break;  // nothing pending: done
+      // the bucket is finished and its heavy arcs relaxed: the far pile's
+      // entries of the next bucket become the pending set
+      hi = ((int64_t)hw[kDsPileMin] / sc.delta + 1) * sc.delta;
+      if ((st = vset_clear(P.F, s)) != GI_OK) break;
+      k_ds_pile_prep<<<1, 32, 0, s>>>(w, kDsPile0 + (cur ^ 1));
+      k_ds_pile_split<<<grid, 256, 0, s>>>(pile[cur], w + kDsPile0 + cur, x, (int32_t)(hi < INT32_MAX ? hi : INT32_MAX),
+                                           fbm, P.F->queue, P.F->count, P.F->bitmap, pile[cur ^ 1],
+                                           w + kDsPile0 + (cur ^ 1), w);
+      if ((st = launch_status(2)) != GI_OK) break;
+      P.F->reps = GI_REP_SPARSE | GI_REP_BITMAP;
+      cur ^= 1;
       continue;
     }
     gi_vset *Fr = light ? &R : &S;
@@ -937,25 +998,53 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
     if (dir == GI_DIR_DENSE_PUSH || (dir == GI_DIR_DENSE_PULL && !pull_ok)) dir = GI_DIR_SPARSE_PUSH;
     g->ctrl_host[kDecision] = dir;
     trace_put(trace, it, g->ctrl_host);
-    if ((st = vset_clear(P.N, s)) != GI_OK) break;
-    if (g->ctrl_host[kMf] > 0) {
+    const int64_t nf = g->ctrl_host[kNf], mf = g->ctrl_host[kMf];
+    auto relax = [&](int32_t d) -> int {
+      GI_TRY(vset_clear(P.N, s));
+      if (mf == 0) return GI_OK;
       OpMinInt op{x, snap, arcs.wt};
-      if (dir == GI_DIR_DENSE_PULL) {
-        st = launch_pull_tiled(g, op, arcs, light ? D->tl : D->th, FSet(), nullptr, out_of(P.N), s, kClassMinPull,
-                               sc.balance == GI_BAL_VERTEX);
-      } else {
-        g->hint_vset = Fr;
-        g->hint_nf = g->ctrl_host[kNf];
-        g->hint_mf = g->ctrl_host[kMf];
-        st = launch_push(g, op, kSrcQueue, Fr, nullptr, out_of(P.N), sc, s, &arcs);
-        g->hint_vset = nullptr;
-        g->hint_nf = g->hint_mf = -1;
+      if (d == GI_DIR_DENSE_PULL)
+        return launch_pull_tiled(g, op, arcs, light ? D->tl : D->th, FSet(), nullptr, out_of(P.N), s, kClassMinPull,
+                                 sc.balance == GI_BAL_VERTEX);
+      g->hint_vset = Fr;
+      g->hint_nf = nf;
+      g->hint_mf = mf;
+      const int r = launch_push(g, op, kSrcQueue, Fr, nullptr, out_of(P.N), sc, s, &arcs);
+      g->hint_vset = nullptr;
+      g->hint_nf = g->hint_mf = -1;
+      return r;
+    };
+    if (prof && pull_ok && prof->rounds < prof->cap) {
+      // both directions from the same state, timed; the pull's result stays
+      const float *f = reinterpret_cast<const float *>(g->ctrl_host + kFeat);
+      for (int k = 0; k < 16; ++k) prof->features[16 * prof->rounds + k] = f[k];
+      float *t3 = prof->times_ms + 3 * prof->rounds;
+      t3[1] = -1.0f;
+      const int32_t dirs[2] = {GI_DIR_SPARSE_PUSH, GI_DIR_DENSE_PULL};
+      for (int k = 0; k < 2 && st == GI_OK; ++k) {
+        if (k == 0 && cudaMemcpyAsync(prof_keep, x, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s) !=
+                          cudaSuccess)
+          st = cuda_fail(cudaGetLastError(), "snapshot", __FILE__, __LINE__);
+        if (k > 0 && cudaMemcpyAsync(x, prof_keep, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s) !=
+                         cudaSuccess)
+          st = cuda_fail(cudaGetLastError(), "restore", __FILE__, __LINE__);
+        if (st != GI_OK) break;
+        cudaEventRecord(prof_ev[0], s);
+        st = relax(dirs[k]);
+        cudaEventRecord(prof_ev[1], s);
+        if (st == GI_OK && cudaEventSynchronize(prof_ev[1]) != cudaSuccess)
+          st = cuda_fail(cudaGetLastError(), "profile sync", __FILE__, __LINE__);
+        float ms = 0.0f;
+        if (st == GI_OK) cudaEventElapsedTime(&ms, prof_ev[0], prof_ev[1]);
+        t3[k == 0 ? 0 : 2] = ms;
       }
-      if (st != GI_OK) break;
+      ++prof->rounds;
+    } else {
+      st = relax(dir);
     }
-    k_ds_merge<<<grid, 256, 0, s>>>(Fq, w, P.N->bitmap, P.N->queue, P.N->count);
+    if (st != GI_OK) break;
     k_snap_reset<<<grid, 256, 0, s>>>(Fr->queue, Fr->count, snap);
-    int launched = 2;
+    int launched = 1;
     if (!light) {  // the bucket's settled list is done with
       k_ds_clear_s<<<grid, 256, 0, s>>>(Sq, w, Sbm);
       k_ds_zero_s<<<1, 32, 0, s>>>(w);
@@ -967,11 +1056,16 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
     ++it;
   }
   if (trace) trace->iterations = it;
+  if (prof_ev[0]) cudaEventDestroy(prof_ev[0]);
+  if (prof_ev[1]) cudaEventDestroy(prof_ev[1]);
+  dev_free(prof_keep, s);
   dev_free(snap, s);
   dev_free(Rq, s);
   dev_free(Sq, s);
-  dev_free(Fq, s);
+  dev_free(pile[0], s);
+  dev_free(pile[1], s);
   dev_free(Sbm, s);
+  dev_free(fbm, s);
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "delta-stepping", __FILE__, __LINE__);
@@ -1406,6 +1500,23 @@ extern "C" int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, 
   cudaStream_t s = (cudaStream_t)stream;
   gi_schedule sc = *sched;
   sc.direction = GI_DIR_HYBRID_PULL;
+  if (kernel_id == GI_K_SSSP && sc.delta > 0) {
+    // delta-stepping rounds: SparsePush and DensePull timed from each state
+    if (!g->symmetric) {
+      set_error("delta-stepping profiles need a symmetric graph (the pull relaxes the split arcs as in-edges)");
+      return GI_ERR_UNSUPPORTED;
+    }
+    int32_t *x = nullptr;
+    GI_TRY(dev_alloc_n(&x, g->n, s));
+    DsProfile prof;
+    prof.cap = cap;
+    prof.features = features;
+    prof.times_ms = times_ms;
+    const int st = deltastep_run(g, x, src, sc, nullptr, s, &prof);
+    dev_free(x, s);
+    *levels = prof.rounds;
+    return st;
+  }
   GI_TRY(ensure_tiles(g, sc, s));
   const bool bfs = kernel_id == GI_K_BFS;
   VsetPair P;

@@ -44,12 +44,14 @@ struct BatchGraph {
   int64_t n, m;
   int32_t maxdeg;
   int32_t delta;  // SSSP distance-threshold step (0: relax every frontier source each round)
+  int32_t t_warp, t_cta;  // expansion bins: sources with >= t_cta arcs go to the CTA, >= t_warp to a warp
 };
 
 struct BatchQuery {
   int32_t graph, src, algo;
   int32_t *out;
-  int32_t index;  // position in the caller's query arrays (times and levels are reported there)
+  int32_t index;    // position in the caller's query arrays (times and levels are reported there)
+  int32_t *parent;  // BFS: canonical parents (NULL: depths only)
 };
 
 struct ClusterWs {  // per-cluster working memory (device pointers)
@@ -198,7 +200,8 @@ struct KeepAll {
   __device__ bool operator()(int32_t, int32_t) const { return true; }
 };
 
-template <class Fn, class Keep = KeepAll>
+// kSrcValue: fn receives the source id itself as its value (BFS parents).
+template <class Fn, class Keep = KeepAll, bool kSrcValue = false>
 __device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_t *curd, const int32_t *live,
                            int64_t nf, int rank, int csize, Fn &fn, Keep keep = Keep()) {
   __shared__ int32_t s_owner, s_a, s_d, s_du;
@@ -211,7 +214,7 @@ __device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_
     int32_t a = 0, d = 0, du = 0;
     if (i < nf) {
       const int32_t u = cur[i];
-      du = curd ? curd[i] : (live ? *(volatile const int32_t *)(live + u) : 0);
+      du = kSrcValue ? u : (curd ? curd[i] : (live ? *(volatile const int32_t *)(live + u) : 0));
       if (keep(u, du)) {
         a = __ldg(G.ptr + u);
         d = __ldg(G.ptr + u + 1) - a;
@@ -220,7 +223,7 @@ __device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_
     while (true) {
       if (tid == 0) s_owner = -1;
       __syncthreads();
-      if (d >= 1024) s_owner = tid;
+      if (d >= G.t_cta) s_owner = tid;
       __syncthreads();
       const int owner = s_owner;
       if (owner < 0) break;
@@ -235,7 +238,7 @@ __device__ void cta_expand(const BatchGraph &G, const int32_t *cur, const int32_
       __syncthreads();
     }
     while (true) {
-      const unsigned bal = __ballot_sync(0xffffffffu, d >= 32);
+      const unsigned bal = __ballot_sync(0xffffffffu, d >= G.t_warp);
       if (!bal) break;
       const int l = __ffs(bal) - 1;
       const int32_t wa = __shfl_sync(0xffffffffu, a, l), wd = __shfl_sync(0xffffffffu, d, l),
@@ -312,15 +315,25 @@ __device__ __forceinline__ void append_batch(const bool (&want)[kBatchArcs], con
 
 // BFS SparsePush of this level's queue: newly reached vertices get depth L+1
 // and join the next queue (their out-degrees summed into the edge count).
-__device__ void batch_bfs_push(const BatchGraph &G, int32_t *depth, const int32_t *cur, int64_t nf, int32_t *next,
-                               int64_t *ncnt, int64_t *necnt, int32_t L, int rank, int csize) {
+// With parents, every source u reaching a vertex of depth L+1 lowers its
+// parent to u by atomicMin (after a plain read shows u is smaller), so the
+// parent ends as the smallest-id in-neighbour one level closer.
+__device__ void batch_bfs_push(const BatchGraph &G, int32_t *depth, int32_t *parent, const int32_t *cur, int64_t nf,
+                               int32_t *next, int64_t *ncnt, int64_t *necnt, int32_t L, int rank, int csize) {
   // a batch's claims first, then one append and one edge-count add per warp
-  auto fn = [&](const int32_t (&)[kBatchArcs], const int32_t (&)[kBatchArcs], const int32_t (&v)[kBatchArcs]) {
+  auto fn = [&](const int32_t (&u)[kBatchArcs], const int32_t (&)[kBatchArcs], const int32_t (&v)[kBatchArcs]) {
     bool won[kBatchArcs];
 #pragma unroll
     for (int j = 0; j < kBatchArcs; ++j) {
       won[j] = false;
-      if (v[j] >= 0 && *(volatile int32_t *)(depth + v[j]) == -1) won[j] = atomicCAS(depth + v[j], -1, L + 1) == -1;
+      if (v[j] < 0) continue;
+      int32_t d = *(volatile int32_t *)(depth + v[j]);
+      if (d == -1) {
+        d = atomicCAS(depth + v[j], -1, L + 1);
+        won[j] = d == -1;
+        if (won[j]) d = L + 1;
+      }
+      if (parent && d == L + 1 && u[j] < *(volatile int32_t *)(parent + v[j])) atomicMin(parent + v[j], u[j]);
     }
     append_batch(won, v, next, ncnt);
     // the won vertices are distinct, so a warp's degree sum is below m < 2^31
@@ -333,12 +346,13 @@ __device__ void batch_bfs_push(const BatchGraph &G, int32_t *depth, const int32_
     if (wdeg && (threadIdx.x & 31) == __ffs(active) - 1)
       atomicAdd(reinterpret_cast<unsigned long long *>(necnt), (unsigned long long)wdeg);
   };
-  cta_expand(G, cur, nullptr, nullptr, nf, rank, csize, fn);
+  cta_expand<decltype(fn), KeepAll, true>(G, cur, nullptr, nullptr, nf, rank, csize, fn);
 }
 
-// BFS DensePull with early exit: the frontier is {u : depth[u] == L}
-__device__ void batch_bfs_pull(const BatchGraph &G, int32_t *depth, int32_t *next, int64_t *ncnt, int64_t *necnt,
-                               int32_t L, int rank, int csize) {
+// BFS DensePull with early exit: the frontier is {u : depth[u] == L}; the
+// first frontier in-neighbour in ascending order is the canonical parent.
+__device__ void batch_bfs_pull(const BatchGraph &G, int32_t *depth, int32_t *parent, int32_t *next, int64_t *ncnt,
+                               int64_t *necnt, int32_t L, int rank, int csize) {
   // as the single-query early-exit pull: each lane probes its row's first 4
   // arcs before any warp-wide scan, the next rows' depth and bounds are
   // fetched under the current probe, found vertices are staged per warp and
@@ -380,12 +394,17 @@ __device__ void batch_bfs_pull(const BatchGraph &G, int32_t *depth, int32_t *nex
     const bool active = v < G.n && dv == -1;
     if (!active) b = a;
     bool found = false;
+    int32_t par = -1;
     for (int32_t e = a; e < b && !found; e += 4) {
       int32_t u[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) u[j] = e + j < b ? G.iidx[e + j] : -1;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) found |= u[j] >= 0 && depth[u[j]] == L;
+      for (int j = 3; j >= 0; --j)
+        if (u[j] >= 0 && depth[u[j]] == L) {
+          found = true;
+          par = u[j];
+        }
       if (b - a >= 32) break;
     }
     const bool big = active && !found && (b - a) >= 32;
@@ -394,15 +413,21 @@ __device__ void batch_bfs_pull(const BatchGraph &G, int32_t *depth, int32_t *nex
       const int l = __ffs(bal) - 1;
       bal &= bal - 1;
       const int32_t lb = __shfl_sync(0xffffffffu, b, l), la = __shfl_sync(0xffffffffu, a, l) + 4;
-      bool hit = false;
-      for (int32_t base = la; base < lb && !hit; base += 32) {
+      int32_t hit = -1;
+      for (int32_t base = la; base < lb && hit < 0; base += 32) {
         const int32_t e = base + lane;
-        hit = __ballot_sync(0xffffffffu, e < lb && depth[G.iidx[e]] == L) != 0;
+        const int32_t u = e < lb ? G.iidx[e] : -1;
+        const unsigned h = __ballot_sync(0xffffffffu, u >= 0 && depth[u] == L);
+        if (h) hit = __shfl_sync(0xffffffffu, u, __ffs(h) - 1);
       }
-      if (lane == l) found = hit;
+      if (lane == l && hit >= 0) {
+        found = true;
+        par = hit;
+      }
     }
     if (found) {
       depth[v] = L + 1;
+      if (parent) parent[v] = par;
       edges += (unsigned long long)(G.ptr[v + 1] - G.ptr[v]);
     }
     const unsigned word = __ballot_sync(0xffffffffu, found);
@@ -513,6 +538,8 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
     if (gtid == 0) t0 = global_ns();
     const bool bfs = Q.algo == GI_ALGO_BFS;
     for (int64_t v = gtid; v < G.n; v += T) Q.out[v] = bfs ? -1 : INT32_MAX;
+    if (bfs && Q.parent)
+      for (int64_t v = gtid; v < G.n; v += T) Q.parent[v] = v == Q.src ? Q.src : INT32_MAX;
     if (!bfs)
       for (int64_t w = gtid; w < (G.n + 31) / 32; w += T) W.inq[w] = 0u;
     if (gtid == 0) {
@@ -554,8 +581,8 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
         const bool pull = (mode == 0) ? false
                                       : batch_decide_pull(G, nf, mf, nu, mu, L, was_pull, nf_prev, mode, alpha, beta,
                                                           sh);
-        if (pull) batch_bfs_pull(G, Q.out, next, ncnt, necnt, L, rank, csize);
-        else batch_bfs_push(G, Q.out, cur, nf, next, ncnt, necnt, L, rank, csize);
+        if (pull) batch_bfs_pull(G, Q.out, Q.parent, next, ncnt, necnt, L, rank, csize);
+        else batch_bfs_push(G, Q.out, Q.parent, cur, nf, next, ncnt, necnt, L, rank, csize);
         was_pull = pull ? 1 : 0;
         nf_prev = nf;
         if (!bar()) return;
@@ -572,6 +599,11 @@ __global__ void __launch_bounds__(kBT) k_batch(const BatchGraph *__restrict__ gr
         if (G.delta > 0 && *(volatile int64_t *)(W.cnt + 8 + L % 4) == 0)
           theta = *(volatile int64_t *)(W.cnt + 12 + L % 4) + G.delta;  // nothing was near: move past the nearest
       }
+    }
+    if (bfs && Q.parent) {  // unreached vertices: -1
+      if (!bar()) return;
+      for (int64_t v = gtid; v < G.n; v += T)
+        if (Q.parent[v] == INT32_MAX) Q.parent[v] = -1;
     }
     if (gtid == 0 && q_ns) q_ns[Q.index] = (int64_t)(global_ns() - t0);
     if (gtid == 0 && q_levels) q_levels[Q.index] = levels;
@@ -635,6 +667,9 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
   GI_ARG(o.selector == GI_DIR_SPARSE_PUSH || o.selector == GI_DIR_HYBRID_PULL || o.selector == GI_DIR_LEARNED,
          "selector must be GI_DIR_SPARSE_PUSH, GI_DIR_HYBRID_PULL or GI_DIR_LEARNED");
   GI_ARG(o.order == 0 || o.order == 1, "order must be 0 (as given) or 1 (largest first)");
+  const int32_t tw = o.t_warp > 0 ? o.t_warp : 32, tc = o.t_cta > 0 ? o.t_cta : 1024;
+  GI_ARG(tw >= 1 && tw <= 32, "t_warp must be in [1, 32] (0: 32)");
+  GI_ARG(tc >= tw, "t_cta must be >= t_warp (0: 1024)");
   std::vector<BatchGraph> hg(n_graphs);
   int64_t nmax = 1;
   for (int i = 0; i < n_graphs; ++i) {
@@ -646,7 +681,8 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
       delta = (int32_t)fmin(scale * g->wt_mean + 0.5, 1e9);
       if (delta < 1) delta = 1;
     }
-    hg[i] = BatchGraph{g->out.ptr, g->out.idx, g->out.wt, g->in.ptr, g->in.idx, g->n, g->m, g->max_deg, delta};
+    hg[i] = BatchGraph{g->out.ptr, g->out.idx, g->out.wt, g->in.ptr, g->in.idx, g->n, g->m, g->max_deg, delta,
+                       tw, tc};
     nmax = g->n > nmax ? g->n : nmax;
   }
   std::vector<BatchQuery> hq(n_q);
@@ -659,7 +695,9 @@ extern "C" int gi_batch_plan_create(gi_graph *const *graphs, int32_t n_graphs, c
     if (q_algo[i] == GI_ALGO_BFS && o.selector != GI_DIR_SPARSE_PUSH)
       GI_ARG(g->has_csc, "pull levels need the in-edges (symmetric graph or gi_load_csc)");
     GI_ARG(out_dev[i] != nullptr, "NULL output");
-    hq[i] = BatchQuery{q_graph[i], q_src[i], q_algo[i], out_dev[i], i};
+    int32_t *par = (o.parents && q_algo[i] == GI_ALGO_BFS) ? o.parents[i] : nullptr;
+    GI_ARG(par == nullptr || (par != out_dev[i]), "a parent array aliases its depth array");
+    hq[i] = BatchQuery{q_graph[i], q_src[i], q_algo[i], out_dev[i], i, par};
   }
   if (o.order == 1) {
     // largest first (longest-processing-time order): vertex count is the proxy
@@ -820,4 +858,7 @@ extern "C" void gi_batch_opts_default(gi_batch_opts *o) {
   o->levels = nullptr;
   o->sssp_delta = 0.0f;
   o->order = 1;
+  o->t_warp = 32;
+  o->t_cta = 1024;
+  o->parents = nullptr;
 }

@@ -213,6 +213,7 @@ int check_schedule(const gi_schedule *sc) {
   GI_ARG(sc->seg_strategy == GI_SEG_FVC || sc->seg_strategy == GI_SEG_EVC, "seg_strategy must be FVC or EVC");
   GI_ARG(sc->persistent >= 0 && sc->persistent <= 2, "persistent must be 0, 1 or 2");
   GI_ARG(sc->delta >= 0, "delta must be >= 0");
+  GI_ARG(sc->block == 128 || sc->block == 256 || sc->block == 512, "block must be 128, 256 or 512");
   return GI_OK;
 }
 

@@ -1042,19 +1042,29 @@ constexpr int kPushBlock = 256;
 constexpr int32_t kHeavyChunk = 4096;  // arcs per chunk of a deferred high-degree source
 constexpr int kMaxTWarp = 64;  // owner table holds kPushBlock * (kMaxTWarp - 1) arcs
 
-template <class Op, int kMode>
-__global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__restrict__ ptr,
+// Owner table of the scan-based gathering: one entry per arc of the block's
+// small sources (below t_warp arcs each); 512-thread blocks need 16-bit owners
+// and hold sources below 32 arcs, to stay within 48 KB of shared memory.
+template <int kBlock>
+struct PushOwners {
+  using T = std::conditional_t<(kBlock > 256), uint16_t, uint8_t>;
+  static constexpr int kMaxTW = kBlock > 256 ? 32 : kMaxTWarp;
+};
+
+template <class Op, int kMode, int kBlock = kPushBlock>
+__global__ void __launch_bounds__(kBlock) k_push(Op op, const int32_t *__restrict__ ptr,
                                                      const int32_t *__restrict__ idx, const int32_t *__restrict__ q,
                                                      const int32_t *__restrict__ qcount, FSet Fbm, int64_t n,
                                                      const uint32_t *__restrict__ to, OutSet out, int32_t t_warp,
                                                      int32_t t_cta, int32_t t_heavy, void *heavy_mem) {
   __shared__ int32_t s_owner, s_u, s_a, s_deg;
-  __shared__ int32_t s_src[kPushBlock], s_beg[kPushBlock], s_off[kPushBlock], s_sw[32];
-  __shared__ uint8_t s_own[kPushBlock * (kMaxTWarp - 1)];
+  __shared__ int32_t s_src[kBlock], s_beg[kBlock], s_off[kBlock], s_sw[32];
+  using Own = typename PushOwners<kBlock>::T;
+  __shared__ Own s_own[kBlock * (PushOwners<kBlock>::kMaxTW - 1)];
   const int tid = threadIdx.x, lane = tid & 31;
-  const bool fine = t_warp <= kMaxTWarp;  // scan-based gathering of small sources
+  const bool fine = t_warp <= PushOwners<kBlock>::kMaxTW;  // scan-based gathering of small sources
   const int64_t total = (kMode == kSrcQueue) ? (int64_t)(*qcount) : n;
-  for (int64_t base = (int64_t)blockIdx.x * kPushBlock; base < total; base += (int64_t)gridDim.x * kPushBlock) {
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < total; base += (int64_t)gridDim.x * kBlock) {
     const int64_t i = base + tid;
     int32_t u = -1, a = 0, deg = 0;
     if (i < total) {
@@ -1091,7 +1101,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__res
         deg = 0;
       }
       __syncthreads();
-      push_strided(op, s_u, s_a, s_deg, tid, kPushBlock, idx, to, out);
+      push_strided(op, s_u, s_a, s_deg, tid, kBlock, idx, to, out);
       __syncthreads();
     }
     // warp-cooperative expansion
@@ -1110,13 +1120,13 @@ __global__ void __launch_bounds__(kPushBlock) k_push(Op op, const int32_t *__res
       s_src[tid] = u;
       s_beg[tid] = a;
       s_off[tid] = off;
-      for (int32_t k = 0; k < deg; ++k) s_own[off + k] = (uint8_t)tid;
+      for (int32_t k = 0; k < deg; ++k) s_own[off + k] = (Own)tid;
       __syncthreads();
-      for (int32_t j0 = tid; j0 < T; j0 += kPushBatch * kPushBlock) {
+      for (int32_t j0 = tid; j0 < T; j0 += kPushBatch * kBlock) {
         int32_t uu[kPushBatch], ee[kPushBatch], vv[kPushBatch];
 #pragma unroll
         for (int b = 0; b < kPushBatch; ++b) {
-          const int32_t j = j0 + b * kPushBlock;
+          const int32_t j = j0 + b * kBlock;
           if (j < T) {
             const int o = s_own[j];
             uu[b] = s_src[o];
@@ -1351,65 +1361,6 @@ struct OpBFSPull {
   }
 };
 
-// Canonical BFS parents for vertices discovered by push levels (which set
-// depth only): the smallest-id in-neighbour one level closer, found by
-// scanning the sorted in-neighbours (4 per round trip; a warp 32 at a time
-// for rows of >= t_warp arcs).  Vertices found by pull levels already hold it.
-static __global__ void __launch_bounds__(256) k_bfs_parents(const int32_t *__restrict__ ptr,
-                                                            const int32_t *__restrict__ idx, int64_t n,
-                                                            const int32_t *__restrict__ depth, int32_t *parent,
-                                                            int32_t t_warp) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (n + 31) >> 5;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
-       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int64_t v = w * 32 + lane;
-    int32_t target = -1, a = 0, b = 0;
-    if (v < n) {
-      const int32_t d = depth[v];
-      if (d > 0 && parent[v] == INT32_MAX) {
-        target = d - 1;
-        a = __ldg(ptr + v);
-        b = __ldg(ptr + v + 1);
-      }
-    }
-    int32_t found = -1;
-    const bool big = target >= 0 && (b - a) >= t_warp;
-    if (target >= 0 && !big) {
-      for (int32_t e = a; e < b && found < 0; e += 4) {
-        int32_t u[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) u[j] = e + j < b ? __ldg(idx + e + j) : -1;
-        bool h[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) h[j] = u[j] >= 0 && depth[u[j]] == target;
-#pragma unroll
-        for (int j = 3; j >= 0; --j)
-          if (h[j]) found = u[j];
-      }
-    }
-    unsigned bal = __ballot_sync(0xffffffffu, big);
-    while (bal) {
-      const int l = __ffs(bal) - 1;
-      bal &= bal - 1;
-      const int32_t la = __shfl_sync(0xffffffffu, a, l), lb = __shfl_sync(0xffffffffu, b, l),
-                    lt = __shfl_sync(0xffffffffu, target, l);
-      int32_t hit = -1;
-      for (int32_t base = la; base < lb; base += 32) {
-        const int32_t e = base + lane;
-        const int32_t u = e < lb ? __ldg(idx + e) : 0;
-        const unsigned hm = __ballot_sync(0xffffffffu, e < lb && depth[u] == lt);
-        if (hm) {
-          hit = __shfl_sync(0xffffffffu, u, __ffs(hm) - 1);
-          break;
-        }
-      }
-      if (lane == l) found = hit;
-    }
-    if (found >= 0) parent[v] = found;
-  }
-}
-
 }  // namespace gi
 
 // =================================================================== host side ==
@@ -1631,9 +1582,21 @@ int launch_push(gi_graph *g, const Op &op, int mode, const gi_vset *from, const 
   int grid;
   const int tok = timing_begin(kClassPush, s);
   if (mode == kSrcQueue) {
-    grid = g->num_sms * (2048 / block);
-    k_push<Op, kSrcQueue><<<grid, block, 0, s>>>(op, c.ptr, c.idx, from->queue, from->count, nullptr, g->n,
-                                                 to, out, tw, tc, th, heavy);
+    // SparsePush takes the schedule's block size (128, 256 or 512 threads);
+    // the grid keeps 2048 threads per SM
+    const int qb = sc.block == 128 || sc.block == 512 ? sc.block : 256;
+    grid = g->num_sms * (2048 / qb);
+    if (qb == 512 && tw != INT32_MAX && tw > PushOwners<512>::kMaxTW) tw = PushOwners<512>::kMaxTW;
+    if (tc < tw) tc = tw;
+    if (qb == 128)
+      k_push<Op, kSrcQueue, 128><<<grid, 128, 0, s>>>(op, c.ptr, c.idx, from->queue, from->count, nullptr, g->n, to,
+                                                      out, tw, tc, th, heavy);
+    else if (qb == 512)
+      k_push<Op, kSrcQueue, 512><<<grid, 512, 0, s>>>(op, c.ptr, c.idx, from->queue, from->count, nullptr, g->n, to,
+                                                      out, tw, tc, th, heavy);
+    else
+      k_push<Op, kSrcQueue><<<grid, block, 0, s>>>(op, c.ptr, c.idx, from->queue, from->count, nullptr, g->n, to,
+                                                   out, tw, tc, th, heavy);
   } else if (mode == kSrcBitmap) {
     grid = grid_for(g, g->n, block, 2048 / block);
     const FSet fs = (sc.dense_rep == GI_REP_BOOL && from->boolmap && (from->reps & GI_REP_BOOL))

@@ -5,11 +5,13 @@
 Training data are per-level timings of SparsePush, DensePush and DensePull
 (gi_selector_profile) for BFS and SSSP on seeded synthetic graphs: R-MAT graphs
 of scales 12-22 with edge factors 8-32 (social/web-like) and 2-D grids with 1%
-local shortcuts of sides 128-2048 (road-like), several sources each.  The
-network learns log(time in us) of each direction; training is full-batch Adam
-with the library's own kernels.  Held-out graphs (other seeds) report the
-recorded cost of the learned choices against Beamer's rule and the
-per-level optimum.
+local shortcuts of sides 128-2048 (road-like), several sources each.  SSSP is
+profiled both in synchronous Bellman-Ford rounds and in delta-stepping rounds
+(gi_schedule.delta; there DensePush is not offered and its target is masked
+out).  The network learns log(time in us) of each direction; training is
+full-batch Adam with the library's own kernels.  Held-out graphs (other seeds)
+report the recorded cost of the learned choices against Beamer's / Ligra's
+rule and the per-level optimum.
 """
 from __future__ import annotations
 
@@ -36,6 +38,11 @@ def workloads(seed_base: int, quick: bool):
     for sc in scales:
         out.append(("sssp", f"rmat{sc}_w", lambda sc=sc: gg.rmat_graph(sc, 16, seed=seed_base + 50 + sc,
                                                                          weights=(1, 1000))))
+    # delta-stepping rounds (bucket widths around the bench's 64 for weights in [1,1000))
+    for sc in scales:
+        for d in (32, 64, 128):
+            out.append((f"sssp_ds{d}", f"rmat{sc}_w", lambda sc=sc: gg.rmat_graph(sc, 16, seed=seed_base + 50 + sc,
+                                                                                 weights=(1, 1000))))
     sides = [128, 256, 512] if quick else [128, 256, 512, 1024, 2048]
     for side in sides:
         out.append(("bfs", f"grid{side}", lambda side=side: gg.grid_graph(side, seed=seed_base + side)))
@@ -43,6 +50,16 @@ def workloads(seed_base: int, quick: bool):
         out.append(("sssp", f"grid{side}_w", lambda side=side: gg.grid_graph(side, seed=seed_base + 7 * side,
                                                                              weights=(1, 100))))
     return out
+
+
+def _sched(algo):
+    """(kernel id, profiling schedule) of a workload tag: bfs, sssp or sssp_ds<delta>."""
+    import paper_1805_00923_gb300 as gi
+    if algo == "bfs":
+        return gi.GI_K_BFS, gi.schedule("hybrid_pull")
+    if algo.startswith("sssp_ds"):
+        return gi.GI_K_SSSP, gi.schedule("hybrid_pull", delta=int(algo[len("sssp_ds"):]))
+    return gi.GI_K_SSSP, gi.schedule("hybrid_pull")
 
 
 def collect(items, n_src: int, max_levels_per_run: int = 400):
@@ -53,9 +70,9 @@ def collect(items, n_src: int, max_levels_per_run: int = 400):
     for algo, name, make in items:
         hg = make()
         g = gi.Graph.from_host(hg)
-        kern = gi.GI_K_BFS if algo == "bfs" else gi.GI_K_SSSP
+        kern, sc = _sched(algo)
         for s in gg.pick_sources(hg, n_src, seed=len(name)):
-            f, t = sel.profile(g, kern, int(s))
+            f, t = sel.profile(g, kern, int(s), sched=sc)
             if len(f) > max_levels_per_run:  # keep long road-like runs from swamping the data
                 keep = np.linspace(0, len(f) - 1, max_levels_per_run).astype(int)
                 f, t = f[keep], t[keep]
@@ -75,17 +92,21 @@ def evaluate(params, mean, inv_std, items, n_src: int):
     for algo, name, make in items:
         hg = make()
         g = gi.Graph.from_host(hg)
-        kern = gi.GI_K_BFS if algo == "bfs" else gi.GI_K_SSSP
+        kern, sc = _sched(algo)
         tot = np.zeros(3)
         for s in gg.pick_sources(hg, n_src, seed=99):
-            f, t = sel.profile(g, kern, int(s))
+            f, t = sel.profile(g, kern, int(s), sched=sc)
             tr = gi.Trace(1 << 16)
             if algo == "bfs":
-                gi.bfs(g, int(s), want_parent=False, sched=gi.schedule("hybrid_pull"), trace=tr)
+                gi.bfs(g, int(s), want_parent=False, sched=sc, trace=tr)
             else:
-                gi.sssp(g, int(s), sched=gi.schedule("hybrid_pull"), trace=tr)
+                gi.sssp(g, int(s), sched=sc, trace=tr)
             rule = tr.as_dict()["direction"][:len(t)]
             learned = sel.choose(params, mean, inv_std, f)
+            # where a direction was not offered (masked, time < 0) the driver
+            # runs SparsePush instead
+            learned = np.where(t[np.arange(len(t)), learned] < 0, 0, learned)
+            t = np.where(t < 0, np.inf, t)
             idx = np.arange(len(t))
             tot += [t[idx, learned].sum(), t[idx, rule].sum(), t.min(axis=1).sum()]
         rows.append(dict(graph=f"{algo}:{name}", learned_ms=tot[0], rule_ms=tot[1], best_ms=tot[2]))
@@ -108,8 +129,9 @@ def main():
     t0 = time.time()
     X, Tms, tags = collect(workloads(1000, args.quick), args.sources)
     t1 = time.time()
-    T = sel.targets(Tms)
-    params, mean, inv_std, losses = sel.train(X, T, steps=args.steps)
+    M = (Tms > 0).astype(np.float32)   # directions not offered in a mode are masked out
+    T = sel.targets(np.where(Tms > 0, Tms, 1.0))
+    params, mean, inv_std, losses = sel.train(X, T, M=M, steps=args.steps)
     t2 = time.time()
     sel.save(args.out, params, mean, inv_std, samples=X.shape[0], steps=args.steps, losses=np.array(losses))
     held = [it for it in workloads(5000, True)]
@@ -117,7 +139,8 @@ def main():
     tot = {k: float(sum(r[k] for r in rows)) for k in ("learned_ms", "rule_ms", "best_ms")}
     report = dict(samples=int(X.shape[0]), collect_s=t1 - t0, train_s=t2 - t1, loss_first=losses[0],
                   loss_last=losses[-1], heldout=rows, heldout_total=tot,
-                  train_choice_share=np.bincount(np.argmin(Tms, 1), minlength=3).tolist())
+                  train_choice_share=np.bincount(np.argmin(np.where(Tms > 0, Tms, np.inf), 1),
+                                                 minlength=3).tolist())
     txt = json.dumps(report, indent=1, default=float)
     print(txt)
     if args.report:

@@ -52,6 +52,56 @@ def test_batch_matches_oracle(gi, cluster, selector):
     assert (ns > 0).all()
 
 
+@pytest.mark.parametrize("cluster", [0, 1, 4])
+@pytest.mark.parametrize("selector", ["sparse_push", "hybrid_pull"])
+def test_batch_bfs_parents(gi, cluster, selector):
+    """BFS queries with a parent array get the canonical (smallest-id) parent
+    of gi_bfs and the oracle, bit-exact; SSSP queries beside them are unchanged."""
+    import torch
+    hgs = _graphs()
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    qs = _queries(hgs, 24, seed=20 + cluster)
+    pars = [torch.empty(max(hgs[g_].n, 1), dtype=torch.int32, device="cuda") if a == "bfs" else None
+            for g_, _, a in qs]
+    res, _ = gi.batch_run(gs, qs, opts=gi.batch_opts(cluster_size=cluster, selector=selector), parents=pars)
+    _check(hgs, qs, res)
+    for (gidx, src, algo), par in zip(qs, pars):
+        if algo == "bfs":
+            assert np.array_equal(par[:hgs[gidx].n].cpu().numpy(), oracle.bfs(hgs[gidx], src)[1]), (gidx, src)
+
+
+@pytest.mark.parametrize("tw,tc", [(1, 1), (8, 64), (32, 32), (16, 4096)])
+def test_batch_bin_thresholds(gi, tw, tc):
+    """Every expansion bin setting (thread / warp / CTA by degree) gives the oracle's results."""
+    hgs = _graphs()
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    qs = _queries(hgs, 32, seed=tw + tc)
+    res, _ = gi.batch_run(gs, qs, opts=gi.batch_opts(cluster_size=2, t_warp=tw, t_cta=tc))
+    _check(hgs, qs, res)
+
+
+def test_batch_bin_thresholds_rejected(gi):
+    hgs = _graphs()[:1]
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    for tw, tc in ((33, 1024), (16, 8)):
+        with pytest.raises(gi.GIError) as e:
+            gi.batch_run(gs, [(0, 0, "bfs")], opts=gi.batch_opts(t_warp=tw, t_cta=tc))
+        assert e.value.code == -1
+
+
+def test_batch_autotune_returns_valid_faster_options(gi):
+    """gi_batch_autotune: the best options found time no slower than the start
+    and still give the oracle's results for every query."""
+    hgs = _graphs()
+    gs = [gi.Graph.from_host(h) for h in hgs]
+    qs = _queries(hgs, 32, seed=77)
+    best, best_ms, start_ms = gi.batch_autotune(gs, qs, start=gi.batch_opts(cluster_size=4), budget=8, seed=5)
+    assert best_ms <= start_ms
+    assert best.cluster_size in (1, 2, 4, 8) and 1 <= best.t_warp <= 32 and best.t_cta >= best.t_warp
+    res, _ = gi.batch_run(gs, qs, opts=best)
+    _check(hgs, qs, res)
+
+
 def test_batch_fewer_clusters_than_queries(gi):
     hgs = _graphs()
     gs = [gi.Graph.from_host(h) for h in hgs]

@@ -441,6 +441,29 @@ def test_pull_tile_sizes(gi, te):
 
 # ----------------------------------------------------------------- autotuner
 
+@pytest.mark.parametrize("block", [128, 512])
+@pytest.mark.parametrize("direction", ["sparse_push", "hybrid_pull"])
+def test_push_block_sizes(gi, direction, block):
+    """SparsePush in 128- and 512-thread blocks (gi_schedule.block) keeps every result exact."""
+    hg = rmat(14, weights=True)
+    g = _load(gi, hg)
+    for src in (0, 77):
+        wd, wp, _ = oracle.bfs(hg, src)
+        d, p = gi.bfs(g, src, sched=gi.schedule(direction, block=block))
+        assert np.array_equal(_np(d), wd) and np.array_equal(_np(p), wp)
+        assert np.array_equal(_np(gi.sssp(g, src, sched=gi.schedule(direction, block=block))), oracle.sssp(hg, src)[0])
+        assert np.array_equal(_np(gi.sssp(g, src, sched=gi.schedule(direction, block=block, delta=40))),
+                              oracle.sssp(hg, src)[0])
+    assert np.array_equal(_np(gi.cc(g, sched=gi.schedule(direction, block=block))), oracle.cc(hg)[0])
+
+
+def test_schedule_block_must_be_a_supported_size(gi):
+    g = _load(gi, rmat(10))
+    with pytest.raises(gi.GIError) as e:
+        gi.bfs(g, 0, sched=gi.schedule("sparse_push", block=192))
+    assert e.value.code == -1
+
+
 @pytest.mark.parametrize("algo", ["bfs", "sssp", "cc", "pagerank", "pagerank_delta"])
 def test_autotune_returns_valid_faster_schedule(gi, algo):
     hg = rmat(14, weights=True)
