@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--m-scale", type=int, default=22, help="R-MAT scale of the PR/PRD/CC workload (and BC)")
     p.add_argument("--m-steps", type=int, default=5, help="timed steps of the PR/PRD/CC extra")
     p.add_argument("--e2e-steps", type=int, default=2)
-    p.add_argument("--repeats", type=int, default=3, help="repeats of the learned vs Beamer comparison")
+    p.add_argument("--repeats", type=int, default=3, help="repeats of the learned vs rule comparison")
+    p.add_argument("--delta", type=int, default=128, help="SSSP bucket width the autotuner starts from")
     p.add_argument("--exhaustive-sources", type=int, default=8)
     p.add_argument("--cpu-sources", type=int, default=4, help="sources of the CPU oracle sample (BFS + SSSP)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="PR/PRD/CC workload: CPU time of the oracle sample")
@@ -574,17 +575,27 @@ def run_bc(args):
     return 0
 
 
-def _sssp_pull_bytes(n, m, tr):
-    """Algorithmic bytes of the SSSP DensePull rounds of one traced query:
-    4(V+1) offsets + 8m (index and frontier test per arc) + 8 m_f (weight and
-    distance per frontier arc) + V/4 (bitmaps) + 4|F_next| per pull round."""
+def _sssp_pull_bytes(n, m, tr, m_light=None):
+    """Algorithmic bytes of the SSSP DensePull rounds of one traced query, per
+    pull round 4(V+1) offsets + 8m' (index and frontier-folded distance per
+    arc) + 8 m_f (weight and distance per source arc) + V/4 (bitmaps) +
+    4|F_next|, where m' is the arcs the round scans: m for Bellman-Ford, the
+    light or heavy arc count for a delta-stepping round (phase 0 / 1; then
+    |F_next| is not recorded and the term is left out)."""
+    import numpy as np
     t = tr.as_dict()
     fr, ed, dr = t["frontier"], t["edges"], t["direction"]
+    ph = t.get("phase", np.zeros(len(dr), np.int32))
     total, rounds = 0, 0
     for i in range(len(dr)):
         if dr[i] == 2:  # GI_DIR_DENSE_PULL
-            nxt = int(fr[i + 1]) if i + 1 < len(fr) else 0
-            total += 4 * (n + 1) + 8 * m + 8 * int(ed[i]) + n // 4 + 4 * nxt
+            if m_light is None:
+                scanned = m
+                nxt = int(fr[i + 1]) if i + 1 < len(fr) else 0
+            else:
+                scanned = m_light if ph[i] == 0 else m - m_light
+                nxt = 0
+            total += 4 * (n + 1) + 8 * scanned + 8 * int(ed[i]) + n // 4 + 4 * nxt
             rounds += 1
     return total, rounds
 
@@ -627,7 +638,7 @@ def oracle_queries(hg, queries, threads):
     return time.perf_counter() - t0, arcs
 
 
-def l_config(hg, n_sources):
+def l_config(hg, n_sources, delta=None):
     return {"workload": "rmat24_bfs_sssp", "graph": "R-MAT symmetrized, int32 weights uniform in [1,1000)",
             "scale": max(0, int(hg.n).bit_length() - 1), "edge_factor": 16, "abc": [0.57, 0.19, 0.19],
             "seed": 1, "n": hg.n, "m": hg.m, "sources": n_sources,
@@ -635,16 +646,19 @@ def l_config(hg, n_sources):
             "step": f"BFS (depth + canonical parent) then SSSP (distance) from each of the {n_sources} sources",
             "gteps_numerator": "per query the sum of degrees of the reached vertices (arcs of the reached "
                                "component, both directions); Graph500 count = half",
-            "schedule": "learned selector per level (SparsePush / DensePush / DensePull), library defaults",
+            "schedule": "learned selector per level / round (SparsePush / DensePush / DensePull); BFS and SSSP "
+                        "level loops as CUDA graphs (gi_schedule.persistent = 2); SSSP by delta-stepping "
+                        f"(bucket width {delta}, autotuned), BFS with canonical parents",
             "l2": "inputs larger than L2 (CSR + weights %.2f GB vs 126 MB L2); no flush"
                   % ((4 * (hg.n + 1) + 8 * hg.m) / 1e9)}
 
 
 def run_config_l(args):
     """R-MAT scale 24 (weights [1,1000)), BFS + SSSP from 64 seeded sources:
-    the timed step runs every source under the learned selector; Beamer's rule
-    (Ligra's |F| + m_f > m/20 for SSSP) and the exhaustive per-level optimum are
-    measured beside it."""
+    the timed step runs every source under the learned selector (level loops
+    as CUDA graphs, SSSP by delta-stepping with the autotuned bucket width);
+    the fixed rules (Beamer's for BFS, Ligra's |F| + m_f > m/20 for SSSP) on
+    the same loops and the exhaustive per-level optimum are measured beside it."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -661,11 +675,22 @@ def run_config_l(args):
     g = gi.Graph.from_host(hg)
     # replicas: rank r serves its own 64 seeded sources (weak scaling)
     srcs = [int(x) for x in gg.pick_sources(hg, args.sources, seed=1 + rank)]
-    pols = {"learned": (gi.schedule("learned"), gi.schedule("learned")),
-            "beamer": (gi.schedule("hybrid_pull"), gi.schedule("hybrid_pull"))}
     depth = torch.empty(n, dtype=torch.int32, device="cuda")
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
     dist_ = torch.empty(n, dtype=torch.int32, device="cuda")
+    # SSSP schedule: the autotuner picks the bucket width and the other knobs
+    # from the learned graph-driven start (untimed set-up; outputs checked)
+    tune_budget = 1 if args.no_extras else args.tune_budget
+    ss_learned, ss_tuned_ms, ss_start_ms = gi.autotune(
+        g, "sssp", src=srcs[0], start=gi.schedule("learned", delta=args.delta, persistent=2), budget=tune_budget,
+        seed=7)
+    delta = int(ss_learned.delta)
+    ss_rule = gi.schedule("hybrid_pull")
+    for f, _ in ss_learned._fields_:
+        setattr(ss_rule, f, getattr(ss_learned, f))
+    ss_rule.direction = gi.GI_DIR_HYBRID_PULL
+    pols = {"learned": (gi.schedule("learned", persistent=2), ss_learned),
+            "rule": (gi.schedule("hybrid_pull", persistent=2), ss_rule)}
     deg = torch.from_numpy(np.diff(hg.row_ptr).astype(np.int64)).cuda()
     # per-query GTEPS numerator: arcs of the reached component (BFS and SSSP
     # reach the same vertices: weights are positive), untimed
@@ -674,15 +699,12 @@ def run_config_l(args):
         gi.bfs(g, s_, want_parent=False, sched=pols["learned"][0], out=(depth, None))
         reach[s_] = int(deg[depth >= 0].sum())
     arcs_per_step = 2 * sum(reach.values())
-    traces = {s_: gi.Trace(4096) for s_ in srcs}
 
-    def one_pass(pol, ev=None):
+    def one_pass(pol):
         bs, ss = pols[pol]
-        for i, s_ in enumerate(srcs):
+        for s_ in srcs:
             gi.bfs(g, s_, sched=bs, out=(depth, parent))
-            if ev is not None:
-                ev[i].record()
-            gi.sssp(g, s_, sched=ss, trace=traces[s_], out=dist_)
+            gi.sssp(g, s_, sched=ss, out=dist_)
         return arcs_per_step
 
     for _ in range(args.warmup):
@@ -695,7 +717,6 @@ def run_config_l(args):
     sampler.start()
     time.sleep(0.3)
     gi.stats_reset()
-    gi.stats_enable(True)
     start, stop = _events()
     start.record()
     for _ in range(args.steps):
@@ -705,8 +726,7 @@ def run_config_l(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    gi.stats_enable(False)
-    launches, pull_launches, pull_ms = gi.stats_read("min_pull")
+    launches, _, _ = gi.stats_read()
     clocks = sampler.stop()
     total_ms = start.elapsed_time(stop)
     if world > 1:
@@ -714,18 +734,39 @@ def run_config_l(args):
         total_ms = replicas.max_over_ranks(total_ms, device="cuda")
     value = world * args.steps * arcs_per_step / (total_ms * 1e-3) / 1e9
 
-    # roofline: the SSSP DensePull rounds (k_pull_tiled<OpMinInt>), CUDA-event
-    # timed per launch on the launching stream inside the timed region
+    # roofline of the dominant kernel, the SSSP DensePull rounds
+    # (k_pull_tiled<OpMinInt>): kernels inside a CUDA graph cannot be timed one
+    # by one, so the same 64 queries run once more with the same schedule
+    # host-driven, every pull launch bracketed by CUDA events on its stream
+    m_light = int((hg.wt < delta).sum()) if delta > 0 else None
+    ss_host = gi.schedule("learned")
+    for f, _ in ss_learned._fields_:
+        setattr(ss_host, f, getattr(ss_learned, f))
+    ss_host.persistent = 0
+    traces = {s_: gi.Trace(4096) for s_ in srcs}
+    for s_ in srcs[:2]:
+        gi.sssp(g, s_, sched=ss_host, trace=traces[s_], out=dist_)
+    torch.cuda.synchronize()
+    gi.stats_reset()
+    gi.stats_enable(True)
+    a0, a1 = _events()
+    a0.record()
+    for s_ in srcs:
+        gi.sssp(g, s_, sched=ss_host, trace=traces[s_], out=dist_)
+    a1.record()
+    torch.cuda.synchronize()
+    gi.stats_enable(False)
+    host_ms = a0.elapsed_time(a1) / len(srcs)
+    _, pull_launches, pull_ms = gi.stats_read("min_pull")
     pull_bytes, pull_rounds = 0, 0
     for s_ in srcs:
-        b_, r_ = _sssp_pull_bytes(n, m, traces[s_])
+        b_, r_ = _sssp_pull_bytes(n, m, traces[s_], m_light)
         pull_bytes += b_
         pull_rounds += r_
-    pull_bytes *= args.steps
     peak, peak_kind = measured_hbm()
     achieved = pull_bytes / (pull_ms * 1e-3) / 1e9 if pull_ms > 0 else 0.0
 
-    # per algorithm, learned vs Beamer, 3 interleaved repeats each (outside the timed region)
+    # learned vs rule per algorithm, 3 interleaved repeats each (outside the timed region)
     def per_alg(pol):
         bs, ss = pols[pol]
         a0, a1 = _events()
@@ -746,9 +787,9 @@ def run_config_l(args):
                 "gteps": arcs_per_step / ((b_ms + s_ms) * 1e-3) / 1e9,
                 "bfs_ms_per_query": b_ms / len(srcs), "sssp_ms_per_query": s_ms / len(srcs)}
 
-    reps = {"learned": [], "beamer": []}
+    reps = {"learned": [], "rule": []}
     for _ in range(args.repeats):
-        for pol in ("learned", "beamer"):
+        for pol in ("learned", "rule"):
             reps[pol].append(per_alg(pol))
     compare = {}
     for pol, rs in reps.items():
@@ -757,33 +798,34 @@ def run_config_l(args):
             vals = [r[k] for r in rs]
             d[k] = {"mean": float(np.mean(vals)), "min": float(np.min(vals)), "max": float(np.max(vals))}
         compare[pol] = d
-    for k in ("bfs_gteps", "sssp_gteps", "gteps"):
-        compare.setdefault("learned_beats_beamer", {})[k] = \
-            compare["learned"][k]["min"] > compare["beamer"][k]["max"]
-    # the same BFS queries with the level loop as a CUDA graph (no host round trip per level)
-    gd = {}
-    for pol, sc in (("graph_driven_rule", gi.schedule("hybrid_pull", persistent=2)),
-                    ("graph_driven_learned", gi.schedule("learned", persistent=2))):
-        gi.bfs(g, srcs[0], sched=sc, out=(depth, parent))
+    beats = {k: compare["learned"][k]["min"] > compare["rule"][k]["max"] for k in ("bfs_gteps", "sssp_gteps", "gteps")}
+    # other forms of the same queries (one pass each): host-driven level loops,
+    # and Bellman-Ford's synchronous rounds (the paper's SSSP)
+    forms = {}
+    for name, bs, ss in (("host_driven_learned", gi.schedule("learned"), ss_host),
+                         ("bellman_ford_graph_driven_learned", None, gi.schedule("learned", persistent=2)),
+                         ("bellman_ford_host_driven_learned", None, gi.schedule("learned"))):
         a0, a1 = _events()
         a0.record()
-        for s_ in srcs:
-            gi.bfs(g, s_, sched=sc, out=(depth, parent))
+        for s_ in srcs[:16]:
+            if bs is not None:
+                gi.bfs(g, s_, sched=bs, out=(depth, parent))
+            gi.sssp(g, s_, sched=ss, out=dist_)
         a1.record()
         torch.cuda.synchronize()
-        gd[pol] = {"bfs_ms_per_query": a0.elapsed_time(a1) / len(srcs),
-                   "bfs_gteps": (arcs_per_step / 2) / (a0.elapsed_time(a1) * 1e-3) / 1e9}
-    # exhaustive best direction per level: every level of a query timed under all
-    # three directions from the same state (gi_selector_profile), minima summed
+        forms[name] = {"ms_per_query_pair" if bs is not None else "sssp_ms_per_query": a0.elapsed_time(a1) / 16}
+    # exhaustive best direction per level / round: each timed alone from the
+    # same state (gi_selector_profile), minima summed
     nx = max(1, min(len(srcs), args.exhaustive_sources))
     ex_ms = {"bfs": 0.0, "sssp": 0.0}
     for s_ in srcs[:nx]:
-        for algo, kid in (("bfs", gi.GI_K_BFS), ("sssp", gi.GI_K_SSSP)):
-            _, t = sel.profile(g, kid, s_)
-            ex_ms[algo] += float(t.min(axis=1).sum())
+        _, t = sel.profile(g, gi.GI_K_BFS, s_)
+        ex_ms["bfs"] += float(t.min(axis=1).sum())
+        _, t = sel.profile(g, gi.GI_K_SSSP, s_, sched=gi.schedule("hybrid_pull", delta=delta))
+        ex_ms["sssp"] += float(np.where(t > 0, t, np.inf).min(axis=1).sum())
     exhaustive = {"sources": nx, "bfs_ms_per_query": ex_ms["bfs"] / nx, "sssp_ms_per_query": ex_ms["sssp"] / nx,
-                  "note": "sum over levels of the fastest direction timed alone, without the per-level statistics "
-                          "kernel and host round trip; BFS without the parent pass"}
+                  "note": "sum over levels (rounds) of the fastest direction timed alone, without the per-level "
+                          "statistics kernel and loop control; BFS without parents"}
 
     # end to end through the C ABI: CSR + weights from pinned host buffers
     # (gi_load_csr), every query's depth, parent and distance copied back to
@@ -836,20 +878,23 @@ def run_config_l(args):
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": l_config(hg, len(srcs)),
-            "per_algorithm": {"learned": compare["learned"], "beamer": compare["beamer"],
-                              "repeats": args.repeats, "learned_beats_beamer_beyond_spread":
-                                  compare["learned_beats_beamer"],
-                              "graph_driven_bfs": gd, "exhaustive_best_per_level": exhaustive,
-                              "gteps_graph500": value / 2},
+            "config": l_config(hg, len(srcs), delta),
+            "per_algorithm": {"learned": compare["learned"], "rule": compare["rule"], "repeats": args.repeats,
+                              "learned_beats_rule_beyond_spread": beats, "other_forms": forms,
+                              "exhaustive_best_per_level": exhaustive, "gteps_graph500": value / 2,
+                              "sssp_autotune": {"schedule": gi.schedule_dict(ss_learned), "tuned_ms": ss_tuned_ms,
+                                                "start_ms": ss_start_ms, "source": srcs[0]}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_pull_tiled<OpMinInt> (SSSP DensePull round, frontier folded into the "
-                                   "gathered start-of-round distances)",
-                         "bytes_model": "per pull round 4(V+1) + 8m + 8 m_f + V/4 + 4|F_next|",
-                         "launches_timed": pull_launches, "pull_rounds_expected": pull_rounds * args.steps,
+                         "kernel": "k_pull_tiled<OpMinInt> (SSSP DensePull rounds over the light / heavy arcs, "
+                                   "frontier folded into the gathered start-of-round distances)",
+                         "bytes_model": "per pull round 4(V+1) + 8m' + 8 m_f + V/4, m' = arcs of the class scanned",
+                         "timed_in": "the same 64 SSSP queries with the same schedule run host-driven after the "
+                                     "timed region, every pull launch bracketed by CUDA events on its stream "
+                                     f"({host_ms:.2f} ms per query)",
+                         "launches_timed": pull_launches, "pull_rounds_expected": pull_rounds,
                          "avg_launch_ms": pull_ms / max(pull_launches, 1),
-                         "peak_kind": f"{peak_kind} hbm_gbs (burst copy; the kernel runs inside a long step)"},
+                         "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * e2e_s / args.e2e_steps, "steps": args.e2e_steps,
                     "form": "gi_load_csr from pinned host CSR + weights, then the 64 BFS + SSSP queries; each "

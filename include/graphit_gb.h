@@ -298,7 +298,10 @@ int gi_edgeset_apply(gi_graph *g, gi_vset *from, gi_vset *to, const gi_schedule 
  * frontier[i] = |F|, edges[i] = m_f (sum of out-degrees over F) and, if
  * features != NULL, the 16 selector features of the iteration at
  * features[16*i .. 16*i+15].  Any array pointer may be NULL.  Iterations past
- * `cap` run but are not recorded; `iterations` counts all of them.
+ * `cap` run but are not recorded; `iterations` counts all of them.  For
+ * delta-stepping SSSP an iteration is a relaxation round: F is the round's
+ * sources, m_f the arcs of the class it relaxes, and phase[i] (may be NULL)
+ * is 0 for a light round and 1 for a bucket's heavy round (0 elsewhere).
  */
 typedef struct gi_trace {
   int32_t cap;        /* entries available in the arrays below                */
@@ -307,6 +310,7 @@ typedef struct gi_trace {
   int64_t *frontier;
   int64_t *edges;
   float *features;
+  int32_t *phase;
 } gi_trace;
 
 /*
@@ -615,6 +619,17 @@ int gi_stats_reset(void);
  * GI_ERR_INVALID_ARG (unknown class), GI_ERR_CUDA.
  */
 int gi_stats_read(int32_t kclass, int64_t *launches, int64_t *timed_launches, double *timed_ms);
+
+/*
+ * Gather ceiling (instrumentation, not in the paper): one launch on `stream`
+ * that streams idx[m] (device, 16-byte aligned; every id in [0, n)) with
+ * 16-byte loads and reads table[idx[i]] (device, n floats) for every i --
+ * the two memory streams of a dense pull with nothing else -- so m divided
+ * by its CUDA-event time bounds the rate at which any pull over the same
+ * source ids can gather.  out (device, one float) is written only to keep the
+ * loads from being removed.  Errors: GI_ERR_INVALID_ARG, GI_ERR_CUDA.
+ */
+int gi_gather_rate(const int32_t *idx, int64_t m, const float *table, int64_t n, float *out, void *stream);
 
 /* ------------------------------------------------------- fault injection -- */
 /*

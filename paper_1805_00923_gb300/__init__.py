@@ -198,10 +198,12 @@ class Trace:
         self.frontier = np.zeros(cap, np.int64)
         self.edges = np.zeros(cap, np.int64)
         self.features = np.zeros((cap, 16), np.float32)
+        self.phase = np.zeros(cap, np.int32)
         self.c = gi_trace(cap, 0, self.direction.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                           self.frontier.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                           self.edges.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                          self.features.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+                          self.features.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                          self.phase.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
 
     @property
     def iterations(self) -> int:
@@ -210,7 +212,8 @@ class Trace:
     def as_dict(self):
         k = min(self.iterations, self.direction.shape[0])
         return dict(direction=self.direction[:k].copy(), frontier=self.frontier[:k].copy(),
-                    edges=self.edges[:k].copy(), features=self.features[:k].copy(), iterations=self.iterations)
+                    edges=self.edges[:k].copy(), features=self.features[:k].copy(), phase=self.phase[:k].copy(),
+                    iterations=self.iterations)
 
 
 def _sched(s):
@@ -303,6 +306,13 @@ def stats_read(kclass: int | str = -1):
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
     check(_C.gi_stats_read(int(kclass), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def gather_rate(idx: torch.Tensor, table: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """gi_gather_rate: launch the gather-ceiling kernel over idx (int32, CUDA) into table (float32, CUDA)."""
+    out = out if out is not None else torch.zeros(1, dtype=torch.float32, device="cuda")
+    check(_C.gi_gather_rate(_vp(idx), idx.numel(), _vp(table), table.numel(), _vp(out), _stream(stream)))
+    return out
 
 
 ALGOS = {"bfs": L.GI_ALGO_BFS, "sssp": L.GI_ALGO_SSSP, "cc": L.GI_ALGO_CC, "pagerank": L.GI_ALGO_PAGERANK,

@@ -46,7 +46,7 @@ class gi_schedule(ctypes.Structure):
 
 class gi_trace(ctypes.Structure):
     _fields_ = [("cap", _i32), ("iterations", _i32), ("direction", _P(_i32)), ("frontier", _P(_i64)),
-                ("edges", _P(_i64)), ("features", _P(_f32))]
+                ("edges", _P(_i64)), ("features", _P(_f32)), ("phase", _P(_i32))]
 
 
 class gi_batch_opts(ctypes.Structure):
@@ -124,6 +124,7 @@ SIGNATURES = {
     "gi_debug_pool_used": (ctypes.c_int, [_P(_i64)]),
     "gi_graph_hot_info": (ctypes.c_int, [_vp, _P(_i32), _P(_i32), _vp]),
     "gi_debug_barrier_phantoms": (ctypes.c_int, [_i32]),
+    "gi_gather_rate": (ctypes.c_int, [_vp, _i64, _vp, _i64, _vp, _vp]),
     "gi_stats_enable": (ctypes.c_int, [ctypes.c_int]),
     "gi_stats_reset": (ctypes.c_int, []),
     "gi_stats_read": (ctypes.c_int, [_i32, _P(_i64), _P(_i64), _P(ctypes.c_double)]),

@@ -230,10 +230,11 @@ static int front_init(gi_graph *g, gi_vset *F, int32_t v, cudaStream_t s) {
   return GI_OK;
 }
 
-static void trace_put(gi_trace *tr, int32_t it, const int64_t *ctrl_host) {
+static void trace_put(gi_trace *tr, int32_t it, const int64_t *ctrl_host, int32_t phase = 0) {
   if (!tr) return;
   tr->iterations = it + 1;
   if (it >= tr->cap) return;
+  if (tr->phase) tr->phase[it] = phase;
   if (tr->direction) tr->direction[it] = (int32_t)ctrl_host[kDecision];
   if (tr->frontier) tr->frontier[it] = ctrl_host[kNf];
   if (tr->edges) tr->edges[it] = ctrl_host[kMf];
@@ -641,14 +642,23 @@ struct DeltaSplit {
   int32_t delta = 0;
   int32_t tile_edges = 0;
   Csr light, heavy;  // same vertices, arcs split by w < delta
+  bool light_alias = false;  // every arc is light: light is the graph's own CSR (not owned)
   int32_t *deg_l = nullptr, *deg_h = nullptr;
   TileSet tl, th;    // pull tiles (symmetric graphs)
   int64_t m_light = 0;
+  void *loop = nullptr;  // cached graph-driven loop over this split (DsLoop)
 };
+
+static void dsloop_free(DeltaSplit *D);
 
 void dstep_free(gi_graph *g, cudaStream_t s) {
   DeltaSplit *D = static_cast<DeltaSplit *>(g->dstep);
   if (!D) return;
+  dsloop_free(D);
+  if (D->light_alias) {  // the light arcs are the graph's own; only its row offsets are ours
+    dev_free(D->light.ptr, s);
+    D->light = Csr();
+  }
   for (Csr *c : {&D->light, &D->heavy}) {
     dev_free(c->ptr, s);
     dev_free(c->idx, s);
@@ -761,14 +771,22 @@ static int dstep_get(gi_graph *g, int32_t delta, int32_t tile_edges, cudaStream_
     st = cuda_fail(cudaGetLastError(), "light arc count", __FILE__, __LINE__);
   D->m_light = ml;
   const int64_t mh = g->m - ml;
-  if (st == GI_OK) st = dev_alloc_n(&D->light.idx, ml, s);
-  if (st == GI_OK) st = dev_alloc_n(&D->light.wt, ml, s);
-  if (st == GI_OK) st = dev_alloc_n(&D->heavy.idx, mh, s);
-  if (st == GI_OK) st = dev_alloc_n(&D->heavy.wt, mh, s);
-  if (st == GI_OK) {
-    k_ds_fill<<<wgrid, 256, 0, s>>>(g->out.ptr, g->out.idx, g->out.wt, n, delta, D->light.ptr, D->heavy.ptr,
-                                    D->light.idx, D->light.wt, D->heavy.idx, D->heavy.wt);
-    st = launch_status(1);
+  if (st == GI_OK && mh == 0) {
+    // every arc is light (Bellman-Ford when delta exceeds every weight): the
+    // light arcs are the graph's own arrays, no copy
+    D->light_alias = true;
+    D->light.idx = g->out.idx;
+    D->light.wt = g->out.wt;
+  } else {
+    if (st == GI_OK) st = dev_alloc_n(&D->light.idx, ml, s);
+    if (st == GI_OK) st = dev_alloc_n(&D->light.wt, ml, s);
+    if (st == GI_OK) st = dev_alloc_n(&D->heavy.idx, mh, s);
+    if (st == GI_OK) st = dev_alloc_n(&D->heavy.wt, mh, s);
+    if (st == GI_OK) {
+      k_ds_fill<<<wgrid, 256, 0, s>>>(g->out.ptr, g->out.idx, g->out.wt, n, delta, D->light.ptr, D->heavy.ptr,
+                                      D->light.idx, D->light.wt, D->heavy.idx, D->heavy.wt);
+      st = launch_status(1);
+    }
   }
   if (st == GI_OK && g->symmetric) st = build_tiles(g, D->light, te, &D->tl, s);
   if (st == GI_OK && g->symmetric) st = build_tiles(g, D->heavy, te, &D->th, s);
@@ -997,8 +1015,10 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
     int32_t dir = (int32_t)g->ctrl_host[kDecision];
     if (dir == GI_DIR_DENSE_PUSH || (dir == GI_DIR_DENSE_PULL && !pull_ok)) dir = GI_DIR_SPARSE_PUSH;
     g->ctrl_host[kDecision] = dir;
-    trace_put(trace, it, g->ctrl_host);
     const int64_t nf = g->ctrl_host[kNf], mf = g->ctrl_host[kMf];
+    // a heavy round without heavy arcs only empties S: not a relaxation round
+    const bool counted = light || mf > 0;
+    if (counted) trace_put(trace, it, g->ctrl_host, light ? 0 : 1);
     auto relax = [&](int32_t d) -> int {
       GI_TRY(vset_clear(P.N, s));
       if (mf == 0) return GI_OK;
@@ -1014,7 +1034,7 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
       g->hint_nf = g->hint_mf = -1;
       return r;
     };
-    if (prof && pull_ok && prof->rounds < prof->cap) {
+    if (prof && counted && pull_ok && prof->rounds < prof->cap) {
       // both directions from the same state, timed; the pull's result stays
       const float *f = reinterpret_cast<const float *>(g->ctrl_host + kFeat);
       for (int k = 0; k < 16; ++k) prof->features[16 * prof->rounds + k] = f[k];
@@ -1053,7 +1073,7 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
     if ((st = launch_status(launched)) != GI_OK) break;
     P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
     P.swap();
-    ++it;
+    if (counted) ++it;
   }
   if (trace) trace->iterations = it;
   if (prof_ev[0]) cudaEventDestroy(prof_ev[0]);
@@ -1072,6 +1092,312 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
   return st;
 }
 
+// ================================================== graph-driven SSSP ==
+// gi_sssp with gi_schedule.persistent = 2: the delta-stepping rounds run as a
+// CUDA graph, a WHILE node whose body holds two rounds (the pending sets a and
+// b swap roles).  Each round: the split kernel (changed vertices -> R, S, far
+// pile), the decision kernel (statistics of R or S, direction, the round's
+// mode), the next pending set cleared, then a SWITCH node that runs only the
+// round's relaxation (light or heavy arcs, push or pull) or the far pile's
+// next bucket, and the epilogue kernel.  No host round trip per round.
+// Bellman-Ford (delta = 0) is the same loop with one bucket holding every
+// arc (delta beyond every weight), which gives its synchronous rounds exactly.
+namespace gi {
+
+__global__ void k_dsg_split(const int32_t *__restrict__ P, const int32_t *__restrict__ Pc,
+                            const int32_t *__restrict__ x, int32_t *dw, int32_t *Rq, int32_t *snap, uint32_t *Sbm,
+                            int32_t *Sq, uint32_t *fbm, int32_t *pile0, int32_t *pile1) {
+  const int lane = threadIdx.x & 31;
+  const int32_t c = *Pc, hi = dw[kDgHi], cur = dw[kDgCur];
+  int32_t *pile = cur ? pile1 : pile0;
+  int32_t *pile_count = dw + kDgPile0 + cur;
+  const int32_t stride = gridDim.x * blockDim.x;
+  int32_t fmin = INT32_MAX;
+  for (int32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < c; i0 += stride) {
+    const int32_t i = i0 + lane;
+    int32_t v = -1, d = INT32_MAX;
+    if (i < c) {
+      v = P[i];
+      d = x[v];
+    }
+    const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
+    const uint32_t bit = v >= 0 ? 1u << (v & 31) : 0u;
+    if (near) {
+      snap[v] = d;
+      if (fbm[v >> 5] & bit) atomicAnd(fbm + (v >> 5), ~bit);
+    }
+    if (far) fmin = min(fmin, d);
+    warp_append(Rq, dw + kDgRc, near, v);
+    warp_append(Sq, dw + kDgSc, near && bit_test_and_set(Sbm, v), v);
+    warp_append(pile, pile_count, far && bit_test_and_set(fbm, v), v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
+  if (lane == 0 && fmin < INT32_MAX) atomicMin(dw + kDgPmin, fmin);
+}
+
+// next bucket: live pile entries below hi -> the pending set N (cleared
+// before), the rest -> the other pile buffer with a fresh minimum
+__global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uint32_t *fbm, int32_t *pile0,
+                                 int32_t *pile1, int32_t *Nq, int32_t *Nc, uint32_t *Nbm) {
+  const int lane = threadIdx.x & 31;
+  const int32_t cur = dw[kDgCur], hi = dw[kDgHi];
+  const int32_t *pile = cur ? pile1 : pile0;
+  int32_t *pile2 = cur ? pile0 : pile1;
+  const int32_t c = dw[kDgPile0 + cur];
+  const int32_t stride = gridDim.x * blockDim.x;
+  int32_t fmin = INT32_MAX;
+  for (int32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < c; i0 += stride) {
+    const int32_t i = i0 + lane;
+    int32_t v = -1, d = INT32_MAX;
+    if (i < c) {
+      v = pile[i];
+      if (!bit_test(fbm, v)) v = -1;
+      else d = x[v];
+    }
+    const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
+    if (near) {
+      atomicAnd(fbm + (v >> 5), ~(1u << (v & 31)));
+      atomicOr(Nbm + (v >> 5), 1u << (v & 31));
+    }
+    if (far) fmin = min(fmin, d);
+    warp_append(Nq, Nc, near, v);
+    warp_append(pile2, dw + kDgPile0 + (cur ^ 1), far, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
+  if (lane == 0 && fmin < INT32_MAX) atomicMin(dw + kDgPmin, fmin);
+}
+
+// round epilogue: the sources' snap entries back to INT32_MAX (and, after a
+// heavy round, S emptied); the last block resets the round counters
+__global__ void k_dsg_post(const int32_t *__restrict__ Rq, const int32_t *__restrict__ Sq, uint32_t *Sbm,
+                           int32_t *snap, int32_t *dw) {
+  __shared__ bool last;
+  const int32_t mode = dw[kDgMode];
+  const bool light = mode == kDgLightPush || mode == kDgLightPull;
+  const bool heavy = mode == kDgHeavyPush || mode == kDgHeavyPull;
+  const int32_t c = light ? dw[kDgRc] : (heavy ? dw[kDgSc] : 0);
+  const int32_t *q = light ? Rq : Sq;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+    const int32_t v = q[i];
+    snap[v] = INT32_MAX;
+    if (heavy) atomicAnd(Sbm + (v >> 5), ~(1u << (v & 31)));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(dw + kDgTicket, 1) == (int32_t)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  dw[kDgTicket] = 0;
+  dw[kDgRc] = 0;
+  if (heavy) dw[kDgSc] = 0;
+  if (mode == kDgAdvance) dw[kDgCur] ^= 1;
+}
+
+__global__ void k_dsg_init(int32_t *dw, int32_t delta, int32_t cap) {
+  if (threadIdx.x < kDgWords) {
+    int32_t v = 0;
+    if (threadIdx.x == kDgHi) v = delta;
+    if (threadIdx.x == kDgPmin) v = INT32_MAX;
+    if (threadIdx.x == kDgCap) v = cap;
+    dw[threadIdx.x] = v;
+  }
+}
+
+struct DsLoop {
+  gi_schedule sc{};
+  int use_selector = -1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int32_t *x = nullptr, *snap = nullptr, *Rq = nullptr, *Sq = nullptr, *pile[2] = {nullptr, nullptr};
+  int32_t *dw = nullptr;
+  uint32_t *Sbm = nullptr, *fbm = nullptr;
+  gi_vset a, b;
+};
+
+static void dsloop_free(DeltaSplit *D) {
+  DsLoop *L = static_cast<DsLoop *>(D->loop);
+  if (!L) return;
+  if (L->exec) cudaGraphExecDestroy(L->exec);
+  if (L->graph) cudaGraphDestroy(L->graph);
+  for (gi_vset *v : {&L->a, &L->b}) {
+    dev_free(v->queue, nullptr);
+    dev_free(v->count, nullptr);
+    dev_free(v->bitmap, nullptr);
+    dev_free(v->boolmap, nullptr);
+  }
+  for (void *p : {(void *)L->x, (void *)L->snap, (void *)L->Rq, (void *)L->Sq, (void *)L->pile[0], (void *)L->pile[1],
+                  (void *)L->dw, (void *)L->Sbm, (void *)L->fbm})
+    dev_free(p, nullptr);
+  delete L;
+  D->loop = nullptr;
+}
+
+// one round F -> N captured on cs into `body`: split, decision, N cleared,
+// switch over the round's relaxation, epilogue
+static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &sc, gi_vset *F, gi_vset *N,
+                     cudaGraph_t body, cudaGraphConditionalHandle hw, cudaStream_t cs) {
+  const int grid = g->num_sms * 4;
+  const bool pull_ok = g->symmetric;
+  cudaGraphConditionalHandle hs;
+  GI_CUDA(cudaGraphConditionalHandleCreate(&hs, body, kDgDone, cudaGraphCondAssignDefault));
+  k_dsg_split<<<grid, 256, 0, cs>>>(F->queue, F->count, L->x, L->dw, L->Rq, L->snap, L->Sbm, L->Sq, L->fbm, L->pile[0],
+                                    L->pile[1]);
+  GI_TRY(launch_status(1));
+  DecideParams p = decide_params(sc, 0, false);
+  GI_TRY(dsg_decide_launch(g, L->Rq, L->Sq, D->deg_l, D->deg_h, L->x, L->snap, L->dw, p, sc.delta, pull_ok,
+                           (unsigned long long)hs, (unsigned long long)hw, cs));
+  GI_CUDA(cudaMemsetAsync(N->bitmap, 0, sizeof(uint32_t) * (size_t)(N->words > 0 ? N->words : 1), cs));
+  GI_CUDA(cudaMemsetAsync(N->count, 0, sizeof(int32_t), cs));
+  // the switch node after what was captured so far
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t ndeps = 0;
+  GI_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+  std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+  cudaGraph_t seg = nullptr;  // capturing into `body`: the same graph comes back
+  GI_CUDA(cudaStreamEndCapture(cs, &seg));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hs;
+  cp.conditional.type = cudaGraphCondTypeSwitch;
+  cp.conditional.size = 5;
+  cudaGraphNode_t sw;
+  GI_CUDA(cudaGraphAddNode(&sw, body, dv.data(), nullptr, dv.size(), &cp));
+  // branches: light push, light pull, heavy push, heavy pull, next bucket
+  gi_vset Rv{}, Sv{};
+  Rv.g = Sv.g = g;
+  Rv.n = Sv.n = g->n;
+  Rv.queue = L->Rq;
+  Rv.count = L->dw + kDgPushL;
+  Rv.reps = GI_REP_SPARSE;
+  Sv.queue = L->Sq;
+  Sv.count = L->dw + kDgPushH;
+  Sv.reps = GI_REP_SPARSE;
+  for (int k = 0; k < 5; ++k) {
+    GI_CUDA(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[k], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed));
+    int st = GI_OK;
+    const bool light = k < 2;
+    const Csr &arcs = light ? D->light : D->heavy;
+    OpMinInt op{L->x, L->snap, arcs.wt};
+    if (k == kDgLightPush || k == kDgHeavyPush) {
+      st = launch_push(g, op, kSrcQueue, light ? &Rv : &Sv, nullptr, out_of(N), sc, cs, &arcs);
+    } else if (k == kDgLightPull || k == kDgHeavyPull) {
+      st = launch_pull_tiled(g, op, arcs, light ? D->tl : D->th, FSet(), nullptr, out_of(N), cs, kClassMinPull,
+                             sc.balance == GI_BAL_VERTEX);
+    } else {
+      k_dsg_pile_split<<<grid, 256, 0, cs>>>(L->x, L->dw, L->fbm, L->pile[0], L->pile[1], N->queue, N->count,
+                                             N->bitmap);
+      st = launch_status(1);
+    }
+    cudaGraph_t got = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &got);
+    GI_TRY(st);
+    if (e != cudaSuccess) return cuda_fail(e, "branch capture", __FILE__, __LINE__);
+  }
+  GI_CUDA(cudaStreamBeginCaptureToGraph(cs, body, &sw, nullptr, 1, cudaStreamCaptureModeRelaxed));
+  k_dsg_post<<<grid, 256, 0, cs>>>(L->Rq, L->Sq, L->Sbm, L->snap, L->dw);
+  GI_TRY(launch_status(1));
+  N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
+  return GI_OK;
+}
+
+static int dsloop_build(gi_graph *g, DeltaSplit *D, const gi_schedule &sc, DsLoop *L, cudaStream_t s) {
+  const int64_t n = g->n;
+  GI_TRY(heavy_get(g, s));
+  for (int32_t **p : {&L->x, &L->snap, &L->Rq, &L->Sq, &L->pile[0], &L->pile[1]}) GI_TRY(dev_alloc_n(p, n, s));
+  GI_TRY(dev_alloc_n(&L->dw, kDgWords, s));
+  GI_TRY(vset_alloc(g, &L->a, s));
+  GI_TRY(vset_alloc(g, &L->b, s));
+  GI_TRY(dev_alloc_n(&L->Sbm, L->a.words, s));
+  GI_TRY(dev_alloc_n(&L->fbm, L->a.words, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  GI_CUDA(cudaGraphCreate(&L->graph, 0));
+  cudaGraphConditionalHandle hw;
+  GI_CUDA(cudaGraphConditionalHandleCreate(&hw, L->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hw;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  GI_CUDA(cudaGraphAddNode(&loop, L->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs;
+  GI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  int st = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess
+               ? GI_OK
+               : cuda_fail(cudaGetLastError(), "begin capture", __FILE__, __LINE__);
+  L->a.reps = L->b.reps = GI_REP_SPARSE | GI_REP_BITMAP;
+  if (st == GI_OK) st = dsg_round(g, D, L, sc, &L->a, &L->b, body, hw, cs);
+  if (st == GI_OK) st = dsg_round(g, D, L, sc, &L->b, &L->a, body, hw, cs);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
+  cudaStreamDestroy(cs);
+  if (st == GI_OK && ec != cudaSuccess) st = cuda_fail(ec, "end capture", __FILE__, __LINE__);
+  if (st == GI_OK && cudaGraphInstantiate(&L->exec, L->graph, 0) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "graph instantiate", __FILE__, __LINE__);
+  return st;
+}
+
+}  // namespace gi
+
+// SSSP distances by the graph-driven loop; rounds = relaxation rounds run
+static int run_graph_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedule &sched, int32_t *rounds,
+                          cudaStream_t s) {
+  gi_schedule sc = sched;
+  sc.balance = sc.balance == GI_BAL_EDGE_PARALLEL ? GI_BAL_EDGE_AWARE : sc.balance;  // needs a host-known |F|
+  sc.persistent = 2;
+  sc.delta = sc.delta > 0 ? sc.delta : INT32_MAX;  // Bellman-Ford: one bucket, every arc light
+  DeltaSplit *D = nullptr;
+  GI_TRY(dstep_get(g, sc.delta, sc.tile_edges, s, &D));
+  const int use_sel = selector_loaded() ? 1 : 0;
+  DsLoop *L = static_cast<DsLoop *>(D->loop);
+  if (L && (std::memcmp(&L->sc, &sc, sizeof(sc)) != 0 || L->use_selector != use_sel)) {
+    dsloop_free(D);
+    L = nullptr;
+  }
+  if (!L) {
+    L = new DsLoop();
+    L->sc = sc;
+    L->use_selector = use_sel;
+    D->loop = L;
+    const int st = dsloop_build(g, D, sc, L, s);
+    if (st != GI_OK) {
+      dsloop_free(D);
+      return st;
+    }
+  }
+  const int64_t n = g->n;
+  k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->x, n, INT32_MAX);
+  k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->snap, n, INT32_MAX);
+  k_set_one<<<1, 1, 0, s>>>(L->x, src, 0);
+  const int64_t cap64 = 4 * n + 16;
+  k_dsg_init<<<1, 32, 0, s>>>(L->dw, sc.delta, (int32_t)(cap64 < INT32_MAX ? cap64 : INT32_MAX));
+  GI_TRY(launch_status(4));
+  GI_CUDA(cudaMemsetAsync(L->Sbm, 0, sizeof(uint32_t) * (size_t)L->a.words, s));
+  GI_CUDA(cudaMemsetAsync(L->fbm, 0, sizeof(uint32_t) * (size_t)L->a.words, s));
+  GI_TRY(front_init(g, &L->a, src, s));
+  GI_TRY(vset_clear(&L->b, s));
+  GI_TRY(ctrl_init(g, 0, 0, s));
+  GI_CUDA(cudaGraphLaunch(L->exec, s));
+  GI_CUDA(cudaMemcpyAsync(dist, L->x, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  int32_t dw[kDgWords];
+  GI_CUDA(cudaMemcpyAsync(dw, L->dw, sizeof(dw), cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  if (dw[kDgErr]) {
+    set_error("graph-driven SSSP reached its round cap");
+    return GI_ERR_TIMEOUT;
+  }
+  *rounds = dw[kDgRound];
+  return GI_OK;
+}
+
 extern "C" int gi_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedule *sched, gi_trace *trace,
                        void *stream) {
   GI_ARG(g != nullptr, "graph is NULL");
@@ -1084,6 +1410,12 @@ extern "C" int gi_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedul
     GI_ARG(g->symmetric || g->in.wt != nullptr, "pull SSSP needs in-edge weights (gi_load_csc with weights)");
   }
   if (sched->persistent == 1) return run_persistent(g, GI_ALGO_SSSP, src, dist, *sched, trace, (cudaStream_t)stream);
+  if (sched->persistent == 2) {
+    int32_t rounds = 0;
+    GI_TRY(run_graph_sssp(g, src, dist, *sched, &rounds, (cudaStream_t)stream));
+    if (trace) trace->iterations = rounds;
+    return GI_OK;
+  }
   if (sched->delta > 0) return deltastep_run(g, dist, src, *sched, trace, (cudaStream_t)stream);
   return minlabel_run(g, dist, GI_K_SSSP, src, *sched, trace, (cudaStream_t)stream);
 }

@@ -543,6 +543,45 @@ extern "C" int gi_stats_read(int32_t kclass, int64_t *launches, int64_t *timed_l
 extern "C" int gi_version(void) { return 100; }
 
 namespace gi {
+// Ceiling of the pull's gathers: stream m source ids with 16-byte loads and
+// gather one 4-byte value per id (each a separate 32-byte sector unless a
+// neighbouring id shares it), nothing else; the sum keeps the loads alive.
+__global__ void __launch_bounds__(256) k_gather_rate(const int32_t *__restrict__ idx, int64_t m,
+                                                     const float *__restrict__ table, float *out) {
+  const int64_t m4 = m >> 2;
+  const int4 *idx4 = reinterpret_cast<const int4 *>(idx);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float acc = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m4; i += 2 * stride) {
+    const int4 a = __ldg(idx4 + i);
+    int4 b = make_int4(-1, -1, -1, -1);
+    if (i + stride < m4) b = __ldg(idx4 + i + stride);
+    acc += __ldg(table + a.x) + __ldg(table + a.y) + __ldg(table + a.z) + __ldg(table + a.w);
+    if (b.x >= 0) acc += __ldg(table + b.x) + __ldg(table + b.y) + __ldg(table + b.z) + __ldg(table + b.w);
+  }
+  for (int64_t i = (m4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+    acc += __ldg(table + __ldg(idx + i));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc == -1.0f) out[0] = acc;  // practically never: keeps the sum live
+}
+}  // namespace gi
+
+extern "C" int gi_gather_rate(const int32_t *idx, int64_t m, const float *table, int64_t n, float *out,
+                              void *stream) {
+  GI_ARG(m >= 0 && n > 0, "m must be >= 0 and n > 0");
+  GI_ARG((idx != nullptr || m == 0) && table != nullptr && out != nullptr, "NULL device pointer");
+  GI_ARG((reinterpret_cast<uintptr_t>(idx) & 15) == 0, "idx must be 16-byte aligned");
+  if (m == 0) return GI_OK;
+  int dev = 0, sms = 0;
+  GI_CUDA(cudaGetDevice(&dev));
+  GI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  gi::k_gather_rate<<<sms * 8, 256, 0, (cudaStream_t)stream>>>(idx, m, table, out);
+  GI_LAUNCH_CHECK();
+  return GI_OK;
+}
+
+namespace gi {
 static void segs_free(gi_graph *g, cudaStream_t s);
 }
 
@@ -1605,6 +1644,112 @@ __global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *
       cudaGraphSetConditional((cudaGraphConditionalHandle)p.cond_handle, go ? 1u : 0u);
     }
   }
+}
+
+// One round of graph-driven delta-stepping: statistics (and, for a heavy
+// round, the settled vertices' start-of-round distances) over R or S, then in
+// the last block the features, the direction (rule, or the MLP as in
+// k_frontier_decide) and the round's mode.
+__global__ void k_dsg_decide(const int32_t *__restrict__ Rq, const int32_t *__restrict__ Sq,
+                             const int32_t *__restrict__ deg_l, const int32_t *__restrict__ deg_h,
+                             const int32_t *__restrict__ x, int32_t *snap, int32_t *dw, int64_t *ctrl, DecideParams p,
+                             int64_t n, int64_t m, int32_t maxdeg, int use_selector, int32_t delta, int pull_ok,
+                             unsigned long long switch_handle, unsigned long long while_handle) {
+  __shared__ unsigned long long s_sum[32];
+  __shared__ float sh[kDIn + kH + kH + 4];
+  __shared__ float feat[kDIn];
+  __shared__ bool last;
+  const int32_t rc = dw[kDgRc], sc = dw[kDgSc];
+  const bool light = rc > 0, heavy = !light && sc > 0;
+  const int32_t c = light ? rc : (heavy ? sc : 0);
+  const int32_t *q = light ? Rq : Sq;
+  const int32_t *deg = light ? deg_l : deg_h;
+  unsigned long long local = 0;
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += stride) {
+    const int32_t v = q[i];
+    local += deg[v];
+    if (heavy) snap[v] = x[v];  // the bucket's vertices are final
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if (lane_id() == 0) s_sum[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_sum[w];
+    atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kMfAcc), b);
+    __threadfence();
+    const unsigned long long t = atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kTicket), 1ull);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int64_t nf = c;
+  const int64_t mf = *(volatile int64_t *)(ctrl + kMfAcc);
+  const int32_t was_pull = (int32_t)ctrl[kWasPull];
+  const int64_t nf_prev = ctrl[kNfPrev];
+  const int32_t round = dw[kDgRound];
+  const bool relax = light || heavy;
+  if (relax && threadIdx.x == 0) level_features(feat, n, m, maxdeg, nf, mf, 0, 0, round, was_pull, nf_prev);
+  __syncthreads();
+  int32_t dir = GI_DIR_SPARSE_PUSH;
+  if (relax) {
+    if (p.mode == 0) {
+      dir = p.forced;
+    } else if (p.mode == 2 && use_selector) {
+      const int32_t k = selector_forward(feat, sh);
+      dir = k == 2 ? GI_DIR_DENSE_PULL : GI_DIR_SPARSE_PUSH;
+    } else {
+      dir = (nf + mf) > m / 20 ? GI_DIR_DENSE_PULL : GI_DIR_SPARSE_PUSH;
+    }
+    if (dir != GI_DIR_DENSE_PULL || !pull_ok) dir = GI_DIR_SPARSE_PUSH;
+  }
+  if (threadIdx.x == 0) {
+    int32_t mode;
+    const int32_t cur = dw[kDgCur];
+    if (relax) {
+      const bool pull = dir == GI_DIR_DENSE_PULL;
+      mode = light ? (pull ? kDgLightPull : kDgLightPush) : (pull ? kDgHeavyPull : kDgHeavyPush);
+      ctrl[kWasPull] = pull ? 1 : 0;
+      ctrl[kNfPrev] = nf;
+      // a heavy round without heavy arcs only empties S: not a relaxation round
+      if (light || mf > 0) dw[kDgRound] = round + 1;
+    } else if (dw[kDgPile0 + cur] > 0) {
+      // the bucket and its heavy round are done: next bucket from the pile
+      mode = kDgAdvance;
+      const int64_t hi = ((int64_t)dw[kDgPmin] / delta + 1) * (int64_t)delta;
+      dw[kDgHi] = (int32_t)(hi < INT32_MAX ? hi : INT32_MAX);
+      dw[kDgPile0 + (cur ^ 1)] = 0;
+      dw[kDgPmin] = INT32_MAX;
+    } else {
+      mode = kDgDone;
+    }
+    if (mode != kDgDone && round >= dw[kDgCap]) {
+      dw[kDgErr] = 1;
+      mode = kDgDone;
+    }
+    dw[kDgMode] = mode;
+    dw[kDgPushL] = mode == kDgLightPush ? rc : 0;
+    dw[kDgPushH] = (mode == kDgHeavyPush && mf > 0) ? sc : 0;
+    ctrl[kNf] = nf;
+    ctrl[kMf] = mf;
+    ctrl[kDecision] = dir;
+    ctrl[kTicket] = 0;
+    ctrl[kMfAcc] = 0;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)switch_handle, (unsigned)mode);
+    cudaGraphSetConditional((cudaGraphConditionalHandle)while_handle, mode != kDgDone ? 1u : 0u);
+  }
+}
+
+int dsg_decide_launch(gi_graph *g, const int32_t *Rq, const int32_t *Sq, const int32_t *deg_l, const int32_t *deg_h,
+                      const int32_t *x, int32_t *snap, int32_t *dw, const DecideParams &p, int32_t delta,
+                      bool pull_ok, unsigned long long switch_handle, unsigned long long while_handle, cudaStream_t s) {
+  k_dsg_decide<<<g->num_sms * 2, 256, 0, s>>>(Rq, Sq, deg_l, deg_h, x, snap, dw, g->ctrl, p, g->n, g->m, g->max_deg,
+                                              g_sel_loaded ? 1 : 0, delta, pull_ok ? 1 : 0, switch_handle,
+                                              while_handle);
+  GI_LAUNCH_CHECK();
+  return GI_OK;
 }
 
 __global__ void k_ctrl_init(int64_t *ctrl, int64_t nu, int64_t mu) {

@@ -299,6 +299,35 @@ struct DecideParams {
 };
 // deg: per-vertex arc counts summed into m_f (NULL = out-degrees)
 int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s, const int32_t *deg = nullptr);
+
+// Graph-driven delta-stepping (gi_sssp with gi_schedule.persistent = 2): the
+// int32 words the per-round kernels share, and the round's mode, which is
+// also the value of the switch node that runs the round's relaxation.
+enum DsgWord {
+  kDgHi = 0,      // end of the current bucket
+  kDgMode = 1,    // DsgMode of the current round
+  kDgRc = 2,      // |R| (this round's light sources)
+  kDgSc = 3,      // |S| (the bucket's settled list)
+  kDgPile0 = 4,   // counts of the two far-pile buffers
+  kDgPile1 = 5,
+  kDgPmin = 6,    // smallest distance recorded in the far pile
+  kDgCur = 7,     // far-pile buffer in use
+  kDgPushL = 8,   // queue length the light push sees (|R| when the round pushes light arcs, else 0)
+  kDgPushH = 9,   // the same for the heavy push over S
+  kDgRound = 10,  // relaxation rounds run
+  kDgCap = 11,    // round cap: reaching it stops the loop with kDgErr set
+  kDgErr = 12,
+  kDgTicket = 13,
+  kDgWords = 16
+};
+enum DsgMode { kDgLightPush = 0, kDgLightPull = 1, kDgHeavyPush = 2, kDgHeavyPull = 3, kDgAdvance = 4, kDgDone = 5 };
+// Statistics and direction of one graph-driven delta-stepping round (one
+// launch on s): light round over R if it is non-empty, else the heavy round
+// over S (whose start-of-round distances it also sets in snap), else the next
+// bucket (advance) or the end; sets the switch and loop conditions.
+int dsg_decide_launch(gi_graph *g, const int32_t *Rq, const int32_t *Sq, const int32_t *deg_l, const int32_t *deg_h,
+                      const int32_t *x, int32_t *snap, int32_t *dw, const DecideParams &p, int32_t delta,
+                      bool pull_ok, unsigned long long switch_handle, unsigned long long while_handle, cudaStream_t s);
 int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s);
 int ctrl_fetch(gi_graph *g, cudaStream_t s);  // copies ctrl to pinned host + syncs
 

@@ -59,7 +59,9 @@ BFS_SCHEDULES = {"hybrid_pull": dict(direction="hybrid_pull"), "learned": dict(d
                  "graph_driven_learned": dict(direction="learned", persistent=2)}
 SSSP_SCHEDULES = {"hybrid_pull": dict(direction="hybrid_pull"), "learned": dict(direction="learned"),
                   "delta_hybrid": dict(direction="hybrid_pull", delta=64),
-                  "delta_learned": dict(direction="learned", delta=64)}
+                  "delta_learned": dict(direction="learned", delta=64),
+                  "graph_driven_delta_learned": dict(direction="learned", delta=64, persistent=2),
+                  "graph_driven_bellman_ford": dict(direction="hybrid_pull", persistent=2)}
 
 
 @pytest.fixture(scope="module")

@@ -218,6 +218,53 @@ def test_sssp_delta_stepping_grid_and_directed(gi):
                                   oracle.sssp(hd, src)[0])
 
 
+@pytest.mark.parametrize("delta", [0, 1, 48, 1 << 20])
+@pytest.mark.parametrize("direction", ["sparse_push", "dense_pull", "hybrid_pull", "learned"])
+def test_sssp_graph_driven(gi, direction, delta):
+    """The graph-driven loop (persistent = 2) gives the oracle's distances, and
+    runs the same rounds as the host-driven loop: Bellman-Ford's synchronous
+    rounds for delta = 0, delta-stepping's otherwise."""
+    from paper_1805_00923_gb300 import selector as sel
+    sel.install()
+    hg = rmat(14, weights=True)
+    g = _load(gi, hg)
+    for src in [0, *gg.pick_sources(hg, 2, seed=6)]:
+        want, fs = oracle.sssp(hg, int(src))
+        tg, th = gi.Trace(8), gi.Trace(8192)
+        d = gi.sssp(g, int(src), sched=gi.schedule(direction, delta=delta, persistent=2), trace=tg)
+        assert np.array_equal(_np(d), want), (src, delta)
+        gi.sssp(g, int(src), sched=gi.schedule(direction, delta=delta), trace=th)
+        assert tg.iterations == th.iterations
+        if delta == 0:
+            assert tg.iterations == len(fs)
+
+
+@pytest.mark.parametrize("name", ["path", "components", "hub_tail", "single", "isolated", "star"])
+def test_sssp_graph_driven_adversarial(gi, name):
+    hg = adversarial(name, weights=True)
+    g = _load(gi, hg)
+    want, _ = oracle.sssp(hg, 0)
+    for delta in (0, 1, 10):
+        for direction in ("hybrid_pull", "sparse_push", "dense_pull"):
+            d = gi.sssp(g, 0, sched=gi.schedule(direction, delta=delta, persistent=2))
+            assert np.array_equal(_np(d), want), (delta, direction)
+
+
+def test_sssp_graph_driven_grid_directed_and_reuse(gi):
+    hg = grid(64, weights=True)
+    g = _load(gi, hg)
+    want = oracle.sssp(hg, 100)[0]
+    for delta in (3, 0, 3, 250):  # the cached loop is rebuilt when the schedule changes
+        assert np.array_equal(_np(gi.sssp(g, 100, sched=gi.schedule("hybrid_pull", delta=delta, persistent=2))), want)
+    hd = _directed(3000, 12000, 4, weights=True)
+    in_ptr, in_col, in_wt = gg.transpose(hd)
+    gd = gi.Graph(hd.row_ptr, hd.col, hd.wt, symmetric=False, in_edges=(in_ptr, in_col, in_wt), validate=True)
+    for delta in (0, 40):
+        for src in (0, 1234):
+            assert np.array_equal(_np(gi.sssp(gd, src, sched=gi.schedule("hybrid_pull", delta=delta, persistent=2))),
+                                  oracle.sssp(hd, src)[0])
+
+
 def test_sssp_delta_stepping_split_reused_and_rebuilt(gi):
     """The light/heavy split is cached per graph and delta: alternating deltas
     rebuilds it each time and keeps every result exact."""
