@@ -798,17 +798,6 @@ static int dstep_get(gi_graph *g, int32_t delta, int32_t tile_edges, cudaStream_
   return GI_OK;
 }
 
-// one warp appends the ids of its lanes with pred set to q (count *qc)
-__device__ __forceinline__ void warp_append(int32_t *q, int32_t *qc, bool pred, int32_t v) {
-  const unsigned b = __ballot_sync(0xffffffffu, pred);
-  if (!b) return;
-  const int lane = threadIdx.x & 31;
-  int32_t base = 0;
-  if (lane == 0) base = atomicAdd(qc, __popc(b));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (pred) q[base + __popc(b & ((1u << lane) - 1u))] = v;
-}
-
 // Device words of delta-stepping (int32, in the graph's control block): the
 // round's R and the bucket's S counts, the counts of the two far-pile
 // buffers and the smallest distance in the far pile.
@@ -1104,38 +1093,6 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
 // arc (delta beyond every weight), which gives its synchronous rounds exactly.
 namespace gi {
 
-__global__ void k_dsg_split(const int32_t *__restrict__ P, const int32_t *__restrict__ Pc,
-                            const int32_t *__restrict__ x, int32_t *dw, int32_t *Rq, int32_t *snap, uint32_t *Sbm,
-                            int32_t *Sq, uint32_t *fbm, int32_t *pile0, int32_t *pile1) {
-  const int lane = threadIdx.x & 31;
-  const int32_t c = *Pc, hi = dw[kDgHi], cur = dw[kDgCur];
-  int32_t *pile = cur ? pile1 : pile0;
-  int32_t *pile_count = dw + kDgPile0 + cur;
-  const int32_t stride = gridDim.x * blockDim.x;
-  int32_t fmin = INT32_MAX;
-  for (int32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < c; i0 += stride) {
-    const int32_t i = i0 + lane;
-    int32_t v = -1, d = INT32_MAX;
-    if (i < c) {
-      v = P[i];
-      d = x[v];
-    }
-    const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
-    const uint32_t bit = v >= 0 ? 1u << (v & 31) : 0u;
-    if (near) {
-      snap[v] = d;
-      if (fbm[v >> 5] & bit) atomicAnd(fbm + (v >> 5), ~bit);
-    }
-    if (far) fmin = min(fmin, d);
-    warp_append(Rq, dw + kDgRc, near, v);
-    warp_append(Sq, dw + kDgSc, near && bit_test_and_set(Sbm, v), v);
-    warp_append(pile, pile_count, far && bit_test_and_set(fbm, v), v);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
-  if (lane == 0 && fmin < INT32_MAX) atomicMin(dw + kDgPmin, fmin);
-}
-
 // next bucket: live pile entries below hi -> the pending set N (cleared
 // before), the rest -> the other pile buffer with a fresh minimum
 __global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uint32_t *fbm, int32_t *pile0,
@@ -1169,21 +1126,28 @@ __global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uin
   if (lane == 0 && fmin < INT32_MAX) atomicMin(dw + kDgPmin, fmin);
 }
 
-// round epilogue: the sources' snap entries back to INT32_MAX (and, after a
-// heavy round, S emptied); the last block resets the round counters
+// round epilogue: the sources' snap entries back to INT32_MAX (after a heavy
+// round: snap_h, and S emptied), and this round's pending set F, consumed by
+// the split, emptied through its queue (it is the next round's output set);
+// the last block resets the round counters
 __global__ void k_dsg_post(const int32_t *__restrict__ Rq, const int32_t *__restrict__ Sq, uint32_t *Sbm,
-                           int32_t *snap, int32_t *dw) {
+                           int32_t *snap, int32_t *snap_h, int32_t *dw, const int32_t *__restrict__ Fq,
+                           int32_t *Fc, uint32_t *Fbm, int64_t *ctrl) {
   __shared__ bool last;
   const int32_t mode = dw[kDgMode];
   const bool light = mode == kDgLightPush || mode == kDgLightPull;
   const bool heavy = mode == kDgHeavyPush || mode == kDgHeavyPull;
   const int32_t c = light ? dw[kDgRc] : (heavy ? dw[kDgSc] : 0);
   const int32_t *q = light ? Rq : Sq;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+  int32_t *sn = light ? snap : snap_h;
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += stride) {
     const int32_t v = q[i];
-    snap[v] = INT32_MAX;
+    sn[v] = INT32_MAX;
     if (heavy) atomicAnd(Sbm + (v >> 5), ~(1u << (v & 31)));
   }
+  const int32_t fc = *Fc;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < fc; i += stride) Fbm[Fq[i] >> 5] = 0u;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1194,7 +1158,11 @@ __global__ void k_dsg_post(const int32_t *__restrict__ Rq, const int32_t *__rest
   __threadfence();
   dw[kDgTicket] = 0;
   dw[kDgRc] = 0;
-  if (heavy) dw[kDgSc] = 0;
+  *Fc = 0;
+  if (heavy) {
+    dw[kDgSc] = 0;
+    ctrl[kSHeavyMf] = 0;
+  }
   if (mode == kDgAdvance) dw[kDgCur] ^= 1;
 }
 
@@ -1213,7 +1181,8 @@ struct DsLoop {
   int use_selector = -1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int32_t *x = nullptr, *snap = nullptr, *Rq = nullptr, *Sq = nullptr, *pile[2] = {nullptr, nullptr};
+  int32_t *x = nullptr, *snap = nullptr, *snap_h = nullptr, *Rq = nullptr, *Sq = nullptr,
+          *pile[2] = {nullptr, nullptr};
   int32_t *dw = nullptr;
   uint32_t *Sbm = nullptr, *fbm = nullptr;
   gi_vset a, b;
@@ -1230,29 +1199,26 @@ static void dsloop_free(DeltaSplit *D) {
     dev_free(v->bitmap, nullptr);
     dev_free(v->boolmap, nullptr);
   }
-  for (void *p : {(void *)L->x, (void *)L->snap, (void *)L->Rq, (void *)L->Sq, (void *)L->pile[0], (void *)L->pile[1],
-                  (void *)L->dw, (void *)L->Sbm, (void *)L->fbm})
+  for (void *p : {(void *)L->x, (void *)L->snap, (void *)L->snap_h, (void *)L->Rq, (void *)L->Sq, (void *)L->pile[0],
+                  (void *)L->pile[1], (void *)L->dw, (void *)L->Sbm, (void *)L->fbm})
     dev_free(p, nullptr);
   delete L;
   D->loop = nullptr;
 }
 
-// one round F -> N captured on cs into `body`: split, decision, N cleared,
-// switch over the round's relaxation, epilogue
+// one round F -> N captured on cs into `body`: split + decision (one kernel),
+// switch over the round's relaxation, epilogue (which also empties F, the
+// next round's output set; N was emptied the same way a round before)
 static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &sc, gi_vset *F, gi_vset *N,
                      cudaGraph_t body, cudaGraphConditionalHandle hw, cudaStream_t cs) {
   const int grid = g->num_sms * 4;
   const bool pull_ok = g->symmetric;
   cudaGraphConditionalHandle hs;
   GI_CUDA(cudaGraphConditionalHandleCreate(&hs, body, kDgDone, cudaGraphCondAssignDefault));
-  k_dsg_split<<<grid, 256, 0, cs>>>(F->queue, F->count, L->x, L->dw, L->Rq, L->snap, L->Sbm, L->Sq, L->fbm, L->pile[0],
-                                    L->pile[1]);
-  GI_TRY(launch_status(1));
+  DsgBuffers B{F->queue, F->count, L->x, L->dw, L->Rq, L->snap, L->snap_h, L->Sq, L->pile[0], L->pile[1], L->Sbm,
+               L->fbm, D->deg_l, D->deg_h};
   DecideParams p = decide_params(sc, 0, false);
-  GI_TRY(dsg_decide_launch(g, L->Rq, L->Sq, D->deg_l, D->deg_h, L->x, L->snap, L->dw, p, sc.delta, pull_ok,
-                           (unsigned long long)hs, (unsigned long long)hw, cs));
-  GI_CUDA(cudaMemsetAsync(N->bitmap, 0, sizeof(uint32_t) * (size_t)(N->words > 0 ? N->words : 1), cs));
-  GI_CUDA(cudaMemsetAsync(N->count, 0, sizeof(int32_t), cs));
+  GI_TRY(dsg_step_launch(g, B, p, sc.delta, pull_ok, (unsigned long long)hs, (unsigned long long)hw, cs));
   // the switch node after what was captured so far
   cudaStreamCaptureStatus cst;
   const cudaGraphNode_t *deps = nullptr;
@@ -1284,7 +1250,7 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
     int st = GI_OK;
     const bool light = k < 2;
     const Csr &arcs = light ? D->light : D->heavy;
-    OpMinInt op{L->x, L->snap, arcs.wt};
+    OpMinInt op{L->x, light ? L->snap : L->snap_h, arcs.wt};
     if (k == kDgLightPush || k == kDgHeavyPush) {
       st = launch_push(g, op, kSrcQueue, light ? &Rv : &Sv, nullptr, out_of(N), sc, cs, &arcs);
     } else if (k == kDgLightPull || k == kDgHeavyPull) {
@@ -1301,7 +1267,8 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
     if (e != cudaSuccess) return cuda_fail(e, "branch capture", __FILE__, __LINE__);
   }
   GI_CUDA(cudaStreamBeginCaptureToGraph(cs, body, &sw, nullptr, 1, cudaStreamCaptureModeRelaxed));
-  k_dsg_post<<<grid, 256, 0, cs>>>(L->Rq, L->Sq, L->Sbm, L->snap, L->dw);
+  k_dsg_post<<<grid, 256, 0, cs>>>(L->Rq, L->Sq, L->Sbm, L->snap, L->snap_h, L->dw, F->queue, F->count, F->bitmap,
+                                   g->ctrl);
   GI_TRY(launch_status(1));
   N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
   return GI_OK;
@@ -1310,7 +1277,8 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
 static int dsloop_build(gi_graph *g, DeltaSplit *D, const gi_schedule &sc, DsLoop *L, cudaStream_t s) {
   const int64_t n = g->n;
   GI_TRY(heavy_get(g, s));
-  for (int32_t **p : {&L->x, &L->snap, &L->Rq, &L->Sq, &L->pile[0], &L->pile[1]}) GI_TRY(dev_alloc_n(p, n, s));
+  for (int32_t **p : {&L->x, &L->snap, &L->snap_h, &L->Rq, &L->Sq, &L->pile[0], &L->pile[1]})
+    GI_TRY(dev_alloc_n(p, n, s));
   GI_TRY(dev_alloc_n(&L->dw, kDgWords, s));
   GI_TRY(vset_alloc(g, &L->a, s));
   GI_TRY(vset_alloc(g, &L->b, s));
@@ -1376,10 +1344,11 @@ static int run_graph_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_sche
   const int64_t n = g->n;
   k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->x, n, INT32_MAX);
   k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->snap, n, INT32_MAX);
+  k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->snap_h, n, INT32_MAX);
   k_set_one<<<1, 1, 0, s>>>(L->x, src, 0);
   const int64_t cap64 = 4 * n + 16;
   k_dsg_init<<<1, 32, 0, s>>>(L->dw, sc.delta, (int32_t)(cap64 < INT32_MAX ? cap64 : INT32_MAX));
-  GI_TRY(launch_status(4));
+  GI_TRY(launch_status(5));
   GI_CUDA(cudaMemsetAsync(L->Sbm, 0, sizeof(uint32_t) * (size_t)L->a.words, s));
   GI_CUDA(cudaMemsetAsync(L->fbm, 0, sizeof(uint32_t) * (size_t)L->a.words, s));
   GI_TRY(front_init(g, &L->a, src, s));

@@ -1646,38 +1646,67 @@ __global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *
   }
 }
 
-// One round of graph-driven delta-stepping: statistics (and, for a heavy
-// round, the settled vertices' start-of-round distances) over R or S, then in
-// the last block the features, the direction (rule, or the MLP as in
-// k_frontier_decide) and the round's mode.
-__global__ void k_dsg_decide(const int32_t *__restrict__ Rq, const int32_t *__restrict__ Sq,
-                             const int32_t *__restrict__ deg_l, const int32_t *__restrict__ deg_h,
-                             const int32_t *__restrict__ x, int32_t *snap, int32_t *dw, int64_t *ctrl, DecideParams p,
-                             int64_t n, int64_t m, int32_t maxdeg, int use_selector, int32_t delta, int pull_ok,
-                             unsigned long long switch_handle, unsigned long long while_handle) {
-  __shared__ unsigned long long s_sum[32];
+// One round of graph-driven delta-stepping, set-up and decision (see
+// dsg_step_launch): the split of P into R / S / far pile with R's light and
+// S's heavy arc counts, then in the last block the features, the direction
+// (rule, or the MLP as in k_frontier_decide) and the round's mode.
+__global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t n, int64_t m, int32_t maxdeg,
+                           int use_selector, int32_t delta, int pull_ok, unsigned long long switch_handle,
+                           unsigned long long while_handle) {
+  __shared__ unsigned long long s_sum[2][32];
   __shared__ float sh[kDIn + kH + kH + 4];
   __shared__ float feat[kDIn];
   __shared__ bool last;
-  const int32_t rc = dw[kDgRc], sc = dw[kDgSc];
-  const bool light = rc > 0, heavy = !light && sc > 0;
-  const int32_t c = light ? rc : (heavy ? sc : 0);
-  const int32_t *q = light ? Rq : Sq;
-  const int32_t *deg = light ? deg_l : deg_h;
-  unsigned long long local = 0;
+  int32_t *dw = B.dw;
+  const int lane = lane_id();
+  const int32_t c = *B.Pc, hi = dw[kDgHi], cur = dw[kDgCur];
+  int32_t *pile = cur ? B.pile1 : B.pile0;
+  int32_t *pile_count = dw + kDgPile0 + cur;
   const int32_t stride = gridDim.x * blockDim.x;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += stride) {
-    const int32_t v = q[i];
-    local += deg[v];
-    if (heavy) snap[v] = x[v];  // the bucket's vertices are final
+  int32_t fmin = INT32_MAX;
+  unsigned long long ml = 0, mh = 0;
+  for (int32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < c; i0 += stride) {
+    const int32_t i = i0 + lane;
+    int32_t v = -1, d = INT32_MAX;
+    if (i < c) {
+      v = B.P[i];
+      d = B.x[v];
+    }
+    const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
+    const uint32_t bit = v >= 0 ? 1u << (v & 31) : 0u;
+    if (near) {
+      B.snap[v] = d;
+      B.snap_h[v] = d;
+      if (B.fbm[v >> 5] & bit) atomicAnd(B.fbm + (v >> 5), ~bit);  // its pile entry is now stale
+      ml += B.deg_l[v];
+    }
+    if (far) fmin = min(fmin, d);
+    const bool snew = near && bit_test_and_set(B.Sbm, v);
+    if (snew) mh += B.deg_h[v];
+    warp_append(B.Rq, dw + kDgRc, near, v);
+    warp_append(B.Sq, dw + kDgSc, snew, v);
+    warp_append(pile, pile_count, far && bit_test_and_set(B.fbm, v), v);
   }
-  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-  if (lane_id() == 0) s_sum[threadIdx.x >> 5] = local;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
+    ml += __shfl_xor_sync(0xffffffffu, ml, o);
+    mh += __shfl_xor_sync(0xffffffffu, mh, o);
+  }
+  if (lane == 0) {
+    if (fmin < INT32_MAX) atomicMin(dw + kDgPmin, fmin);
+    s_sum[0][threadIdx.x >> 5] = ml;
+    s_sum[1][threadIdx.x >> 5] = mh;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long b = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_sum[w];
-    atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kMfAcc), b);
+    unsigned long long bl = 0, bh = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      bl += s_sum[0][w];
+      bh += s_sum[1][w];
+    }
+    if (bl) atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kMfAcc), bl);
+    if (bh) atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kSHeavyMf), bh);
     __threadfence();
     const unsigned long long t = atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + kTicket), 1ull);
     last = (t == gridDim.x - 1);
@@ -1685,8 +1714,11 @@ __global__ void k_dsg_decide(const int32_t *__restrict__ Rq, const int32_t *__re
   __syncthreads();
   if (!last) return;
   __threadfence();
-  const int64_t nf = c;
-  const int64_t mf = *(volatile int64_t *)(ctrl + kMfAcc);
+  const int32_t rc = *(volatile int32_t *)(dw + kDgRc), sc = *(volatile int32_t *)(dw + kDgSc);
+  const bool light = rc > 0, heavy = !light && sc > 0;
+  const int64_t nf = light ? rc : (heavy ? sc : 0);
+  const int64_t mf = light ? *(volatile int64_t *)(ctrl + kMfAcc)
+                           : (heavy ? *(volatile int64_t *)(ctrl + kSHeavyMf) : 0);
   const int32_t was_pull = (int32_t)ctrl[kWasPull];
   const int64_t nf_prev = ctrl[kNfPrev];
   const int32_t round = dw[kDgRound];
@@ -1707,7 +1739,6 @@ __global__ void k_dsg_decide(const int32_t *__restrict__ Rq, const int32_t *__re
   }
   if (threadIdx.x == 0) {
     int32_t mode;
-    const int32_t cur = dw[kDgCur];
     if (relax) {
       const bool pull = dir == GI_DIR_DENSE_PULL;
       mode = light ? (pull ? kDgLightPull : kDgLightPush) : (pull ? kDgHeavyPull : kDgHeavyPush);
@@ -1718,8 +1749,8 @@ __global__ void k_dsg_decide(const int32_t *__restrict__ Rq, const int32_t *__re
     } else if (dw[kDgPile0 + cur] > 0) {
       // the bucket and its heavy round are done: next bucket from the pile
       mode = kDgAdvance;
-      const int64_t hi = ((int64_t)dw[kDgPmin] / delta + 1) * (int64_t)delta;
-      dw[kDgHi] = (int32_t)(hi < INT32_MAX ? hi : INT32_MAX);
+      const int64_t hi2 = ((int64_t)dw[kDgPmin] / delta + 1) * (int64_t)delta;
+      dw[kDgHi] = (int32_t)(hi2 < INT32_MAX ? hi2 : INT32_MAX);
       dw[kDgPile0 + (cur ^ 1)] = 0;
       dw[kDgPmin] = INT32_MAX;
     } else {
@@ -1742,12 +1773,10 @@ __global__ void k_dsg_decide(const int32_t *__restrict__ Rq, const int32_t *__re
   }
 }
 
-int dsg_decide_launch(gi_graph *g, const int32_t *Rq, const int32_t *Sq, const int32_t *deg_l, const int32_t *deg_h,
-                      const int32_t *x, int32_t *snap, int32_t *dw, const DecideParams &p, int32_t delta,
-                      bool pull_ok, unsigned long long switch_handle, unsigned long long while_handle, cudaStream_t s) {
-  k_dsg_decide<<<g->num_sms * 2, 256, 0, s>>>(Rq, Sq, deg_l, deg_h, x, snap, dw, g->ctrl, p, g->n, g->m, g->max_deg,
-                                              g_sel_loaded ? 1 : 0, delta, pull_ok ? 1 : 0, switch_handle,
-                                              while_handle);
+int dsg_step_launch(gi_graph *g, const DsgBuffers &b, const DecideParams &p, int32_t delta, bool pull_ok,
+                    unsigned long long switch_handle, unsigned long long while_handle, cudaStream_t s) {
+  k_dsg_step<<<g->num_sms * 4, 256, 0, s>>>(b, g->ctrl, p, g->n, g->m, g->max_deg, g_sel_loaded ? 1 : 0, delta,
+                                            pull_ok ? 1 : 0, switch_handle, while_handle);
   GI_LAUNCH_CHECK();
   return GI_OK;
 }

@@ -80,6 +80,7 @@ enum CtrlSlot {
   kMfAcc = 10,    // m_f accumulator of the statistics kernel (its last block returns it to 0)
   kFeat = 16,     // 16 float features stored as float bits in 8 int64 words (slots 16..23)
   kDsSlots = 32,  // delta-stepping SSSP: 8 int32 round words in slots 32..35 (fetched with the rest)
+  kSHeavyMf = 11, // graph-driven delta-stepping: heavy arcs of the bucket's settled list so far
 };
 
 // --------------------------------------------------------------- graph --
@@ -321,13 +322,24 @@ enum DsgWord {
   kDgWords = 16
 };
 enum DsgMode { kDgLightPush = 0, kDgLightPull = 1, kDgHeavyPush = 2, kDgHeavyPull = 3, kDgAdvance = 4, kDgDone = 5 };
-// Statistics and direction of one graph-driven delta-stepping round (one
-// launch on s): light round over R if it is non-empty, else the heavy round
-// over S (whose start-of-round distances it also sets in snap), else the next
-// bucket (advance) or the end; sets the switch and loop conditions.
-int dsg_decide_launch(gi_graph *g, const int32_t *Rq, const int32_t *Sq, const int32_t *deg_l, const int32_t *deg_h,
-                      const int32_t *x, int32_t *snap, int32_t *dw, const DecideParams &p, int32_t delta,
-                      bool pull_ok, unsigned long long switch_handle, unsigned long long while_handle, cudaStream_t s);
+// One graph-driven delta-stepping round's set-up, one launch on s: splits the
+// vertices whose distance changed (P) into this round's light sources R
+// (snap), the bucket's settled list S (snap_h keeps their latest distance)
+// and the far pile, summing R's light and S's heavy arc counts as it goes;
+// its last block then picks the round: the light round over R if R is
+// non-empty, else the bucket's heavy round over S, else the next bucket
+// (advance) or the end, with its direction (rule or the MLP), and sets the
+// switch and loop conditions.
+struct DsgBuffers {
+  const int32_t *P;
+  const int32_t *Pc;
+  const int32_t *x;
+  int32_t *dw, *Rq, *snap, *snap_h, *Sq, *pile0, *pile1;
+  uint32_t *Sbm, *fbm;
+  const int32_t *deg_l, *deg_h;
+};
+int dsg_step_launch(gi_graph *g, const DsgBuffers &b, const DecideParams &p, int32_t delta, bool pull_ok,
+                    unsigned long long switch_handle, unsigned long long while_handle, cudaStream_t s);
 int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s);
 int ctrl_fetch(gi_graph *g, cudaStream_t s);  // copies ctrl to pinned host + syncs
 
@@ -368,6 +380,18 @@ __device__ __forceinline__ bool bit_test_and_set(uint32_t *bm, int32_t v) {
   uint32_t mask = 1u << (v & 31);
   uint32_t old = atomicOr(bm + (v >> 5), mask);
   return (old & mask) == 0;
+}
+
+// one warp appends the ids of its lanes with pred set to q (count *qc); all
+// 32 lanes must call it
+__device__ __forceinline__ void warp_append(int32_t *q, int32_t *qc, bool pred, int32_t v) {
+  const unsigned b = __ballot_sync(0xffffffffu, pred);
+  if (!b) return;
+  const int lane = threadIdx.x & 31;
+  int32_t base = 0;
+  if (lane == 0) base = atomicAdd(qc, __popc(b));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (pred) q[base + __popc(b & ((1u << lane) - 1u))] = v;
 }
 
 
