@@ -923,6 +923,31 @@ def run_config_l(args):
     return 0
 
 
+def gather_ceiling(col, n, reps=5):
+    """Gathers per second of gi_gather_rate (the two memory streams of a pull and
+    nothing else) over the graph's own source ids and over uniform random ids
+    of the same count, both into an n-float table; best of `reps` launches."""
+    import torch
+    import paper_1805_00923_gb300 as gi
+    idx = torch.from_numpy(col).cuda()
+    rnd = torch.randint(0, n, (idx.numel(),), dtype=torch.int32, device="cuda",
+                        generator=torch.Generator(device="cuda").manual_seed(5))
+    table = torch.rand(n, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, ids in (("graph_ids", idx), ("uniform_random_ids", rnd)):
+        best = 1e30
+        for _ in range(reps + 1):
+            a, b = _events()
+            a.record()
+            gi.gather_rate(ids, table)
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        out[name] = {"gathers_per_s": ids.numel() / (best * 1e-3), "ms": best}
+    del idx, rnd, table
+    return out
+
+
 def rmat22_summary(args, hg, g, steps, value, total_ms, per_alg_ms, edges, launches, pr_launches, pr_ms, pr_s,
                    tuned, clocks):
     """The config-M step's numbers, for embedding in the BFS/SSSP line."""
@@ -931,6 +956,8 @@ def rmat22_summary(args, hg, g, steps, value, total_ms, per_alg_ms, edges, launc
     peak, peak_kind = measured_hbm()
     avg_ms = pr_ms / max(pr_launches, 1)
     achieved = (8 * m + 12 * n + 4) / (avg_ms * 1e-3) / 1e9
+    ceil = gather_ceiling(hg.col, n)
+    pull_rate = m / (avg_ms * 1e-3)
     out = {"workload": workload_config(hg, args.m_scale), "value": value, "unit": "GTEPS", "steps": steps,
            "ms_per_step": total_ms / steps,
            "per_algorithm": {
@@ -942,7 +969,9 @@ def rmat22_summary(args, hg, g, steps, value, total_ms, per_alg_ms, edges, launc
            "numerators": "PR 20m; PRD m per pull round + m_f per push round; CC m (every vertex reached)",
            "roofline_pr_pull": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                                 "bytes_model": "8m + 12n + 4 per launch", "avg_launch_ms": avg_ms,
-                                "launches_timed": pr_launches, "peak_kind": f"{peak_kind} hbm_gbs"},
+                                "launches_timed": pr_launches, "peak_kind": f"{peak_kind} hbm_gbs",
+                                "gather_ceiling": ceil, "pull_gathers_per_s": pull_rate,
+                                "frac_of_gather_ceiling_graph_ids": pull_rate / ceil["graph_ids"]["gathers_per_s"]},
            "autotuned": tuned, "gpu_launches": launches, "clocks": clocks}
     g.free()
     return out

@@ -810,10 +810,13 @@ __global__ void k_ds_round_init(int32_t *w) {
 // Splits the vertices whose distance changed last round (P): those below hi
 // form this round's R (snap = their distance), join the bucket's settled list
 // S once and leave the far pile if they were in it; the rest join the far
-// pile once (bitmap fbm) and lower its recorded minimum.
+// pile once and lower its recorded minimum.
+// P holds each vertex once, so the S and pile membership flags (bucket
+// number s_mark[v], byte pile_in[v]) are plain reads and writes.
 __global__ void k_ds_split(const int32_t *__restrict__ P, const int32_t *__restrict__ Pc,
-                           const int32_t *__restrict__ x, int32_t hi, int32_t *Rq, int32_t *snap, uint32_t *Sbm,
-                           int32_t *Sq, uint32_t *fbm, int32_t *pile, int32_t *pile_count, int32_t *w) {
+                           const int32_t *__restrict__ x, int32_t hi, int32_t *Rq, int32_t *snap, int32_t *s_mark,
+                           int32_t epoch, int32_t *Sq, uint8_t *pile_in, int32_t *pile, int32_t *pile_count,
+                           int32_t *w) {
   const int lane = threadIdx.x & 31;
   const int32_t c = *Pc;
   const int32_t stride = gridDim.x * blockDim.x;
@@ -826,27 +829,38 @@ __global__ void k_ds_split(const int32_t *__restrict__ P, const int32_t *__restr
       d = x[v];
     }
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
-    const uint32_t bit = v >= 0 ? 1u << (v & 31) : 0u;
+    bool snew = false, pnew = false;
     if (near) {
       snap[v] = d;
-      if (fbm[v >> 5] & bit) atomicAnd(fbm + (v >> 5), ~bit);  // its pile entry is now stale
+      if (pile_in[v]) pile_in[v] = 0;  // its pile entry is now stale
+      if (s_mark[v] != epoch) {
+        s_mark[v] = epoch;
+        snew = true;
+      }
     }
-    if (far) fmin = min(fmin, d);
+    if (far) {
+      fmin = min(fmin, d);
+      if (!pile_in[v]) {
+        pile_in[v] = 1;
+        pnew = true;
+      }
+    }
     warp_append(Rq, w + kDsR, near, v);
-    warp_append(Sq, w + kDsS, near && bit_test_and_set(Sbm, v), v);
-    warp_append(pile, pile_count, far && bit_test_and_set(fbm, v), v);
+    warp_append(Sq, w + kDsS, snew, v);
+    warp_append(pile, pile_count, pnew, v);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
   if (lane == 0 && fmin < INT32_MAX) atomicMin(w + kDsPileMin, fmin);
 }
 
-// Next bucket: the far pile's live entries (bit still set in fbm) below hi
-// leave it for the pending set P (queue + bitmap; P is empty here), the rest
-// are compacted into the other pile buffer, whose minimum is recomputed.
+// Next bucket: the far pile's live entries (pile_in still set) below hi
+// leave it for the pending set P (queue only; P is empty here and nothing
+// reads its bitmap before it is cleared), the rest are compacted into the
+// other pile buffer, whose minimum is recomputed.
 __global__ void k_ds_pile_split(const int32_t *__restrict__ pile, const int32_t *__restrict__ pile_count,
-                                const int32_t *__restrict__ x, int32_t hi, uint32_t *fbm, int32_t *Pq, int32_t *Pc,
-                                uint32_t *Pbm, int32_t *pile2, int32_t *pile2_count, int32_t *w) {
+                                const int32_t *__restrict__ x, int32_t hi, uint8_t *pile_in, int32_t *Pq,
+                                int32_t *Pc, int32_t *pile2, int32_t *pile2_count, int32_t *w) {
   const int lane = threadIdx.x & 31;
   const int32_t c = *pile_count;
   const int32_t stride = gridDim.x * blockDim.x;
@@ -856,14 +870,11 @@ __global__ void k_ds_pile_split(const int32_t *__restrict__ pile, const int32_t 
     int32_t v = -1, d = INT32_MAX;
     if (i < c) {
       v = pile[i];
-      if (!bit_test(fbm, v)) v = -1;  // left the pile after it was queued
+      if (!pile_in[v]) v = -1;  // left the pile after it was queued
       else d = x[v];
     }
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
-    if (near) {
-      atomicAnd(fbm + (v >> 5), ~(1u << (v & 31)));
-      atomicOr(Pbm + (v >> 5), 1u << (v & 31));
-    }
+    if (near) pile_in[v] = 0;
     if (far) fmin = min(fmin, d);
     warp_append(Pq, Pc, near, v);
     warp_append(pile2, pile2_count, far, v);
@@ -878,14 +889,6 @@ __global__ void k_ds_pile_prep(int32_t *w, int32_t target) {
   if (threadIdx.x == 0) {
     w[target] = 0;
     w[kDsPileMin] = INT32_MAX;
-  }
-}
-
-__global__ void k_ds_clear_s(const int32_t *__restrict__ Sq, int32_t *w, uint32_t *Sbm) {
-  const int32_t c = w[kDsS];
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
-    const int32_t v = Sq[i];
-    atomicAnd(Sbm + (v >> 5), ~(1u << (v & 31)));
   }
 }
 
@@ -919,8 +922,9 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
   const bool pull_ok = g->symmetric;
   VsetPair P;
   gi_vset R{}, S{};
-  int32_t *snap = nullptr, *Rq = nullptr, *Sq = nullptr, *pile[2] = {nullptr, nullptr};
-  uint32_t *Sbm = nullptr, *fbm = nullptr;
+  int32_t *snap = nullptr, *Rq = nullptr, *Sq = nullptr, *pile[2] = {nullptr, nullptr}, *s_mark = nullptr;
+  uint8_t *pile_in = nullptr;
+  int32_t epoch = 0;  // bucket number
   // the words live in the graph's control block, so the fetch of the
   // statistics brings them to the host in the same pinned copy
   int32_t *w = reinterpret_cast<int32_t *>(g->ctrl + kDsSlots);
@@ -931,8 +935,8 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
   if (st == GI_OK) st = dev_alloc_n(&Sq, n, s);
   if (st == GI_OK) st = dev_alloc_n(&pile[0], n, s);
   if (st == GI_OK) st = dev_alloc_n(&pile[1], n, s);
-  if (st == GI_OK) st = dev_alloc_n(&Sbm, P.a.words, s);
-  if (st == GI_OK) st = dev_alloc_n(&fbm, P.a.words, s);
+  if (st == GI_OK) st = dev_alloc_n(&s_mark, n, s);
+  if (st == GI_OK) st = dev_alloc_n(&pile_in, n, s);
   int32_t *prof_keep = nullptr;
   cudaEvent_t prof_ev[2] = {nullptr, nullptr};
   if (prof) {
@@ -943,11 +947,11 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
   if (st == GI_OK) {
     k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(x, n, INT32_MAX);
     k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(snap, n, INT32_MAX);
+    k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(s_mark, n, -1);
     k_set_one<<<1, 1, 0, s>>>(x, src, 0);
-    st = launch_status(3);
+    st = launch_status(4);
   }
-  if (st == GI_OK && (cudaMemsetAsync(Sbm, 0, sizeof(uint32_t) * (size_t)P.a.words, s) != cudaSuccess ||
-                      cudaMemsetAsync(fbm, 0, sizeof(uint32_t) * (size_t)P.a.words, s) != cudaSuccess))
+  if (st == GI_OK && cudaMemsetAsync(pile_in, 0, (size_t)(n > 0 ? n : 1), s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "delta-stepping init", __FILE__, __LINE__);
   if (st == GI_OK) st = front_init(g, P.F, src, s);
   if (st == GI_OK) st = ctrl_init(g, 0, 0, s);  // also zeroes the words
@@ -970,8 +974,8 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
   int32_t it = 0;
   while (st == GI_OK) {
     k_ds_round_init<<<1, 32, 0, s>>>(w);
-    k_ds_split<<<grid, 256, 0, s>>>(P.F->queue, P.F->count, x, (int32_t)(hi < INT32_MAX ? hi : INT32_MAX), Rq, snap,
-                                    Sbm, Sq, fbm, pile[cur], w + kDsPile0 + cur, w);
+    k_ds_split<<<g->num_sms * 2, 256, 0, s>>>(P.F->queue, P.F->count, x, (int32_t)(hi < INT32_MAX ? hi : INT32_MAX),
+                                              Rq, snap, s_mark, epoch, Sq, pile_in, pile[cur], w + kDsPile0 + cur, w);
     if ((st = launch_status(2)) != GI_OK) break;
     DecideParams p = decide_params(sc, it, false);
     if ((st = frontier_decide(g, &R, p, s, D->deg_l)) != GI_OK) break;
@@ -985,8 +989,8 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
       if ((st = vset_clear(P.F, s)) != GI_OK) break;
       k_ds_pile_prep<<<1, 32, 0, s>>>(w, kDsPile0 + (cur ^ 1));
       k_ds_pile_split<<<grid, 256, 0, s>>>(pile[cur], w + kDsPile0 + cur, x, (int32_t)(hi < INT32_MAX ? hi : INT32_MAX),
-                                           fbm, P.F->queue, P.F->count, P.F->bitmap, pile[cur ^ 1],
-                                           w + kDsPile0 + (cur ^ 1), w);
+                                           pile_in, P.F->queue, P.F->count, pile[cur ^ 1], w + kDsPile0 + (cur ^ 1),
+                                           w);
       if ((st = launch_status(2)) != GI_OK) break;
       P.F->reps = GI_REP_SPARSE | GI_REP_BITMAP;
       cur ^= 1;
@@ -1055,9 +1059,9 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
     k_snap_reset<<<grid, 256, 0, s>>>(Fr->queue, Fr->count, snap);
     int launched = 1;
     if (!light) {  // the bucket's settled list is done with
-      k_ds_clear_s<<<grid, 256, 0, s>>>(Sq, w, Sbm);
       k_ds_zero_s<<<1, 32, 0, s>>>(w);
-      launched += 2;
+      ++epoch;
+      launched += 1;
     }
     if ((st = launch_status(launched)) != GI_OK) break;
     P.N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
@@ -1073,8 +1077,8 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
   dev_free(Sq, s);
   dev_free(pile[0], s);
   dev_free(pile[1], s);
-  dev_free(Sbm, s);
-  dev_free(fbm, s);
+  dev_free(s_mark, s);
+  dev_free(pile_in, s);
   pair_free(P, s);
   if (st == GI_OK && cudaStreamSynchronize(s) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "delta-stepping", __FILE__, __LINE__);
@@ -1095,8 +1099,8 @@ namespace gi {
 
 // next bucket: live pile entries below hi -> the pending set N (cleared
 // before), the rest -> the other pile buffer with a fresh minimum
-__global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uint32_t *fbm, int32_t *pile0,
-                                 int32_t *pile1, int32_t *Nq, int32_t *Nc, uint32_t *Nbm) {
+__global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uint8_t *pile_in, int32_t *pile0,
+                                 int32_t *pile1, int32_t *Nq, int32_t *Nc) {
   const int lane = threadIdx.x & 31;
   const int32_t cur = dw[kDgCur], hi = dw[kDgHi];
   const int32_t *pile = cur ? pile1 : pile0;
@@ -1109,14 +1113,11 @@ __global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uin
     int32_t v = -1, d = INT32_MAX;
     if (i < c) {
       v = pile[i];
-      if (!bit_test(fbm, v)) v = -1;
+      if (!pile_in[v]) v = -1;  // left the pile after it was queued
       else d = x[v];
     }
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
-    if (near) {
-      atomicAnd(fbm + (v >> 5), ~(1u << (v & 31)));
-      atomicOr(Nbm + (v >> 5), 1u << (v & 31));
-    }
+    if (near) pile_in[v] = 0;
     if (far) fmin = min(fmin, d);
     warp_append(Nq, Nc, near, v);
     warp_append(pile2, dw + kDgPile0 + (cur ^ 1), far, v);
@@ -1127,12 +1128,12 @@ __global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uin
 }
 
 // round epilogue: the sources' snap entries back to INT32_MAX (after a heavy
-// round: snap_h, and S emptied), and this round's pending set F, consumed by
-// the split, emptied through its queue (it is the next round's output set);
-// the last block resets the round counters
-__global__ void k_dsg_post(const int32_t *__restrict__ Rq, const int32_t *__restrict__ Sq, uint32_t *Sbm,
-                           int32_t *snap, int32_t *snap_h, int32_t *dw, const int32_t *__restrict__ Fq,
-                           int32_t *Fc, uint32_t *Fbm, int64_t *ctrl) {
+// round: snap_h, and the next bucket number), and this round's pending set F,
+// consumed by the split, emptied through its queue (it is the next round's
+// output set); the last block resets the round counters
+__global__ void k_dsg_post(const int32_t *__restrict__ Rq, const int32_t *__restrict__ Sq, int32_t *snap,
+                           int32_t *snap_h, int32_t *dw, const int32_t *__restrict__ Fq, int32_t *Fc, uint32_t *Fbm,
+                           int64_t *ctrl) {
   __shared__ bool last;
   const int32_t mode = dw[kDgMode];
   const bool light = mode == kDgLightPush || mode == kDgLightPull;
@@ -1141,11 +1142,7 @@ __global__ void k_dsg_post(const int32_t *__restrict__ Rq, const int32_t *__rest
   const int32_t *q = light ? Rq : Sq;
   int32_t *sn = light ? snap : snap_h;
   const int32_t stride = gridDim.x * blockDim.x;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += stride) {
-    const int32_t v = q[i];
-    sn[v] = INT32_MAX;
-    if (heavy) atomicAnd(Sbm + (v >> 5), ~(1u << (v & 31)));
-  }
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += stride) sn[q[i]] = INT32_MAX;
   const int32_t fc = *Fc;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < fc; i += stride) Fbm[Fq[i] >> 5] = 0u;
   __syncthreads();
@@ -1161,6 +1158,7 @@ __global__ void k_dsg_post(const int32_t *__restrict__ Rq, const int32_t *__rest
   *Fc = 0;
   if (heavy) {
     dw[kDgSc] = 0;
+    dw[kDgEpoch] += 1;
     ctrl[kSHeavyMf] = 0;
   }
   if (mode == kDgAdvance) dw[kDgCur] ^= 1;
@@ -1182,9 +1180,9 @@ struct DsLoop {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int32_t *x = nullptr, *snap = nullptr, *snap_h = nullptr, *Rq = nullptr, *Sq = nullptr,
-          *pile[2] = {nullptr, nullptr};
+          *pile[2] = {nullptr, nullptr}, *s_mark = nullptr;
   int32_t *dw = nullptr;
-  uint32_t *Sbm = nullptr, *fbm = nullptr;
+  uint8_t *pile_in = nullptr;
   gi_vset a, b;
 };
 
@@ -1200,7 +1198,7 @@ static void dsloop_free(DeltaSplit *D) {
     dev_free(v->boolmap, nullptr);
   }
   for (void *p : {(void *)L->x, (void *)L->snap, (void *)L->snap_h, (void *)L->Rq, (void *)L->Sq, (void *)L->pile[0],
-                  (void *)L->pile[1], (void *)L->dw, (void *)L->Sbm, (void *)L->fbm})
+                  (void *)L->pile[1], (void *)L->dw, (void *)L->s_mark, (void *)L->pile_in})
     dev_free(p, nullptr);
   delete L;
   D->loop = nullptr;
@@ -1215,8 +1213,8 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
   const bool pull_ok = g->symmetric;
   cudaGraphConditionalHandle hs;
   GI_CUDA(cudaGraphConditionalHandleCreate(&hs, body, kDgDone, cudaGraphCondAssignDefault));
-  DsgBuffers B{F->queue, F->count, L->x, L->dw, L->Rq, L->snap, L->snap_h, L->Sq, L->pile[0], L->pile[1], L->Sbm,
-               L->fbm, D->deg_l, D->deg_h};
+  DsgBuffers B{F->queue, F->count, L->x, L->dw, L->Rq, L->snap, L->snap_h, L->Sq, L->pile[0], L->pile[1], L->s_mark,
+               L->pile_in, D->deg_l, D->deg_h};
   DecideParams p = decide_params(sc, 0, false);
   GI_TRY(dsg_step_launch(g, B, p, sc.delta, pull_ok, (unsigned long long)hs, (unsigned long long)hw, cs));
   // the switch node after what was captured so far
@@ -1257,8 +1255,7 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
       st = launch_pull_tiled(g, op, arcs, light ? D->tl : D->th, FSet(), nullptr, out_of(N), cs, kClassMinPull,
                              sc.balance == GI_BAL_VERTEX);
     } else {
-      k_dsg_pile_split<<<grid, 256, 0, cs>>>(L->x, L->dw, L->fbm, L->pile[0], L->pile[1], N->queue, N->count,
-                                             N->bitmap);
+      k_dsg_pile_split<<<grid, 256, 0, cs>>>(L->x, L->dw, L->pile_in, L->pile[0], L->pile[1], N->queue, N->count);
       st = launch_status(1);
     }
     cudaGraph_t got = nullptr;
@@ -1267,8 +1264,8 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
     if (e != cudaSuccess) return cuda_fail(e, "branch capture", __FILE__, __LINE__);
   }
   GI_CUDA(cudaStreamBeginCaptureToGraph(cs, body, &sw, nullptr, 1, cudaStreamCaptureModeRelaxed));
-  k_dsg_post<<<grid, 256, 0, cs>>>(L->Rq, L->Sq, L->Sbm, L->snap, L->snap_h, L->dw, F->queue, F->count, F->bitmap,
-                                   g->ctrl);
+  k_dsg_post<<<g->num_sms * 2, 256, 0, cs>>>(L->Rq, L->Sq, L->snap, L->snap_h, L->dw, F->queue, F->count, F->bitmap,
+                                             g->ctrl);
   GI_TRY(launch_status(1));
   N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
   return GI_OK;
@@ -1277,13 +1274,12 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
 static int dsloop_build(gi_graph *g, DeltaSplit *D, const gi_schedule &sc, DsLoop *L, cudaStream_t s) {
   const int64_t n = g->n;
   GI_TRY(heavy_get(g, s));
-  for (int32_t **p : {&L->x, &L->snap, &L->snap_h, &L->Rq, &L->Sq, &L->pile[0], &L->pile[1]})
+  for (int32_t **p : {&L->x, &L->snap, &L->snap_h, &L->Rq, &L->Sq, &L->pile[0], &L->pile[1], &L->s_mark})
     GI_TRY(dev_alloc_n(p, n, s));
   GI_TRY(dev_alloc_n(&L->dw, kDgWords, s));
+  GI_TRY(dev_alloc_n(&L->pile_in, n, s));
   GI_TRY(vset_alloc(g, &L->a, s));
   GI_TRY(vset_alloc(g, &L->b, s));
-  GI_TRY(dev_alloc_n(&L->Sbm, L->a.words, s));
-  GI_TRY(dev_alloc_n(&L->fbm, L->a.words, s));
   GI_CUDA(cudaStreamSynchronize(s));
   GI_CUDA(cudaGraphCreate(&L->graph, 0));
   cudaGraphConditionalHandle hw;
@@ -1345,12 +1341,12 @@ static int run_graph_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_sche
   k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->x, n, INT32_MAX);
   k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->snap, n, INT32_MAX);
   k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->snap_h, n, INT32_MAX);
+  k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->s_mark, n, -1);
   k_set_one<<<1, 1, 0, s>>>(L->x, src, 0);
   const int64_t cap64 = 4 * n + 16;
   k_dsg_init<<<1, 32, 0, s>>>(L->dw, sc.delta, (int32_t)(cap64 < INT32_MAX ? cap64 : INT32_MAX));
-  GI_TRY(launch_status(5));
-  GI_CUDA(cudaMemsetAsync(L->Sbm, 0, sizeof(uint32_t) * (size_t)L->a.words, s));
-  GI_CUDA(cudaMemsetAsync(L->fbm, 0, sizeof(uint32_t) * (size_t)L->a.words, s));
+  GI_TRY(launch_status(6));
+  GI_CUDA(cudaMemsetAsync(L->pile_in, 0, (size_t)(n > 0 ? n : 1), s));
   GI_TRY(front_init(g, &L->a, src, s));
   GI_TRY(vset_clear(&L->b, s));
   GI_TRY(ctrl_init(g, 0, 0, s));

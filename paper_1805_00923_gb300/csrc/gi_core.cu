@@ -1659,7 +1659,8 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
   __shared__ bool last;
   int32_t *dw = B.dw;
   const int lane = lane_id();
-  const int32_t c = *B.Pc, hi = dw[kDgHi], cur = dw[kDgCur];
+  // P holds each vertex once, so the membership flags need no atomics
+  const int32_t c = *B.Pc, hi = dw[kDgHi], cur = dw[kDgCur], epoch = dw[kDgEpoch];
   int32_t *pile = cur ? B.pile1 : B.pile0;
   int32_t *pile_count = dw + kDgPile0 + cur;
   const int32_t stride = gridDim.x * blockDim.x;
@@ -1673,19 +1674,28 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
       d = B.x[v];
     }
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
-    const uint32_t bit = v >= 0 ? 1u << (v & 31) : 0u;
+    bool snew = false, pnew = false;
     if (near) {
       B.snap[v] = d;
       B.snap_h[v] = d;
-      if (B.fbm[v >> 5] & bit) atomicAnd(B.fbm + (v >> 5), ~bit);  // its pile entry is now stale
+      if (B.pile_in[v]) B.pile_in[v] = 0;  // its pile entry is now stale
       ml += B.deg_l[v];
+      if (B.s_mark[v] != epoch) {
+        B.s_mark[v] = epoch;
+        snew = true;
+        mh += B.deg_h[v];
+      }
     }
-    if (far) fmin = min(fmin, d);
-    const bool snew = near && bit_test_and_set(B.Sbm, v);
-    if (snew) mh += B.deg_h[v];
+    if (far) {
+      fmin = min(fmin, d);
+      if (!B.pile_in[v]) {
+        B.pile_in[v] = 1;
+        pnew = true;
+      }
+    }
     warp_append(B.Rq, dw + kDgRc, near, v);
     warp_append(B.Sq, dw + kDgSc, snew, v);
-    warp_append(pile, pile_count, far && bit_test_and_set(B.fbm, v), v);
+    warp_append(pile, pile_count, pnew, v);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -1775,7 +1785,7 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
 
 int dsg_step_launch(gi_graph *g, const DsgBuffers &b, const DecideParams &p, int32_t delta, bool pull_ok,
                     unsigned long long switch_handle, unsigned long long while_handle, cudaStream_t s) {
-  k_dsg_step<<<g->num_sms * 4, 256, 0, s>>>(b, g->ctrl, p, g->n, g->m, g->max_deg, g_sel_loaded ? 1 : 0, delta,
+  k_dsg_step<<<g->num_sms * 2, 256, 0, s>>>(b, g->ctrl, p, g->n, g->m, g->max_deg, g_sel_loaded ? 1 : 0, delta,
                                             pull_ok ? 1 : 0, switch_handle, while_handle);
   GI_LAUNCH_CHECK();
   return GI_OK;

@@ -319,6 +319,7 @@ enum DsgWord {
   kDgCap = 11,    // round cap: reaching it stops the loop with kDgErr set
   kDgErr = 12,
   kDgTicket = 13,
+  kDgEpoch = 14,  // bucket number: S membership is s_mark[v] == epoch (no clearing between buckets)
   kDgWords = 16
 };
 enum DsgMode { kDgLightPush = 0, kDgLightPull = 1, kDgHeavyPush = 2, kDgHeavyPull = 3, kDgAdvance = 4, kDgDone = 5 };
@@ -335,7 +336,8 @@ struct DsgBuffers {
   const int32_t *Pc;
   const int32_t *x;
   int32_t *dw, *Rq, *snap, *snap_h, *Sq, *pile0, *pile1;
-  uint32_t *Sbm, *fbm;
+  int32_t *s_mark;   // bucket number in which v last joined S
+  uint8_t *pile_in;  // 1 while v waits in the far pile
   const int32_t *deg_l, *deg_h;
 };
 int dsg_step_launch(gi_graph *g, const DsgBuffers &b, const DecideParams &p, int32_t delta, bool pull_ok,

@@ -1162,6 +1162,9 @@ __global__ void __launch_bounds__(kPushBlock) k_push_heavy(Op op, const int32_t 
                                                            int64_t n, const uint32_t *__restrict__ to, OutSet out) {
   const HeavyList heavy = heavy_at(heavy_mem, n);
   const unsigned long long c64 = *(volatile unsigned long long *)heavy.ctr;
+  // nothing deferred: the list is already empty, and no block takes a ticket
+  // (the expansion of an empty list otherwise costs a ticket per block)
+  if (c64 == 0ull) return;
   const int32_t H = (int32_t)(c64 >> 32), C = (int32_t)(c64 & 0xffffffffull);
   for (int32_t c = blockIdx.x; c < C; c += gridDim.x) {
     int32_t lo = 0, hi = H - 1;  // last entry whose first chunk is <= c

@@ -28,19 +28,25 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def workloads(seed_base: int, quick: bool):
+def workloads(seed_base: int, quick: bool, large: bool = True):
+    """Training (or held-out) graphs: R-MAT up to scale 22 with three edge
+    factors and, with `large`, scale 24 at edge factor 16 (the size of the
+    benchmark's BFS/SSSP graph, from other seeds than its seed 1), plus grids."""
     import graphgen as gg
     out = []
     scales = [12, 14, 16, 18] if quick else [12, 14, 16, 18, 20, 22]
+    big = [24] if large else []
     for sc in scales:
         for ef in (8, 16, 32):
             out.append(("bfs", f"rmat{sc}_ef{ef}", lambda sc=sc, ef=ef: gg.rmat_graph(sc, ef, seed=seed_base + sc)))
-    for sc in scales:
+    for sc in big:
+        out.append(("bfs", f"rmat{sc}_ef16", lambda sc=sc: gg.rmat_graph(sc, 16, seed=seed_base + sc)))
+    for sc in scales + big:
         out.append(("sssp", f"rmat{sc}_w", lambda sc=sc: gg.rmat_graph(sc, 16, seed=seed_base + 50 + sc,
                                                                          weights=(1, 1000))))
-    # delta-stepping rounds (bucket widths around the bench's 64 for weights in [1,1000))
-    for sc in scales:
-        for d in (32, 64, 128):
+    # delta-stepping rounds (bucket widths around the benchmark's for weights in [1,1000))
+    for sc in scales + big:
+        for d in ((32, 64, 128, 256) if sc >= 20 else (32, 64, 128)):
             out.append((f"sssp_ds{d}", f"rmat{sc}_w", lambda sc=sc: gg.rmat_graph(sc, 16, seed=seed_base + 50 + sc,
                                                                                  weights=(1, 1000))))
     sides = [128, 256, 512] if quick else [128, 256, 512, 1024, 2048]
@@ -67,9 +73,14 @@ def collect(items, n_src: int, max_levels_per_run: int = 400):
     import paper_1805_00923_gb300 as gi
     from paper_1805_00923_gb300 import selector as sel
     X, T, tags = [], [], []
+    last = (None, None, None)  # consecutive items on the same graph reuse it
     for algo, name, make in items:
-        hg = make()
-        g = gi.Graph.from_host(hg)
+        if last[0] != name:
+            if last[2] is not None:
+                last[2].free()
+            hg = make()
+            last = (name, hg, gi.Graph.from_host(hg))
+        _, hg, g = last
         kern, sc = _sched(algo)
         for s in gg.pick_sources(hg, n_src, seed=len(name)):
             f, t = sel.profile(g, kern, int(s), sched=sc)
@@ -79,7 +90,8 @@ def collect(items, n_src: int, max_levels_per_run: int = 400):
             X.append(f)
             T.append(t)
             tags += [f"{algo}:{name}"] * len(f)
-        g.free()
+    if last[2] is not None:
+        last[2].free()
     return np.concatenate(X), np.concatenate(T), np.array(tags)
 
 
@@ -134,7 +146,12 @@ def main():
     params, mean, inv_std, losses = sel.train(X, T, M=M, steps=args.steps)
     t2 = time.time()
     sel.save(args.out, params, mean, inv_std, samples=X.shape[0], steps=args.steps, losses=np.array(losses))
-    held = [it for it in workloads(5000, True)]
+    held = [it for it in workloads(5000, True, large=False)]
+    # the benchmark's size, another seed: BFS, Bellman-Ford and delta-stepping at 128
+    import graphgen as gg
+    held += [("bfs", "rmat24_ef16", lambda: gg.rmat_graph(24, 16, seed=5024)),
+             ("sssp", "rmat24_w", lambda: gg.rmat_graph(24, 16, seed=5074, weights=(1, 1000))),
+             ("sssp_ds128", "rmat24_w", lambda: gg.rmat_graph(24, 16, seed=5074, weights=(1, 1000)))]
     rows = evaluate(params, mean, inv_std, held, 2)
     tot = {k: float(sum(r[k] for r in rows)) for k in ("learned_ms", "rule_ms", "best_ms")}
     report = dict(samples=int(X.shape[0]), collect_s=t1 - t0, train_s=t2 - t1, loss_first=losses[0],
