@@ -68,6 +68,12 @@ def parse():
                    help="profiling case: run just this algorithm --steps times on the workload graph")
     p.add_argument("--hot-cache", type=int, choices=[0, 1, 2], default=0,
                    help="profiling case: PageRank / PageRankDelta pulls with the hot-source cache")
+    p.add_argument("--only-delta", type=int, default=0,
+                   help="profiling case: SSSP bucket width (0 = Bellman-Ford)")
+    p.add_argument("--only-persistent", type=int, choices=[0, 1, 2], default=0,
+                   help="profiling case: single-query mode of BFS / SSSP (2 = graph-driven loop)")
+    p.add_argument("--only-direction", default="hybrid_pull",
+                   help="profiling case: direction of BFS / SSSP (hybrid_pull, learned, ...)")
     return p.parse_args()
 
 
@@ -508,6 +514,11 @@ def run_only(args):
     torch.cuda.set_device(0)
     hg = gg.rmat_graph(args.scale, seed=1, weights=(1, 1000) if args.only == "sssp" else None)
     g = gi.Graph.from_host(hg)
+    # BFS / SSSP from the first of the seeded sources of the BFS/SSSP workload
+    src = int(gg.pick_sources(hg, 1, seed=1)[0])
+    if args.only_direction == "learned":
+        from paper_1805_00923_gb300 import selector as sel
+        sel.install()
     for _ in range(args.steps):
         if args.only == "pagerank":
             gi.pagerank(g, DAMPING, PR_ITERS, sched=gi.schedule("dense_pull", hot_cache=args.hot_cache))
@@ -516,13 +527,14 @@ def run_only(args):
         elif args.only == "cc":
             gi.cc(g)
         elif args.only == "bfs":
-            gi.bfs(g, 0)
+            gi.bfs(g, src, sched=gi.schedule(args.only_direction, persistent=args.only_persistent))
         elif args.only == "bc":
             gi.bc(g, int(gg.pick_sources(hg, 10, seed=1)[0]), sched=gi.schedule("hybrid_pull", rule="ligra"))
         else:
-            gi.sssp(g, 0)
+            gi.sssp(g, src, sched=gi.schedule(args.only_direction, delta=args.only_delta,
+                                               persistent=args.only_persistent))
     torch.cuda.synchronize()
-    print(json.dumps({"only": args.only, "scale": args.scale, "n": hg.n, "m": hg.m, "runs": args.steps}))
+    print(json.dumps({"only": args.only, "scale": args.scale, "n": hg.n, "m": hg.m, "runs": args.steps, "source": src}))
     return 0
 
 
@@ -593,6 +605,8 @@ def _sssp_pull_bytes(n, m, tr, m_light=None):
                 scanned = m
                 nxt = int(fr[i + 1]) if i + 1 < len(fr) else 0
             else:
+                if ed[i] == 0:  # sources without arcs of the class: nothing is launched
+                    continue
                 scanned = m_light if ph[i] == 0 else m - m_light
                 nxt = 0
             total += 4 * (n + 1) + 8 * scanned + 8 * int(ed[i]) + n // 4 + 4 * nxt
@@ -1143,13 +1157,22 @@ def run_grid4096(args):
 
 
 def run_batch512(args):
-    """32 graphs (16 R-MAT scale 12-20, ef 8-32; 16 grids 256-2048), 512 BFS/SSSP queries in one launch."""
+    """32 graphs (16 R-MAT scale 12-20, ef 8-32; 16 grids 256-2048), 512 BFS/SSSP
+    queries in one launch per GPU.  With N ranks the queries are dealt by
+    graph size (replicas.shard_balanced) and every rank holds the graphs; the
+    time is the slowest rank's, latencies gather on rank 0.  Also the batch
+    autotuner's options against the defaults, at identical outputs."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     import graphgen as gg
     import paper_1805_00923_gb300 as gi
+    from paper_1805_00923_gb300 import replicas
     from paper_1805_00923_gb300 import selector as sel
-    torch.cuda.set_device(0)
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
     sel.install()
     rng = np.random.default_rng(1)
     hgs = [gg.rmat_graph(int(rng.integers(12, 21)), int(rng.choice([8, 16, 32])), seed=100 + i, weights=(1, 1000))
@@ -1157,31 +1180,58 @@ def run_batch512(args):
     hgs += [gg.grid_graph(int(rng.choice([256, 512, 1024, 2048])), seed=200 + i, weights=(1, 1000))
             for i in range(16)]
     gs = [gi.Graph.from_host(h) for h in hgs]
-    qs = []
+    qs_all = []
     for i in range(512):
         k = int(rng.integers(0, 32))
-        qs.append((k, int(gg.pick_sources(hgs[k], 1, seed=1000 + i)[0]), "bfs" if i % 2 == 0 else "sssp"))
-    edges = sum(hgs[q[0]].m for q in qs)
-    out = {}
-    for cs, order in ((2, 1), (4, 1), (4, 0), (8, 1)):
-        plan = gi.BatchPlan(gs, qs, opts=gi.batch_opts(cluster_size=cs, selector="learned", order=order))
+        qs_all.append((k, int(gg.pick_sources(hgs[k], 1, seed=1000 + i)[0]), "bfs" if i % 2 == 0 else "sssp"))
+    mine = replicas.shard_balanced([hgs[q[0]].n for q in qs_all], rank, world) if world > 1 else list(range(512))
+    qs = [qs_all[i] for i in mine]
+    edges = sum(hgs[q[0]].m for q in qs_all)
+
+    def timed(opts):
+        plan = gi.BatchPlan(gs, qs, opts=opts)
         plan.launch()
         plan.results()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
         a, b = _events()
         a.record()
         plan.launch()
         b.record()
         torch.cuda.synchronize()
-        _, ns, lev = plan.results()
-        plan.free()
+        res, ns, lev = plan.results()
         ms = a.elapsed_time(b)
-        out[f"cluster{cs}" + ("" if order == 1 else "_as_given")] = {"ms": ms, "gteps_nominal": edges / (ms * 1e-3) / 1e9,
-                               "p50_ms": float(np.percentile(ns, 50) / 1e6),
-                               "p99_ms": float(np.percentile(ns, 99) / 1e6)}
-    best = max(out.values(), key=lambda r: r["gteps_nominal"])
-    print(json.dumps({"metric": METRIC, "workload": "batch512", "value": best["gteps_nominal"], "unit": "GTEPS",
-                      "graphs": 32, "queries": 512, "results": out,
-                      "note": "nominal GTEPS = sum over queries of the graph's m / time"}))
+        plan.free()
+        ms_all = replicas.max_over_ranks(ms, device="cuda") if world > 1 else ms
+        ns_all = np.concatenate(replicas.gather_objects(ns)) if world > 1 else ns
+        return ms_all, ns_all
+
+    out = {}
+    for cs, order in ((2, 1), (4, 1), (4, 0), (8, 1)):
+        ms, ns = timed(gi.batch_opts(cluster_size=cs, selector="learned", order=order))
+        out[f"cluster{cs}" + ("" if order == 1 else "_as_given")] = {
+            "ms": ms, "gteps_nominal": edges / (ms * 1e-3) / 1e9,
+            "p50_ms": float(np.percentile(ns, 50) / 1e6), "p99_ms": float(np.percentile(ns, 99) / 1e6)}
+    # the batch autotuner on this rank's queries (untimed search; outputs checked)
+    start = gi.batch_opts(cluster_size=4, selector="learned")
+    best, best_ms, start_ms = gi.batch_autotune(gs, qs, start=start, budget=args.tune_budget, seed=11)
+    ms, ns = timed(best)
+    out["autotuned"] = {"ms": ms, "gteps_nominal": edges / (ms * 1e-3) / 1e9,
+                        "p50_ms": float(np.percentile(ns, 50) / 1e6), "p99_ms": float(np.percentile(ns, 99) / 1e6),
+                        "options": {f: getattr(best, f) for f in ("cluster_size", "t_warp", "t_cta", "sssp_delta",
+                                                                  "order")},
+                        "search_best_ms": best_ms, "search_start_ms": start_ms}
+    best_row = max((v for k, v in out.items()), key=lambda r: r["gteps_nominal"])
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "workload": "batch512", "value": best_row["gteps_nominal"],
+                          "unit": "GTEPS", "graphs": 32, "queries": 512, "n_gpus": world,
+                          "sharding": "queries dealt by graph size over the ranks (each rank holds every graph)"
+                          if world > 1 else None, "results": out,
+                          "note": "nominal GTEPS = sum over queries of the graph's m / time (slowest rank)"}))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 

@@ -27,6 +27,19 @@ def shard(n_items: int, rank: int, world_size: int) -> range:
     return range(lo, lo + base + (1 if rank < extra else 0))
 
 
+def shard_balanced(costs, rank: int, world_size: int) -> list[int]:
+    """Item indices owned by `rank` when items of the given costs are dealt
+    longest first to the rank with the least cost so far (ties to the lower
+    rank): every item exactly once, deterministic on every rank."""
+    load = [0.0] * world_size
+    owner = [0] * len(costs)
+    for i in sorted(range(len(costs)), key=lambda i: (-float(costs[i]), i)):
+        r = min(range(world_size), key=lambda r: (load[r], r))
+        owner[i] = r
+        load[r] += float(costs[i])
+    return [i for i in range(len(costs)) if owner[i] == rank]
+
+
 def max_over_ranks(x: float, device: str = "cpu") -> float:
     if not (dist.is_available() and dist.is_initialized()):
         return float(x)

@@ -140,6 +140,14 @@ def main():
     from paper_1805_00923_gb300 import selector as sel
     t0 = time.time()
     X, Tms, tags = collect(workloads(1000, args.quick), args.sources)
+    # Feature 14 says whether the previous level pulled.  In the profiles it
+    # follows the rule's choices; run by the network it follows the network's
+    # own, while the timed kernels do not depend on it.  Every sample is
+    # therefore given with both values, so that the network cannot learn
+    # "pulled before, pull again" from the rule and feed it back to itself.
+    X2 = X.copy()
+    X2[:, 14] = 1.0 - X2[:, 14]
+    X, Tms, tags = np.concatenate([X, X2]), np.concatenate([Tms, Tms]), np.concatenate([tags, tags])
     t1 = time.time()
     M = (Tms > 0).astype(np.float32)   # directions not offered in a mode are masked out
     T = sel.targets(np.where(Tms > 0, Tms, 1.0))

@@ -57,6 +57,14 @@ def test_sssp_pull_bytes_counts_pull_rounds_only():
     want = sum(4 * (n + 1) + 8 * m + 8 * e + n // 4 + 4 * nx for e, nx in ((200, 900), (5000, 50)))
     assert bench._sssp_pull_bytes(n, m, T()) == (want, 2)
 
+    class D:  # delta-stepping: light (phase 0) and heavy (1) rounds; a pull round without arcs launches nothing
+        def as_dict(self):
+            return {"frontier": np.array([1, 40, 900, 50, 7]), "edges": np.array([3, 200, 5000, 300, 0]),
+                    "direction": np.array([0, 2, 2, 0, 2]), "phase": np.array([0, 0, 1, 0, 1])}
+    ml = 6000
+    want = (4 * (n + 1) + 8 * ml + 8 * 200 + n // 4) + (4 * (n + 1) + 8 * (m - ml) + 8 * 5000 + n // 4)
+    assert bench._sssp_pull_bytes(n, m, D(), ml) == (want, 2)
+
 
 def test_reference_arm_json_line():
     """`--impl reference` prints one JSON line with the contract's keys and
