@@ -72,6 +72,8 @@ def parse():
                    help="profiling case: SSSP bucket width (0 = Bellman-Ford)")
     p.add_argument("--only-persistent", type=int, choices=[0, 1, 2], default=0,
                    help="profiling case: single-query mode of BFS / SSSP (2 = graph-driven loop)")
+    p.add_argument("--only-source", type=int, default=0,
+                   help="profiling case: BFS / SSSP source (-1: the first seeded source of the BFS/SSSP workload)")
     p.add_argument("--only-direction", default="hybrid_pull",
                    help="profiling case: direction of BFS / SSSP (hybrid_pull, learned, ...)")
     return p.parse_args()
@@ -514,8 +516,8 @@ def run_only(args):
     torch.cuda.set_device(0)
     hg = gg.rmat_graph(args.scale, seed=1, weights=(1, 1000) if args.only == "sssp" else None)
     g = gi.Graph.from_host(hg)
-    # BFS / SSSP from the first of the seeded sources of the BFS/SSSP workload
-    src = int(gg.pick_sources(hg, 1, seed=1)[0])
+    # BFS / SSSP source: --only-source, or the first of the BFS/SSSP workload's seeded sources when -1
+    src = args.only_source if args.only_source >= 0 else int(gg.pick_sources(hg, 1, seed=1)[0])
     if args.only_direction == "learned":
         from paper_1805_00923_gb300 import selector as sel
         sel.install()
