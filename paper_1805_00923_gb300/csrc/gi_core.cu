@@ -1628,9 +1628,14 @@ __global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *
     ctrl[kNu] = nu;
     ctrl[kMu] = mu;
     ctrl[kDecision] = dir;
-    ctrl[kWasPull] = (dir == GI_DIR_DENSE_PULL) ? 1 : 0;
+    // the previous-level features describe the last non-empty frontier: a
+    // statistics pass over an empty set (delta-stepping's R before a heavy
+    // round; the last check of the other loops) leaves them as they were
+    if (nf > 0) {
+      ctrl[kWasPull] = (dir == GI_DIR_DENSE_PULL) ? 1 : 0;
+      ctrl[kNfPrev] = nf;
+    }
     ctrl[kLevel] = level;
-    ctrl[kNfPrev] = nf;
     ctrl[kTicket] = 0;
     ctrl[kMfAcc] = 0;
     if (p.clear_qc) *p.clear_qc = 0;  // every block has passed its clearing loop
