@@ -1129,17 +1129,24 @@ def run_grid4096(args):
         b.record()
         torch.cuda.synchronize()
         pers_ms = a.elapsed_time(b) / 4
-        graph_ms = None
-        if algo == "bfs":  # the level loop as a CUDA graph (BFS)
-            gsc = gi.schedule("hybrid_pull", persistent=2)
-            gi.bfs(g, int(srcs[0]), want_parent=False, sched=gsc)
+        # the level loop as a CUDA graph (BFS; SSSP by delta-stepping at
+        # bucket widths of 1x, 2x and 4x the mean weight, and Bellman-Ford)
+        graph = {}
+        for name, gsc in ((("rule", gi.schedule("hybrid_pull", persistent=2)),
+                           ("learned", gi.schedule("learned", persistent=2))) if algo == "bfs" else
+                          tuple((f"delta{d}_learned", gi.schedule("learned", persistent=2, delta=d))
+                                for d in (50, 100, 200))):
+            run = (lambda s_: gi.bfs(g, int(s_), want_parent=False, sched=gsc)) if algo == "bfs" \
+                else (lambda s_: gi.sssp(g, int(s_), sched=gsc))
+            run(srcs[0])
             a, b = _events()
             a.record()
             for s_ in srcs[:4]:
-                gi.bfs(g, int(s_), want_parent=False, sched=gsc)
+                run(s_)
             b.record()
             torch.cuda.synchronize()
-            graph_ms = a.elapsed_time(b) / 4
+            graph[name] = a.elapsed_time(b) / 4
+        graph_ms = graph
         qs = [(0, int(s_), algo) for s_ in srcs]
         plan = gi.BatchPlan([g], qs, opts=gi.batch_opts(cluster_size=8, selector="learned"))
         plan.launch()
