@@ -1512,7 +1512,7 @@ namespace gi {
 constexpr int kDIn = 16, kH = 64, kDOut = 3;
 constexpr int kNParam = kH * kDIn + kH + kH * kH + kH + kDOut * kH + kDOut;
 
-__device__ float d_sel_params[kNParam];
+__device__ __align__(16) float d_sel_params[kNParam];  // 16-byte aligned rows: W2 and W3 start at multiples of 4
 __device__ float d_sel_mean[kDIn];
 __device__ float d_sel_istd[kDIn];
 static bool g_sel_loaded = false;
@@ -1521,28 +1521,47 @@ bool selector_loaded() { return g_sel_loaded; }
 
 // MLP forward by one block (>= 64 threads); returns argmin of predicted log-time
 __device__ int32_t selector_forward(const float *x_raw, float *sh /* >= 16+64+64+3 floats */) {
+  // Called by all 256 threads of one block.  Layers 1 and 2: four threads
+  // per hidden unit, each a quarter of the dot product with 16-byte weight
+  // loads, summed by shuffles; layer 3: one warp per output.  Every load is
+  // independent, so a decision costs a few memory round trips rather than a
+  // chain of 64 dependent ones per thread.
   float *x = sh, *h1 = sh + kDIn, *h2 = h1 + kH, *y = h2 + kH;
   const float *W1 = d_sel_params, *b1 = W1 + kH * kDIn, *W2 = b1 + kH, *b2 = W2 + kH * kH, *W3 = b2 + kH,
               *b3 = W3 + kDOut * kH;
-  int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31;
   if (t < kDIn) x[t] = (x_raw[t] - d_sel_mean[t]) * d_sel_istd[t];
   __syncthreads();
-  if (t < kH) {
-    float s = b1[t];
-    for (int i = 0; i < kDIn; ++i) s = fmaf(W1[t * kDIn + i], x[i], s);
-    h1[t] = fmaxf(s, 0.0f);
+  const int unit = t >> 2, part = t & 3;  // 64 units x 4 parts = 256 threads
+  if (unit < kH) {
+    const float4 w = *reinterpret_cast<const float4 *>(W1 + unit * kDIn + part * 4);
+    float s = w.x * x[part * 4] + w.y * x[part * 4 + 1] + w.z * x[part * 4 + 2] + w.w * x[part * 4 + 3];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (part == 0) h1[unit] = fmaxf(s + b1[unit], 0.0f);
   }
   __syncthreads();
-  if (t < kH) {
-    float s = b2[t];
-    for (int i = 0; i < kH; ++i) s = fmaf(W2[t * kH + i], h1[i], s);
-    h2[t] = fmaxf(s, 0.0f);
+  if (unit < kH) {
+    const float4 *w4 = reinterpret_cast<const float4 *>(W2 + unit * kH + part * 16);
+    const float *hp = h1 + part * 16;
+    float s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 w = w4[j];
+      s += w.x * hp[4 * j] + w.y * hp[4 * j + 1] + w.z * hp[4 * j + 2] + w.w * hp[4 * j + 3];
+    }
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (part == 0) h2[unit] = fmaxf(s + b2[unit], 0.0f);
   }
   __syncthreads();
-  if (t < kDOut) {
-    float s = b3[t];
-    for (int i = 0; i < kH; ++i) s = fmaf(W3[t * kH + i], h2[i], s);
-    y[t] = s;
+  const int out = t >> 5;
+  if (out < kDOut) {
+    const float2 w = *reinterpret_cast<const float2 *>(W3 + out * kH + lane * 2);
+    float s = w.x * h2[lane * 2] + w.y * h2[lane * 2 + 1];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[out] = s + b3[out];
   }
   __syncthreads();
   int32_t best = 0;
