@@ -595,12 +595,13 @@ def _sssp_pull_bytes(n, m, tr, m_light=None):
     arc) + 8 m_f (weight and distance per source arc) + V/4 (bitmaps) +
     4|F_next|, where m' is the arcs the round scans: m for Bellman-Ford, the
     light or heavy arc count for a delta-stepping round (phase 0 / 1; then
-    |F_next| is not recorded and the term is left out)."""
+    |F_next| is not recorded and the term is left out).  Returns (bytes,
+    pull rounds, arcs the pull rounds scanned)."""
     import numpy as np
     t = tr.as_dict()
     fr, ed, dr = t["frontier"], t["edges"], t["direction"]
     ph = t.get("phase", np.zeros(len(dr), np.int32))
-    total, rounds = 0, 0
+    total, rounds, arcs = 0, 0, 0
     for i in range(len(dr)):
         if dr[i] == 2:  # GI_DIR_DENSE_PULL
             if m_light is None:
@@ -613,7 +614,8 @@ def _sssp_pull_bytes(n, m, tr, m_light=None):
                 nxt = 0
             total += 4 * (n + 1) + 8 * scanned + 8 * int(ed[i]) + n // 4 + 4 * nxt
             rounds += 1
-    return total, rounds
+            arcs += scanned
+    return total, rounds, arcs
 
 
 def host_cpu():
@@ -778,13 +780,18 @@ def run_config_l(args):
     gi.stats_enable(False)
     host_ms = a0.elapsed_time(a1) / len(srcs)
     _, pull_launches, pull_ms = gi.stats_read("min_pull")
-    pull_bytes, pull_rounds = 0, 0
+    pull_bytes, pull_rounds, pull_arcs = 0, 0, 0
     for s_ in srcs:
-        b_, r_ = _sssp_pull_bytes(n, m, traces[s_], m_light)
+        b_, r_, a_ = _sssp_pull_bytes(n, m, traces[s_], m_light)
         pull_bytes += b_
         pull_rounds += r_
+        pull_arcs += a_
     peak, peak_kind = measured_hbm()
     achieved = pull_bytes / (pull_ms * 1e-3) / 1e9 if pull_ms > 0 else 0.0
+    # the second ceiling of a pull: one gathered 4-byte value per arc
+    # (gi_gather_rate over this graph's source ids into an n-entry table)
+    ceil = gather_ceiling(hg.col, n)
+    pull_rate = pull_arcs / (pull_ms * 1e-3) if pull_ms > 0 else 0.0
 
     # learned vs rule per algorithm, 3 interleaved repeats each (outside the timed region)
     def per_alg(pol):
@@ -916,7 +923,9 @@ def run_config_l(args):
                                      f"({host_ms:.2f} ms per query)",
                          "launches_timed": pull_launches, "pull_rounds_expected": pull_rounds,
                          "avg_launch_ms": pull_ms / max(pull_launches, 1),
-                         "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"},
+                         "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                         "gather_ceiling": ceil, "pull_gathers_per_s": pull_rate,
+                         "frac_of_gather_ceiling_graph_ids": pull_rate / ceil["graph_ids"]["gathers_per_s"]},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * e2e_s / args.e2e_steps, "steps": args.e2e_steps,
                     "form": "gi_load_csr from pinned host CSR + weights, then the 64 BFS + SSSP queries; each "

@@ -55,7 +55,7 @@ def test_sssp_pull_bytes_counts_pull_rounds_only():
                     "direction": np.array([0, 2, 2, 0])}
     n, m = 1000, 20000
     want = sum(4 * (n + 1) + 8 * m + 8 * e + n // 4 + 4 * nx for e, nx in ((200, 900), (5000, 50)))
-    assert bench._sssp_pull_bytes(n, m, T()) == (want, 2)
+    assert bench._sssp_pull_bytes(n, m, T()) == (want, 2, 2 * m)
 
     class D:  # delta-stepping: light (phase 0) and heavy (1) rounds; a pull round without arcs launches nothing
         def as_dict(self):
@@ -63,7 +63,7 @@ def test_sssp_pull_bytes_counts_pull_rounds_only():
                     "direction": np.array([0, 2, 2, 0, 2]), "phase": np.array([0, 0, 1, 0, 1])}
     ml = 6000
     want = (4 * (n + 1) + 8 * ml + 8 * 200 + n // 4) + (4 * (n + 1) + 8 * (m - ml) + 8 * 5000 + n // 4)
-    assert bench._sssp_pull_bytes(n, m, D(), ml) == (want, 2)
+    assert bench._sssp_pull_bytes(n, m, D(), ml) == (want, 2, m)
 
 
 def test_reference_arm_json_line():
