@@ -846,14 +846,44 @@ def run_config_l(args):
     # same state (gi_selector_profile), minima summed
     nx = max(1, min(len(srcs), args.exhaustive_sources))
     ex_ms = {"bfs": 0.0, "sssp": 0.0}
+    # the same per-level times summed over the direction each policy picks
+    # (its host-driven trace: the levels and rounds do not depend on the
+    # directions), so that the policies' direction choices compare without
+    # their loop overheads
+    replay = {a: {"learned": 0.0, "rule": 0.0, "levels": 0, "unmatched": 0} for a in ("bfs", "sssp")}
+
+    def chosen(algo, t, pol):
+        tr = gi.Trace(1 << 14)
+        if algo == "bfs":
+            gi.bfs(g, s_, want_parent=False, sched=gi.schedule(pol), trace=tr)
+        else:
+            gi.sssp(g, s_, sched=gi.schedule(pol, delta=delta), trace=tr, out=dist_)
+        torch.cuda.synchronize()
+        d = tr.as_dict()["direction"]
+        k = min(len(t), len(d))
+        replay[algo]["unmatched"] += abs(len(t) - len(d))
+        return float(sum(t[i, int(d[i])] for i in range(k)))
+
     for s_ in srcs[:nx]:
         _, t = sel.profile(g, gi.GI_K_BFS, s_)
         ex_ms["bfs"] += float(t.min(axis=1).sum())
+        for pol, name in (("learned", "learned"), ("hybrid_pull", "rule")):
+            replay["bfs"][name] += chosen("bfs", t, pol)
+        replay["bfs"]["levels"] += len(t)
         _, t = sel.profile(g, gi.GI_K_SSSP, s_, sched=gi.schedule("hybrid_pull", delta=delta))
         ex_ms["sssp"] += float(np.where(t > 0, t, np.inf).min(axis=1).sum())
+        for pol, name in (("learned", "learned"), ("hybrid_pull", "rule")):
+            replay["sssp"][name] += chosen("sssp", t, pol)
+        replay["sssp"]["levels"] += len(t)
+    for a in replay:
+        for k in ("learned", "rule"):
+            replay[a][k] /= nx
+        replay[a]["best"] = ex_ms[a] / nx
     exhaustive = {"sources": nx, "bfs_ms_per_query": ex_ms["bfs"] / nx, "sssp_ms_per_query": ex_ms["sssp"] / nx,
+                  "policies_replayed_ms_per_query": replay,
                   "note": "sum over levels (rounds) of the fastest direction timed alone, without the per-level "
-                          "statistics kernel and loop control; BFS without parents"}
+                          "statistics kernel and loop control; BFS without parents.  policies_replayed: the same "
+                          "per-level times summed over each policy's own choices"}
 
     # end to end through the C ABI: CSR + weights from pinned host buffers
     # (gi_load_csr), every query's depth, parent and distance copied back to
@@ -1066,7 +1096,13 @@ def run_levels(args):
 
     depth, _ = gi.bfs(g, src, want_parent=False)
     _, tb = sel.profile(g, gi.GI_K_BFS, src)
+    # the same levels with the pull walking every vertex instead of the
+    # compacted list of unvisited vertices with in-arcs (gi_schedule.dst_list)
+    _, tb0 = sel.profile(g, gi.GI_K_BFS, src, sched=gi.schedule("hybrid_pull", dst_list=0))
     lv = _bfs_level_bytes(depth, col, row, row_ptr, deg, tb.shape[0])
+    has_arcs = deg > 0
+    for i in range(tb.shape[0]):
+        lv[i]["n_u_live"] = int((((depth > i) | (depth < 0)) & has_arcs).sum())
 
     def bfs_bytes(i):
         x = lv[i]
@@ -1088,6 +1124,11 @@ def run_levels(args):
                 "dense_pull": pull}
 
     bfs_rows = rows(tb, bfs_bytes)
+    for r, t0 in zip(bfs_rows, tb0[:, 2]):
+        ms = float(t0)
+        b = r["dense_pull"]["bytes"]
+        gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        r["dense_pull_all_vertices"] = {"ms": ms, "bytes": b, "gbs": gbs, "frac": gbs / peak}
     sssp_rows = rows(ts[:len(d["frontier"])], sssp_bytes)
 
     def best(rs):

@@ -222,11 +222,11 @@ typedef struct gi_schedule {
                         /* persistent kernel (the batched engine's whole-GPU mode), the */
                         /* direction chosen on the device (LEARNED: the MLP; SPARSE_PUSH */
                         /* or DENSE_PUSH: push only; otherwise Beamer's rule); the trace */
-                        /* then records only the level count.  2 (gi_bfs only; gi_sssp  */
-                        /* runs host-driven) = the level loop is a CUDA graph (a WHILE */
-                        /* node over the library's per-level kernels, direction and     */
-                        /* loop condition set on the device, no host round trip per     */
-                        /* level), built on first use and cached per graph and schedule; */
+                        /* then records only the level count.  2 = the level loop is a */
+                        /* CUDA graph (a WHILE node over the library's per-level or    */
+                        /* per-round kernels, direction and loop condition set on the  */
+                        /* device, no host round trip per level; gi_sssp: see there),  */
+                        /* built on first use and cached per graph and schedule;       */
                         /* trace: level count only.  0 = one host-driven round per level. */
   int32_t hot_cache;    /* PageRank / PageRankDelta / CC / SSSP DensePull over the whole */
                         /* graph (CC and SSSP: their driver rounds):                   */
@@ -242,12 +242,17 @@ typedef struct gi_schedule {
   int32_t delta;        /* gi_sssp only: 0 = Bellman-Ford in synchronous rounds (Sec. 7);  */
                         /* > 0 = delta-stepping with buckets of this width in weight units */
                         /* (see gi_sssp); same distances either way                        */
+  int32_t dst_list;     /* gi_bfs (and gi_selector_profile's BFS) DensePull levels: 1 =    */
+                        /* walk a compacted list of the unvisited vertices that have       */
+                        /* in-arcs (the destination filter kept sparse: built once per     */
+                        /* graph, 12 bytes per such vertex, shrunk at every pull level);   */
+                        /* 0 = walk every vertex.  Same depths and parents either way.     */
 } gi_schedule;
 
 /* Defaults: HYBRID_PULL, BITMAP, EDGE_AWARE, 1 segment (FVC when segmented), 256
  * threads, t_warp 32, t_cta 256, Beamer alpha 14 beta 24, 2048-arc tiles, t_heavy 256,
- * not persistent, hot_cache 0, delta 0.  Every driver rejects a schedule with a field out of
- * range with GI_ERR_INVALID_ARG. */
+ * not persistent, hot_cache 0, delta 0, dst_list 1.  Every driver rejects a schedule with a
+ * field out of range with GI_ERR_INVALID_ARG. */
 void gi_schedule_default(gi_schedule *s);
 
 /* ------------------------------------------------------------ edgeset apply -- */
@@ -560,8 +565,9 @@ int gi_batch_plan_free(gi_batch_plan *p);
  * start->direction/balance/rule and searches tile_edges, t_warp, t_cta,
  * t_heavy, block, hot_cache (not BFS), the dense frontier representation
  * dense_rep (not PageRank), num_segments and seg_strategy (PageRank
- * DensePull), delta (SSSP: Bellman-Ford or delta-stepping bucket widths) and,
- * for rule-based BFS hybrids, Beamer's alpha/beta: random candidates for the
+ * DensePull), delta (SSSP: Bellman-Ford or delta-stepping bucket widths),
+ * dst_list (BFS) and, for rule-based BFS hybrids, Beamer's alpha/beta: random
+ * candidates for the
  * first third of `budget`
  * trials, then hill climbing around the best.  Each candidate runs once to
  * warm up and is timed (best of 2) with CUDA events on `stream`; a candidate

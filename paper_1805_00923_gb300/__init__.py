@@ -52,7 +52,10 @@ def schedule(direction="hybrid_pull", **kw) -> gi_schedule:
     if isinstance(direction, str):
         direction = L.DIRECTIONS[direction]
     s.direction = direction
+    fields = {f for f, _ in gi_schedule._fields_}
     for k, v in kw.items():
+        if k not in fields:
+            raise TypeError(f"gi_schedule has no field {k!r}")
         if k == "balance" and isinstance(v, str):
             v = {"vertex": GI_BAL_VERTEX, "edge_aware": GI_BAL_EDGE_AWARE, "edge_parallel": L.GI_BAL_EDGE_PARALLEL}[v]
         if k == "seg_strategy" and isinstance(v, str):

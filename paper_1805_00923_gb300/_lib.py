@@ -41,7 +41,8 @@ class gi_schedule(ctypes.Structure):
     _fields_ = [("direction", _i32), ("dense_rep", _u32), ("balance", _i32), ("num_segments", _i32),
                 ("block", _i32), ("t_warp", _i32), ("t_cta", _i32), ("rule", _i32), ("alpha", _f32),
                 ("beta", _f32), ("tile_edges", _i32), ("t_heavy", _i32), ("persistent", _i32),
-                ("hot_cache", _i32), ("seg_strategy", _i32), ("delta", _i32)]
+                ("hot_cache", _i32), ("seg_strategy", _i32), ("delta", _i32),
+                ("dst_list", _i32)]
 
 
 class gi_trace(ctypes.Structure):

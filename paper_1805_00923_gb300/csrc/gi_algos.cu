@@ -22,7 +22,9 @@ __global__ void k_iota2(int32_t *a, int32_t *b, int64_t n) {
     a[i] = b[i] = (int32_t)i;
 }
 
-__global__ void k_bfs_init(int32_t *depth, int32_t *parent, int64_t n, int32_t src) {
+__global__ void k_bfs_init(int32_t *depth, int32_t *parent, int64_t n, int32_t src, int32_t *unv_st = nullptr) {
+  // the compacted unvisited walk starts from the live list (BfsUnv)
+  if (unv_st && blockIdx.x == 0 && threadIdx.x < 4) unv_st[threadIdx.x] = threadIdx.x == 0 ? -1 : 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     depth[i] = i == src ? 0 : -1;
     if (parent) parent[i] = i == src ? src : INT32_MAX;
@@ -353,6 +355,7 @@ struct GraphLoop {
   int32_t *depth = nullptr;
   int32_t *parent = nullptr;  // canonical parents, INT32_MAX until found
   int32_t *gm = nullptr;
+  BfsUnv unv;  // compacted unvisited walk of the pull levels (st == nullptr: off)
   gi_vset a, b;
 };
 
@@ -401,7 +404,7 @@ static int graph_level(gi_graph *g, const gi_schedule &sc, GraphLoop *L, gi_vset
     k_pull_bfs<<<grid_for(g, g->n, 256), 256, 0, cs>>>(g->in.ptr, g->in.idx, g->n,
                                                       FSet(static_cast<const uint32_t *>(F->bitmap)), nullptr,
                                                       L->depth, L->parent, 0, tw, N->bitmap, N->queue, N->count,
-                                                      L->gm);
+                                                      L->gm, nullptr, 0, L->unv);
     GI_LAUNCH_CHECK();
   }
   N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
@@ -410,6 +413,7 @@ static int graph_level(gi_graph *g, const gi_schedule &sc, GraphLoop *L, gi_vset
 
 static int graph_loop_build(gi_graph *g, const gi_schedule &sc, GraphLoop *L, cudaStream_t s) {
   GI_TRY(heavy_get(g, s));
+  if (sc.dst_list && g->has_csc) GI_TRY(bfs_unv_get(g, s, &L->unv));
   GI_TRY(dev_alloc_n(&L->depth, g->n, s));
   GI_TRY(dev_alloc_n(&L->parent, g->n, s));
   GI_TRY(dev_alloc_n(&L->gm, kGmWords, s));
@@ -468,7 +472,7 @@ static int run_graph_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *pare
       return st;
     }
   }
-  k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(L->depth, L->parent, g->n, src);
+  k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(L->depth, L->parent, g->n, src, L->unv.st);
   k_gm_init<<<1, 32, 0, s>>>(L->gm, (int32_t)(g->n + 1 < INT32_MAX ? g->n + 1 : INT32_MAX));
   GI_TRY(launch_status(2));
   GI_TRY(front_init(g, &L->a, src, s));
@@ -516,12 +520,15 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
     return run_persistent(g, GI_ALGO_BFS, src, depth, sc, trace, s, parent);
   }
   GI_TRY(ensure_tiles(g, sc, s));
+  BfsUnv U;
+  if (sc.dst_list && g->has_csc) GI_TRY(bfs_unv_get(g, s, &U));
   VsetPair P;
   int st = pair_alloc(g, P, s);
   if (st == GI_OK) {
-    k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(depth, parent, g->n, src);
+    k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(depth, parent, g->n, src, U.st);
     st = launch_status(1);
   }
+  g->bfs_unv_query = U;  // this query's pull levels walk the compacted list
   if (st == GI_OK) st = front_init(g, P.F, src, s);
   if (st == GI_OK) st = ctrl_init(g, g->n, g->m, s);
   if (st == GI_OK)
@@ -535,6 +542,7 @@ extern "C" int gi_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent,
       gi_bfs_args a{depth, parent, it + 1};
       return apply_dispatch(g, P.F, nullptr, dir, sc, GI_K_BFS, &a, P.N, GI_NO_DEDUP, s);
     });
+  g->bfs_unv_query = BfsUnv{};
   if (st == GI_OK && parent) {
     k_parent_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n);
     st = launch_status(1);
@@ -1825,10 +1833,15 @@ extern "C" int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, 
   if (st == GI_OK && !bfs) st = dev_alloc_n(&snap, g->n, s);
   if (st == GI_OK && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess))
     st = cuda_fail(cudaGetLastError(), "event create", __FILE__, __LINE__);
+  BfsUnv U;
+  if (st == GI_OK && bfs && sc.dst_list) st = bfs_unv_get(g, s, &U);
   if (st == GI_OK) {
     if (bfs) {
-      k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(x, nullptr, g->n, src);
+      // every level's pull runs last, from the state the pushes were timed
+      // on, so the compacted list advances exactly as in gi_bfs
+      k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(x, nullptr, g->n, src, U.st);
       st = launch_status(1);
+      g->bfs_unv_query = U;
     } else {
       k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(x, g->n, INT32_MAX);
       k_fill_i32<<<grid_for(g, g->n, 256), 256, 0, s>>>(snap, g->n, INT32_MAX);
@@ -1886,6 +1899,7 @@ extern "C" int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, 
     ++lv;
   }
   *levels = lv;
+  g->bfs_unv_query = BfsUnv{};
   if (ev[0]) cudaEventDestroy(ev[0]);
   if (ev[1]) cudaEventDestroy(ev[1]);
   dev_free(x, s);

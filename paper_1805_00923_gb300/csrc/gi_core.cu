@@ -185,6 +185,59 @@ int bfs_defer_get(gi_graph *g, cudaStream_t s) {
   return GI_OK;
 }
 
+__global__ void k_has_in_arcs(const int32_t *__restrict__ ptr, int64_t n, int32_t *flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = __ldg(ptr + v + 1) > __ldg(ptr + v) ? 1 : 0;
+}
+
+__global__ void k_live_scatter(const int32_t *__restrict__ flag, const int32_t *__restrict__ pos, int64_t n,
+                               int32_t *live) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    if (flag[v]) live[pos[v]] = (int32_t)v;
+}
+
+int bfs_unv_get(gi_graph *g, cudaStream_t s, BfsUnv *out) {
+  if (!g->bfs_unv) {
+    // vertices with in-arcs, ascending: flags, exclusive scan, scatter
+    int32_t *flag = nullptr, *pos = nullptr;
+    GI_TRY(ws_scratch(g, &flag, &pos, s));
+    k_has_in_arcs<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->in.ptr, g->n, flag);
+    GI_LAUNCH_CHECK();
+    GI_TRY(scan_exclusive(g, flag, pos, g->n, s));
+    int32_t total = 0;
+    GI_CUDA(cudaMemcpyAsync(&total, pos + g->n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GI_CUDA(cudaStreamSynchronize(s));
+    // st (4 words, padded to 16 bytes), live, list0, list1
+    const size_t len = (size_t)(total > 0 ? total : 1);
+    void *mem = nullptr;
+    GI_TRY(dev_alloc(&mem, 16 + 3 * sizeof(int32_t) * len, s));
+    int32_t *live = reinterpret_cast<int32_t *>(static_cast<unsigned char *>(mem) + 16);
+    k_live_scatter<<<grid_for(g, g->n, 256), 256, 0, s>>>(flag, pos, g->n, live);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      dev_free(mem, s);
+      return cuda_fail(e, "live list", __FILE__, __LINE__);
+    }
+    g->bfs_unv = mem;
+    g->bfs_unv_n = total;
+  }
+  const size_t len = (size_t)(g->bfs_unv_n > 0 ? g->bfs_unv_n : 1);
+  unsigned char *b = static_cast<unsigned char *>(g->bfs_unv);
+  out->st = reinterpret_cast<int32_t *>(b);
+  out->live = reinterpret_cast<const int32_t *>(b + 16);
+  out->list0 = reinterpret_cast<int32_t *>(b + 16) + len;
+  out->list1 = out->list0 + len;
+  out->nlive = g->bfs_unv_n;
+  return GI_OK;
+}
+
+void bfs_unv_free(gi_graph *g, cudaStream_t s) {
+  dev_free(g->bfs_unv, s);
+  g->bfs_unv = nullptr;
+  g->bfs_unv_n = 0;
+  g->bfs_unv_query = BfsUnv{};
+}
+
 int heavy_get(gi_graph *g, cudaStream_t s) {
   if (g->heavy_mem) return GI_OK;
   // the expansion kernel returns counter and ticket to zero after each use
@@ -604,6 +657,7 @@ static void graph_release(gi_graph *g, cudaStream_t s) {
   dev_free(g->ctrl, s);
   dev_free(g->heavy_mem, s);
   dev_free(g->bfs_defer, s);
+  bfs_unv_free(g, s);
   ws_free(g, s);
   pinned_ctrl_put(g->ctrl_host);
   delete g;
@@ -698,6 +752,7 @@ extern "C" int gi_load_csc(gi_graph *g, const int32_t *in_offsets, const int32_t
   cudaStream_t s = (cudaStream_t)stream;
   if (g->symmetric) return GI_OK;  // the CSR already is the in-edge view
   graph_loop_free(g);              // its kernels hold the in-edge arrays
+  bfs_unv_free(g, s);              // built from the in-edges
   if (g->has_csc) {
     free_tile_cache(g, s);
     dev_free(g->in.ptr, s);
@@ -1878,4 +1933,5 @@ extern "C" void gi_schedule_default(gi_schedule *s) {
   s->hot_cache = 0;
   s->seg_strategy = GI_SEG_FVC;
   s->delta = 0;
+  s->dst_list = 1;
 }

@@ -136,6 +136,21 @@ struct HotSet {
 
 struct Workspace;  // per-graph scratch (frontiers, buffers); defined in gi_core.cu
 
+// The unvisited destinations of the early-exit BFS pull as a compacted list
+// (the destination filter of Sec. 2 kept sparse).  `live` lists, ascending,
+// the vertices with in-arcs (built once per graph: the others can never be
+// reached); each pull level walks its input list and appends the vertices it
+// leaves unvisited to the other list, so later pull levels touch only rows
+// that can still be reached.  st[0] = the input of the next pull (-1: live;
+// 0 / 1: list0 / list1), st[1] / st[2] = the counts of list0 / list1, st[3] =
+// the walking launch's ticket (its last block flips st[0] and empties the
+// next output).  A query starts at {-1, 0, 0, 0} (k_bfs_init).
+struct BfsUnv {
+  const int32_t *live = nullptr;
+  int32_t *list0 = nullptr, *list1 = nullptr;
+  int32_t *st = nullptr;  // nullptr: walk every vertex
+  int32_t nlive = 0;
+};
 }  // namespace gi
 
 struct gi_graph {
@@ -162,6 +177,11 @@ struct gi_graph {
   int64_t *ctrl = nullptr;       // device control block (kCtrlWords)
   void *heavy_mem = nullptr;     // HeavyList storage (counter, ticket, 2n entries), allocated on first use
   void *bfs_defer = nullptr;     // BfsDefer storage of the early-exit BFS pull, allocated on first use
+  void *bfs_unv = nullptr;       // BfsUnv storage (live list, two lists, state), built on first use
+  int32_t bfs_unv_n = 0;         // its live-list length
+  // BfsUnv state of the running gi_bfs query (st == nullptr outside one):
+  // its DensePull levels walk the compacted unvisited list
+  gi::BfsUnv bfs_unv_query;
   int64_t *ctrl_host = nullptr;  // pinned mirror
   gi::Workspace *ws = nullptr;
   int device = 0;
@@ -244,6 +264,9 @@ __host__ __device__ inline BfsDefer bfs_defer_at(void *mem, int32_t cap) {
   return d;
 }
 int bfs_defer_get(gi_graph *g, cudaStream_t s);  // allocates g->bfs_defer on first use
+
+int bfs_unv_get(gi_graph *g, cudaStream_t s, BfsUnv *out);  // builds the lists on first use
+void bfs_unv_free(gi_graph *g, cudaStream_t s);
 
 // exclusive scan of n int32 counts into out[n+1] (out[n] = total); scratch owned by g's workspace
 int scan_exclusive(gi_graph *g, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);

@@ -104,7 +104,8 @@ int apply_dispatch(gi_graph *g, gi_vset *from, gi_vset *to, int32_t dir, const g
         }
         const int tok = timing_begin(kClassBfsPull, s);
         k_pull_bfs<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->in.ptr, g->in.idx, g->n, F, to_bm, a->depth, a->parent,
-                                                          a->level, tw, o.bm, o.q, o.qc, nullptr, defer, dcap);
+                                                          a->level, tw, o.bm, o.q, o.qc, nullptr, defer, dcap,
+                                                          to_bm == nullptr ? g->bfs_unv_query : BfsUnv{});
         if (defer)
           k_pull_bfs_deferred<<<g->num_sms * 8, 256, 0, s>>>(g->in.ptr, g->in.idx, F, defer, dcap, a->depth,
                                                               a->parent, a->level, o.bm, o.q, o.qc);
@@ -214,6 +215,7 @@ int check_schedule(const gi_schedule *sc) {
   GI_ARG(sc->persistent >= 0 && sc->persistent <= 2, "persistent must be 0, 1 or 2");
   GI_ARG(sc->delta >= 0, "delta must be >= 0");
   GI_ARG(sc->block == 128 || sc->block == 256 || sc->block == 512, "block must be 128, 256 or 512");
+  GI_ARG(sc->dst_list == 0 || sc->dst_list == 1, "dst_list must be 0 or 1");
   return GI_OK;
 }
 

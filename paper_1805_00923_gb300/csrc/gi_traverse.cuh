@@ -723,59 +723,81 @@ __global__ void k_pull_fixup(Op op, const int4 *__restrict__ splits, int32_t num
 }
 
 // ------------------------------------------------------------- BFS pull ------
-// DensePull for BFS with early exit (Sec. 2): a warp owns 32 consecutive
-// destinations (one output bitmap word).  Unvisited destinations scan their
-// in-neighbours in ascending order and stop at the first frontier member,
-// which is the smallest-id parent.  Rows with at least t_warp arcs are
-// scanned by the whole warp 32 arcs at a time (ballot picks the first hit).
+// DensePull for BFS with early exit (Sec. 2): a warp owns 32 destinations.
+// Unvisited destinations scan their in-neighbours in ascending order and
+// stop at the first frontier member, which is the smallest-id parent.  Rows
+// with at least t_warp arcs are scanned by the whole warp 32 arcs at a time
+// (ballot picks the first hit).  The destinations are either all vertices
+// (32 consecutive ones per warp: one output bitmap word) or, with U.st set,
+// the entries of the compacted unvisited list (BfsUnv): then the vertices
+// left unvisited are appended to the other list, and the found ones set
+// their output bits by one atomicOr per distinct word of the warp.
 static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                                                   int64_t n, FSet F,
                                                   const uint32_t *__restrict__ to, int32_t *depth, int32_t *parent,
                                                   int32_t level, int32_t t_warp, uint32_t *out_bm, int32_t *out_q,
                                                   int32_t *out_qc, const int32_t *gm = nullptr,
-                                                  void *defer = nullptr, int32_t defer_cap = 0) {
+                                                  void *defer = nullptr, int32_t defer_cap = 0,
+                                                  BfsUnv U = BfsUnv{}) {
   if (gm) {  // graph-driven level: run only when this level pulls
     if (gm[kGmPull] == 0) return;
     level = gm[kGmLevel] + 1;
   }
   // found vertices are staged per warp in shared memory and appended to the
   // queue kQBuf - 32 or more at a time: one atomic per flush, not one per
-  // 32 vertices, and no wait on its return in every iteration
+  // 32 vertices, and no wait on its return in every iteration; so are the
+  // vertices left for the next pull level (listed walk)
   constexpr int kQBuf = 128;
   __shared__ int32_t s_q[8][kQBuf];  // blockDim.x == 256
+  __shared__ int32_t s_u[8][kQBuf];
   const int lane = threadIdx.x & 31;
   int32_t *wq = s_q[threadIdx.x >> 5];
-  int32_t qn = 0;  // staged entries (warp-uniform)
-  const auto flush = [&]() {
+  int32_t *wu = s_u[threadIdx.x >> 5];
+  int32_t qn = 0, un = 0;  // staged entries (warp-uniform)
+  const auto flush = [&](int32_t *buf, int32_t cnt, int32_t *dst, int32_t *dst_count) {
     __syncwarp();
     int32_t base = 0;
-    if (lane == 0) base = atomicAdd(out_qc, qn);
+    if (lane == 0) base = atomicAdd(dst_count, cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
-    for (int32_t j = lane; j < qn; j += 32) out_q[base + j] = wq[j];
+    for (int32_t j = lane; j < cnt; j += 32) dst[base + j] = buf[j];
     __syncwarp();
-    qn = 0;
   };
-  const int64_t nw = (n + 31) >> 5;
+  // the walk: every vertex, or the input list of the compacted walk
+  const bool listed = U.st != nullptr;
+  int32_t cur = -1;
+  const int32_t *in_list = nullptr;
+  int32_t *next_list = nullptr, *next_count = nullptr;
+  int64_t items = n;
+  if (listed) {
+    cur = U.st[0];
+    in_list = cur < 0 ? U.live : (cur == 0 ? U.list0 : U.list1);
+    items = cur < 0 ? U.nlive : U.st[1 + cur];
+    next_list = cur == 0 ? U.list1 : U.list0;
+    next_count = U.st + (cur == 0 ? 2 : 1);
+  }
+  const int64_t nw = (items + 31) >> 5;
   const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // the depth word and row bounds of the warp's next 32 vertices are loaded
-  // while the current ones are probed (one round trip per iteration fewer)
-  int32_t ndv = 0, na = 0, nb = 0;
+  // the vertex, depth word and row bounds of the warp's next 32 entries are
+  // loaded while the current ones are probed (one round trip per iteration fewer)
+  int32_t nv = -1, ndv = 0, na = 0, nb = 0;
   const auto fetch = [&](int64_t ww) {
-    const int64_t vv = ww * 32 + lane;
-    if (ww < nw && vv < n) {
-      ndv = depth[vv];
-      na = __ldg(ptr + vv);
-      nb = __ldg(ptr + vv + 1);
+    const int64_t ii = ww * 32 + lane;
+    nv = -1;
+    if (ww < nw && ii < items) {
+      nv = listed ? in_list[ii] : (int32_t)ii;
+      ndv = depth[nv];
+      na = __ldg(ptr + nv);
+      nb = __ldg(ptr + nv + 1);
     }
   };
   int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   fetch(w);
   for (; w < nw; w += wstride) {
-    const int64_t v = w * 32 + lane;
+    const int32_t v = nv;
     const int32_t dv = ndv;
     int32_t a = na, b = nb;
     fetch(w + wstride);
-    const bool active = v < n && dv == -1 && in_set(to, (int32_t)v);
+    const bool active = v >= 0 && dv == -1 && in_set(to, v);
     if (!active) b = a;
     int32_t found = -1;
     // every lane first probes the first 4 arcs of its own row: 4 independent
@@ -821,7 +843,7 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
         const unsigned long long old = atomicAdd(D.ctr, (1ull << 32) | nch);
         const int32_t j = (int32_t)(old >> 32);
         if (j < defer_cap) {  // always: each queued row holds more than m / defer_cap arcs
-          D.row[j] = (int32_t)v;
+          D.row[j] = v;
           D.from[j] = stop;
           D.base[j] = (int32_t)(old & 0xffffffffull);
           D.best[j] = INT32_MAX;
@@ -834,16 +856,61 @@ static __global__ void __launch_bounds__(256) k_pull_bfs(const int32_t *__restri
       depth[v] = level;
       if (parent) parent[v] = found;
     }
+    if (listed) {
+      // still unvisited (not reached, filtered out by `to`, or deferred):
+      // walked again at the next pull level
+      const bool keep = v >= 0 && dv == -1 && !got;
+      const unsigned kw = __ballot_sync(0xffffffffu, keep);
+      if (kw) {
+        if (keep) wu[un + __popc(kw & ((1u << lane) - 1u))] = v;
+        un += __popc(kw);
+        if (un > kQBuf - 32) {
+          flush(wu, un, next_list, next_count);
+          un = 0;
+        }
+      }
+    }
     const unsigned word = __ballot_sync(0xffffffffu, got);
-    if (out_bm == nullptr) continue;
-    if (lane == 0 && word) out_bm[w] |= word;
-    if (word) {
-      if (got) wq[qn + __popc(word & ((1u << lane) - 1u))] = (int32_t)v;
-      qn += __popc(word);
-      if (qn > kQBuf - 32) flush();
+    if (out_bm == nullptr || word == 0) continue;
+    if (!listed) {
+      if (lane == 0) out_bm[w] |= word;
+    } else {
+      // one atomicOr per distinct bitmap word among the found lanes
+      const int32_t myw = v >> 5;
+      unsigned todo = word;
+      while (todo) {
+        const int l = __ffs(todo) - 1;
+        const int32_t wl = __shfl_sync(0xffffffffu, myw, l);
+        const bool mine = got && myw == wl;
+        const unsigned bits = __reduce_or_sync(0xffffffffu, mine ? (1u << (v & 31)) : 0u);
+        todo &= ~__ballot_sync(0xffffffffu, mine);
+        if (lane == l) atomicOr(out_bm + wl, bits);
+      }
+    }
+    if (got) wq[qn + __popc(word & ((1u << lane) - 1u))] = v;
+    qn += __popc(word);
+    if (qn > kQBuf - 32) {
+      flush(wq, qn, out_q, out_qc);
+      qn = 0;
     }
   }
-  if (out_bm != nullptr && qn > 0) flush();
+  if (out_bm != nullptr && qn > 0) flush(wq, qn, out_q, out_qc);
+  if (!listed) return;
+  if (un > 0) flush(wu, un, next_list, next_count);
+  // the last block to finish makes the list just written the next input and
+  // empties the one just read (every block has read the state before its ticket)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(U.st + 3, 1) == (int32_t)gridDim.x - 1) {
+      __threadfence();
+      const int32_t nxt = cur == 0 ? 1 : 0;
+      U.st[0] = nxt;
+      U.st[1 + (nxt ^ 1)] = 0;
+      U.st[3] = 0;
+      __threadfence();
+    }
+  }
 }
 
 // The deferred rows of k_pull_bfs: block task c is chunk c of the queue (the

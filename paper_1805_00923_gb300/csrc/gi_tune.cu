@@ -151,6 +151,8 @@ extern "C" int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_sche
     knobs.push_back(knob(&gi_schedule::dense_rep, {(int32_t)GI_REP_BITMAP, (int32_t)GI_REP_BOOL}));
   // SSSP: Bellman-Ford rounds (0) or delta-stepping with these bucket widths
   if (algo == GI_ALGO_SSSP) knobs.push_back(knob(&gi_schedule::delta, {0, 16, 32, 48, 64, 96, 128, 256}));
+  // BFS pull levels over every vertex or over the compacted unvisited list
+  if (algo == GI_ALGO_BFS) knobs.push_back(knob(&gi_schedule::dst_list, {0, 1}));
   std::mt19937_64 rng(seed);
   const int reps = 2;
   gi_schedule cur = *start, top = *start;

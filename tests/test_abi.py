@@ -83,3 +83,35 @@ def test_schedule_defaults(lib):
 def test_selector_param_count_matches_oracle(lib):
     import oracle
     assert lib.gi_selector_num_params() == oracle.mlp_num_params()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets: a C program built against include/graphit_gb.h prints them."""
+    from paper_1805_00923_gb300 import _lib as L
+    structs = ["gi_schedule", "gi_trace", "gi_batch_opts", "gi_bfs_args", "gi_sssp_args", "gi_cc_args",
+               "gi_sum_args", "gi_probe_args"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "graphit_gb.h"', "int main(void) {"]
+    for name in structs:
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in getattr(L, name)._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    r = subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            a, b, c = ln.split()
+            got[(a, b)] = int(c)
+    for name in structs:
+        cls = getattr(L, name)
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)

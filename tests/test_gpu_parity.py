@@ -721,6 +721,107 @@ def test_bfs_pull_deferred_rows_directed_graph(gi):
             assert np.array_equal(_np(p), want_p), (direction, s)
 
 
+def _two_rmat_blobs_on_a_path():
+    """Two R-MAT 12 components (each with its isolated vertices) joined by a
+    30-vertex path, so that a BFS from the first pulls, pushes along the path
+    and pulls again in the second: the compacted unvisited list is walked,
+    goes stale over push levels and is walked again."""
+    a = rmat(12)
+    src = np.repeat(np.arange(a.n, dtype=np.int64), np.diff(a.row_ptr))
+    e = np.stack([src, a.col.astype(np.int64)], 1)
+    e = e[e[:, 0] < e[:, 1]]
+    off = a.n + 30
+    path = [(int(a.col[0]) if a.m else 0, a.n)] + [(a.n + i, a.n + i + 1) for i in range(29)]
+    hub_b = off + int(np.argmax(np.diff(a.row_ptr)))
+    path.append((a.n + 29, hub_b))
+    pairs = np.concatenate([e, e + off, np.array(path, np.int64)])
+    return gg.from_edge_list(off + a.n, map(tuple, pairs.tolist()))
+
+
+@pytest.mark.parametrize("persistent", [0, 2])
+@pytest.mark.parametrize("direction", ["dense_pull", "hybrid_pull", "learned"])
+def test_bfs_unvisited_list(gi, direction, persistent):
+    """DensePull levels over the compacted list of unvisited vertices with
+    in-arcs (dst_list 1) and over every vertex (dst_list 0): identical depths
+    and parents, equal to the oracle's, on R-MAT (isolated vertices), on two
+    components joined by a path (pull, push, pull again) and on a grid."""
+    graphs = [rmat(16), _two_rmat_blobs_on_a_path(), grid(64)]
+    for hg in graphs:
+        g = _load(gi, hg)
+        for src in [0, *gg.pick_sources(hg, 2, seed=4)]:
+            want_d, want_p, _ = oracle.bfs(hg, int(src))
+            for dl in (1, 0):
+                d, p = gi.bfs(g, int(src), sched=gi.schedule(direction, persistent=persistent, dst_list=dl))
+                assert np.array_equal(_np(d), want_d), (hg.name, src, dl)
+                assert np.array_equal(_np(p), want_p), (hg.name, src, dl)
+        g.free()
+
+
+def test_bfs_unvisited_list_survives_push_levels(gi):
+    """The path graph's hybrid run really pulls, pushes, then pulls again."""
+    hg = _two_rmat_blobs_on_a_path()
+    g = _load(gi, hg)
+    src = int(gg.pick_sources(hg, 1, seed=4)[0])
+    tr = gi.Trace(256)
+    gi.bfs(g, src, sched=gi.schedule("hybrid_pull"), trace=tr)
+    dirs = tr.as_dict()["direction"].tolist()
+    pulls = [i for i, x in enumerate(dirs) if x == gi.GI_DIR_DENSE_PULL]
+    assert pulls and any(dirs[i] != gi.GI_DIR_DENSE_PULL for i in range(pulls[0], pulls[-1])), dirs
+
+
+@pytest.mark.parametrize("name", ADVERSARIAL)
+def test_bfs_unvisited_list_adversarial(gi, name):
+    """No arcs at all (an empty live list), one vertex, a star, a path."""
+    hg = adversarial(name)
+    g = _load(gi, hg)
+    for src in sorted({0, hg.n // 2, hg.n - 1}):
+        want_d, want_p, _ = oracle.bfs(hg, src)
+        for direction in ("dense_pull", "hybrid_pull"):
+            for persistent in (0, 2):
+                d, p = gi.bfs(g, src, sched=gi.schedule(direction, persistent=persistent))
+                assert np.array_equal(_np(d), want_d), (name, src, direction, persistent)
+                assert np.array_equal(_np(p), want_p), (name, src, direction, persistent)
+
+
+def test_bfs_unvisited_list_directed_and_profile(gi):
+    """A directed graph: the list holds the vertices with in-arcs (some have
+    none, some have no out-arcs); and gi_selector_profile walks it too, with
+    the same per-level features either way."""
+    rng = np.random.default_rng(21)
+    n = 6000
+    e = rng.integers(0, n // 2, (30_000, 2))
+    e[:, 1] += rng.integers(0, 2, e.shape[0]) * (n // 2)  # half the ids have no out-arcs, some no in-arcs
+    hg = gg.from_edge_list(n, map(tuple, e), symmetrize=False)
+    in_ptr, in_col, _ = gg.transpose(hg)
+    g = gi.Graph(hg.row_ptr, hg.col, symmetric=False, in_edges=(in_ptr, in_col, None))
+    for s_ in (0, 7, 2999):
+        want_d, want_p, _ = oracle.bfs(hg, s_, in_edges=(in_ptr, in_col))
+        for direction in ("dense_pull", "hybrid_pull"):
+            for dl in (0, 1):
+                d, p = gi.bfs(g, s_, sched=gi.schedule(direction, dst_list=dl))
+                assert np.array_equal(_np(d), want_d), (s_, direction, dl)
+                assert np.array_equal(_np(p), want_p), (s_, direction, dl)
+    from paper_1805_00923_gb300 import selector as sel
+    hs = rmat(14)
+    gs = _load(gi, hs)
+    f1, t1 = sel.profile(gs, gi.GI_K_BFS, 3, sched=gi.schedule("hybrid_pull", dst_list=1))
+    f0, t0 = sel.profile(gs, gi.GI_K_BFS, 3, sched=gi.schedule("hybrid_pull", dst_list=0))
+    assert f1.shape == f0.shape and np.array_equal(f1, f0)
+    assert (t1[:, 2] > 0).all() and (t0[:, 2] > 0).all()
+    # the run after the profile starts from a fresh list
+    want_d, want_p, _ = oracle.bfs(hs, 3)
+    d, p = gi.bfs(gs, 3, sched=gi.schedule("dense_pull"))
+    assert np.array_equal(_np(d), want_d) and np.array_equal(_np(p), want_p)
+
+
+def test_schedule_rejects_unknown_fields_and_bad_dst_list(gi):
+    with pytest.raises(TypeError):
+        gi.schedule("hybrid_pull", no_such_field=1)
+    g = _load(gi, rmat(10))
+    with pytest.raises(gi.GIError):
+        gi.bfs(g, 0, sched=gi.schedule("hybrid_pull", dst_list=2))
+
+
 @pytest.mark.parametrize("hub_in_to", [True, False])
 def test_edgeset_apply_bfs_deferred_row_with_to_set(gi, hub_in_to):
     """The operator form of the early-exit pull: a hub whose frontier sources
