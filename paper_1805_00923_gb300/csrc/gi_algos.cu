@@ -1096,21 +1096,30 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
 // ================================================== graph-driven SSSP ==
 // gi_sssp with gi_schedule.persistent = 2: the delta-stepping rounds run as a
 // CUDA graph, a WHILE node whose body holds two rounds (the pending sets a and
-// b swap roles).  Each round: the split kernel (changed vertices -> R, S, far
-// pile), the decision kernel (statistics of R or S, direction, the round's
-// mode), the next pending set cleared, then a SWITCH node that runs only the
-// round's relaxation (light or heavy arcs, push or pull) or the far pile's
-// next bucket, and the epilogue kernel.  No host round trip per round.
+// b swap roles).  Each round is one kernel that splits the changed vertices
+// into R, S and the far pile, empties their set and decides the round
+// (statistics of R or S, direction, mode), then a SWITCH node that runs only
+// the round's relaxation (light or heavy arcs, push or pull) or the far
+// pile's next bucket.  No host round trip per round.
+// The snapshots (snap for R, snap_h for S) are not reset after a round: an
+// entry, once set, equals its vertex's distance at the last split (a vertex
+// whose distance drops is pending at the next split, is near and gets a new
+// entry), and its arcs of that class were relaxed from that value in the
+// round that set it (light) or in its bucket's heavy round (heavy).  A pull
+// that reads such an entry again improves nothing, so every round changes
+// exactly the vertices it changes with the entries reset, push or pull.
 // Bellman-Ford (delta = 0) is the same loop with one bucket holding every
 // arc (delta beyond every weight), which gives its synchronous rounds exactly.
 namespace gi {
 
 // next bucket: live pile entries below hi -> the pending set N (cleared
-// before), the rest -> the other pile buffer with a fresh minimum
+// before), the rest -> the pile buffer in use from now on (kDgCur, which the
+// split kernel has just switched; its count was zeroed there) with a fresh
+// minimum
 __global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uint8_t *pile_in, int32_t *pile0,
                                  int32_t *pile1, int32_t *Nq, int32_t *Nc) {
   const int lane = threadIdx.x & 31;
-  const int32_t cur = dw[kDgCur], hi = dw[kDgHi];
+  const int32_t cur = dw[kDgCur] ^ 1, hi = dw[kDgHi];  // cur: the buffer being thinned
   const int32_t *pile = cur ? pile1 : pile0;
   int32_t *pile2 = cur ? pile0 : pile1;
   const int32_t c = dw[kDgPile0 + cur];
@@ -1133,43 +1142,6 @@ __global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uin
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
   if (lane == 0 && fmin < INT32_MAX) atomicMin(dw + kDgPmin, fmin);
-}
-
-// round epilogue: the sources' snap entries back to INT32_MAX (after a heavy
-// round: snap_h, and the next bucket number), and this round's pending set F,
-// consumed by the split, emptied through its queue (it is the next round's
-// output set); the last block resets the round counters
-__global__ void k_dsg_post(const int32_t *__restrict__ Rq, const int32_t *__restrict__ Sq, int32_t *snap,
-                           int32_t *snap_h, int32_t *dw, const int32_t *__restrict__ Fq, int32_t *Fc, uint32_t *Fbm,
-                           int64_t *ctrl) {
-  __shared__ bool last;
-  const int32_t mode = dw[kDgMode];
-  const bool light = mode == kDgLightPush || mode == kDgLightPull;
-  const bool heavy = mode == kDgHeavyPush || mode == kDgHeavyPull;
-  const int32_t c = light ? dw[kDgRc] : (heavy ? dw[kDgSc] : 0);
-  const int32_t *q = light ? Rq : Sq;
-  int32_t *sn = light ? snap : snap_h;
-  const int32_t stride = gridDim.x * blockDim.x;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += stride) sn[q[i]] = INT32_MAX;
-  const int32_t fc = *Fc;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < fc; i += stride) Fbm[Fq[i] >> 5] = 0u;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(dw + kDgTicket, 1) == (int32_t)gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last || threadIdx.x != 0) return;
-  __threadfence();
-  dw[kDgTicket] = 0;
-  dw[kDgRc] = 0;
-  *Fc = 0;
-  if (heavy) {
-    dw[kDgSc] = 0;
-    dw[kDgEpoch] += 1;
-    ctrl[kSHeavyMf] = 0;
-  }
-  if (mode == kDgAdvance) dw[kDgCur] ^= 1;
 }
 
 __global__ void k_dsg_init(int32_t *dw, int32_t delta, int32_t cap) {
@@ -1221,8 +1193,8 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
   const bool pull_ok = g->symmetric;
   cudaGraphConditionalHandle hs;
   GI_CUDA(cudaGraphConditionalHandleCreate(&hs, body, kDgDone, cudaGraphCondAssignDefault));
-  DsgBuffers B{F->queue, F->count, L->x, L->dw, L->Rq, L->snap, L->snap_h, L->Sq, L->pile[0], L->pile[1], L->s_mark,
-               L->pile_in, D->deg_l, D->deg_h};
+  DsgBuffers B{F->queue, F->count, F->bitmap, L->x, L->dw, L->Rq, L->snap, L->snap_h, L->Sq, L->pile[0], L->pile[1],
+               L->s_mark, L->pile_in, D->deg_l, D->deg_h};
   DecideParams p = decide_params(sc, 0, false);
   GI_TRY(dsg_step_launch(g, B, p, sc.delta, pull_ok, (unsigned long long)hs, (unsigned long long)hw, cs));
   // the switch node after what was captured so far
@@ -1271,10 +1243,8 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
     GI_TRY(st);
     if (e != cudaSuccess) return cuda_fail(e, "branch capture", __FILE__, __LINE__);
   }
+  // the next round's kernels follow the switch node
   GI_CUDA(cudaStreamBeginCaptureToGraph(cs, body, &sw, nullptr, 1, cudaStreamCaptureModeRelaxed));
-  k_dsg_post<<<g->num_sms * 2, 256, 0, cs>>>(L->Rq, L->Sq, L->snap, L->snap_h, L->dw, F->queue, F->count, F->bitmap,
-                                             g->ctrl);
-  GI_TRY(launch_status(1));
   N->reps = GI_REP_SPARSE | GI_REP_BITMAP;
   return GI_OK;
 }

@@ -134,6 +134,9 @@ struct Barrier {
 __device__ bool batch_decide_pull(const BatchGraph &G, int64_t nf, int64_t mf, int64_t nu, int64_t mu, int32_t level,
                                   int32_t was_pull, int64_t nf_prev, int mode, float alpha, float beta, float *sh) {
   if (mode == 2) {
+    // as the single-query selector: frontiers with |F| + m_f below m / 200
+    // push without an evaluation (uniform across the CTAs: same inputs)
+    if ((nf + mf) * 200 < G.m) return false;
     float *x = sh, *h1 = sh + 16, *h2 = h1 + 64, *y = h2 + 64;
     const float *W1 = d_bsel_params, *b1 = W1 + 64 * 16, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
                 *b3 = W3 + 3 * 64;

@@ -1574,6 +1574,14 @@ static bool g_sel_loaded = false;
 
 bool selector_loaded() { return g_sel_loaded; }
 
+// The learned selector is consulted only where the two directions can cost
+// alike: a frontier with |F| + m_f below m / kSelGate is pushed without an
+// evaluation (a pull walks every row or tile, a push of so few arcs costs a
+// small fraction of that), which also keeps the network's latency off the
+// many small levels and rounds.
+constexpr int64_t kSelGate = 200;
+__device__ __forceinline__ bool selector_gated(int64_t nf, int64_t mf, int64_t m) { return (nf + mf) * kSelGate < m; }
+
 // MLP forward by one block (>= 64 threads); returns argmin of predicted log-time
 __device__ int32_t selector_forward(const float *x_raw, float *sh /* >= 16+64+64+3 floats */) {
   // Called by all 256 threads of one block.  Layers 1 and 2: four threads
@@ -1681,8 +1689,12 @@ __global__ void k_frontier_decide(const int32_t *__restrict__ q, const int32_t *
   if (p.mode == 0) {
     dir = p.forced;
   } else if (p.mode == 2 && use_selector) {
-    int32_t k = selector_forward(feat, sh);
-    dir = k == 0 ? GI_DIR_SPARSE_PUSH : (k == 1 ? GI_DIR_DENSE_PUSH : GI_DIR_DENSE_PULL);
+    if (selector_gated(nf, mf, m)) {
+      dir = GI_DIR_SPARSE_PUSH;
+    } else {
+      int32_t k = selector_forward(feat, sh);
+      dir = k == 0 ? GI_DIR_SPARSE_PUSH : (k == 1 ? GI_DIR_DENSE_PUSH : GI_DIR_DENSE_PULL);
+    }
   } else {
     bool dense;
     if (p.rule == GI_RULE_LIGRA || !p.track_unvisited) {
@@ -1751,6 +1763,7 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
     if (i < c) {
       v = B.P[i];
       d = B.x[v];
+      B.Pbm[v >> 5] = 0u;  // the whole word: every bit set in it belongs to P
     }
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
     bool snew = false, pnew = false;
@@ -1819,8 +1832,10 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
     if (p.mode == 0) {
       dir = p.forced;
     } else if (p.mode == 2 && use_selector) {
-      const int32_t k = selector_forward(feat, sh);
-      dir = k == 2 ? GI_DIR_DENSE_PULL : GI_DIR_SPARSE_PUSH;
+      if (!selector_gated(nf, mf, m)) {
+        const int32_t k = selector_forward(feat, sh);
+        dir = k == 2 ? GI_DIR_DENSE_PULL : GI_DIR_SPARSE_PUSH;
+      }
     } else {
       dir = (nf + mf) > m / 20 ? GI_DIR_DENSE_PULL : GI_DIR_SPARSE_PUSH;
     }
@@ -1828,20 +1843,37 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
   }
   if (threadIdx.x == 0) {
     int32_t mode;
+    // every block has read P's count and appended to R: both are spent (the
+    // light push reads R's length from kDgPushL)
+    *B.Pc = 0;
+    dw[kDgRc] = 0;
     if (relax) {
       const bool pull = dir == GI_DIR_DENSE_PULL;
-      mode = light ? (pull ? kDgLightPull : kDgLightPush) : (pull ? kDgHeavyPull : kDgHeavyPush);
+      // sources without arcs of the class relax nothing: the push branch with
+      // an empty queue, whatever the direction (no pull over the class's arcs)
+      const bool run_pull = pull && mf > 0;
+      mode = light ? (run_pull ? kDgLightPull : kDgLightPush) : (run_pull ? kDgHeavyPull : kDgHeavyPush);
       ctrl[kWasPull] = pull ? 1 : 0;
       ctrl[kNfPrev] = nf;
       // a heavy round without heavy arcs only empties S: not a relaxation round
       if (light || mf > 0) dw[kDgRound] = round + 1;
+      if (!light) {
+        // the heavy round closes the bucket: S starts again (the heavy push
+        // reads S's length from kDgPushH, and S's members are settled, so
+        // none of them is in a later P)
+        dw[kDgSc] = 0;
+        dw[kDgEpoch] = epoch + 1;
+        ctrl[kSHeavyMf] = 0;
+      }
     } else if (dw[kDgPile0 + cur] > 0) {
-      // the bucket and its heavy round are done: next bucket from the pile
+      // the bucket and its heavy round are done: next bucket from the pile,
+      // which the pile split reads from buffer cur and thins into cur ^ 1
       mode = kDgAdvance;
       const int64_t hi2 = ((int64_t)dw[kDgPmin] / delta + 1) * (int64_t)delta;
       dw[kDgHi] = (int32_t)(hi2 < INT32_MAX ? hi2 : INT32_MAX);
       dw[kDgPile0 + (cur ^ 1)] = 0;
       dw[kDgPmin] = INT32_MAX;
+      dw[kDgCur] = cur ^ 1;
     } else {
       mode = kDgDone;
     }
@@ -1850,7 +1882,7 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
       mode = kDgDone;
     }
     dw[kDgMode] = mode;
-    dw[kDgPushL] = mode == kDgLightPush ? rc : 0;
+    dw[kDgPushL] = (mode == kDgLightPush && mf > 0) ? rc : 0;
     dw[kDgPushH] = (mode == kDgHeavyPush && mf > 0) ? sc : 0;
     ctrl[kNf] = nf;
     ctrl[kMf] = mf;

@@ -341,7 +341,6 @@ enum DsgWord {
   kDgRound = 10,  // relaxation rounds run
   kDgCap = 11,    // round cap: reaching it stops the loop with kDgErr set
   kDgErr = 12,
-  kDgTicket = 13,
   kDgEpoch = 14,  // bucket number: S membership is s_mark[v] == epoch (no clearing between buckets)
   kDgWords = 16
 };
@@ -349,14 +348,17 @@ enum DsgMode { kDgLightPush = 0, kDgLightPull = 1, kDgHeavyPush = 2, kDgHeavyPul
 // One graph-driven delta-stepping round's set-up, one launch on s: splits the
 // vertices whose distance changed (P) into this round's light sources R
 // (snap), the bucket's settled list S (snap_h keeps their latest distance)
-// and the far pile, summing R's light and S's heavy arc counts as it goes;
-// its last block then picks the round: the light round over R if R is
-// non-empty, else the bucket's heavy round over S, else the next bucket
-// (advance) or the end, with its direction (rule or the MLP), and sets the
-// switch and loop conditions.
+// and the far pile, summing R's light and S's heavy arc counts as it goes,
+// and empties P's set (bitmap words through its queue, then its count) for
+// its next use as an output; its last block then picks the round: the light
+// round over R if R is non-empty, else the bucket's heavy round over S, else
+// the next bucket (advance) or the end, with its direction (rule or the MLP),
+// resets the counters the round has consumed and sets the switch and loop
+// conditions.
 struct DsgBuffers {
   const int32_t *P;
-  const int32_t *Pc;
+  int32_t *Pc;
+  uint32_t *Pbm;  // P's bitmap
   const int32_t *x;
   int32_t *dw, *Rq, *snap, *snap_h, *Sq, *pile0, *pile1;
   int32_t *s_mark;   // bucket number in which v last joined S

@@ -95,13 +95,29 @@ def train(X: np.ndarray, T: np.ndarray, M: np.ndarray | None = None, steps: int 
     return p.cpu().numpy(), mean, inv_std, losses
 
 
+# |F| + m_f below m / SELECTOR_GATE: the library pushes without consulting
+# the network (the same constant as the decision kernels)
+SELECTOR_GATE = 200
+
+
+def gated(X: np.ndarray) -> np.ndarray:
+    """Rows of raw features X whose frontier the library pushes without an
+    evaluation (features 0, 1, 5 are log2(1 + |F|), log2(1 + m_f), log2(1 + m))."""
+    nf = np.rint(np.exp2(X[:, 0].astype(np.float64)) - 1.0)
+    mf = np.rint(np.exp2(X[:, 1].astype(np.float64)) - 1.0)
+    m = np.rint(np.exp2(X[:, 5].astype(np.float64)) - 1.0)
+    return (nf + mf) * SELECTOR_GATE < m
+
+
 def choose(params: np.ndarray, mean: np.ndarray, inv_std: np.ndarray, X: np.ndarray) -> np.ndarray:
-    """Directions (0 SparsePush, 1 DensePush, 2 DensePull) the network picks for raw features X."""
+    """Directions (0 SparsePush, 1 DensePush, 2 DensePull) the learned policy
+    picks for raw features X: the network's, except SparsePush on gated rows."""
     if X.shape[0] == 0:
         return np.zeros(0, np.int64)
     p = torch.from_numpy(params.astype(np.float32)).cuda()
     Xn = torch.from_numpy(((X - mean) * inv_std).astype(np.float32)).cuda()
-    return forward(p, Xn).argmin(dim=1).cpu().numpy()
+    k = forward(p, Xn).argmin(dim=1).cpu().numpy()
+    return np.where(gated(X), 0, k)
 
 
 def save(path: str, params, mean, inv_std, **meta):

@@ -95,17 +95,17 @@ def collect(items, n_src: int, max_levels_per_run: int = 400):
     return np.concatenate(X), np.concatenate(T), np.array(tags)
 
 
-def evaluate(params, mean, inv_std, items, n_src: int):
-    """Recorded cost of learned vs Beamer/Ligra vs per-level best on held-out runs."""
+def heldout_profiles(items, n_src: int):
+    """Per-level features and timings of held-out runs with the rule's own
+    choices (one profile per source), for replaying any candidate network."""
     import graphgen as gg
     import paper_1805_00923_gb300 as gi
     from paper_1805_00923_gb300 import selector as sel
-    rows = []
+    runs = []
     for algo, name, make in items:
         hg = make()
         g = gi.Graph.from_host(hg)
         kern, sc = _sched(algo)
-        tot = np.zeros(3)
         for s in gg.pick_sources(hg, n_src, seed=99):
             f, t = sel.profile(g, kern, int(s), sched=sc)
             tr = gi.Trace(1 << 16)
@@ -113,17 +113,67 @@ def evaluate(params, mean, inv_std, items, n_src: int):
                 gi.bfs(g, int(s), want_parent=False, sched=sc, trace=tr)
             else:
                 gi.sssp(g, int(s), sched=sc, trace=tr)
-            rule = tr.as_dict()["direction"][:len(t)]
-            learned = sel.choose(params, mean, inv_std, f)
-            # where a direction was not offered (masked, time < 0) the driver
-            # runs SparsePush instead
-            learned = np.where(t[np.arange(len(t)), learned] < 0, 0, learned)
-            t = np.where(t < 0, np.inf, t)
-            idx = np.arange(len(t))
-            tot += [t[idx, learned].sum(), t[idx, rule].sum(), t.min(axis=1).sum()]
-        rows.append(dict(graph=f"{algo}:{name}", learned_ms=tot[0], rule_ms=tot[1], best_ms=tot[2]))
+            runs.append((f"{algo}:{name}", f, t, tr.as_dict()["direction"][:len(t)]))
         g.free()
-    return rows
+    return runs
+
+
+def evaluate(params, mean, inv_std, runs):
+    """Recorded cost of learned vs Beamer/Ligra vs per-level best on held-out runs."""
+    from paper_1805_00923_gb300 import selector as sel
+    rows = {}
+    for graph, f, t, rule in runs:
+        learned = sel.choose(params, mean, inv_std, f)
+        # where a direction was not offered (masked, time < 0) the driver
+        # runs SparsePush instead
+        learned = np.where(t[np.arange(len(t)), learned] < 0, 0, learned)
+        tt = np.where(t < 0, np.inf, t)
+        idx = np.arange(len(tt))
+        r = rows.setdefault(graph, np.zeros(3))
+        r += [tt[idx, learned].sum(), tt[idx, rule].sum(), tt.min(axis=1).sum()]
+    return [dict(graph=k, learned_ms=v[0], rule_ms=v[1], best_ms=v[2]) for k, v in rows.items()]
+
+
+def validate_end_to_end(cands, n_src: int = 8):
+    """Each candidate network run by the graph-driven BFS and delta-stepping
+    SSSP loops (the benchmark's forms) on a held-out R-MAT 24 graph (another
+    seed than the benchmark's), timed with CUDA events against the rules on
+    the same loops.  Returns per candidate the summed ratio learned / rule
+    over BFS and SSSP (lower is better), with the times."""
+    import torch
+    import graphgen as gg
+    import paper_1805_00923_gb300 as gi
+    from paper_1805_00923_gb300 import selector as sel
+    hg = gg.rmat_graph(24, 16, seed=5074, weights=(1, 1000))
+    g = gi.Graph.from_host(hg)
+    srcs = [int(s) for s in gg.pick_sources(hg, n_src, seed=77)]
+    d0 = torch.empty(hg.n, dtype=torch.int32, device="cuda")
+    d1 = torch.empty_like(d0)
+
+    def timed(algo, sc):
+        run = (lambda s: gi.bfs(g, s, sched=sc, out=(d0, d1))) if algo == "bfs" else \
+            (lambda s: gi.sssp(g, s, sched=sc, out=d0))
+        run(srcs[0])
+        best = float("inf")
+        for _ in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for s in srcs:
+                run(s)
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b) / len(srcs))
+        return best
+
+    scheds = {"bfs": ("bfs", dict(persistent=2)), "sssp_ds128": ("sssp", dict(persistent=2, delta=128))}
+    rule = {k: timed(a, gi.schedule("hybrid_pull", **kw)) for k, (a, kw) in scheds.items()}
+    out = []
+    for params, mean, inv_std in cands:
+        sel.selector_load(params, mean, inv_std)
+        t = {k: timed(a, gi.schedule("learned", **kw)) for k, (a, kw) in scheds.items()}
+        out.append(dict(score=sum(t[k] / rule[k] for k in t), learned_ms=t, rule_ms=rule))
+    g.free()
+    return out
 
 
 def main():
@@ -132,6 +182,9 @@ def main():
                                                   "selector_weights.npz"))
     ap.add_argument("--sources", type=int, default=4)
     ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--candidates", type=int, default=4,
+                    help="networks trained from different initial weights; the one that runs fastest "
+                         "end to end on the held-out R-MAT 24 graph is kept")
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--report", default=None)
     args = ap.parse_args()
@@ -151,19 +204,31 @@ def main():
     t1 = time.time()
     M = (Tms > 0).astype(np.float32)   # directions not offered in a mode are masked out
     T = sel.targets(np.where(Tms > 0, Tms, 1.0))
-    params, mean, inv_std, losses = sel.train(X, T, M=M, steps=args.steps)
+    cands, all_losses = [], []
+    for seed in range(max(1, args.candidates)):
+        params, mean, inv_std, losses = sel.train(X, T, M=M, steps=args.steps, seed=seed)
+        cands.append((params, mean, inv_std))
+        all_losses.append(losses)
     t2 = time.time()
-    sel.save(args.out, params, mean, inv_std, samples=X.shape[0], steps=args.steps, losses=np.array(losses))
     held = [it for it in workloads(5000, True, large=False)]
     # the benchmark's size, another seed: BFS, Bellman-Ford and delta-stepping at 128
     import graphgen as gg
     held += [("bfs", "rmat24_ef16", lambda: gg.rmat_graph(24, 16, seed=5024)),
              ("sssp", "rmat24_w", lambda: gg.rmat_graph(24, 16, seed=5074, weights=(1, 1000))),
              ("sssp_ds128", "rmat24_w", lambda: gg.rmat_graph(24, 16, seed=5074, weights=(1, 1000)))]
-    rows = evaluate(params, mean, inv_std, held, 2)
+    runs = heldout_profiles(held, 2)
+    val = validate_end_to_end(cands) if len(cands) > 1 else [dict(score=0.0)]
+    pick = int(np.argmin([v["score"] for v in val]))
+    params, mean, inv_std = cands[pick]
+    losses = all_losses[pick]
+    sel.save(args.out, params, mean, inv_std, samples=X.shape[0], steps=args.steps, losses=np.array(losses),
+             init_seed=pick)
+    rows = evaluate(params, mean, inv_std, runs)
     tot = {k: float(sum(r[k] for r in rows)) for k in ("learned_ms", "rule_ms", "best_ms")}
+    cand_tot = [float(sum(r["learned_ms"] for r in evaluate(*c, runs))) for c in cands]
     report = dict(samples=int(X.shape[0]), collect_s=t1 - t0, train_s=t2 - t1, loss_first=losses[0],
-                  loss_last=losses[-1], heldout=rows, heldout_total=tot,
+                  loss_last=losses[-1], heldout=rows, heldout_total=tot, picked_init_seed=pick,
+                  candidates=[dict(init_seed=i, heldout_learned_ms=cand_tot[i], **val[i]) for i in range(len(cands))],
                   train_choice_share=np.bincount(np.argmin(np.where(Tms > 0, Tms, np.inf), 1),
                                                  minlength=3).tolist())
     txt = json.dumps(report, indent=1, default=float)

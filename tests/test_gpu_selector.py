@@ -112,11 +112,19 @@ def test_learned_schedule_bit_exact_and_fused_inference(gi):
             assert np.array_equal(d.cpu().numpy(), want_d) and np.array_equal(p.cpu().numpy(), want_p)
             t = tr.as_dict()
             # the fused kernel's choice equals the batched forward kernel's argmin
-            # on the same features, wherever the margin exceeds float noise
-            Xn = torch.from_numpy(((t["features"] - mean) * inv_std).astype(np.float32)).cuda()
+            # on the same features, wherever the margin exceeds float noise, and
+            # SparsePush where |F| + m_f < m / 200 (no evaluation there)
+            f = t["features"]
+            Xn = torch.from_numpy(((f - mean) * inv_std).astype(np.float32)).cuda()
             Y = sel.forward(torch.from_numpy(params).cuda(), Xn).cpu().numpy()
             srt = np.sort(Y, axis=1)
-            clear = (srt[:, 1] - srt[:, 0]) > 1e-3
+            nfmf = t["frontier"].astype(np.float64) + t["edges"].astype(np.float64)
+            gate = nfmf * sel.SELECTOR_GATE < hg.m
+            # the replay's gate from the (rounded) features agrees away from the boundary
+            far = np.abs(nfmf * sel.SELECTOR_GATE / hg.m - 1.0) > 1e-3
+            assert np.array_equal(gate[far], sel.gated(f)[far])
+            assert (t["direction"][gate] == 0).all()
+            clear = ((srt[:, 1] - srt[:, 0]) > 1e-3) & ~gate
             assert np.array_equal(t["direction"][clear], Y.argmin(1)[clear])
 
 
