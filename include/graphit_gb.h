@@ -333,10 +333,32 @@ int gi_bfs(gi_graph *g, int32_t src, int32_t *depth_dev, int32_t *parent_dev, co
            gi_trace *trace, void *stream);
 
 /*
- * Frontier Bellman-Ford from src on the graph's int32 weights (Sec. 7's SSSP):
- * synchronous rounds; round r relaxes the out-arcs of vertices whose distance
- * dropped in round r-1 using their start-of-round distance.  dist_dev[n]:
- * INT32_MAX if unreachable.  GI_ERR_INVALID_ARG if the graph has no weights.
+ * Single-source shortest paths from src on the graph's non-negative int32
+ * weights; dist_dev[n]: the distance, INT32_MAX if unreachable (sums are
+ * clamped at INT32_MAX).  Same distances under every schedule.
+ * sched->delta == 0: frontier Bellman-Ford (Sec. 7's SSSP) in synchronous
+ * rounds; round r relaxes the out-arcs of vertices whose distance dropped in
+ * round r-1 using their start-of-round distance, in the direction the
+ * schedule picks per round.
+ * sched->delta > 0: delta-stepping (buckets of that width in weight units;
+ * arcs lighter than delta are light): each bucket's light arcs are relaxed in
+ * synchronous rounds until no distance in the bucket drops, then the heavy
+ * arcs of the vertices settled in the bucket in one round, then the next
+ * non-empty bucket.  Each round's direction (push over the round's sources, or
+ * pull over every vertex's light or heavy in-arcs) is the schedule's; on a
+ * directed graph delta-stepping rounds push (the arc classes are split from
+ * the out-edges, once per graph and width, and cached).  The trace records
+ * the counted rounds with their phase (0 light, 1 heavy).
+ * sched->persistent: 0 = host-driven rounds; 1 = the batched engine's
+ * whole-GPU persistent kernel (near/far rounds; trace: round count only);
+ * 2 = the rounds as a CUDA graph (delta-stepping, or Bellman-Ford as one
+ * bucket holding every arc), built on first use and cached per graph, width
+ * and schedule; trace: round count only.  Syncs the stream.
+ * Errors: GI_ERR_INVALID_ARG (NULL, no weights, src out of range, bad
+ * schedule, a DENSE_PULL or HYBRID_PULL schedule on a directed graph loaded
+ * without in-edge weights), GI_ERR_UNSUPPORTED (a forced pull direction
+ * without in-edges), GI_ERR_TIMEOUT (a round cap or bounded wait of the
+ * persistent / graph-driven modes), GI_ERR_OOM, GI_ERR_CUDA.
  */
 int gi_sssp(gi_graph *g, int32_t src, int32_t *dist_dev, const gi_schedule *sched, gi_trace *trace,
             void *stream);
@@ -438,7 +460,10 @@ int gi_bc(gi_graph *g, int32_t src, double *dependency_dev, double *sigma_dev, i
  * Load the learned direction selector: a 16-64-64-3 ReLU perceptron, params as
  * float32 W1[64][16], b1[64], W2[64][64], b2[64], W3[3][64], b3[3] (host memory,
  * `count` = 5443 floats), plus feature normalisation mean[16] and inv_std[16].
- * Used by GI_DIR_LEARNED; until loaded, LEARNED falls back to the Beamer rule.
+ * Used by GI_DIR_LEARNED: the network picks the argmin of its predicted
+ * log-times for a frontier with |F| + m_f >= m / 200; a smaller frontier is
+ * pushed (SparsePush) without an evaluation.  Until loaded, LEARNED falls back
+ * to the Beamer rule.
  * Errors: GI_ERR_INVALID_ARG (NULL or count != 5443), GI_ERR_CUDA.
  */
 int gi_selector_load(const float *params, int32_t count, const float *mean, const float *inv_std);
@@ -471,9 +496,14 @@ int gi_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t t,
  * and continue from the common result.  For level i < cap, features[16*i..]
  * (host) receive the level's 16 selector features and times_ms[3*i..] (host)
  * the three durations in milliseconds; *levels the number of levels recorded.
- * Syncs the stream.  Needs the in-edges (symmetric graph or gi_load_csc).
+ * With sched->delta > 0 (GI_K_SSSP, symmetric graphs): the counted
+ * delta-stepping rounds, SparsePush and DensePull over the round's arc class
+ * timed (DensePush is not offered: its time is -1).  BFS pulls follow
+ * sched->dst_list.  Syncs the stream.  Needs the in-edges (symmetric graph or
+ * gi_load_csc).
  * Errors: GI_ERR_INVALID_ARG (NULL, other kernel_id, src out of range, cap < 0),
- * GI_ERR_UNSUPPORTED (no in-edges), GI_ERR_OOM, GI_ERR_CUDA.
+ * GI_ERR_UNSUPPORTED (no in-edges; delta-stepping on a directed graph),
+ * GI_ERR_OOM, GI_ERR_CUDA.
  */
 int gi_selector_profile(gi_graph *g, int32_t kernel_id, int32_t src, const gi_schedule *sched, int32_t cap,
                         float *features, float *times_ms, int32_t *levels, void *stream);
