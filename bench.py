@@ -201,15 +201,15 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash():
+def kernel_source_hash(op="OpPR"):
     """Hash of the code of the timed kernel (k_pull_tiled with its staging
-    helpers, the PageRank edge function and the hot-source cap), so a recorded
+    helpers, the edge function `op` and the hot-source cap), so a recorded
     ncu traffic figure is used only while that code is unchanged."""
     with open(os.path.join(ROOT, "paper_1805_00923_gb300", "csrc", "gi_traverse.cuh")) as fh:
         src = fh.read()
     a = src.index("constexpr int kBatch = 8;")
     b = src.index("// Warp tiles (tile_edges = 256)")
-    c = src.index("struct OpPR {")
+    c = src.index(f"struct {op} {{")
     d = src.index("};", c)
     # code only: comment lines and blank lines do not change the kernel
     code = [ln.split("//")[0].rstrip() for ln in (src[a:b] + src[c:d]).splitlines()]
@@ -219,12 +219,12 @@ def kernel_source_hash():
     return hashlib.sha256("\n".join(ln for ln in code if ln).encode()).hexdigest()[:16]
 
 
-def recorded_traffic(kernel, workload):
+def recorded_traffic(kernel, workload, op="OpPR"):
     """DRAM bytes per launch from profiles/traffic.txt if recorded for the current kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    want = kernel_source_hash()
+    want = kernel_source_hash(op)
     for ln in open(path):
         parts = ln.split()
         if len(parts) >= 4 and not ln.startswith("#") and parts[0] == want and parts[1] == kernel \
@@ -278,6 +278,12 @@ def run_rmat22(args, extra=False):
     tuned = {"pagerank": dict(gi.schedule_dict(pr_s), tuned_ms=pr_tuned_ms, default_ms=pr_start_ms),
              "pagerank_delta": dict(gi.schedule_dict(prd_s), tuned_ms=prd_tuned_ms, default_ms=prd_start_ms),
              "cc": dict(gi.schedule_dict(cc_s), tuned_ms=cc_tuned_ms, default_ms=cc_start_ms)}
+    if not args.no_extras:
+        # the tuner's own gain: the same search from the library's default
+        # DensePull schedule (no hot-source cache), reported beside the timed one
+        d_s, d_tuned, d_start = gi.autotune(g, "pagerank", start=gi.schedule("dense_pull"), budget=args.tune_budget,
+                                            seed=1)
+        tuned["pagerank_from_library_defaults"] = dict(gi.schedule_dict(d_s), tuned_ms=d_tuned, default_ms=d_start)
     # the three PageRank directions of the workload, one timed run each (untimed setup)
     compare = {}
     for name, sc in ([] if (args.no_extras or extra) else
@@ -618,6 +624,10 @@ def _sssp_pull_bytes(n, m, tr, m_light=None):
     return total, rounds, arcs
 
 
+PULL_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, average over the 6 pull launches of one "
+                     "query (source 16536593, width 128, host-driven, Ligra's rule)")
+
+
 def host_cpu():
     """(nproc, CPU model name) of this host."""
     model = ""
@@ -703,6 +713,13 @@ def run_config_l(args):
         g, "sssp", src=srcs[0], start=gi.schedule("learned", delta=args.delta, persistent=2), budget=tune_budget,
         seed=7)
     delta = int(ss_learned.delta)
+    # the tuner's own gain: the same search from the library's default SSSP
+    # schedule (Bellman-Ford rounds, learned, graph-driven), reported only
+    tune_defaults = None
+    if not args.no_extras:
+        d_s, d_tuned, d_start = gi.autotune(g, "sssp", src=srcs[0], start=gi.schedule("learned", persistent=2),
+                                            budget=args.tune_budget, seed=7)
+        tune_defaults = {"schedule": gi.schedule_dict(d_s), "tuned_ms": d_tuned, "start_ms": d_start}
     ss_rule = gi.schedule("hybrid_pull")
     for f, _ in ss_learned._fields_:
         setattr(ss_rule, f, getattr(ss_learned, f))
@@ -792,6 +809,9 @@ def run_config_l(args):
     # (gi_gather_rate over this graph's source ids into an n-entry table)
     ceil = gather_ceiling(hg.col, n)
     pull_rate = pull_arcs / (pull_ms * 1e-3) if pull_ms > 0 else 0.0
+    # DRAM traffic per launch from one ncu capture of this workload's pulls
+    # (recorded with the kernel's source hash; null once the code changes)
+    traffic = recorded_traffic("k_pull_tiled_OpMinInt", f"rmat{args.scale}_delta{delta}", op="OpMinInt")
 
     # learned vs rule per algorithm, 3 interleaved repeats each (outside the timed region)
     def per_alg(pol):
@@ -942,9 +962,10 @@ def run_config_l(args):
                               "learned_beats_beyond_spread": beats, "other_forms": forms,
                               "exhaustive_best_per_level": exhaustive, "gteps_graph500": value / 2,
                               "sssp_autotune": {"schedule": gi.schedule_dict(ss_learned), "tuned_ms": ss_tuned_ms,
-                                                "start_ms": ss_start_ms, "source": srcs[0]}},
+                                                "start_ms": ss_start_ms, "source": srcs[0],
+                                                "from_library_defaults": tune_defaults}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_pull_tiled<OpMinInt> (SSSP DensePull rounds over the light / heavy arcs, "
                                    "frontier folded into the gathered start-of-round distances)",
                          "bytes_model": "per pull round 4(V+1) + 8m' + 8 m_f + V/4, m' = arcs of the class scanned",
@@ -954,6 +975,7 @@ def run_config_l(args):
                          "launches_timed": pull_launches, "pull_rounds_expected": pull_rounds,
                          "avg_launch_ms": pull_ms / max(pull_launches, 1),
                          "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                         "traffic_from": PULL_TRAFFIC_NOTE if traffic is not None else None,
                          "gather_ceiling": ceil, "pull_gathers_per_s": pull_rate,
                          "frac_of_gather_ceiling_graph_ids": pull_rate / ceil["graph_ids"]["gathers_per_s"]},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

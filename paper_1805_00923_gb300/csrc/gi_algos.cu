@@ -36,6 +36,14 @@ __global__ void k_parent_fix(int32_t *parent, int64_t n) {
     if (parent[i] == INT32_MAX) parent[i] = -1;
 }
 
+// the graph-driven loop's parents copied out with the same fix-up (one pass)
+__global__ void k_parent_copy_fix(int32_t *__restrict__ dst, const int32_t *__restrict__ src, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = src[i];
+    dst[i] = p == INT32_MAX ? -1 : p;
+  }
+}
+
 __global__ void k_set_one(int32_t *x, int32_t i, int32_t val) { x[i] = val; }
 
 // snapshot maintenance for synchronous rounds: frontier members carry their
@@ -481,8 +489,7 @@ static int run_graph_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *pare
   GI_CUDA(cudaGraphLaunch(L->exec, s));
   GI_CUDA(cudaMemcpyAsync(depth, L->depth, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
   if (parent) {
-    GI_CUDA(cudaMemcpyAsync(parent, L->parent, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
-    k_parent_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, g->n);
+    k_parent_copy_fix<<<grid_for(g, g->n, 256), 256, 0, s>>>(parent, L->parent, g->n);
     GI_TRY(launch_status(1));
   }
   int32_t gm[kGmWords];
