@@ -659,9 +659,22 @@ struct DeltaSplit {
   Csr light, heavy;  // same vertices, arcs split by w < delta
   bool light_alias = false;  // every arc is light: light is the graph's own CSR (not owned)
   int32_t *deg_l = nullptr, *deg_h = nullptr;
-  TileSet tl, th;    // pull tiles (symmetric graphs)
+  // The pulls' views (symmetric graphs, block tiles): only the rows that have
+  // arcs of the class (rows_l / rows_h; their offsets in light_c / heavy_c,
+  // whose arcs are light's / heavy's), so a pull skips the empty rows; with
+  // warp tiles they are light / heavy themselves (compacted false).
+  bool compacted = false;
+  Csr light_c, heavy_c;
+  int32_t *rows_l = nullptr, *rows_h = nullptr;
+  TileSet tl, th;    // pull tiles (symmetric graphs) over light_c / heavy_c
   int64_t m_light = 0;
   void *loop = nullptr;  // cached graph-driven loop over this split (DsLoop)
+  // the CSR a pull of the class reads: the compacted view with the tiles, the
+  // full rows for the vertex-parallel pull (one thread per vertex)
+  const Csr &pull_csr(bool light_class, bool vertex_parallel) const {
+    if (vertex_parallel || !compacted) return light_class ? light : heavy;
+    return light_class ? light_c : heavy_c;
+  }
 };
 
 static void dsloop_free(DeltaSplit *D);
@@ -681,10 +694,59 @@ void dstep_free(gi_graph *g, cudaStream_t s) {
   }
   dev_free(D->deg_l, s);
   dev_free(D->deg_h, s);
+  if (D->compacted) {  // the compacted views own their offsets and row lists only
+    dev_free(D->light_c.ptr, s);
+    dev_free(D->heavy_c.ptr, s);
+    dev_free(D->rows_l, s);
+    dev_free(D->rows_h, s);
+  }
   free_tiles(&D->tl, s);
   free_tiles(&D->th, s);
   delete D;
   g->dstep = nullptr;
+}
+
+__global__ void k_nonempty(const int32_t *__restrict__ deg, int64_t n, int32_t *flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = deg[v] > 0 ? 1 : 0;
+}
+
+// rows[pos[v]] = v and ptr_c[pos[v]] = ptr[v] for the rows with arcs; the
+// closing offset ptr_c[k] = ptr[n] (k = pos[n], the scan's total)
+__global__ void k_compact_rows(const int32_t *__restrict__ deg, const int32_t *__restrict__ pos,
+                               const int32_t *__restrict__ ptr, int64_t n, int32_t *rows, int32_t *ptr_c) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (v == n) {
+      ptr_c[pos[n]] = ptr[n];
+    } else if (deg[v] > 0) {
+      rows[pos[v]] = (int32_t)v;
+      ptr_c[pos[v]] = ptr[v];
+    }
+  }
+}
+
+// The row-compacted view of class c (degrees deg): its rows with arcs and
+// their offsets, and block tiles over them.
+static int compact_class(gi_graph *g, const Csr &c, const int32_t *deg, int32_t te, Csr *cc, int32_t **rows,
+                         TileSet *ts, cudaStream_t s) {
+  const int64_t n = g->n;
+  int32_t *flag = nullptr, *pos = nullptr;
+  GI_TRY(ws_scratch(g, &flag, &pos, s));
+  k_nonempty<<<grid_for(g, n, 256), 256, 0, s>>>(deg, n, flag);
+  GI_TRY(launch_status(1));
+  GI_TRY(scan_exclusive(g, flag, pos, n, s));
+  int32_t k = 0;
+  GI_CUDA(cudaMemcpyAsync(&k, pos + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GI_CUDA(cudaStreamSynchronize(s));
+  GI_TRY(dev_alloc_n(rows, k, s));
+  GI_TRY(dev_alloc_n(&cc->ptr, (int64_t)k + 1, s));
+  cc->idx = c.idx;
+  cc->wt = c.wt;
+  k_compact_rows<<<grid_for(g, n + 1, 256), 256, 0, s>>>(deg, pos, c.ptr, n, *rows, cc->ptr);
+  GI_TRY(launch_status(1));
+  GI_TRY(build_tiles(g, *cc, te, ts, s, k));
+  ts->rows = *rows;
+  return GI_OK;
 }
 
 // light arcs per row, one warp per row
@@ -803,8 +865,16 @@ static int dstep_get(gi_graph *g, int32_t delta, int32_t tile_edges, cudaStream_
       st = launch_status(1);
     }
   }
-  if (st == GI_OK && g->symmetric) st = build_tiles(g, D->light, te, &D->tl, s);
-  if (st == GI_OK && g->symmetric) st = build_tiles(g, D->heavy, te, &D->th, s);
+  if (st == GI_OK && g->symmetric) {
+    if (te != kWarpTileEdges) {
+      D->compacted = true;
+      st = compact_class(g, D->light, D->deg_l, te, &D->light_c, &D->rows_l, &D->tl, s);
+      if (st == GI_OK) st = compact_class(g, D->heavy, D->deg_h, te, &D->heavy_c, &D->rows_h, &D->th, s);
+    } else {
+      st = build_tiles(g, D->light, te, &D->tl, s);
+      if (st == GI_OK) st = build_tiles(g, D->heavy, te, &D->th, s);
+    }
+  }
   if (st != GI_OK) {
     dstep_free(g, s);
     return st;
@@ -1032,8 +1102,8 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
       if (mf == 0) return GI_OK;
       OpMinInt op{x, snap, arcs.wt};
       if (d == GI_DIR_DENSE_PULL)
-        return launch_pull_tiled(g, op, arcs, light ? D->tl : D->th, FSet(), nullptr, out_of(P.N), s, kClassMinPull,
-                                 sc.balance == GI_BAL_VERTEX);
+        return launch_pull_tiled(g, op, D->pull_csr(light, sc.balance == GI_BAL_VERTEX), light ? D->tl : D->th, FSet(),
+                                 nullptr, out_of(P.N), s, kClassMinPull, sc.balance == GI_BAL_VERTEX);
       g->hint_vset = Fr;
       g->hint_nf = nf;
       g->hint_mf = mf;
@@ -1239,8 +1309,8 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
     if (k == kDgLightPush || k == kDgHeavyPush) {
       st = launch_push(g, op, kSrcQueue, light ? &Rv : &Sv, nullptr, out_of(N), sc, cs, &arcs);
     } else if (k == kDgLightPull || k == kDgHeavyPull) {
-      st = launch_pull_tiled(g, op, arcs, light ? D->tl : D->th, FSet(), nullptr, out_of(N), cs, kClassMinPull,
-                             sc.balance == GI_BAL_VERTEX);
+      st = launch_pull_tiled(g, op, D->pull_csr(light, sc.balance == GI_BAL_VERTEX), light ? D->tl : D->th, FSet(),
+                             nullptr, out_of(N), cs, kClassMinPull, sc.balance == GI_BAL_VERTEX);
     } else {
       k_dsg_pile_split<<<grid, 256, 0, cs>>>(L->x, L->dw, L->pile_in, L->pile[0], L->pile[1], N->queue, N->count);
       st = launch_status(1);

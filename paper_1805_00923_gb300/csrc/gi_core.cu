@@ -870,11 +870,11 @@ __global__ void k_tile_close(int4 *tiles, const int32_t *__restrict__ tile_row, 
   }
 }
 
-int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cudaStream_t s) {
+int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cudaStream_t s, int64_t nrows) {
   free_tiles(ts, s);
   GI_TRY(ws_get(g, s));
   ts->tile_edges = tile_edges;
-  int64_t n = g->n;
+  int64_t n = nrows >= 0 ? nrows : g->n;
   if (n == 0) return GI_OK;
   int32_t *cnt = g->ws->tmp_i32, *scnt = g->ws->tmp2_i32;
   int32_t *off = nullptr, *soff = nullptr, *tile_row = nullptr;

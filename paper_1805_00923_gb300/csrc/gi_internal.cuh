@@ -98,6 +98,9 @@ struct Csr {
 struct TileSet {
   int4 *tiles = nullptr;
   int4 *splits = nullptr;  // {row, first tile, piece count, 0}
+  // tiles over a row-compacted CSR (only the rows that have arcs): row r of
+  // the tiles is vertex rows[r] (not owned); nullptr: row r is vertex r
+  const int32_t *rows = nullptr;
   int32_t num_tiles = 0;
   int32_t num_splits = 0;
   int32_t tile_edges = 0;
@@ -274,7 +277,8 @@ int scan_exclusive(gi_graph *g, const int32_t *in, int32_t *out, int64_t n, cuda
 int ws_scratch(gi_graph *g, int32_t **a, int32_t **b, cudaStream_t s);
 
 // tiles
-int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cudaStream_t s);
+// nrows < 0: the graph's n rows
+int build_tiles(gi_graph *g, const Csr &c, int32_t tile_edges, TileSet *ts, cudaStream_t s, int64_t nrows = -1);
 int use_tiles(gi_graph *g, int32_t tile_edges, cudaStream_t s);  // select (building once) the in-edge tiles
 void free_tile_cache(gi_graph *g, cudaStream_t s);
 void graph_loop_free(gi_graph *g);  // the cached graph-driven BFS (gi_algos.cu)

@@ -93,6 +93,7 @@ __device__ __forceinline__ void mark_consecutive(const OutSet &o, int32_t v0, bo
 
 struct OpMinInt {  // CC (no weights) and SSSP (weights): x[v] = min(x[v], snap[u] + w)
   using V = int32_t;
+  static constexpr bool kIdentityKeeps = true;  // finish(v, identity()) changes nothing
   int32_t *x;
   const int32_t *snap;
   const int32_t *wt;  // pull: in-edge weights; push: out-edge weights (same array for symmetric graphs)
@@ -402,6 +403,43 @@ struct SkipZeroTerms : std::false_type {};
 template <class Op>
 struct SkipZeroTerms<Op, std::void_t<decltype(Op::kSkipZeroTerms)>> : std::bool_constant<Op::kSkipZeroTerms> {};
 
+// Ops whose finish() with the identity (no candidate reached the row) changes
+// nothing (min reductions): such rows skip finish() and its load of the
+// vertex's current value.
+template <class Op, class = void>
+struct IdentityKeeps : std::false_type {};
+template <class Op>
+struct IdentityKeeps<Op, std::void_t<decltype(Op::kIdentityKeeps)>> : std::bool_constant<Op::kIdentityKeeps> {};
+
+template <class Op>
+__device__ __forceinline__ bool worth_finishing(typename Op::V acc) {
+  if constexpr (IdentityKeeps<Op>::value) return acc != Op::identity();
+  else return true;
+}
+
+// Output marks of one warp whose lanes hold ascending but not consecutive
+// vertices (rows of a row-compacted tile set): one atomicOr per distinct
+// bitmap word of the marked lanes, one queue append for the warp.
+__device__ __forceinline__ void mark_rows(const OutSet &o, int32_t v, bool mod) {
+  const unsigned ball = __ballot_sync(0xffffffffu, mod);
+  if (!ball) return;
+  const int lane = threadIdx.x & 31;
+  const int32_t myw = v >> 5;
+  unsigned todo = ball;
+  while (todo) {
+    const int l = __ffs(todo) - 1;
+    const int32_t wl = __shfl_sync(0xffffffffu, myw, l);
+    const bool mine = mod && myw == wl;
+    const unsigned bits = __reduce_or_sync(0xffffffffu, mine ? (1u << (v & 31)) : 0u);
+    todo &= ~__ballot_sync(0xffffffffu, mine);
+    if (lane == l) atomicOr(o.bm + wl, bits);
+  }
+  int32_t base = 0;
+  if (lane == 0) base = atomicAdd(o.qc, __popc(ball));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (mod) o.q[base + __popc(ball & ((1u << lane) - 1u))] = v;
+}
+
 template <class Op>
 __device__ __forceinline__ typename Op::V combine_term(typename Op::V acc, typename Op::V x) {
   if constexpr (SkipZeroTerms<Op>::value) {
@@ -431,7 +469,8 @@ __device__ __forceinline__ void pull_tile(const Gather<Op, kMode> &G, const int4
                                           const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                                           const uint32_t *__restrict__ to, const OutSet &out,
                                           typename Op::V *partial, typename Op::V *vals, int32_t *rp,
-                                          typename Op::V *s_red, const int tid, const Sync &sync) {
+                                          typename Op::V *s_red, const int tid, const Sync &sync,
+                                          const int32_t *__restrict__ rows = nullptr) {
   using V = typename Op::V;
   const Op &op = G.op;
   const int lane = tid & 31, warp = tid >> 5;
@@ -456,7 +495,7 @@ __device__ __forceinline__ void pull_tile(const Gather<Op, kMode> &G, const int4
     sync();
     for (int i0 = 0; i0 < R; i0 += kBlock) {
       const int i = i0 + tid;
-      const int32_t v = r0 + i;
+      const int32_t v = rows ? (i < R ? __ldg(rows + r0 + i) : -1) : r0 + i;
       // rows the destination filters reject are not reduced at all
       const bool want = i < R && in_set(to, v) && op.dst_ok(v);
       int32_t a = 0, b = 0;
@@ -479,14 +518,18 @@ __device__ __forceinline__ void pull_tile(const Gather<Op, kMode> &G, const int4
         if (lane == l) acc = x;
       }
       bool mod = false;
-      if (want) mod = op.finish(v, acc);
-      if (out.enabled()) mark_consecutive(out, r0 + i0 + (tid & ~31), mod);
+      if (want && worth_finishing<Op>(acc)) mod = op.finish(v, acc);
+      if (out.enabled()) {
+        if (rows) mark_rows(out, v, mod);
+        else mark_consecutive(out, r0 + i0 + (tid & ~31), mod);
+      }
     }
     sync();
   } else {
     // one long row (or a piece of it): nothing to gather when its destination is filtered out
     const int32_t r = T.x, e0 = T.z;
-    const int32_t ne = (in_set(to, r) && op.dst_ok(r)) ? T.w - T.z : 0;
+    const int32_t vr = rows ? __ldg(rows + r) : r;
+    const int32_t ne = (in_set(to, vr) && op.dst_ok(vr)) ? T.w - T.z : 0;
     V x = Op::identity();
     for (int32_t k0 = tid; k0 < ne; k0 += kBatch * kBlock) {
       int32_t u[kBatch];
@@ -511,7 +554,7 @@ __device__ __forceinline__ void pull_tile(const Gather<Op, kMode> &G, const int4
       V y = Op::identity();
       for (int w = 0; w < kBlock / 32; ++w) y = Op::combine(y, s_red[w]);
       if (T.y == r) {
-        if (ne > 0 && op.finish(r, y) && out.enabled()) out_mark(out, r);
+        if (ne > 0 && worth_finishing<Op>(y) && op.finish(vr, y) && out.enabled()) out_mark(out, vr);
       } else {
         partial[t] = y;
       }
@@ -525,7 +568,8 @@ __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__r
                                                        const int32_t *__restrict__ idx, const int4 *__restrict__ tiles,
                                                        int32_t num_tiles, FSet F,
                                                        const uint32_t *__restrict__ to, OutSet out,
-                                                       typename Op::V *partial, const float *__restrict__ hot) {
+                                                       typename Op::V *partial, const float *__restrict__ hot,
+                                                       const int32_t *__restrict__ rows) {
   using V = typename Op::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *vals = reinterpret_cast<V *>(smem_raw);
@@ -535,7 +579,7 @@ __global__ void __launch_bounds__(kBlock) k_pull_tiled(Op op, const int32_t *__r
   const Gather<Op, kMode> G{op, F, hot};
   for (int32_t t = blockIdx.x; t < num_tiles; t += gridDim.x)
     pull_tile<Op, kBlock, kMode>(G, tiles[t], t, ptr, idx, to, out, partial, vals, rp, s_red, threadIdx.x,
-                                 BlockSync{});
+                                 BlockSync{}, rows);
 }
 
 // Hot-source pull (GPU form of the cache partitioning of Sec. 2) with a
@@ -712,13 +756,16 @@ __global__ void __launch_bounds__(256) k_pull_vertex(Op op, const int32_t *__res
 
 template <class Op>
 __global__ void k_pull_fixup(Op op, const int4 *__restrict__ splits, int32_t num_splits,
-                             const typename Op::V *__restrict__ partial, const uint32_t *__restrict__ to, OutSet out) {
+                             const typename Op::V *__restrict__ partial, const uint32_t *__restrict__ to, OutSet out,
+                             const int32_t *__restrict__ rows = nullptr) {
   using V = typename Op::V;
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < num_splits; s += gridDim.x * blockDim.x) {
     const int4 S = splits[s];
+    const int32_t v = rows ? __ldg(rows + S.x) : S.x;
     V y = Op::identity();
     for (int32_t k = 0; k < S.z; ++k) y = Op::combine(y, partial[S.y + k]);
-    if (in_set(to, S.x) && op.dst_ok(S.x) && op.finish(S.x, y) && out.enabled()) out_mark(out, S.x);
+    if (in_set(to, v) && op.dst_ok(v) && worth_finishing<Op>(y) && op.finish(v, y) && out.enabled())
+      out_mark(out, v);
   }
 }
 
@@ -1485,7 +1532,8 @@ int launch_pull_tiled_te(const Op &op, const int32_t *ptr, const int32_t *idx, c
                                  (int)smem));
   }
   k_pull_tiled<Op, kB, kTE, kMode><<<ts.num_tiles, kB, smem, s>>>(op, ptr, idx, ts.tiles, ts.num_tiles, F, to, out,
-                                                                  reinterpret_cast<typename Op::V *>(ts.partial), hot);
+                                                                  reinterpret_cast<typename Op::V *>(ts.partial), hot,
+                                                                  ts.rows);
   return GI_OK;
 }
 
@@ -1559,6 +1607,10 @@ int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts
   }
   if (ts.num_tiles == 0) return GI_OK;
   const int tok = timing_begin(kclass, s);
+  if (ts.rows != nullptr && ts.tile_edges == kWarpTileEdges) {
+    set_error("warp tiles over a row-compacted CSR are not supported");
+    return GI_ERR_UNSUPPORTED;
+  }
   switch (ts.tile_edges) {
     case kWarpTileEdges: {
       constexpr int kCap = kWarpTileEdges + kWarpTileEdges / kLongRowDiv;
@@ -1583,7 +1635,7 @@ int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts
   GI_LAUNCH_CHECK();
   if (ts.num_splits > 0) {
     k_pull_fixup<Op><<<div_up(ts.num_splits, 128), 128, 0, s>>>(
-        op, ts.splits, ts.num_splits, reinterpret_cast<const typename Op::V *>(ts.partial), to, out);
+        op, ts.splits, ts.num_splits, reinterpret_cast<const typename Op::V *>(ts.partial), to, out, ts.rows);
     GI_LAUNCH_CHECK();
   }
   return GI_OK;

@@ -166,6 +166,26 @@ def test_sssp_delta_stepping_rmat(gi, direction, delta):
         assert np.array_equal(_np(d), want), (src, delta)
 
 
+@pytest.mark.parametrize("te", [256, 512, 2048, 8192])
+@pytest.mark.parametrize("persistent", [0, 2])
+def test_sssp_delta_stepping_pull_tile_sizes(gi, te, persistent):
+    """The delta-stepping pulls over the row-compacted light / heavy views
+    (block tiles: only the rows with arcs of the class) and over the full
+    rows (warp tiles, 256 arcs), host- and graph-driven, forced DensePull and
+    the hybrid rule, against the oracle; the R-MAT graph has isolated
+    vertices and hubs whose rows are split over several tiles."""
+    hg = rmat(16, weights=True)
+    g = _load(gi, hg)
+    for src in [0, *gg.pick_sources(hg, 2, seed=5)]:
+        want, _ = oracle.sssp(hg, int(src))
+        for direction in ("dense_pull", "hybrid_pull"):
+            for delta in (64, 1 << 20):
+                d = gi.sssp(g, int(src), sched=gi.schedule(direction, delta=delta, tile_edges=te,
+                                                           persistent=persistent))
+                assert np.array_equal(_np(d), want), (src, direction, delta)
+    g.free()
+
+
 @pytest.mark.parametrize("balance", ["edge_aware", "vertex", "edge_parallel"])
 def test_sssp_delta_stepping_rounds_do_not_depend_on_direction(gi, balance):
     """Push and pull relax the same arcs of the same sources in every round
