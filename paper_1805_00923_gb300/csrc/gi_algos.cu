@@ -930,9 +930,7 @@ __global__ void k_ds_split(const int32_t *__restrict__ P, const int32_t *__restr
         pnew = true;
       }
     }
-    warp_append(Rq, w + kDsR, near, v);
-    warp_append(Sq, w + kDsS, snew, v);
-    warp_append(pile, pile_count, pnew, v);
+    warp_append3(Rq, w + kDsR, near, Sq, w + kDsS, snew, pile, pile_count, pnew, v);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
@@ -961,8 +959,7 @@ __global__ void k_ds_pile_split(const int32_t *__restrict__ pile, const int32_t 
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
     if (near) pile_in[v] = 0;
     if (far) fmin = min(fmin, d);
-    warp_append(Pq, Pc, near, v);
-    warp_append(pile2, pile2_count, far, v);
+    warp_append3(Pq, Pc, near, pile2, pile2_count, far, nullptr, nullptr, false, v);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
@@ -1055,11 +1052,11 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
   S.reps = GI_REP_SPARSE;
   int64_t hi = sc.delta;  // end of the current bucket (distance of src = 0)
   int cur = 0;            // far-pile buffer in use
-  const int grid = g->num_sms * 4;
+  const int grid = g->num_sms * 8;
   int32_t it = 0;
   while (st == GI_OK) {
     k_ds_round_init<<<1, 32, 0, s>>>(w);
-    k_ds_split<<<g->num_sms * 2, 256, 0, s>>>(P.F->queue, P.F->count, x, (int32_t)(hi < INT32_MAX ? hi : INT32_MAX),
+    k_ds_split<<<g->num_sms * 8, 256, 0, s>>>(P.F->queue, P.F->count, x, (int32_t)(hi < INT32_MAX ? hi : INT32_MAX),
                                               Rq, snap, s_mark, epoch, Sq, pile_in, pile[cur], w + kDsPile0 + cur, w);
     if ((st = launch_status(2)) != GI_OK) break;
     DecideParams p = decide_params(sc, it, false);
@@ -1213,8 +1210,7 @@ __global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uin
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
     if (near) pile_in[v] = 0;
     if (far) fmin = min(fmin, d);
-    warp_append(Nq, Nc, near, v);
-    warp_append(pile2, dw + kDgPile0 + (cur ^ 1), far, v);
+    warp_append3(Nq, Nc, near, pile2, dw + kDgPile0 + (cur ^ 1), far, nullptr, nullptr, false, v);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
@@ -1266,7 +1262,7 @@ static void dsloop_free(DeltaSplit *D) {
 // next round's output set; N was emptied the same way a round before)
 static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &sc, gi_vset *F, gi_vset *N,
                      cudaGraph_t body, cudaGraphConditionalHandle hw, cudaStream_t cs) {
-  const int grid = g->num_sms * 4;
+  const int grid = g->num_sms * 8;
   const bool pull_ok = g->symmetric;
   cudaGraphConditionalHandle hs;
   GI_CUDA(cudaGraphConditionalHandleCreate(&hs, body, kDgDone, cudaGraphCondAssignDefault));

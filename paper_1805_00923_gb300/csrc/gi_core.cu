@@ -1785,9 +1785,7 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
         pnew = true;
       }
     }
-    warp_append(B.Rq, dw + kDgRc, near, v);
-    warp_append(B.Sq, dw + kDgSc, snew, v);
-    warp_append(pile, pile_count, pnew, v);
+    warp_append3(B.Rq, dw + kDgRc, near, B.Sq, dw + kDgSc, snew, pile, pile_count, pnew, v);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -1896,7 +1894,9 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
 
 int dsg_step_launch(gi_graph *g, const DsgBuffers &b, const DecideParams &p, int32_t delta, bool pull_ok,
                     unsigned long long switch_handle, unsigned long long while_handle, cudaStream_t s) {
-  k_dsg_step<<<g->num_sms * 2, 256, 0, s>>>(b, g->ctrl, p, g->n, g->m, g->max_deg, g_sel_loaded ? 1 : 0, delta,
+  // six blocks per SM: the kernel's registers allow six 256-thread blocks,
+  // and its per-vertex chain of dependent loads wants every warp it can get
+  k_dsg_step<<<g->num_sms * 6, 256, 0, s>>>(b, g->ctrl, p, g->n, g->m, g->max_deg, g_sel_loaded ? 1 : 0, delta,
                                             pull_ok ? 1 : 0, switch_handle, while_handle);
   GI_LAUNCH_CHECK();
   return GI_OK;
@@ -1919,7 +1919,7 @@ int ctrl_init(gi_graph *g, int64_t nu, int64_t mu, cudaStream_t s) {
 
 int frontier_decide(gi_graph *g, gi_vset *F, const DecideParams &p, cudaStream_t s, const int32_t *deg) {
   GI_TRY(vset_ensure_queue(F, s));
-  int blocks = g->num_sms * 2;
+  int blocks = g->num_sms * 6;  // as many resident 256-thread blocks as its registers allow
   k_frontier_decide<<<blocks, 256, 0, s>>>(F->queue, F->count, deg ? deg : g->out_deg, g->ctrl, p, g->n, g->m,
                                            g->max_deg, g_sel_loaded ? 1 : 0);
   GI_LAUNCH_CHECK();

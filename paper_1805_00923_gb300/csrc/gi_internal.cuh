@@ -425,5 +425,29 @@ __device__ __forceinline__ void warp_append(int32_t *q, int32_t *qc, bool pred, 
   if (pred) q[base + __popc(b & ((1u << lane) - 1u))] = v;
 }
 
+// warp_append to up to three queues at once: the three reservations are
+// issued back to back and their results awaited together (one atomic round
+// trip per warp iteration instead of three); q2 may be unused (p2 false)
+__device__ __forceinline__ void warp_append3(int32_t *q0, int32_t *c0, bool p0, int32_t *q1, int32_t *c1, bool p1,
+                                             int32_t *q2, int32_t *c2, bool p2, int32_t v) {
+  const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1),
+                 b2 = __ballot_sync(0xffffffffu, p2);
+  if (!(b0 | b1 | b2)) return;
+  const int lane = threadIdx.x & 31;
+  int32_t x0 = 0, x1 = 0, x2 = 0;
+  if (lane == 0) {
+    if (b0) x0 = atomicAdd(c0, __popc(b0));
+    if (b1) x1 = atomicAdd(c1, __popc(b1));
+    if (b2) x2 = atomicAdd(c2, __popc(b2));
+  }
+  x0 = __shfl_sync(0xffffffffu, x0, 0);
+  x1 = __shfl_sync(0xffffffffu, x1, 0);
+  x2 = __shfl_sync(0xffffffffu, x2, 0);
+  const unsigned lt = (1u << lane) - 1u;
+  if (p0) q0[x0 + __popc(b0 & lt)] = v;
+  if (p1) q1[x1 + __popc(b1 & lt)] = v;
+  if (p2) q2[x2 + __popc(b2 & lt)] = v;
+}
+
 
 }  // namespace gi
