@@ -203,16 +203,20 @@ class ClockSampler:
 
 def kernel_source_hash(op="OpPR"):
     """Hash of the code of the timed kernel (k_pull_tiled with its staging
-    helpers, the edge function `op` and the hot-source cap), so a recorded
-    ncu traffic figure is used only while that code is unchanged."""
+    helpers, the edge function `op` -- "+"-joined names for an edge function
+    and the one it extends -- and the hot-source cap), so a recorded ncu
+    traffic figure is used only while that code is unchanged."""
+    import re
     with open(os.path.join(ROOT, "paper_1805_00923_gb300", "csrc", "gi_traverse.cuh")) as fh:
         src = fh.read()
     a = src.index("constexpr int kBatch = 8;")
     b = src.index("// Warp tiles (tile_edges = 256)")
-    c = src.index(f"struct {op} {{")
-    d = src.index("};", c)
+    parts = src[a:b]
+    for name in op.split("+"):
+        c = re.search(rf"struct {name}\b[^{{;]*{{", src).start()
+        parts += src[c:src.index("};", c)]
     # code only: comment lines and blank lines do not change the kernel
-    code = [ln.split("//")[0].rstrip() for ln in (src[a:b] + src[c:d]).splitlines()]
+    code = [ln.split("//")[0].rstrip() for ln in parts.splitlines()]
     # the hot-source cap (a constant of the shared header) changes what the kernel reads
     with open(os.path.join(ROOT, "paper_1805_00923_gb300", "csrc", "gi_internal.cuh")) as fh:
         code += [ln.split("//")[0].rstrip() for ln in fh if ln.startswith("constexpr int kHotMax")]
@@ -774,7 +778,7 @@ def run_config_l(args):
     value = world * args.steps * arcs_per_step / (total_ms * 1e-3) / 1e9
 
     # roofline of the dominant kernel, the SSSP DensePull rounds
-    # (k_pull_tiled<OpMinInt>): kernels inside a CUDA graph cannot be timed one
+    # (k_pull_tiled<OpMinInt / OpMinIntBounded>): kernels inside a CUDA graph cannot be timed one
     # by one, so the same 64 queries run once more with the same schedule
     # host-driven, every pull launch bracketed by CUDA events on its stream
     m_light = int((hg.wt < delta).sum()) if delta > 0 else None
@@ -787,6 +791,7 @@ def run_config_l(args):
         gi.sssp(g, s_, sched=ss_host, trace=traces[s_], out=dist_)
     torch.cuda.synchronize()
     gi.stats_reset()
+    gi.stats_pull_arcs(g, reset=True)
     gi.stats_enable(True)
     a0, a1 = _events()
     a0.record()
@@ -797,12 +802,18 @@ def run_config_l(args):
     gi.stats_enable(False)
     host_ms = a0.elapsed_time(a1) / len(srcs)
     _, pull_launches, pull_ms = gi.stats_read("min_pull")
-    pull_bytes, pull_rounds, pull_arcs = 0, 0, 0
+    # the arcs the pulls gathered, counted by the library (a delta-stepping
+    # pull skips the long rows at or below the round's least candidate), in
+    # place of every arc of the class in the 8m' term
+    gathered = gi.stats_pull_arcs(g, reset=True)
+    pull_bytes, pull_rounds, class_arcs = 0, 0, 0
     for s_ in srcs:
         b_, r_, a_ = _sssp_pull_bytes(n, m, traces[s_], m_light)
         pull_bytes += b_
         pull_rounds += r_
-        pull_arcs += a_
+        class_arcs += a_
+    pull_bytes += 8 * (gathered - class_arcs)
+    pull_arcs = gathered
     peak, peak_kind = measured_hbm()
     achieved = pull_bytes / (pull_ms * 1e-3) / 1e9 if pull_ms > 0 else 0.0
     # the second ceiling of a pull: one gathered 4-byte value per arc
@@ -811,7 +822,8 @@ def run_config_l(args):
     pull_rate = pull_arcs / (pull_ms * 1e-3) if pull_ms > 0 else 0.0
     # DRAM traffic per launch from one ncu capture of this workload's pulls
     # (recorded with the kernel's source hash; null once the code changes)
-    traffic = recorded_traffic("k_pull_tiled_OpMinInt", f"rmat{args.scale}_delta{delta}", op="OpMinInt")
+    traffic = recorded_traffic("k_pull_tiled_OpMinInt_and_Bounded", f"rmat{args.scale}_delta{delta}",
+                               op="OpMinInt+OpMinIntBounded")
 
     # learned vs rule per algorithm, 3 interleaved repeats each (outside the timed region)
     def per_alg(pol):
@@ -966,9 +978,14 @@ def run_config_l(args):
                                                 "from_library_defaults": tune_defaults}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_pull_tiled<OpMinInt> (SSSP DensePull rounds over the light / heavy arcs, "
-                                   "frontier folded into the gathered start-of-round distances)",
-                         "bytes_model": "per pull round 4(V+1) + 8m' + 8 m_f + V/4, m' = arcs of the class scanned",
+                         "kernel": "k_pull_tiled<OpMinInt> (light rounds) / <OpMinIntBounded> (heavy rounds): SSSP "
+                                   "delta-stepping DensePull over the row-compacted light / heavy arcs, frontier "
+                                   "folded into the gathered start-of-round distances; heavy rounds skip the rows at "
+                                   "or below the bucket's end",
+                         "bytes_model": "per pull round 4(V+1) + 8m' + 8 m_f + V/4, m' = the arcs the round's pull "
+                                        "gathered (library counter: the class's arcs less the long rows its bound "
+                                        "filter skipped)",
+                         "arcs_gathered": gathered, "arcs_of_the_classes": class_arcs,
                          "timed_in": "the same 64 SSSP queries with the same schedule run host-driven after the "
                                      "timed region, every pull launch bracketed by CUDA events on its stream "
                                      f"({host_ms:.2f} ms per query)",

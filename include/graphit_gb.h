@@ -657,6 +657,17 @@ int gi_stats_reset(void);
 int gi_stats_read(int32_t kclass, int64_t *launches, int64_t *timed_launches, double *timed_ms);
 
 /*
+ * Instrumentation (not in the paper): *arcs = the arcs that the block-tiled
+ * DensePulls on g gathered (staged for reduction) while per-launch timing
+ * was on, since the last reset -- every arc of a short tile, the arcs of a
+ * long row only when its destination passes the filters; warp tiles and the
+ * vertex-parallel pull are not counted.  reset != 0 zeroes the count after
+ * reading it.  Synchronizes the device.  Errors: GI_ERR_INVALID_ARG (NULL),
+ * GI_ERR_CUDA.
+ */
+int gi_stats_pull_arcs(gi_graph *g, int32_t reset, int64_t *arcs);
+
+/*
  * Gather ceiling (instrumentation, not in the paper): one launch on `stream`
  * that streams idx[m] (device, 16-byte aligned; every id in [0, n)) with
  * 16-byte loads and reads table[idx[i]] (device, n floats) for every i --

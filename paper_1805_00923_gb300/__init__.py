@@ -311,6 +311,13 @@ def stats_read(kclass: int | str = -1):
     return a.value, b.value, c.value
 
 
+def stats_pull_arcs(g: Graph, reset: bool = False) -> int:
+    """gi_stats_pull_arcs: arcs the block-tiled pulls on g gathered while timing was on."""
+    a = ctypes.c_int64()
+    check(_C.gi_stats_pull_arcs(g.handle, 1 if reset else 0, ctypes.byref(a)))
+    return a.value
+
+
 def gather_rate(idx: torch.Tensor, table: torch.Tensor, out: torch.Tensor | None = None, stream=None):
     """gi_gather_rate: launch the gather-ceiling kernel over idx (int32, CUDA) into table (float32, CUDA)."""
     out = out if out is not None else torch.zeros(1, dtype=torch.float32, device="cuda")

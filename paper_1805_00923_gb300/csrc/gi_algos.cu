@@ -886,7 +886,7 @@ static int dstep_get(gi_graph *g, int32_t delta, int32_t tile_edges, cudaStream_
 // Device words of delta-stepping (int32, in the graph's control block): the
 // round's R and the bucket's S counts, the counts of the two far-pile
 // buffers and the smallest distance in the far pile.
-enum DsWord { kDsR = 0, kDsS = 1, kDsPile0 = 2, kDsPile1 = 3, kDsPileMin = 4 };
+enum DsWord { kDsR = 0, kDsS = 1, kDsPile0 = 2, kDsPile1 = 3, kDsPileMin = 4, kDsHi = 5 };
 
 __global__ void k_ds_round_init(int32_t *w) {
   if (threadIdx.x == 0) w[kDsR] = 0;
@@ -967,10 +967,12 @@ __global__ void k_ds_pile_split(const int32_t *__restrict__ pile, const int32_t 
 }
 
 // before a pile split: the target buffer empty, its minimum to be recomputed
-__global__ void k_ds_pile_prep(int32_t *w, int32_t target) {
+// a new bucket ending at hi: the next pile buffer emptied, its minimum reset
+__global__ void k_ds_pile_prep(int32_t *w, int32_t target, int32_t hi) {
   if (threadIdx.x == 0) {
     w[target] = 0;
     w[kDsPileMin] = INT32_MAX;
+    w[kDsHi] = hi;
   }
 }
 
@@ -1038,7 +1040,8 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
   if (st == GI_OK) st = front_init(g, P.F, src, s);
   if (st == GI_OK) st = ctrl_init(g, 0, 0, s);  // also zeroes the words
   if (st == GI_OK) {
-    k_ds_pile_prep<<<1, 32, 0, s>>>(w, kDsPile0);  // pile minimum = INT32_MAX
+    // pile minimum = INT32_MAX, first bucket [0, delta)
+    k_ds_pile_prep<<<1, 32, 0, s>>>(w, kDsPile0, sc.delta);
     st = launch_status(1);
   }
   // R and S are vertex sets with the queue form only; their counters are words
@@ -1069,7 +1072,7 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
       // entries of the next bucket become the pending set
       hi = ((int64_t)hw[kDsPileMin] / sc.delta + 1) * sc.delta;
       if ((st = vset_clear(P.F, s)) != GI_OK) break;
-      k_ds_pile_prep<<<1, 32, 0, s>>>(w, kDsPile0 + (cur ^ 1));
+      k_ds_pile_prep<<<1, 32, 0, s>>>(w, kDsPile0 + (cur ^ 1), (int32_t)(hi < INT32_MAX ? hi : INT32_MAX));
       k_ds_pile_split<<<grid, 256, 0, s>>>(pile[cur], w + kDsPile0 + cur, x, (int32_t)(hi < INT32_MAX ? hi : INT32_MAX),
                                            pile_in, P.F->queue, P.F->count, pile[cur ^ 1], w + kDsPile0 + (cur ^ 1),
                                            w);
@@ -1098,9 +1101,15 @@ static int deltastep_run(gi_graph *g, int32_t *x, int32_t src, const gi_schedule
       GI_TRY(vset_clear(P.N, s));
       if (mf == 0) return GI_OK;
       OpMinInt op{x, snap, arcs.wt};
-      if (d == GI_DIR_DENSE_PULL)
-        return launch_pull_tiled(g, op, D->pull_csr(light, sc.balance == GI_BAL_VERTEX), light ? D->tl : D->th, FSet(),
-                                 nullptr, out_of(P.N), s, kClassMinPull, sc.balance == GI_BAL_VERTEX);
+      if (d == GI_DIR_DENSE_PULL) {
+        const Csr &pc = D->pull_csr(light, sc.balance == GI_BAL_VERTEX);
+        const bool vp = sc.balance == GI_BAL_VERTEX;
+        if (light)
+          return launch_pull_tiled(g, op, pc, D->tl, FSet(), nullptr, out_of(P.N), s, kClassMinPull, vp);
+        // heavy round: rows at or below the bucket's end are not pulled
+        const OpMinIntBounded opb{op, w + kDsHi, 0};
+        return launch_pull_tiled(g, opb, pc, D->th, FSet(), nullptr, out_of(P.N), s, kClassMinPull, vp);
+      }
       g->hint_vset = Fr;
       g->hint_nf = nf;
       g->hint_mf = mf;
@@ -1305,8 +1314,16 @@ static int dsg_round(gi_graph *g, DeltaSplit *D, DsLoop *L, const gi_schedule &s
     if (k == kDgLightPush || k == kDgHeavyPush) {
       st = launch_push(g, op, kSrcQueue, light ? &Rv : &Sv, nullptr, out_of(N), sc, cs, &arcs);
     } else if (k == kDgLightPull || k == kDgHeavyPull) {
-      st = launch_pull_tiled(g, op, D->pull_csr(light, sc.balance == GI_BAL_VERTEX), light ? D->tl : D->th, FSet(),
-                             nullptr, out_of(N), cs, kClassMinPull, sc.balance == GI_BAL_VERTEX);
+      const Csr &pc = D->pull_csr(light, sc.balance == GI_BAL_VERTEX);
+      if (!light) {
+        // heavy round: rows at or below the bucket's end are not pulled
+        const OpMinIntBounded opb{op, L->dw + kDgHi, 0};
+        st = launch_pull_tiled(g, opb, pc, light ? D->tl : D->th, FSet(), nullptr, out_of(N), cs, kClassMinPull,
+                               sc.balance == GI_BAL_VERTEX);
+      } else {
+        st = launch_pull_tiled(g, op, pc, light ? D->tl : D->th, FSet(), nullptr, out_of(N), cs, kClassMinPull,
+                               sc.balance == GI_BAL_VERTEX);
+      }
     } else {
       k_dsg_pile_split<<<grid, 256, 0, cs>>>(L->x, L->dw, L->pile_in, L->pile[0], L->pile[1], N->queue, N->count);
       st = launch_status(1);

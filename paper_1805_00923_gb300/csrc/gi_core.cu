@@ -63,6 +63,8 @@ static cudaEvent_t pool_event() {
   return e;
 }
 
+bool timing_on() { return g_timing.load(std::memory_order_relaxed); }
+
 int timing_begin(int kclass, cudaStream_t s) {
   if (!g_timing.load(std::memory_order_relaxed)) return -1;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -593,6 +595,14 @@ extern "C" int gi_stats_read(int32_t kclass, int64_t *launches, int64_t *timed_l
   if (timed_ms) *timed_ms = ms;
   return GI_OK;
 }
+extern "C" int gi_stats_pull_arcs(gi_graph *g, int32_t reset, int64_t *arcs) {
+  GI_ARG(g != nullptr && arcs != nullptr, "NULL argument");
+  GI_CUDA(cudaDeviceSynchronize());
+  GI_CUDA(cudaMemcpy(arcs, g->ctrl + kPullArcs, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  if (reset) GI_CUDA(cudaMemset(g->ctrl + kPullArcs, 0, sizeof(int64_t)));
+  return GI_OK;
+}
+
 extern "C" int gi_version(void) { return 100; }
 
 namespace gi {
@@ -1903,7 +1913,8 @@ int dsg_step_launch(gi_graph *g, const DsgBuffers &b, const DecideParams &p, int
 }
 
 __global__ void k_ctrl_init(int64_t *ctrl, int64_t nu, int64_t mu) {
-  for (int i = threadIdx.x; i < kCtrlWords; i += blockDim.x) ctrl[i] = 0;
+  for (int i = threadIdx.x; i < kCtrlWords; i += blockDim.x)
+    if (i != kPullArcs) ctrl[i] = 0;
   __syncthreads();
   if (threadIdx.x == 0) {
     ctrl[kNu] = nu;

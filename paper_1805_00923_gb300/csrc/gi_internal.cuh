@@ -25,6 +25,7 @@ int launch_status(int n);
 enum KernelClass { kClassPrPull = 0, kClassPrdPull = 1, kClassMinPull = 2, kClassPush = 3, kClassBfsPull = 4,
                    kClassOtherPull = 5, kClassBatch = 6, kNumClasses = 7 };
 int timing_begin(int kclass, cudaStream_t s);
+bool timing_on();  // per-launch event timing (gi_stats_enable) is on
 void timing_end(int token, cudaStream_t s);
 
 }  // namespace gi
@@ -80,6 +81,7 @@ enum CtrlSlot {
   kMfAcc = 10,    // m_f accumulator of the statistics kernel (its last block returns it to 0)
   kFeat = 16,     // 16 float features stored as float bits in 8 int64 words (slots 16..23)
   kDsSlots = 32,  // delta-stepping SSSP: 8 int32 round words in slots 32..35 (fetched with the rest)
+  kPullArcs = 40, // arcs the block-tiled pulls gathered while timing was on (kept by ctrl_init)
   kSHeavyMf = 11, // graph-driven delta-stepping: heavy arcs of the bucket's settled list so far
 };
 

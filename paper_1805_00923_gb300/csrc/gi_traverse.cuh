@@ -125,6 +125,22 @@ struct OpMinInt {  // CC (no weights) and SSSP (weights): x[v] = min(x[v], snap[
   }
 };
 
+// OpMinInt for rounds whose candidates have a floor: none that can lower a
+// distance is below max(*bound - bound_off, 0), so rows whose distance is
+// already at or below it are not pulled (dst_ok; long rows skip their
+// gathers too).  Delta-stepping's heavy rounds: the floor is the bucket's
+// end hi (S lies in [hi - delta, hi) and heavy arcs weigh at least delta).
+// Light rounds (floor hi - delta) do without: their long rows are few, and
+// the per-row test costs more than it saves.
+struct OpMinIntBounded : OpMinInt {
+  const int32_t *bound;
+  int32_t bound_off;
+  __device__ bool dst_ok(int32_t v) const {
+    const int32_t b = *bound;
+    return x[v] > (b > bound_off ? b - bound_off : 0);
+  }
+};
+
 struct SumCount {
   float s;
   int32_t c;
@@ -766,6 +782,35 @@ __global__ void k_pull_fixup(Op op, const int4 *__restrict__ splits, int32_t num
     for (int32_t k = 0; k < S.z; ++k) y = Op::combine(y, partial[S.y + k]);
     if (in_set(to, v) && op.dst_ok(v) && worth_finishing<Op>(y) && op.finish(v, y) && out.enabled())
       out_mark(out, v);
+  }
+}
+
+// Instrumentation (gi_stats_pull_arcs): the arcs the block tiles will gather,
+// by pull_tile's rules -- every arc of a short tile, a long row's arcs only
+// if its destination passes the filters -- evaluated before the pull changes
+// any distance; one atomic per block.
+template <class Op>
+__global__ void k_pull_count(Op op, const int4 *__restrict__ tiles, int32_t num_tiles, const int32_t *__restrict__ rows,
+                             const uint32_t *__restrict__ to, unsigned long long *ctr) {
+  unsigned long long c = 0;
+  for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < num_tiles; t += gridDim.x * blockDim.x) {
+    const int4 T = tiles[t];
+    if (T.y > T.x) {
+      c += (unsigned long long)(T.w - T.z);
+    } else {
+      const int32_t vr = rows ? __ldg(rows + T.x) : T.x;
+      if (in_set(to, vr) && op.dst_ok(vr)) c += (unsigned long long)(T.w - T.z);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ unsigned long long s_c[8];
+  if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_c[w];
+    if (b) atomicAdd(ctr, b);
   }
 }
 
@@ -1606,6 +1651,13 @@ int launch_pull_tiled(gi_graph *g, const Op &op, const Csr &c, const TileSet &ts
     return GI_OK;
   }
   if (ts.num_tiles == 0) return GI_OK;
+  if (timing_on() && ts.tile_edges != kWarpTileEdges) {
+    // instrumentation, outside the timed launch: the arcs the block tiles
+    // are about to gather, by the pull's own tile and filter rules
+    k_pull_count<Op><<<grid_for(g, ts.num_tiles, 256), 256, 0, s>>>(
+        op, ts.tiles, ts.num_tiles, ts.rows, to, reinterpret_cast<unsigned long long *>(g->ctrl + kPullArcs));
+    GI_LAUNCH_CHECK();
+  }
   const int tok = timing_begin(kclass, s);
   if (ts.rows != nullptr && ts.tile_edges == kWarpTileEdges) {
     set_error("warp tiles over a row-compacted CSR are not supported");

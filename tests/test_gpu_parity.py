@@ -867,3 +867,30 @@ def test_edgeset_apply_bfs_deferred_row_with_to_set(gi, hub_in_to):
     else:
         assert d[0] == -1 and out.size == 0
     assert d[3] == -1 and d[4] == -1  # leaves 3 and 4: their only in-neighbour (the hub) is not in F
+
+
+def test_pull_arc_counter(gi):
+    """gi_stats_pull_arcs: with timing on, a block-tiled PageRank pull gathers
+    every arc once per iteration; a delta-stepping pull skips the long rows
+    its bound filter rejects, so it gathers at most the class's arcs per
+    round; with timing off nothing is counted."""
+    hg = rmat(14, weights=True)
+    g = _load(gi, hg)
+    gi.stats_pull_arcs(g, reset=True)
+    gi.pagerank(g, 0.85, 3, sched=gi.schedule("dense_pull", tile_edges=2048))
+    assert gi.stats_pull_arcs(g) == 0  # timing off
+    gi.stats_enable(True)
+    try:
+        gi.stats_pull_arcs(g, reset=True)
+        gi.pagerank(g, 0.85, 3, sched=gi.schedule("dense_pull", tile_edges=2048))
+        assert gi.stats_pull_arcs(g, reset=True) == 3 * hg.m
+        tr = gi.Trace(1 << 12)
+        d = gi.sssp(g, 0, sched=gi.schedule("dense_pull", delta=64), trace=tr)
+        arcs = gi.stats_pull_arcs(g, reset=True)
+        rounds = tr.as_dict()["iterations"]
+        assert 0 < arcs <= rounds * hg.m
+    finally:
+        gi.stats_enable(False)
+        gi.stats_reset()
+    want, _ = oracle.sssp(hg, 0)
+    assert np.array_equal(_np(d), want)
