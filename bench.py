@@ -1058,6 +1058,8 @@ def rmat22_summary(args, hg, g, steps, value, total_ms, per_alg_ms, edges, launc
     achieved = (8 * m + 12 * n + 4) / (avg_ms * 1e-3) / 1e9
     ceil = gather_ceiling(hg.col, n)
     pull_rate = m / (avg_ms * 1e-3)
+    hot = int(pr_s.hot_cache) if pr_s.direction == gi.GI_DIR_DENSE_PULL and pr_s.num_segments == 1 else 0
+    kname = {0: "k_pull_tiled_OpPR", 1: "k_pull_hot_OpPR", 2: "k_pull_tiled_hotL1_OpPR"}[hot]
     out = {"workload": workload_config(hg, args.m_scale), "value": value, "unit": "GTEPS", "steps": steps,
            "ms_per_step": total_ms / steps,
            "per_algorithm": {
@@ -1068,6 +1070,7 @@ def rmat22_summary(args, hg, g, steps, value, total_ms, per_alg_ms, edges, launc
                "cc": {"gteps": edges[2] / (per_alg_ms[2] * 1e-3) / 1e9, "ms": per_alg_ms[2] / steps}},
            "numerators": "PR 20m; PRD m per pull round + m_f per push round; CC m (every vertex reached)",
            "roofline_pr_pull": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                "kernel": kname, "traffic": recorded_traffic(kname, f"rmat{args.m_scale}"),
                                 "bytes_model": "8m + 12n + 4 per launch", "avg_launch_ms": avg_ms,
                                 "launches_timed": pr_launches, "peak_kind": f"{peak_kind} hbm_gbs",
                                 "gather_ceiling": ceil, "pull_gathers_per_s": pull_rate,
