@@ -749,18 +749,51 @@ static int compact_class(gi_graph *g, const Csr &c, const int32_t *deg, int32_t 
   return GI_OK;
 }
 
-// light arcs per row, one warp per row
+// Rows with more than kDsLongRow arcs are split by a whole block instead of
+// one warp (a hub row of 10^5-10^6 arcs walked by one warp took tens of ms);
+// the warp kernels queue them (long[0] = count, long[1..] = rows).
+constexpr int64_t kDsLongRow = 4096;
+
+// light arcs per row, one warp per row; long rows queued for k_ds_count_long
 __global__ void k_ds_count(const int32_t *__restrict__ ptr, const int32_t *__restrict__ wt, int64_t n, int32_t delta,
-                           int32_t *cnt) {
+                           int32_t *cnt, int32_t *longq) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     const int64_t a = __ldg(ptr + v), b = __ldg(ptr + v + 1);
+    if (b - a > kDsLongRow) {
+      if (lane == 0) longq[1 + atomicAdd(longq, 1)] = (int32_t)v;
+      continue;
+    }
     int32_t c = 0;
     for (int64_t e = a + lane; e < b; e += 32) c += __ldg(wt + e) < delta ? 1 : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lane == 0) cnt[v] = c;
+  }
+}
+
+// the queued long rows' light arcs, one block (256 threads) per row
+__global__ void __launch_bounds__(256) k_ds_count_long(const int32_t *__restrict__ ptr,
+                                                       const int32_t *__restrict__ wt, int32_t delta,
+                                                       const int32_t *__restrict__ longq, int32_t *cnt) {
+  __shared__ int32_t s_c[8];
+  const int32_t nl = longq[0];
+  for (int32_t j = blockIdx.x; j < nl; j += gridDim.x) {
+    const int32_t v = longq[1 + j];
+    const int64_t a = __ldg(ptr + v), b = __ldg(ptr + v + 1);
+    int32_t c = 0;
+    for (int64_t e = a + threadIdx.x; e < b; e += 256) c += __ldg(wt + e) < delta ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int32_t t = 0;
+      for (int w = 0; w < 8; ++w) t += s_c[w];
+      cnt[v] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -787,6 +820,7 @@ __global__ void k_ds_fill(const int32_t *__restrict__ ptr, const int32_t *__rest
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     const int64_t a = __ldg(ptr + v), b = __ldg(ptr + v + 1);
+    if (b - a > kDsLongRow) continue;  // k_ds_fill_long
     int64_t lo = __ldg(lptr + v), ho = __ldg(hptr + v);
     for (int64_t e0 = a; e0 < b; e0 += 32) {
       const int64_t e = e0 + lane;
@@ -810,6 +844,61 @@ __global__ void k_ds_fill(const int32_t *__restrict__ ptr, const int32_t *__rest
   }
 }
 
+// the queued long rows' stable split, one block (256 threads) per row: each
+// 256-arc chunk is placed by a block-wide prefix of its light (heavy) flags,
+// chunks in order
+__global__ void __launch_bounds__(256) k_ds_fill_long(const int32_t *__restrict__ ptr,
+                                                      const int32_t *__restrict__ idx,
+                                                      const int32_t *__restrict__ wt, int32_t delta,
+                                                      const int32_t *__restrict__ lptr,
+                                                      const int32_t *__restrict__ hptr,
+                                                      const int32_t *__restrict__ longq, int32_t *lidx, int32_t *lwt,
+                                                      int32_t *hidx, int32_t *hwt) {
+  __shared__ int32_t s_l[8], s_h[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  const int32_t nl = longq[0];
+  for (int32_t j = blockIdx.x; j < nl; j += gridDim.x) {
+    const int32_t v = longq[1 + j];
+    const int64_t a = __ldg(ptr + v), b = __ldg(ptr + v + 1);
+    int64_t lo = __ldg(lptr + v), ho = __ldg(hptr + v);
+    for (int64_t e0 = a; e0 < b; e0 += 256) {
+      const int64_t e = e0 + threadIdx.x;
+      const bool ok = e < b;
+      const int32_t w = ok ? __ldg(wt + e) : 0, u = ok ? __ldg(idx + e) : 0;
+      const bool li = ok && w < delta, hv = ok && !li;
+      const unsigned bl = __ballot_sync(0xffffffffu, li), bh = __ballot_sync(0xffffffffu, hv);
+      if (lane == 0) {
+        s_l[warp] = __popc(bl);
+        s_h[warp] = __popc(bh);
+      }
+      __syncthreads();
+      int32_t pl = 0, ph = 0, tl = 0, th = 0;
+      for (int k = 0; k < 8; ++k) {
+        if (k < warp) {
+          pl += s_l[k];
+          ph += s_h[k];
+        }
+        tl += s_l[k];
+        th += s_h[k];
+      }
+      if (li) {
+        const int64_t p = lo + pl + __popc(bl & below);
+        lidx[p] = u;
+        lwt[p] = w;
+      }
+      if (hv) {
+        const int64_t p = ho + ph + __popc(bh & below);
+        hidx[p] = u;
+        hwt[p] = w;
+      }
+      lo += tl;
+      ho += th;
+      __syncthreads();
+    }
+  }
+}
+
 static int dstep_get(gi_graph *g, int32_t delta, int32_t tile_edges, cudaStream_t s, DeltaSplit **out) {
   DeltaSplit *D = static_cast<DeltaSplit *>(g->dstep);
   const int32_t te = tile_edges > 0 ? tile_edges : 2048;
@@ -828,11 +917,16 @@ static int dstep_get(gi_graph *g, int32_t delta, int32_t tile_edges, cudaStream_
   if (st == GI_OK) st = dev_alloc_n(&D->deg_l, n, s);
   if (st == GI_OK) st = dev_alloc_n(&D->deg_h, n, s);
   const int wgrid = grid_for(g, n * 32, 256);
-  int32_t *cnt = nullptr;
+  int32_t *cnt = nullptr, *longq = nullptr;
   if (st == GI_OK) st = dev_alloc_n(&cnt, n, s);
+  // at most m / kDsLongRow rows are long
+  if (st == GI_OK) st = dev_alloc_n(&longq, 2 + g->m / kDsLongRow, s);
+  if (st == GI_OK && cudaMemsetAsync(longq, 0, sizeof(int32_t), s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "long-row queue", __FILE__, __LINE__);
   if (st == GI_OK) {
-    k_ds_count<<<wgrid, 256, 0, s>>>(g->out.ptr, g->out.wt, n, delta, cnt);
-    st = launch_status(1);
+    k_ds_count<<<wgrid, 256, 0, s>>>(g->out.ptr, g->out.wt, n, delta, cnt, longq);
+    k_ds_count_long<<<g->num_sms * 8, 256, 0, s>>>(g->out.ptr, g->out.wt, delta, longq, cnt);
+    st = launch_status(2);
   }
   if (st == GI_OK) st = scan_exclusive(g, cnt, D->light.ptr, n, s);
   dev_free(cnt, s);
@@ -862,9 +956,13 @@ static int dstep_get(gi_graph *g, int32_t delta, int32_t tile_edges, cudaStream_
     if (st == GI_OK) {
       k_ds_fill<<<wgrid, 256, 0, s>>>(g->out.ptr, g->out.idx, g->out.wt, n, delta, D->light.ptr, D->heavy.ptr,
                                       D->light.idx, D->light.wt, D->heavy.idx, D->heavy.wt);
-      st = launch_status(1);
+      k_ds_fill_long<<<g->num_sms * 8, 256, 0, s>>>(g->out.ptr, g->out.idx, g->out.wt, delta, D->light.ptr,
+                                                     D->heavy.ptr, longq, D->light.idx, D->light.wt, D->heavy.idx,
+                                                     D->heavy.wt);
+      st = launch_status(2);
     }
   }
+  dev_free(longq, s);
   if (st == GI_OK && g->symmetric) {
     if (te != kWarpTileEdges) {
       D->compacted = true;
