@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--scale", type=int, default=24, help="R-MAT scale of the BFS/SSSP workload")
     p.add_argument("--m-scale", type=int, default=22, help="R-MAT scale of the PR/PRD/CC workload (and BC)")
     p.add_argument("--m-steps", type=int, default=5, help="timed steps of the PR/PRD/CC extra")
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--repeats", type=int, default=3, help="repeats of the learned vs rule comparison")
     p.add_argument("--delta", type=int, default=128, help="SSSP bucket width the autotuner starts from")
     p.add_argument("--exhaustive-sources", type=int, default=8)
@@ -931,16 +931,28 @@ def run_config_l(args):
     h2d = 4 * (n + 1) + 8 * m
     d2h = len(srcs) * 3 * 4 * n
 
-    def e2e_step():
-        ge = gi.Graph(rp_h.numpy(), col_h.numpy(), wt_h.numpy(), symmetric=True)
-        bs, ss = pols["learned"]
+    bs_l, ss_l = pols["learned"]
+    load_stream = torch.cuda.Stream()
+    dev = torch.cuda.current_device()
+
+    def load_graph(box):
+        # gi_load_csr from the pinned host buffers, then the schedule's per-graph
+        # set-up (delta-stepping split, CUDA-graph loops) built ahead of the
+        # queries (gi_prepare), on their own stream
+        torch.cuda.set_device(dev)
+        ge = gi.Graph(rp_h.numpy(), col_h.numpy(), wt_h.numpy(), symmetric=True, stream=load_stream)
+        gi.prepare(ge, "bfs", bs_l, stream=load_stream)
+        gi.prepare(ge, "sssp", ss_l, stream=load_stream)
+        box["g"] = ge
+
+    def queries(ge):
         for i, s_ in enumerate(srcs):
             k = i % slots
             if slot_free[k] is not None:
                 slot_free[k].synchronize()  # the host has the slot's previous results
             dd, pp, ds = dev_out[k]
-            gi.bfs(ge, s_, sched=bs, out=(dd, pp))
-            gi.sssp(ge, s_, sched=ss, out=ds)
+            gi.bfs(ge, s_, sched=bs_l, out=(dd, pp))
+            gi.sssp(ge, s_, sched=ss_l, out=ds)
             done = torch.cuda.Event()
             done.record()
             side.wait_event(done)
@@ -952,13 +964,27 @@ def run_config_l(args):
             slot_free[k] = ev
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.current_stream().synchronize()
-        ge.free()
 
-    e2e_step()  # warm-up (allocator pool, pinned slabs)
+    def e2e_run(K):
+        # like a data loader: a second host thread loads step k+1's graph (and
+        # its set-up) while step k's queries run; the first load, every copy in
+        # and every result copy out lie inside the timed region
+        box = {}
+        load_graph(box)
+        for k in range(K):
+            ge, box = box["g"], {}
+            th = threading.Thread(target=load_graph, args=(box,)) if k + 1 < K else None
+            if th:
+                th.start()
+            queries(ge)
+            if th:
+                th.join()
+            ge.free()
+
+    e2e_run(1)  # warm-up (allocator pool, pinned slabs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        e2e_step()
+    e2e_run(args.e2e_steps)
     e2e_s = time.perf_counter() - t0
     if world > 1:
         from paper_1805_00923_gb300 import replicas
@@ -997,9 +1023,11 @@ def run_config_l(args):
                          "frac_of_gather_ceiling_graph_ids": pull_rate / ceil["graph_ids"]["gathers_per_s"]},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * e2e_s / args.e2e_steps, "steps": args.e2e_steps,
-                    "form": "gi_load_csr from pinned host CSR + weights, then the 64 BFS + SSSP queries; each "
-                            "query's depth, parent and distance copied to pinned host memory on a side stream "
-                            "(8 result slots reused once the host has them); load, queries and copies timed"},
+                    "form": "per step gi_load_csr from pinned host CSR + weights and gi_prepare (the schedule's "
+                            "per-graph set-up), then the 64 BFS + SSSP queries; each query's depth, parent and "
+                            "distance copied to pinned host memory on a side stream (8 result slots reused once the "
+                            "host has them); step k+1's load and set-up run in a second host thread on their own "
+                            "stream under step k's queries; from the first load on, everything is timed"},
             "gpu_launches": launches, "clocks": clocks}
     if not args.no_extras:
         line["config_m_pr_prd_cc"] = run_rmat22(args, extra=True)

@@ -364,6 +364,20 @@ int gi_sssp(gi_graph *g, int32_t src, int32_t *dist_dev, const gi_schedule *sche
             void *stream);
 
 /*
+ * Builds ahead of the queries what a driver of `algo` (GI_ALGO_*) run with
+ * `sched` would build on its first call on g (not in the paper; the results
+ * of later calls do not change): the pull tiles of sched->tile_edges; for
+ * GI_ALGO_SSSP with delta > 0 (or persistent == 2) the light / heavy arc split
+ * and its pull views; for persistent == 2 the CUDA-graph level loop (BFS,
+ * SSSP); for a host-driven GI_ALGO_BFS with dst_list the unvisited-list
+ * storage.  Work is enqueued on `stream`, which is synchronized before the
+ * return.  May run in another host thread while queries run on other
+ * graphs.  Errors: GI_ERR_INVALID_ARG (NULL, unknown algo, bad schedule,
+ * SSSP without weights), GI_ERR_OOM, GI_ERR_CUDA.
+ */
+int gi_prepare(gi_graph *g, int32_t algo, const gi_schedule *sched, void *stream);
+
+/*
  * Connected components by synchronous min-label propagation (Sec. 7's CC):
  * label_dev[n] = smallest vertex id of v's component (symmetric graphs).
  * Syncs the stream.  Errors: GI_ERR_INVALID_ARG, GI_ERR_UNSUPPORTED (DENSE_PULL

@@ -311,6 +311,12 @@ def stats_read(kclass: int | str = -1):
     return a.value, b.value, c.value
 
 
+def prepare(g: Graph, algo: str, sched=None, stream=None):
+    """gi_prepare: build what `algo` ("bfs", "sssp", ...) run with `sched` needs on g, ahead of the queries."""
+    check(_C.gi_prepare(g.handle, int(ALGOS[algo] if isinstance(algo, str) else algo), ctypes.byref(_sched(sched)),
+                        _stream(stream)))
+
+
 def stats_pull_arcs(g: Graph, reset: bool = False) -> int:
     """gi_stats_pull_arcs: arcs the block-tiled pulls on g gathered while timing was on."""
     a = ctypes.c_int64()

@@ -130,6 +130,7 @@ SIGNATURES = {
     "gi_stats_reset": (ctypes.c_int, []),
     "gi_stats_read": (ctypes.c_int, [_i32, _P(_i64), _P(_i64), _P(ctypes.c_double)]),
     "gi_stats_pull_arcs": (ctypes.c_int, [_vp, _i32, _P(_i64)]),
+    "gi_prepare": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
 }
 KCLASS = {"pr_pull": 0, "prd_pull": 1, "min_pull": 2, "push": 3, "bfs_pull": 4, "other_pull": 5, "batch": 6}
 

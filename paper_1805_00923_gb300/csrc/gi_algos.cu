@@ -458,8 +458,8 @@ static int graph_loop_build(gi_graph *g, const gi_schedule &sc, GraphLoop *L, cu
 
 // BFS depths (and canonical parents, parent may be NULL) by the graph-driven
 // loop; levels = number of levels
-static int run_graph_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent, const gi_schedule &sched,
-                         int32_t *levels, cudaStream_t s) {
+// the graph's cached BFS loop for `sched`, built (or rebuilt) if needed
+static int graph_loop_get(gi_graph *g, const gi_schedule &sched, cudaStream_t s, GraphLoop **out) {
   gi_schedule sc = sched;
   sc.balance = sc.balance == GI_BAL_EDGE_PARALLEL ? GI_BAL_EDGE_AWARE : sc.balance;  // needs a host-known |F|
   if (!g->has_csc) sc.direction = GI_DIR_SPARSE_PUSH;
@@ -480,6 +480,14 @@ static int run_graph_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *pare
       return st;
     }
   }
+  *out = L;
+  return GI_OK;
+}
+
+static int run_graph_bfs(gi_graph *g, int32_t src, int32_t *depth, int32_t *parent, const gi_schedule &sched,
+                         int32_t *levels, cudaStream_t s) {
+  GraphLoop *L = nullptr;
+  GI_TRY(graph_loop_get(g, sched, s, &L));
   k_bfs_init<<<grid_for(g, g->n, 256), 256, 0, s>>>(L->depth, L->parent, g->n, src, L->unv.st);
   k_gm_init<<<1, 32, 0, s>>>(L->gm, (int32_t)(g->n + 1 < INT32_MAX ? g->n + 1 : INT32_MAX));
   GI_TRY(launch_status(2));
@@ -1478,8 +1486,9 @@ static int dsloop_build(gi_graph *g, DeltaSplit *D, const gi_schedule &sc, DsLoo
 }  // namespace gi
 
 // SSSP distances by the graph-driven loop; rounds = relaxation rounds run
-static int run_graph_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedule &sched, int32_t *rounds,
-                          cudaStream_t s) {
+// the graph's cached delta-stepping split and graph-driven loop for `sched`,
+// built (or rebuilt) if needed; *sc_out receives the loop's normalized schedule
+static int dsloop_get(gi_graph *g, const gi_schedule &sched, cudaStream_t s, DsLoop **out, gi_schedule *sc_out) {
   gi_schedule sc = sched;
   sc.balance = sc.balance == GI_BAL_EDGE_PARALLEL ? GI_BAL_EDGE_AWARE : sc.balance;  // needs a host-known |F|
   sc.persistent = 2;
@@ -1503,6 +1512,16 @@ static int run_graph_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_sche
       return st;
     }
   }
+  *out = L;
+  if (sc_out) *sc_out = sc;
+  return GI_OK;
+}
+
+static int run_graph_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedule &sched, int32_t *rounds,
+                          cudaStream_t s) {
+  DsLoop *L = nullptr;
+  gi_schedule sc;
+  GI_TRY(dsloop_get(g, sched, s, &L, &sc));
   const int64_t n = g->n;
   k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->x, n, INT32_MAX);
   k_fill_i32<<<grid_for(g, n, 256), 256, 0, s>>>(L->snap, n, INT32_MAX);
@@ -1549,6 +1568,35 @@ extern "C" int gi_sssp(gi_graph *g, int32_t src, int32_t *dist, const gi_schedul
   }
   if (sched->delta > 0) return deltastep_run(g, dist, src, *sched, trace, (cudaStream_t)stream);
   return minlabel_run(g, dist, GI_K_SSSP, src, *sched, trace, (cudaStream_t)stream);
+}
+
+extern "C" int gi_prepare(gi_graph *g, int32_t algo, const gi_schedule *sched, void *stream) {
+  GI_ARG(g != nullptr, "graph is NULL");
+  GI_TRY(check_schedule(sched));
+  GI_ARG(algo >= GI_ALGO_BFS && algo <= GI_ALGO_PAGERANK_DELTA, "unknown algo");
+  cudaStream_t s = (cudaStream_t)stream;
+  const gi_schedule &sc = *sched;
+  GI_TRY(ensure_tiles(g, sc, s));
+  if (algo == GI_ALGO_BFS) {
+    if (sc.persistent == 2) {
+      GraphLoop *L = nullptr;
+      GI_TRY(graph_loop_get(g, sc, s, &L));
+    } else if (sc.dst_list && g->has_csc && sc.persistent == 0) {
+      BfsUnv U;
+      GI_TRY(bfs_unv_get(g, s, &U));
+    }
+  } else if (algo == GI_ALGO_SSSP) {
+    GI_ARG(g->out.wt != nullptr, "SSSP needs edge weights");
+    if (sc.persistent == 2) {
+      DsLoop *L = nullptr;
+      GI_TRY(dsloop_get(g, sc, s, &L, nullptr));
+    } else if (sc.delta > 0 && sc.persistent == 0) {
+      DeltaSplit *D = nullptr;
+      GI_TRY(dstep_get(g, sc.delta, sc.tile_edges, s, &D));
+    }
+  }
+  GI_CUDA(cudaStreamSynchronize(s));
+  return GI_OK;
 }
 
 extern "C" int gi_cc(gi_graph *g, int32_t *label, const gi_schedule *sched, gi_trace *trace, void *stream) {

@@ -894,3 +894,48 @@ def test_pull_arc_counter(gi):
         gi.stats_reset()
     want, _ = oracle.sssp(hg, 0)
     assert np.array_equal(_np(d), want)
+
+
+def test_prepare_then_queries(gi):
+    """gi_prepare builds a schedule's per-graph set-up ahead of the queries
+    (also from a second host thread while queries run on another graph); the
+    queries then give the oracle's results."""
+    import threading
+    hg = rmat(15, weights=True)
+    srcs = [int(s) for s in gg.pick_sources(hg, 3, seed=8)]
+    want = {s: oracle.sssp(hg, s)[0] for s in srcs}
+    want_b = {s: oracle.bfs(hg, s)[:2] for s in srcs}
+    for sched in (gi.schedule("hybrid_pull", delta=64, persistent=2), gi.schedule("hybrid_pull", delta=64),
+                  gi.schedule("learned", persistent=2)):
+        g = _load(gi, hg)
+        gi.prepare(g, "sssp", sched)
+        gi.prepare(g, "bfs", sched)
+        for s in srcs:
+            assert np.array_equal(_np(gi.sssp(g, s, sched=sched)), want[s])
+            d, p = gi.bfs(g, s, sched=sched)
+            assert np.array_equal(_np(d), want_b[s][0]) and np.array_equal(_np(p), want_b[s][1])
+        g.free()
+    # a second graph loaded and prepared in another thread while the first one serves queries
+    sched = gi.schedule("learned", delta=64, persistent=2)
+    g1 = _load(gi, hg)
+    box = {}
+
+    def other():
+        torch.cuda.set_device(0)
+        st = torch.cuda.Stream()
+        g2 = gi.Graph.from_host(hg, stream=st)
+        gi.prepare(g2, "sssp", sched, stream=st)
+        gi.prepare(g2, "bfs", sched, stream=st)
+        box["g"] = g2
+
+    th = threading.Thread(target=other)
+    th.start()
+    for s in srcs:
+        assert np.array_equal(_np(gi.sssp(g1, s, sched=sched)), want[s])
+    th.join()
+    for s in srcs:
+        assert np.array_equal(_np(gi.sssp(box["g"], s, sched=sched)), want[s])
+    g1.free()
+    box["g"].free()
+    with pytest.raises(gi.GIError):
+        gi.prepare(_load(gi, rmat(10)), "sssp", gi.schedule("hybrid_pull", delta=64))  # no weights
