@@ -1014,24 +1014,27 @@ __global__ void k_ds_split(const int32_t *__restrict__ P, const int32_t *__restr
   int32_t fmin = INT32_MAX;
   for (int32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < c; i0 += stride) {
     const int32_t i = i0 + lane;
-    int32_t v = -1, d = INT32_MAX;
+    int32_t v = -1, d = INT32_MAX, sm = epoch;
+    uint8_t pin = 0;
     if (i < c) {
       v = P[i];
-      d = x[v];
+      d = x[v];  // with the membership words, in one round trip
+      sm = s_mark[v];
+      pin = pile_in[v];
     }
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
     bool snew = false, pnew = false;
     if (near) {
       snap[v] = d;
-      if (pile_in[v]) pile_in[v] = 0;  // its pile entry is now stale
-      if (s_mark[v] != epoch) {
+      if (pin) pile_in[v] = 0;  // its pile entry is now stale
+      if (sm != epoch) {
         s_mark[v] = epoch;
         snew = true;
       }
     }
     if (far) {
       fmin = min(fmin, d);
-      if (!pile_in[v]) {
+      if (!pin) {
         pile_in[v] = 1;
         pnew = true;
       }
@@ -1059,8 +1062,10 @@ __global__ void k_ds_pile_split(const int32_t *__restrict__ pile, const int32_t 
     int32_t v = -1, d = INT32_MAX;
     if (i < c) {
       v = pile[i];
-      if (!pile_in[v]) v = -1;  // left the pile after it was queued
-      else d = x[v];
+      const uint8_t pin = pile_in[v];
+      const int32_t dv = x[v];  // loaded with the flag, one round trip
+      if (!pin) v = -1;  // left the pile after it was queued
+      else d = dv;
     }
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
     if (near) pile_in[v] = 0;
@@ -1319,8 +1324,10 @@ __global__ void k_dsg_pile_split(const int32_t *__restrict__ x, int32_t *dw, uin
     int32_t v = -1, d = INT32_MAX;
     if (i < c) {
       v = pile[i];
-      if (!pile_in[v]) v = -1;  // left the pile after it was queued
-      else d = x[v];
+      const uint8_t pin = pile_in[v];
+      const int32_t dv = x[v];  // loaded with the flag, one round trip
+      if (!pin) v = -1;  // left the pile after it was queued
+      else d = dv;
     }
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
     if (near) pile_in[v] = 0;

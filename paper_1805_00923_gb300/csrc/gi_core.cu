@@ -1769,10 +1769,17 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
   unsigned long long ml = 0, mh = 0;
   for (int32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < c; i0 += stride) {
     const int32_t i = i0 + lane;
-    int32_t v = -1, d = INT32_MAX;
+    int32_t v = -1, d = INT32_MAX, sm = epoch, dl = 0, dh = 0;
+    uint8_t pin = 0;
     if (i < c) {
       v = B.P[i];
+      // every per-vertex word the split may need, loaded together (one
+      // round trip after v instead of a chain of them behind the branches)
       d = B.x[v];
+      sm = B.s_mark[v];
+      pin = B.pile_in[v];
+      dl = B.deg_l[v];
+      dh = B.deg_h[v];
       B.Pbm[v >> 5] = 0u;  // the whole word: every bit set in it belongs to P
     }
     const bool near = v >= 0 && d < hi, far = v >= 0 && !near;
@@ -1780,17 +1787,17 @@ __global__ void k_dsg_step(DsgBuffers B, int64_t *ctrl, DecideParams p, int64_t 
     if (near) {
       B.snap[v] = d;
       B.snap_h[v] = d;
-      if (B.pile_in[v]) B.pile_in[v] = 0;  // its pile entry is now stale
-      ml += B.deg_l[v];
-      if (B.s_mark[v] != epoch) {
+      if (pin) B.pile_in[v] = 0;  // its pile entry is now stale
+      ml += dl;
+      if (sm != epoch) {
         B.s_mark[v] = epoch;
         snew = true;
-        mh += B.deg_h[v];
+        mh += dh;
       }
     }
     if (far) {
       fmin = min(fmin, d);
-      if (!B.pile_in[v]) {
+      if (!pin) {
         B.pile_in[v] = 1;
         pnew = true;
       }
