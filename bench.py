@@ -285,8 +285,8 @@ def run_rmat22(args, extra=False):
     if not args.no_extras:
         # the tuner's own gain: the same search from the library's default
         # DensePull schedule (no hot-source cache), reported beside the timed one
-        d_s, d_tuned, d_start = gi.autotune(g, "pagerank", start=gi.schedule("dense_pull"), budget=args.tune_budget,
-                                            seed=1)
+        d_s, d_tuned, d_start = gi.autotune(g, "pagerank", start=gi.schedule("dense_pull"),
+                                            budget=2 * args.tune_budget, seed=1)
         tuned["pagerank_from_library_defaults"] = dict(gi.schedule_dict(d_s), tuned_ms=d_tuned, default_ms=d_start)
     # the three PageRank directions of the workload, one timed run each (untimed setup)
     compare = {}
@@ -722,7 +722,7 @@ def run_config_l(args):
     tune_defaults = None
     if not args.no_extras:
         d_s, d_tuned, d_start = gi.autotune(g, "sssp", src=srcs[0], start=gi.schedule("learned", persistent=2),
-                                            budget=args.tune_budget, seed=7)
+                                            budget=2 * args.tune_budget, seed=7)
         tune_defaults = {"schedule": gi.schedule_dict(d_s), "tuned_ms": d_tuned, "start_ms": d_start}
     ss_rule = gi.schedule("hybrid_pull")
     for f, _ in ss_learned._fields_:

@@ -178,11 +178,21 @@ extern "C" int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_sche
       const int which = (int)(rng() % nk);
       const int dirn = (rng() & 1) ? 1 : -1;
       if (which < (int)knobs.size()) {
+        // a neighbouring value, or (every other move) any other value of the
+        // knob, so that a knob whose middle value is worse can still jump
         auto &k = knobs[which];
+        const int nv = (int)k.values.size();
         int pos = 0;
-        while (pos < (int)k.values.size() && k.values[pos] != k.get(top)) ++pos;
-        pos = pos >= (int)k.values.size() ? 0 : pos + dirn;
-        if (pos < 0 || pos >= (int)k.values.size()) continue;
+        while (pos < nv && k.values[pos] != k.get(top)) ++pos;
+        if (rng() & 2) {
+          if (nv < 2) continue;
+          const int cur_pos = pos >= nv ? -1 : pos;
+          do pos = (int)(rng() % nv);
+          while (pos == cur_pos);
+        } else {
+          pos = pos >= nv ? 0 : pos + dirn;
+          if (pos < 0 || pos >= nv) continue;
+        }
         k.set(cand, k.values[pos]);
       } else {
         const float *vals = which == (int)knobs.size() ? alphas : betas;
