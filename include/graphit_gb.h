@@ -613,8 +613,8 @@ int gi_batch_plan_free(gi_batch_plan *p);
  * dst_list (BFS) and, for rule-based BFS hybrids, Beamer's alpha/beta: random
  * candidates for the
  * first third of `budget`
- * trials, then hill climbing around the best (one knob per trial, moved to
- * a neighbouring value or to any other of its values).  Each candidate runs once to
+ * trials, then a coordinate sweep around the best (one knob at a time, each
+ * of its other values in turn, then the next knob).  Each candidate runs once to
  * warm up and is timed (best of 2) with CUDA events on `stream`; a candidate
  * whose output differs from start's (integers bit-exact, ranks beyond 1e-4
  * relative) is rejected.  *best receives the fastest valid schedule, *best_ms

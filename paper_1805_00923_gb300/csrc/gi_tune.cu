@@ -165,6 +165,7 @@ extern "C" int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_sche
   const bool tune_ab = algo == GI_ALGO_BFS && (start->direction == GI_DIR_HYBRID_PULL ||
                                                start->direction == GI_DIR_HYBRID_DPUSH);
   const float alphas[] = {4.f, 8.f, 14.f, 24.f, 48.f}, betas[] = {8.f, 16.f, 24.f, 48.f, 96.f};
+  int sweep_knob = 0, sweep_val = 0;  // position of the coordinate sweep
   for (int32_t trial = 1; trial < budget && st == GI_OK; ++trial) {
     gi_schedule cand = top;
     if (trial < budget / 3) {  // random phase
@@ -173,36 +174,35 @@ extern "C" int gi_autotune(gi_graph *g, int32_t algo, int32_t src, const gi_sche
         cand.alpha = alphas[rng() % 5];
         cand.beta = betas[rng() % 5];
       }
-    } else {  // hill climbing around the best
+    } else {
+      // coordinate sweep around the best: one knob at a time (the
+      // algorithm-specific ones, pushed last, first), each of its other
+      // values in turn, then the next knob (a knob's values are all tried
+      // before another knob moves, so interacting knobs keep their order)
       const int nk = (int)knobs.size() + (tune_ab ? 2 : 0);
-      const int which = (int)(rng() % nk);
-      const int dirn = (rng() & 1) ? 1 : -1;
-      if (which < (int)knobs.size()) {
-        // a neighbouring value, or (every other move) any other value of the
-        // knob, so that a knob whose middle value is worse can still jump
-        auto &k = knobs[which];
-        const int nv = (int)k.values.size();
-        int pos = 0;
-        while (pos < nv && k.values[pos] != k.get(top)) ++pos;
-        if (rng() & 2) {
-          if (nv < 2) continue;
-          const int cur_pos = pos >= nv ? -1 : pos;
-          do pos = (int)(rng() % nv);
-          while (pos == cur_pos);
-        } else {
-          pos = pos >= nv ? 0 : pos + dirn;
-          if (pos < 0 || pos >= nv) continue;
+      bool found = false;
+      for (int guard = 0; guard < 2 * nk && !found; ++guard) {
+        const int which = nk - 1 - (sweep_knob % nk);
+        const int nv = which < (int)knobs.size() ? (int)knobs[which].values.size() : 5;
+        if (sweep_val >= nv) {
+          ++sweep_knob;
+          sweep_val = 0;
+          continue;
         }
-        k.set(cand, k.values[pos]);
-      } else {
-        const float *vals = which == (int)knobs.size() ? alphas : betas;
-        float &f = which == (int)knobs.size() ? cand.alpha : cand.beta;
-        int pos = 0;
-        while (pos < 5 && vals[pos] != f) ++pos;
-        pos = pos >= 5 ? 2 : pos + dirn;
-        if (pos < 0 || pos >= 5) continue;
-        f = vals[pos];
+        const int pos = sweep_val++;
+        if (which < (int)knobs.size()) {
+          auto &k = knobs[which];
+          if (k.values[pos] == k.get(top)) continue;
+          k.set(cand, k.values[pos]);
+        } else {
+          const float *vals = which == (int)knobs.size() ? alphas : betas;
+          float &f = which == (int)knobs.size() ? cand.alpha : cand.beta;
+          if (vals[pos] == f) continue;
+          f = vals[pos];
+        }
+        found = true;
       }
+      if (!found) continue;
     }
     if (cand.t_cta < cand.t_warp) cand.t_cta = cand.t_warp;
     double t = 0.0;
