@@ -1,6 +1,7 @@
 """Host-side pieces of bench.py that need no GPU: the per-level byte model of
-the early-exit BFS pull (checked against a brute-force scan) and the JSON line
-of the CPU reference arm."""
+the early-exit BFS pull (checked against a brute-force scan), the JSON line
+of the CPU reference arm, and the rule that ties a recorded ncu traffic
+figure to the kernel code it was captured on."""
 import json
 import os
 import subprocess
@@ -83,3 +84,42 @@ def test_reference_arm_json_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["config"]["workload"] == "rmat24_bfs_sssp" and d["config"]["sources"] == 64
+
+
+def test_recorded_traffic_follows_the_kernel_code(tmp_path, monkeypatch):
+    """roofline.traffic is read from profiles/traffic.txt only while the code
+    it was captured on is unchanged: comment and blank-line edits keep the
+    kernel hash, an edit of the tile loop or of the edge function drops it."""
+    csrc = tmp_path / "paper_1805_00923_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    real = os.path.join(ROOT, "paper_1805_00923_gb300", "csrc")
+    traverse = open(os.path.join(real, "gi_traverse.cuh")).read()
+    (csrc / "gi_internal.cuh").write_text(open(os.path.join(real, "gi_internal.cuh")).read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    op = "OpMinInt+OpMinIntBounded"
+
+    def hashed(text):
+        (csrc / "gi_traverse.cuh").write_text(text)
+        return bench.kernel_source_hash(op)
+
+    h = hashed(traverse)
+    (tmp_path / "profiles" / "traffic.txt").write_text(f"# hash kernel workload bytes\n{h} kname wl 123 (1 launch)\n")
+    assert bench.recorded_traffic("kname", "wl", op=op) == 123.0
+    assert bench.recorded_traffic("kname", "other", op=op) is None
+
+    line = "constexpr int kBatch = 8;"
+    assert traverse.count(line) == 1
+    assert hashed(traverse.replace(line, line + "  // a note\n\n// another\n")) == h
+    assert bench.recorded_traffic("kname", "wl", op=op) == 123.0
+
+    staged = "u[j] = k < ne ? G.src(idx + e0 + k) : -1;"  # the tile staging loop
+    assert staged in traverse
+    assert hashed(traverse.replace(staged, staged.replace("-1", "-2"), 1)) != h
+    assert bench.recorded_traffic("kname", "wl", op=op) is None
+
+    combine = "__device__ static V combine(V a, V b) { return a < b ? a : b; }"
+    i = traverse.index("struct OpMinInt ")
+    edited = traverse[:i] + traverse[i:].replace(combine, combine.replace("a < b", "a <= b"), 1)
+    assert hashed(edited) != h
+    assert bench.recorded_traffic("kname", "wl", op=op) is None
