@@ -78,6 +78,21 @@ def test_schedule_defaults(lib):
     assert (s.t_warp, s.t_cta, s.rule, s.alpha, s.beta, s.tile_edges) == (32, 256, L.GI_RULE_BEAMER, 14.0, 24.0,
                                                                           2048)
     assert (s.t_heavy, s.persistent, s.hot_cache, s.seg_strategy) == (256, 0, 0, 0)
+    assert (s.delta, s.dst_list) == (0, 1)
+
+
+def test_schedule_binding_fields(lib):
+    """The binding's schedule(): library defaults, a named direction, string
+    enums mapped to the header's values, and no silently ignored field."""
+    import pytest
+    import paper_1805_00923_gb300 as gi
+    from paper_1805_00923_gb300 import _lib as L
+    s = gi.schedule("learned", balance="edge_parallel", rule="ligra", seg_strategy="evc", delta=128, tile_edges=4096)
+    assert s.direction == L.GI_DIR_LEARNED and s.balance == L.GI_BAL_EDGE_PARALLEL
+    assert s.rule == L.GI_RULE_LIGRA and s.seg_strategy == L.GI_SEG_EVC
+    assert (s.delta, s.tile_edges, s.t_warp, s.dst_list) == (128, 4096, 32, 1)
+    with pytest.raises(TypeError):
+        gi.schedule("dense_pull", tile_edge=4096)
 
 
 def test_selector_param_count_matches_oracle(lib):
