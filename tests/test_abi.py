@@ -130,3 +130,33 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+
+
+def test_constants_match_the_header(tmp_path):
+    """Every GI_* constant the header defines has the same value in the
+    binding (the timing classes as its KCLASS table): a C program built
+    against include/graphit_gb.h prints them."""
+    import re
+    import subprocess
+    from paper_1805_00923_gb300 import _lib as L
+    header = open(os.path.join(ROOT, "include", "graphit_gb.h")).read()
+    names = re.findall(r"^#define (GI_[A-Z0-9_]+)[ \t]+\S", header, re.M)
+    assert len(names) > 40
+    lines = ['#include <stdio.h>', '#include "graphit_gb.h"', "int main(void) {"]
+    lines += [f'  printf("{n} %lld\\n", (long long)({n}));' for n in names]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    r = subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                     check=True).stdout.splitlines())
+    for n in names:
+        if n.startswith("GI_KCLASS_"):
+            mine = L.KCLASS[n[len("GI_KCLASS_"):].lower()]
+        else:
+            assert hasattr(L, n), n
+            mine = getattr(L, n)
+        assert int(got[n]) == int(mine), n
