@@ -160,3 +160,47 @@ def test_constants_match_the_header(tmp_path):
             assert hasattr(L, n), n
             mine = getattr(L, n)
         assert int(got[n]) == int(mine), n
+
+
+def test_null_handles_are_argument_errors(lib):
+    """Each entry point that takes a graph, vertexset or plan reports a NULL
+    one as GI_ERR_INVALID_ARG with a message, before any device work (so
+    this runs without a GPU); the free functions take NULL as a no-op."""
+    from paper_1805_00923_gb300 import _lib as L
+    s = L.gi_schedule()
+    lib.gi_schedule_default(ctypes.byref(s))
+    o = L.gi_batch_opts()
+    lib.gi_batch_opts_default(ctypes.byref(o))
+    p, i64, i32, u32, d = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_uint32(), ctypes.c_double()
+    f = ctypes.c_float
+    calls = {
+        "gi_load_csc": lambda: lib.gi_load_csc(None, None, None, None, 0, None),
+        "gi_graph_info": lambda: lib.gi_graph_info(None, ctypes.byref(i64), ctypes.byref(i64), ctypes.byref(i32)),
+        "gi_graph_hot_info": lambda: lib.gi_graph_hot_info(None, ctypes.byref(i32), ctypes.byref(i32), None),
+        "gi_graph_build_segments": lambda: lib.gi_graph_build_segments(None, 2, 0, None),
+        "gi_vset_create": lambda: lib.gi_vset_create(None, 0, 0, None, ctypes.byref(p)),
+        "gi_vset_size": lambda: lib.gi_vset_size(None, ctypes.byref(i64), None),
+        "gi_vset_reps": lambda: lib.gi_vset_reps(None, ctypes.byref(u32)),
+        "gi_vset_to_sparse": lambda: lib.gi_vset_to_sparse(None, None),
+        "gi_edgeset_apply": lambda: lib.gi_edgeset_apply(None, None, None, ctypes.byref(s), 0, None, None, 0, None),
+        "gi_sssp": lambda: lib.gi_sssp(None, 0, None, ctypes.byref(s), None, None),
+        "gi_prepare": lambda: lib.gi_prepare(None, 0, ctypes.byref(s), None),
+        "gi_cc": lambda: lib.gi_cc(None, None, ctypes.byref(s), None, None),
+        "gi_pagerank_delta": lambda: lib.gi_pagerank_delta(None, f(0.85), f(1e-7), 10, None, ctypes.byref(s), None,
+                                                           None),
+        "gi_bc": lambda: lib.gi_bc(None, 0, None, None, 0, ctypes.byref(s), None, None),
+        "gi_pagerank_static": lambda: lib.gi_pagerank_static(None, None, None, 10, 5, f(0.85), 20, None, None),
+        "gi_batch_plan_launch": lambda: lib.gi_batch_plan_launch(None, None),
+        "gi_autotune": lambda: lib.gi_autotune(None, 0, 0, ctypes.byref(s), 4, 1, ctypes.byref(s), ctypes.byref(d),
+                                               ctypes.byref(d), None),
+        "gi_stats_pull_arcs": lambda: lib.gi_stats_pull_arcs(None, 0, ctypes.byref(i64)),
+        "gi_mlp_forward": lambda: lib.gi_mlp_forward(None, None, 4, None, None),
+        "gi_selector_profile": lambda: lib.gi_selector_profile(None, 0, 0, ctypes.byref(s), 16, None, None, None,
+                                                               None),
+    }
+    for name, call in calls.items():
+        assert call() == L.GI_ERR_INVALID_ARG, name
+        assert lib.gi_last_error().startswith(b"invalid argument"), name
+    assert lib.gi_stats_read(99, ctypes.byref(i64), ctypes.byref(i64), None) == L.GI_ERR_INVALID_ARG
+    assert lib.gi_vset_free(None) == L.GI_OK
+    assert lib.gi_batch_plan_free(None) == L.GI_OK
